@@ -1,0 +1,286 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only builds INPUT fields (moduli, eigenstrain, boundary data) for
+the elasticity problem of Section 2.1, Eq. (1a)-(1d).  It contains none of the
+solver's arithmetic (no finite differences, no smoothing, no transfers) and is
+the one module that both the CUDA path's callers and the CPU oracle import.
+
+Field conventions shared by every consumer:
+
+* A grid has ``n = (nx, ny, nz)`` nodes.  In a non-periodic direction the
+  nodes include both boundary planes and ``h = (hi - lo) / (n - 1)``; in a
+  periodic direction ``n`` counts the unique nodes and ``h = (hi - lo) / n``.
+* Scalar fields are numpy arrays of shape ``(nz, ny, nx)`` (x fastest), so a
+  node's flat index is ``i + nx * (j + ny * k)``.
+* Vector fields are ``(3, nz, ny, nx)``; symmetric second-order tensors
+  (eigenstrain, mean strain) are 6 tensor components in the order
+  11, 22, 33, 23, 31, 12 (tensor shears, not doubled).
+* Isotropic moduli are ``(2, nz, ny, nx)`` = (lambda, mu).  General moduli are
+  the 21 upper-triangle entries of the 6x6 Voigt matrix (Section 4.3, the
+  Voigt form of the cubic tensor, Voigt order 11, 22, 33, 23, 31, 12), stored
+  row by row: C11 C12 C13 C14 C15 C16 C22 C23 ... C66, shape
+  ``(21, nz, ny, nx)``.
+* Boundary faces are numbered 0..5 = -x, +x, -y, +y, -z, +z; each face carries
+  one (type, value) pair per displacement component.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+from typing import Optional
+
+import numpy as np
+
+# boundary-row types (Section 2.1, Eq. 1b-1d)
+DIRICHLET = 1
+TRACTION = 2
+NEUMANN = 3
+
+MODULI_ISO = 2
+MODULI_GEN21 = 21
+
+_VOIGT = ((0, 5, 4), (5, 1, 3), (4, 3, 2))
+
+
+@dataclasses.dataclass
+class Problem:
+    """One elasticity problem on a single uniform node grid."""
+    n: tuple                      # (nx, ny, nz)
+    periodic: tuple = (False, False, False)
+    lo: tuple = (0.0, 0.0, 0.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+    moduli_kind: int = MODULI_ISO
+    moduli: Optional[np.ndarray] = None          # (2|21, nz, ny, nx)
+    eigenstrain: Optional[np.ndarray] = None     # (6, nz, ny, nx)
+    body_force: Optional[np.ndarray] = None      # (3, nz, ny, nx)
+    mean_strain: Optional[np.ndarray] = None     # (6,), fully periodic grids only
+    # bc[face][comp] = (type, uniform value)
+    bc: list = dataclasses.field(default_factory=list)
+    dirichlet_values: Optional[np.ndarray] = None  # (3, nz, ny, nx) overrides face values
+    # face_values[f] = (3, nz, ny, nx): per-node boundary data of face f (its
+    # Dirichlet value, traction or normal derivative), read on that face only
+    face_values: Optional[dict] = None
+    name: str = ""
+
+    @property
+    def h(self):
+        out = []
+        for d in range(3):
+            span = self.hi[d] - self.lo[d]
+            out.append(span / self.n[d] if self.periodic[d] else span / (self.n[d] - 1))
+        return tuple(out)
+
+    def coords(self):
+        """Node coordinates X, Y, Z, each (nz, ny, nx)."""
+        h = self.h
+        ax = [self.lo[d] + h[d] * np.arange(self.n[d]) for d in range(3)]
+        Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        return X, Y, Z
+
+
+def lame(E, nu):
+    E = np.asarray(E, dtype=np.float64)
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    return lam, mu
+
+
+def tanh_profile(s, w):
+    """Diffuse indicator: 1 well inside (s < 0), 0 well outside, width w."""
+    return 0.5 * (1.0 - np.tanh(2.0 * s / w))
+
+
+def all_faces(kind, value=0.0):
+    return [[(kind, value)] * 3 for _ in range(6)]
+
+
+# --------------------------------------------------------------------------
+# moduli tensors used only to build inputs (Section 4.3)
+# --------------------------------------------------------------------------
+
+def cubic_voigt(c11, c12, c44):
+    V = np.zeros((6, 6))
+    V[:3, :3] = c12
+    for a in range(3):
+        V[a, a] = c11
+        V[a + 3, a + 3] = c44
+    return V
+
+
+def voigt_to_tensor(V):
+    T = np.zeros((3, 3, 3, 3))
+    for i, j, k, l in itertools.product(range(3), repeat=4):
+        T[i, j, k, l] = V[_VOIGT[i][j], _VOIGT[k][l]]
+    return T
+
+
+def tensor_to_upper21(T):
+    V = np.zeros((6, 6))
+    for i, j, k, l in itertools.product(range(3), repeat=4):
+        V[_VOIGT[i][j], _VOIGT[k][l]] = T[i, j, k, l]
+    return np.array([V[a, b] for a in range(6) for b in range(a, 6)])
+
+
+def rotate_tensor(T, R):
+    """Rotated modulus tensor of Section 4.3: C'_pqst = R_pi R_qj C_ijkl R_sk R_tl."""
+    return np.einsum("pi,qj,sk,tl,ijkl->pqst", R, R, R, R, T)
+
+
+def random_rotation(rng):
+    """Uniform random rotation from a uniform unit quaternion (Shoemake, 1992)."""
+    u1, u2, u3 = rng.random(3)
+    a, b = np.sqrt(1.0 - u1), np.sqrt(u1)
+    q = np.array([a * np.sin(2 * np.pi * u2), a * np.cos(2 * np.pi * u2),
+                  b * np.sin(2 * np.pi * u3), b * np.cos(2 * np.pi * u3)])
+    x, y, z, w = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def iso_to_upper21(lam, mu):
+    """Isotropic (lambda, mu) fields written as the 21 Voigt components."""
+    lam = np.asarray(lam)
+    out = np.zeros((21,) + lam.shape)
+    k = 0
+    for a in range(6):
+        for b in range(a, 6):
+            if a < 3 and b < 3:
+                out[k] = lam + (2.0 * mu if a == b else 0.0)
+            elif a == b:
+                out[k] = mu
+            k += 1
+    return out
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+def eshelby_sphere(n=33, radius=0.2, width_cells=3.0, E_matrix=1.0, E_incl=2.0, nu=0.3,
+                   eps_star=1e-3, centre=(0.5, 0.5, 0.5)):
+    """Spherical Eshelby inhomogeneity on the unit cube (Section 4.1 analogue):
+    tanh-blended isotropic moduli, eigenstrain eps_star * phi * I, u = 0 on all faces."""
+    p = Problem(n=(n, n, n), name=f"eshelby_sphere_{n}")
+    X, Y, Z = p.coords()
+    h = p.h[0]
+    r = np.sqrt((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2)
+    phi = tanh_profile(r - radius, width_cells * h)
+    lam, mu = lame(E_matrix * (1.0 - phi) + E_incl * phi, nu)
+    p.moduli_kind = MODULI_ISO
+    p.moduli = np.stack([lam, mu])
+    eps = np.zeros((6,) + phi.shape)
+    eps[0] = eps[1] = eps[2] = eps_star * phi
+    p.eigenstrain = eps
+    p.bc = all_faces(DIRICHLET, 0.0)
+    return p
+
+
+def polycrystal(n=257, grains=20, seed=0, c11=1.68, c12=1.21, c44=0.75, width_cells=4.0,
+                strain=1e-3):
+    """Voronoi polycrystal (Section 4.3 analogue): rotated cubic grains blended by the
+    linear mixture rule over tanh grain-boundary profiles; u_x = -+strain/2 on the x
+    faces, zero shear traction there, traction-free y and z faces."""
+    rng = np.random.default_rng(seed)
+    p = Problem(n=(n, n, n), name=f"polycrystal_{n}_{grains}g")
+    centres = rng.random((grains, 3))
+    rots = [random_rotation(rng) for _ in range(grains)]
+    base = voigt_to_tensor(cubic_voigt(c11, c12, c44))
+    grain_c = np.stack([tensor_to_upper21(rotate_tensor(base, R)) for R in rots])
+    h = p.h[0]
+    w = width_cells * h
+    X, Y, Z = p.coords()
+    shape = X.shape
+    # distance-squared to every centre, one z-slab at a time to bound memory
+    C = np.zeros((21,) + shape)
+    for k0 in range(0, shape[0], 16):
+        sl = slice(k0, min(shape[0], k0 + 16))
+        pts = np.stack([X[sl], Y[sl], Z[sl]], axis=-1)
+        d2 = np.stack([np.sum((pts - c) ** 2, axis=-1) for c in centres])
+        nearest = np.argmin(d2, axis=0)
+        cn = centres[nearest]
+        d2n = np.min(d2, axis=0)
+        s = np.empty_like(d2)
+        for g in range(grains):
+            sep = np.linalg.norm(centres[g] - cn, axis=-1)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                s[g] = np.where(sep > 0, (d2[g] - d2n) / (2.0 * np.where(sep > 0, sep, 1.0)), np.inf)
+        s_other = np.where(np.arange(grains)[:, None, None, None] == nearest[None], np.inf, s)
+        s_near = -np.min(s_other, axis=0)
+        s = np.where(np.arange(grains)[:, None, None, None] == nearest[None], s_near[None], s)
+        eta = tanh_profile(s, w)
+        tot = eta.sum(axis=0)
+        C[:, sl] = np.einsum("gc,g...->c...", grain_c, eta) / tot
+    p.moduli_kind = MODULI_GEN21
+    p.moduli = C
+    bc = all_faces(TRACTION, 0.0)
+    bc[0] = [(DIRICHLET, -0.5 * strain), (TRACTION, 0.0), (TRACTION, 0.0)]
+    bc[1] = [(DIRICHLET, +0.5 * strain), (TRACTION, 0.0), (TRACTION, 0.0)]
+    p.bc = bc
+    return p
+
+
+def penny_crack(n=65, radius=0.25, width=3.0 / 256, E=1.0, nu=0.3, soft=1e-2, strain=1e-3):
+    """Penny-shaped diffuse crack (Section 4.2 analogue) in the plane z = 0.5:
+    E is reduced to soft * E inside the crack profile, soft capped at 1 % of the
+    matrix modulus as Section 4.2 does for numerical stability; u_z = -+strain/2 on
+    the z faces with zero shear traction there, traction-free x and y faces."""
+    p = Problem(n=(n, n, n), name=f"penny_crack_{n}")
+    X, Y, Z = p.coords()
+    rho = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+    d = np.sqrt(np.maximum(rho - radius, 0.0) ** 2 + (Z - 0.5) ** 2)
+    phi = 1.0 - np.tanh(d / width) ** 2
+    lam, mu = lame(E * ((1.0 - phi) + soft * phi), nu)
+    p.moduli_kind = MODULI_ISO
+    p.moduli = np.stack([lam, mu])
+    bc = all_faces(TRACTION, 0.0)
+    bc[4] = [(TRACTION, 0.0), (TRACTION, 0.0), (DIRICHLET, -0.5 * strain)]
+    bc[5] = [(TRACTION, 0.0), (TRACTION, 0.0), (DIRICHLET, +0.5 * strain)]
+    p.bc = bc
+    return p
+
+
+def ellipsoid_rve(n, seed, nu=0.3, width_cells=3.0, strain_norm=1e-3):
+    """Periodic RVE with 1-8 random ellipsoidal inclusions (stiffness ratio 0.5-4) under
+    a random symmetric mean strain of Frobenius norm strain_norm.  ``n`` counts the
+    node planes including the duplicated periodic face, so the grid keeps n - 1
+    unique nodes per direction."""
+    rng = np.random.default_rng(seed)
+    m = n - 1
+    p = Problem(n=(m, m, m), periodic=(True, True, True), name=f"rve_{n}_{seed}")
+    X, Y, Z = p.coords()
+    h = p.h[0]
+    w = width_cells * h
+    E = np.ones(X.shape)
+    for _ in range(int(rng.integers(1, 9))):
+        axes = rng.uniform(0.05, 0.2, 3)
+        R = random_rotation(rng)
+        c = rng.random(3)
+        ratio = rng.uniform(0.5, 4.0)
+        best = None
+        for sh in itertools.product((-1.0, 0.0, 1.0), repeat=3):   # periodic images
+            dx = X - c[0] - sh[0]
+            dy = Y - c[1] - sh[1]
+            dz = Z - c[2] - sh[2]
+            q = [R[0, a] * dx + R[1, a] * dy + R[2, a] * dz for a in range(3)]
+            rad = np.sqrt(sum((q[a] / axes[a]) ** 2 for a in range(3)))
+            s = (rad - 1.0) * axes.min()
+            best = s if best is None else np.minimum(best, s)
+        phi = tanh_profile(best, w)
+        E = E * (1.0 - phi) + ratio * phi
+    lam, mu = lame(E, nu)
+    p.moduli_kind = MODULI_ISO
+    p.moduli = np.stack([lam, mu])
+    G = rng.normal(size=(3, 3))
+    S = 0.5 * (G + G.T)
+    S *= strain_norm / np.linalg.norm(S)
+    p.mean_strain = np.array([S[0, 0], S[1, 1], S[2, 2], S[1, 2], S[2, 0], S[0, 1]])
+    p.bc = []
+    return p
+
+
+def batch_sizes(count=256, seed=0, choices=(33, 65, 97, 129)):
+    rng = np.random.default_rng(seed)
+    return [int(v) for v in rng.choice(choices, size=count)]
