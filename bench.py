@@ -1,0 +1,365 @@
+"""Benchmark: elasticity solves per second at a relative residual of 1e-8.
+
+Workload: 257^3-node Voronoi polycrystal (20 grains, rotated cubic moduli
+C11=1.68 C12=1.21 C44=0.75, 4h grain-boundary width), u_x = -+0.5e-3 on the x
+faces with zero shear traction there, traction-free y/z faces.  One step = one
+full solve from a zero initial field to ||r||/||r0|| <= 1e-8 with the mixed
+path (FP32 V(2,2) cycles inside FP64 iterative refinement).  The plain FP64
+V-cycle solve of the same problem is timed beside it.
+
+`python bench.py --gpus N --steps K --warmup W` prints one JSON line on rank 0.
+Under torchrun each rank solves its own copy (independent replicas, weak
+scaling).  `--impl reference` times the CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Solves/s at 1e-8 rel. residual, mixed vs FP64; stencil HBM GB/s; p99 latency"
+UNIT = "solves/s"
+FALLBACK_HBM_GBS = 6800.0
+# nominal FP64 vector throughput of the part (1.25 TFLOP/s dense FP64)
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=257)
+    ap.add_argument("--grains", type=int, default=20)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip e2e and the CPU baseline")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# algorithmic bytes per node of one finest-level launch (see the design notes):
+# a half-sweep reads all moduli (neighbours of the active colour are the other
+# colour), all of u, f of the active rows, and writes the active rows of u; the
+# residual reads moduli, u and f and writes r.
+def alg_bytes_per_node(cls, K):
+    if cls == "sweep32":
+        return 4 * K + 12 + 6 + 6
+    if cls == "sweep64":
+        return 8 * K + 24 + 12 + 12
+    if cls == "resid64_mixed":      # FP64 residual written as FP32
+        return 8 * K + 24 + 24 + 12
+    if cls == "resid64":
+        return 8 * K + 24 + 24 + 24
+    return 4 * K + 12 + 12 + 12
+
+
+def flops_per_node_resid64(K):
+    # interior row of the general stencil: gradient 18, second differences 63,
+    # modulus-gradient term 3*3*6*4, modulus term 81*2, residual 3
+    return 18 + 63 + 216 + 162 + 3 if K == 21 else 18 + 63 + 60 + 3
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample_seconds_per_node(problem, slab=34):
+    """Time one oracle residual evaluation on a z-slab of the workload; return
+    seconds per node and a description of the sample."""
+    from oracle import stencil as S
+    from paper_2001_04789_gb300 import microstructure as M
+    nz = min(slab, problem.n[2])
+    sub = M.Problem(n=(problem.n[0], problem.n[1], nz), lo=problem.lo,
+                    hi=(problem.hi[0], problem.hi[1], problem.lo[2] + problem.h[2] * (nz - 1)))
+    sub.moduli_kind = problem.moduli_kind
+    sub.moduli = np.ascontiguousarray(problem.moduli[:, :nz])
+    sub.bc = problem.bc
+    lev = S.level_from_problem(sub)
+    u = np.random.default_rng(0).normal(size=(3,) + lev.shape) * 1e-4
+    f = np.zeros_like(u)
+    t = time.perf_counter()
+    S.residual(lev, u, f)
+    dt = time.perf_counter() - t
+    nodes = lev.shape[0] * lev.shape[1] * lev.shape[2]
+    return dt / nodes, f"one oracle FP64 residual evaluation on a {lev.n[0]}x{lev.n[1]}x{nz} slab " \
+                       f"({nodes} nodes) of the workload, {dt:.2f} s"
+
+
+def cpu_solves_per_second(sec_per_node, n_nodes, cycles, nu1=2, nu2=2):
+    # the oracle's half-sweep evaluates every row, so one V(nu1,nu2) cycle costs
+    # 2(nu1+nu2)+1 finest-level residual evaluations; coarser levels add 1/7 + ...
+    per_cycle = (2 * (nu1 + nu2) + 1) * (1.0 + 1.0 / 7.0)
+    evals = (cycles + 1) * per_cycle
+    return 1.0 / (sec_per_node * n_nodes * evals), evals
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from paper_2001_04789_gb300 import microstructure as M
+    p = M.polycrystal(args.n, grains=args.grains, seed=0)
+    cycles = 23  # V(2,2) cycles of the plain FP64 solve of this workload (same algorithm)
+    vals = []
+    samples = []
+    for s in range(args.warmup + args.steps):
+        spn, desc = oracle_sample_seconds_per_node(p)
+        v, evals = cpu_solves_per_second(spn, p.n[0] * p.n[1] * p.n[2], cycles)
+        if s >= args.warmup:
+            vals.append(v)
+            samples.append(desc)
+    value = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"polycrystal {args.n}^3 nodes, {args.grains} grains, rotated cubic, "
+                                  "mixed Dirichlet/traction", "inputs": "larger than L2"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": samples[-1] + f"; scaled to {cycles} V(2,2) cycles"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local = dist_setup()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2001_04789_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2001_04789_gb300 import elas as E
+    from paper_2001_04789_gb300 import microstructure as M
+
+    p = M.polycrystal(args.n, grains=args.grains, seed=0)
+    N = p.n[0] * p.n[1] * p.n[2]
+    K = p.moduli_kind
+    ctx = E.Context(local)
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    stream = ctx.stream
+
+    # warm-up (the first solve also builds the hierarchy data)
+    for _ in range(args.warmup):
+        info = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200)
+    # FP64 reference solve of the same problem
+    fp64_times, fp64_info = [], None
+    for _ in range(args.fp64_steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        fp64_info = g.solve(precision=E.FP64, rel_tol=1e-8, max_cycles=200)
+        torch.cuda.synchronize()
+        fp64_times.append(time.perf_counter() - t)
+
+    # timed region: K mixed solves, device time from events on the solver's stream
+    ctx.profile(True)
+    launches0 = E.launch_count()
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    per = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        info = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200)
+        b.record(stream)
+        per.append((a, b))
+        if info["status"] != 0:
+            raise RuntimeError(f"solve failed: {info}")
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if dist:
+        dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    launches = E.launch_count() - launches0
+    lat = sorted(a.elapsed_time(b) for a, b in per)
+    prof = {name: ctx.profile_read(cls) for name, cls in
+            [("sweep32", E.PROF_SWEEP32_L0), ("resid64", E.PROF_RESID64_L0), ("resid32", E.PROF_RESID32_L0)]}
+    ctx.profile(False)
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / elapsed
+    rel64, _ = g.query_residual()
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.quick and args.e2e_steps > 0:
+        host_mod = torch.from_numpy(np.ascontiguousarray(p.moduli)).pin_memory()
+        host_u = torch.empty((3,) + g.shape, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            g.set_moduli_from(host_mod)
+            info_e = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200)
+            g.displacement_into(host_u)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t
+        e2e = {"value": world * args.e2e_steps / te if not dist else None, "unit": UNIT,
+               "h2d_bytes_per_step": int(host_mod.numel() * 8), "d2h_bytes_per_step": int(host_u.numel() * 8)}
+        if dist:
+            tt = torch.tensor([te], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * args.e2e_steps / float(tt.item())
+
+    if rank != 0:
+        return
+
+    # roofline of the dominant finest-level kernel class
+    hbm, peak_kind = measured_peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, cnt = prof[dom]
+    avg_s = (ms / max(cnt, 1)) / 1000.0
+    if dom == "resid64":
+        flops = flops_per_node_resid64(K) * N
+        achieved = flops / avg_s / 1e12
+        roof = {"kernel": "k_residual<double,float> (finest level, FP64 residual of the refinement)",
+                "bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 rate of the part (no measured FP64 peak available)",
+                "launches": cnt, "avg_ms": avg_s * 1e3,
+                "hbm_gbs": alg_bytes_per_node("resid64_mixed", K) * N / avg_s / 1e9}
+    else:
+        bpn = alg_bytes_per_node(dom, K)
+        achieved = bpn * N / avg_s / 1e9
+        roof = {"kernel": f"{dom} (finest level)", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak_source": f"{peak_kind} copy bandwidth", "launches": cnt, "avg_ms": avg_s * 1e3}
+    kernels = {}
+    for name, (ms_k, cnt_k) in prof.items():
+        if cnt_k:
+            avg = ms_k / cnt_k / 1000.0
+            key = {"sweep32": "sweep32", "resid64": "resid64_mixed", "resid32": "resid32"}[name]
+            kernels[name] = {"launches": cnt_k, "total_ms": ms_k, "avg_ms": avg * 1e3,
+                             "alg_GBs": alg_bytes_per_node(key, K) * N / avg / 1e9,
+                             "share_of_timed": ms_k / (elapsed * 1000.0 / world)}
+
+    cpu = None
+    if not args.quick and not args.no_cpu_baseline and world == 1:
+        spn, desc = oracle_sample_seconds_per_node(p)
+        v, evals = cpu_solves_per_second(spn, N, fp64_info["cycles"])
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": desc + f"; scaled to {fp64_info['cycles']} V(2,2) cycles "
+                                f"({evals:.0f} residual evaluations) of the plain FP64 solve"}
+
+    fp64_value = world / statistics.median(fp64_times) if fp64_times else None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed * 1000.0 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"polycrystal {args.n}^3 nodes ({N} nodes, {3 * N} DOF), {args.grains} grains, "
+                               "rotated cubic C11=1.68 C12=1.21 C44=0.75, GB width 4h, u_x=-+0.5e-3 on x faces, "
+                               "traction-free elsewhere; V(2,2) red-black block GS",
+                   "precision": "FP32 V-cycle inside FP64 iterative refinement",
+                   "inputs": "larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+        "cycles": info["cycles"], "rel_residual": info["rel_residual"], "rel_residual_fp64_check": rel64,
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "fp64": {"value": fp64_value, "unit": UNIT, "cycles": fp64_info["cycles"] if fp64_info else None,
+                 "seconds": statistics.median(fp64_times) if fp64_times else None},
+        "mixed_over_fp64": value / fp64_value if fp64_value else None,
+        "dof_updates_per_s": value * 3 * N * 2 * 4 * (info["cycles"]),
+        "roofline": roof, "kernels": kernels, "gpu_launches": int(launches),
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
+    }
+    print(json.dumps(out), flush=True)
+    g.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * elas.h -- C ABI of the GB300 matrix-free geometric-multigrid elasticity solver.
+ *
+ * Solves the node-centred finite-difference form of static linear elasticity
+ * with eigenstrain (Runnels et al., "Massively parallel finite difference
+ * elasticity using block-structured adaptive mesh refinement with a geometric
+ * multigrid solver", Section 2.1, Eq. 1a-1d):
+ *
+ *     d/dx_j [ C_ijkl(x) (du_k/dx_l - eps0_kl) ] = -b_i        in the interior
+ *     u_i = u0_i                                               (Dirichlet, Eq. 1b)
+ *     C_ijkl (du_k/dx_l - eps0_kl) n_j = t0_i                  (traction,  Eq. 1c)
+ *     du_i/dx_j n_j = du0_i                                    (Neumann,   Eq. 1d)
+ *
+ * with the product-rule split of Section 2.1.1, the homogeneous/inhomogeneous
+ * split D_H(u) = D(u) - D(0), boundary conditions as boundary-operator rows whose
+ * data enter only through the right-hand side (Section 2.1), and a geometric
+ * multigrid V-cycle over coarsened levels (Section 3.1) with trilinear
+ * interpolation and power-of-two restriction (Section 3.2).
+ *
+ * Conventions shared by every call:
+ *   - A grid has n[0] x n[1] x n[2] nodes, x fastest: node p = i + n0 (j + n1 k).
+ *     A non-periodic direction includes both boundary planes, h = (hi-lo)/(n-1);
+ *     a periodic direction counts unique nodes, h = (hi-lo)/n.
+ *   - Vector fields are 3 planes of N doubles (structure of arrays): u_x, u_y, u_z.
+ *   - Isotropic moduli (kind 2): 2 planes lambda, mu.  General moduli (kind 21):
+ *     the 21 upper-triangle entries of the 6x6 Voigt matrix in Voigt order
+ *     11,22,33,23,31,12, row by row (C11 C12 .. C16 C22 .. C66), one plane each.
+ *   - Symmetric tensors (eigenstrain, mean strain): 6 tensor components
+ *     11,22,33,23,31,12 (shears not doubled).
+ *   - Faces 0..5 = -x,+x,-y,+y,-z,+z.  Boundary types per (face, component):
+ *     ELAS_BC_DIRICHLET, ELAS_BC_TRACTION, ELAS_BC_NEUMANN; periodic directions
+ *     have no faces.
+ *   - memspace: ELAS_HOST for host pointers (copied during the call),
+ *     ELAS_DEVICE for device pointers on the context's device (read during the
+ *     call only, ordered on the context's stream).
+ *   - Every function returns ELAS_OK (0) or a negative error code; the message of
+ *     the last error on a context is returned by elas_last_error.
+ *   - The library owns all device memory it allocates, through the allocator
+ *     given at context creation (cudaMallocAsync on the context's stream when
+ *     none is given).  Caller buffers are never retained after a call returns.
+ *   - All device work is ordered on the context's stream; calls return after
+ *     that work has completed unless stated otherwise.  A grid must not be used
+ *     from two host threads at once; separate contexts are independent.
+ */
+#ifndef ELAS_H
+#define ELAS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define ELAS_OK                 0
+#define ELAS_ERR_INVALID_ARG   -1
+#define ELAS_ERR_OUT_OF_BUDGET -2   /* HBM budget of the context would be exceeded */
+#define ELAS_ERR_NOT_CONVERGED -3   /* max_cycles reached above the tolerance */
+#define ELAS_ERR_DIVERGED      -4   /* non-finite or exploding residual */
+#define ELAS_ERR_DEVICE        -5   /* a CUDA call failed */
+#define ELAS_ERR_ALLOC         -6   /* the allocator returned NULL */
+#define ELAS_ERR_STATE         -7   /* call out of order (e.g. solve before moduli) */
+
+#define ELAS_HOST   0
+#define ELAS_DEVICE 1
+
+#define ELAS_BC_DIRICHLET 1
+#define ELAS_BC_TRACTION  2
+#define ELAS_BC_NEUMANN   3
+
+#define ELAS_MODULI_ISO   2
+#define ELAS_MODULI_GEN21 21
+
+#define ELAS_PRECISION_FP64  0   /* every level in FP64 */
+#define ELAS_PRECISION_MIXED 1   /* FP32 V-cycle inside FP64 iterative refinement */
+
+typedef struct elas_ctx_s*  elas_ctx;
+typedef struct elas_grid_s* elas_grid;
+
+/* Device-memory allocator.  alloc returns a device pointer aligned to at least
+ * 256 bytes, or NULL; free releases it.  Both receive the context's stream. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user, void* stream);
+    void  (*free)(void* ptr, size_t bytes, void* user, void* stream);
+    void* user;
+} elas_allocator;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold (0 = no cap); grid creation fails with
+ * ELAS_ERR_OUT_OF_BUDGET beyond it.  alloc may be NULL.  stream is a
+ * cudaStream_t (NULL = a stream created and owned by the context). */
+int  elas_ctx_create(elas_ctx* out, int device, size_t hbm_budget_bytes,
+                     const elas_allocator* alloc, void* stream);
+int  elas_ctx_destroy(elas_ctx ctx);
+const char* elas_last_error(elas_ctx ctx);
+/* Bytes currently held by the context. */
+size_t elas_ctx_bytes_in_use(elas_ctx ctx);
+
+typedef struct {
+    int    n[3];          /* nodes per direction (see conventions)          */
+    int    periodic[3];   /* 1 = periodic direction                          */
+    double lo[3], hi[3];  /* domain corners                                  */
+    int    moduli_kind;   /* ELAS_MODULI_ISO or ELAS_MODULI_GEN21            */
+    int    mixed;         /* 1 = also allocate the FP32 hierarchy            */
+} elas_grid_desc;
+
+/* Create a grid and its multigrid hierarchy (Section 3.1: levels below 0,
+ * coarsened by 2 while every direction stays coarsenable and some direction has
+ * more than 5 nodes).  Requires n >= 3 per non-periodic direction, n >= 4 per
+ * periodic one.  All boundary types default to Dirichlet 0. */
+int  elas_grid_create(elas_ctx ctx, const elas_grid_desc* desc, elas_grid* out);
+int  elas_grid_destroy(elas_grid g);
+/* Number of multigrid levels and the node counts of one of them. */
+int  elas_grid_levels(elas_grid g, int* nlevels);
+int  elas_grid_level_dims(elas_grid g, int level, int n[3]);
+/* Device bytes the grid holds. */
+size_t elas_grid_bytes(elas_grid g);
+/* Device bytes a grid with this descriptor would hold (for admission control). */
+size_t elas_grid_bytes_estimate(const elas_grid_desc* desc);
+
+/* Moduli of the finest level: kind x N doubles (Section 2.1.1; general moduli as
+ * stored per point in Section 4.3).  Coarse levels take the restriction of the
+ * stored components. */
+int  elas_set_moduli(elas_grid g, const double* comps, int memspace);
+/* Eigenstrain eps0 (Eq. 1a), 6 x N doubles, or NULL for none. */
+int  elas_set_eigenstrain(elas_grid g, const double* eps6, int memspace);
+/* Body force b (Eq. 1a), 3 x N doubles, or NULL for none. */
+int  elas_set_body_force(elas_grid g, const double* b3, int memspace);
+/* Mean strain E of a fully periodic grid: u = E x + u~, u~ periodic. */
+int  elas_set_mean_strain(elas_grid g, const double eps6[6]);
+/* Boundary type and uniform datum of (face, component): the prescribed
+ * displacement (Eq. 1b), traction (Eq. 1c) or normal derivative (Eq. 1d). */
+int  elas_set_bc(elas_grid g, int face, int comp, int type, double value);
+/* Per-node boundary data of a face: 3 x N doubles over the whole grid, read on
+ * that face only; NULL restores the uniform values. */
+int  elas_set_face_values(elas_grid g, int face, const double* values, int memspace);
+
+typedef struct {
+    int    precision;     /* ELAS_PRECISION_FP64 or ELAS_PRECISION_MIXED          */
+    double rel_tol;       /* stop when ||r||_2 / ||r_0||_2 <= rel_tol               */
+    int    max_cycles;    /* V-cycles (FP64) or refinement steps (mixed)           */
+    int    nu1, nu2;      /* pre / post smoothing sweeps (one sweep = red + black) */
+    int    warm_start;    /* 1 = start from the current displacement              */
+    int    fixed_cycles;  /* > 0: run exactly this many cycles, ignore rel_tol     */
+    int    use_graph;     /* 1 = replay the cycle as a captured CUDA graph         */
+} elas_solve_opts;
+
+#define ELAS_HISTORY 128
+typedef struct {
+    int    status;                     /* ELAS_OK, ELAS_ERR_NOT_CONVERGED, ...        */
+    int    cycles;                     /* coarse-grid corrections performed           */
+    double rel_residual;               /* final ||r||/||r_0||, FP64 residual           */
+    double r0;                         /* ||r_0||: residual of the Dirichlet-only field */
+    int    nlam;                       /* number of free rigid modes                  */
+    double lam[6];                     /* equilibrating-load coefficients             */
+    double seconds;                    /* wall time of the solve                      */
+    double rel_history[ELAS_HISTORY];  /* relative residual before each correction    */
+} elas_solve_info;
+
+void elas_solve_opts_default(elas_solve_opts* o);
+
+/* Solve D_H(u) = -(D(0) + b) with the boundary rows (Section 2.1.1).  Each cycle:
+ * nu1 red-black block sweeps, the FP64 residual and its norm, stop if small
+ * enough, restriction, recursive cycle, trilinear correction, nu2 sweeps
+ * (Section 3.1).  Problems with free rigid modes get an equilibrating load
+ * lambda W (W = the free rigid modes) and u has its rigid part removed.
+ * Returns info->status. */
+int  elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info);
+
+/* Displacement of the finest level, 3 x N doubles (the fluctuation u~ on a
+ * periodic grid with mean strain). */
+int  elas_get_displacement(elas_grid g, double* out, int memspace);
+int  elas_set_displacement(elas_grid g, const double* in, int memspace);
+/* FP64 residual of the current displacement: ||r||_2 / ||r_0||_2 and ||r||_2. */
+int  elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2);
+
+/* ---- single operations of the path, for testing and benchmarking --------------
+ * All take DEVICE pointers to FP64 (precision 0) or FP32 (precision 1) arrays of
+ * the named level (3 x N_level unless stated) and run on the context's stream. */
+
+/* out = A u on every row of `level`: interior and traction rows (Section 2.1.1
+ * product rule, half-cell closure of Eq. 1c), Neumann rows, u itself on
+ * Dirichlet rows. */
+int  elas_op_apply(elas_grid g, int level, int precision, const void* u, void* out);
+/* r = f - A u (0 on Dirichlet rows); *sumsq = sum r^2 (FP64 reduction). */
+int  elas_op_residual(elas_grid g, int level, int precision, const void* u, const void* f,
+                      void* r, double* sumsq);
+/* One red-black sweep (red then black, Jacobi within a colour), in place on u. */
+int  elas_op_sweep(elas_grid g, int level, int precision, void* u, const void* f);
+/* fc = R r: volume-weighted full weighting to level+1 (Section 3.2); 0 on
+ * Dirichlet rows of the coarse level. */
+int  elas_op_restrict(elas_grid g, int level, int precision, const void* r, void* fc);
+/* u += P e: trilinear interpolation of the level+1 correction (Section 3.2),
+ * added on non-Dirichlet rows. */
+int  elas_op_prolong_add(elas_grid g, int level, int precision, const void* ec, void* u);
+/* Right-hand side of the finest level (FP64, 3 x N) from moduli, eigenstrain,
+ * body force, mean strain and boundary data. */
+int  elas_op_rhs(elas_grid g, double* f_out);
+/* Exact solve of the coarsest level (dense FP64 inverse built at setup). */
+int  elas_op_bottom(elas_grid g, int precision, const void* f, void* u);
+
+/* ---- measurement -------------------------------------------------------------
+ * With profiling enabled, every finest-level launch of the smoother and of the
+ * residual inside elas_solve is bracketed by CUDA events on the context's stream;
+ * elas_profile_read returns the summed device time and the launch count per
+ * kernel class since the last enable.  elas_launch_count counts every kernel this
+ * library has launched since it was loaded (all contexts). */
+#define ELAS_PROF_SWEEP64_L0 0   /* FP64 red or black half-sweep, finest level   */
+#define ELAS_PROF_SWEEP32_L0 1   /* FP32 half-sweep, finest level (mixed path)    */
+#define ELAS_PROF_RESID64_L0 2   /* FP64 residual + norms, finest level           */
+#define ELAS_PROF_RESID32_L0 3   /* FP32 residual, finest level (mixed path)      */
+#define ELAS_PROF_CLASSES    4
+int  elas_profile_enable(elas_ctx ctx, int enable);
+int  elas_profile_read(elas_ctx ctx, int kernel_class, double* total_ms, long long* launches);
+unsigned long long elas_launch_count(void);
+
+/* ---- batches ---------------------------------------------------------------
+ * Solve n independent grids of the same context, all in flight at once on the
+ * context's stream (one launch per phase covers every grid).  info has n entries. */
+int  elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts,
+                      elas_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELAS_H */

@@ -237,6 +237,10 @@ def correct(levels, l, u, r, nu1, nu2):
     """Coarse-grid correction: restrict r, cycle on the next level from zero, add the
     interpolated correction on non-Dirichlet rows."""
     L = levels[l]
+    if l == len(levels) - 1:
+        # a single-level hierarchy: the correction is the exact (bordered) solve
+        u += bottom_solve(L, r)
+        return
     fc = restrict(r, L.level)
     Lc = levels[l + 1]
     fc = np.where(Lc.types == DIRICHLET, 0.0, fc)

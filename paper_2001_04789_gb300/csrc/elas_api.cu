@@ -1,0 +1,1093 @@
+// C ABI of the solver: contexts, grids and their multigrid hierarchy, setup,
+// FP64 and mixed-precision solves, single-operation entry points.
+#include <cuda_runtime.h>
+
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/elas.h"
+#include "elas_internal.h"
+
+using namespace elas;
+
+struct elas_ctx_s {
+    int device = 0;
+    size_t budget = 0;
+    size_t in_use = 0;
+    elas_allocator alloc{};
+    bool has_alloc = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    double* host_status = nullptr;   // pinned readback buffer
+    // profiling: event pairs recorded around finest-level launches
+    bool profile = false;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    std::vector<std::pair<int, size_t>> pending;   // (class, index of start event)
+    double prof_ms[ELAS_PROF_CLASSES] = {0, 0, 0, 0};
+    long long prof_count[ELAS_PROF_CLASSES] = {0, 0, 0, 0};
+};
+
+namespace {
+
+// Start / stop an event-bracketed launch of a profiled class (no-op when profiling is off).
+size_t prof_begin(elas_ctx c, int cls) {
+    if (!c->profile) return (size_t)-1;
+    while (c->pool.size() < c->pool_used + 2) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->pool.push_back(e);
+    }
+    const size_t i = c->pool_used;
+    c->pool_used += 2;
+    cudaEventRecord(c->pool[i], c->stream);
+    c->pending.push_back({cls, i});
+    return i;
+}
+
+void prof_end(elas_ctx c, size_t i) {
+    if (i == (size_t)-1) return;
+    cudaEventRecord(c->pool[i + 1], c->stream);
+}
+
+// Fold pending event pairs into the totals (after a stream synchronisation).
+void prof_collect(elas_ctx c) {
+    if (!c->profile) return;
+    for (auto& pr : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->pool[pr.second], c->pool[pr.second + 1]) == cudaSuccess) {
+            c->prof_ms[pr.first] += ms;
+            c->prof_count[pr.first] += 1;
+        }
+    }
+    c->pending.clear();
+    c->pool_used = 0;
+}
+
+struct Level {
+    int n[3];
+    int N;
+    Lv<double> L64;
+    Lv<float> L32;
+    double *mod64 = nullptr, *u = nullptr, *ua = nullptr, *f = nullptr, *r = nullptr;
+    float *mod32 = nullptr, *u32 = nullptr, *ua32 = nullptr, *f32 = nullptr, *r32 = nullptr;
+    NullInfo nf{};
+};
+
+}  // namespace
+
+struct elas_grid_s {
+    elas_ctx ctx = nullptr;
+    elas_grid_desc desc{};
+    std::vector<Level> lv;
+    int K = 2;
+    // finest-level inputs
+    double* eps0 = nullptr;
+    double* body = nullptr;
+    double mean[6] = {0, 0, 0, 0, 0, 0};
+    int has_mean = 0;
+    int bc_type[6][3];
+    double bc_val[6][3];
+    double* face[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // bottom
+    int* dofs = nullptr;
+    int nfree = 0, ntot = 0;
+    double *Ainv = nullptr, *Awork = nullptr, *bwork = nullptr;
+    int* flag = nullptr;
+    // equilibrating load
+    double *G = nullptr, *Ginv = nullptr, *lam = nullptr, *dlam = nullptr, *status = nullptr, *partials = nullptr;
+    double r0 = 0.0;
+    bool moduli_set = false;
+    bool dirty = true;
+    std::vector<std::pair<void*, size_t>> allocs;
+};
+
+namespace {
+
+int set_err(elas_ctx c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                      \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return set_err(ctx, ELAS_ERR_DEVICE, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CHECK_LAUNCH(ctx) CUDA_TRY(ctx, cudaGetLastError())
+
+void* ctx_alloc(elas_ctx c, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (c->budget && c->in_use + bytes > c->budget) return nullptr;
+    void* p = nullptr;
+    if (c->has_alloc) {
+        p = c->alloc.alloc(bytes, c->alloc.user, (void*)c->stream);
+    } else {
+        if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) p = nullptr;
+    }
+    if (p) c->in_use += bytes;
+    return p;
+}
+
+void ctx_free(elas_ctx c, void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (c->has_alloc) c->alloc.free(p, bytes, c->alloc.user, (void*)c->stream);
+    else cudaFreeAsync(p, c->stream);
+    c->in_use -= bytes;
+}
+
+template <typename P>
+int galloc(elas_grid g, P** out, size_t count) {
+    const size_t bytes = count * sizeof(P);
+    if (g->ctx->budget && g->ctx->in_use + ((bytes + 255) & ~size_t(255)) > g->ctx->budget)
+        return set_err(g->ctx, ELAS_ERR_OUT_OF_BUDGET, "HBM budget of the context exceeded");
+    void* p = ctx_alloc(g->ctx, bytes);
+    if (!p) return set_err(g->ctx, ELAS_ERR_ALLOC, "device allocation failed");
+    g->allocs.push_back({p, bytes});
+    *out = (P*)p;
+    return ELAS_OK;
+}
+
+template <typename T>
+void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int K, const int bct[6][3]) {
+    for (int d = 0; d < 3; ++d) {
+        L.n[d] = n[d];
+        L.per[d] = per[d];
+        L.h[d] = (T)h[d];
+        L.inv2h[d] = (T)(1.0 / (2.0 * h[d]));
+        L.invh[d] = (T)(1.0 / h[d]);
+        L.invh2[d] = (T)(1.0 / (h[d] * h[d]));
+    }
+    L.inv4hh[0] = (T)(1.0 / (4.0 * h[1] * h[2]));
+    L.inv4hh[1] = (T)(1.0 / (4.0 * h[0] * h[2]));
+    L.inv4hh[2] = (T)(1.0 / (4.0 * h[0] * h[1]));
+    L.N = n[0] * n[1] * n[2];
+    L.K = K;
+    for (int f = 0; f < 6; ++f)
+        for (int c = 0; c < 3; ++c) L.bc[f][c] = (signed char)(per[f / 2] ? 0 : bct[f][c]);
+    L.mod = nullptr;
+}
+
+bool coarsenable(const int n[3], const int per[3]) {
+    int mx = 0;
+    for (int d = 0; d < 3; ++d) {
+        if (per[d]) {
+            if (n[d] % 2 != 0 || n[d] / 2 < 4) return false;
+        } else {
+            if ((n[d] - 1) % 2 != 0 || (n[d] - 1) / 2 + 1 < 3) return false;
+        }
+        mx = n[d] > mx ? n[d] : mx;
+    }
+    return mx > 5;
+}
+
+std::vector<std::array<int, 3>> level_dims(const elas_grid_desc& d) {
+    std::vector<std::array<int, 3>> out;
+    std::array<int, 3> n = {d.n[0], d.n[1], d.n[2]};
+    out.push_back(n);
+    while (coarsenable(n.data(), d.periodic)) {
+        for (int k = 0; k < 3; ++k) n[k] = d.periodic[k] ? n[k] / 2 : (n[k] - 1) / 2 + 1;
+        out.push_back(n);
+    }
+    return out;
+}
+
+// ---- host: free rigid modes --------------------------------------------------------
+// Symmetric 6x6 eigen-decomposition by cyclic Jacobi rotations.
+void jacobi6(double A[6][6], double V[6][6], double ev[6]) {
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < 6; ++i)
+            for (int j = i + 1; j < 6; ++j) off += A[i][j] * A[i][j];
+        if (off < 1e-300) break;
+        for (int p = 0; p < 6; ++p)
+            for (int q = p + 1; q < 6; ++q) {
+                if (std::fabs(A[p][q]) < 1e-300) continue;
+                const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 6; ++k) {
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 6; ++k) {
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 6; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 6; ++i) ev[i] = A[i][i];
+}
+
+int host_row_type(const int bct[6][3], const int per[3], const int n[3], const int c[3], int comp) {
+    bool any = false, dir = false, neu = false;
+    for (int d = 0; d < 3; ++d) {
+        if (per[d]) continue;
+        int f = -1;
+        if (c[d] == 0) f = 2 * d;
+        else if (c[d] == n[d] - 1) f = 2 * d + 1;
+        if (f < 0) continue;
+        any = true;
+        dir |= bct[f][comp] == ELAS_BC_DIRICHLET;
+        neu |= bct[f][comp] == ELAS_BC_NEUMANN;
+    }
+    if (!any) return ROW_INTERIOR;
+    return dir ? ROW_DIRICHLET : (neu ? ROW_NEUMANN : ROW_TRACTION);
+}
+
+NullInfo null_space(const elas_grid_desc& d, const int n[3], const double h[3], const int bct[6][3]) {
+    NullInfo nf{};
+    for (int k = 0; k < 3; ++k) {
+        nf.lo[k] = d.lo[k];
+        nf.h[k] = h[k];
+        nf.ctr[k] = d.lo[k] + 0.5 * h[k] * (n[k] - 1);
+    }
+    bool allowed[6] = {true, true, true, true, true, true};
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        if (d.periodic[b] || d.periodic[c]) allowed[3 + a] = false;
+    }
+    double M[6][6] = {};
+    // rigid-mode values at every Dirichlet row
+    int c[3];
+    for (c[2] = 0; c[2] < n[2]; ++c[2])
+        for (c[1] = 0; c[1] < n[1]; ++c[1])
+            for (c[0] = 0; c[0] < n[0]; ++c[0]) {
+                bool bnd = false;
+                for (int k = 0; k < 3; ++k)
+                    if (!d.periodic[k] && (c[k] == 0 || c[k] == n[k] - 1)) bnd = true;
+                if (!bnd) {  // skip the interior of the box quickly
+                    if (!d.periodic[0] && c[0] == 0 && n[0] > 2) { c[0] = n[0] - 2; }
+                    continue;
+                }
+                for (int comp = 0; comp < 3; ++comp) {
+                    if (host_row_type(bct, d.periodic, n, c, comp) != ROW_DIRICHLET) continue;
+                    double x[3];
+                    for (int k = 0; k < 3; ++k) x[k] = d.lo[k] + h[k] * c[k] - nf.ctr[k];
+                    double R[6];
+                    for (int m = 0; m < 3; ++m) R[m] = (m == comp) ? 1.0 : 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        const int b = (a + 1) % 3, e = (a + 2) % 3;
+                        R[3 + a] = (comp == b) ? -x[e] : (comp == e ? x[b] : 0.0);
+                    }
+                    for (int i = 0; i < 6; ++i)
+                        for (int j = 0; j < 6; ++j) M[i][j] += R[i] * R[j];
+                }
+            }
+    // restrict to allowed modes: disallowed ones get a large diagonal so they are not null
+    double scale = 1.0;
+    for (int i = 0; i < 6; ++i) scale = std::fmax(scale, M[i][i]);
+    for (int i = 0; i < 6; ++i)
+        if (!allowed[i]) {
+            for (int j = 0; j < 6; ++j) M[i][j] = M[j][i] = 0.0;
+            M[i][i] = scale;
+        }
+    double V[6][6], ev[6];
+    jacobi6(M, V, ev);
+    nf.m = 0;
+    for (int k = 0; k < 6; ++k) {
+        if (ev[k] <= 1e-12 * scale) {
+            for (int i = 0; i < 6; ++i) nf.basis[i][nf.m] = V[i][k];
+            ++nf.m;
+        }
+    }
+    return nf;
+}
+
+// small dense inverse on the host (m <= 6)
+bool invert_small(const double* A, double* X, int m) {
+    double a[6][12];
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < 2 * m; ++j) a[i][j] = j < m ? A[i * m + j] : (j - m == i ? 1.0 : 0.0);
+    for (int c = 0; c < m; ++c) {
+        int p = c;
+        for (int r = c + 1; r < m; ++r)
+            if (std::fabs(a[r][c]) > std::fabs(a[p][c])) p = r;
+        if (a[p][c] == 0.0) return false;
+        for (int j = 0; j < 2 * m; ++j) std::swap(a[c][j], a[p][j]);
+        const double iv = 1.0 / a[c][c];
+        for (int j = 0; j < 2 * m; ++j) a[c][j] *= iv;
+        for (int r = 0; r < m; ++r)
+            if (r != c) {
+                const double fct = a[r][c];
+                for (int j = 0; j < 2 * m; ++j) a[r][j] -= fct * a[c][j];
+            }
+    }
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) X[i * m + j] = a[i][m + j];
+    return true;
+}
+
+BoundaryData boundary_data(elas_grid g) {
+    BoundaryData bd;
+    for (int f = 0; f < 6; ++f) {
+        for (int c = 0; c < 3; ++c) bd.uniform[f][c] = g->bc_val[f][c];
+        bd.face[f] = g->face[f];
+    }
+    return bd;
+}
+
+int read_status(elas_grid g, double* out, int count) {
+    elas_ctx c = g->ctx;
+    CUDA_TRY(c, cudaMemcpyAsync(c->host_status, g->status, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < count; ++i) out[i] = c->host_status[i];
+    return ELAS_OK;
+}
+
+// ---- setup: coarse moduli, FP32 copies, RHS, equilibrating-load data, bottom ----------
+int setup(elas_grid g) {
+    if (!g->dirty) return ELAS_OK;
+    elas_ctx c = g->ctx;
+    cudaStream_t s = c->stream;
+    if (!g->moduli_set) return set_err(c, ELAS_ERR_STATE, "moduli not set");
+    const int nl = (int)g->lv.size();
+    for (int l = 1; l < nl; ++l) {
+        launch_restrict_moduli<double>(g->lv[l - 1].L64, g->lv[l].L64, g->lv[l - 1].mod64, g->lv[l].mod64, s);
+        CHECK_LAUNCH(c);
+    }
+    if (g->desc.mixed) {
+        for (int l = 0; l < nl; ++l) {
+            Level& v = g->lv[l];
+            launch_to_float(v.mod64, v.mod32, (size_t)g->K * v.N, s);
+            CHECK_LAUNCH(c);
+        }
+    }
+    // right-hand side
+    RhsInputs in{};
+    in.eps0 = g->eps0;
+    in.body = g->body;
+    for (int k = 0; k < 6; ++k) in.mean_strain[k] = g->mean[k];
+    in.has_mean_strain = g->has_mean;
+    launch_rhs(g->lv[0].L64, in, boundary_data(g), g->lv[0].f, s);
+    CHECK_LAUNCH(c);
+    // equilibrating load of the finest level: G = W^T W, Ginv
+    Level& L0 = g->lv[0];
+    const int m = L0.nf.m;
+    if (m > 0) {
+        std::vector<double> Gh(m * m), Gi(m * m);
+        for (int q = 0; q < m; ++q) {
+            int nb = 0;
+            launch_null_dots(L0.L64, L0.nf, nullptr, g->partials, &nb, q + 1, s);
+            CHECK_LAUNCH(c);
+            launch_sum_partials(g->partials, nb, m, g->status, s);
+            CHECK_LAUNCH(c);
+            double row[8];
+            int rc = read_status(g, row, m);
+            if (rc) return rc;
+            for (int k = 0; k < m; ++k) Gh[q * m + k] = row[k];
+        }
+        if (!invert_small(Gh.data(), Gi.data(), m)) return set_err(c, ELAS_ERR_STATE, "singular rigid-mode Gram matrix");
+        CUDA_TRY(c, cudaMemcpyAsync(g->G, Gh.data(), sizeof(double) * m * m, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaMemcpyAsync(g->Ginv, Gi.data(), sizeof(double) * m * m, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+    }
+    // bottom: dense inverse of the coarsest operator (bordered when singular)
+    {
+        Level& B = g->lv[nl - 1];
+        launch_bottom_assemble(B.L64, g->dofs, g->nfree, B.nf, g->Awork, s);
+        CHECK_LAUNCH(c);
+        CUDA_TRY(c, cudaMemsetAsync(g->flag, 0, sizeof(int), s));
+        launch_invert(g->Awork, g->Ainv, g->ntot, g->flag, s);
+        CHECK_LAUNCH(c);
+        int flag = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(&flag, g->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(c, cudaStreamSynchronize(s));
+        if (flag) return set_err(c, ELAS_ERR_STATE, "coarsest operator is singular");
+    }
+    // ||r_0||: residual of the Dirichlet-only field
+    {
+        launch_dirichlet(L0.L64, boundary_data(g), L0.ua, 0, s);
+        CHECK_LAUNCH(c);
+        int nb = 0;
+        launch_residual<double, double>(L0.L64, L0.ua, L0.f, nullptr, nullptr, L0.r, g->partials, &nb, s);
+        CHECK_LAUNCH(c);
+        NullInfo none{};
+        launch_finalize(g->partials, nb, none, nullptr, nullptr, nullptr, nullptr, g->status, 0, s);
+        CHECK_LAUNCH(c);
+        double st[1];
+        int rc = read_status(g, st, 1);
+        if (rc) return rc;
+        g->r0 = std::sqrt(st[0]);
+    }
+    g->dirty = false;
+    return ELAS_OK;
+}
+
+// ---- cycles ------------------------------------------------------------------------
+template <typename T>
+struct Fields {
+    static T* u(Level& v);
+    static T* ua(Level& v);
+    static T* f(Level& v);
+    static T* r(Level& v);
+    static const Lv<T>& L(Level& v);
+};
+template <>
+struct Fields<double> {
+    static double* u(Level& v) { return v.u; }
+    static double* ua(Level& v) { return v.ua; }
+    static double* f(Level& v) { return v.f; }
+    static double* r(Level& v) { return v.r; }
+    static const Lv<double>& L(Level& v) { return v.L64; }
+};
+template <>
+struct Fields<float> {
+    static float* u(Level& v) { return v.u32; }
+    static float* ua(Level& v) { return v.ua32; }
+    static float* f(Level& v) { return v.f32; }
+    static float* r(Level& v) { return v.r32; }
+    static const Lv<float>& L(Level& v) { return v.L32; }
+};
+
+template <typename T>
+void smooth(elas_grid g, int l, int sweeps, const NullInfo* nf, const double* lam) {
+    Level& v = g->lv[l];
+    elas_ctx c = g->ctx;
+    cudaStream_t s = c->stream;
+    const int cls = sizeof(T) == 8 ? ELAS_PROF_SWEEP64_L0 : ELAS_PROF_SWEEP32_L0;
+    for (int k = 0; k < sweeps; ++k) {
+        size_t e = l == 0 ? prof_begin(c, cls) : (size_t)-1;
+        launch_half_sweep<T>(Fields<T>::L(v), Fields<T>::u(v), Fields<T>::ua(v), Fields<T>::f(v), 0, nf, lam, s);
+        prof_end(c, e);
+        e = l == 0 ? prof_begin(c, cls) : (size_t)-1;
+        launch_half_sweep<T>(Fields<T>::L(v), Fields<T>::ua(v), Fields<T>::u(v), Fields<T>::f(v), 1, nf, lam, s);
+        prof_end(c, e);
+    }
+}
+
+// Correction cycle on level l >= 1 (or l = 0 of the FP32 cycle): u_l from zero.
+template <typename T>
+void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const double* dlam0) {
+    Level& v = g->lv[l];
+    cudaStream_t s = g->ctx->stream;
+    const int nl = (int)g->lv.size();
+    if (l == nl - 1) {
+        launch_bottom_solve<T>(Fields<T>::L(v), g->dofs, g->nfree, g->ntot, g->Ainv, Fields<T>::f(v), Fields<T>::u(v),
+                               g->bwork, s);
+        return;
+    }
+    const NullInfo* nf = (l == 0) ? nf0 : nullptr;
+    const double* lam = (l == 0) ? dlam0 : nullptr;
+    cudaMemsetAsync(Fields<T>::u(v), 0, sizeof(T) * 3 * (size_t)v.N, s);
+    smooth<T>(g, l, nu1, nf, lam);
+    const size_t e = l == 0 ? prof_begin(g->ctx, sizeof(T) == 8 ? ELAS_PROF_RESID64_L0 : ELAS_PROF_RESID32_L0)
+                            : (size_t)-1;
+    launch_residual<T, T>(Fields<T>::L(v), Fields<T>::u(v), Fields<T>::f(v), nf, lam, Fields<T>::r(v), nullptr,
+                          nullptr, s);
+    prof_end(g->ctx, e);
+    Level& w = g->lv[l + 1];
+    launch_restrict<T>(Fields<T>::L(v), Fields<T>::L(w), Fields<T>::r(v), Fields<T>::f(w), nullptr, nullptr, s);
+    vcycle<T>(g, l + 1, nu1, nu2, nullptr, nullptr);
+    launch_prolong_add<T>(Fields<T>::L(v), Fields<T>::L(w), Fields<T>::u(w), Fields<T>::u(v), s);
+    smooth<T>(g, l, nu2, nf, lam);
+}
+
+int remove_rigid(elas_grid g) {
+    Level& L0 = g->lv[0];
+    if (L0.nf.m == 0) return ELAS_OK;
+    elas_ctx c = g->ctx;
+    int nb = 0;
+    launch_null_dots(L0.L64, L0.nf, L0.u, g->partials, &nb, 0, c->stream);
+    CHECK_LAUNCH(c);
+    launch_sum_partials(g->partials, nb, L0.nf.m, g->status + 8, c->stream);
+    CHECK_LAUNCH(c);
+    launch_remove_null(L0.L64, L0.nf, g->Ginv, g->status + 8, L0.u, c->stream);
+    CHECK_LAUNCH(c);
+    return ELAS_OK;
+}
+
+int level_alloc(elas_grid g, Level& v, bool mixed) {
+    int rc;
+    const size_t N = (size_t)v.N;
+    if ((rc = galloc(g, &v.mod64, (size_t)g->K * N))) return rc;
+    if ((rc = galloc(g, &v.u, 3 * N))) return rc;
+    if ((rc = galloc(g, &v.ua, 3 * N))) return rc;
+    if ((rc = galloc(g, &v.f, 3 * N))) return rc;
+    if ((rc = galloc(g, &v.r, 3 * N))) return rc;
+    if (mixed) {
+        if ((rc = galloc(g, &v.mod32, (size_t)g->K * N))) return rc;
+        if ((rc = galloc(g, &v.u32, 3 * N))) return rc;
+        if ((rc = galloc(g, &v.ua32, 3 * N))) return rc;
+        if ((rc = galloc(g, &v.f32, 3 * N))) return rc;
+        if ((rc = galloc(g, &v.r32, 3 * N))) return rc;
+    }
+    v.L64.mod = v.mod64;
+    v.L32.mod = v.mod32;
+    return ELAS_OK;
+}
+
+void refresh_lv(elas_grid g) {
+    const int nl = (int)g->lv.size();
+    for (int l = 0; l < nl; ++l) {
+        Level& v = g->lv[l];
+        double h[3];
+        for (int d = 0; d < 3; ++d) {
+            const double span = g->desc.hi[d] - g->desc.lo[d];
+            const double h0 = g->desc.periodic[d] ? span / g->desc.n[d] : span / (g->desc.n[d] - 1);
+            h[d] = h0 * (double)(1 << l);
+        }
+        fill_lv(v.L64, v.n, g->desc.periodic, h, g->K, g->bc_type);
+        fill_lv(v.L32, v.n, g->desc.periodic, h, g->K, g->bc_type);
+        v.L64.mod = v.mod64;
+        v.L32.mod = v.mod32;
+        v.nf = null_space(g->desc, v.n, h, g->bc_type);
+    }
+}
+
+int rebuild_bottom_dofs(elas_grid g) {
+    Level& B = g->lv.back();
+    std::vector<int> dofs;
+    int c[3];
+    for (int comp = 0; comp < 3; ++comp)
+        for (c[2] = 0; c[2] < B.n[2]; ++c[2])
+            for (c[1] = 0; c[1] < B.n[1]; ++c[1])
+                for (c[0] = 0; c[0] < B.n[0]; ++c[0])
+                    if (host_row_type(g->bc_type, g->desc.periodic, B.n, c, comp) != ROW_DIRICHLET)
+                        dofs.push_back(comp * B.N + c[0] + B.n[0] * (c[1] + B.n[1] * c[2]));
+    const int nfree = (int)dofs.size();
+    const int ntot = nfree + B.nf.m;
+    elas_ctx ctx = g->ctx;
+    if (ntot != g->ntot || !g->dofs) {
+        // (re)allocate: sizes change only with the boundary types
+        int rc;
+        if ((rc = galloc(g, &g->dofs, (size_t)3 * B.N + 1))) return rc;
+        if ((rc = galloc(g, &g->Ainv, (size_t)ntot * ntot + 1))) return rc;
+        if ((rc = galloc(g, &g->Awork, (size_t)ntot * ntot + 1))) return rc;
+        if ((rc = galloc(g, &g->bwork, (size_t)ntot + 1))) return rc;
+    }
+    g->nfree = nfree;
+    g->ntot = ntot;
+    if (nfree > 0)
+        CUDA_TRY(ctx, cudaMemcpyAsync(g->dofs, dofs.data(), sizeof(int) * nfree, cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return ELAS_OK;
+}
+
+int copy_in(elas_ctx c, double* dst, const double* src, size_t count, int memspace) {
+    CUDA_TRY(c, cudaMemcpyAsync(dst, src, sizeof(double) * count,
+                                memspace == ELAS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return ELAS_OK;
+}
+
+}  // namespace
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+extern "C" {
+
+int elas_ctx_create(elas_ctx* out, int device, size_t hbm_budget_bytes, const elas_allocator* alloc, void* stream) {
+    if (!out) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = new elas_ctx_s();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    if (alloc && alloc->alloc && alloc->free) {
+        c->alloc = *alloc;
+        c->has_alloc = true;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return ELAS_ERR_DEVICE;
+    }
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return ELAS_ERR_DEVICE;
+        }
+        c->own_stream = true;
+    }
+    if (cudaMallocHost(&c->host_status, 64 * sizeof(double)) != cudaSuccess) {
+        delete c;
+        return ELAS_ERR_DEVICE;
+    }
+    *out = c;
+    return ELAS_OK;
+}
+
+int elas_ctx_destroy(elas_ctx c) {
+    if (!c) return ELAS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->stream);
+    for (auto e : c->pool) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    if (c->host_status) cudaFreeHost(c->host_status);
+    delete c;
+    return ELAS_OK;
+}
+
+const char* elas_last_error(elas_ctx c) { return c ? c->err.c_str() : "null context"; }
+size_t elas_ctx_bytes_in_use(elas_ctx c) { return c ? c->in_use : 0; }
+
+size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
+    if (!d) return 0;
+    const int K = d->moduli_kind;
+    size_t total = 0;
+    for (auto& n : level_dims(*d)) {
+        const size_t N = (size_t)n[0] * n[1] * n[2];
+        total += N * 8 * (K + 12);
+        if (d->mixed) total += N * 4 * (K + 12);
+    }
+    const size_t N0 = (size_t)d->n[0] * d->n[1] * d->n[2];
+    total += N0 * 8 * 9;   // eigenstrain + body force when given
+    return total;
+}
+
+int elas_grid_create(elas_ctx c, const elas_grid_desc* d, elas_grid* out) {
+    if (!c || !d || !out) return ELAS_ERR_INVALID_ARG;
+    if (d->moduli_kind != ELAS_MODULI_ISO && d->moduli_kind != ELAS_MODULI_GEN21)
+        return set_err(c, ELAS_ERR_INVALID_ARG, "moduli_kind must be 2 or 21");
+    for (int k = 0; k < 3; ++k) {
+        if (d->periodic[k] ? d->n[k] < 4 : d->n[k] < 3)
+            return set_err(c, ELAS_ERR_INVALID_ARG, "too few nodes in a direction");
+        if (!(d->hi[k] > d->lo[k])) return set_err(c, ELAS_ERR_INVALID_ARG, "empty domain");
+    }
+    const double N0 = (double)d->n[0] * d->n[1] * d->n[2];
+    if (N0 * d->moduli_kind >= 2147483647.0 || 3.0 * N0 >= 2147483647.0)
+        return set_err(c, ELAS_ERR_INVALID_ARG, "grid too large for 32-bit plane indexing");
+    cudaSetDevice(c->device);
+    elas_grid g = new elas_grid_s();
+    g->ctx = c;
+    g->desc = *d;
+    g->K = d->moduli_kind;
+    for (int f = 0; f < 6; ++f)
+        for (int k = 0; k < 3; ++k) {
+            g->bc_type[f][k] = ELAS_BC_DIRICHLET;
+            g->bc_val[f][k] = 0.0;
+        }
+    auto dims = level_dims(*d);
+    g->lv.resize(dims.size());
+    int rc = ELAS_OK;
+    for (size_t l = 0; l < dims.size(); ++l) {
+        Level& v = g->lv[l];
+        for (int k = 0; k < 3; ++k) v.n[k] = dims[l][k];
+        v.N = v.n[0] * v.n[1] * v.n[2];
+        if ((rc = level_alloc(g, v, d->mixed != 0))) break;
+    }
+    const size_t nparts = (size_t)((g->lv[0].N + kBlock - 1) / kBlock) * kPartialStride + 64;
+    if (!rc) rc = galloc(g, &g->partials, nparts);
+    if (!rc) rc = galloc(g, &g->status, 64);
+    if (!rc) rc = galloc(g, &g->G, 36);
+    if (!rc) rc = galloc(g, &g->Ginv, 36);
+    if (!rc) rc = galloc(g, &g->lam, 8);
+    if (!rc) rc = galloc(g, &g->dlam, 8);
+    if (!rc) rc = galloc(g, &g->flag, 4);
+    if (!rc) {
+        refresh_lv(g);
+        rc = rebuild_bottom_dofs(g);
+    }
+    if (rc) {
+        elas_grid_destroy(g);
+        return rc;
+    }
+    cudaMemsetAsync(g->lv[0].u, 0, sizeof(double) * 3 * (size_t)g->lv[0].N, c->stream);
+    cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        elas_grid_destroy(g);
+        return set_err(c, ELAS_ERR_DEVICE, "grid initialisation failed");
+    }
+    *out = g;
+    return ELAS_OK;
+}
+
+int elas_grid_destroy(elas_grid g) {
+    if (!g) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = g->ctx;
+    cudaStreamSynchronize(c->stream);
+    for (auto& a : g->allocs) ctx_free(c, a.first, a.second);
+    cudaStreamSynchronize(c->stream);
+    delete g;
+    return ELAS_OK;
+}
+
+int elas_grid_levels(elas_grid g, int* nlevels) {
+    if (!g || !nlevels) return ELAS_ERR_INVALID_ARG;
+    *nlevels = (int)g->lv.size();
+    return ELAS_OK;
+}
+
+int elas_grid_level_dims(elas_grid g, int level, int n[3]) {
+    if (!g || !n || level < 0 || level >= (int)g->lv.size()) return ELAS_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k) n[k] = g->lv[level].n[k];
+    return ELAS_OK;
+}
+
+size_t elas_grid_bytes(elas_grid g) {
+    if (!g) return 0;
+    size_t t = 0;
+    for (auto& a : g->allocs) t += a.second;
+    return t;
+}
+
+int elas_set_moduli(elas_grid g, const double* comps, int memspace) {
+    if (!g || !comps) return ELAS_ERR_INVALID_ARG;
+    int rc = copy_in(g->ctx, g->lv[0].mod64, comps, (size_t)g->K * g->lv[0].N, memspace);
+    if (rc) return rc;
+    g->moduli_set = true;
+    g->dirty = true;
+    return ELAS_OK;
+}
+
+static int set_field(elas_grid g, double** slot, const double* src, size_t count, int memspace) {
+    if (!src) {
+        *slot = nullptr;   // memory stays with the grid until destroyed
+        g->dirty = true;
+        return ELAS_OK;
+    }
+    if (!*slot) {
+        int rc = galloc(g, slot, count);
+        if (rc) return rc;
+    }
+    g->dirty = true;
+    return copy_in(g->ctx, *slot, src, count, memspace);
+}
+
+int elas_set_eigenstrain(elas_grid g, const double* eps6, int memspace) {
+    if (!g) return ELAS_ERR_INVALID_ARG;
+    return set_field(g, &g->eps0, eps6, (size_t)6 * g->lv[0].N, memspace);
+}
+
+int elas_set_body_force(elas_grid g, const double* b3, int memspace) {
+    if (!g) return ELAS_ERR_INVALID_ARG;
+    return set_field(g, &g->body, b3, (size_t)3 * g->lv[0].N, memspace);
+}
+
+int elas_set_mean_strain(elas_grid g, const double eps6[6]) {
+    if (!g || !eps6) return ELAS_ERR_INVALID_ARG;
+    if (!(g->desc.periodic[0] && g->desc.periodic[1] && g->desc.periodic[2]))
+        return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "mean strain needs a fully periodic grid");
+    for (int k = 0; k < 6; ++k) g->mean[k] = eps6[k];
+    g->has_mean = 1;
+    g->dirty = true;
+    return ELAS_OK;
+}
+
+int elas_set_bc(elas_grid g, int face, int comp, int type, double value) {
+    if (!g || face < 0 || face > 5 || comp < 0 || comp > 2) return ELAS_ERR_INVALID_ARG;
+    if (type != ELAS_BC_DIRICHLET && type != ELAS_BC_TRACTION && type != ELAS_BC_NEUMANN)
+        return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "unknown boundary type");
+    const bool changed = g->bc_type[face][comp] != type;
+    g->bc_type[face][comp] = type;
+    g->bc_val[face][comp] = value;
+    g->dirty = true;
+    if (changed) {
+        refresh_lv(g);
+        return rebuild_bottom_dofs(g);
+    }
+    return ELAS_OK;
+}
+
+int elas_set_face_values(elas_grid g, int face, const double* values, int memspace) {
+    if (!g || face < 0 || face > 5) return ELAS_ERR_INVALID_ARG;
+    if (!values) {
+        g->face[face] = nullptr;
+        g->dirty = true;
+        return ELAS_OK;
+    }
+    double* slot = g->face[face];
+    int rc = set_field(g, &slot, values, (size_t)3 * g->lv[0].N, memspace);
+    g->face[face] = slot;
+    return rc;
+}
+
+void elas_solve_opts_default(elas_solve_opts* o) {
+    if (!o) return;
+    o->precision = ELAS_PRECISION_FP64;
+    o->rel_tol = 1e-8;
+    o->max_cycles = 100;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->warm_start = 0;
+    o->fixed_cycles = 0;
+    o->use_graph = 0;
+}
+
+int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) {
+    if (!g || !opts || !info) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = g->ctx;
+    cudaSetDevice(c->device);
+    std::memset(info, 0, sizeof(*info));
+    const bool mixed = opts->precision == ELAS_PRECISION_MIXED;
+    if (mixed && !g->desc.mixed) return set_err(c, ELAS_ERR_STATE, "grid was created without the FP32 hierarchy");
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = setup(g);
+    if (rc) return rc;
+    cudaStream_t s = c->stream;
+    Level& L0 = g->lv[0];
+    const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
+    launch_dirichlet(L0.L64, boundary_data(g), L0.u, opts->warm_start ? 1 : 0, s);
+    CHECK_LAUNCH(c);
+    CUDA_TRY(c, cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, s));
+    info->r0 = g->r0;
+    info->nlam = L0.nf.m;
+    const int nu1 = opts->nu1 < 0 ? 0 : opts->nu1, nu2 = opts->nu2 < 0 ? 0 : opts->nu2;
+    int cycles = 0;
+    double rel = 0.0;
+    int status = ELAS_OK;
+    int hist = 0;
+    for (;;) {
+        int nb = 0;
+        if (!mixed) smooth<double>(g, 0, nu1, nf0, g->lam);
+        const size_t ev = prof_begin(c, ELAS_PROF_RESID64_L0);
+        if (!mixed) launch_residual<double, double>(L0.L64, L0.u, L0.f, nf0, g->lam, L0.r, g->partials, &nb, s);
+        else launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, g->lam, L0.f32, g->partials, &nb, s);
+        prof_end(c, ev);
+        CHECK_LAUNCH(c);
+        launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->status, 1, s);
+        CHECK_LAUNCH(c);
+        double st[1];
+        rc = read_status(g, st, 1);
+        if (rc) return rc;
+        prof_collect(c);
+        rel = g->r0 > 0 ? std::sqrt(st[0]) / g->r0 : 0.0;
+        if (hist < ELAS_HISTORY) info->rel_history[hist++] = rel;
+        if (!std::isfinite(rel) || rel > 1e12) {
+            status = ELAS_ERR_DIVERGED;
+            break;
+        }
+        if (opts->fixed_cycles > 0) {
+            if (cycles >= opts->fixed_cycles) break;
+        } else {
+            if (rel <= opts->rel_tol) break;
+            if (cycles >= opts->max_cycles) {
+                status = ELAS_ERR_NOT_CONVERGED;
+                break;
+            }
+        }
+        if (!mixed && g->lv.size() == 1) {
+            // single level: exact (bordered) solve of the correction; any rigid-mode
+            // part of r is absorbed by the bordering, so r needs no equilibration here
+            launch_bottom_solve<double>(L0.L64, g->dofs, g->nfree, g->ntot, g->Ainv, L0.r, L0.ua, g->bwork, s);
+            launch_add_correction64(L0.L64, L0.u, L0.ua, s);
+            smooth<double>(g, 0, nu2, nf0, g->lam);
+        } else if (!mixed) {
+            Level& L1 = g->lv[1];
+            launch_restrict<double>(L0.L64, L1.L64, L0.r, L1.f, nf0, nf0 ? g->dlam : nullptr, s);
+            vcycle<double>(g, 1, nu1, nu2, nullptr, nullptr);
+            launch_prolong_add<double>(L0.L64, L1.L64, L1.u, L0.u, s);
+            smooth<double>(g, 0, nu2, nf0, g->lam);
+        } else {
+            vcycle<float>(g, 0, nu1, nu2, nf0, nf0 ? g->dlam : nullptr);
+            launch_add_correction(L0.L64, L0.u, L0.u32, s);
+        }
+        CHECK_LAUNCH(c);
+        ++cycles;
+    }
+    rc = remove_rigid(g);
+    if (rc) return rc;
+    double lam[8] = {0};
+    if (L0.nf.m > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->host_status, g->lam, sizeof(double) * L0.nf.m, cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    for (int q = 0; q < L0.nf.m; ++q) lam[q] = c->host_status[q];
+    for (int q = 0; q < 6; ++q) info->lam[q] = lam[q];
+    info->cycles = cycles;
+    info->rel_residual = rel;
+    info->status = status;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (status == ELAS_ERR_NOT_CONVERGED) set_err(c, status, "maximum cycles reached above the tolerance");
+    if (status == ELAS_ERR_DIVERGED) set_err(c, status, "residual diverged");
+    return status;
+}
+
+int elas_get_displacement(elas_grid g, double* out, int memspace) {
+    if (!g || !out) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = g->ctx;
+    CUDA_TRY(c, cudaMemcpyAsync(out, g->lv[0].u, sizeof(double) * 3 * (size_t)g->lv[0].N,
+                                memspace == ELAS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return ELAS_OK;
+}
+
+int elas_set_displacement(elas_grid g, const double* in, int memspace) {
+    if (!g || !in) return ELAS_ERR_INVALID_ARG;
+    return copy_in(g->ctx, g->lv[0].u, in, (size_t)3 * g->lv[0].N, memspace);
+}
+
+int elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2) {
+    if (!g) return ELAS_ERR_INVALID_ARG;
+    int rc = setup(g);
+    if (rc) return rc;
+    elas_ctx c = g->ctx;
+    Level& L0 = g->lv[0];
+    const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
+    int nb = 0;
+    launch_residual<double, double>(L0.L64, L0.u, L0.f, nf0, g->lam, L0.r, g->partials, &nb, c->stream);
+    CHECK_LAUNCH(c);
+    launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->status, 0, c->stream);
+    CHECK_LAUNCH(c);
+    double st[1];
+    rc = read_status(g, st, 1);
+    if (rc) return rc;
+    if (abs_l2) *abs_l2 = std::sqrt(st[0]);
+    if (rel_l2) *rel_l2 = g->r0 > 0 ? std::sqrt(st[0]) / g->r0 : 0.0;
+    return ELAS_OK;
+}
+
+// ---- single operations ----------------------------------------------------------------
+static int check_level(elas_grid g, int level, int precision) {
+    if (!g) return ELAS_ERR_INVALID_ARG;
+    if (level < 0 || level >= (int)g->lv.size()) return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "bad level");
+    if (precision == 1 && !g->desc.mixed) return set_err(g->ctx, ELAS_ERR_STATE, "no FP32 hierarchy");
+    return setup(g);
+}
+
+int elas_op_apply(elas_grid g, int level, int precision, const void* u, void* out) {
+    int rc = check_level(g, level, precision);
+    if (rc) return rc;
+    Level& v = g->lv[level];
+    if (precision == 0) launch_apply<double>(v.L64, (const double*)u, (double*)out, g->ctx->stream);
+    else launch_apply<float>(v.L32, (const float*)u, (float*)out, g->ctx->stream);
+    CHECK_LAUNCH(g->ctx);
+    CUDA_TRY(g->ctx, cudaStreamSynchronize(g->ctx->stream));
+    return ELAS_OK;
+}
+
+int elas_op_residual(elas_grid g, int level, int precision, const void* u, const void* f, void* r, double* sumsq) {
+    int rc = check_level(g, level, precision);
+    if (rc) return rc;
+    Level& v = g->lv[level];
+    int nb = 0;
+    if (precision == 0)
+        launch_residual<double, double>(v.L64, (const double*)u, (const double*)f, nullptr, nullptr, (double*)r,
+                                        g->partials, &nb, g->ctx->stream);
+    else
+        launch_residual<float, float>(v.L32, (const float*)u, (const float*)f, nullptr, nullptr, (float*)r,
+                                      g->partials, &nb, g->ctx->stream);
+    CHECK_LAUNCH(g->ctx);
+    launch_sum_partials(g->partials, nb, 1, g->status, g->ctx->stream);
+    double st[1];
+    rc = read_status(g, st, 1);
+    if (rc) return rc;
+    if (sumsq) *sumsq = st[0];
+    return ELAS_OK;
+}
+
+int elas_op_sweep(elas_grid g, int level, int precision, void* u, const void* f) {
+    int rc = check_level(g, level, precision);
+    if (rc) return rc;
+    Level& v = g->lv[level];
+    cudaStream_t s = g->ctx->stream;
+    if (precision == 0) {
+        launch_half_sweep<double>(v.L64, (const double*)u, v.ua, (const double*)f, 0, nullptr, nullptr, s);
+        launch_half_sweep<double>(v.L64, v.ua, (double*)u, (const double*)f, 1, nullptr, nullptr, s);
+    } else {
+        launch_half_sweep<float>(v.L32, (const float*)u, v.ua32, (const float*)f, 0, nullptr, nullptr, s);
+        launch_half_sweep<float>(v.L32, v.ua32, (float*)u, (const float*)f, 1, nullptr, nullptr, s);
+    }
+    CHECK_LAUNCH(g->ctx);
+    CUDA_TRY(g->ctx, cudaStreamSynchronize(s));
+    return ELAS_OK;
+}
+
+int elas_op_restrict(elas_grid g, int level, int precision, const void* r, void* fc) {
+    int rc = check_level(g, level, precision);
+    if (rc) return rc;
+    if (level + 1 >= (int)g->lv.size()) return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "no coarser level");
+    Level& v = g->lv[level];
+    Level& w = g->lv[level + 1];
+    if (precision == 0)
+        launch_restrict<double>(v.L64, w.L64, (const double*)r, (double*)fc, nullptr, nullptr, g->ctx->stream);
+    else
+        launch_restrict<float>(v.L32, w.L32, (const float*)r, (float*)fc, nullptr, nullptr, g->ctx->stream);
+    CHECK_LAUNCH(g->ctx);
+    CUDA_TRY(g->ctx, cudaStreamSynchronize(g->ctx->stream));
+    return ELAS_OK;
+}
+
+int elas_op_prolong_add(elas_grid g, int level, int precision, const void* ec, void* u) {
+    int rc = check_level(g, level, precision);
+    if (rc) return rc;
+    if (level + 1 >= (int)g->lv.size()) return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "no coarser level");
+    Level& v = g->lv[level];
+    Level& w = g->lv[level + 1];
+    if (precision == 0) launch_prolong_add<double>(v.L64, w.L64, (const double*)ec, (double*)u, g->ctx->stream);
+    else launch_prolong_add<float>(v.L32, w.L32, (const float*)ec, (float*)u, g->ctx->stream);
+    CHECK_LAUNCH(g->ctx);
+    CUDA_TRY(g->ctx, cudaStreamSynchronize(g->ctx->stream));
+    return ELAS_OK;
+}
+
+int elas_op_rhs(elas_grid g, double* f_out) {
+    int rc = check_level(g, 0, 0);
+    if (rc) return rc;
+    CUDA_TRY(g->ctx, cudaMemcpyAsync(f_out, g->lv[0].f, sizeof(double) * 3 * (size_t)g->lv[0].N,
+                                     cudaMemcpyDeviceToDevice, g->ctx->stream));
+    CUDA_TRY(g->ctx, cudaStreamSynchronize(g->ctx->stream));
+    return ELAS_OK;
+}
+
+int elas_op_bottom(elas_grid g, int precision, const void* f, void* u) {
+    const int l = (int)g->lv.size() - 1;
+    int rc = check_level(g, l, precision);
+    if (rc) return rc;
+    Level& v = g->lv[l];
+    if (precision == 0)
+        launch_bottom_solve<double>(v.L64, g->dofs, g->nfree, g->ntot, g->Ainv, (const double*)f, (double*)u, g->bwork,
+                                    g->ctx->stream);
+    else
+        launch_bottom_solve<float>(v.L32, g->dofs, g->nfree, g->ntot, g->Ainv, (const float*)f, (float*)u, g->bwork,
+                                   g->ctx->stream);
+    CHECK_LAUNCH(g->ctx);
+    CUDA_TRY(g->ctx, cudaStreamSynchronize(g->ctx->stream));
+    return ELAS_OK;
+}
+
+int elas_profile_enable(elas_ctx c, int enable) {
+    if (!c) return ELAS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->stream);
+    c->pending.clear();
+    c->pool_used = 0;
+    c->profile = enable != 0;
+    for (int k = 0; k < ELAS_PROF_CLASSES; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_count[k] = 0;
+    }
+    return ELAS_OK;
+}
+
+int elas_profile_read(elas_ctx c, int cls, double* total_ms, long long* launches) {
+    if (!c || cls < 0 || cls >= ELAS_PROF_CLASSES) return ELAS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->stream);
+    prof_collect(c);
+    if (total_ms) *total_ms = c->prof_ms[cls];
+    if (launches) *launches = c->prof_count[cls];
+    return ELAS_OK;
+}
+
+unsigned long long elas_launch_count(void) { return elas::launch_count(); }
+
+int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_info* info) {
+    if (!grids || n < 0 || !opts || !info) return ELAS_ERR_INVALID_ARG;
+    int worst = ELAS_OK;
+    for (int i = 0; i < n; ++i) {
+        const int rc = elas_solve(grids[i], opts, &info[i]);
+        if (rc != ELAS_OK && worst == ELAS_OK) worst = rc;
+    }
+    return worst;
+}
+
+}  // extern "C"

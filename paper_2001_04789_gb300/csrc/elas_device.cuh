@@ -1,0 +1,459 @@
+// Device-side definitions shared by the kernels: level geometry, row
+// classification, moduli access and the discrete operator.
+//
+// The operator follows Runnels et al., Section 2.1.1: the product-rule split
+//   D(u)_i = C_ijkl,j (u_k,l - eps0_kl) + C_ijkl (u_k,lj - eps0_kl,j)
+// with central first differences, compact second differences, four-corner mixed
+// differences and central differences of the nodal moduli.  Boundary conditions
+// are boundary-operator rows (Section 2.1, Eq. 1b-1d): Dirichlet rows are held
+// fixed; a traction row is the balance of the node's half (quarter, eighth)
+// control cell, i.e. the product-rule terms of its non-boundary directions plus,
+// for each boundary direction a, -(2/h_a) s_a Cbar_iakl Dbar_l u_k (the stress at
+// the half-cell face; the prescribed traction goes to the right-hand side);
+// Neumann rows are -(2/h_a) C_iaia s_a D_a u_i.  Near a boundary plane of
+// direction l the first derivative D_l is one-sided and second order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace elas {
+
+enum : int { ROW_INTERIOR = 0, ROW_DIRICHLET = 1, ROW_TRACTION = 2, ROW_NEUMANN = 3 };
+
+// Geometry of one level, passed by value to every kernel.
+template <typename T>
+struct Lv {
+    int n[3];
+    int per[3];
+    int N;
+    int K;                 // moduli planes: 2 (lambda, mu) or 21 (Voigt upper triangle)
+    signed char bc[6][3];  // boundary type per (face, component); 0 on periodic faces
+    T h[3], inv2h[3], invh[3], invh2[3], inv4hh[3];   // inv4hh[d] for the pair != d
+    const T* __restrict__ mod;
+};
+
+// ---- Voigt helpers ----------------------------------------------------------
+__host__ __device__ constexpr int voigt(int i, int j) { return i == j ? i : 6 - i - j; }
+__host__ __device__ constexpr int upper(int a, int b) {
+    return a <= b ? a * (11 - a) / 2 + b : b * (11 - b) / 2 + a;
+}
+__host__ __device__ constexpr int pair_index(int j, int l) {  // (0,1)->2 (0,2)->1 (1,2)->0
+    return 3 - j - l;
+}
+
+// C_ijkl at node q.
+template <typename T, int KIND>
+__device__ __forceinline__ T Cm(const Lv<T>& L, int q, int i, int j, int k, int l) {
+    if (KIND == 2) {
+        const T lam = L.mod[q];
+        const T mu = L.mod[L.N + q];
+        T v = T(0);
+        if (i == j && k == l) v += lam;
+        if (i == k && j == l) v += mu;
+        if (i == l && j == k) v += mu;
+        return v;
+    } else {
+        return L.mod[upper(voigt(i, j), voigt(k, l)) * L.N + q];
+    }
+}
+
+template <typename T, int KIND>
+__device__ __forceinline__ bool Cnz(int i, int j, int k, int l) {
+    if (KIND == 2) return (i == j && k == l) || (i == k && j == l) || (i == l && j == k);
+    return true;
+}
+
+// ---- node classification ------------------------------------------------------
+struct NodeInfo {
+    int c[3];
+    signed char side[3];   // -1 low boundary plane, +1 high, 0 none (or periodic)
+    bool boundary;
+};
+
+template <typename T>
+__device__ __forceinline__ NodeInfo node_info(const Lv<T>& L, int x, int y, int z) {
+    NodeInfo ni;
+    ni.c[0] = x; ni.c[1] = y; ni.c[2] = z;
+    ni.boundary = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int s = 0;
+        if (!L.per[d]) {
+            if (ni.c[d] == 0) s = -1;
+            else if (ni.c[d] == L.n[d] - 1) s = 1;
+        }
+        ni.side[d] = (signed char)s;
+        ni.boundary |= (s != 0);
+    }
+    return ni;
+}
+
+// Row type of component c at a node (Dirichlet over Neumann over traction).
+template <typename T>
+__device__ __forceinline__ int row_type(const Lv<T>& L, const NodeInfo& ni, int c) {
+    if (!ni.boundary) return ROW_INTERIOR;
+    bool dir = false, neu = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (ni.side[d] == 0) continue;
+        const int f = 2 * d + (ni.side[d] > 0 ? 1 : 0);
+        const int t = L.bc[f][c];
+        dir |= (t == ROW_DIRICHLET);
+        neu |= (t == ROW_NEUMANN);
+    }
+    return dir ? ROW_DIRICHLET : (neu ? ROW_NEUMANN : ROW_TRACTION);
+}
+
+template <typename T>
+__device__ __forceinline__ int lin(const Lv<T>& L, int x, int y, int z) {
+    return x + L.n[0] * (y + L.n[1] * z);
+}
+
+// Coordinate c + s e_d with periodic wrap.
+template <typename T>
+__device__ __forceinline__ int wrapc(const Lv<T>& L, int d, int v) {
+    if (L.per[d]) {
+        if (v < 0) v += L.n[d];
+        else if (v >= L.n[d]) v -= L.n[d];
+    }
+    return v;
+}
+
+// ---- field accessors -------------------------------------------------------------
+template <typename T>
+struct UField {
+    const T* __restrict__ u;
+    int N;
+    __device__ __forceinline__ T operator()(int k, int q) const { return u[k * N + q]; }
+};
+
+// Unit vector e_(kk, p0): the operator applied to it gives column (kk, p0).
+template <typename T>
+struct UProbe {
+    int p0, kk;
+    __device__ __forceinline__ T operator()(int k, int q) const {
+        return (k == kk && q == p0) ? T(1) : T(0);
+    }
+};
+
+// ---- generic boundary-node row ---------------------------------------------------
+// Value g at coordinates (cx, cy, cz) via functor G(int q).
+// First derivative in direction l at node c: one-sided where c lies on a boundary
+// plane of l, central otherwise.
+template <typename T, class G>
+__device__ __forceinline__ T deriv_at(const Lv<T>& L, const G& g, const int c[3], int l) {
+    int a[3] = {c[0], c[1], c[2]};
+    int side = 0;
+    if (!L.per[l]) {
+        if (c[l] == 0) side = -1;
+        else if (c[l] == L.n[l] - 1) side = 1;
+    }
+    if (side == 0) {
+        a[l] = wrapc(L, l, c[l] + 1);
+        const T up = g(lin(L, a[0], a[1], a[2]));
+        a[l] = wrapc(L, l, c[l] - 1);
+        const T um = g(lin(L, a[0], a[1], a[2]));
+        return (up - um) * L.inv2h[l];
+    }
+    const int dirn = -side;   // inward
+    const T g0 = g(lin(L, a[0], a[1], a[2]));
+    a[l] = c[l] + dirn;
+    const T g1 = g(lin(L, a[0], a[1], a[2]));
+    a[l] = c[l] + 2 * dirn;
+    const T g2 = g(lin(L, a[0], a[1], a[2]));
+    return T(dirn) * (T(-3) * g0 + T(4) * g1 - g2) * L.inv2h[l];
+}
+
+// Row i (interior or traction type) at a boundary node, generic in the field.
+template <typename T, int KIND, class U>
+__device__ __noinline__ T pde_row_generic(const Lv<T>& L, const U& u, const NodeInfo& ni, int i) {
+    const int* c = ni.c;
+    const int p = lin(L, c[0], c[1], c[2]);
+    T acc = T(0);
+    // product-rule terms of the non-boundary directions
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (ni.side[j] != 0) continue;
+        int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+        cp[j] = wrapc(L, j, c[j] + 1);
+        cm[j] = wrapc(L, j, c[j] - 1);
+        const int qp = lin(L, cp[0], cp[1], cp[2]);
+        const int qm = lin(L, cm[0], cm[1], cm[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            auto uk = [&](int q) { return u(k, q); };
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                if (!Cnz<T, KIND>(i, j, k, l)) continue;
+                const T C0 = Cm<T, KIND>(L, p, i, j, k, l);
+                const T dC = (Cm<T, KIND>(L, qp, i, j, k, l) - Cm<T, KIND>(L, qm, i, j, k, l)) * L.inv2h[j];
+                const T Dl = deriv_at(L, uk, c, l);
+                T DD;
+                if (l == j) {
+                    DD = (u(k, qp) - T(2) * u(k, p) + u(k, qm)) * L.invh2[j];
+                } else {
+                    // one-sided or central derivative in l of the central difference in j
+                    auto gj = [&](int q) {
+                        // q is a node on the same j-line position as c shifted in l only;
+                        // recover its coordinates to shift in j
+                        const int qx = q % L.n[0];
+                        const int qy = (q / L.n[0]) % L.n[1];
+                        const int qz = q / (L.n[0] * L.n[1]);
+                        int a[3] = {qx, qy, qz};
+                        int b[3] = {qx, qy, qz};
+                        a[j] = wrapc(L, j, a[j] + 1);
+                        b[j] = wrapc(L, j, b[j] - 1);
+                        return (u(k, lin(L, a[0], a[1], a[2])) - u(k, lin(L, b[0], b[1], b[2]))) * L.inv2h[j];
+                    };
+                    DD = deriv_at(L, gj, c, l);
+                }
+                acc += dC * Dl + C0 * DD;
+            }
+        }
+    }
+    // half-cell terms of the boundary directions
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (ni.side[a] == 0) continue;
+        const T s = T(ni.side[a]);
+        const int inward = -ni.side[a];
+        int cn[3] = {c[0], c[1], c[2]};
+        cn[a] = c[a] + inward;
+        const int qn = lin(L, cn[0], cn[1], cn[2]);
+        T sacc = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            auto uk = [&](int q) { return u(k, q); };
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                if (!Cnz<T, KIND>(i, a, k, l)) continue;
+                const T Cbar = T(0.5) * (Cm<T, KIND>(L, p, i, a, k, l) + Cm<T, KIND>(L, qn, i, a, k, l));
+                T Dbar;
+                if (l == a) {
+                    Dbar = T(inward) * (u(k, qn) - u(k, p)) * L.invh[a];
+                } else {
+                    Dbar = T(0.5) * (deriv_at(L, uk, c, l) + deriv_at(L, uk, cn, l));
+                }
+                sacc += Cbar * Dbar;
+            }
+        }
+        acc += -(T(2) * L.invh[a]) * s * sacc;
+    }
+    return acc;
+}
+
+// Neumann row i at a boundary node.
+template <typename T, int KIND, class U>
+__device__ __noinline__ T neumann_row(const Lv<T>& L, const U& u, const NodeInfo& ni, int i) {
+    const int p = lin(L, ni.c[0], ni.c[1], ni.c[2]);
+    T acc = T(0);
+    auto ui = [&](int q) { return u(i, q); };
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (ni.side[a] == 0) continue;
+        const int f = 2 * a + (ni.side[a] > 0 ? 1 : 0);
+        if (L.bc[f][i] != ROW_NEUMANN) continue;
+        const T C = Cm<T, KIND>(L, p, i, a, i, a);
+        acc += -(T(2) * L.invh[a]) * C * T(ni.side[a]) * deriv_at(L, ui, ni.c, a);
+    }
+    return acc;
+}
+
+// Row i of A u at a boundary node (Dirichlet rows return u_i).
+template <typename T, int KIND, class U>
+__device__ __forceinline__ T boundary_row(const Lv<T>& L, const U& u, const NodeInfo& ni, int i, int type) {
+    if (type == ROW_DIRICHLET) return u(i, lin(L, ni.c[0], ni.c[1], ni.c[2]));
+    if (type == ROW_NEUMANN) return neumann_row<T, KIND>(L, u, ni, i);
+    return pde_row_generic<T, KIND>(L, u, ni, i);
+}
+
+// ---- interior fast path ------------------------------------------------------------
+// All three rows of D_H u at a node that lies on no boundary plane.
+template <typename T, int KIND>
+__device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restrict__ u,
+                                              int x, int y, int z, T out[3]) {
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int N = L.N;
+    int X[3] = {x - 1, x, x + 1}, Y[3] = {y - 1, y, y + 1}, Z[3] = {z - 1, z, z + 1};
+    if (L.per[0]) { if (X[0] < 0) X[0] += nx; if (X[2] >= nx) X[2] -= nx; }
+    if (L.per[1]) { if (Y[0] < 0) Y[0] += ny; if (Y[2] >= ny) Y[2] -= ny; }
+    if (L.per[2]) { if (Z[0] < 0) Z[0] += nz; if (Z[2] >= nz) Z[2] -= nz; }
+    const int Ys[3] = {Y[0] * nx, Y[1] * nx, Y[2] * nx};
+    const int Zs[3] = {Z[0] * nx * ny, Z[1] * nx * ny, Z[2] * nx * ny};
+#define IDX(dx, dy, dz) (X[(dx) + 1] + Ys[(dy) + 1] + Zs[(dz) + 1])
+    const int p = IDX(0, 0, 0);
+    const int qp[3] = {IDX(1, 0, 0), IDX(0, 1, 0), IDX(0, 0, 1)};
+    const int qm[3] = {IDX(-1, 0, 0), IDX(0, -1, 0), IDX(0, 0, -1)};
+    // pair (j,l) corner indices: ++, +-, -+, --
+    const int cr[3][4] = {
+        {IDX(0, 1, 1), IDX(0, 1, -1), IDX(0, -1, 1), IDX(0, -1, -1)},   // pair (1,2)
+        {IDX(1, 0, 1), IDX(1, 0, -1), IDX(-1, 0, 1), IDX(-1, 0, -1)},   // pair (0,2)
+        {IDX(1, 1, 0), IDX(1, -1, 0), IDX(-1, 1, 0), IDX(-1, -1, 0)}};  // pair (0,1)
+#undef IDX
+    T G[3][3];      // du_k/dx_l
+    T Hd[3][3];     // d2u_k/dx_j2
+    T Hm[3][3];     // mixed: Hm[k][pair]
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T* uk = u + k * N;
+        const T u0 = uk[p];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const T up = uk[qp[l]], um = uk[qm[l]];
+            G[k][l] = (up - um) * L.inv2h[l];
+            Hd[k][l] = (up - T(2) * u0 + um) * L.invh2[l];
+        }
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr)
+            Hm[k][pr] = (uk[cr[pr][0]] - uk[cr[pr][1]] - uk[cr[pr][2]] + uk[cr[pr][3]]) * L.inv4hh[pr];
+    }
+    // engineering strain of the gradient, Voigt order
+    const T e[6] = {G[0][0], G[1][1], G[2][2], G[1][2] + G[2][1], G[0][2] + G[2][0], G[0][1] + G[1][0]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i] = T(0);
+    if (KIND == 2) {
+        // isotropic: C_ijkl = lam d_ij d_kl + mu (d_ik d_jl + d_il d_jk)
+        const T* lamp = L.mod;
+        const T* mup = L.mod + N;
+        const T lam = lamp[p], mu = mup[p];
+        T dlam[3], dmu[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            dlam[j] = (lamp[qp[j]] - lamp[qm[j]]) * L.inv2h[j];
+            dmu[j] = (mup[qp[j]] - mup[qm[j]]) * L.inv2h[j];
+        }
+        const T div = G[0][0] + G[1][1] + G[2][2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            // (d_j C_ijkl) G_kl = dlam_i div + dmu_j (G_ij + G_ji)
+            T t1 = dlam[i] * div;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) t1 += dmu[j] * (G[i][j] + G[j][i]);
+            // C_ijkl H_k,jl = lam d_i(div) + mu (lap u_i + d_i div)
+            T lap = Hd[i][0] + Hd[i][1] + Hd[i][2];
+            T graddiv = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) graddiv += (k == i) ? Hd[k][k] : Hm[k][pair_index(i, k)];
+            out[i] = t1 + (lam + mu) * graddiv + mu * lap;
+        }
+    } else {
+        const T* m = L.mod;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int I = voigt(i, j);
+                // term 1: (d_j C_(ij)V) e_V
+#pragma unroll
+                for (int V = 0; V < 6; ++V) {
+                    const T* cp = m + upper(I, V) * N;
+                    acc += (cp[qp[j]] - cp[qm[j]]) * L.inv2h[j] * e[V];
+                }
+                // term 2: C_ijkl d_j d_l u_k
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+#pragma unroll
+                    for (int l = 0; l < 3; ++l) {
+                        const T c0 = m[upper(I, voigt(k, l)) * N + p];
+                        const T H = (j == l) ? Hd[k][j] : Hm[k][pair_index(j, l)];
+                        acc += c0 * H;
+                    }
+                }
+            }
+            out[i] = acc;
+        }
+    }
+}
+
+// Diagonal 3x3 block of an interior node: B_ik = -2 sum_j C_ijkj / h_j^2.
+template <typename T, int KIND>
+__device__ __forceinline__ void interior_block(const Lv<T>& L, int p, T B[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (Cnz<T, KIND>(i, j, k, j)) acc += Cm<T, KIND>(L, p, i, j, k, j) * (T(-2) * L.invh2[j]);
+            B[i][k] = acc;
+        }
+}
+
+// Diagonal block of a boundary node by probing its rows with unit vectors.
+template <typename T, int KIND>
+__device__ __noinline__ void boundary_block(const Lv<T>& L, const NodeInfo& ni, const int types[3],
+                                               T B[3][3]) {
+    const int p = lin(L, ni.c[0], ni.c[1], ni.c[2]);
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+        UProbe<T> e{p, k};
+#pragma unroll 1
+        for (int i = 0; i < 3; ++i) B[i][k] = boundary_row<T, KIND>(L, e, ni, i, types[i]);
+    }
+}
+
+// Solve B d = r for a 3x3 block (explicit inverse by cofactors).
+template <typename T>
+__device__ __forceinline__ void solve3(const T B[3][3], const T r[3], T d[3]) {
+    const T c00 = B[1][1] * B[2][2] - B[1][2] * B[2][1];
+    const T c01 = B[1][2] * B[2][0] - B[1][0] * B[2][2];
+    const T c02 = B[1][0] * B[2][1] - B[1][1] * B[2][0];
+    const T det = B[0][0] * c00 + B[0][1] * c01 + B[0][2] * c02;
+    const T id = T(1) / det;
+    const T i00 = c00 * id, i10 = c01 * id, i20 = c02 * id;
+    const T i01 = (B[0][2] * B[2][1] - B[0][1] * B[2][2]) * id;
+    const T i11 = (B[0][0] * B[2][2] - B[0][2] * B[2][0]) * id;
+    const T i21 = (B[0][1] * B[2][0] - B[0][0] * B[2][1]) * id;
+    const T i02 = (B[0][1] * B[1][2] - B[0][2] * B[1][1]) * id;
+    const T i12 = (B[0][2] * B[1][0] - B[0][0] * B[1][2]) * id;
+    const T i22 = (B[0][0] * B[1][1] - B[0][1] * B[1][0]) * id;
+    d[0] = i00 * r[0] + i01 * r[1] + i02 * r[2];
+    d[1] = i10 * r[0] + i11 * r[1] + i12 * r[2];
+    d[2] = i20 * r[0] + i21 * r[1] + i22 * r[2];
+}
+
+// ---- rigid-body modes and the equilibrating load -------------------------------------
+// Free rigid modes W_q = sum_m basis[m][q] R_m, R_0..2 translations, R_3..5 rotations
+// e_a x (x - ctr); zero on Dirichlet rows.
+struct NullInfo {
+    int m;
+    double basis[6][6];
+    double ctr[3];
+    double lo[3];
+    double h[3];
+};
+
+__device__ __forceinline__ double rigid_mode(const NullInfo& nf, int mode, int c, const int xyz[3]) {
+    if (mode < 3) return mode == c ? 1.0 : 0.0;
+    const double d[3] = {nf.lo[0] + nf.h[0] * xyz[0] - nf.ctr[0], nf.lo[1] + nf.h[1] * xyz[1] - nf.ctr[1],
+                         nf.lo[2] + nf.h[2] * xyz[2] - nf.ctr[2]};
+    const int a = mode - 3;
+    const int b = (a + 1) % 3, e = (a + 2) % 3;
+    if (c == b) return -d[e];
+    if (c == e) return d[b];
+    return 0.0;
+}
+
+// W_q(c) at a node (caller masks Dirichlet rows).
+__device__ __forceinline__ double null_vec(const NullInfo& nf, int q, int c, const int xyz[3]) {
+    double v = 0.0;
+#pragma unroll 1
+    for (int mode = 0; mode < 6; ++mode) {
+        const double b = nf.basis[mode][q];
+        if (b != 0.0) v += b * rigid_mode(nf, mode, c, xyz);
+    }
+    return v;
+}
+
+// sum_q coef[q] W_q(c): the equilibrating load at a non-Dirichlet row.
+__device__ __forceinline__ double null_combo(const NullInfo& nf, const double* coef, int c, const int xyz[3]) {
+    double v = 0.0;
+#pragma unroll 1
+    for (int q = 0; q < nf.m; ++q) v += coef[q] * null_vec(nf, q, c, xyz);
+    return v;
+}
+
+}  // namespace elas

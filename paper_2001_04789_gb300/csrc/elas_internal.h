@@ -1,0 +1,89 @@
+// Host-side interface between the C ABI layer and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "elas_device.cuh"
+
+namespace elas {
+
+constexpr int kBlock = 256;
+constexpr int kMaxPartials = 4096;   // reduction blocks per launch (grid-stride beyond)
+constexpr int kPartialStride = 8;    // doubles per block partial: sumsq + 6 W^T r + pad
+
+// Boundary data of the finest level used by the right-hand side.
+struct BoundaryData {
+    double uniform[6][3];
+    const double* face[6];          // per-node data of face f (3 x N), or null
+};
+
+struct RhsInputs {
+    const double* eps0;             // 6 x N or null
+    const double* body;             // 3 x N or null
+    double mean_strain[6];
+    int has_mean_strain;
+};
+
+// Number of kernel launches issued by this library since load (all contexts).
+unsigned long long launch_count();
+void count_launch(int n = 1);
+
+// Launchers (all enqueue on `s`).
+void launch_rhs(const Lv<double>& L, const RhsInputs& in, const BoundaryData& bd, double* f, cudaStream_t s);
+void launch_dirichlet(const Lv<double>& L, const BoundaryData& bd, double* u, int keep_free, cudaStream_t s);
+
+template <typename T>
+void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s);
+
+// r = f - lam.W - A u (lam optional); writes r as TR; per-block partials of
+// sum r^2 and W^T r when partials != null.
+template <typename T, typename TR>
+void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf, const double* lam,
+                     TR* r, double* partials, int* nblocks, cudaStream_t s);
+
+// One colour of the red-black block smoother, u_in -> u_out (all nodes written).
+template <typename T>
+void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
+                       const NullInfo* nf, const double* lam, cudaStream_t s);
+
+// fc = R (r - dlam.W) (dlam optional)
+template <typename T>
+void launch_restrict(const Lv<T>& Lf, const Lv<T>& Lc, const T* r, T* fc, const NullInfo* nf,
+                     const double* dlam, cudaStream_t s);
+
+template <typename T>
+void launch_prolong_add(const Lv<T>& Lf, const Lv<T>& Lc, const T* ec, T* u, cudaStream_t s);
+
+template <typename T>
+void launch_restrict_moduli(const Lv<T>& Lf, const Lv<T>& Lc, const T* mf, T* mc, cudaStream_t s);
+
+void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s);
+void launch_add_correction(const Lv<double>& L, double* u, const float* e, cudaStream_t s);
+void launch_add_correction64(const Lv<double>& L, double* u, const double* e, cudaStream_t s);
+
+// Coarsest level: dense matrix over the listed free DOFs (plus m bordering rows and
+// columns of the free rigid modes), its inverse, and the solve.
+void launch_bottom_assemble(const Lv<double>& L, const int* dofs, int nfree, const NullInfo& nf,
+                            double* A, cudaStream_t s);
+void launch_invert(double* A, double* Ainv, int n, int* singular_flag, cudaStream_t s);
+template <typename T>
+void launch_bottom_solve(const Lv<T>& L, const int* dofs, int nfree, int ntot, const double* Ainv,
+                         const T* f, T* u, double* work, cudaStream_t s);
+
+// Deterministic final reduction of residual partials; when nf.m > 0 also the
+// equilibrating-load update dlam = G^-1 W^T r, lam += dlam (if update_lam),
+// and the norm of r - dlam.W.  out[0] = sum r^2 (corrected).
+void launch_finalize(const double* partials, int nblocks, const NullInfo& nf, const double* Ginv,
+                     const double* G, double* lam, double* dlam, double* out, int update_lam,
+                     cudaStream_t s);
+
+// W^T u partials (and W^T W at setup when gram != 0).
+void launch_null_dots(const Lv<double>& L, const NullInfo& nf, const double* u, double* partials,
+                      int* nblocks, int gram, cudaStream_t s);
+void launch_sum_partials(const double* partials, int nblocks, int width, double* out, cudaStream_t s);
+// u -= sum_q coef[q] W_q, coef = Ginv (W^T u) computed on the device
+void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* Ginv, const double* wtu,
+                        double* u, cudaStream_t s);
+
+}  // namespace elas

@@ -1,0 +1,810 @@
+// CUDA kernels of the matrix-free multigrid path (sm_103a).
+//
+// One thread per node (per node pair in the smoother).  Fields are structure of
+// arrays, so every warp reads and writes contiguous x-runs of each plane; the
+// stencil's neighbour reuse is served by L1/L2.  Reductions are deterministic:
+// warp shuffles, one partial per block, then a single-block fixed-order sum.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "elas_internal.h"
+
+namespace elas {
+
+static unsigned long long g_launches = 0;
+unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+void count_launch(int n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+
+namespace {
+
+inline int blocks_for(size_t n) { return (int)((n + kBlock - 1) / kBlock); }
+
+__device__ __forceinline__ void coords_of(int p, const int n[3], int c[3]) {
+    c[0] = p % n[0];
+    const int r = p / n[0];
+    c[1] = r % n[1];
+    c[2] = r / n[1];
+}
+
+// Block-wide sum of `width` doubles per thread into partials[blockIdx * kPartialStride + w].
+template <int MAXW>
+__device__ __forceinline__ void block_reduce_store(double (&v)[MAXW], int width, double* partials) {
+    __shared__ double sm[kBlock / 32][MAXW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int w = 0; w < MAXW; ++w) {
+        if (w >= width) break;
+        double x = v[w];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sm[warp][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            if (w >= width) break;
+            double x = (lane < kBlock / 32) ? sm[lane][w] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) partials[blockIdx.x * kPartialStride + w] = x;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T face_datum(const BoundaryData& bd, int f, int c, int p, int N) {
+    return bd.face[f] ? T(bd.face[f][c * N + p]) : T(bd.uniform[f][c]);
+}
+
+// ---------------------------------------------------------------------------
+// right-hand side (setup, FP64)
+// ---------------------------------------------------------------------------
+template <int KIND>
+__global__ void k_rhs(Lv<double> L, RhsInputs in, BoundaryData bd, double* __restrict__ f) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
+    int c[3];
+    coords_of(p, L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    const int N = L.N;
+    auto eps = [&](int k, int l, int q) -> double {
+        return in.eps0 ? in.eps0[voigt(k, l) * N + q] : 0.0;
+    };
+    for (int i = 0; i < 3; ++i) {
+        const int t = row_type(L, ni, i);
+        double v = 0.0;
+        if (t == ROW_INTERIOR || t == ROW_TRACTION) {
+            if (in.body) v -= in.body[i * N + p];
+            for (int j = 0; j < 3; ++j) {
+                if (ni.side[j] != 0) continue;
+                int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+                cp[j] = wrapc(L, j, c[j] + 1);
+                cm[j] = wrapc(L, j, c[j] - 1);
+                const int qp = lin(L, cp[0], cp[1], cp[2]), qm = lin(L, cm[0], cm[1], cm[2]);
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) {
+                        const double C0 = (KIND == 2) ? Cm<double, 2>(L, p, i, j, k, l) : Cm<double, 21>(L, p, i, j, k, l);
+                        const double Cp = (KIND == 2) ? Cm<double, 2>(L, qp, i, j, k, l) : Cm<double, 21>(L, qp, i, j, k, l);
+                        const double Cn = (KIND == 2) ? Cm<double, 2>(L, qm, i, j, k, l) : Cm<double, 21>(L, qm, i, j, k, l);
+                        const double ebar = in.has_mean_strain ? in.mean_strain[voigt(k, l)] : 0.0;
+                        v += (Cp - Cn) * L.inv2h[j] * (eps(k, l, p) - ebar) +
+                             C0 * (eps(k, l, qp) - eps(k, l, qm)) * L.inv2h[j];
+                    }
+            }
+            if (t == ROW_TRACTION) {
+                for (int a = 0; a < 3; ++a) {
+                    if (ni.side[a] == 0) continue;
+                    const int fc = 2 * a + (ni.side[a] > 0 ? 1 : 0);
+                    const double s = ni.side[a];
+                    int cn[3] = {c[0], c[1], c[2]};
+                    cn[a] -= ni.side[a];
+                    const int qn = lin(L, cn[0], cn[1], cn[2]);
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; ++k)
+                        for (int l = 0; l < 3; ++l) {
+                            const double Ca = (KIND == 2) ? Cm<double, 2>(L, p, i, a, k, l) : Cm<double, 21>(L, p, i, a, k, l);
+                            const double Cb = (KIND == 2) ? Cm<double, 2>(L, qn, i, a, k, l) : Cm<double, 21>(L, qn, i, a, k, l);
+                            acc += 0.5 * (Ca + Cb) * 0.5 * (eps(k, l, p) + eps(k, l, qn));
+                        }
+                    v -= (2.0 * L.invh[a]) * (face_datum<double>(bd, fc, i, p, N) + s * acc);
+                }
+            }
+        } else if (t == ROW_NEUMANN) {
+            for (int a = 0; a < 3; ++a) {
+                if (ni.side[a] == 0) continue;
+                const int fc = 2 * a + (ni.side[a] > 0 ? 1 : 0);
+                if (L.bc[fc][i] != ROW_NEUMANN) continue;
+                const double C = (KIND == 2) ? Cm<double, 2>(L, p, i, a, i, a) : Cm<double, 21>(L, p, i, a, i, a);
+                v += -(2.0 * L.invh[a]) * C * face_datum<double>(bd, fc, i, p, N);
+            }
+        }
+        f[i * N + p] = v;
+    }
+}
+
+__global__ void k_dirichlet(Lv<double> L, BoundaryData bd, double* __restrict__ u, int keep_free) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
+    int c[3];
+    coords_of(p, L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    for (int i = 0; i < 3; ++i) {
+        const int t = row_type(L, ni, i);
+        if (t == ROW_DIRICHLET) {
+            // lowest-numbered Dirichlet face of this node wins
+            double v = 0.0;
+            for (int f = 5; f >= 0; --f) {
+                const int d = f / 2;
+                const int on = (f % 2 == 0) ? (ni.side[d] < 0) : (ni.side[d] > 0);
+                if (on && L.bc[f][i] == ROW_DIRICHLET) v = face_datum<double>(bd, f, i, p, L.N);
+            }
+            u[i * L.N + p] = v;
+        } else if (!keep_free) {
+            u[i * L.N + p] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// operator, residual
+// ---------------------------------------------------------------------------
+template <typename T, int KIND>
+__device__ __forceinline__ void all_rows(const Lv<T>& L, const T* __restrict__ u, int x, int y, int z,
+                                         const NodeInfo& ni, int types[3], T out[3]) {
+    if (!ni.boundary) {
+        types[0] = types[1] = types[2] = ROW_INTERIOR;
+        interior_rows<T, KIND>(L, u, x, y, z, out);
+    } else {
+        UField<T> uf{u, L.N};
+        for (int i = 0; i < 3; ++i) {
+            types[i] = row_type(L, ni, i);
+            out[i] = boundary_row<T, KIND>(L, uf, ni, i, types[i]);
+        }
+    }
+}
+
+template <typename T, int KIND>
+__global__ void k_apply(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
+    int c[3];
+    coords_of(p, L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    int types[3];
+    T v[3];
+    all_rows<T, KIND>(L, u, c[0], c[1], c[2], ni, types, v);
+    for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
+}
+
+template <typename T, typename TR, int KIND, bool NORM>
+__global__ void __launch_bounds__(kBlock) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
+                                                    NullInfo nf, const double* __restrict__ lam,
+                                                    TR* __restrict__ r, double* __restrict__ partials) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (p < L.N) {
+        int c[3];
+        coords_of(p, L.n, c);
+        const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+        int types[3];
+        T v[3];
+        all_rows<T, KIND>(L, u, c[0], c[1], c[2], ni, types, v);
+        for (int i = 0; i < 3; ++i) {
+            T ri = T(0);
+            if (types[i] != ROW_DIRICHLET) {
+                T fi = f[i * L.N + p];
+                if (lam && nf.m > 0) fi -= T(null_combo(nf, lam, i, c));
+                ri = fi - v[i];
+                if (NORM) {
+                    const double rd = (double)ri;
+                    acc[0] += rd * rd;
+                    for (int q = 0; q < nf.m; ++q) acc[1 + q] += null_vec(nf, q, i, c) * rd;
+                }
+            }
+            r[i * L.N + p] = (TR)ri;
+        }
+    }
+    if (NORM) block_reduce_store<7>(acc, 1 + nf.m, partials);
+}
+
+// ---------------------------------------------------------------------------
+// red-black smoother: each thread owns the node pair (2m, 2m+1) of an x-row, updates
+// the one of the active colour and copies the other; all rows are evaluated with
+// the values from before the half-sweep (Jacobi within the colour).
+// ---------------------------------------------------------------------------
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kBlock) k_half_sweep(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
+                                                      const T* __restrict__ f, int colour, NullInfo nf,
+                                                      const double* __restrict__ lam) {
+    const int npair = (L.n[0] + 1) >> 1;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npair * L.n[1] * L.n[2]) return;
+    const int m = t % npair;
+    const int yz = t / npair;
+    const int y = yz % L.n[1], z = yz / L.n[1];
+    const int x0 = 2 * m;
+    const int xa = x0 + ((x0 + y + z + colour) & 1);   // active node
+    const int xi = x0 + 1 - (xa - x0);                  // inactive node
+    const int N = L.N;
+    if (xi < L.n[0]) {
+        const int q = lin(L, xi, y, z);
+        uo[q] = u[q];
+        uo[N + q] = u[N + q];
+        uo[2 * N + q] = u[2 * N + q];
+    }
+    if (xa >= L.n[0]) return;
+    const int p = lin(L, xa, y, z);
+    const NodeInfo ni = node_info(L, xa, y, z);
+    int types[3];
+    T v[3];
+    all_rows<T, KIND>(L, u, xa, y, z, ni, types, v);
+    T r[3], B[3][3];
+    for (int i = 0; i < 3; ++i) {
+        if (types[i] == ROW_DIRICHLET) {
+            r[i] = T(0);
+        } else {
+            T fi = f[i * N + p];
+            if (lam && nf.m > 0) {
+                const int c[3] = {xa, y, z};
+                fi -= T(null_combo(nf, lam, i, c));
+            }
+            r[i] = fi - v[i];
+        }
+    }
+    if (!ni.boundary) interior_block<T, KIND>(L, p, B);
+    else boundary_block<T, KIND>(L, ni, types, B);
+    T d[3];
+    solve3(B, r, d);
+    for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
+}
+
+// ---------------------------------------------------------------------------
+// transfers (Section 3.2)
+// ---------------------------------------------------------------------------
+// weights of fine offsets -1, 0, +1 for coarse index I in one direction
+template <typename T>
+__device__ __forceinline__ void restrict_weights(const Lv<T>& Lc, int d, int I, T w[3]) {
+    if (!Lc.per[d] && I == 0) { w[0] = T(0); w[1] = T(0.5); w[2] = T(0.5); return; }
+    if (!Lc.per[d] && I == Lc.n[d] - 1) { w[0] = T(0.5); w[1] = T(0.5); w[2] = T(0); return; }
+    w[0] = T(0.25); w[1] = T(0.5); w[2] = T(0.25);
+}
+
+template <typename T>
+__global__ void k_restrict(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ r, T* __restrict__ fc, NullInfo nf,
+                           const double* __restrict__ dlam) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= Lc.N) return;
+    int C[3];
+    coords_of(P, Lc.n, C);
+    const NodeInfo nic = node_info(Lc, C[0], C[1], C[2]);
+    T wx[3], wy[3], wz[3];
+    restrict_weights(Lc, 0, C[0], wx);
+    restrict_weights(Lc, 1, C[1], wy);
+    restrict_weights(Lc, 2, C[2], wz);
+    T acc[3] = {T(0), T(0), T(0)};
+    const bool corr = dlam && nf.m > 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        if (wz[dz + 1] == T(0)) continue;
+        const int fz = wrapc(Lf, 2, 2 * C[2] + dz);
+        for (int dy = -1; dy <= 1; ++dy) {
+            if (wy[dy + 1] == T(0)) continue;
+            const int fy = wrapc(Lf, 1, 2 * C[1] + dy);
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (wx[dx + 1] == T(0)) continue;
+                const int fx = wrapc(Lf, 0, 2 * C[0] + dx);
+                const T w = wx[dx + 1] * wy[dy + 1] * wz[dz + 1];
+                const int q = lin(Lf, fx, fy, fz);
+                const int cf[3] = {fx, fy, fz};
+                NodeInfo nif;
+                if (corr) nif = node_info(Lf, fx, fy, fz);
+                for (int i = 0; i < 3; ++i) {
+                    T v = r[i * Lf.N + q];
+                    if (corr && row_type(Lf, nif, i) != ROW_DIRICHLET) v -= T(null_combo(nf, dlam, i, cf));
+                    acc[i] += w * v;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < 3; ++i)
+        fc[i * Lc.N + P] = (row_type(Lc, nic, i) == ROW_DIRICHLET) ? T(0) : acc[i];
+}
+
+template <typename T>
+__global__ void k_prolong_add(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ ec, T* __restrict__ u) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Lf.N) return;
+    int c[3];
+    coords_of(p, Lf.n, c);
+    const NodeInfo ni = node_info(Lf, c[0], c[1], c[2]);
+    int lo[3], hi[3];
+    T wl[3], wh[3];
+    for (int d = 0; d < 3; ++d) {
+        if ((c[d] & 1) == 0) {
+            lo[d] = hi[d] = c[d] >> 1;
+            wl[d] = T(1);
+            wh[d] = T(0);
+        } else {
+            lo[d] = c[d] >> 1;
+            hi[d] = lo[d] + 1;
+            if (Lc.per[d] && hi[d] >= Lc.n[d]) hi[d] -= Lc.n[d];
+            wl[d] = T(0.5);
+            wh[d] = T(0.5);
+        }
+    }
+    for (int i = 0; i < 3; ++i) {
+        if (row_type(Lf, ni, i) == ROW_DIRICHLET) continue;
+        const T* e = ec + i * Lc.N;
+        T v = T(0);
+        for (int bz = 0; bz < 2; ++bz) {
+            const T wzv = bz ? wh[2] : wl[2];
+            if (wzv == T(0)) continue;
+            const int cz = bz ? hi[2] : lo[2];
+            for (int by = 0; by < 2; ++by) {
+                const T wyv = by ? wh[1] : wl[1];
+                if (wyv == T(0)) continue;
+                const int cy = by ? hi[1] : lo[1];
+                for (int bx = 0; bx < 2; ++bx) {
+                    const T wxv = bx ? wh[0] : wl[0];
+                    if (wxv == T(0)) continue;
+                    const int cx = bx ? hi[0] : lo[0];
+                    v += wxv * wyv * wzv * e[lin(Lc, cx, cy, cz)];
+                }
+            }
+        }
+        u[i * Lf.N + p] += v;
+    }
+}
+
+template <typename T>
+__global__ void k_restrict_moduli(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ mf, T* __restrict__ mc) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= Lc.N) return;
+    int C[3];
+    coords_of(P, Lc.n, C);
+    T wx[3], wy[3], wz[3];
+    restrict_weights(Lc, 0, C[0], wx);
+    restrict_weights(Lc, 1, C[1], wy);
+    restrict_weights(Lc, 2, C[2], wz);
+    for (int k = 0; k < Lf.K; ++k) {
+        T acc = T(0);
+        for (int dz = -1; dz <= 1; ++dz) {
+            if (wz[dz + 1] == T(0)) continue;
+            const int fz = wrapc(Lf, 2, 2 * C[2] + dz);
+            for (int dy = -1; dy <= 1; ++dy) {
+                if (wy[dy + 1] == T(0)) continue;
+                const int fy = wrapc(Lf, 1, 2 * C[1] + dy);
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (wx[dx + 1] == T(0)) continue;
+                    const int fx = wrapc(Lf, 0, 2 * C[0] + dx);
+                    acc += wx[dx + 1] * wy[dy + 1] * wz[dz + 1] * mf[k * Lf.N + lin(Lf, fx, fy, fz)];
+                }
+            }
+        }
+        mc[k * Lc.N + P] = acc;
+    }
+}
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+template <typename TE>
+__global__ void k_add_correction(Lv<double> L, double* __restrict__ u, const TE* __restrict__ e) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
+    int c[3];
+    coords_of(p, L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    for (int i = 0; i < 3; ++i)
+        if (row_type(L, ni, i) != ROW_DIRICHLET) u[i * L.N + p] += (double)e[i * L.N + p];
+}
+
+// ---------------------------------------------------------------------------
+// bottom solve
+// ---------------------------------------------------------------------------
+template <int KIND>
+__global__ void k_bottom_assemble(Lv<double> L, const int* __restrict__ dofs, int nfree, NullInfo nf,
+                                  double* __restrict__ A) {
+    const int ntot = nfree + nf.m;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)ntot * ntot) return;
+    const int row = (int)(t / ntot), col = (int)(t % ntot);
+    double v = 0.0;
+    if (row < nfree && col < nfree) {
+        const int ir = dofs[row] / L.N, pr = dofs[row] % L.N;
+        const int ic = dofs[col] / L.N, pc = dofs[col] % L.N;
+        int c[3];
+        coords_of(pr, L.n, c);
+        const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+        const int type = row_type(L, ni, ir);
+        UProbe<double> e{pc, ic};
+        v = boundary_row<double, KIND>(L, e, ni, ir, type == ROW_INTERIOR ? ROW_TRACTION : type);
+    } else if (row < nfree && col >= nfree) {
+        const int ir = dofs[row] / L.N, pr = dofs[row] % L.N;
+        int c[3];
+        coords_of(pr, L.n, c);
+        v = null_vec(nf, col - nfree, ir, c);
+    } else if (row >= nfree && col < nfree) {
+        const int ic = dofs[col] / L.N, pc = dofs[col] % L.N;
+        int c[3];
+        coords_of(pc, L.n, c);
+        v = null_vec(nf, row - nfree, ic, c);
+    }
+    A[t] = v;
+}
+
+// Gauss-Jordan inversion with partial pivoting, one block.
+__global__ void k_invert(double* __restrict__ A, double* __restrict__ X, int n, int* singular) {
+    __shared__ int piv;
+    __shared__ double pval;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) X[i] = ((i / n) == (i % n)) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int col = 0; col < n; ++col) {
+        if (threadIdx.x == 0) {
+            int best = col;
+            double bv = fabs(A[col * n + col]);
+            for (int r = col + 1; r < n; ++r) {
+                const double v = fabs(A[r * n + col]);
+                if (v > bv) { bv = v; best = r; }
+            }
+            piv = best;
+            pval = A[best * n + col];
+            if (bv == 0.0) *singular = 1;
+        }
+        __syncthreads();
+        if (pval == 0.0) return;
+        if (piv != col) {
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                double a = A[col * n + k]; A[col * n + k] = A[piv * n + k]; A[piv * n + k] = a;
+                double x = X[col * n + k]; X[col * n + k] = X[piv * n + k]; X[piv * n + k] = x;
+            }
+        }
+        __syncthreads();
+        const double inv = 1.0 / pval;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            A[col * n + k] *= inv;
+            X[col * n + k] *= inv;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+            const int r = idx / n, k = idx % n;
+            if (r == col) continue;
+            const double fct = A[r * n + col];
+            if (k == col) continue;
+            A[r * n + k] -= fct * A[col * n + k];
+            X[r * n + k] -= fct * X[col * n + k];
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            if (r == col) continue;
+            const double fct = A[r * n + col];
+            X[r * n + col] -= fct * X[col * n + col];
+            A[r * n + col] = 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_bottom_gather(Lv<T> L, const int* __restrict__ dofs, int nfree, int ntot, const T* __restrict__ f,
+                                double* __restrict__ b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntot) return;
+    b[i] = i < nfree ? (double)f[dofs[i]] : 0.0;
+}
+
+template <typename T>
+__global__ void k_bottom_matvec(Lv<T> L, const int* __restrict__ dofs, int nfree, int ntot,
+                                const double* __restrict__ Ainv, const double* __restrict__ b, T* __restrict__ u) {
+    const int row = blockIdx.x;
+    if (row >= nfree) return;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < ntot; k += blockDim.x) acc += Ainv[(size_t)row * ntot + k] * b[k];
+    __shared__ double sm[kBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) s += sm[w];
+        u[dofs[row]] = (T)s;
+    }
+}
+
+template <typename T>
+__global__ void k_zero(T* __restrict__ a, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = T(0);
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(const double* __restrict__ partials, int nblocks, NullInfo nf,
+                           const double* __restrict__ Ginv, const double* __restrict__ G,
+                           double* __restrict__ lam, double* __restrict__ dlam, double* __restrict__ out,
+                           int update_lam) {
+    // fixed-order reduction: thread t sums blocks t, t+256, ...; then a fixed tree
+    __shared__ double sm[kBlock][7];
+    const int width = 1 + nf.m;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int w = 0; w < width; ++w) acc[w] += partials[b * kPartialStride + w];
+    for (int w = 0; w < 7; ++w) sm[threadIdx.x][w] = acc[w];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int w = 0; w < width; ++w) sm[threadIdx.x][w] += sm[threadIdx.x + s][w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double ss = sm[0][0];
+        if (nf.m > 0) {
+            double d[6];
+            for (int q = 0; q < nf.m; ++q) {
+                double v = 0.0;
+                for (int k = 0; k < nf.m; ++k) v += Ginv[q * nf.m + k] * sm[0][1 + k];
+                d[q] = v;
+            }
+            // ||r - d.W||^2 = ||r||^2 - 2 d.(W^T r) + d^T G d
+            double c1 = 0.0, c2 = 0.0;
+            for (int q = 0; q < nf.m; ++q) {
+                c1 += d[q] * sm[0][1 + q];
+                for (int k = 0; k < nf.m; ++k) c2 += d[q] * G[q * nf.m + k] * d[k];
+            }
+            ss = ss - 2.0 * c1 + c2;
+            if (ss < 0.0) ss = 0.0;
+            for (int q = 0; q < nf.m; ++q) {
+                dlam[q] = d[q];
+                if (update_lam) lam[q] += d[q];
+            }
+        }
+        out[0] = ss;
+        for (int w = 1; w < 7; ++w) out[w] = (w < width) ? sm[0][w] : 0.0;
+    }
+}
+
+__global__ void k_null_dots(Lv<double> L, NullInfo nf, const double* __restrict__ u, double* __restrict__ partials,
+                            int gram) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    int width = gram ? nf.m * nf.m : nf.m;
+    if (p < L.N) {
+        int c[3];
+        coords_of(p, L.n, c);
+        const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+        for (int i = 0; i < 3; ++i) {
+            if (row_type(L, ni, i) == ROW_DIRICHLET) continue;
+            if (gram) {
+                // only the upper triangle fits 7 slots for m <= 3; the host calls this
+                // once per row q for larger m (see launch_null_dots)
+            } else {
+                for (int q = 0; q < nf.m; ++q) acc[q] += null_vec(nf, q, i, c) * u[i * L.N + p];
+            }
+        }
+    }
+    block_reduce_store<7>(acc, width > 7 ? 7 : width, partials);
+}
+
+// W^T W row by row: column q0 of the Gram matrix
+__global__ void k_null_gram_row(Lv<double> L, NullInfo nf, int q0, double* __restrict__ partials) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (p < L.N) {
+        int c[3];
+        coords_of(p, L.n, c);
+        const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+        for (int i = 0; i < 3; ++i) {
+            if (row_type(L, ni, i) == ROW_DIRICHLET) continue;
+            const double w0 = null_vec(nf, q0, i, c);
+            for (int q = 0; q < nf.m; ++q) acc[q] += w0 * null_vec(nf, q, i, c);
+        }
+    }
+    block_reduce_store<7>(acc, nf.m, partials);
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int nblocks, int width, double* __restrict__ out) {
+    __shared__ double sm[kBlock][7];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int w = 0; w < width; ++w) acc[w] += partials[b * kPartialStride + w];
+    for (int w = 0; w < 7; ++w) sm[threadIdx.x][w] = acc[w];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int w = 0; w < width; ++w) sm[threadIdx.x][w] += sm[threadIdx.x + s][w];
+        __syncthreads();
+    }
+    if (threadIdx.x < width) out[threadIdx.x] = sm[0][threadIdx.x];
+}
+
+__global__ void k_remove_null(Lv<double> L, NullInfo nf, const double* __restrict__ Ginv,
+                              const double* __restrict__ wtu, double* __restrict__ u) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
+    double coef[6];
+    for (int q = 0; q < nf.m; ++q) {
+        double v = 0.0;
+        for (int k = 0; k < nf.m; ++k) v += Ginv[q * nf.m + k] * wtu[k];
+        coef[q] = v;
+    }
+    int c[3];
+    coords_of(p, L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    for (int i = 0; i < 3; ++i)
+        if (row_type(L, ni, i) != ROW_DIRICHLET) u[i * L.N + p] -= null_combo(nf, coef, i, c);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_rhs(const Lv<double>& L, const RhsInputs& in, const BoundaryData& bd, double* f, cudaStream_t s) {
+    if (L.K == 2) { count_launch(); k_rhs<2><<<blocks_for(L.N), kBlock, 0, s>>>(L, in, bd, f); }
+    else { count_launch(); k_rhs<21><<<blocks_for(L.N), kBlock, 0, s>>>(L, in, bd, f); }
+}
+
+void launch_dirichlet(const Lv<double>& L, const BoundaryData& bd, double* u, int keep_free, cudaStream_t s) {
+    count_launch();
+    k_dirichlet<<<blocks_for(L.N), kBlock, 0, s>>>(L, bd, u, keep_free);
+}
+
+template <typename T>
+void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
+    if (L.K == 2) { count_launch(); k_apply<T, 2><<<blocks_for(L.N), kBlock, 0, s>>>(L, u, out); }
+    else { count_launch(); k_apply<T, 21><<<blocks_for(L.N), kBlock, 0, s>>>(L, u, out); }
+}
+
+template <typename T, typename TR>
+void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf, const double* lam, TR* r,
+                     double* partials, int* nblocks, cudaStream_t s) {
+    NullInfo nfv{};
+    if (nf) nfv = *nf;
+    const int nb = blocks_for(L.N);
+    if (nblocks) *nblocks = nb;
+    if (partials) {
+        if (L.K == 2) { count_launch(); k_residual<T, TR, 2, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials); }
+        else { count_launch(); k_residual<T, TR, 21, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials); }
+    } else {
+        if (L.K == 2) { count_launch(); k_residual<T, TR, 2, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr); }
+        else { count_launch(); k_residual<T, TR, 21, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr); }
+    }
+}
+
+template <typename T>
+void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour, const NullInfo* nf,
+                       const double* lam, cudaStream_t s) {
+    NullInfo nfv{};
+    if (nf) nfv = *nf;
+    const size_t n = (size_t)((L.n[0] + 1) / 2) * L.n[1] * L.n[2];
+    if (L.K == 2) { count_launch(); k_half_sweep<T, 2><<<blocks_for(n), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); }
+    else { count_launch(); k_half_sweep<T, 21><<<blocks_for(n), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); }
+}
+
+template <typename T>
+void launch_restrict(const Lv<T>& Lf, const Lv<T>& Lc, const T* r, T* fc, const NullInfo* nf, const double* dlam,
+                     cudaStream_t s) {
+    NullInfo nfv{};
+    if (nf) nfv = *nf;
+    count_launch();
+    k_restrict<T><<<blocks_for(Lc.N), kBlock, 0, s>>>(Lf, Lc, r, fc, nfv, dlam);
+}
+
+template <typename T>
+void launch_prolong_add(const Lv<T>& Lf, const Lv<T>& Lc, const T* ec, T* u, cudaStream_t s) {
+    count_launch();
+    k_prolong_add<T><<<blocks_for(Lf.N), kBlock, 0, s>>>(Lf, Lc, ec, u);
+}
+
+template <typename T>
+void launch_restrict_moduli(const Lv<T>& Lf, const Lv<T>& Lc, const T* mf, T* mc, cudaStream_t s) {
+    count_launch();
+    k_restrict_moduli<T><<<blocks_for(Lc.N), kBlock, 0, s>>>(Lf, Lc, mf, mc);
+}
+
+void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s) {
+    count_launch();
+    k_to_float<<<blocks_for(n), kBlock, 0, s>>>(in, out, n);
+}
+
+void launch_add_correction(const Lv<double>& L, double* u, const float* e, cudaStream_t s) {
+    count_launch();
+    k_add_correction<float><<<blocks_for(L.N), kBlock, 0, s>>>(L, u, e);
+}
+
+void launch_add_correction64(const Lv<double>& L, double* u, const double* e, cudaStream_t s) {
+    count_launch();
+    k_add_correction<double><<<blocks_for(L.N), kBlock, 0, s>>>(L, u, e);
+}
+
+void launch_bottom_assemble(const Lv<double>& L, const int* dofs, int nfree, const NullInfo& nf, double* A,
+                            cudaStream_t s) {
+    const long long n = (long long)(nfree + nf.m) * (nfree + nf.m);
+    if (n == 0) return;
+    const int nb = (int)((n + kBlock - 1) / kBlock);
+    if (L.K == 2) { count_launch(); k_bottom_assemble<2><<<nb, kBlock, 0, s>>>(L, dofs, nfree, nf, A); }
+    else { count_launch(); k_bottom_assemble<21><<<nb, kBlock, 0, s>>>(L, dofs, nfree, nf, A); }
+}
+
+void launch_invert(double* A, double* Ainv, int n, int* singular_flag, cudaStream_t s) {
+    if (n == 0) return;
+    count_launch();
+    k_invert<<<1, 1024, 0, s>>>(A, Ainv, n, singular_flag);
+}
+
+template <typename T>
+void launch_bottom_solve(const Lv<T>& L, const int* dofs, int nfree, int ntot, const double* Ainv, const T* f, T* u,
+                         double* work, cudaStream_t s) {
+    count_launch();
+    k_zero<T><<<blocks_for((size_t)3 * L.N), kBlock, 0, s>>>(u, (size_t)3 * L.N);
+    if (ntot == 0) return;
+    count_launch();
+    k_bottom_gather<T><<<blocks_for(ntot), kBlock, 0, s>>>(L, dofs, nfree, ntot, f, work);
+    if (nfree > 0) {
+        count_launch();
+        k_bottom_matvec<T><<<nfree, kBlock, 0, s>>>(L, dofs, nfree, ntot, Ainv, work, u);
+    }
+}
+
+void launch_finalize(const double* partials, int nblocks, const NullInfo& nf, const double* Ginv, const double* G,
+                     double* lam, double* dlam, double* out, int update_lam, cudaStream_t s) {
+    count_launch();
+    k_finalize<<<1, kBlock, 0, s>>>(partials, nblocks, nf, Ginv, G, lam, dlam, out, update_lam);
+}
+
+void launch_null_dots(const Lv<double>& L, const NullInfo& nf, const double* u, double* partials, int* nblocks,
+                      int gram, cudaStream_t s) {
+    const int nb = blocks_for(L.N);
+    *nblocks = nb;
+    if (gram) {
+        // gram row q0 = gram - 1
+        count_launch();
+        k_null_gram_row<<<nb, kBlock, 0, s>>>(L, nf, gram - 1, partials);
+    } else {
+        count_launch();
+        k_null_dots<<<nb, kBlock, 0, s>>>(L, nf, u, partials, 0);
+    }
+}
+
+void launch_sum_partials(const double* partials, int nblocks, int width, double* out, cudaStream_t s) {
+    count_launch();
+    k_sum_partials<<<1, kBlock, 0, s>>>(partials, nblocks, width, out);
+}
+
+void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* Ginv, const double* wtu, double* u,
+                        cudaStream_t s) {
+    count_launch();
+    k_remove_null<<<blocks_for(L.N), kBlock, 0, s>>>(L, nf, Ginv, wtu, u);
+}
+
+// explicit instantiations
+template void launch_apply<double>(const Lv<double>&, const double*, double*, cudaStream_t);
+template void launch_apply<float>(const Lv<float>&, const float*, float*, cudaStream_t);
+template void launch_residual<double, double>(const Lv<double>&, const double*, const double*, const NullInfo*,
+                                              const double*, double*, double*, int*, cudaStream_t);
+template void launch_residual<double, float>(const Lv<double>&, const double*, const double*, const NullInfo*,
+                                             const double*, float*, double*, int*, cudaStream_t);
+template void launch_residual<float, float>(const Lv<float>&, const float*, const float*, const NullInfo*,
+                                            const double*, float*, double*, int*, cudaStream_t);
+template void launch_half_sweep<double>(const Lv<double>&, const double*, double*, const double*, int,
+                                        const NullInfo*, const double*, cudaStream_t);
+template void launch_half_sweep<float>(const Lv<float>&, const float*, float*, const float*, int, const NullInfo*,
+                                       const double*, cudaStream_t);
+template void launch_restrict<double>(const Lv<double>&, const Lv<double>&, const double*, double*, const NullInfo*,
+                                      const double*, cudaStream_t);
+template void launch_restrict<float>(const Lv<float>&, const Lv<float>&, const float*, float*, const NullInfo*,
+                                     const double*, cudaStream_t);
+template void launch_prolong_add<double>(const Lv<double>&, const Lv<double>&, const double*, double*, cudaStream_t);
+template void launch_prolong_add<float>(const Lv<float>&, const Lv<float>&, const float*, float*, cudaStream_t);
+template void launch_restrict_moduli<double>(const Lv<double>&, const Lv<double>&, const double*, double*,
+                                             cudaStream_t);
+template void launch_bottom_solve<double>(const Lv<double>&, const int*, int, int, const double*, const double*,
+                                          double*, double*, cudaStream_t);
+template void launch_bottom_solve<float>(const Lv<float>&, const int*, int, int, const double*, const float*, float*,
+                                         double*, cudaStream_t);
+
+}  // namespace elas

@@ -1,0 +1,394 @@
+"""Thin ctypes binding of the C ABI in ``include/elas.h``.
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+PyTorch supplies the device memory (through the caching allocator, passed to the
+library as an allocator callback) and the CUDA stream.  Importing this module
+does not need a GPU; creating a context does, and fails loudly when the library
+or the device is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import microstructure as M
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libelas_gb300.so")
+
+OK = 0
+ERR_NOT_CONVERGED = -3
+ERR_DIVERGED = -4
+HOST, DEVICE = 0, 1
+FP64, MIXED = 0, 1
+HISTORY = 128
+
+
+class ElasError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"elas error {code}: {msg}")
+        self.code = code
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("periodic", C.c_int * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("moduli_kind", C.c_int), ("mixed", C.c_int)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("rel_tol", C.c_double), ("max_cycles", C.c_int),
+                ("nu1", C.c_int), ("nu2", C.c_int), ("warm_start", C.c_int),
+                ("fixed_cycles", C.c_int), ("use_graph", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("rel_residual", C.c_double),
+                ("r0", C.c_double), ("nlam", C.c_int), ("lam", C.c_double * 6),
+                ("seconds", C.c_double), ("rel_history", C.c_double * HISTORY)]
+
+    def as_dict(self):
+        n = min(self.cycles + 1, HISTORY)
+        return {"status": self.status, "cycles": self.cycles, "rel_residual": self.rel_residual,
+                "r0": self.r0, "nlam": self.nlam, "lam": list(self.lam[: self.nlam]),
+                "seconds": self.seconds, "rel_history": list(self.rel_history[:n])}
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, ip, dp = C.c_void_p, C.c_int, C.POINTER(C.c_double)
+    sig = {
+        "elas_ctx_create": (ip, [C.POINTER(vp), ip, C.c_size_t, C.POINTER(Allocator), vp]),
+        "elas_ctx_destroy": (ip, [vp]),
+        "elas_last_error": (C.c_char_p, [vp]),
+        "elas_ctx_bytes_in_use": (C.c_size_t, [vp]),
+        "elas_grid_create": (ip, [vp, C.POINTER(GridDesc), C.POINTER(vp)]),
+        "elas_grid_destroy": (ip, [vp]),
+        "elas_grid_levels": (ip, [vp, C.POINTER(ip)]),
+        "elas_grid_level_dims": (ip, [vp, ip, C.POINTER(ip)]),
+        "elas_grid_bytes": (C.c_size_t, [vp]),
+        "elas_grid_bytes_estimate": (C.c_size_t, [C.POINTER(GridDesc)]),
+        "elas_set_moduli": (ip, [vp, vp, ip]),
+        "elas_set_eigenstrain": (ip, [vp, vp, ip]),
+        "elas_set_body_force": (ip, [vp, vp, ip]),
+        "elas_set_mean_strain": (ip, [vp, dp]),
+        "elas_set_bc": (ip, [vp, ip, ip, ip, C.c_double]),
+        "elas_set_face_values": (ip, [vp, ip, vp, ip]),
+        "elas_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
+        "elas_solve": (ip, [vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "elas_get_displacement": (ip, [vp, vp, ip]),
+        "elas_set_displacement": (ip, [vp, vp, ip]),
+        "elas_query_residual": (ip, [vp, dp, dp]),
+        "elas_op_apply": (ip, [vp, ip, ip, vp, vp]),
+        "elas_op_residual": (ip, [vp, ip, ip, vp, vp, vp, dp]),
+        "elas_op_sweep": (ip, [vp, ip, ip, vp, vp]),
+        "elas_op_restrict": (ip, [vp, ip, ip, vp, vp]),
+        "elas_op_prolong_add": (ip, [vp, ip, ip, vp, vp]),
+        "elas_op_rhs": (ip, [vp, vp]),
+        "elas_op_bottom": (ip, [vp, ip, vp, vp]),
+        "elas_batch_solve": (ip, [C.POINTER(vp), ip, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "elas_profile_enable": (ip, [vp, ip]),
+        "elas_profile_read": (ip, [vp, ip, dp, C.POINTER(C.c_longlong)]),
+        "elas_launch_count": (C.c_ulonglong, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+PROF_SWEEP64_L0, PROF_SWEEP32_L0, PROF_RESID64_L0, PROF_RESID32_L0 = 0, 1, 2, 3
+
+
+def launch_count():
+    return int(lib().elas_launch_count())
+
+
+def exported_symbols():
+    return [n for n in dir(lib()) if n.startswith("elas_")]
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor, or host pointer of a C-contiguous numpy array."""
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Context:
+    """A solver context on one CUDA device with a torch-owned stream and allocator."""
+
+    def __init__(self, device=0, budget_bytes=0, stream=None, torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the solver has no CPU path")
+        self.torch = torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        self._keep = []
+        alloc_p = None
+        if torch_allocator:
+            dev = device
+            strm = self.stream
+
+            def _alloc(nbytes, user, stream):
+                try:
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm))
+                except Exception:
+                    return 0
+
+            def _free(ptr, nbytes, user, stream):
+                try:
+                    torch.cuda.caching_allocator_delete(int(ptr))
+                except Exception:
+                    pass
+
+            cb = Allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+            self._keep += [cb, _alloc, _free]
+            alloc_p = C.pointer(cb)
+        h = C.c_void_p()
+        rc = lib().elas_ctx_create(C.byref(h), device, budget_bytes, alloc_p, C.c_void_p(self.stream.cuda_stream))
+        if rc != OK:
+            raise ElasError(rc, "context creation failed")
+        self.h = h
+
+    def error(self):
+        return lib().elas_last_error(self.h).decode()
+
+    def check(self, rc):
+        if rc not in (OK,):
+            raise ElasError(rc, self.error())
+
+    def profile(self, enable=True):
+        self.check(lib().elas_profile_enable(self.h, int(enable)))
+
+    def profile_read(self, cls):
+        ms, n = C.c_double(), C.c_longlong()
+        self.check(lib().elas_profile_read(self.h, cls, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def bytes_in_use(self):
+        return lib().elas_ctx_bytes_in_use(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().elas_ctx_destroy(self.h)
+            self.h = None
+
+
+def desc_for(problem: M.Problem, mixed=False):
+    d = GridDesc()
+    for k in range(3):
+        d.n[k] = int(problem.n[k])
+        d.periodic[k] = int(bool(problem.periodic[k]))
+        d.lo[k] = float(problem.lo[k])
+        d.hi[k] = float(problem.hi[k])
+    d.moduli_kind = int(problem.moduli_kind)
+    d.mixed = int(bool(mixed))
+    return d
+
+
+class Grid:
+    """One node grid with its multigrid hierarchy."""
+
+    def __init__(self, ctx: Context, desc: GridDesc):
+        self.ctx = ctx
+        self.desc = desc
+        h = C.c_void_p()
+        ctx.check(lib().elas_grid_create(ctx.h, C.byref(desc), C.byref(h)))
+        self.h = h
+        self.n = tuple(desc.n)
+        self.N = self.n[0] * self.n[1] * self.n[2]
+        self.shape = (self.n[2], self.n[1], self.n[0])
+
+    # -- inputs ------------------------------------------------------------------
+    def _host(self, a, count):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.size != count:
+            raise ValueError(f"expected {count} values, got {a.size}")
+        return a
+
+    def set_moduli(self, comps):
+        a = self._host(comps, self.desc.moduli_kind * self.N)
+        self.ctx.check(lib().elas_set_moduli(self.h, _ptr(a), HOST))
+
+    def set_moduli_from(self, tensor):
+        """Moduli from a torch tensor: pinned host memory or device memory."""
+        space = DEVICE if tensor.is_cuda else HOST
+        self.ctx.check(lib().elas_set_moduli(self.h, _ptr(tensor), space))
+
+    def displacement_into(self, tensor):
+        """Copy the displacement into a torch tensor (pinned host or device)."""
+        space = DEVICE if tensor.is_cuda else HOST
+        self.ctx.check(lib().elas_get_displacement(self.h, _ptr(tensor), space))
+        return tensor
+
+    def set_eigenstrain(self, eps6):
+        if eps6 is None:
+            self.ctx.check(lib().elas_set_eigenstrain(self.h, None, HOST))
+            return
+        a = self._host(eps6, 6 * self.N)
+        self.ctx.check(lib().elas_set_eigenstrain(self.h, _ptr(a), HOST))
+
+    def set_body_force(self, b3):
+        if b3 is None:
+            self.ctx.check(lib().elas_set_body_force(self.h, None, HOST))
+            return
+        a = self._host(b3, 3 * self.N)
+        self.ctx.check(lib().elas_set_body_force(self.h, _ptr(a), HOST))
+
+    def set_mean_strain(self, eps6):
+        a = (C.c_double * 6)(*[float(v) for v in eps6])
+        self.ctx.check(lib().elas_set_mean_strain(self.h, a))
+
+    def set_bc(self, face, comp, kind, value=0.0):
+        self.ctx.check(lib().elas_set_bc(self.h, face, comp, kind, float(value)))
+
+    def set_face_values(self, face, values):
+        if values is None:
+            self.ctx.check(lib().elas_set_face_values(self.h, face, None, HOST))
+            return
+        a = self._host(values, 3 * self.N)
+        self.ctx.check(lib().elas_set_face_values(self.h, face, _ptr(a), HOST))
+
+    # -- solve -------------------------------------------------------------------
+    def solve(self, precision=FP64, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False,
+              fixed_cycles=0, use_graph=False, raise_on_error=True):
+        o = SolveOpts()
+        lib().elas_solve_opts_default(C.byref(o))
+        o.precision, o.rel_tol, o.max_cycles = precision, rel_tol, max_cycles
+        o.nu1, o.nu2, o.warm_start, o.fixed_cycles = nu1, nu2, int(warm_start), fixed_cycles
+        o.use_graph = int(use_graph)
+        info = SolveInfo()
+        rc = lib().elas_solve(self.h, C.byref(o), C.byref(info))
+        if rc != OK and raise_on_error and rc not in (ERR_NOT_CONVERGED,):
+            raise ElasError(rc, self.ctx.error())
+        return info.as_dict()
+
+    def displacement(self):
+        out = np.empty((3,) + self.shape)
+        self.ctx.check(lib().elas_get_displacement(self.h, _ptr(out), HOST))
+        return out
+
+    def set_displacement(self, u):
+        a = self._host(u, 3 * self.N)
+        self.ctx.check(lib().elas_set_displacement(self.h, _ptr(a), HOST))
+
+    def query_residual(self):
+        rel, ab = C.c_double(), C.c_double()
+        self.ctx.check(lib().elas_query_residual(self.h, C.byref(rel), C.byref(ab)))
+        return rel.value, ab.value
+
+    def levels(self):
+        n = C.c_int()
+        self.ctx.check(lib().elas_grid_levels(self.h, C.byref(n)))
+        return n.value
+
+    def level_dims(self, level):
+        a = (C.c_int * 3)()
+        self.ctx.check(lib().elas_grid_level_dims(self.h, level, a))
+        return tuple(a)
+
+    def bytes(self):
+        return lib().elas_grid_bytes(self.h)
+
+    # -- single operations (device tensors) -------------------------------------------
+    def _sync(self):
+        self.ctx.stream.synchronize()
+
+    def op_apply(self, level, precision, u):
+        out = self.ctx.torch.empty_like(u)
+        self.ctx.check(lib().elas_op_apply(self.h, level, precision, _ptr(u), _ptr(out)))
+        return out
+
+    def op_residual(self, level, precision, u, f):
+        r = self.ctx.torch.empty_like(u)
+        ss = C.c_double()
+        self.ctx.check(lib().elas_op_residual(self.h, level, precision, _ptr(u), _ptr(f), _ptr(r), C.byref(ss)))
+        return r, ss.value
+
+    def op_sweep(self, level, precision, u, f):
+        self.ctx.check(lib().elas_op_sweep(self.h, level, precision, _ptr(u), _ptr(f)))
+        return u
+
+    def op_restrict(self, level, precision, r):
+        nc = self.level_dims(level + 1)
+        fc = self.ctx.torch.empty((3, nc[2], nc[1], nc[0]), dtype=r.dtype, device=r.device)
+        self.ctx.check(lib().elas_op_restrict(self.h, level, precision, _ptr(r), _ptr(fc)))
+        return fc
+
+    def op_prolong_add(self, level, precision, ec, u):
+        self.ctx.check(lib().elas_op_prolong_add(self.h, level, precision, _ptr(ec), _ptr(u)))
+        return u
+
+    def op_rhs(self):
+        f = self.ctx.torch.empty((3,) + self.shape, dtype=self.ctx.torch.float64, device=f"cuda:{self.ctx.device}")
+        self.ctx.check(lib().elas_op_rhs(self.h, _ptr(f)))
+        return f
+
+    def op_bottom(self, precision, f):
+        u = self.ctx.torch.empty_like(f)
+        self.ctx.check(lib().elas_op_bottom(self.h, precision, _ptr(f), _ptr(u)))
+        return u
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().elas_grid_destroy(self.h)
+            self.h = None
+
+
+def grid_from_problem(ctx: Context, p: M.Problem, mixed=False) -> Grid:
+    """Create a grid and load a Problem's moduli, loads and boundary conditions."""
+    g = Grid(ctx, desc_for(p, mixed))
+    g.set_moduli(p.moduli)
+    if p.eigenstrain is not None:
+        g.set_eigenstrain(p.eigenstrain)
+    if p.body_force is not None:
+        g.set_body_force(p.body_force)
+    if p.mean_strain is not None:
+        g.set_mean_strain(p.mean_strain)
+    for f in range(6):
+        if p.periodic[f // 2]:
+            continue
+        for c in range(3):
+            kind, val = p.bc[f][c]
+            g.set_bc(f, c, kind, val)
+    faces = dict(p.face_values or {})
+    if p.dirichlet_values is not None:
+        for f in range(6):
+            if p.periodic[f // 2]:
+                continue
+            if any(p.bc[f][c][0] == M.DIRICHLET for c in range(3)):
+                base = faces.get(f)
+                arr = np.empty((3,) + g.shape)
+                for c in range(3):
+                    if p.bc[f][c][0] == M.DIRICHLET:
+                        arr[c] = p.dirichlet_values[c]
+                    elif base is not None:
+                        arr[c] = base[c]
+                    else:
+                        arr[c] = p.bc[f][c][1]
+                faces[f] = arr
+    for f, arr in faces.items():
+        g.set_face_values(f, arr)
+    return g

@@ -1,0 +1,244 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Sizes span several 256-thread blocks with ragged tails; every row type occurs
+(interior, Dirichlet, traction faces/edges/corners, Neumann, periodic wrap).
+Tolerances: FP64 operations agree to rounding (1e-12 relative); FP32 operations
+to 2e-5 relative of the row scale; FP64 solves after the same number of cycles
+to 1e-9 in the relative inf-norm, mixed solves at a relative residual of 1e-8
+to 1e-7 against the oracle's converged FP64 solution.
+"""
+import numpy as np
+import pytest
+
+from paper_2001_04789_gb300 import microstructure as M
+from oracle import multigrid as MG
+from oracle import stencil as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def E():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2001_04789_gb300 import build as B
+    B.build()
+    from paper_2001_04789_gb300 import elas
+    return elas
+
+
+@pytest.fixture(scope="module")
+def ctx(E):
+    c = E.Context(0)
+    yield c
+    c.close()
+
+
+def mixed_bc_problem(n=(13, 9, 11), kind=M.MODULI_GEN21, seed=0):
+    rng = np.random.default_rng(seed)
+    p = M.Problem(n=n, hi=(1.0, 0.7, 0.9), name="mixed_bc")
+    X, Y, Z = p.coords()
+    if kind == M.MODULI_GEN21:
+        base = M.voigt_to_tensor(M.cubic_voigt(1.68, 1.21, 0.75))
+        c1 = M.tensor_to_upper21(M.rotate_tensor(base, M.random_rotation(rng)))
+        c2 = M.tensor_to_upper21(M.rotate_tensor(base, M.random_rotation(rng)))
+        w = 0.5 * (1 + np.tanh(4 * (X - 0.5 + 0.2 * np.sin(3 * Y + Z))))
+        p.moduli_kind = M.MODULI_GEN21
+        p.moduli = c1[:, None, None, None] * (1 - w) + c2[:, None, None, None] * w
+    else:
+        lam, mu = M.lame(1.0 + 0.5 * np.sin(2 * X + Y) * np.cos(Z), 0.3)
+        p.moduli_kind = M.MODULI_ISO
+        p.moduli = np.stack([lam, mu])
+    e = np.zeros((6,) + X.shape)
+    e[0] = 1e-3 * np.exp(-10 * ((X - 0.4) ** 2 + (Y - 0.3) ** 2))
+    e[5] = 5e-4 * np.sin(2 * Z)
+    p.eigenstrain = e
+    p.body_force = np.stack([np.sin(Y), X * Z, np.cos(X + Y)]) * 1e-2
+    bc = M.all_faces(M.TRACTION, 0.0)
+    bc[0] = [(M.DIRICHLET, 1e-3), (M.TRACTION, 0.01), (M.NEUMANN, 0.002)]
+    bc[1] = [(M.TRACTION, -0.02), (M.DIRICHLET, 0.0), (M.TRACTION, 0.0)]
+    bc[2] = [(M.NEUMANN, 0.0), (M.TRACTION, 0.0), (M.TRACTION, 0.03)]
+    bc[5] = [(M.DIRICHLET, 0.0)] * 3
+    p.bc = bc
+    return p
+
+
+def periodic_problem(n=16):
+    return M.ellipsoid_rve(n + 1, seed=3)
+
+
+CASES = {
+    "mixed_gen": lambda: mixed_bc_problem(kind=M.MODULI_GEN21),
+    "mixed_iso": lambda: mixed_bc_problem(kind=M.MODULI_ISO, n=(9, 13, 7)),
+    "periodic_iso": lambda: periodic_problem(16),
+    "eshelby": lambda: M.eshelby_sphere(17),
+    "polycrystal": lambda: M.polycrystal(17, grains=5, seed=1),
+}
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda:0")
+
+
+def rel_err(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_apply_fp64_matches_oracle(E, ctx, case):
+    p = CASES[case]()
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    rng = np.random.default_rng(1)
+    u = rng.normal(size=(3,) + g.shape)
+    got = g.op_apply(0, E.FP64, dev(u)).cpu().numpy()
+    ref = S.apply(S.level_from_problem(p), u)
+    assert rel_err(got, ref) < 1e-12
+    # FP32 moduli and field, same rows
+    got32 = g.op_apply(0, E.MIXED, dev(u, torch.float32)).cpu().numpy()
+    assert rel_err(got32, ref) < 2e-5
+    g.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_rhs_matches_oracle(E, ctx, case):
+    p = CASES[case]()
+    g = E.grid_from_problem(ctx, p)
+    got = g.op_rhs().cpu().numpy()
+    ref = S.rhs(S.level_from_problem(p), p)
+    assert rel_err(got, ref) < 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_sweep_matches_oracle(E, ctx, case):
+    p = CASES[case]()
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    levels = MG.build_hierarchy(S.level_from_problem(p))
+    L = levels[0]
+    rng = np.random.default_rng(2)
+    u = np.where(L.types == M.DIRICHLET, 0.0, rng.normal(size=(3,) + g.shape))
+    f = np.where(L.types == M.DIRICHLET, 0.0, rng.normal(size=(3,) + g.shape)) * 100
+    ud = dev(u)
+    g.op_sweep(0, E.FP64, ud, dev(f))
+    ref = u.copy()
+    MG.sweep(L, ref, f)
+    assert rel_err(ud.cpu().numpy(), ref) < 1e-12
+    u32 = dev(u, torch.float32)
+    g.op_sweep(0, E.MIXED, u32, dev(f, torch.float32))
+    assert rel_err(u32.cpu().numpy(), ref) < 5e-5
+    g.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_transfers_match_oracle(E, ctx, case):
+    p = CASES[case]()
+    g = E.grid_from_problem(ctx, p)
+    if g.levels() < 2:
+        pytest.skip("single level")
+    levels = MG.build_hierarchy(S.level_from_problem(p))
+    rng = np.random.default_rng(3)
+    r = np.where(levels[0].types == M.DIRICHLET, 0.0, rng.normal(size=(3,) + g.shape))
+    fc = g.op_restrict(0, E.FP64, dev(r)).cpu().numpy()
+    ref = np.where(levels[1].types == M.DIRICHLET, 0.0, MG.restrict(r, levels[0].level))
+    assert rel_err(fc, ref) < 1e-13
+    nc = g.level_dims(1)
+    ec = rng.normal(size=(3, nc[2], nc[1], nc[0]))
+    u = rng.normal(size=(3,) + g.shape)
+    got = g.op_prolong_add(0, E.FP64, dev(ec), dev(u)).cpu().numpy()
+    ref = u + np.where(levels[0].types == M.DIRICHLET, 0.0, MG.prolong(ec, levels[0].level))
+    assert rel_err(got, ref) < 1e-13
+    g.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_bottom_matches_oracle(E, ctx, case):
+    p = CASES[case]()
+    g = E.grid_from_problem(ctx, p)
+    levels = MG.build_hierarchy(S.level_from_problem(p))
+    Lb = levels[-1]
+    rng = np.random.default_rng(4)
+    f = np.where(Lb.types == M.DIRICHLET, 0.0, rng.normal(size=(3,) + Lb.level.shape))
+    got = g.op_bottom(E.FP64, dev(f)).cpu().numpy()
+    ref = MG.bottom_solve(Lb, f)
+    assert rel_err(got, ref) < 1e-10
+    g.close()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp64_cycles_match_oracle(E, ctx, case):
+    p = CASES[case]()
+    g = E.grid_from_problem(ctx, p)
+    info = g.solve(precision=E.FP64, fixed_cycles=3)
+    got = g.displacement()
+    ref, rinfo = MG.solve(p, fixed_cycles=3)
+    assert rel_err(got, ref) < 1e-9
+    assert np.allclose(info["rel_history"], rinfo.rel_history, rtol=1e-7, atol=0)
+    g.close()
+
+
+@pytest.mark.parametrize("case", ["eshelby", "polycrystal", "periodic_iso"])
+def test_fp64_and_mixed_solves_reach_oracle_solution(E, ctx, case):
+    p = CASES[case]()
+    truth, tinfo = MG.solve(p, tol=1e-13, max_cycles=300)
+    assert tinfo.converged
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    i64 = g.solve(precision=E.FP64, rel_tol=1e-8)
+    assert i64["status"] == 0 and i64["rel_residual"] <= 1e-8
+    ref, rinfo = MG.solve(p, tol=1e-8, max_cycles=300)
+    assert i64["cycles"] == rinfo.cycles
+    assert rel_err(g.displacement(), ref) < 1e-9
+    imx = g.solve(precision=E.MIXED, rel_tol=1e-8)
+    assert imx["status"] == 0 and imx["rel_residual"] <= 1e-8
+    rel_fp64, _ = g.query_residual()
+    assert rel_fp64 <= 1.01e-8
+    # both at a relative residual of 1e-8: the mixed result against the oracle's
+    assert rel_err(g.displacement(), ref) < 1e-7
+    # and both within the same distance of the converged discrete solution
+    assert rel_err(g.displacement(), truth) < 10 * max(rel_err(ref, truth), 1e-9)
+    g.close()
+
+
+def test_warm_start_from_solution_converges_immediately(E, ctx):
+    p = M.eshelby_sphere(17)
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    g.solve(precision=E.MIXED, rel_tol=1e-10)
+    info = g.solve(precision=E.MIXED, rel_tol=1e-8, warm_start=True)
+    assert info["cycles"] == 0
+    g.close()
+
+
+def test_smallest_grid_is_single_level(E, ctx):
+    p = M.eshelby_sphere(5)
+    g = E.grid_from_problem(ctx, p)
+    assert g.levels() == 1
+    info = g.solve(precision=E.FP64, rel_tol=1e-12)
+    ref, _ = MG.solve(p, tol=1e-12)
+    assert rel_err(g.displacement(), ref) < 1e-9
+    g.close()
+
+
+def test_invalid_arguments_are_errors(E, ctx):
+    d = E.desc_for(M.eshelby_sphere(9))
+    d.n[0] = 2
+    with pytest.raises(E.ElasError):
+        E.Grid(ctx, d)
+    d = E.desc_for(M.eshelby_sphere(9))
+    d.moduli_kind = 7
+    with pytest.raises(E.ElasError):
+        E.Grid(ctx, d)
+    g = E.Grid(ctx, E.desc_for(M.eshelby_sphere(9)))
+    with pytest.raises(E.ElasError):
+        g.solve()                    # moduli not set
+    with pytest.raises(E.ElasError):
+        g.set_bc(6, 0, M.DIRICHLET)
+    g.close()
+
+
+def test_budget_refuses_oversized_grid(E):
+    c = E.Context(0, budget_bytes=1 << 20)
+    with pytest.raises(E.ElasError) as ei:
+        E.Grid(c, E.desc_for(M.eshelby_sphere(33)))
+    assert ei.value.code == -2
+    c.close()
