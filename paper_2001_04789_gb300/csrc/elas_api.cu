@@ -77,6 +77,8 @@ struct Level {
     Lv<float> L32;
     double *mod64 = nullptr, *u = nullptr, *ua = nullptr, *f = nullptr, *r = nullptr;
     float *mod32 = nullptr, *u32 = nullptr, *ua32 = nullptr, *f32 = nullptr, *r32 = nullptr;
+    int* bnd = nullptr;   // boundary-plane nodes of this level
+    int nbnd = 0;
     NullInfo nf{};
 };
 
@@ -177,6 +179,8 @@ void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int 
     for (int f = 0; f < 6; ++f)
         for (int c = 0; c < 3; ++c) L.bc[f][c] = (signed char)(per[f / 2] ? 0 : bct[f][c]);
     L.mod = nullptr;
+    L.bnodes = nullptr;
+    L.nbnd = 0;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -534,6 +538,23 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     }
     v.L64.mod = v.mod64;
     v.L32.mod = v.mod32;
+    // list of the nodes that lie on a boundary plane of a non-periodic direction
+    std::vector<int> b;
+    const int* per = g->desc.periodic;
+    for (int z = 0; z < v.n[2]; ++z)
+        for (int y = 0; y < v.n[1]; ++y)
+            for (int x = 0; x < v.n[0]; ++x) {
+                const bool on = (!per[0] && (x == 0 || x == v.n[0] - 1)) || (!per[1] && (y == 0 || y == v.n[1] - 1)) ||
+                                (!per[2] && (z == 0 || z == v.n[2] - 1));
+                if (on) b.push_back(x + v.n[0] * (y + v.n[1] * z));
+            }
+    v.nbnd = (int)b.size();
+    if (v.nbnd) {
+        if ((rc = galloc(g, &v.bnd, b.size()))) return rc;
+        elas_ctx c = g->ctx;
+        CUDA_TRY(c, cudaMemcpyAsync(v.bnd, b.data(), sizeof(int) * b.size(), cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
     return ELAS_OK;
 }
 
@@ -551,6 +572,8 @@ void refresh_lv(elas_grid g) {
         fill_lv(v.L32, v.n, g->desc.periodic, h, g->K, g->bc_type);
         v.L64.mod = v.mod64;
         v.L32.mod = v.mod32;
+        v.L64.bnodes = v.L32.bnodes = v.bnd;
+        v.L64.nbnd = v.L32.nbnd = v.nbnd;
         v.nf = null_space(g->desc, v.n, h, g->bc_type);
     }
 }

@@ -31,6 +31,8 @@ struct Lv {
     signed char bc[6][3];  // boundary type per (face, component); 0 on periodic faces
     T h[3], inv2h[3], invh[3], invh2[3], inv4hh[3];   // inv4hh[d] for the pair != d
     const T* __restrict__ mod;
+    const int* __restrict__ bnodes;   // linear indices of the nodes on boundary planes
+    int nbnd;
 };
 
 // ---- Voigt helpers ----------------------------------------------------------
@@ -120,59 +122,57 @@ __device__ __forceinline__ int wrapc(const Lv<T>& L, int d, int v) {
     return v;
 }
 
-// ---- field accessors -------------------------------------------------------------
+// ---- field accessors (coordinates already wrapped / in range) ----------------------
 template <typename T>
 struct UField {
     const T* __restrict__ u;
-    int N;
-    __device__ __forceinline__ T operator()(int k, int q) const { return u[k * N + q]; }
+    int N, n0, n1;
+    __device__ __forceinline__ T at(int k, const int a[3]) const { return u[k * N + a[0] + n0 * (a[1] + n1 * a[2])]; }
 };
 
-// Unit vector e_(kk, p0): the operator applied to it gives column (kk, p0).
+// Unit vector e_(kk, c0): the operator applied to it gives column (kk, c0).
 template <typename T>
 struct UProbe {
-    int p0, kk;
-    __device__ __forceinline__ T operator()(int k, int q) const {
-        return (k == kk && q == p0) ? T(1) : T(0);
+    int kk, c0[3];
+    __device__ __forceinline__ T at(int k, const int a[3]) const {
+        return (k == kk && a[0] == c0[0] && a[1] == c0[1] && a[2] == c0[2]) ? T(1) : T(0);
     }
 };
 
-// ---- generic boundary-node row ---------------------------------------------------
-// Value g at coordinates (cx, cy, cz) via functor G(int q).
-// First derivative in direction l at node c: one-sided where c lies on a boundary
-// plane of l, central otherwise.
+// ---- generic boundary-node row -----------------------------------------------------
+// First derivative in direction l at node c of the field given by g(int[3]): one-sided
+// second order where c lies on a boundary plane of l, central otherwise.
 template <typename T, class G>
-__device__ __forceinline__ T deriv_at(const Lv<T>& L, const G& g, const int c[3], int l) {
-    int a[3] = {c[0], c[1], c[2]};
+__device__ __forceinline__ T deriv_c(const Lv<T>& L, const G& g, const int c[3], int l) {
     int side = 0;
     if (!L.per[l]) {
         if (c[l] == 0) side = -1;
         else if (c[l] == L.n[l] - 1) side = 1;
     }
+    int a[3] = {c[0], c[1], c[2]};
     if (side == 0) {
         a[l] = wrapc(L, l, c[l] + 1);
-        const T up = g(lin(L, a[0], a[1], a[2]));
+        const T up = g(a);
         a[l] = wrapc(L, l, c[l] - 1);
-        const T um = g(lin(L, a[0], a[1], a[2]));
+        const T um = g(a);
         return (up - um) * L.inv2h[l];
     }
     const int dirn = -side;   // inward
-    const T g0 = g(lin(L, a[0], a[1], a[2]));
+    const T g0 = g(a);
     a[l] = c[l] + dirn;
-    const T g1 = g(lin(L, a[0], a[1], a[2]));
+    const T g1 = g(a);
     a[l] = c[l] + 2 * dirn;
-    const T g2 = g(lin(L, a[0], a[1], a[2]));
+    const T g2 = g(a);
     return T(dirn) * (T(-3) * g0 + T(4) * g1 - g2) * L.inv2h[l];
 }
 
-// Row i (interior or traction type) at a boundary node, generic in the field.
+// Row i (interior or traction type) at a node, generic in the field.
 template <typename T, int KIND, class U>
 __device__ __noinline__ T pde_row_generic(const Lv<T>& L, const U& u, const NodeInfo& ni, int i) {
     const int* c = ni.c;
     const int p = lin(L, c[0], c[1], c[2]);
     T acc = T(0);
     // product-rule terms of the non-boundary directions
-#pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (ni.side[j] != 0) continue;
         int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
@@ -180,40 +180,28 @@ __device__ __noinline__ T pde_row_generic(const Lv<T>& L, const U& u, const Node
         cm[j] = wrapc(L, j, c[j] - 1);
         const int qp = lin(L, cp[0], cp[1], cp[2]);
         const int qm = lin(L, cm[0], cm[1], cm[2]);
-#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            auto uk = [&](int q) { return u(k, q); };
-#pragma unroll
+            auto uk = [&](const int a[3]) { return u.at(k, a); };
+            // central difference in j of u_k, as a field
+            auto gj = [&](const int a[3]) {
+                int ap[3] = {a[0], a[1], a[2]}, am[3] = {a[0], a[1], a[2]};
+                ap[j] = wrapc(L, j, a[j] + 1);
+                am[j] = wrapc(L, j, a[j] - 1);
+                return (u.at(k, ap) - u.at(k, am)) * L.inv2h[j];
+            };
             for (int l = 0; l < 3; ++l) {
                 if (!Cnz<T, KIND>(i, j, k, l)) continue;
                 const T C0 = Cm<T, KIND>(L, p, i, j, k, l);
                 const T dC = (Cm<T, KIND>(L, qp, i, j, k, l) - Cm<T, KIND>(L, qm, i, j, k, l)) * L.inv2h[j];
-                const T Dl = deriv_at(L, uk, c, l);
+                const T Dl = deriv_c(L, uk, c, l);
                 T DD;
-                if (l == j) {
-                    DD = (u(k, qp) - T(2) * u(k, p) + u(k, qm)) * L.invh2[j];
-                } else {
-                    // one-sided or central derivative in l of the central difference in j
-                    auto gj = [&](int q) {
-                        // q is a node on the same j-line position as c shifted in l only;
-                        // recover its coordinates to shift in j
-                        const int qx = q % L.n[0];
-                        const int qy = (q / L.n[0]) % L.n[1];
-                        const int qz = q / (L.n[0] * L.n[1]);
-                        int a[3] = {qx, qy, qz};
-                        int b[3] = {qx, qy, qz};
-                        a[j] = wrapc(L, j, a[j] + 1);
-                        b[j] = wrapc(L, j, b[j] - 1);
-                        return (u(k, lin(L, a[0], a[1], a[2])) - u(k, lin(L, b[0], b[1], b[2]))) * L.inv2h[j];
-                    };
-                    DD = deriv_at(L, gj, c, l);
-                }
+                if (l == j) DD = (u.at(k, cp) - T(2) * u.at(k, c) + u.at(k, cm)) * L.invh2[j];
+                else DD = deriv_c(L, gj, c, l);
                 acc += dC * Dl + C0 * DD;
             }
         }
     }
     // half-cell terms of the boundary directions
-#pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (ni.side[a] == 0) continue;
         const T s = T(ni.side[a]);
@@ -222,19 +210,14 @@ __device__ __noinline__ T pde_row_generic(const Lv<T>& L, const U& u, const Node
         cn[a] = c[a] + inward;
         const int qn = lin(L, cn[0], cn[1], cn[2]);
         T sacc = T(0);
-#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            auto uk = [&](int q) { return u(k, q); };
-#pragma unroll
+            auto uk = [&](const int b[3]) { return u.at(k, b); };
             for (int l = 0; l < 3; ++l) {
                 if (!Cnz<T, KIND>(i, a, k, l)) continue;
                 const T Cbar = T(0.5) * (Cm<T, KIND>(L, p, i, a, k, l) + Cm<T, KIND>(L, qn, i, a, k, l));
                 T Dbar;
-                if (l == a) {
-                    Dbar = T(inward) * (u(k, qn) - u(k, p)) * L.invh[a];
-                } else {
-                    Dbar = T(0.5) * (deriv_at(L, uk, c, l) + deriv_at(L, uk, cn, l));
-                }
+                if (l == a) Dbar = T(inward) * (u.at(k, cn) - u.at(k, c)) * L.invh[a];
+                else Dbar = T(0.5) * (deriv_c(L, uk, c, l) + deriv_c(L, uk, cn, l));
                 sacc += Cbar * Dbar;
             }
         }
@@ -248,22 +231,21 @@ template <typename T, int KIND, class U>
 __device__ __noinline__ T neumann_row(const Lv<T>& L, const U& u, const NodeInfo& ni, int i) {
     const int p = lin(L, ni.c[0], ni.c[1], ni.c[2]);
     T acc = T(0);
-    auto ui = [&](int q) { return u(i, q); };
-#pragma unroll
+    auto ui = [&](const int a[3]) { return u.at(i, a); };
     for (int a = 0; a < 3; ++a) {
         if (ni.side[a] == 0) continue;
         const int f = 2 * a + (ni.side[a] > 0 ? 1 : 0);
         if (L.bc[f][i] != ROW_NEUMANN) continue;
         const T C = Cm<T, KIND>(L, p, i, a, i, a);
-        acc += -(T(2) * L.invh[a]) * C * T(ni.side[a]) * deriv_at(L, ui, ni.c, a);
+        acc += -(T(2) * L.invh[a]) * C * T(ni.side[a]) * deriv_c(L, ui, ni.c, a);
     }
     return acc;
 }
 
-// Row i of A u at a boundary node (Dirichlet rows return u_i).
+// Row i of A u at any node (Dirichlet rows return u_i).
 template <typename T, int KIND, class U>
 __device__ __forceinline__ T boundary_row(const Lv<T>& L, const U& u, const NodeInfo& ni, int i, int type) {
-    if (type == ROW_DIRICHLET) return u(i, lin(L, ni.c[0], ni.c[1], ni.c[2]));
+    if (type == ROW_DIRICHLET) return u.at(i, ni.c);
     if (type == ROW_NEUMANN) return neumann_row<T, KIND>(L, u, ni, i);
     return pde_row_generic<T, KIND>(L, u, ni, i);
 }
@@ -382,16 +364,62 @@ __device__ __forceinline__ void interior_block(const Lv<T>& L, int p, T B[3][3])
         }
 }
 
-// Diagonal block of a boundary node by probing its rows with unit vectors.
+// Diagonal 3x3 block of a boundary node, B_ik = d(A u)_i / d u_k at the node itself:
+// the product-rule terms contribute C_ijkj (-2/h_j^2) and (d_j C_ijkl) c_l, the
+// half-cell terms -(2/h_a) s_a Cbar_iakl (s_a/h_a for l = a, c_l/2 otherwise), with
+// c_l = -+3/(2 h_l) the node's weight in its one-sided derivative of direction l.
 template <typename T, int KIND>
-__device__ __noinline__ void boundary_block(const Lv<T>& L, const NodeInfo& ni, const int types[3],
-                                               T B[3][3]) {
-    const int p = lin(L, ni.c[0], ni.c[1], ni.c[2]);
-#pragma unroll 1
-    for (int k = 0; k < 3; ++k) {
-        UProbe<T> e{p, k};
-#pragma unroll 1
-        for (int i = 0; i < 3; ++i) B[i][k] = boundary_row<T, KIND>(L, e, ni, i, types[i]);
+__device__ __noinline__ void boundary_block(const Lv<T>& L, const NodeInfo& ni, const int types[3], T B[3][3]) {
+    const int* c = ni.c;
+    const int p = lin(L, c[0], c[1], c[2]);
+    T cl[3];
+    for (int l = 0; l < 3; ++l)
+        cl[l] = ni.side[l] < 0 ? T(-1.5) * L.invh[l] : (ni.side[l] > 0 ? T(1.5) * L.invh[l] : T(0));
+    for (int i = 0; i < 3; ++i) {
+        for (int k = 0; k < 3; ++k) B[i][k] = (types[i] == ROW_DIRICHLET && i == k) ? T(1) : T(0);
+        if (types[i] == ROW_DIRICHLET) continue;
+        if (types[i] == ROW_NEUMANN) {
+            T acc = T(0);
+            for (int a = 0; a < 3; ++a) {
+                if (ni.side[a] == 0) continue;
+                const int f = 2 * a + (ni.side[a] > 0 ? 1 : 0);
+                if (L.bc[f][i] != ROW_NEUMANN) continue;
+                acc += -(T(2) * L.invh[a]) * Cm<T, KIND>(L, p, i, a, i, a) * T(ni.side[a]) * cl[a];
+            }
+            B[i][i] = acc;
+            continue;
+        }
+        for (int k = 0; k < 3; ++k) {
+            T acc = T(0);
+            for (int j = 0; j < 3; ++j) {
+                if (ni.side[j] != 0) continue;
+                int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+                cp[j] = wrapc(L, j, c[j] + 1);
+                cm[j] = wrapc(L, j, c[j] - 1);
+                const int qp = lin(L, cp[0], cp[1], cp[2]), qm = lin(L, cm[0], cm[1], cm[2]);
+                for (int l = 0; l < 3; ++l) {
+                    if (!Cnz<T, KIND>(i, j, k, l)) continue;
+                    if (cl[l] != T(0))
+                        acc += (Cm<T, KIND>(L, qp, i, j, k, l) - Cm<T, KIND>(L, qm, i, j, k, l)) * L.inv2h[j] * cl[l];
+                    if (l == j) acc += Cm<T, KIND>(L, p, i, j, k, j) * (T(-2) * L.invh2[j]);
+                }
+            }
+            for (int a = 0; a < 3; ++a) {
+                if (ni.side[a] == 0) continue;
+                const T s = T(ni.side[a]);
+                int cn[3] = {c[0], c[1], c[2]};
+                cn[a] = c[a] - ni.side[a];
+                const int qn = lin(L, cn[0], cn[1], cn[2]);
+                for (int l = 0; l < 3; ++l) {
+                    if (!Cnz<T, KIND>(i, a, k, l)) continue;
+                    const T coef = (l == a) ? s * L.invh[a] : T(0.5) * cl[l];
+                    if (coef == T(0)) continue;
+                    const T Cbar = T(0.5) * (Cm<T, KIND>(L, p, i, a, k, l) + Cm<T, KIND>(L, qn, i, a, k, l));
+                    acc += -(T(2) * L.invh[a]) * s * Cbar * coef;
+                }
+            }
+            B[i][k] = acc;
+        }
     }
 }
 

@@ -147,114 +147,204 @@ __global__ void k_dirichlet(Lv<double> L, BoundaryData bd, double* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// operator, residual
+// operator, residual, smoother.  Each comes as an interior kernel over the box of
+// nodes on no boundary plane (the fast stencil, no divergence) and a boundary
+// kernel over the level's list of boundary-plane nodes (generic rows).
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void interior_box(const Lv<T>& L, int lo[3], int cnt[3]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = L.per[d] ? 0 : 1;
+        cnt[d] = L.per[d] ? L.n[d] : L.n[d] - 2;
+    }
+}
+
+template <typename T>
+__host__ __device__ inline size_t interior_count(const Lv<T>& L) {
+    size_t c = 1;
+    for (int d = 0; d < 3; ++d) c *= (size_t)(L.per[d] ? L.n[d] : L.n[d] - 2);
+    return c;
+}
+
+template <typename T>
+__host__ __device__ inline size_t interior_pairs(const Lv<T>& L) {
+    const int cx = L.per[0] ? L.n[0] : L.n[0] - 2;
+    const int cy = L.per[1] ? L.n[1] : L.n[1] - 2;
+    const int cz = L.per[2] ? L.n[2] : L.n[2] - 2;
+    return (size_t)((cx + 1) / 2) * cy * cz;
+}
+
 template <typename T, int KIND>
-__device__ __forceinline__ void all_rows(const Lv<T>& L, const T* __restrict__ u, int x, int y, int z,
-                                         const NodeInfo& ni, int types[3], T out[3]) {
-    if (!ni.boundary) {
-        types[0] = types[1] = types[2] = ROW_INTERIOR;
-        interior_rows<T, KIND>(L, u, x, y, z, out);
-    } else {
-        UField<T> uf{u, L.N};
-        for (int i = 0; i < 3; ++i) {
-            types[i] = row_type(L, ni, i);
-            out[i] = boundary_row<T, KIND>(L, uf, ni, i, types[i]);
-        }
+__device__ __forceinline__ void boundary_rows_all(const Lv<T>& L, const T* __restrict__ u, const NodeInfo& ni,
+                                                  int types[3], T out[3]) {
+    UField<T> uf{u, L.N, L.n[0], L.n[1]};
+    for (int i = 0; i < 3; ++i) {
+        types[i] = row_type(L, ni, i);
+        out[i] = boundary_row<T, KIND>(L, uf, ni, i, types[i]);
     }
 }
 
 template <typename T, int KIND>
-__global__ void k_apply(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.N) return;
+__global__ void __launch_bounds__(kBlock) k_apply_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
+    int lo[3], cnt[3];
+    interior_box(L, lo, cnt);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt[0] * cnt[1] * cnt[2]) return;
+    const int x = lo[0] + t % cnt[0], y = lo[1] + (t / cnt[0]) % cnt[1], z = lo[2] + t / (cnt[0] * cnt[1]);
+    T v[3];
+    interior_rows<T, KIND>(L, u, x, y, z, v);
+    const int p = lin(L, x, y, z);
+    for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
+}
+
+template <typename T, int KIND>
+__global__ void k_apply_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.nbnd) return;
+    const int p = L.bnodes[t];
     int c[3];
     coords_of(p, L.n, c);
     const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
     int types[3];
     T v[3];
-    all_rows<T, KIND>(L, u, c[0], c[1], c[2], ni, types, v);
+    boundary_rows_all<T, KIND>(L, u, ni, types, v);
     for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
 }
 
+// r = f - lam.W - A u on one node's rows; accumulates sum r^2 and W^T r.
+template <typename T, typename TR, bool NORM>
+__device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restrict__ f, const NullInfo& nf,
+                                               const double* __restrict__ lam, const int c[3], int p,
+                                               const int types[3], const T v[3], TR* __restrict__ r,
+                                               double acc[7]) {
+    for (int i = 0; i < 3; ++i) {
+        T ri = T(0);
+        if (types[i] != ROW_DIRICHLET) {
+            T fi = f[i * L.N + p];
+            if (lam && nf.m > 0) fi -= T(null_combo(nf, lam, i, c));
+            ri = fi - v[i];
+            if (NORM) {
+                const double rd = (double)ri;
+                acc[0] += rd * rd;
+                for (int q = 0; q < nf.m; ++q) acc[1 + q] += null_vec(nf, q, i, c) * rd;
+            }
+        }
+        r[i * L.N + p] = (TR)ri;
+    }
+}
+
 template <typename T, typename TR, int KIND, bool NORM>
-__global__ void __launch_bounds__(kBlock) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
-                                                    NullInfo nf, const double* __restrict__ lam,
-                                                    TR* __restrict__ r, double* __restrict__ partials) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kBlock) k_residual_int(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
+                                                        NullInfo nf, const double* __restrict__ lam,
+                                                        TR* __restrict__ r, double* __restrict__ partials) {
+    int lo[3], cnt[3];
+    interior_box(L, lo, cnt);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (p < L.N) {
+    if (t < cnt[0] * cnt[1] * cnt[2]) {
+        const int c[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
+        T v[3];
+        interior_rows<T, KIND>(L, u, c[0], c[1], c[2], v);
+        const int types[3] = {ROW_INTERIOR, ROW_INTERIOR, ROW_INTERIOR};
+        residual_store<T, TR, NORM>(L, f, nf, lam, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
+    }
+    if (NORM) block_reduce_store<7>(acc, 1 + nf.m, partials);
+}
+
+template <typename T, typename TR, int KIND, bool NORM>
+__global__ void __launch_bounds__(kBlock) k_residual_bnd(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
+                                                        NullInfo nf, const double* __restrict__ lam,
+                                                        TR* __restrict__ r, double* __restrict__ partials) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (t < L.nbnd) {
+        const int p = L.bnodes[t];
         int c[3];
         coords_of(p, L.n, c);
         const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
         int types[3];
         T v[3];
-        all_rows<T, KIND>(L, u, c[0], c[1], c[2], ni, types, v);
-        for (int i = 0; i < 3; ++i) {
-            T ri = T(0);
-            if (types[i] != ROW_DIRICHLET) {
-                T fi = f[i * L.N + p];
-                if (lam && nf.m > 0) fi -= T(null_combo(nf, lam, i, c));
-                ri = fi - v[i];
-                if (NORM) {
-                    const double rd = (double)ri;
-                    acc[0] += rd * rd;
-                    for (int q = 0; q < nf.m; ++q) acc[1 + q] += null_vec(nf, q, i, c) * rd;
-                }
-            }
-            r[i * L.N + p] = (TR)ri;
-        }
+        boundary_rows_all<T, KIND>(L, u, ni, types, v);
+        residual_store<T, TR, NORM>(L, f, nf, lam, c, p, types, v, r, acc);
     }
     if (NORM) block_reduce_store<7>(acc, 1 + nf.m, partials);
 }
 
-// ---------------------------------------------------------------------------
-// red-black smoother: each thread owns the node pair (2m, 2m+1) of an x-row, updates
-// the one of the active colour and copies the other; all rows are evaluated with
-// the values from before the half-sweep (Jacobi within the colour).
-// ---------------------------------------------------------------------------
+// Red-black smoother, interior nodes: each thread owns the x-pair (x0, x0+1) of the
+// interior box, updates the one of the active colour and copies the other; every
+// row uses the values from before the half-sweep (Jacobi within the colour).
 template <typename T, int KIND>
-__global__ void __launch_bounds__(kBlock) k_half_sweep(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
-                                                      const T* __restrict__ f, int colour, NullInfo nf,
-                                                      const double* __restrict__ lam) {
-    const int npair = (L.n[0] + 1) >> 1;
+__global__ void __launch_bounds__(kBlock) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
+                                                          const T* __restrict__ f, int colour, NullInfo nf,
+                                                          const double* __restrict__ lam) {
+    int lo[3], cnt[3];
+    interior_box(L, lo, cnt);
+    const int npair = (cnt[0] + 1) >> 1;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= npair * L.n[1] * L.n[2]) return;
+    if (t >= npair * cnt[1] * cnt[2]) return;
     const int m = t % npair;
     const int yz = t / npair;
-    const int y = yz % L.n[1], z = yz / L.n[1];
-    const int x0 = 2 * m;
-    const int xa = x0 + ((x0 + y + z + colour) & 1);   // active node
-    const int xi = x0 + 1 - (xa - x0);                  // inactive node
+    const int y = lo[1] + yz % cnt[1], z = lo[2] + yz / cnt[1];
+    const int x0 = lo[0] + 2 * m;
+    const int xend = lo[0] + cnt[0];          // one past the last interior x
+    const int xa = x0 + ((x0 + y + z + colour) & 1);
+    const int xi = (xa == x0) ? x0 + 1 : x0;
     const int N = L.N;
-    if (xi < L.n[0]) {
+    if (xi < xend) {
         const int q = lin(L, xi, y, z);
         uo[q] = u[q];
         uo[N + q] = u[N + q];
         uo[2 * N + q] = u[2 * N + q];
     }
-    if (xa >= L.n[0]) return;
+    if (xa >= xend) return;
     const int p = lin(L, xa, y, z);
-    const NodeInfo ni = node_info(L, xa, y, z);
+    T v[3];
+    interior_rows<T, KIND>(L, u, xa, y, z, v);
+    T r[3], B[3][3], d[3];
+    const int c[3] = {xa, y, z};
+    for (int i = 0; i < 3; ++i) {
+        T fi = f[i * N + p];
+        if (lam && nf.m > 0) fi -= T(null_combo(nf, lam, i, c));
+        r[i] = fi - v[i];
+    }
+    interior_block<T, KIND>(L, p, B);
+    solve3(B, r, d);
+    for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + d[i];
+}
+
+// Red-black smoother, boundary-plane nodes (one thread per listed node).
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
+                                                          const T* __restrict__ f, int colour, NullInfo nf,
+                                                          const double* __restrict__ lam) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.nbnd) return;
+    const int p = L.bnodes[t];
+    const int N = L.N;
+    int c[3];
+    coords_of(p, L.n, c);
+    if (((c[0] + c[1] + c[2]) & 1) != colour) {
+        uo[p] = u[p];
+        uo[N + p] = u[N + p];
+        uo[2 * N + p] = u[2 * N + p];
+        return;
+    }
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
     int types[3];
     T v[3];
-    all_rows<T, KIND>(L, u, xa, y, z, ni, types, v);
-    T r[3], B[3][3];
+    boundary_rows_all<T, KIND>(L, u, ni, types, v);
+    T r[3], B[3][3], d[3];
     for (int i = 0; i < 3; ++i) {
         if (types[i] == ROW_DIRICHLET) {
             r[i] = T(0);
         } else {
             T fi = f[i * N + p];
-            if (lam && nf.m > 0) {
-                const int c[3] = {xa, y, z};
-                fi -= T(null_combo(nf, lam, i, c));
-            }
+            if (lam && nf.m > 0) fi -= T(null_combo(nf, lam, i, c));
             r[i] = fi - v[i];
         }
     }
-    if (!ni.boundary) interior_block<T, KIND>(L, p, B);
-    else boundary_block<T, KIND>(L, ni, types, B);
-    T d[3];
+    boundary_block<T, KIND>(L, ni, types, B);
     solve3(B, r, d);
     for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
 }
@@ -419,7 +509,8 @@ __global__ void k_bottom_assemble(Lv<double> L, const int* __restrict__ dofs, in
         coords_of(pr, L.n, c);
         const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
         const int type = row_type(L, ni, ir);
-        UProbe<double> e{pc, ic};
+        UProbe<double> e{ic, {0, 0, 0}};
+        coords_of(pc, L.n, e.c0);
         v = boundary_row<double, KIND>(L, e, ni, ir, type == ROW_INTERIOR ? ROW_TRACTION : type);
     } else if (row < nfree && col >= nfree) {
         const int ir = dofs[row] / L.N, pr = dofs[row] % L.N;
@@ -655,8 +746,17 @@ void launch_dirichlet(const Lv<double>& L, const BoundaryData& bd, double* u, in
 
 template <typename T>
 void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
-    if (L.K == 2) { count_launch(); k_apply<T, 2><<<blocks_for(L.N), kBlock, 0, s>>>(L, u, out); }
-    else { count_launch(); k_apply<T, 21><<<blocks_for(L.N), kBlock, 0, s>>>(L, u, out); }
+    const size_t ni = interior_count(L);
+    if (ni) {
+        count_launch();
+        if (L.K == 2) k_apply_int<T, 2><<<blocks_for(ni), kBlock, 0, s>>>(L, u, out);
+        else k_apply_int<T, 21><<<blocks_for(ni), kBlock, 0, s>>>(L, u, out);
+    }
+    if (L.nbnd) {
+        count_launch();
+        if (L.K == 2) k_apply_bnd<T, 2><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u, out);
+        else k_apply_bnd<T, 21><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u, out);
+    }
 }
 
 template <typename T, typename TR>
@@ -664,14 +764,30 @@ void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf,
                      double* partials, int* nblocks, cudaStream_t s) {
     NullInfo nfv{};
     if (nf) nfv = *nf;
-    const int nb = blocks_for(L.N);
-    if (nblocks) *nblocks = nb;
-    if (partials) {
-        if (L.K == 2) { count_launch(); k_residual<T, TR, 2, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials); }
-        else { count_launch(); k_residual<T, TR, 21, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials); }
-    } else {
-        if (L.K == 2) { count_launch(); k_residual<T, TR, 2, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr); }
-        else { count_launch(); k_residual<T, TR, 21, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr); }
+    const size_t ni = interior_count(L);
+    const int nbi = ni ? blocks_for(ni) : 0;
+    const int nbb = L.nbnd ? blocks_for(L.nbnd) : 0;
+    if (nblocks) *nblocks = nbi + nbb;
+    double* pb = partials ? partials + (size_t)nbi * kPartialStride : nullptr;
+    if (nbi) {
+        count_launch();
+        if (partials) {
+            if (L.K == 2) k_residual_int<T, TR, 2, true><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
+            else k_residual_int<T, TR, 21, true><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
+        } else {
+            if (L.K == 2) k_residual_int<T, TR, 2, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
+            else k_residual_int<T, TR, 21, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
+        }
+    }
+    if (nbb) {
+        count_launch();
+        if (partials) {
+            if (L.K == 2) k_residual_bnd<T, TR, 2, true><<<nbb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, pb);
+            else k_residual_bnd<T, TR, 21, true><<<nbb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, pb);
+        } else {
+            if (L.K == 2) k_residual_bnd<T, TR, 2, false><<<nbb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
+            else k_residual_bnd<T, TR, 21, false><<<nbb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
+        }
     }
 }
 
@@ -680,9 +796,17 @@ void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int 
                        const double* lam, cudaStream_t s) {
     NullInfo nfv{};
     if (nf) nfv = *nf;
-    const size_t n = (size_t)((L.n[0] + 1) / 2) * L.n[1] * L.n[2];
-    if (L.K == 2) { count_launch(); k_half_sweep<T, 2><<<blocks_for(n), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); }
-    else { count_launch(); k_half_sweep<T, 21><<<blocks_for(n), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); }
+    const size_t np = interior_pairs(L);
+    if (np) {
+        count_launch();
+        if (L.K == 2) k_half_sweep_int<T, 2><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+        else k_half_sweep_int<T, 21><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+    }
+    if (L.nbnd) {
+        count_launch();
+        if (L.K == 2) k_half_sweep_bnd<T, 2><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+        else k_half_sweep_bnd<T, 21><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+    }
 }
 
 template <typename T>
