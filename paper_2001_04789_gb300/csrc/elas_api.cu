@@ -75,7 +75,7 @@ struct Level {
     int N;
     Lv<double> L64;
     Lv<float> L32;
-    double *mod64 = nullptr, *u = nullptr, *ua = nullptr, *f = nullptr, *r = nullptr;
+    double *mod64 = nullptr, *u = nullptr, *ua = nullptr, *f = nullptr, *r = nullptr, *divc = nullptr;
     float *mod32 = nullptr, *u32 = nullptr, *ua32 = nullptr, *f32 = nullptr, *r32 = nullptr;
     int* bnd = nullptr;   // boundary-plane nodes of this level
     int nbnd = 0;
@@ -181,6 +181,7 @@ void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int 
     L.mod = nullptr;
     L.bnodes = nullptr;
     L.nbnd = 0;
+    L.divc = nullptr;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -370,6 +371,14 @@ int setup(elas_grid g) {
         launch_restrict_moduli<double>(g->lv[l - 1].L64, g->lv[l].L64, g->lv[l - 1].mod64, g->lv[l].mod64, s);
         CHECK_LAUNCH(c);
     }
+    for (int l = 0; l < nl; ++l) {
+        if (g->lv[l].divc) {
+            Lv<double> Lm = g->lv[l].L64;
+            Lm.divc = nullptr;
+            launch_divc(Lm, g->lv[l].divc, s);
+            CHECK_LAUNCH(c);
+        }
+    }
     if (g->desc.mixed) {
         for (int l = 0; l < nl; ++l) {
             Level& v = g->lv[l];
@@ -525,6 +534,7 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     int rc;
     const size_t N = (size_t)v.N;
     if ((rc = galloc(g, &v.mod64, (size_t)g->K * N))) return rc;
+    if (g->K == 21 && (rc = galloc(g, &v.divc, 18 * N))) return rc;
     if ((rc = galloc(g, &v.u, 3 * N))) return rc;
     if ((rc = galloc(g, &v.ua, 3 * N))) return rc;
     if ((rc = galloc(g, &v.f, 3 * N))) return rc;
@@ -574,6 +584,7 @@ void refresh_lv(elas_grid g) {
         v.L32.mod = v.mod32;
         v.L64.bnodes = v.L32.bnodes = v.bnd;
         v.L64.nbnd = v.L32.nbnd = v.nbnd;
+        v.L64.divc = v.divc;
         v.nf = null_space(g->desc, v.n, h, g->bc_type);
     }
 }
@@ -670,7 +681,7 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
     size_t total = 0;
     for (auto& n : level_dims(*d)) {
         const size_t N = (size_t)n[0] * n[1] * n[2];
-        total += N * 8 * (K + 12);
+        total += N * 8 * (K + 12 + (K == 21 ? 18 : 0));
         if (d->mixed) total += N * 4 * (K + 12);
     }
     const size_t N0 = (size_t)d->n[0] * d->n[1] * d->n[2];

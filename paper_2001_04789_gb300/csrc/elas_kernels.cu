@@ -185,7 +185,7 @@ __device__ __forceinline__ void boundary_rows_all(const Lv<T>& L, const T* __res
     }
 }
 
-template <typename T, int KIND>
+template <typename T, int KIND, bool HM>
 __global__ void __launch_bounds__(kBlock) k_apply_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
     int lo[3], cnt[3];
     interior_box(L, lo, cnt);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_int(Lv<T> L, const T* __restri
     if (t >= cnt[0] * cnt[1] * cnt[2]) return;
     const int x = lo[0] + t % cnt[0], y = lo[1] + (t / cnt[0]) % cnt[1], z = lo[2] + t / (cnt[0] * cnt[1]);
     T v[3];
-    interior_rows<T, KIND>(L, u, x, y, z, v);
+    interior_rows<T, KIND, HM>(L, u, x, y, z, v);
     const int p = lin(L, x, y, z);
     for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
 }
@@ -234,7 +234,7 @@ __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restri
     }
 }
 
-template <typename T, typename TR, int KIND, bool NORM>
+template <typename T, typename TR, int KIND, bool NORM, bool HM>
 __global__ void __launch_bounds__(kBlock) k_residual_int(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                                         NullInfo nf, const double* __restrict__ lam,
                                                         TR* __restrict__ r, double* __restrict__ partials) {
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_int(Lv<T> L, const T* __res
     if (t < cnt[0] * cnt[1] * cnt[2]) {
         const int c[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
         T v[3];
-        interior_rows<T, KIND>(L, u, c[0], c[1], c[2], v);
+        interior_rows<T, KIND, HM>(L, u, c[0], c[1], c[2], v);
         const int types[3] = {ROW_INTERIOR, ROW_INTERIOR, ROW_INTERIOR};
         residual_store<T, TR, NORM>(L, f, nf, lam, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
     }
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_bnd(Lv<T> L, const T* __res
 // Red-black smoother, interior nodes: each thread owns the x-pair (x0, x0+1) of the
 // interior box, updates the one of the active colour and copies the other; every
 // row uses the values from before the half-sweep (Jacobi within the colour).
-template <typename T, int KIND>
+template <typename T, int KIND, bool HM>
 __global__ void __launch_bounds__(kBlock) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
                                                           const T* __restrict__ f, int colour, NullInfo nf,
                                                           const double* __restrict__ lam) {
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kBlock) k_half_sweep_int(Lv<T> L, const T* __r
     if (xa >= xend) return;
     const int p = lin(L, xa, y, z);
     T v[3];
-    interior_rows<T, KIND>(L, u, xa, y, z, v);
+    interior_rows<T, KIND, HM>(L, u, xa, y, z, v);
     T r[3], B[3][3], d[3];
     const int c[3] = {xa, y, z};
     for (int i = 0; i < 3; ++i) {
@@ -473,6 +473,30 @@ __global__ void k_restrict_moduli(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ mf, 
         }
         mc[k * Lc.N + P] = acc;
     }
+}
+
+// M_iV = sum_j (C_(ij)V(p+e_j) - C_(ij)V(p-e_j)) / 2h_j at interior nodes, 0 elsewhere.
+template <typename T>
+__global__ void k_divc(Lv<T> L, T* __restrict__ M) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
+    int c[3];
+    coords_of(p, L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    for (int i = 0; i < 3; ++i)
+        for (int V = 0; V < 6; ++V) {
+            T acc = T(0);
+            if (!ni.boundary) {
+                for (int j = 0; j < 3; ++j) {
+                    int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+                    cp[j] = wrapc(L, j, c[j] + 1);
+                    cm[j] = wrapc(L, j, c[j] - 1);
+                    const T* cc = L.mod + upper(voigt(i, j), V) * L.N;
+                    acc += (cc[lin(L, cp[0], cp[1], cp[2])] - cc[lin(L, cm[0], cm[1], cm[2])]) * L.inv2h[j];
+                }
+            }
+            M[(i * 6 + V) * L.N + p] = acc;
+        }
 }
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
@@ -749,8 +773,9 @@ void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
     const size_t ni = interior_count(L);
     if (ni) {
         count_launch();
-        if (L.K == 2) k_apply_int<T, 2><<<blocks_for(ni), kBlock, 0, s>>>(L, u, out);
-        else k_apply_int<T, 21><<<blocks_for(ni), kBlock, 0, s>>>(L, u, out);
+        if (L.K == 2) k_apply_int<T, 2, false><<<blocks_for(ni), kBlock, 0, s>>>(L, u, out);
+        else if (L.divc) k_apply_int<T, 21, true><<<blocks_for(ni), kBlock, 0, s>>>(L, u, out);
+        else k_apply_int<T, 21, false><<<blocks_for(ni), kBlock, 0, s>>>(L, u, out);
     }
     if (L.nbnd) {
         count_launch();
@@ -772,11 +797,13 @@ void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf,
     if (nbi) {
         count_launch();
         if (partials) {
-            if (L.K == 2) k_residual_int<T, TR, 2, true><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
-            else k_residual_int<T, TR, 21, true><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
+            if (L.K == 2) k_residual_int<T, TR, 2, true, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
+            else if (L.divc) k_residual_int<T, TR, 21, true, true><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
+            else k_residual_int<T, TR, 21, true, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
         } else {
-            if (L.K == 2) k_residual_int<T, TR, 2, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
-            else k_residual_int<T, TR, 21, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
+            if (L.K == 2) k_residual_int<T, TR, 2, false, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
+            else if (L.divc) k_residual_int<T, TR, 21, false, true><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
+            else k_residual_int<T, TR, 21, false, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
         }
     }
     if (nbb) {
@@ -799,8 +826,9 @@ void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int 
     const size_t np = interior_pairs(L);
     if (np) {
         count_launch();
-        if (L.K == 2) k_half_sweep_int<T, 2><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
-        else k_half_sweep_int<T, 21><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+        if (L.K == 2) k_half_sweep_int<T, 2, false><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+        else if (L.divc) k_half_sweep_int<T, 21, true><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+        else k_half_sweep_int<T, 21, false><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
     }
     if (L.nbnd) {
         count_launch();
@@ -828,6 +856,11 @@ template <typename T>
 void launch_restrict_moduli(const Lv<T>& Lf, const Lv<T>& Lc, const T* mf, T* mc, cudaStream_t s) {
     count_launch();
     k_restrict_moduli<T><<<blocks_for(Lc.N), kBlock, 0, s>>>(Lf, Lc, mf, mc);
+}
+
+void launch_divc(const Lv<double>& L, double* M, cudaStream_t s) {
+    count_launch();
+    k_divc<double><<<blocks_for(L.N), kBlock, 0, s>>>(L, M);
 }
 
 void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s) {
