@@ -104,6 +104,7 @@ struct elas_grid_s {
     int* flag = nullptr;
     // equilibrating load
     double *G = nullptr, *Ginv = nullptr, *lam = nullptr, *dlam = nullptr, *status = nullptr, *partials = nullptr;
+    double *alam = nullptr, *adlam = nullptr;   // loads as rigid motions (t, w)
     double r0 = 0.0;
     bool moduli_set = false;
     bool dirty = true;
@@ -436,7 +437,7 @@ int setup(elas_grid g) {
         launch_residual<double, double>(L0.L64, L0.ua, L0.f, nullptr, nullptr, L0.r, g->partials, &nb, s);
         CHECK_LAUNCH(c);
         NullInfo none{};
-        launch_finalize(g->partials, nb, none, nullptr, nullptr, nullptr, nullptr, g->status, 0, s);
+        launch_finalize(g->partials, nb, none, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, g->status, 0, s);
         CHECK_LAUNCH(c);
         double st[1];
         int rc = read_status(g, st, 1);
@@ -727,6 +728,8 @@ int elas_grid_create(elas_ctx c, const elas_grid_desc* d, elas_grid* out) {
     if (!rc) rc = galloc(g, &g->Ginv, 36);
     if (!rc) rc = galloc(g, &g->lam, 8);
     if (!rc) rc = galloc(g, &g->dlam, 8);
+    if (!rc) rc = galloc(g, &g->alam, 8);
+    if (!rc) rc = galloc(g, &g->adlam, 8);
     if (!rc) rc = galloc(g, &g->flag, 4);
     if (!rc) {
         refresh_lv(g);
@@ -874,6 +877,10 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
     launch_dirichlet(L0.L64, boundary_data(g), L0.u, opts->warm_start ? 1 : 0, s);
     CHECK_LAUNCH(c);
     CUDA_TRY(c, cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, s));
+    CUDA_TRY(c, cudaMemsetAsync(g->alam, 0, sizeof(double) * 8, s));
+    CUDA_TRY(c, cudaMemsetAsync(g->adlam, 0, sizeof(double) * 8, s));
+    const double* load = nf0 ? g->alam : nullptr;     // current equilibrating load
+    const double* dload = nf0 ? g->adlam : nullptr;   // its latest increment
     info->r0 = g->r0;
     info->nlam = L0.nf.m;
     const int nu1 = opts->nu1 < 0 ? 0 : opts->nu1, nu2 = opts->nu2 < 0 ? 0 : opts->nu2;
@@ -883,13 +890,13 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
     int hist = 0;
     for (;;) {
         int nb = 0;
-        if (!mixed) smooth<double>(g, 0, nu1, nf0, g->lam);
+        if (!mixed) smooth<double>(g, 0, nu1, nf0, load);
         const size_t ev = prof_begin(c, ELAS_PROF_RESID64_L0);
-        if (!mixed) launch_residual<double, double>(L0.L64, L0.u, L0.f, nf0, g->lam, L0.r, g->partials, &nb, s);
-        else launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, g->lam, L0.f32, g->partials, &nb, s);
+        if (!mixed) launch_residual<double, double>(L0.L64, L0.u, L0.f, nf0, load, L0.r, g->partials, &nb, s);
+        else launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, load, L0.f32, g->partials, &nb, s);
         prof_end(c, ev);
         CHECK_LAUNCH(c);
-        launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->status, 1, s);
+        launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1, s);
         CHECK_LAUNCH(c);
         double st[1];
         rc = read_status(g, st, 1);
@@ -915,15 +922,15 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
             // part of r is absorbed by the bordering, so r needs no equilibration here
             launch_bottom_solve<double>(L0.L64, g->dofs, g->nfree, g->ntot, g->Ainv, L0.r, L0.ua, g->bwork, s);
             launch_add_correction64(L0.L64, L0.u, L0.ua, s);
-            smooth<double>(g, 0, nu2, nf0, g->lam);
+            smooth<double>(g, 0, nu2, nf0, load);
         } else if (!mixed) {
             Level& L1 = g->lv[1];
-            launch_restrict<double>(L0.L64, L1.L64, L0.r, L1.f, nf0, nf0 ? g->dlam : nullptr, s);
+            launch_restrict<double>(L0.L64, L1.L64, L0.r, L1.f, nf0, dload, s);
             vcycle<double>(g, 1, nu1, nu2, nullptr, nullptr);
             launch_prolong_add<double>(L0.L64, L1.L64, L1.u, L0.u, s);
-            smooth<double>(g, 0, nu2, nf0, g->lam);
+            smooth<double>(g, 0, nu2, nf0, load);
         } else {
-            vcycle<float>(g, 0, nu1, nu2, nf0, nf0 ? g->dlam : nullptr);
+            vcycle<float>(g, 0, nu1, nu2, nf0, dload);
             launch_add_correction(L0.L64, L0.u, L0.u32, s);
         }
         CHECK_LAUNCH(c);
@@ -969,9 +976,11 @@ int elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2) {
     Level& L0 = g->lv[0];
     const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
     int nb = 0;
-    launch_residual<double, double>(L0.L64, L0.u, L0.f, nf0, g->lam, L0.r, g->partials, &nb, c->stream);
+    launch_residual<double, double>(L0.L64, L0.u, L0.f, nf0, nf0 ? g->alam : nullptr, L0.r, g->partials, &nb,
+                                    c->stream);
     CHECK_LAUNCH(c);
-    launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->status, 0, c->stream);
+    launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 0,
+                    c->stream);
     CHECK_LAUNCH(c);
     double st[1];
     rc = read_status(g, st, 1);

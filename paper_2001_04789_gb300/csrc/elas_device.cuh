@@ -495,6 +495,19 @@ __device__ __forceinline__ double null_vec(const NullInfo& nf, int q, int c, con
     return v;
 }
 
+// Equilibrating load at a non-Dirichlet row from its rigid-motion form a = (t, w):
+// t_c + (w x d)_c, d = x - ctr.  (sum_q lam_q W_q = t + w x d with t, w = basis lam.)
+template <typename T>
+__device__ __forceinline__ T rigid_load(const NullInfo& nf, const double* __restrict__ a, int comp, const int c[3]) {
+    const T d0 = T(nf.lo[0] - nf.ctr[0]) + T(nf.h[0]) * T(c[0]);
+    const T d1 = T(nf.lo[1] - nf.ctr[1]) + T(nf.h[1]) * T(c[1]);
+    const T d2 = T(nf.lo[2] - nf.ctr[2]) + T(nf.h[2]) * T(c[2]);
+    const T w0 = T(a[3]), w1 = T(a[4]), w2 = T(a[5]);
+    if (comp == 0) return T(a[0]) + (w1 * d2 - w2 * d1);
+    if (comp == 1) return T(a[1]) + (w2 * d0 - w0 * d2);
+    return T(a[2]) + (w0 * d1 - w1 * d0);
+}
+
 // sum_q coef[q] W_q(c): the equilibrating load at a non-Dirichlet row.
 __device__ __forceinline__ double null_combo(const NullInfo& nf, const double* coef, int c, const int xyz[3]) {
     double v = 0.0;

@@ -36,8 +36,9 @@ void launch_dirichlet(const Lv<double>& L, const BoundaryData& bd, double* u, in
 template <typename T>
 void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s);
 
-// r = f - lam.W - A u (lam optional); writes r as TR; per-block partials of
-// sum r^2 and W^T r when partials != null.
+// r = f - load - A u (load optional: the equilibrating load as 6 numbers t, w, applied
+// as t + w x d); writes r as TR; per-block partials of sum r^2 and of the six
+// rigid-motion moments of r when partials != null.
 template <typename T, typename TR>
 void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf, const double* lam,
                      TR* r, double* partials, int* nblocks, cudaStream_t s);
@@ -77,8 +78,8 @@ void launch_bottom_solve(const Lv<T>& L, const int* dofs, int nfree, int ntot, c
 // equilibrating-load update dlam = G^-1 W^T r, lam += dlam (if update_lam),
 // and the norm of r - dlam.W.  out[0] = sum r^2 (corrected).
 void launch_finalize(const double* partials, int nblocks, const NullInfo& nf, const double* Ginv,
-                     const double* G, double* lam, double* dlam, double* out, int update_lam,
-                     cudaStream_t s);
+                     const double* G, double* lam, double* dlam, double* alam, double* adlam, double* out,
+                     int update_lam, cudaStream_t s);
 
 // W^T u partials (and W^T W at setup when gram != 0).
 void launch_null_dots(const Lv<double>& L, const NullInfo& nf, const double* u, double* partials,

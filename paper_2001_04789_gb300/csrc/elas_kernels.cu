@@ -212,25 +212,37 @@ __global__ void k_apply_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ ou
     for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
 }
 
-// r = f - lam.W - A u on one node's rows; accumulates sum r^2 and W^T r.
+// r = f - load - A u on one node's rows (load = t + w x d, the equilibrating load);
+// accumulates sum r^2 and the six rigid-motion moments sum r, sum d x r.
 template <typename T, typename TR, bool NORM>
 __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restrict__ f, const NullInfo& nf,
-                                               const double* __restrict__ lam, const int c[3], int p,
+                                               const double* __restrict__ load, const int c[3], int p,
                                                const int types[3], const T v[3], TR* __restrict__ r,
                                                double acc[7]) {
+    double rr[3];
     for (int i = 0; i < 3; ++i) {
         T ri = T(0);
         if (types[i] != ROW_DIRICHLET) {
             T fi = f[i * L.N + p];
-            if (lam && nf.m > 0) fi -= T(null_combo(nf, lam, i, c));
+            if (load) fi -= rigid_load<T>(nf, load, i, c);
             ri = fi - v[i];
-            if (NORM) {
-                const double rd = (double)ri;
-                acc[0] += rd * rd;
-                for (int q = 0; q < nf.m; ++q) acc[1 + q] += null_vec(nf, q, i, c) * rd;
-            }
         }
+        rr[i] = (double)ri;
         r[i * L.N + p] = (TR)ri;
+    }
+    if (NORM) {
+        acc[0] += rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+        if (nf.m > 0) {
+            const double d0 = nf.lo[0] + nf.h[0] * c[0] - nf.ctr[0];
+            const double d1 = nf.lo[1] + nf.h[1] * c[1] - nf.ctr[1];
+            const double d2 = nf.lo[2] + nf.h[2] * c[2] - nf.ctr[2];
+            acc[1] += rr[0];
+            acc[2] += rr[1];
+            acc[3] += rr[2];
+            acc[4] += d1 * rr[2] - d2 * rr[1];
+            acc[5] += d2 * rr[0] - d0 * rr[2];
+            acc[6] += d0 * rr[1] - d1 * rr[0];
+        }
     }
 }
 
@@ -249,7 +261,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_int(Lv<T> L, const T* __res
         const int types[3] = {ROW_INTERIOR, ROW_INTERIOR, ROW_INTERIOR};
         residual_store<T, TR, NORM>(L, f, nf, lam, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
     }
-    if (NORM) block_reduce_store<7>(acc, 1 + nf.m, partials);
+    if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
 }
 
 template <typename T, typename TR, int KIND, bool NORM>
@@ -268,7 +280,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_bnd(Lv<T> L, const T* __res
         boundary_rows_all<T, KIND>(L, u, ni, types, v);
         residual_store<T, TR, NORM>(L, f, nf, lam, c, p, types, v, r, acc);
     }
-    if (NORM) block_reduce_store<7>(acc, 1 + nf.m, partials);
+    if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
 }
 
 // Red-black smoother, interior nodes: each thread owns the x-pair (x0, x0+1) of the
@@ -305,7 +317,7 @@ __global__ void __launch_bounds__(kBlock) k_half_sweep_int(Lv<T> L, const T* __r
     const int c[3] = {xa, y, z};
     for (int i = 0; i < 3; ++i) {
         T fi = f[i * N + p];
-        if (lam && nf.m > 0) fi -= T(null_combo(nf, lam, i, c));
+        if (lam) fi -= rigid_load<T>(nf, lam, i, c);
         r[i] = fi - v[i];
     }
     interior_block<T, KIND>(L, p, B);
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __r
             r[i] = T(0);
         } else {
             T fi = f[i * N + p];
-            if (lam && nf.m > 0) fi -= T(null_combo(nf, lam, i, c));
+            if (lam) fi -= rigid_load<T>(nf, lam, i, c);
             r[i] = fi - v[i];
         }
     }
@@ -373,7 +385,7 @@ __global__ void k_restrict(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ r, T* __res
     restrict_weights(Lc, 1, C[1], wy);
     restrict_weights(Lc, 2, C[2], wz);
     T acc[3] = {T(0), T(0), T(0)};
-    const bool corr = dlam && nf.m > 0;
+    const bool corr = dlam != nullptr;
     for (int dz = -1; dz <= 1; ++dz) {
         if (wz[dz + 1] == T(0)) continue;
         const int fz = wrapc(Lf, 2, 2 * C[2] + dz);
@@ -390,7 +402,7 @@ __global__ void k_restrict(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ r, T* __res
                 if (corr) nif = node_info(Lf, fx, fy, fz);
                 for (int i = 0; i < 3; ++i) {
                     T v = r[i * Lf.N + q];
-                    if (corr && row_type(Lf, nif, i) != ROW_DIRICHLET) v -= T(null_combo(nf, dlam, i, cf));
+                    if (corr && row_type(Lf, nif, i) != ROW_DIRICHLET) v -= rigid_load<T>(nf, dlam, i, cf);
                     acc[i] += w * v;
                 }
             }
@@ -638,13 +650,16 @@ __global__ void k_zero(T* __restrict__ a, size_t n) {
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
+// Deterministic sum of the residual partials; with free rigid modes also
+//   W^T r = basis^T mom,  dlam = G^-1 W^T r,  lam += dlam,
+//   a_lam = basis lam, a_dlam = basis dlam (the loads as t + w x d),
+//   ||r - dlam.W||^2 = ||r||^2 - 2 dlam.W^T r + dlam^T G dlam.
 __global__ void k_finalize(const double* __restrict__ partials, int nblocks, NullInfo nf,
                            const double* __restrict__ Ginv, const double* __restrict__ G,
-                           double* __restrict__ lam, double* __restrict__ dlam, double* __restrict__ out,
-                           int update_lam) {
-    // fixed-order reduction: thread t sums blocks t, t+256, ...; then a fixed tree
+                           double* __restrict__ lam, double* __restrict__ dlam, double* __restrict__ alam,
+                           double* __restrict__ adlam, double* __restrict__ out, int update_lam) {
     __shared__ double sm[kBlock][7];
-    const int width = 1 + nf.m;
+    const int width = nf.m > 0 ? 7 : 1;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
         for (int w = 0; w < width; ++w) acc[w] += partials[b * kPartialStride + w];
@@ -658,16 +673,20 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, Nul
     if (threadIdx.x == 0) {
         double ss = sm[0][0];
         if (nf.m > 0) {
-            double d[6];
+            double wtr[6], d[6];
             for (int q = 0; q < nf.m; ++q) {
                 double v = 0.0;
-                for (int k = 0; k < nf.m; ++k) v += Ginv[q * nf.m + k] * sm[0][1 + k];
+                for (int mo = 0; mo < 6; ++mo) v += nf.basis[mo][q] * sm[0][1 + mo];
+                wtr[q] = v;
+            }
+            for (int q = 0; q < nf.m; ++q) {
+                double v = 0.0;
+                for (int k = 0; k < nf.m; ++k) v += Ginv[q * nf.m + k] * wtr[k];
                 d[q] = v;
             }
-            // ||r - d.W||^2 = ||r||^2 - 2 d.(W^T r) + d^T G d
             double c1 = 0.0, c2 = 0.0;
             for (int q = 0; q < nf.m; ++q) {
-                c1 += d[q] * sm[0][1 + q];
+                c1 += d[q] * wtr[q];
                 for (int k = 0; k < nf.m; ++k) c2 += d[q] * G[q * nf.m + k] * d[k];
             }
             ss = ss - 2.0 * c1 + c2;
@@ -676,9 +695,17 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, Nul
                 dlam[q] = d[q];
                 if (update_lam) lam[q] += d[q];
             }
+            for (int mo = 0; mo < 6; ++mo) {
+                double a = 0.0, b = 0.0;
+                for (int q = 0; q < nf.m; ++q) {
+                    a += nf.basis[mo][q] * lam[q];
+                    b += nf.basis[mo][q] * d[q];
+                }
+                alam[mo] = a;
+                adlam[mo] = b;
+            }
         }
         out[0] = ss;
-        for (int w = 1; w < 7; ++w) out[w] = (w < width) ? sm[0][w] : 0.0;
     }
 }
 
@@ -908,9 +935,10 @@ void launch_bottom_solve(const Lv<T>& L, const int* dofs, int nfree, int ntot, c
 }
 
 void launch_finalize(const double* partials, int nblocks, const NullInfo& nf, const double* Ginv, const double* G,
-                     double* lam, double* dlam, double* out, int update_lam, cudaStream_t s) {
+                     double* lam, double* dlam, double* alam, double* adlam, double* out, int update_lam,
+                     cudaStream_t s) {
     count_launch();
-    k_finalize<<<1, kBlock, 0, s>>>(partials, nblocks, nf, Ginv, G, lam, dlam, out, update_lam);
+    k_finalize<<<1, kBlock, 0, s>>>(partials, nblocks, nf, Ginv, G, lam, dlam, alam, adlam, out, update_lam);
 }
 
 void launch_null_dots(const Lv<double>& L, const NullInfo& nf, const double* u, double* partials, int* nblocks,
