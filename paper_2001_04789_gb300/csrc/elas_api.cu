@@ -267,6 +267,9 @@ NullInfo null_space(const elas_grid_desc& d, const int n[3], const double h[3], 
         nf.lo[k] = d.lo[k];
         nf.h[k] = h[k];
         nf.ctr[k] = d.lo[k] + 0.5 * h[k] * (n[k] - 1);
+        nf.off[k] = nf.lo[k] - nf.ctr[k];
+        nf.off32[k] = (float)nf.off[k];
+        nf.h32[k] = (float)h[k];
     }
     bool allowed[6] = {true, true, true, true, true, true};
     for (int a = 0; a < 3; ++a) {
@@ -549,15 +552,16 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     }
     v.L64.mod = v.mod64;
     v.L32.mod = v.mod32;
-    // list of the nodes that lie on a boundary plane of a non-periodic direction
+    // list of the nodes on two or three boundary planes (face nodes are enumerated
+    // arithmetically by the face kernels)
     std::vector<int> b;
     const int* per = g->desc.periodic;
     for (int z = 0; z < v.n[2]; ++z)
         for (int y = 0; y < v.n[1]; ++y)
             for (int x = 0; x < v.n[0]; ++x) {
-                const bool on = (!per[0] && (x == 0 || x == v.n[0] - 1)) || (!per[1] && (y == 0 || y == v.n[1] - 1)) ||
-                                (!per[2] && (z == 0 || z == v.n[2] - 1));
-                if (on) b.push_back(x + v.n[0] * (y + v.n[1] * z));
+                const int on = (!per[0] && (x == 0 || x == v.n[0] - 1)) + (!per[1] && (y == 0 || y == v.n[1] - 1)) +
+                               (!per[2] && (z == 0 || z == v.n[2] - 1));
+                if (on >= 2) b.push_back(x + v.n[0] * (y + v.n[1] * z));   // edges and corners
             }
     v.nbnd = (int)b.size();
     if (v.nbnd) {
@@ -728,8 +732,8 @@ int elas_grid_create(elas_ctx c, const elas_grid_desc* d, elas_grid* out) {
     if (!rc) rc = galloc(g, &g->Ginv, 36);
     if (!rc) rc = galloc(g, &g->lam, 8);
     if (!rc) rc = galloc(g, &g->dlam, 8);
-    if (!rc) rc = galloc(g, &g->alam, 8);
-    if (!rc) rc = galloc(g, &g->adlam, 8);
+    if (!rc) rc = galloc(g, &g->alam, kLoadDoubles);
+    if (!rc) rc = galloc(g, &g->adlam, kLoadDoubles);
     if (!rc) rc = galloc(g, &g->flag, 4);
     if (!rc) {
         refresh_lv(g);
@@ -877,8 +881,8 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
     launch_dirichlet(L0.L64, boundary_data(g), L0.u, opts->warm_start ? 1 : 0, s);
     CHECK_LAUNCH(c);
     CUDA_TRY(c, cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, s));
-    CUDA_TRY(c, cudaMemsetAsync(g->alam, 0, sizeof(double) * 8, s));
-    CUDA_TRY(c, cudaMemsetAsync(g->adlam, 0, sizeof(double) * 8, s));
+    CUDA_TRY(c, cudaMemsetAsync(g->alam, 0, sizeof(double) * kLoadDoubles, s));
+    CUDA_TRY(c, cudaMemsetAsync(g->adlam, 0, sizeof(double) * kLoadDoubles, s));
     const double* load = nf0 ? g->alam : nullptr;     // current equilibrating load
     const double* dload = nf0 ? g->adlam : nullptr;   // its latest increment
     info->r0 = g->r0;

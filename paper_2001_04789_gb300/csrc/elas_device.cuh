@@ -31,7 +31,7 @@ struct Lv {
     signed char bc[6][3];  // boundary type per (face, component); 0 on periodic faces
     T h[3], inv2h[3], invh[3], invh2[3], inv4hh[3];   // inv4hh[d] for the pair != d
     const T* __restrict__ mod;
-    const int* __restrict__ bnodes;   // linear indices of the nodes on boundary planes
+    const int* __restrict__ bnodes;   // linear indices of the edge and corner nodes
     int nbnd;
     // optional: M_iV = sum_j d_j C_(ij)V (18 planes, interior nodes), precomputed so the
     // modulus-gradient term costs 18 FMAs instead of 54 differences
@@ -442,6 +442,132 @@ __device__ __noinline__ void boundary_block(const Lv<T>& L, const NodeInfo& ni, 
     }
 }
 
+// ---- face-node fast path ------------------------------------------------------------
+// Rows and diagonal block of a node on exactly one boundary plane (direction A, side
+// -1|+1): the product-rule terms of the two tangential directions (central, with the
+// normal derivative one-sided) plus the half-cell term of direction A.  Tangential
+// neighbours exist (face interiors exclude edges; periodic tangents wrap).
+template <typename T, int KIND, int A>
+__device__ __forceinline__ void face_node(const Lv<T>& L, const T* __restrict__ u, const int c[3], int side,
+                                          const int types[3], T out[3], T B[3][3], bool wantB) {
+    constexpr int T1 = (A + 1) % 3, T2 = (A + 2) % 3;
+    const int N = L.N;
+    const int inward = -side;
+    // coordinates along A for depths 0,1,2 and tangential neighbours (wrapped)
+    const int ca[3] = {c[A], c[A] + inward, c[A] + 2 * inward};
+    const int t1m = wrapc(L, T1, c[T1] - 1), t1p = wrapc(L, T1, c[T1] + 1);
+    const int t2m = wrapc(L, T2, c[T2] - 1), t2p = wrapc(L, T2, c[T2] + 1);
+    auto idx = [&](int xa, int x1, int x2) {
+        int q[3];
+        q[A] = xa;
+        q[T1] = x1;
+        q[T2] = x2;
+        return q[0] + L.n[0] * (q[1] + L.n[1] * q[2]);
+    };
+    const int c1 = c[T1], c2 = c[T2];
+    const int p = idx(ca[0], c1, c2);
+    const int pin = idx(ca[1], c1, c2);
+    int q1p[3], q1m[3], q2p[3], q2m[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        q1p[m] = idx(ca[m], t1p, c2);
+        q1m[m] = idx(ca[m], t1m, c2);
+        q2p[m] = idx(ca[m], c1, t2p);
+        q2m[m] = idx(ca[m], c1, t2m);
+    }
+    const int cpp = idx(ca[0], t1p, t2p), cpm = idx(ca[0], t1p, t2m);
+    const int cmp = idx(ca[0], t1m, t2p), cmm = idx(ca[0], t1m, t2m);
+    const int q2in = idx(ca[2], c1, c2);
+    // derivatives: G[k][l] at the node; Dbar[k][l] at the half-cell face; second
+    // derivatives X[k][j][l] for tangential j
+    T G[3][3], Db[3][3], Hjj[3][3], H12[3], HjA[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T* uk = u + k * N;
+        const T u0 = uk[p], u1 = uk[pin], u2 = uk[q2in];
+        G[k][A] = T(inward) * (T(-3) * u0 + T(4) * u1 - u2) * L.inv2h[A];
+        Db[k][A] = T(inward) * (u1 - u0) * L.invh[A];
+        T d1[3], d2[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            d1[m] = (uk[q1p[m]] - uk[q1m[m]]) * L.inv2h[T1];
+            d2[m] = (uk[q2p[m]] - uk[q2m[m]]) * L.inv2h[T2];
+        }
+        G[k][T1] = d1[0];
+        G[k][T2] = d2[0];
+        Db[k][T1] = T(0.5) * (d1[0] + d1[1]);
+        Db[k][T2] = T(0.5) * (d2[0] + d2[1]);
+        Hjj[k][T1] = (uk[q1p[0]] - T(2) * u0 + uk[q1m[0]]) * L.invh2[T1];
+        Hjj[k][T2] = (uk[q2p[0]] - T(2) * u0 + uk[q2m[0]]) * L.invh2[T2];
+        Hjj[k][A] = T(0);
+        H12[k] = (uk[cpp] - uk[cpm] - uk[cmp] + uk[cmm]) * L.inv4hh[A];
+        HjA[k][T1] = T(inward) * (T(-3) * d1[0] + T(4) * d1[1] - d1[2]) * L.inv2h[A];
+        HjA[k][T2] = T(inward) * (T(-3) * d2[0] + T(4) * d2[1] - d2[2]) * L.inv2h[A];
+        HjA[k][A] = T(0);
+    }
+    // DD(k; j, l) for j tangential
+    auto DD = [&](int k, int j, int l) -> T {
+        if (l == j) return Hjj[k][j];
+        if (l == A) return HjA[k][j];
+        return H12[k];
+    };
+    const int qt[2][2] = {{q1p[0], q1m[0]}, {q2p[0], q2m[0]}};
+    const T cA = T(side) * T(1.5) * L.invh[A];   // node weight in its one-sided A-derivative
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int f = 2 * A + (side > 0 ? 1 : 0);
+        if (types[i] == ROW_DIRICHLET) {
+            out[i] = u[i * N + p];
+            if (wantB) { B[i][0] = B[i][1] = B[i][2] = T(0); B[i][i] = T(1); }
+            continue;
+        }
+        if (types[i] == ROW_NEUMANN) {
+            const T C = Cm<T, KIND>(L, p, i, A, i, A);
+            out[i] = -(T(2) * L.invh[A]) * C * T(side) * G[i][A];
+            if (wantB) {
+                B[i][0] = B[i][1] = B[i][2] = T(0);
+                B[i][i] = -(T(2) * L.invh[A]) * C * T(side) * cA;
+            }
+            (void)f;
+            continue;
+        }
+        T acc = T(0);
+        T b[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int j = jj == 0 ? T1 : T2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    if (!Cnz<T, KIND>(i, j, k, l)) continue;
+                    const T C0 = Cm<T, KIND>(L, p, i, j, k, l);
+                    const T dC = (Cm<T, KIND>(L, qt[jj][0], i, j, k, l) - Cm<T, KIND>(L, qt[jj][1], i, j, k, l)) *
+                                 L.inv2h[j];
+                    acc += dC * G[k][l] + C0 * DD(k, j, l);
+                    if (wantB) {
+                        if (l == A) b[k] += dC * cA;
+                        if (l == j) b[k] += C0 * (T(-2) * L.invh2[j]);
+                    }
+                }
+            }
+        }
+        T sacc = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                if (!Cnz<T, KIND>(i, A, k, l)) continue;
+                const T Cb = T(0.5) * (Cm<T, KIND>(L, p, i, A, k, l) + Cm<T, KIND>(L, pin, i, A, k, l));
+                sacc += Cb * Db[k][l];
+                if (wantB && l == A) b[k] += -(T(2) * L.invh[A] * L.invh[A]) * Cb;
+            }
+        }
+        out[i] = acc - (T(2) * L.invh[A]) * T(side) * sacc;
+        if (wantB) { B[i][0] = b[0]; B[i][1] = b[1]; B[i][2] = b[2]; }
+    }
+}
+
 // Solve B d = r for a 3x3 block (explicit inverse by cofactors).
 template <typename T>
 __device__ __forceinline__ void solve3(const T B[3][3], const T r[3], T d[3]) {
@@ -471,7 +597,15 @@ struct NullInfo {
     double ctr[3];
     double lo[3];
     double h[3];
+    double off[3];      // lo - ctr
+    float off32[3];     // the same offsets and spacings in FP32 for FP32 kernels
+    float h32[3];
 };
+
+// A load array holds the rigid motion (t, w) as 6 doubles at [0, 6) and as 6 floats
+// starting at double offset 8.
+constexpr int kLoadFloatOffset = 8;
+constexpr int kLoadDoubles = 12;
 
 __device__ __forceinline__ double rigid_mode(const NullInfo& nf, int mode, int c, const int xyz[3]) {
     if (mode < 3) return mode == c ? 1.0 : 0.0;
@@ -499,13 +633,21 @@ __device__ __forceinline__ double null_vec(const NullInfo& nf, int q, int c, con
 // t_c + (w x d)_c, d = x - ctr.  (sum_q lam_q W_q = t + w x d with t, w = basis lam.)
 template <typename T>
 __device__ __forceinline__ T rigid_load(const NullInfo& nf, const double* __restrict__ a, int comp, const int c[3]) {
-    const T d0 = T(nf.lo[0] - nf.ctr[0]) + T(nf.h[0]) * T(c[0]);
-    const T d1 = T(nf.lo[1] - nf.ctr[1]) + T(nf.h[1]) * T(c[1]);
-    const T d2 = T(nf.lo[2] - nf.ctr[2]) + T(nf.h[2]) * T(c[2]);
-    const T w0 = T(a[3]), w1 = T(a[4]), w2 = T(a[5]);
-    if (comp == 0) return T(a[0]) + (w1 * d2 - w2 * d1);
-    if (comp == 1) return T(a[1]) + (w2 * d0 - w0 * d2);
-    return T(a[2]) + (w0 * d1 - w1 * d0);
+    const T* at = sizeof(T) == 8 ? (const T*)a : (const T*)(a + kLoadFloatOffset);
+    T d0, d1, d2;
+    if (sizeof(T) == 8) {
+        d0 = T(nf.off[0]) + T(nf.h[0]) * T(c[0]);
+        d1 = T(nf.off[1]) + T(nf.h[1]) * T(c[1]);
+        d2 = T(nf.off[2]) + T(nf.h[2]) * T(c[2]);
+    } else {
+        d0 = T(nf.off32[0]) + T(nf.h32[0]) * T(c[0]);
+        d1 = T(nf.off32[1]) + T(nf.h32[1]) * T(c[1]);
+        d2 = T(nf.off32[2]) + T(nf.h32[2]) * T(c[2]);
+    }
+    const T w0 = at[3], w1 = at[4], w2 = at[5];
+    if (comp == 0) return at[0] + (w1 * d2 - w2 * d1);
+    if (comp == 1) return at[1] + (w2 * d0 - w0 * d2);
+    return at[2] + (w0 * d1 - w1 * d0);
 }
 
 // sum_q coef[q] W_q(c): the equilibrating load at a non-Dirichlet row.

@@ -362,6 +362,113 @@ __global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __r
 }
 
 // ---------------------------------------------------------------------------
+// face nodes: nodes on exactly one boundary plane, enumerated per direction A
+// (both sides): thread -> (side, slow tangential, fast tangential)
+// ---------------------------------------------------------------------------
+template <typename T, int A>
+__host__ __device__ inline void face_extent(const Lv<T>& L, int& n_fast, int& n_slow) {
+    constexpr int ta = A == 0 ? 1 : 0;
+    constexpr int tb = A == 2 ? 1 : 2;
+    n_fast = L.per[ta] ? L.n[ta] : L.n[ta] - 2;
+    n_slow = L.per[tb] ? L.n[tb] : L.n[tb] - 2;
+}
+
+template <typename T, int A>
+__device__ __forceinline__ bool face_coords(const Lv<T>& L, int t, int c[3], int& side) {
+    constexpr int ta = A == 0 ? 1 : 0;
+    constexpr int tb = A == 2 ? 1 : 2;
+    int nf, ns;
+    face_extent<T, A>(L, nf, ns);
+    if (t >= 2 * nf * ns) return false;
+    const int i_fast = t % nf;
+    const int rest = t / nf;
+    const int i_slow = rest % ns;
+    const int sd = rest / ns;
+    c[ta] = (L.per[ta] ? 0 : 1) + i_fast;
+    c[tb] = (L.per[tb] ? 0 : 1) + i_slow;
+    c[A] = sd == 0 ? 0 : L.n[A] - 1;
+    side = sd == 0 ? -1 : 1;
+    return true;
+}
+
+template <typename T, int A>
+__device__ __forceinline__ void face_types(const Lv<T>& L, int side, int types[3]) {
+    const int f = 2 * A + (side > 0 ? 1 : 0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int t = L.bc[f][i];
+        types[i] = t == ROW_DIRICHLET ? ROW_DIRICHLET : (t == ROW_NEUMANN ? ROW_NEUMANN : ROW_TRACTION);
+    }
+}
+
+template <typename T, int KIND, int A>
+__global__ void __launch_bounds__(kBlock) k_apply_face(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
+    int c[3], side;
+    if (!face_coords<T, A>(L, blockIdx.x * blockDim.x + threadIdx.x, c, side)) return;
+    int types[3];
+    face_types<T, A>(L, side, types);
+    T v[3], B[3][3];
+    face_node<T, KIND, A>(L, u, c, side, types, v, B, false);
+    const int p = lin(L, c[0], c[1], c[2]);
+    for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
+}
+
+template <typename T, typename TR, int KIND, int A, bool NORM>
+__global__ void __launch_bounds__(kBlock) k_residual_face(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
+                                                         NullInfo nf, const double* __restrict__ load,
+                                                         TR* __restrict__ r, double* __restrict__ partials) {
+    int c[3], side;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (face_coords<T, A>(L, blockIdx.x * blockDim.x + threadIdx.x, c, side)) {
+        int types[3];
+        face_types<T, A>(L, side, types);
+        T v[3], B[3][3];
+        face_node<T, KIND, A>(L, u, c, side, types, v, B, false);
+        residual_store<T, TR, NORM>(L, f, nf, load, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
+    }
+    if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
+}
+
+template <typename T, int KIND, int A>
+__global__ void __launch_bounds__(kBlock) k_half_sweep_face(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
+                                                           const T* __restrict__ f, int colour, NullInfo nf,
+                                                           const double* __restrict__ load) {
+    int c[3], side;
+    if (!face_coords<T, A>(L, blockIdx.x * blockDim.x + threadIdx.x, c, side)) return;
+    const int N = L.N;
+    const int p = lin(L, c[0], c[1], c[2]);
+    if (((c[0] + c[1] + c[2]) & 1) != colour) {
+        uo[p] = u[p];
+        uo[N + p] = u[N + p];
+        uo[2 * N + p] = u[2 * N + p];
+        return;
+    }
+    int types[3];
+    face_types<T, A>(L, side, types);
+    T v[3], B[3][3], r[3], d[3];
+    face_node<T, KIND, A>(L, u, c, side, types, v, B, true);
+    for (int i = 0; i < 3; ++i) {
+        if (types[i] == ROW_DIRICHLET) {
+            r[i] = T(0);
+        } else {
+            T fi = f[i * N + p];
+            if (load) fi -= rigid_load<T>(nf, load, i, c);
+            r[i] = fi - v[i];
+        }
+    }
+    solve3(B, r, d);
+    for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
+}
+
+template <typename T, int A>
+inline size_t face_count(const Lv<T>& L) {
+    if (L.per[A]) return 0;
+    int nf, ns;
+    face_extent<T, A>(L, nf, ns);
+    return (size_t)2 * nf * ns;
+}
+
+// ---------------------------------------------------------------------------
 // transfers (Section 3.2)
 // ---------------------------------------------------------------------------
 // weights of fine offsets -1, 0, +1 for coarse index I in one direction
@@ -703,6 +810,8 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, Nul
                 }
                 alam[mo] = a;
                 adlam[mo] = b;
+                ((float*)(alam + kLoadFloatOffset))[mo] = (float)a;
+                ((float*)(adlam + kLoadFloatOffset))[mo] = (float)b;
             }
         }
         out[0] = ss;
@@ -795,6 +904,42 @@ void launch_dirichlet(const Lv<double>& L, const BoundaryData& bd, double* u, in
     k_dirichlet<<<blocks_for(L.N), kBlock, 0, s>>>(L, bd, u, keep_free);
 }
 
+template <typename T, int A>
+void launch_faces_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
+    const size_t n = face_count<T, A>(L);
+    if (!n) return;
+    count_launch();
+    if (L.K == 2) k_apply_face<T, 2, A><<<blocks_for(n), kBlock, 0, s>>>(L, u, out);
+    else k_apply_face<T, 21, A><<<blocks_for(n), kBlock, 0, s>>>(L, u, out);
+}
+
+template <typename T, typename TR, int A>
+int launch_faces_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo& nfv, const double* load, TR* r,
+                          double* partials, cudaStream_t s) {
+    const size_t n = face_count<T, A>(L);
+    if (!n) return 0;
+    const int nb = blocks_for(n);
+    count_launch();
+    if (partials) {
+        if (L.K == 2) k_residual_face<T, TR, 2, A, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, load, r, partials);
+        else k_residual_face<T, TR, 21, A, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, load, r, partials);
+    } else {
+        if (L.K == 2) k_residual_face<T, TR, 2, A, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, load, r, nullptr);
+        else k_residual_face<T, TR, 21, A, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, load, r, nullptr);
+    }
+    return nb;
+}
+
+template <typename T, int A>
+void launch_faces_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour, const NullInfo& nfv,
+                        const double* load, cudaStream_t s) {
+    const size_t n = face_count<T, A>(L);
+    if (!n) return;
+    count_launch();
+    if (L.K == 2) k_half_sweep_face<T, 2, A><<<blocks_for(n), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, load);
+    else k_half_sweep_face<T, 21, A><<<blocks_for(n), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, load);
+}
+
 template <typename T>
 void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
     const size_t ni = interior_count(L);
@@ -804,6 +949,9 @@ void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
         else if (L.divc) k_apply_int<T, 21, true><<<blocks_for(ni), kBlock, 0, s>>>(L, u, out);
         else k_apply_int<T, 21, false><<<blocks_for(ni), kBlock, 0, s>>>(L, u, out);
     }
+    launch_faces_apply<T, 0>(L, u, out, s);
+    launch_faces_apply<T, 1>(L, u, out, s);
+    launch_faces_apply<T, 2>(L, u, out, s);
     if (L.nbnd) {
         count_launch();
         if (L.K == 2) k_apply_bnd<T, 2><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u, out);
@@ -819,8 +967,12 @@ void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf,
     const size_t ni = interior_count(L);
     const int nbi = ni ? blocks_for(ni) : 0;
     const int nbb = L.nbnd ? blocks_for(L.nbnd) : 0;
-    if (nblocks) *nblocks = nbi + nbb;
-    double* pb = partials ? partials + (size_t)nbi * kPartialStride : nullptr;
+    int off = nbi;
+    off += launch_faces_residual<T, TR, 0>(L, u, f, nfv, lam, r, partials ? partials + (size_t)off * kPartialStride : nullptr, s);
+    off += launch_faces_residual<T, TR, 1>(L, u, f, nfv, lam, r, partials ? partials + (size_t)off * kPartialStride : nullptr, s);
+    off += launch_faces_residual<T, TR, 2>(L, u, f, nfv, lam, r, partials ? partials + (size_t)off * kPartialStride : nullptr, s);
+    if (nblocks) *nblocks = off + nbb;
+    double* pb = partials ? partials + (size_t)off * kPartialStride : nullptr;
     if (nbi) {
         count_launch();
         if (partials) {
@@ -857,6 +1009,9 @@ void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int 
         else if (L.divc) k_half_sweep_int<T, 21, true><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
         else k_half_sweep_int<T, 21, false><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
     }
+    launch_faces_sweep<T, 0>(L, u_in, u_out, f, colour, nfv, lam, s);
+    launch_faces_sweep<T, 1>(L, u_in, u_out, f, colour, nfv, lam, s);
+    launch_faces_sweep<T, 2>(L, u_in, u_out, f, colour, nfv, lam, s);
     if (L.nbnd) {
         count_launch();
         if (L.K == 2) k_half_sweep_bnd<T, 2><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
