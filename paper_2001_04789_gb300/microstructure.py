@@ -222,24 +222,127 @@ def polycrystal(n=257, grains=20, seed=0, c11=1.68, c12=1.21, c44=0.75, width_ce
     return p
 
 
-def penny_crack(n=65, radius=0.25, width=3.0 / 256, E=1.0, nu=0.3, soft=1e-2, strain=1e-3):
+def crack_indicator(X, Y, Z, radius=0.25, width=3.0 / 256):
+    """Diffuse penny-crack indicator: 1 on the disc (radius, plane z = 0.5), decaying
+    as 1 - tanh^2(d / width) with the distance d to the disc."""
+    rho = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+    d = np.sqrt(np.maximum(rho - radius, 0.0) ** 2 + (Z - 0.5) ** 2)
+    return 1.0 - np.tanh(d / width) ** 2
+
+
+def penny_crack(n=65, radius=0.25, width=3.0 / 256, E=1.0, nu=0.3, soft=1e-2, strain=1e-3,
+                clamp_lateral=False, box=None):
     """Penny-shaped diffuse crack (Section 4.2 analogue) in the plane z = 0.5:
     E is reduced to soft * E inside the crack profile, soft capped at 1 % of the
     matrix modulus as Section 4.2 does for numerical stability; u_z = -+strain/2 on
-    the z faces with zero shear traction there, traction-free x and y faces."""
-    p = Problem(n=(n, n, n), name=f"penny_crack_{n}")
+    the z faces (u_x = u_y = 0 there too when clamp_lateral, else zero shear
+    traction), traction-free x and y faces.  ``box = (n3, lo3, hi3)`` evaluates the
+    same fields on a sub-box of the unit cube."""
+    if box is None:
+        p = Problem(n=(n, n, n), name=f"penny_crack_{n}")
+    else:
+        p = Problem(n=tuple(box[0]), lo=tuple(box[1]), hi=tuple(box[2]), name="penny_crack_box")
     X, Y, Z = p.coords()
-    rho = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
-    d = np.sqrt(np.maximum(rho - radius, 0.0) ** 2 + (Z - 0.5) ** 2)
-    phi = 1.0 - np.tanh(d / width) ** 2
+    phi = crack_indicator(X, Y, Z, radius, width)
     lam, mu = lame(E * ((1.0 - phi) + soft * phi), nu)
     p.moduli_kind = MODULI_ISO
     p.moduli = np.stack([lam, mu])
     bc = all_faces(TRACTION, 0.0)
-    bc[4] = [(TRACTION, 0.0), (TRACTION, 0.0), (DIRICHLET, -0.5 * strain)]
-    bc[5] = [(TRACTION, 0.0), (TRACTION, 0.0), (DIRICHLET, +0.5 * strain)]
+    lat = DIRICHLET if clamp_lateral else TRACTION
+    bc[4] = [(lat, 0.0), (lat, 0.0), (DIRICHLET, -0.5 * strain)]
+    bc[5] = [(lat, 0.0), (lat, 0.0), (DIRICHLET, +0.5 * strain)]
     p.bc = bc
     return p
+
+
+# --------------------------------------------------------------------------
+# block-structured AMR layouts (Section 3.1: levels of refinement by 2, tagged
+# where the indicator varies fast; one box per level, properly nested)
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class AmrLevel:
+    """One AMR level.  Node indices are global in the level's own index space
+    (node i of level l sits at lo + i * h_l).  The level's grid is its valid box plus
+    one ghost layer on every coarse/fine face; ``problem`` lives on that grid, with
+    Dirichlet rows on the ghost faces (their values come from the coarser level)."""
+    level: int
+    h: float
+    valid_lo: tuple
+    valid_hi: tuple
+    grid_lo: tuple
+    ghost: tuple            # 6 flags: face has a coarse/fine ghost layer
+    problem: Problem
+
+
+def _tag_box(phi, h, thresh, block, parent_lo, parent_hi, n_level):
+    """Box (in the next finer level's global node indices) covering every aligned
+    block of `block` fine cells that contains a tagged coarse cell, i.e. a coarse
+    cell with a corner node where |grad phi| h > thresh; clipped to stay one coarse
+    cell inside the parent box except on the physical boundary."""
+    g = np.gradient(phi, h)
+    tag = np.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2) * h > thresh   # (z, y, x)
+    if not tag.any():
+        return None
+    idx = np.argwhere(tag)
+    lo_c = idx.min(axis=0)[::-1] + np.array(parent_lo)     # coarse global (x, y, z)
+    hi_c = idx.max(axis=0)[::-1] + np.array(parent_lo)
+    lo_f = 2 * np.maximum(lo_c - 1, 0)
+    hi_f = 2 * (hi_c + 1)
+    lo_f = (lo_f // block) * block
+    hi_f = -(-hi_f // block) * block
+    nmax = 2 * (n_level - 1)
+    lo_f = np.maximum(lo_f, 0)
+    hi_f = np.minimum(hi_f, nmax)
+    for d in range(3):
+        if parent_lo[d] > 0:
+            lo_f[d] = max(lo_f[d], 2 * (parent_lo[d] + 1))
+        if parent_hi[d] < n_level - 1:
+            hi_f[d] = min(hi_f[d], 2 * (parent_hi[d] - 1))
+    if np.any(hi_f - lo_f < 4):
+        return None
+    return tuple(int(v) for v in lo_f), tuple(int(v) for v in hi_f)
+
+
+def amr_layout(make_box_problem, base_n, nlevels, indicator, thresh=0.1, block=32):
+    """Build the AMR levels of a unit-cube workload.  ``make_box_problem(n3, lo3, hi3)``
+    returns the workload's Problem on a node box; ``indicator(X, Y, Z)`` is the field
+    whose gradient tags cells for refinement."""
+    base = make_box_problem((base_n,) * 3, (0.0,) * 3, (1.0,) * 3)
+    levels = [AmrLevel(0, 1.0 / (base_n - 1), (0, 0, 0), (base_n - 1,) * 3, (0, 0, 0),
+                       (False,) * 6, base)]
+    n_level = base_n
+    for l in range(1, nlevels):
+        par = levels[-1]
+        X, Y, Z = par.problem.coords()
+        gl, gh = par.grid_lo, tuple(par.grid_lo[d] + par.problem.n[d] - 1 for d in range(3))
+        phi = indicator(X, Y, Z)
+        box = _tag_box(phi, par.h, thresh, block, par.valid_lo, par.valid_hi, n_level)
+        if box is None:
+            break
+        n_level = 2 * (n_level - 1) + 1
+        h = par.h / 2.0
+        vlo, vhi = box
+        ghost = []
+        for f in range(6):
+            d = f // 2
+            ghost.append(vlo[d] > 0 if f % 2 == 0 else vhi[d] < n_level - 1)
+        glo = tuple(vlo[d] - (1 if ghost[2 * d] else 0) for d in range(3))
+        ghi = tuple(vhi[d] + (1 if ghost[2 * d + 1] else 0) for d in range(3))
+        n3 = tuple(ghi[d] - glo[d] + 1 for d in range(3))
+        lo3 = tuple(glo[d] * h for d in range(3))
+        hi3 = tuple(ghi[d] * h for d in range(3))
+        prob = make_box_problem(n3, lo3, hi3)
+        prob.bc = [list(prob.bc[f]) if not ghost[f] else [(DIRICHLET, 0.0)] * 3 for f in range(6)]
+        levels.append(AmrLevel(l, h, vlo, vhi, glo, tuple(ghost), prob))
+    return levels
+
+
+def amr_penny_crack(base_n=65, nlevels=3, block=32, thresh=0.1, width=3.0 / 256, **kw):
+    """Penny crack on a 3-level layout, ratio 2 (laterally clamped z grips)."""
+    mk = lambda n3, lo3, hi3: penny_crack(width=width, clamp_lateral=True, box=(n3, lo3, hi3), **kw)
+    ind = lambda X, Y, Z: crack_indicator(X, Y, Z, width=width)
+    return amr_layout(mk, base_n, nlevels, ind, thresh, block)
 
 
 def ellipsoid_rve(n, seed, nu=0.3, width_cells=3.0, strain_norm=1e-3):

@@ -1,0 +1,157 @@
+"""Pins of the oracle's composite (reflux-free) AMR treatment, Section 3.2 and
+Appendix A: the effective coarse/fine stencil printed in Appendix A, exactness on
+affine fields, and convergence of the composite cycle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2001_04789_gb300 import microstructure as M
+from oracle import amr as A
+from oracle import stencil as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "appendix_a_stencil.json")
+
+
+def laplacian_box(mu=0.7):
+    """lambda = -mu: the elastic operator becomes mu * Laplacian on each component,
+    the scalar setting of Appendix A."""
+    def mk(n3, lo3, hi3):
+        p = M.Problem(n=tuple(n3), lo=tuple(lo3), hi=tuple(hi3))
+        shape = (n3[2], n3[1], n3[0])
+        p.moduli_kind = M.MODULI_ISO
+        p.moduli = np.stack([np.full(shape, -mu), np.full(shape, mu)])
+        p.bc = M.all_faces(M.DIRICHLET, 0.0)
+        return p
+    return mk
+
+
+def two_level(mu=0.7):
+    ind = lambda X, Y, Z: np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) / 0.02)
+    specs = M.amr_layout(laplacian_box(mu), 17, 2, ind, thresh=0.3, block=8)
+    assert len(specs) == 2 and all(specs[1].ghost)
+    return specs, A.build(specs)
+
+
+def test_appendix_a_one_d_effective_stencil():
+    gold = json.load(open(GOLD))["one_d"]["coefficients_times_dxf2"]
+    mu = 0.7
+    specs, data = two_level(mu)
+    c, f = data
+    rng = np.random.default_rng(0)
+    # fields varying in x only
+    uc = np.broadcast_to(rng.normal(size=c.L.level.n[0])[None, None, None, :], (3,) + c.L.level.shape).copy()
+    uf = np.broadcast_to(rng.normal(size=f.L.level.n[0])[None, None, None, :], (3,) + f.L.level.shape).copy()
+    A.inject(f, uf, c, uc)
+    A.fill_ghosts(c, uc, f, uf)
+    sp = f.spec
+    lo = sp.valid_lo[0]
+    ix = lo - sp.grid_lo[0]                     # grid index of the C/F node in x
+    jy = (sp.valid_lo[1] + sp.valid_hi[1]) // 2 - sp.grid_lo[1]
+    kz = (sp.valid_lo[2] + sp.valid_hi[2]) // 2 - sp.grid_lo[2]
+    row = S.pde_rows(f.L.level, uf)[0, kz, jy, ix]
+    h = f.L.level.h[0]
+    cI = lo // 2 - c.spec.grid_lo[0]            # coarse node coincident with the C/F node
+    expect = mu * (gold["fine_inward"] * uf[0, kz, jy, ix + 1] + gold["fine_node"] * uf[0, kz, jy, ix]
+                   + gold["coarse_outward"] * uc[0, 0, 0, cI - 1]) / h ** 2
+    assert np.isclose(row, expect, rtol=1e-12, atol=1e-12 * abs(expect))
+    kc = (sp.grid_lo[2] + kz) // 2 - c.spec.grid_lo[2]
+    jc = (sp.grid_lo[1] + jy) // 2 - c.spec.grid_lo[1]
+    assert np.isclose(uc[0, kc, jc, cI], uf[0, kz, jy, ix])      # injection
+
+
+def test_appendix_a_two_d_corner_effective_stencil():
+    gold = json.load(open(GOLD))["two_d_corner"]
+    gx, gy = gold["x_part_times_dxf2"], gold["y_part_times_dyf2"]
+    mu = 0.7
+    specs, data = two_level(mu)
+    c, f = data
+    rng = np.random.default_rng(1)
+    ny_c, nx_c = c.L.level.shape[1:]
+    ny_f, nx_f = f.L.level.shape[1:]
+    uc = np.broadcast_to(rng.normal(size=(ny_c, nx_c))[None, None], (3,) + c.L.level.shape).copy()
+    uf = np.broadcast_to(rng.normal(size=(ny_f, nx_f))[None, None], (3,) + f.L.level.shape).copy()
+    A.inject(f, uf, c, uc)
+    A.fill_ghosts(c, uc, f, uf)
+    sp = f.spec
+    ix, jy = sp.valid_lo[0] - sp.grid_lo[0], sp.valid_lo[1] - sp.grid_lo[1]
+    kz = (sp.valid_lo[2] + sp.valid_hi[2]) // 2 - sp.grid_lo[2]
+    row = S.pde_rows(f.L.level, uf)[1, kz, jy, ix]
+    hx, hy = f.L.level.h[0], f.L.level.h[1]
+    cI, cJ = sp.valid_lo[0] // 2 - c.spec.grid_lo[0], sp.valid_lo[1] // 2 - c.spec.grid_lo[1]
+    expect = mu * ((gx["fine_inward"] * uf[1, kz, jy, ix + 1] + gx["fine_node"] * uf[1, kz, jy, ix]
+                    + gx["coarse_outward"] * uc[1, 0, cJ, cI - 1]) / hx ** 2
+                   + (gy["fine_inward"] * uf[1, kz, jy + 1, ix] + gy["fine_node"] * uf[1, kz, jy, ix]
+                      + gy["coarse_outward"] * uc[1, 0, cJ - 1, cI]) / hy ** 2)
+    assert np.isclose(row, expect, rtol=1e-12, atol=1e-12 * abs(expect))
+
+
+def test_composite_solve_reproduces_affine_field_exactly():
+    G = np.array([[1.0, 0.3, -0.2], [0.1, -0.5, 0.4], [0.2, 0.0, 0.7]]) * 1e-3
+    b = np.array([1e-4, -2e-4, 3e-4])
+
+    def mk(n3, lo3, hi3):
+        p = M.Problem(n=tuple(n3), lo=tuple(lo3), hi=tuple(hi3))
+        X, Y, Z = p.coords()
+        lam, mu = M.lame(np.ones(X.shape), 0.3)
+        p.moduli_kind = M.MODULI_ISO
+        p.moduli = np.stack([lam, mu])
+        x = [X, Y, Z]
+        ue = np.stack([sum(G[k, l] * x[l] for l in range(3)) + b[k] for k in range(3)])
+        p.bc = M.all_faces(M.DIRICHLET, 0.0)
+        p.face_values = {f_: ue for f_ in range(6)}
+        return p
+
+    ind = lambda X, Y, Z: np.exp(-((X - 0.4) ** 2 + (Y - 0.6) ** 2 + (Z - 0.5) ** 2) / 0.02)
+    specs = M.amr_layout(mk, 17, 3, ind, thresh=0.15, block=8)
+    assert len(specs) == 3
+    u, info = A.solve(specs, tol=1e-12, max_cycles=60)
+    assert info["converged"]
+    for sp, ul in zip(specs, u):
+        X, Y, Z = sp.problem.coords()
+        x = [X, Y, Z]
+        ue = np.stack([sum(G[k, l] * x[l] for l in range(3)) + b[k] for k in range(3)])
+        assert np.abs(ul - ue).max() < 1e-11
+
+
+def test_composite_cycle_converges_on_penny_crack():
+    specs = M.amr_penny_crack(base_n=17, nlevels=2, block=8, width=3.0 / 32)
+    u, info = A.solve(specs, tol=1e-9, max_cycles=60)
+    assert info["converged"], info["rel_history"][-5:]
+
+
+def test_composite_solution_approaches_uniform_fine_solution():
+    """With the refined box around the only structure of the field, the composite
+    solution on the fine box approaches the uniform fine-grid solution as the box
+    grows: the error of a 2-level solve stays far below the coarse-grid error."""
+    from oracle import multigrid as MG
+
+    def mk(n3, lo3, hi3):
+        p = M.Problem(n=tuple(n3), lo=tuple(lo3), hi=tuple(hi3))
+        X, Y, Z = p.coords()
+        E = 1.0 + 0.8 * np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) / 0.01)
+        lam, mu = M.lame(E, 0.3)
+        p.moduli_kind = M.MODULI_ISO
+        p.moduli = np.stack([lam, mu])
+        e = np.zeros((6,) + X.shape)
+        e[0] = e[1] = e[2] = 1e-3 * np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) / 0.01)
+        p.eigenstrain = e
+        p.bc = M.all_faces(M.DIRICHLET, 0.0)
+        return p
+
+    ind = lambda X, Y, Z: np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) / 0.01)
+    specs = M.amr_layout(mk, 17, 2, ind, thresh=0.05, block=8)
+    u, info = A.solve(specs, tol=1e-11, max_cycles=80)
+    assert info["converged"]
+    fine = mk((33, 33, 33), (0, 0, 0), (1, 1, 1))
+    uf, _ = MG.solve(fine, tol=1e-11, max_cycles=80)
+    coarse = mk((17, 17, 17), (0, 0, 0), (1, 1, 1))
+    uc, _ = MG.solve(coarse, tol=1e-11, max_cycles=80)
+    sp = specs[1]
+    sl = tuple(slice(sp.valid_lo[d], sp.valid_hi[d] + 1) for d in (2, 1, 0))
+    ul = u[1][(slice(None),) + tuple(slice(sp.valid_lo[d] - sp.grid_lo[d], sp.valid_hi[d] - sp.grid_lo[d] + 1)
+                                     for d in (2, 1, 0))]
+    err_amr = np.abs(ul - uf[(slice(None),) + sl]).max()
+    err_coarse = np.abs(uc - uf[:, ::2, ::2, ::2]).max()
+    assert err_amr < 0.5 * err_coarse, (err_amr, err_coarse)
