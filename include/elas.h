@@ -102,12 +102,16 @@ typedef struct {
     double lo[3], hi[3];  /* domain corners                                  */
     int    moduli_kind;   /* ELAS_MODULI_ISO or ELAS_MODULI_GEN21            */
     int    mixed;         /* 1 = also allocate the FP32 hierarchy            */
+    int    max_levels;    /* 0 = coarsen automatically; 1 = this level only (AMR
+                             fine levels: smoothed, never solved on their own)  */
 } elas_grid_desc;
 
 /* Create a grid and its multigrid hierarchy (Section 3.1: levels below 0,
  * coarsened by 2 while every direction stays coarsenable and some direction has
  * more than 5 nodes).  Requires n >= 3 per non-periodic direction, n >= 4 per
- * periodic one.  All boundary types default to Dirichlet 0. */
+ * periodic one, and (unless max_levels == 1) node counts that coarsen down to a
+ * bottom level of at most 6000 unknowns (e.g. n = 2^k m + 1 with small m).  All
+ * boundary types default to Dirichlet 0. */
 int  elas_grid_create(elas_ctx ctx, const elas_grid_desc* desc, elas_grid* out);
 int  elas_grid_destroy(elas_grid g);
 /* Number of multigrid levels and the node counts of one of them. */
@@ -213,6 +217,32 @@ int  elas_op_bottom(elas_grid g, int precision, const void* f, void* u);
 int  elas_profile_enable(elas_ctx ctx, int enable);
 int  elas_profile_read(elas_ctx ctx, int kernel_class, double* total_ms, long long* launches);
 unsigned long long elas_launch_count(void);
+
+/* ---- block-structured AMR (Section 3.1, reflux-free coarse/fine, Section 3.2,
+ * Appendix A) ------------------------------------------------------------------
+ * nlevels grids of one context: level 0 covers the domain (with its multigrid
+ * hierarchy); level l >= 1 is one box at half the spacing of level l-1, created
+ * with max_levels = 1.  Placement: node i of level l's global index space sits at
+ * lo + i h_0 / 2^l; grid_lo is the global index of the grid's first node, the valid
+ * box [valid_lo, valid_hi] is the part it solves for, and ghost[f] marks a
+ * coarse/fine face carrying one ghost layer (set that face's boundary type to
+ * Dirichlet).  The caller creates, loads and destroys the grids; elas_amr holds
+ * work arrays only.  Covered coarse moduli are replaced by the restriction of the
+ * finer level's (operator equivalence across levels).  Solve: the composite cycle
+ * (ghosts by trilinear interpolation of the coarser level, covered coarse nodes by
+ * injection, restricted fine residuals on covered nodes, level-0 V-cycle); FP64;
+ * the problem must have no free rigid modes.  Level solutions are read with
+ * elas_get_displacement on each grid. */
+typedef struct elas_amr_s* elas_amr;
+typedef struct {
+    int grid_lo[3];
+    int valid_lo[3];
+    int valid_hi[3];
+    int ghost[6];
+} elas_amr_level;
+int  elas_amr_create(elas_grid* grids, const elas_amr_level* levels, int nlevels, elas_amr* out);
+int  elas_amr_destroy(elas_amr a);
+int  elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* info);
 
 /* ---- batches ---------------------------------------------------------------
  * Solve n independent grids of the same context, all in flight at once on the

@@ -78,8 +78,9 @@ def coarse_moduli(specs):
 def build(specs):
     out = []
     mods = coarse_moduli(specs)
-    for sp, mod in zip(specs, mods):
-        sp.problem.moduli = mod
+    specs = [dataclasses.replace(sp, problem=dataclasses.replace(sp.problem, moduli=mod))
+             for sp, mod in zip(specs, mods)]
+    for sp in specs:
         lev = S.level_from_problem(sp.problem)
         if sp.level == 0:
             levels0 = MG.build_hierarchy(lev)

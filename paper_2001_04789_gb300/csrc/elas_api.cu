@@ -202,7 +202,7 @@ std::vector<std::array<int, 3>> level_dims(const elas_grid_desc& d) {
     std::vector<std::array<int, 3>> out;
     std::array<int, 3> n = {d.n[0], d.n[1], d.n[2]};
     out.push_back(n);
-    while (coarsenable(n.data(), d.periodic)) {
+    while (d.max_levels != 1 && coarsenable(n.data(), d.periodic)) {
         for (int k = 0; k < 3; ++k) n[k] = d.periodic[k] ? n[k] / 2 : (n[k] - 1) / 2 + 1;
         out.push_back(n);
     }
@@ -420,7 +420,7 @@ int setup(elas_grid g) {
         CUDA_TRY(c, cudaStreamSynchronize(s));
     }
     // bottom: dense inverse of the coarsest operator (bordered when singular)
-    {
+    if (g->ntot > 0) {
         Level& B = g->lv[nl - 1];
         launch_bottom_assemble(B.L64, g->dofs, g->nfree, B.nf, g->Awork, s);
         CHECK_LAUNCH(c);
@@ -604,9 +604,17 @@ int rebuild_bottom_dofs(elas_grid g) {
                 for (c[0] = 0; c[0] < B.n[0]; ++c[0])
                     if (host_row_type(g->bc_type, g->desc.periodic, B.n, c, comp) != ROW_DIRICHLET)
                         dofs.push_back(comp * B.N + c[0] + B.n[0] * (c[1] + B.n[1] * c[2]));
-    const int nfree = (int)dofs.size();
-    const int ntot = nfree + B.nf.m;
+    int nfree = (int)dofs.size();
+    int ntot = nfree + B.nf.m;
     elas_ctx ctx = g->ctx;
+    if (g->desc.max_levels == 1) {
+        nfree = ntot = 0;   // smoothed only, no bottom solve
+        g->nfree = g->ntot = 0;
+        return ELAS_OK;
+    }
+    if (ntot > 6000)
+        return set_err(ctx, ELAS_ERR_INVALID_ARG,
+                       "node counts do not coarsen to a small bottom level (use n = 2^k m + 1 with small m)");
     if (ntot != g->ntot || !g->dofs) {
         // (re)allocate: sizes change only with the boundary types
         int rc;
@@ -872,6 +880,7 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
     std::memset(info, 0, sizeof(*info));
     const bool mixed = opts->precision == ELAS_PRECISION_MIXED;
     if (mixed && !g->desc.mixed) return set_err(c, ELAS_ERR_STATE, "grid was created without the FP32 hierarchy");
+    if (g->desc.max_levels == 1) return set_err(c, ELAS_ERR_STATE, "grid has no multigrid hierarchy (AMR level)");
     const auto t0 = std::chrono::steady_clock::now();
     int rc = setup(g);
     if (rc) return rc;
@@ -1135,6 +1144,265 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
         if (rc != ELAS_OK && worst == ELAS_OK) worst = rc;
     }
     return worst;
+}
+
+}  // extern "C"
+
+// ======================================================================================
+// block-structured AMR: composite reflux-free cycle
+// ======================================================================================
+struct elas_amr_s {
+    std::vector<elas_grid> g;
+    std::vector<AmrBox> box;
+    std::vector<double*> res, rpass, cor, cora, tmp;
+    std::vector<std::pair<void*, size_t>> allocs;
+    double* partials = nullptr;
+    size_t npart = 0;
+};
+
+namespace {
+
+struct LevelSwap {
+    Level& v;
+    double *u, *ua, *f, *r;
+    LevelSwap(Level& lv, double* nu, double* nua, double* nf, double* nr) : v(lv), u(lv.u), ua(lv.ua), f(lv.f), r(lv.r) {
+        v.u = nu;
+        v.ua = nua;
+        v.f = nf;
+        v.r = nr;
+    }
+    ~LevelSwap() {
+        v.u = u;
+        v.ua = ua;
+        v.f = f;
+        v.r = r;
+    }
+};
+
+int amr_composite_residual(elas_amr a) {
+    const int nl = (int)a->g.size();
+    elas_ctx c = a->g[0]->ctx;
+    cudaStream_t s = c->stream;
+    for (int l = nl - 1; l >= 1; --l)
+        launch_amr_interp(a->g[l]->lv[0].L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->g[l - 1]->lv[0].u,
+                          a->g[l]->lv[0].u, 0, s);
+    for (int l = 0; l < nl; ++l) {
+        Level& v = a->g[l]->lv[0];
+        launch_residual<double, double>(v.L64, v.u, v.f, nullptr, nullptr, a->res[l], nullptr, nullptr, s);
+    }
+    for (int l = nl - 1; l >= 1; --l)
+        launch_amr_restrict(a->g[l]->lv[0].L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->res[l],
+                            a->res[l - 1], 3, 1, s);
+    CHECK_LAUNCH(c);
+    return ELAS_OK;
+}
+
+int amr_norm(elas_amr a, double* out) {
+    const int nl = (int)a->g.size();
+    elas_ctx c = a->g[0]->ctx;
+    cudaStream_t s = c->stream;
+    int off = 0;
+    for (int l = 0; l < nl; ++l)
+        off += launch_amr_norm(a->g[l]->lv[0].L64, a->box[l], l + 1 < nl ? &a->box[l + 1] : nullptr, a->res[l],
+                               a->partials + (size_t)off * kPartialStride, s);
+    launch_sum_partials(a->partials, off, 1, a->g[0]->status, s);
+    CHECK_LAUNCH(c);
+    double st[1];
+    int rc = read_status(a->g[0], st, 1);
+    if (rc) return rc;
+    *out = std::sqrt(st[0]);
+    return ELAS_OK;
+}
+
+void amr_cycle(elas_amr a, int nu1, int nu2) {
+    const int nl = (int)a->g.size();
+    cudaStream_t s = a->g[0]->ctx->stream;
+    for (int l = 0; l < nl; ++l) {
+        const size_t bytes = sizeof(double) * 3 * (size_t)a->g[l]->lv[0].N;
+        cudaMemcpyAsync(a->rpass[l], a->res[l], bytes, cudaMemcpyDeviceToDevice, s);
+    }
+    for (int l = nl - 1; l >= 1; --l) {
+        elas_grid gl = a->g[l];
+        Level& v = gl->lv[0];
+        cudaMemsetAsync(a->cor[l], 0, sizeof(double) * 3 * (size_t)v.N, s);
+        {
+            LevelSwap sw(v, a->cor[l], a->cora[l], a->res[l], a->tmp[l]);
+            smooth<double>(gl, 0, nu1, nullptr, nullptr);
+            launch_residual<double, double>(v.L64, v.u, v.f, nullptr, nullptr, a->rpass[l], nullptr, nullptr, s);
+        }
+        launch_amr_restrict(v.L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->rpass[l], a->rpass[l - 1], 3, 1,
+                            s);
+        if (l - 1 >= 1)
+            cudaMemcpyAsync(a->res[l - 1], a->rpass[l - 1], sizeof(double) * 3 * (size_t)a->g[l - 1]->lv[0].N,
+                            cudaMemcpyDeviceToDevice, s);
+    }
+    {
+        Level& v0 = a->g[0]->lv[0];
+        LevelSwap sw(v0, a->cor[0], a->cora[0], nl > 1 ? a->rpass[0] : a->res[0], a->tmp[0]);
+        vcycle<double>(a->g[0], 0, nu1, nu2, nullptr, nullptr);
+    }
+    for (int l = 1; l < nl; ++l) {
+        elas_grid gl = a->g[l];
+        Level& v = gl->lv[0];
+        const Lv<double>& Lc = a->g[l - 1]->lv[0].L64;
+        launch_amr_interp(v.L64, a->box[l], Lc, a->box[l - 1], a->cor[l - 1], a->cor[l], 1, s);
+        launch_amr_interp(v.L64, a->box[l], Lc, a->box[l - 1], a->cor[l - 1], a->cor[l], 0, s);
+        LevelSwap sw(v, a->cor[l], a->cora[l], a->res[l], a->tmp[l]);
+        smooth<double>(gl, 0, nu2, nullptr, nullptr);
+    }
+    for (int l = 0; l < nl; ++l) launch_amr_add(a->g[l]->lv[0].L64, a->box[l], a->g[l]->lv[0].u, a->cor[l], s);
+    for (int l = nl - 1; l >= 1; --l)
+        launch_amr_inject(a->g[l]->lv[0].L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->g[l]->lv[0].u,
+                          a->g[l - 1]->lv[0].u, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int elas_amr_create(elas_grid* grids, const elas_amr_level* levels, int nlevels, elas_amr* out) {
+    if (!grids || !levels || nlevels < 1 || !out) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = grids[0]->ctx;
+    for (int l = 0; l < nlevels; ++l) {
+        if (!grids[l] || grids[l]->ctx != c) return set_err(c, ELAS_ERR_INVALID_ARG, "AMR grids must share a context");
+        if (grids[l]->K != grids[0]->K) return set_err(c, ELAS_ERR_INVALID_ARG, "AMR levels need one moduli kind");
+        if (l > 0 && grids[l]->desc.max_levels != 1)
+            return set_err(c, ELAS_ERR_INVALID_ARG, "AMR levels above 0 must be created with max_levels = 1");
+    }
+    elas_amr a = new elas_amr_s();
+    size_t parts = 64;
+    for (int l = 0; l < nlevels; ++l) {
+        elas_grid g = grids[l];
+        AmrBox b{};
+        for (int d = 0; d < 3; ++d) {
+            b.grid_lo[d] = levels[l].grid_lo[d];
+            b.valid_lo[d] = levels[l].valid_lo[d];
+            b.valid_hi[d] = levels[l].valid_hi[d];
+            b.count[d] = (grids[0]->desc.n[d] - 1) * (1 << l) + 1;
+            const int glo = b.grid_lo[d], ghi = glo + g->desc.n[d] - 1;
+            if (b.valid_lo[d] < glo || b.valid_hi[d] > ghi || b.valid_lo[d] > b.valid_hi[d] ||
+                (l > 0 && ((b.valid_lo[d] & 1) || (b.valid_hi[d] & 1)))) {
+                delete a;
+                return set_err(c, ELAS_ERR_INVALID_ARG, "AMR valid box outside its grid or not coarse-aligned");
+            }
+        }
+        for (int f = 0; f < 6; ++f) b.ghost[f] = levels[l].ghost[f];
+        a->g.push_back(g);
+        a->box.push_back(b);
+        parts += (size_t)((g->lv[0].N + kBlock - 1) / kBlock) * kPartialStride;
+    }
+    auto alloc = [&](double** p, size_t count) -> int {
+        const size_t bytes = count * sizeof(double);
+        void* q = ctx_alloc(c, bytes);
+        if (!q) return set_err(c, ELAS_ERR_ALLOC, "AMR work arrays: allocation failed");
+        a->allocs.push_back({q, bytes});
+        *p = (double*)q;
+        return ELAS_OK;
+    };
+    int rc = alloc(&a->partials, parts);
+    for (int l = 0; l < nlevels && !rc; ++l) {
+        const size_t n3 = 3 * (size_t)grids[l]->lv[0].N;
+        double *r1, *r2, *r3, *r4, *r5;
+        if ((rc = alloc(&r1, n3)) || (rc = alloc(&r2, n3)) || (rc = alloc(&r3, n3)) || (rc = alloc(&r4, n3)) ||
+            (rc = alloc(&r5, n3)))
+            break;
+        a->res.push_back(r1);
+        a->rpass.push_back(r2);
+        a->cor.push_back(r3);
+        a->cora.push_back(r4);
+        a->tmp.push_back(r5);
+    }
+    if (rc) {
+        elas_amr_destroy(a);
+        return rc;
+    }
+    *out = a;
+    return ELAS_OK;
+}
+
+int elas_amr_destroy(elas_amr a) {
+    if (!a) return ELAS_ERR_INVALID_ARG;
+    if (!a->g.empty()) {
+        elas_ctx c = a->g[0]->ctx;
+        cudaStreamSynchronize(c->stream);
+        for (auto& p : a->allocs) ctx_free(c, p.first, p.second);
+        cudaStreamSynchronize(c->stream);
+    }
+    delete a;
+    return ELAS_OK;
+}
+
+int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* info) {
+    if (!a || !opts || !info) return ELAS_ERR_INVALID_ARG;
+    const int nl = (int)a->g.size();
+    elas_ctx c = a->g[0]->ctx;
+    cudaSetDevice(c->device);
+    std::memset(info, 0, sizeof(*info));
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = c->stream;
+    bool dirty = false;
+    for (auto g : a->g) dirty |= g->dirty;
+    if (dirty) {
+        for (int l = nl - 1; l >= 1; --l) {
+            if (!a->g[l]->moduli_set || !a->g[l - 1]->moduli_set) return set_err(c, ELAS_ERR_STATE, "moduli not set");
+            launch_amr_restrict(a->g[l]->lv[0].L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1],
+                                a->g[l]->lv[0].mod64, a->g[l - 1]->lv[0].mod64, a->g[l]->K, 0, s);
+            a->g[l - 1]->dirty = true;
+        }
+        CHECK_LAUNCH(c);
+    }
+    for (auto g : a->g) {
+        int rc = setup(g);
+        if (rc) return rc;
+    }
+    if (a->g[0]->lv[0].nf.m > 0) return set_err(c, ELAS_ERR_STATE, "AMR solve needs a problem without free rigid modes");
+    for (int l = 0; l < nl; ++l) launch_dirichlet(a->g[l]->lv[0].L64, boundary_data(a->g[l]), a->g[l]->lv[0].u, 0, s);
+    for (int l = nl - 1; l >= 1; --l)
+        launch_amr_inject(a->g[l]->lv[0].L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->g[l]->lv[0].u,
+                          a->g[l - 1]->lv[0].u, s);
+    int rc = amr_composite_residual(a);
+    if (rc) return rc;
+    double r0 = 0.0;
+    if ((rc = amr_norm(a, &r0))) return rc;
+    info->r0 = r0;
+    const int nu1 = opts->nu1 < 0 ? 0 : opts->nu1, nu2 = opts->nu2 < 0 ? 0 : opts->nu2;
+    int cycles = 0, hist = 0, status = ELAS_OK;
+    double rel = 0.0;
+    for (;;) {
+        double nr = 0.0;
+        if (cycles > 0) {
+            if ((rc = amr_composite_residual(a))) return rc;
+            if ((rc = amr_norm(a, &nr))) return rc;
+        } else {
+            nr = r0;
+        }
+        rel = r0 > 0 ? nr / r0 : 0.0;
+        if (hist < ELAS_HISTORY) info->rel_history[hist++] = rel;
+        if (!std::isfinite(rel) || rel > 1e12) {
+            status = ELAS_ERR_DIVERGED;
+            break;
+        }
+        if (opts->fixed_cycles > 0) {
+            if (cycles >= opts->fixed_cycles) break;
+        } else {
+            if (rel <= opts->rel_tol) break;
+            if (cycles >= opts->max_cycles) {
+                status = ELAS_ERR_NOT_CONVERGED;
+                break;
+            }
+        }
+        amr_cycle(a, nu1, nu2);
+        CHECK_LAUNCH(c);
+        ++cycles;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    info->cycles = cycles;
+    info->rel_residual = rel;
+    info->status = status;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (status == ELAS_ERR_NOT_CONVERGED) set_err(c, status, "maximum cycles reached above the tolerance");
+    if (status == ELAS_ERR_DIVERGED) set_err(c, status, "residual diverged");
+    return status;
 }
 
 }  // extern "C"

@@ -89,4 +89,30 @@ void launch_sum_partials(const double* partials, int nblocks, int width, double*
 void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* Ginv, const double* wtu,
                         double* u, cudaStream_t s);
 
+// ---- block-structured AMR transfers ------------------------------------------------
+// Placement of one AMR level's grid in its level's global node index space.
+struct AmrBox {
+    int grid_lo[3];
+    int valid_lo[3];
+    int valid_hi[3];
+    int ghost[6];
+    int count[3];      // global node count of the level per direction
+};
+
+// mode 0: ghost nodes := I(coarse); mode 1: valid non-Dirichlet nodes += I(coarse)
+void launch_amr_interp(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
+                       const double* cfield, double* ffield, int mode, cudaStream_t s);
+// covered coarse nodes := coincident fine values
+void launch_amr_inject(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
+                       const double* ffield, double* cfield, cudaStream_t s);
+// covered coarse nodes := renormalised restriction of a K-plane fine field
+// (zero on coarse Dirichlet rows when zero_dirichlet)
+void launch_amr_restrict(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
+                         const double* ffield, double* cfield, int K, int zero_dirichlet, cudaStream_t s);
+// partials of sum res^2 over valid nodes not covered by the next level (cov may be null)
+int launch_amr_norm(const Lv<double>& L, const AmrBox& b, const AmrBox* cov, const double* res, double* partials,
+                    cudaStream_t s);
+// u += cor on every node that is not a ghost
+void launch_amr_add(const Lv<double>& L, const AmrBox& b, double* u, const double* cor, cudaStream_t s);
+
 }  // namespace elas

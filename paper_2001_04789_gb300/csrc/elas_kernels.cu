@@ -889,6 +889,163 @@ __global__ void k_remove_null(Lv<double> L, NullInfo nf, const double* __restric
         if (row_type(L, ni, i) != ROW_DIRICHLET) u[i * L.N + p] -= null_combo(nf, coef, i, c);
 }
 
+
+// ---------------------------------------------------------------------------
+// block-structured AMR transfers (reflux-free coarse/fine treatment)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool amr_is_ghost(const AmrBox& b, const int n[3], const int c[3]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (b.ghost[2 * d] && c[d] == 0) return true;
+        if (b.ghost[2 * d + 1] && c[d] == n[d] - 1) return true;
+    }
+    return false;
+}
+
+__global__ void k_amr_interp(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc, const double* __restrict__ cf,
+                             double* __restrict__ ff, int mode) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Lf.N) return;
+    int c[3];
+    coords_of(p, Lf.n, c);
+    const bool ghost = amr_is_ghost(bf, Lf.n, c);
+    if ((mode == 0) != ghost) return;
+    int i0[3], i1[3];
+    double w1[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int g = bf.grid_lo[d] + c[d];
+        i0[d] = g / 2 - bc.grid_lo[d];
+        i1[d] = (g + 1) / 2 - bc.grid_lo[d];
+        w1[d] = (g & 1) ? 0.5 : 0.0;
+    }
+    const NodeInfo ni = node_info(Lf, c[0], c[1], c[2]);
+    for (int k = 0; k < 3; ++k) {
+        if (mode == 1 && row_type(Lf, ni, k) == ROW_DIRICHLET) continue;
+        const double* e = cf + (size_t)k * Lc.N;
+        double v = 0.0;
+        for (int bz = 0; bz < 2; ++bz) {
+            const double wz = bz ? w1[2] : 1.0 - w1[2];
+            if (wz == 0.0) continue;
+            for (int by = 0; by < 2; ++by) {
+                const double wy = by ? w1[1] : 1.0 - w1[1];
+                if (wy == 0.0) continue;
+                for (int bx = 0; bx < 2; ++bx) {
+                    const double wx = bx ? w1[0] : 1.0 - w1[0];
+                    if (wx == 0.0) continue;
+                    v += wx * wy * wz *
+                         e[lin(Lc, bx ? i1[0] : i0[0], by ? i1[1] : i0[1], bz ? i1[2] : i0[2])];
+                }
+            }
+        }
+        if (mode == 0) ff[(size_t)k * Lf.N + p] = v;
+        else ff[(size_t)k * Lf.N + p] += v;
+    }
+}
+
+// covered coarse box (in coarse local coordinates): coarse global I with 2I in [valid_lo, valid_hi]
+__device__ __forceinline__ void amr_cov_box(const AmrBox& bf, const AmrBox& bc, int lo[3], int cnt[3]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int a = (bf.valid_lo[d] + 1) / 2, b = bf.valid_hi[d] / 2;
+        lo[d] = a - bc.grid_lo[d];
+        cnt[d] = b - a + 1;
+    }
+}
+
+__global__ void k_amr_inject(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc, const double* __restrict__ ffield,
+                             double* __restrict__ cfield) {
+    int lo[3], cnt[3];
+    amr_cov_box(bf, bc, lo, cnt);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt[0] * cnt[1] * cnt[2]) return;
+    const int cc[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
+    int fc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) fc[d] = 2 * (bc.grid_lo[d] + cc[d]) - bf.grid_lo[d];
+    const int pc = lin(Lc, cc[0], cc[1], cc[2]), pf = lin(Lf, fc[0], fc[1], fc[2]);
+    for (int k = 0; k < 3; ++k) cfield[(size_t)k * Lc.N + pc] = ffield[(size_t)k * Lf.N + pf];
+}
+
+__global__ void k_amr_restrict(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc, const double* __restrict__ ffield,
+                               double* __restrict__ cfield, int K, int zero_dirichlet) {
+    int lo[3], cnt[3];
+    amr_cov_box(bf, bc, lo, cnt);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt[0] * cnt[1] * cnt[2]) return;
+    const int cc[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
+    double w[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int fcg = 2 * (bc.grid_lo[d] + cc[d]);
+        double ww[3];
+        if (fcg == 0) { ww[0] = 0.0; ww[1] = 0.5; ww[2] = 0.5; }
+        else if (fcg == bf.count[d] - 1) { ww[0] = 0.5; ww[1] = 0.5; ww[2] = 0.0; }
+        else { ww[0] = 0.25; ww[1] = 0.5; ww[2] = 0.25; }
+        double sum = 0.0;
+        for (int o = -1; o <= 1; ++o) {
+            const int g = fcg + o;
+            if (g < bf.valid_lo[d] || g > bf.valid_hi[d]) ww[o + 1] = 0.0;
+            sum += ww[o + 1];
+        }
+        for (int o = 0; o < 3; ++o) w[d][o] = ww[o] / sum;
+    }
+    const NodeInfo nic = node_info(Lc, cc[0], cc[1], cc[2]);
+    const int pc = lin(Lc, cc[0], cc[1], cc[2]);
+    for (int k = 0; k < K; ++k) {
+        double acc = 0.0;
+        for (int oz = -1; oz <= 1; ++oz) {
+            if (w[2][oz + 1] == 0.0) continue;
+            for (int oy = -1; oy <= 1; ++oy) {
+                if (w[1][oy + 1] == 0.0) continue;
+                for (int ox = -1; ox <= 1; ++ox) {
+                    if (w[0][ox + 1] == 0.0) continue;
+                    const int fx = 2 * (bc.grid_lo[0] + cc[0]) + ox - bf.grid_lo[0];
+                    const int fy = 2 * (bc.grid_lo[1] + cc[1]) + oy - bf.grid_lo[1];
+                    const int fz = 2 * (bc.grid_lo[2] + cc[2]) + oz - bf.grid_lo[2];
+                    acc += w[0][ox + 1] * w[1][oy + 1] * w[2][oz + 1] * ffield[(size_t)k * Lf.N + lin(Lf, fx, fy, fz)];
+                }
+            }
+        }
+        if (zero_dirichlet && k < 3 && row_type(Lc, nic, k) == ROW_DIRICHLET) acc = 0.0;
+        cfield[(size_t)k * Lc.N + pc] = acc;
+    }
+}
+
+__global__ void k_amr_norm(Lv<double> L, AmrBox b, AmrBox cov, int has_cov, const double* __restrict__ res,
+                           double* __restrict__ partials) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (p < L.N) {
+        int c[3];
+        coords_of(p, L.n, c);
+        bool skip = amr_is_ghost(b, L.n, c);
+        if (!skip && has_cov) {
+            bool in = true;
+            for (int d = 0; d < 3; ++d) {
+                const int g2 = 2 * (b.grid_lo[d] + c[d]);
+                in &= (g2 >= cov.valid_lo[d] && g2 <= cov.valid_hi[d]);
+            }
+            skip = in;
+        }
+        if (!skip)
+            for (int k = 0; k < 3; ++k) {
+                const double r = res[(size_t)k * L.N + p];
+                acc[0] += r * r;
+            }
+    }
+    block_reduce_store<7>(acc, 1, partials);
+}
+
+__global__ void k_amr_add(Lv<double> L, AmrBox b, double* __restrict__ u, const double* __restrict__ cor) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
+    int c[3];
+    coords_of(p, L.n, c);
+    if (amr_is_ghost(b, L.n, c)) return;
+    for (int k = 0; k < 3; ++k) u[(size_t)k * L.N + p] += cor[(size_t)k * L.N + p];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1119,6 +1276,45 @@ void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* G
                         cudaStream_t s) {
     count_launch();
     k_remove_null<<<blocks_for(L.N), kBlock, 0, s>>>(L, nf, Ginv, wtu, u);
+}
+
+void launch_amr_interp(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
+                       const double* cfield, double* ffield, int mode, cudaStream_t s) {
+    count_launch();
+    k_amr_interp<<<blocks_for(Lf.N), kBlock, 0, s>>>(Lf, bf, Lc, bc, cfield, ffield, mode);
+}
+
+static size_t amr_cov_count(const AmrBox& bf) {
+    size_t n = 1;
+    for (int d = 0; d < 3; ++d) n *= (size_t)(bf.valid_hi[d] / 2 - (bf.valid_lo[d] + 1) / 2 + 1);
+    return n;
+}
+
+void launch_amr_inject(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
+                       const double* ffield, double* cfield, cudaStream_t s) {
+    count_launch();
+    k_amr_inject<<<blocks_for(amr_cov_count(bf)), kBlock, 0, s>>>(Lf, bf, Lc, bc, ffield, cfield);
+}
+
+void launch_amr_restrict(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
+                         const double* ffield, double* cfield, int K, int zero_dirichlet, cudaStream_t s) {
+    count_launch();
+    k_amr_restrict<<<blocks_for(amr_cov_count(bf)), kBlock, 0, s>>>(Lf, bf, Lc, bc, ffield, cfield, K, zero_dirichlet);
+}
+
+int launch_amr_norm(const Lv<double>& L, const AmrBox& b, const AmrBox* cov, const double* res, double* partials,
+                    cudaStream_t s) {
+    const int nb = blocks_for(L.N);
+    AmrBox cv{};
+    if (cov) cv = *cov;
+    count_launch();
+    k_amr_norm<<<nb, kBlock, 0, s>>>(L, b, cv, cov ? 1 : 0, res, partials);
+    return nb;
+}
+
+void launch_amr_add(const Lv<double>& L, const AmrBox& b, double* u, const double* cor, cudaStream_t s) {
+    count_launch();
+    k_amr_add<<<blocks_for(L.N), kBlock, 0, s>>>(L, b, u, cor);
 }
 
 // explicit instantiations

@@ -34,7 +34,13 @@ class ElasError(RuntimeError):
 
 class GridDesc(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("periodic", C.c_int * 3), ("lo", C.c_double * 3),
-                ("hi", C.c_double * 3), ("moduli_kind", C.c_int), ("mixed", C.c_int)]
+                ("hi", C.c_double * 3), ("moduli_kind", C.c_int), ("mixed", C.c_int),
+                ("max_levels", C.c_int)]
+
+
+class AmrLevelDesc(C.Structure):
+    _fields_ = [("grid_lo", C.c_int * 3), ("valid_lo", C.c_int * 3), ("valid_hi", C.c_int * 3),
+                ("ghost", C.c_int * 6)]
 
 
 class SolveOpts(C.Structure):
@@ -106,6 +112,9 @@ def lib():
         "elas_op_bottom": (ip, [vp, ip, vp, vp]),
         "elas_batch_solve": (ip, [C.POINTER(vp), ip, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "elas_profile_enable": (ip, [vp, ip]),
+        "elas_amr_create": (ip, [C.POINTER(vp), C.POINTER(AmrLevelDesc), ip, C.POINTER(vp)]),
+        "elas_amr_destroy": (ip, [vp]),
+        "elas_amr_solve": (ip, [vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "elas_profile_read": (ip, [vp, ip, dp, C.POINTER(C.c_longlong)]),
         "elas_launch_count": (C.c_ulonglong, []),
     }
@@ -196,8 +205,9 @@ class Context:
             self.h = None
 
 
-def desc_for(problem: M.Problem, mixed=False):
+def desc_for(problem: M.Problem, mixed=False, max_levels=0):
     d = GridDesc()
+    d.max_levels = int(max_levels)
     for k in range(3):
         d.n[k] = int(problem.n[k])
         d.periodic[k] = int(bool(problem.periodic[k]))
@@ -357,9 +367,9 @@ class Grid:
             self.h = None
 
 
-def grid_from_problem(ctx: Context, p: M.Problem, mixed=False) -> Grid:
+def grid_from_problem(ctx: Context, p: M.Problem, mixed=False, max_levels=0) -> Grid:
     """Create a grid and load a Problem's moduli, loads and boundary conditions."""
-    g = Grid(ctx, desc_for(p, mixed))
+    g = Grid(ctx, desc_for(p, mixed, max_levels))
     g.set_moduli(p.moduli)
     if p.eigenstrain is not None:
         g.set_eigenstrain(p.eigenstrain)
@@ -392,3 +402,54 @@ def grid_from_problem(ctx: Context, p: M.Problem, mixed=False) -> Grid:
     for f, arr in faces.items():
         g.set_face_values(f, arr)
     return g
+
+
+def _opts(precision=FP64, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False, fixed_cycles=0,
+          use_graph=False):
+    o = SolveOpts()
+    lib().elas_solve_opts_default(C.byref(o))
+    o.precision, o.rel_tol, o.max_cycles = precision, rel_tol, max_cycles
+    o.nu1, o.nu2, o.warm_start, o.fixed_cycles = nu1, nu2, int(warm_start), fixed_cycles
+    o.use_graph = int(use_graph)
+    return o
+
+
+class Amr:
+    """Composite (reflux-free) AMR solve over the levels of an AMR layout
+    (``microstructure.AmrLevel`` list): one grid per level, level 0 with its
+    multigrid hierarchy, finer levels smoothed only."""
+
+    def __init__(self, ctx: Context, specs):
+        self.ctx = ctx
+        self.specs = specs
+        self.grids = [grid_from_problem(ctx, sp.problem, max_levels=0 if sp.level == 0 else 1) for sp in specs]
+        descs = (AmrLevelDesc * len(specs))()
+        for i, sp in enumerate(specs):
+            for d in range(3):
+                descs[i].grid_lo[d] = sp.grid_lo[d]
+                descs[i].valid_lo[d] = sp.valid_lo[d]
+                descs[i].valid_hi[d] = sp.valid_hi[d]
+            for f in range(6):
+                descs[i].ghost[f] = int(sp.ghost[f])
+        arr = (C.c_void_p * len(specs))(*[g.h for g in self.grids])
+        h = C.c_void_p()
+        ctx.check(lib().elas_amr_create(arr, descs, len(specs), C.byref(h)))
+        self.h = h
+
+    def solve(self, rel_tol=1e-8, max_cycles=200, nu1=2, nu2=2, fixed_cycles=0, raise_on_error=True):
+        info = SolveInfo()
+        rc = lib().elas_amr_solve(self.h, C.byref(_opts(FP64, rel_tol, max_cycles, nu1, nu2, False, fixed_cycles)),
+                                  C.byref(info))
+        if rc != OK and raise_on_error and rc != ERR_NOT_CONVERGED:
+            raise ElasError(rc, self.ctx.error())
+        return info.as_dict()
+
+    def displacements(self):
+        return [g.displacement() for g in self.grids]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().elas_amr_destroy(self.h)
+            self.h = None
+        for g in self.grids:
+            g.close()

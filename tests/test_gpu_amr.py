@@ -1,0 +1,97 @@
+"""Composite (reflux-free) AMR solve through the C ABI against the oracle's
+composite cycle: same layout, same cycles, every level element by element
+(FP64, 1e-9 relative), and exactness on an affine field."""
+import numpy as np
+import pytest
+
+from paper_2001_04789_gb300 import microstructure as M
+from oracle import amr as A
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def E():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2001_04789_gb300 import build as B
+    B.build()
+    from paper_2001_04789_gb300 import elas
+    return elas
+
+
+@pytest.fixture(scope="module")
+def ctx(E):
+    c = E.Context(0)
+    yield c
+    c.close()
+
+
+def layouts():
+    return {
+        "crack2": lambda: M.amr_penny_crack(base_n=17, nlevels=2, block=8, width=3.0 / 32),
+        "crack3": lambda: M.amr_penny_crack(base_n=17, nlevels=3, block=8, width=3.0 / 64),
+    }
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name", list(layouts()))
+def test_amr_fixed_cycles_match_oracle(E, ctx, name):
+    specs = layouts()[name]()
+    amr = E.Amr(ctx, specs)
+    info = amr.solve(fixed_cycles=3)
+    got = amr.displacements()
+    ref, rinfo = A.solve(specs, fixed_cycles=3)
+    for l, (g, r) in enumerate(zip(got, ref)):
+        valid = np.ones(g.shape[1:], bool)
+        sp = specs[l]
+        sl = (slice(None),) + tuple(slice(sp.valid_lo[d] - sp.grid_lo[d], sp.valid_hi[d] - sp.grid_lo[d] + 1)
+                                    for d in (2, 1, 0))
+        assert rel_err(g[sl], r[sl]) < 1e-9, (name, l)
+    assert np.allclose(info["rel_history"], rinfo["rel_history"], rtol=1e-7)
+    amr.close()
+
+
+def test_amr_converged_solve_matches_oracle(E, ctx):
+    specs = layouts()["crack2"]()
+    amr = E.Amr(ctx, specs)
+    info = amr.solve(rel_tol=1e-8)
+    ref, rinfo = A.solve(specs, tol=1e-8)
+    assert info["status"] == 0 and info["cycles"] == rinfo["cycles"]
+    for g, r in zip(amr.displacements(), ref):
+        assert rel_err(g, r) < 1e-9
+    amr.close()
+
+
+def test_amr_affine_field_is_exact(E, ctx):
+    G = np.array([[1.0, 0.3, -0.2], [0.1, -0.5, 0.4], [0.2, 0.0, 0.7]]) * 1e-3
+
+    def mk(n3, lo3, hi3):
+        p = M.Problem(n=tuple(n3), lo=tuple(lo3), hi=tuple(hi3))
+        X, Y, Z = p.coords()
+        lam, mu = M.lame(np.ones(X.shape), 0.3)
+        p.moduli_kind = M.MODULI_ISO
+        p.moduli = np.stack([lam, mu])
+        x = [X, Y, Z]
+        ue = np.stack([sum(G[k, l] * x[l] for l in range(3)) for k in range(3)])
+        p.bc = M.all_faces(M.DIRICHLET, 0.0)
+        p.face_values = {f: ue for f in range(6)}
+        return p
+
+    ind = lambda X, Y, Z: np.exp(-((X - 0.4) ** 2 + (Y - 0.6) ** 2 + (Z - 0.5) ** 2) / 0.02)
+    specs = M.amr_layout(mk, 17, 3, ind, thresh=0.15, block=8)
+    amr = E.Amr(ctx, specs)
+    info = amr.solve(rel_tol=1e-12, max_cycles=80)
+    assert info["status"] == 0
+    for sp, ul in zip(specs, amr.displacements()):
+        X, Y, Z = sp.problem.coords()
+        x = [X, Y, Z]
+        ue = np.stack([sum(G[k, l] * x[l] for l in range(3)) for k in range(3)])
+        sl = (slice(None),) + tuple(slice(sp.valid_lo[d] - sp.grid_lo[d], sp.valid_hi[d] - sp.grid_lo[d] + 1)
+                                    for d in (2, 1, 0))
+        assert np.abs(ul[sl] - ue[sl]).max() < 1e-11
+    amr.close()
