@@ -32,6 +32,8 @@ struct elas_ctx_s {
     std::vector<std::pair<int, size_t>> pending;   // (class, index of start event)
     double prof_ms[ELAS_PROF_CLASSES] = {0, 0, 0, 0};
     long long prof_count[ELAS_PROF_CLASSES] = {0, 0, 0, 0};
+    std::vector<cudaStream_t> branch;        // streams of the batched graph's branches
+    std::vector<cudaEvent_t> branch_ev;
 };
 
 namespace {
@@ -183,6 +185,7 @@ void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int 
     L.bnodes = nullptr;
     L.nbnd = 0;
     L.divc = nullptr;
+    L.active = nullptr;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -679,6 +682,8 @@ int elas_ctx_destroy(elas_ctx c) {
     if (!c) return ELAS_ERR_INVALID_ARG;
     cudaStreamSynchronize(c->stream);
     for (auto e : c->pool) cudaEventDestroy(e);
+    for (auto st : c->branch) cudaStreamDestroy(st);
+    for (auto e : c->branch_ev) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     if (c->host_status) cudaFreeHost(c->host_status);
     delete c;
@@ -1138,11 +1143,157 @@ unsigned long long elas_launch_count(void) { return elas::launch_count(); }
 
 int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_info* info) {
     if (!grids || n < 0 || !opts || !info) return ELAS_ERR_INVALID_ARG;
+    if (n == 0) return ELAS_OK;
+    elas_ctx c = grids[0]->ctx;
+    bool batched = opts->precision == ELAS_PRECISION_MIXED && n > 1;
+    for (int i = 0; i < n; ++i) {
+        if (!grids[i]) return ELAS_ERR_INVALID_ARG;
+        if (grids[i]->ctx != c || !grids[i]->desc.mixed || grids[i]->desc.max_levels == 1) batched = false;
+    }
+    if (!batched) {
+        int worst = ELAS_OK;
+        for (int i = 0; i < n; ++i) {
+            const int rc = elas_solve(grids[i], opts, &info[i]);
+            if (rc != ELAS_OK && worst == ELAS_OK) worst = rc;
+        }
+        return worst;
+    }
+    cudaSetDevice(c->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < n; ++i) {
+        std::memset(&info[i], 0, sizeof(info[i]));
+        const int rc = setup(grids[i]);
+        if (rc) return rc;
+    }
+    cudaStream_t main = c->stream;
+    // per-member flags, counters and histories
+    const size_t hist_len = ELAS_HISTORY;
+    const size_t bytes = n * (2 * sizeof(int)) + 256 + n * hist_len * sizeof(double);
+    void* mem = ctx_alloc(c, bytes);
+    if (!mem) return set_err(c, ELAS_ERR_ALLOC, "batch work arrays: allocation failed");
+    int* flags = (int*)mem;
+    int* counts = flags + n;
+    double* hist = (double*)((char*)mem + (((size_t)2 * n * sizeof(int) + 255) & ~size_t(255)));
+    std::vector<int> h_flags(n, 1), h_counts(n, 0);
+    CUDA_TRY(c, cudaMemcpyAsync(flags, h_flags.data(), sizeof(int) * n, cudaMemcpyHostToDevice, main));
+    CUDA_TRY(c, cudaMemcpyAsync(counts, h_counts.data(), sizeof(int) * n, cudaMemcpyHostToDevice, main));
+    for (int i = 0; i < n; ++i) {
+        elas_grid g = grids[i];
+        Level& L0 = g->lv[0];
+        launch_dirichlet(L0.L64, boundary_data(g), L0.u, opts->warm_start ? 1 : 0, main);
+        cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, main);
+        cudaMemsetAsync(g->alam, 0, sizeof(double) * kLoadDoubles, main);
+        cudaMemsetAsync(g->adlam, 0, sizeof(double) * kLoadDoubles, main);
+        for (auto& v : g->lv) {
+            v.L64.active = flags + i;
+            v.L32.active = flags + i;
+        }
+    }
+    CHECK_LAUNCH(c);
+    CUDA_TRY(c, cudaStreamSynchronize(main));
+    // branches of the graph
+    const int S = n < 32 ? n : 32;
+    while ((int)c->branch.size() < S) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        c->branch.push_back(st);
+        c->branch_ev.push_back(ev);
+    }
+    cudaEvent_t fork;
+    CUDA_TRY(c, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    const bool prof = c->profile;
+    c->profile = false;
+    const int nu1 = opts->nu1 < 0 ? 0 : opts->nu1, nu2 = opts->nu2 < 0 ? 0 : opts->nu2;
+    const int K = 2;   // refinement steps per graph replay
+    const unsigned long long launches0 = launch_count();
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(c, cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(fork, main);
+    for (int b = 0; b < S; ++b) cudaStreamWaitEvent(c->branch[b], fork, 0);
+    for (int it = 0; it < K; ++it) {
+        for (int i = 0; i < n; ++i) {
+            elas_grid g = grids[i];
+            Level& L0 = g->lv[0];
+            c->stream = c->branch[i % S];
+            const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
+            int nb = 0;
+            launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, nf0 ? g->alam : nullptr, L0.f32, g->partials, &nb,
+                                           c->stream);
+            BatchFlags bfl{flags + i, counts + i, hist + (size_t)i * hist_len, (int)hist_len, g->r0, opts->rel_tol,
+                           opts->fixed_cycles > 0 ? opts->fixed_cycles : opts->max_cycles};
+            launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1,
+                            c->stream, bfl);
+            vcycle<float>(g, 0, nu1, nu2, nf0, nf0 ? g->adlam : nullptr);
+            launch_add_correction(L0.L64, L0.u, L0.u32, c->stream);
+        }
+    }
+    for (int b = 0; b < S; ++b) {
+        cudaEventRecord(c->branch_ev[b], c->branch[b]);
+        cudaStreamWaitEvent(main, c->branch_ev[b], 0);
+    }
+    c->stream = main;
+    cudaError_t ce = cudaStreamEndCapture(main, &graph);
+    c->profile = prof;
+    const unsigned long long per_replay = launch_count() - launches0;
+    count_launch(-(int)per_replay);   // captured, not launched: counted per replay below
+    cudaGraphExec_t exec = nullptr;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    int rc = ELAS_OK;
+    if (ce != cudaSuccess) {
+        rc = set_err(c, ELAS_ERR_DEVICE, std::string("batched graph: ") + cudaGetErrorString(ce));
+    } else {
+        const int max_replays = (opts->fixed_cycles > 0 ? opts->fixed_cycles : opts->max_cycles) / K + 2;
+        for (int r = 0; r < max_replays; ++r) {
+            ce = cudaGraphLaunch(exec, main);
+            if (ce != cudaSuccess) break;
+            count_launch((int)per_replay);
+            cudaMemcpyAsync(h_flags.data(), flags, sizeof(int) * n, cudaMemcpyDeviceToHost, main);
+            ce = cudaStreamSynchronize(main);
+            if (ce != cudaSuccess) break;
+            bool any = false;
+            for (int i = 0; i < n; ++i) any |= h_flags[i] != 0;
+            if (!any) break;
+        }
+        if (ce != cudaSuccess) rc = set_err(c, ELAS_ERR_DEVICE, std::string("batched replay: ") + cudaGetErrorString(ce));
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaEventDestroy(fork);
+    for (int i = 0; i < n; ++i)
+        for (auto& v : grids[i]->lv) {
+            v.L64.active = nullptr;
+            v.L32.active = nullptr;
+        }
+    if (rc) {
+        ctx_free(c, mem, bytes);
+        return rc;
+    }
+    std::vector<double> h_hist((size_t)n * hist_len);
+    CUDA_TRY(c, cudaMemcpyAsync(h_counts.data(), counts, sizeof(int) * n, cudaMemcpyDeviceToHost, main));
+    CUDA_TRY(c, cudaMemcpyAsync(h_hist.data(), hist, sizeof(double) * n * hist_len, cudaMemcpyDeviceToHost, main));
     int worst = ELAS_OK;
     for (int i = 0; i < n; ++i) {
-        const int rc = elas_solve(grids[i], opts, &info[i]);
-        if (rc != ELAS_OK && worst == ELAS_OK) worst = rc;
+        const int rr = remove_rigid(grids[i]);
+        if (rr) return rr;
     }
+    CUDA_TRY(c, cudaStreamSynchronize(main));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < n; ++i) {
+        const int cnt = h_counts[i] < (int)hist_len ? h_counts[i] : (int)hist_len;
+        for (int k = 0; k < cnt; ++k) info[i].rel_history[k] = h_hist[(size_t)i * hist_len + k];
+        info[i].cycles = h_counts[i] > 0 ? h_counts[i] - 1 : 0;
+        info[i].rel_residual = cnt > 0 ? h_hist[(size_t)i * hist_len + cnt - 1] : 0.0;
+        info[i].r0 = grids[i]->r0;
+        info[i].nlam = grids[i]->lv[0].nf.m;
+        info[i].seconds = secs;
+        const bool ok = opts->fixed_cycles > 0 ? true : info[i].rel_residual <= opts->rel_tol;
+        info[i].status = ok ? ELAS_OK : ELAS_ERR_NOT_CONVERGED;
+        if (!ok && worst == ELAS_OK) worst = ELAS_ERR_NOT_CONVERGED;
+    }
+    ctx_free(c, mem, bytes);
+    if (worst) set_err(c, worst, "a batch member did not reach the tolerance");
     return worst;
 }
 

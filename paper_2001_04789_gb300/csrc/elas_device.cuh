@@ -36,6 +36,8 @@ struct Lv {
     // optional: M_iV = sum_j d_j C_(ij)V (18 planes, interior nodes), precomputed so the
     // modulus-gradient term costs 18 FMAs instead of 54 differences
     const T* __restrict__ divc;
+    // optional per-grid flag of a batched solve: kernels of a converged member return at once
+    const int* __restrict__ active;
 };
 
 // ---- Voigt helpers ----------------------------------------------------------

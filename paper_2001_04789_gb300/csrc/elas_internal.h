@@ -77,9 +77,18 @@ void launch_bottom_solve(const Lv<T>& L, const int* dofs, int nfree, int ntot, c
 // Deterministic final reduction of residual partials; when nf.m > 0 also the
 // equilibrating-load update dlam = G^-1 W^T r, lam += dlam (if update_lam),
 // and the norm of r - dlam.W.  out[0] = sum r^2 (corrected).
+// Per-member convergence control of a batched solve (all null = not batched).
+struct BatchFlags {
+    int* active;        // 1 while the member still iterates
+    int* count;         // residual evaluations so far
+    double* hist;       // relative residual history
+    int hist_len;
+    double r0, tol;
+    int max_cycles;
+};
 void launch_finalize(const double* partials, int nblocks, const NullInfo& nf, const double* Ginv,
                      const double* G, double* lam, double* dlam, double* alam, double* adlam, double* out,
-                     int update_lam, cudaStream_t s);
+                     int update_lam, cudaStream_t s, BatchFlags bflags = BatchFlags{});
 
 // W^T u partials (and W^T W at setup when gram != 0).
 void launch_null_dots(const Lv<double>& L, const NullInfo& nf, const double* u, double* partials,

@@ -250,6 +250,7 @@ template <typename T, typename TR, int KIND, bool NORM, bool HM>
 __global__ void __launch_bounds__(kBlock) k_residual_int(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                                         NullInfo nf, const double* __restrict__ lam,
                                                         TR* __restrict__ r, double* __restrict__ partials) {
+    if (L.active && *L.active == 0) return;
     int lo[3], cnt[3];
     interior_box(L, lo, cnt);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,6 +269,7 @@ template <typename T, typename TR, int KIND, bool NORM>
 __global__ void __launch_bounds__(kBlock) k_residual_bnd(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                                         NullInfo nf, const double* __restrict__ lam,
                                                         TR* __restrict__ r, double* __restrict__ partials) {
+    if (L.active && *L.active == 0) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     if (t < L.nbnd) {
@@ -290,6 +292,7 @@ template <typename T, int KIND, bool HM>
 __global__ void __launch_bounds__(kBlock) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
                                                           const T* __restrict__ f, int colour, NullInfo nf,
                                                           const double* __restrict__ lam) {
+    if (L.active && *L.active == 0) return;
     int lo[3], cnt[3];
     interior_box(L, lo, cnt);
     const int npair = (cnt[0] + 1) >> 1;
@@ -330,6 +333,7 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
                                                           const T* __restrict__ f, int colour, NullInfo nf,
                                                           const double* __restrict__ lam) {
+    if (L.active && *L.active == 0) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L.nbnd) return;
     const int p = L.bnodes[t];
@@ -417,6 +421,7 @@ template <typename T, typename TR, int KIND, int A, bool NORM>
 __global__ void __launch_bounds__(kBlock) k_residual_face(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                                          NullInfo nf, const double* __restrict__ load,
                                                          TR* __restrict__ r, double* __restrict__ partials) {
+    if (L.active && *L.active == 0) return;
     int c[3], side;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     if (face_coords<T, A>(L, blockIdx.x * blockDim.x + threadIdx.x, c, side)) {
@@ -433,6 +438,7 @@ template <typename T, int KIND, int A>
 __global__ void __launch_bounds__(kBlock) k_half_sweep_face(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
                                                            const T* __restrict__ f, int colour, NullInfo nf,
                                                            const double* __restrict__ load) {
+    if (L.active && *L.active == 0) return;
     int c[3], side;
     if (!face_coords<T, A>(L, blockIdx.x * blockDim.x + threadIdx.x, c, side)) return;
     const int N = L.N;
@@ -482,6 +488,7 @@ __device__ __forceinline__ void restrict_weights(const Lv<T>& Lc, int d, int I, 
 template <typename T>
 __global__ void k_restrict(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ r, T* __restrict__ fc, NullInfo nf,
                            const double* __restrict__ dlam) {
+    if (Lf.active && *Lf.active == 0) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= Lc.N) return;
     int C[3];
@@ -521,6 +528,7 @@ __global__ void k_restrict(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ r, T* __res
 
 template <typename T>
 __global__ void k_prolong_add(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ ec, T* __restrict__ u) {
+    if (Lf.active && *Lf.active == 0) return;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= Lf.N) return;
     int c[3];
@@ -625,6 +633,7 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
 
 template <typename TE>
 __global__ void k_add_correction(Lv<double> L, double* __restrict__ u, const TE* __restrict__ e) {
+    if (L.active && *L.active == 0) return;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= L.N) return;
     int c[3];
@@ -724,6 +733,7 @@ __global__ void k_invert(double* __restrict__ A, double* __restrict__ X, int n, 
 template <typename T>
 __global__ void k_bottom_gather(Lv<T> L, const int* __restrict__ dofs, int nfree, int ntot, const T* __restrict__ f,
                                 double* __restrict__ b) {
+    if (L.active && *L.active == 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ntot) return;
     b[i] = i < nfree ? (double)f[dofs[i]] : 0.0;
@@ -732,6 +742,7 @@ __global__ void k_bottom_gather(Lv<T> L, const int* __restrict__ dofs, int nfree
 template <typename T>
 __global__ void k_bottom_matvec(Lv<T> L, const int* __restrict__ dofs, int nfree, int ntot,
                                 const double* __restrict__ Ainv, const double* __restrict__ b, T* __restrict__ u) {
+    if (L.active && *L.active == 0) return;
     const int row = blockIdx.x;
     if (row >= nfree) return;
     double acc = 0.0;
@@ -764,7 +775,8 @@ __global__ void k_zero(T* __restrict__ a, size_t n) {
 __global__ void k_finalize(const double* __restrict__ partials, int nblocks, NullInfo nf,
                            const double* __restrict__ Ginv, const double* __restrict__ G,
                            double* __restrict__ lam, double* __restrict__ dlam, double* __restrict__ alam,
-                           double* __restrict__ adlam, double* __restrict__ out, int update_lam) {
+                           double* __restrict__ adlam, double* __restrict__ out, int update_lam, BatchFlags bf) {
+    if (bf.active && *bf.active == 0) return;
     __shared__ double sm[kBlock][7];
     const int width = nf.m > 0 ? 7 : 1;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -815,6 +827,14 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, Nul
             }
         }
         out[0] = ss;
+        if (bf.active) {
+            // batched solve: record the relative residual, stop this member when done
+            const double rel = bf.r0 > 0.0 ? sqrt(ss) / bf.r0 : 0.0;
+            const int k = *bf.count;
+            if (k < bf.hist_len) bf.hist[k] = rel;
+            *bf.count = k + 1;
+            if (!(rel > bf.tol) || k >= bf.max_cycles || !isfinite(rel)) *bf.active = 0;
+        }
     }
 }
 
@@ -1248,9 +1268,9 @@ void launch_bottom_solve(const Lv<T>& L, const int* dofs, int nfree, int ntot, c
 
 void launch_finalize(const double* partials, int nblocks, const NullInfo& nf, const double* Ginv, const double* G,
                      double* lam, double* dlam, double* alam, double* adlam, double* out, int update_lam,
-                     cudaStream_t s) {
+                     cudaStream_t s, BatchFlags bflags) {
     count_launch();
-    k_finalize<<<1, kBlock, 0, s>>>(partials, nblocks, nf, Ginv, G, lam, dlam, alam, adlam, out, update_lam);
+    k_finalize<<<1, kBlock, 0, s>>>(partials, nblocks, nf, Ginv, G, lam, dlam, alam, adlam, out, update_lam, bflags);
 }
 
 void launch_null_dots(const Lv<double>& L, const NullInfo& nf, const double* u, double* partials, int* nblocks,
