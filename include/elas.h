@@ -250,6 +250,26 @@ int  elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* in
 int  elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts,
                       elas_solve_info* info);
 
+/* ---- serving: continuous batching at refinement-step granularity -----------------
+ * A server owns no grids: the caller keeps hierarchies resident and submits solves
+ * of them (typically warm-started).  elas_server_step admits waiting requests into
+ * free slots (at most max_active), advances every active request by one
+ * refinement step (FP64 residual, FP32 V-cycle, FP64 update; mixed precision,
+ * grids created with mixed = 1), all members' kernels interleaved on parallel
+ * streams, and retires the ones that reached their tolerance.  A grid must not be
+ * submitted again before its request has been polled as done.  Results are the
+ * same as a lone elas_solve with the same options (same kernels in the same
+ * order per grid). */
+typedef struct elas_server_s* elas_server;
+int  elas_server_create(elas_ctx ctx, int max_active, elas_server* out);
+int  elas_server_destroy(elas_server s);
+int  elas_server_submit(elas_server s, elas_grid g, const elas_solve_opts* opts, long long* ticket);
+/* One step; *active and *waiting receive the counts after it. */
+int  elas_server_step(elas_server s, int* active, int* waiting);
+/* 1 when the request is done (info filled, latency from submit to retirement in
+ * seconds), 0 while pending, negative on error. */
+int  elas_server_poll(elas_server s, long long ticket, elas_solve_info* info, double* latency_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <deque>
+#include <map>
 #include <vector>
 
 #include "../../include/elas.h"
@@ -109,7 +111,8 @@ struct elas_grid_s {
     double *alam = nullptr, *adlam = nullptr;   // loads as rigid motions (t, w)
     double r0 = 0.0;
     bool moduli_set = false;
-    bool dirty = true;
+    bool dirty = true;         // moduli or boundary types changed: rebuild everything
+    bool rhs_dirty = true;     // only loads / boundary data changed: rebuild the right-hand side
     std::vector<std::pair<void*, size_t>> allocs;
 };
 
@@ -367,13 +370,46 @@ int read_status(elas_grid g, double* out, int count) {
     return ELAS_OK;
 }
 
+// Right-hand side of the finest level and ||r_0|| (loads and boundary data only).
+int setup_rhs(elas_grid g) {
+    elas_ctx c = g->ctx;
+    cudaStream_t s = c->stream;
+    Level& L0 = g->lv[0];
+    // right-hand side
+    RhsInputs in{};
+    in.eps0 = g->eps0;
+    in.body = g->body;
+    for (int k = 0; k < 6; ++k) in.mean_strain[k] = g->mean[k];
+    in.has_mean_strain = g->has_mean;
+    launch_rhs(g->lv[0].L64, in, boundary_data(g), g->lv[0].f, s);
+    CHECK_LAUNCH(c);
+    // ||r_0||: residual of the Dirichlet-only field
+    {
+        launch_dirichlet(L0.L64, boundary_data(g), L0.ua, 0, s);
+        CHECK_LAUNCH(c);
+        int nb = 0;
+        launch_residual<double, double>(L0.L64, L0.ua, L0.f, nullptr, nullptr, L0.r, g->partials, &nb, s);
+        CHECK_LAUNCH(c);
+        NullInfo none{};
+        launch_finalize(g->partials, nb, none, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, g->status, 0, s);
+        CHECK_LAUNCH(c);
+        double st[1];
+        int rc = read_status(g, st, 1);
+        if (rc) return rc;
+        g->r0 = std::sqrt(st[0]);
+    }
+    g->rhs_dirty = false;
+    return ELAS_OK;
+}
+
 // ---- setup: coarse moduli, FP32 copies, RHS, equilibrating-load data, bottom ----------
 int setup(elas_grid g) {
-    if (!g->dirty) return ELAS_OK;
+    if (!g->dirty && !g->rhs_dirty) return ELAS_OK;
     elas_ctx c = g->ctx;
     cudaStream_t s = c->stream;
     if (!g->moduli_set) return set_err(c, ELAS_ERR_STATE, "moduli not set");
     const int nl = (int)g->lv.size();
+    if (!g->dirty) return setup_rhs(g);
     for (int l = 1; l < nl; ++l) {
         launch_restrict_moduli<double>(g->lv[l - 1].L64, g->lv[l].L64, g->lv[l - 1].mod64, g->lv[l].mod64, s);
         CHECK_LAUNCH(c);
@@ -393,14 +429,6 @@ int setup(elas_grid g) {
             CHECK_LAUNCH(c);
         }
     }
-    // right-hand side
-    RhsInputs in{};
-    in.eps0 = g->eps0;
-    in.body = g->body;
-    for (int k = 0; k < 6; ++k) in.mean_strain[k] = g->mean[k];
-    in.has_mean_strain = g->has_mean;
-    launch_rhs(g->lv[0].L64, in, boundary_data(g), g->lv[0].f, s);
-    CHECK_LAUNCH(c);
     // equilibrating load of the finest level: G = W^T W, Ginv
     Level& L0 = g->lv[0];
     const int m = L0.nf.m;
@@ -435,22 +463,12 @@ int setup(elas_grid g) {
         CUDA_TRY(c, cudaStreamSynchronize(s));
         if (flag) return set_err(c, ELAS_ERR_STATE, "coarsest operator is singular");
     }
-    // ||r_0||: residual of the Dirichlet-only field
     {
-        launch_dirichlet(L0.L64, boundary_data(g), L0.ua, 0, s);
-        CHECK_LAUNCH(c);
-        int nb = 0;
-        launch_residual<double, double>(L0.L64, L0.ua, L0.f, nullptr, nullptr, L0.r, g->partials, &nb, s);
-        CHECK_LAUNCH(c);
-        NullInfo none{};
-        launch_finalize(g->partials, nb, none, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, g->status, 0, s);
-        CHECK_LAUNCH(c);
-        double st[1];
-        int rc = read_status(g, st, 1);
+        int rc = setup_rhs(g);
         if (rc) return rc;
-        g->r0 = std::sqrt(st[0]);
     }
     g->dirty = false;
+    g->rhs_dirty = false;
     return ELAS_OK;
 }
 
@@ -807,14 +825,14 @@ int elas_set_moduli(elas_grid g, const double* comps, int memspace) {
 static int set_field(elas_grid g, double** slot, const double* src, size_t count, int memspace) {
     if (!src) {
         *slot = nullptr;   // memory stays with the grid until destroyed
-        g->dirty = true;
+        g->rhs_dirty = true;
         return ELAS_OK;
     }
     if (!*slot) {
         int rc = galloc(g, slot, count);
         if (rc) return rc;
     }
-    g->dirty = true;
+    g->rhs_dirty = true;
     return copy_in(g->ctx, *slot, src, count, memspace);
 }
 
@@ -834,7 +852,7 @@ int elas_set_mean_strain(elas_grid g, const double eps6[6]) {
         return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "mean strain needs a fully periodic grid");
     for (int k = 0; k < 6; ++k) g->mean[k] = eps6[k];
     g->has_mean = 1;
-    g->dirty = true;
+    g->rhs_dirty = true;
     return ELAS_OK;
 }
 
@@ -845,7 +863,8 @@ int elas_set_bc(elas_grid g, int face, int comp, int type, double value) {
     const bool changed = g->bc_type[face][comp] != type;
     g->bc_type[face][comp] = type;
     g->bc_val[face][comp] = value;
-    g->dirty = true;
+    if (changed) g->dirty = true;
+    else g->rhs_dirty = true;
     if (changed) {
         refresh_lv(g);
         return rebuild_bottom_dofs(g);
@@ -857,7 +876,7 @@ int elas_set_face_values(elas_grid g, int face, const double* values, int memspa
     if (!g || face < 0 || face > 5) return ELAS_ERR_INVALID_ARG;
     if (!values) {
         g->face[face] = nullptr;
-        g->dirty = true;
+        g->rhs_dirty = true;
         return ELAS_OK;
     }
     double* slot = g->face[face];
@@ -1554,6 +1573,205 @@ int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* inf
     if (status == ELAS_ERR_NOT_CONVERGED) set_err(c, status, "maximum cycles reached above the tolerance");
     if (status == ELAS_ERR_DIVERGED) set_err(c, status, "residual diverged");
     return status;
+}
+
+}  // extern "C"
+
+// ======================================================================================
+// serving: continuous batching at refinement-step granularity
+// ======================================================================================
+namespace {
+struct ServerReq {
+    long long ticket;
+    elas_grid g;
+    elas_solve_opts opts;
+    int slot = -1;
+    std::chrono::steady_clock::time_point t_submit;
+};
+struct ServerDone {
+    elas_solve_info info;
+    double latency;
+};
+}  // namespace
+
+struct elas_server_s {
+    elas_ctx ctx;
+    int max_active;
+    long long next = 1;
+    std::deque<ServerReq> waiting;
+    std::vector<ServerReq> active;
+    std::vector<int> free_slots;
+    std::map<long long, ServerDone> done;
+    int* flags = nullptr;
+    int* counts = nullptr;
+    double* hist = nullptr;
+    void* mem = nullptr;
+    size_t bytes = 0;
+    std::vector<int> h_flags, h_counts;
+};
+
+extern "C" {
+
+int elas_server_create(elas_ctx c, int max_active, elas_server* out) {
+    if (!c || max_active < 1 || !out) return ELAS_ERR_INVALID_ARG;
+    elas_server s = new elas_server_s();
+    s->ctx = c;
+    s->max_active = max_active;
+    s->bytes = (size_t)max_active * 2 * sizeof(int) + 256 + (size_t)max_active * ELAS_HISTORY * sizeof(double);
+    s->mem = ctx_alloc(c, s->bytes);
+    if (!s->mem) {
+        delete s;
+        return set_err(c, ELAS_ERR_ALLOC, "server work arrays: allocation failed");
+    }
+    s->flags = (int*)s->mem;
+    s->counts = s->flags + max_active;
+    s->hist = (double*)((char*)s->mem + (((size_t)2 * max_active * sizeof(int) + 255) & ~size_t(255)));
+    for (int i = max_active - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->h_flags.assign(max_active, 0);
+    s->h_counts.assign(max_active, 0);
+    *out = s;
+    return ELAS_OK;
+}
+
+int elas_server_destroy(elas_server s) {
+    if (!s) return ELAS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(s->ctx->stream);
+    for (auto& r : s->active)
+        for (auto& v : r.g->lv) v.L64.active = v.L32.active = nullptr;
+    ctx_free(s->ctx, s->mem, s->bytes);
+    delete s;
+    return ELAS_OK;
+}
+
+int elas_server_submit(elas_server s, elas_grid g, const elas_solve_opts* opts, long long* ticket) {
+    if (!s || !g || !opts || !ticket) return ELAS_ERR_INVALID_ARG;
+    if (g->ctx != s->ctx || !g->desc.mixed || g->desc.max_levels == 1)
+        return set_err(s->ctx, ELAS_ERR_INVALID_ARG, "server requests need grids of its context with mixed = 1");
+    ServerReq r;
+    r.ticket = s->next++;
+    r.g = g;
+    r.opts = *opts;
+    r.t_submit = std::chrono::steady_clock::now();
+    s->waiting.push_back(r);
+    *ticket = r.ticket;
+    return ELAS_OK;
+}
+
+int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
+    if (!s) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = s->ctx;
+    cudaSetDevice(c->device);
+    cudaStream_t main = c->stream;
+    // admit
+    while (!s->waiting.empty() && !s->free_slots.empty()) {
+        ServerReq r = s->waiting.front();
+        s->waiting.pop_front();
+        r.slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        elas_grid g = r.g;
+        int rc = setup(g);
+        if (rc) return rc;
+        Level& L0 = g->lv[0];
+        launch_dirichlet(L0.L64, boundary_data(g), L0.u, r.opts.warm_start ? 1 : 0, main);
+        cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, main);
+        cudaMemsetAsync(g->alam, 0, sizeof(double) * kLoadDoubles, main);
+        cudaMemsetAsync(g->adlam, 0, sizeof(double) * kLoadDoubles, main);
+        const int one = 1, zero = 0;
+        cudaMemcpyAsync(s->flags + r.slot, &one, sizeof(int), cudaMemcpyHostToDevice, main);
+        cudaMemcpyAsync(s->counts + r.slot, &zero, sizeof(int), cudaMemcpyHostToDevice, main);
+        CUDA_TRY(c, cudaStreamSynchronize(main));
+        for (auto& v : g->lv) v.L64.active = v.L32.active = s->flags + r.slot;
+        s->active.push_back(r);
+    }
+    if (!s->active.empty()) {
+        // one refinement step of every active request, interleaved on branch streams
+        const int S = (int)s->active.size() < 32 ? (int)s->active.size() : 32;
+        while ((int)c->branch.size() < S) {
+            cudaStream_t st;
+            cudaEvent_t ev;
+            CUDA_TRY(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            CUDA_TRY(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            c->branch.push_back(st);
+            c->branch_ev.push_back(ev);
+        }
+        cudaEvent_t fork = c->branch_ev[0];
+        CUDA_TRY(c, cudaEventRecord(fork, main));
+        for (int b = 0; b < S; ++b) cudaStreamWaitEvent(c->branch[b], fork, 0);
+        const bool prof = c->profile;
+        c->profile = false;
+        for (size_t k = 0; k < s->active.size(); ++k) {
+            ServerReq& r = s->active[k];
+            elas_grid g = r.g;
+            Level& L0 = g->lv[0];
+            c->stream = c->branch[k % S];
+            const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
+            int nb = 0;
+            launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, nf0 ? g->alam : nullptr, L0.f32, g->partials, &nb,
+                                           c->stream);
+            BatchFlags bfl{s->flags + r.slot, s->counts + r.slot, s->hist + (size_t)r.slot * ELAS_HISTORY,
+                           ELAS_HISTORY, g->r0, r.opts.rel_tol,
+                           r.opts.fixed_cycles > 0 ? r.opts.fixed_cycles : r.opts.max_cycles};
+            launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1,
+                            c->stream, bfl);
+            vcycle<float>(g, 0, r.opts.nu1, r.opts.nu2, nf0, nf0 ? g->adlam : nullptr);
+            launch_add_correction(L0.L64, L0.u, L0.u32, c->stream);
+        }
+        c->stream = main;
+        c->profile = prof;
+        for (int b = 0; b < S; ++b) {
+            cudaEventRecord(c->branch_ev[b], c->branch[b]);
+            cudaStreamWaitEvent(main, c->branch_ev[b], 0);
+        }
+        CHECK_LAUNCH(c);
+        CUDA_TRY(c, cudaMemcpyAsync(s->h_flags.data(), s->flags, sizeof(int) * s->max_active, cudaMemcpyDeviceToHost, main));
+        CUDA_TRY(c, cudaMemcpyAsync(s->h_counts.data(), s->counts, sizeof(int) * s->max_active, cudaMemcpyDeviceToHost,
+                                    main));
+        CUDA_TRY(c, cudaStreamSynchronize(main));
+        // retire
+        std::vector<ServerReq> keep;
+        for (auto& r : s->active) {
+            if (s->h_flags[r.slot]) {
+                keep.push_back(r);
+                continue;
+            }
+            elas_grid g = r.g;
+            for (auto& v : g->lv) v.L64.active = v.L32.active = nullptr;
+            int rc = remove_rigid(g);
+            if (rc) return rc;
+            ServerDone d{};
+            const int cnt = s->h_counts[r.slot] < ELAS_HISTORY ? s->h_counts[r.slot] : ELAS_HISTORY;
+            std::vector<double> h(cnt > 0 ? cnt : 1);
+            if (cnt > 0)
+                CUDA_TRY(c, cudaMemcpyAsync(h.data(), s->hist + (size_t)r.slot * ELAS_HISTORY, sizeof(double) * cnt,
+                                            cudaMemcpyDeviceToHost, main));
+            CUDA_TRY(c, cudaStreamSynchronize(main));
+            for (int k = 0; k < cnt; ++k) d.info.rel_history[k] = h[k];
+            d.info.cycles = s->h_counts[r.slot] > 0 ? s->h_counts[r.slot] - 1 : 0;
+            d.info.rel_residual = cnt > 0 ? h[cnt - 1] : 0.0;
+            d.info.r0 = g->r0;
+            d.info.nlam = g->lv[0].nf.m;
+            const bool ok = r.opts.fixed_cycles > 0 || d.info.rel_residual <= r.opts.rel_tol;
+            d.info.status = ok ? ELAS_OK : ELAS_ERR_NOT_CONVERGED;
+            d.latency = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_submit).count();
+            d.info.seconds = d.latency;
+            s->done[r.ticket] = d;
+            s->free_slots.push_back(r.slot);
+        }
+        s->active.swap(keep);
+    }
+    if (n_active) *n_active = (int)s->active.size();
+    if (n_waiting) *n_waiting = (int)s->waiting.size();
+    return ELAS_OK;
+}
+
+int elas_server_poll(elas_server s, long long ticket, elas_solve_info* info, double* latency_s) {
+    if (!s) return ELAS_ERR_INVALID_ARG;
+    auto it = s->done.find(ticket);
+    if (it == s->done.end()) return 0;
+    if (info) *info = it->second.info;
+    if (latency_s) *latency_s = it->second.latency;
+    s->done.erase(it);
+    return 1;
 }
 
 }  // extern "C"

@@ -113,6 +113,11 @@ def lib():
         "elas_batch_solve": (ip, [C.POINTER(vp), ip, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "elas_profile_enable": (ip, [vp, ip]),
         "elas_amr_create": (ip, [C.POINTER(vp), C.POINTER(AmrLevelDesc), ip, C.POINTER(vp)]),
+        "elas_server_create": (ip, [vp, ip, C.POINTER(vp)]),
+        "elas_server_destroy": (ip, [vp]),
+        "elas_server_submit": (ip, [vp, vp, C.POINTER(SolveOpts), C.POINTER(C.c_longlong)]),
+        "elas_server_step": (ip, [vp, C.POINTER(ip), C.POINTER(ip)]),
+        "elas_server_poll": (ip, [vp, C.c_longlong, C.POINTER(SolveInfo), dp]),
         "elas_amr_destroy": (ip, [vp]),
         "elas_amr_solve": (ip, [vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "elas_profile_read": (ip, [vp, ip, dp, C.POINTER(C.c_longlong)]),
@@ -470,3 +475,36 @@ def batch_solve(grids, precision=MIXED, rel_tol=1e-8, max_cycles=100, nu1=2, nu2
     if rc != OK and raise_on_error and rc != ERR_NOT_CONVERGED:
         raise ElasError(rc, grids[0].ctx.error())
     return [infos[i].as_dict() for i in range(n)]
+
+
+class Server:
+    """Continuous-batching step engine of the C library (see elas_server_* in elas.h)."""
+
+    def __init__(self, ctx: Context, max_active=16):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx.check(lib().elas_server_create(ctx.h, max_active, C.byref(h)))
+        self.h = h
+
+    def submit(self, grid: Grid, **kw):
+        t = C.c_longlong()
+        self.ctx.check(lib().elas_server_submit(self.h, grid.h, C.byref(_opts(MIXED, **kw)), C.byref(t)))
+        return t.value
+
+    def step(self):
+        a, w = C.c_int(), C.c_int()
+        self.ctx.check(lib().elas_server_step(self.h, C.byref(a), C.byref(w)))
+        return a.value, w.value
+
+    def poll(self, ticket):
+        info = SolveInfo()
+        lat = C.c_double()
+        rc = lib().elas_server_poll(self.h, ticket, C.byref(info), C.byref(lat))
+        if rc < 0:
+            raise ElasError(rc, self.ctx.error())
+        return (info.as_dict(), lat.value) if rc == 1 else None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().elas_server_destroy(self.h)
+            self.h = None
