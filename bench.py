@@ -77,9 +77,11 @@ def alg_bytes_per_node(cls, K):
 
 
 def flops_per_node_resid64(K):
-    # interior row of the general stencil: gradient 18, second differences 63,
-    # modulus-gradient term 3*3*6*4, modulus term 81*2, residual 3
-    return 18 + 63 + 216 + 162 + 3 if K == 21 else 18 + 63 + 60 + 3
+    """FP64 flops of one interior residual row triple as executed (an FMA counts 2):
+    general moduli with the precomputed modulus divergence: gradient 18, compact
+    second differences 36, mixed differences 36, strain 3, Voigt pairing 9,
+    modulus-divergence term 36, modulus term 108, residual 3; isotropic: 161."""
+    return 249 if K == 21 else 161
 
 
 class Clocks:
@@ -130,6 +132,25 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(value, dist=None):
+    """Largest value over all ranks (the job's wall time is its slowest rank's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(elapsed_local, steps_per_rank, dist=None):
+    """Whole-job throughput of independent replicas: all ranks' units over the
+    slowest rank's time."""
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    t = max_over_ranks(elapsed_local, dist)
+    return world * steps_per_rank / t, t
 
 
 def dist_setup():
@@ -268,11 +289,7 @@ def main():
     prof = {name: ctx.profile_read(cls) for name, cls in
             [("sweep32", E.PROF_SWEEP32_L0), ("resid64", E.PROF_RESID64_L0), ("resid32", E.PROF_RESID32_L0)]}
     ctx.profile(False)
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * args.steps / elapsed
+    value, elapsed = whole_job_value(elapsed, args.steps, dist)
     rel64, _ = g.query_residual()
 
     # end to end through the C ABI with pinned host buffers
@@ -288,12 +305,8 @@ def main():
             g.displacement_into(host_u)
         torch.cuda.synchronize()
         te = time.perf_counter() - t
-        e2e = {"value": world * args.e2e_steps / te if not dist else None, "unit": UNIT,
+        e2e = {"value": whole_job_value(te, args.e2e_steps, dist)[0], "unit": UNIT,
                "h2d_bytes_per_step": int(host_mod.numel() * 8), "d2h_bytes_per_step": int(host_u.numel() * 8)}
-        if dist:
-            tt = torch.tensor([te], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e["value"] = world * args.e2e_steps / float(tt.item())
 
     if rank != 0:
         return
