@@ -245,7 +245,8 @@ def main():
     g = E.grid_from_problem(ctx, p, mixed=True)
     stream = ctx.stream
 
-    # warm-up (the first solve also builds the hierarchy data)
+    # launch-shape autotuning of the smoother (per level), then warm-up solves
+    tune_ms = g.autotune()
     for _ in range(args.warmup):
         info = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200)
     # FP64 reference solve of the same problem
@@ -365,6 +366,7 @@ def main():
         "mixed_over_fp64": value / fp64_value if fp64_value else None,
         "dof_updates_per_s": value * 3 * N * 2 * 4 * (info["cycles"]),
         "roofline": roof, "kernels": kernels, "gpu_launches": int(launches),
+        "autotune": {"finest_fp32_sweep_ms_per_shape": tune_ms, "table": E.autotune_dump().strip().splitlines()},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
     }
     print(json.dumps(out), flush=True)

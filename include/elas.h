@@ -218,6 +218,18 @@ int  elas_profile_enable(elas_ctx ctx, int enable);
 int  elas_profile_read(elas_ctx ctx, int kernel_class, double* total_ms, long long* launches);
 unsigned long long elas_launch_count(void);
 
+/* ---- autotuner ---------------------------------------------------------------
+ * The interior smoother has several launch shapes (threads per block x minimum
+ * resident blocks per SM, which bounds registers per thread).  elas_autotune
+ * times each shape on every level of the grid, in FP32 (mixed grids) and FP64,
+ * and keeps the fastest per (level dimensions, moduli kind, precision) in a
+ * process-wide table used by every later launch.  times_ms (optional) receives
+ * the FP32 timings of the finest level, one per shape.  The table can be saved
+ * and restored as text (one "nx ny nz kind bytes divc shape" line per entry). */
+int  elas_autotune(elas_grid g, float* times_ms, int ntimes);
+int  elas_autotune_dump(char* buf, int cap);   /* returns the text length */
+int  elas_autotune_load(const char* text);     /* returns the entries read */
+
 /* ---- block-structured AMR (Section 3.1, reflux-free coarse/fine, Section 3.2,
  * Appendix A) ------------------------------------------------------------------
  * nlevels grids of one context: level 0 covers the domain (with its multigrid

@@ -1160,6 +1160,31 @@ int elas_profile_read(elas_ctx c, int cls, double* total_ms, long long* launches
 
 unsigned long long elas_launch_count(void) { return elas::launch_count(); }
 
+int elas_autotune(elas_grid g, float* times_ms, int ntimes) {
+    if (!g) return ELAS_ERR_INVALID_ARG;
+    int rc = setup(g);
+    if (rc) return rc;
+    elas_ctx c = g->ctx;
+    for (size_t l = 0; l < g->lv.size(); ++l) {
+        Level& v = g->lv[l];
+        float ms[kNumSweepVariants];
+        if (g->desc.mixed) {
+            cudaMemsetAsync(v.u32, 0, sizeof(float) * 3 * (size_t)v.N, c->stream);
+            cudaMemsetAsync(v.f32, 0, sizeof(float) * 3 * (size_t)v.N, c->stream);
+            tune_sweep<float>(v.L32, v.u32, v.ua32, v.f32, c->stream, ms);
+            if (l == 0 && times_ms)
+                for (int k = 0; k < kNumSweepVariants && k < ntimes; ++k) times_ms[k] = ms[k];
+        }
+        tune_sweep<double>(v.L64, v.u, v.ua, v.f, c->stream, nullptr);
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CHECK_LAUNCH(c);
+    return ELAS_OK;
+}
+
+int elas_autotune_dump(char* buf, int cap) { return tune_table_dump(buf, cap); }
+int elas_autotune_load(const char* text) { return text ? tune_table_load(text) : 0; }
+
 int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_info* info) {
     if (!grids || n < 0 || !opts || !info) return ELAS_ERR_INVALID_ARG;
     if (n == 0) return ELAS_OK;

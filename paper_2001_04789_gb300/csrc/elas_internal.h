@@ -29,6 +29,15 @@ struct RhsInputs {
 unsigned long long launch_count();
 void count_launch(int n = 1);
 
+// Interior smoother launch variants (block size, minimum blocks per SM) and the
+// autotuner that picks one per level shape and precision.
+constexpr int kNumSweepVariants = 5;
+constexpr int kDefaultSweepVariant = 0;
+template <typename T>
+int tune_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, cudaStream_t s, float* ms_out);
+int tune_table_dump(char* buf, int cap);
+int tune_table_load(const char* text);
+
 // Launchers (all enqueue on `s`).
 void launch_rhs(const Lv<double>& L, const RhsInputs& in, const BoundaryData& bd, double* f, cudaStream_t s);
 void launch_dirichlet(const Lv<double>& L, const BoundaryData& bd, double* u, int keep_free, cudaStream_t s);

@@ -6,6 +6,13 @@
 // warp shuffles, one partial per block, then a single-block fixed-order sum.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <array>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "elas_internal.h"
 
@@ -288,8 +295,8 @@ __global__ void __launch_bounds__(kBlock) k_residual_bnd(Lv<T> L, const T* __res
 // Red-black smoother, interior nodes: each thread owns the x-pair (x0, x0+1) of the
 // interior box, updates the one of the active colour and copies the other; every
 // row uses the values from before the half-sweep (Jacobi within the colour).
-template <typename T, int KIND, bool HM>
-__global__ void __launch_bounds__(kBlock) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
+template <typename T, int KIND, bool HM, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
                                                           const T* __restrict__ f, int colour, NullInfo nf,
                                                           const double* __restrict__ lam) {
     if (L.active && *L.active == 0) return;
@@ -1174,6 +1181,123 @@ void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf,
     }
 }
 
+// ---- launch variants of the interior smoother and their tuning table -----------------
+// (threads per block, minimum resident blocks per SM) pairs; the second number
+// bounds the registers per thread and so trades registers for resident warps.
+static const int kSweepVariants[kNumSweepVariants][2] = {{256, 1}, {256, 2}, {256, 3}, {256, 4}, {128, 8}};
+
+static std::mutex g_tune_mu;
+static std::map<std::array<int, 6>, int> g_tune;
+
+template <typename T>
+static std::array<int, 6> tune_key(const Lv<T>& L) {
+    return {L.n[0], L.n[1], L.n[2], L.K, (int)sizeof(T), L.divc ? 1 : 0};
+}
+
+template <typename T>
+int sweep_variant_for(const Lv<T>& L) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(L));
+    return it == g_tune.end() ? kDefaultSweepVariant : it->second;
+}
+
+template <typename T>
+void set_sweep_variant(const Lv<T>& L, int v) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(L)] = v;
+}
+
+int tune_table_dump(char* buf, int cap) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::string out;
+    for (auto& kv : g_tune) {
+        char line[128];
+        snprintf(line, sizeof(line), "%d %d %d %d %d %d %d\n", kv.first[0], kv.first[1], kv.first[2], kv.first[3],
+                 kv.first[4], kv.first[5], kv.second);
+        out += line;
+    }
+    if (buf && cap > 0) {
+        const int n = (int)out.size() < cap - 1 ? (int)out.size() : cap - 1;
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return (int)out.size();
+}
+
+int tune_table_load(const char* text) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int count = 0;
+    const char* p = text;
+    while (p && *p) {
+        std::array<int, 6> k;
+        int v, used = 0;
+        if (sscanf(p, "%d %d %d %d %d %d %d%n", &k[0], &k[1], &k[2], &k[3], &k[4], &k[5], &v, &used) != 7) break;
+        if (v >= 0 && v < kNumSweepVariants) {
+            g_tune[k] = v;
+            ++count;
+        }
+        p += used;
+        while (*p == '\n' || *p == ' ') ++p;
+    }
+    return count;
+}
+
+template <typename T, int KIND, bool HM>
+void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
+                       const NullInfo& nfv, const double* lam, cudaStream_t s) {
+    const int bs = kSweepVariants[v][0];
+    const int nb = (int)((np + bs - 1) / bs);
+    switch (v) {
+        case 0: k_half_sweep_int<T, KIND, HM, 256, 1><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
+        case 1: k_half_sweep_int<T, KIND, HM, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
+        case 2: k_half_sweep_int<T, KIND, HM, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
+        case 3: k_half_sweep_int<T, KIND, HM, 256, 4><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
+        default: k_half_sweep_int<T, KIND, HM, 128, 8><<<nb, 128, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
+    }
+}
+
+// Time every variant of the interior half-sweep on one level (buffers as given) and
+// keep the fastest in the tuning table.  Returns the chosen variant.
+template <typename T>
+int tune_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, cudaStream_t s, float* ms_out) {
+    const size_t np = interior_pairs(L);
+    if (!np) return kDefaultSweepVariant;
+    NullInfo nfv{};
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int best = kDefaultSweepVariant;
+    float best_ms = 1e30f;
+    for (int v = 0; v < kNumSweepVariants; ++v) {
+        auto run = [&]() {
+            if (L.K == 2) sweep_int_variant<T, 2, false>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
+            else if (L.divc) sweep_int_variant<T, 21, true>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
+            else sweep_int_variant<T, 21, false>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
+        };
+        run();
+        cudaEventRecord(a, s);
+        const int reps = 5;
+        for (int r = 0; r < reps; ++r) run();
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        ms /= reps;
+        if (ms_out) ms_out[v] = ms;
+        if (cudaGetLastError() == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    set_sweep_variant(L, best);
+    return best;
+}
+
+template int tune_sweep<float>(const Lv<float>&, const float*, float*, const float*, cudaStream_t, float*);
+template int tune_sweep<double>(const Lv<double>&, const double*, double*, const double*, cudaStream_t, float*);
+
 template <typename T>
 void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour, const NullInfo* nf,
                        const double* lam, cudaStream_t s) {
@@ -1182,9 +1306,10 @@ void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int 
     const size_t np = interior_pairs(L);
     if (np) {
         count_launch();
-        if (L.K == 2) k_half_sweep_int<T, 2, false><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
-        else if (L.divc) k_half_sweep_int<T, 21, true><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
-        else k_half_sweep_int<T, 21, false><<<blocks_for(np), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+        const int v = sweep_variant_for(L);
+        if (L.K == 2) sweep_int_variant<T, 2, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        else if (L.divc) sweep_int_variant<T, 21, true>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        else sweep_int_variant<T, 21, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
     }
     launch_faces_sweep<T, 0>(L, u_in, u_out, f, colour, nfv, lam, s);
     launch_faces_sweep<T, 1>(L, u_in, u_out, f, colour, nfv, lam, s);

@@ -114,6 +114,9 @@ def lib():
         "elas_profile_enable": (ip, [vp, ip]),
         "elas_amr_create": (ip, [C.POINTER(vp), C.POINTER(AmrLevelDesc), ip, C.POINTER(vp)]),
         "elas_server_create": (ip, [vp, ip, C.POINTER(vp)]),
+        "elas_autotune": (ip, [vp, C.POINTER(C.c_float), ip]),
+        "elas_autotune_dump": (ip, [C.c_char_p, ip]),
+        "elas_autotune_load": (ip, [C.c_char_p]),
         "elas_server_destroy": (ip, [vp]),
         "elas_server_submit": (ip, [vp, vp, C.POINTER(SolveOpts), C.POINTER(C.c_longlong)]),
         "elas_server_step": (ip, [vp, C.POINTER(ip), C.POINTER(ip)]),
@@ -366,10 +369,28 @@ class Grid:
         self.ctx.check(lib().elas_op_bottom(self.h, precision, _ptr(f), _ptr(u)))
         return u
 
+    def autotune(self):
+        """Pick the fastest smoother launch shape per level; returns the finest
+        level's FP32 timings (ms) per shape."""
+        t = (C.c_float * 8)()
+        self.ctx.check(lib().elas_autotune(self.h, t, 8))
+        return list(t[:5])
+
     def close(self):
         if getattr(self, "h", None):
             lib().elas_grid_destroy(self.h)
             self.h = None
+
+
+def autotune_dump():
+    n = lib().elas_autotune_dump(None, 0)
+    buf = C.create_string_buffer(n + 1)
+    lib().elas_autotune_dump(buf, n + 1)
+    return buf.value.decode()
+
+
+def autotune_load(text):
+    return lib().elas_autotune_load(text.encode())
 
 
 def grid_from_problem(ctx: Context, p: M.Problem, mixed=False, max_levels=0) -> Grid:

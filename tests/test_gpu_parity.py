@@ -242,3 +242,17 @@ def test_budget_refuses_oversized_grid(E):
         E.Grid(c, E.desc_for(M.eshelby_sphere(33)))
     assert ei.value.code == -2
     c.close()
+
+
+def test_autotuned_launch_shapes_do_not_change_results(E, ctx):
+    p = CASES["mixed_gen"]()
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    before = g.solve(precision=E.MIXED, rel_tol=0.0, fixed_cycles=3)
+    ub = g.displacement()
+    times = g.autotune()
+    assert len(times) == 5 and all(t > 0 for t in times)
+    assert len(E.autotune_dump().strip().splitlines()) >= 1
+    after = g.solve(precision=E.MIXED, rel_tol=0.0, fixed_cycles=3)
+    assert np.array_equal(ub, g.displacement())
+    assert before["rel_history"] == after["rel_history"]
+    g.close()
