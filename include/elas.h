@@ -146,7 +146,8 @@ typedef struct {
     int    nu1, nu2;      /* pre / post smoothing sweeps (one sweep = red + black) */
     int    warm_start;    /* 1 = start from the current displacement              */
     int    fixed_cycles;  /* > 0: run exactly this many cycles, ignore rel_tol     */
-    int    use_graph;     /* 1 = replay the cycle as a captured CUDA graph         */
+    int    use_graph;     /* reserved (batched solves always use a CUDA graph)     */
+    int    inner_cycles;  /* mixed: FP32 V-cycles per FP64 refinement step (>= 1)  */
 } elas_solve_opts;
 
 #define ELAS_HISTORY 128

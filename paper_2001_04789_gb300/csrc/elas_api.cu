@@ -516,7 +516,7 @@ void smooth(elas_grid g, int l, int sweeps, const NullInfo* nf, const double* la
 
 // Correction cycle on level l >= 1 (or l = 0 of the FP32 cycle): u_l from zero.
 template <typename T>
-void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const double* dlam0) {
+void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const double* dlam0, bool zero_init = true) {
     Level& v = g->lv[l];
     cudaStream_t s = g->ctx->stream;
     const int nl = (int)g->lv.size();
@@ -527,7 +527,7 @@ void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const dou
     }
     const NullInfo* nf = (l == 0) ? nf0 : nullptr;
     const double* lam = (l == 0) ? dlam0 : nullptr;
-    cudaMemsetAsync(Fields<T>::u(v), 0, sizeof(T) * 3 * (size_t)v.N, s);
+    if (zero_init) cudaMemsetAsync(Fields<T>::u(v), 0, sizeof(T) * 3 * (size_t)v.N, s);
     smooth<T>(g, l, nu1, nf, lam);
     const size_t e = l == 0 ? prof_begin(g->ctx, sizeof(T) == 8 ? ELAS_PROF_RESID64_L0 : ELAS_PROF_RESID32_L0)
                             : (size_t)-1;
@@ -895,6 +895,7 @@ void elas_solve_opts_default(elas_solve_opts* o) {
     o->warm_start = 0;
     o->fixed_cycles = 0;
     o->use_graph = 0;
+    o->inner_cycles = 1;
 }
 
 int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) {
@@ -967,7 +968,9 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
             launch_prolong_add<double>(L0.L64, L1.L64, L1.u, L0.u, s);
             smooth<double>(g, 0, nu2, nf0, load);
         } else {
-            vcycle<float>(g, 0, nu1, nu2, nf0, dload);
+            // FP32 V-cycles on the correction equation, the first from zero
+            const int inner = opts->inner_cycles > 1 ? opts->inner_cycles : 1;
+            for (int k = 0; k < inner; ++k) vcycle<float>(g, 0, nu1, nu2, nf0, dload, k == 0);
             launch_add_correction(L0.L64, L0.u, L0.u32, s);
         }
         CHECK_LAUNCH(c);
@@ -1269,7 +1272,8 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
                            opts->fixed_cycles > 0 ? opts->fixed_cycles : opts->max_cycles};
             launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1,
                             c->stream, bfl);
-            vcycle<float>(g, 0, nu1, nu2, nf0, nf0 ? g->adlam : nullptr);
+            for (int k = 0; k < (opts->inner_cycles > 1 ? opts->inner_cycles : 1); ++k)
+                vcycle<float>(g, 0, nu1, nu2, nf0, nf0 ? g->adlam : nullptr, k == 0);
             launch_add_correction(L0.L64, L0.u, L0.u32, c->stream);
         }
     }
@@ -1738,7 +1742,8 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
                            r.opts.fixed_cycles > 0 ? r.opts.fixed_cycles : r.opts.max_cycles};
             launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1,
                             c->stream, bfl);
-            vcycle<float>(g, 0, r.opts.nu1, r.opts.nu2, nf0, nf0 ? g->adlam : nullptr);
+            for (int k = 0; k < (r.opts.inner_cycles > 1 ? r.opts.inner_cycles : 1); ++k)
+                vcycle<float>(g, 0, r.opts.nu1, r.opts.nu2, nf0, nf0 ? g->adlam : nullptr, k == 0);
             launch_add_correction(L0.L64, L0.u, L0.u32, c->stream);
         }
         c->stream = main;

@@ -46,7 +46,7 @@ class AmrLevelDesc(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("rel_tol", C.c_double), ("max_cycles", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("warm_start", C.c_int),
-                ("fixed_cycles", C.c_int), ("use_graph", C.c_int)]
+                ("fixed_cycles", C.c_int), ("use_graph", C.c_int), ("inner_cycles", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -291,12 +291,8 @@ class Grid:
 
     # -- solve -------------------------------------------------------------------
     def solve(self, precision=FP64, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False,
-              fixed_cycles=0, use_graph=False, raise_on_error=True):
-        o = SolveOpts()
-        lib().elas_solve_opts_default(C.byref(o))
-        o.precision, o.rel_tol, o.max_cycles = precision, rel_tol, max_cycles
-        o.nu1, o.nu2, o.warm_start, o.fixed_cycles = nu1, nu2, int(warm_start), fixed_cycles
-        o.use_graph = int(use_graph)
+              fixed_cycles=0, use_graph=False, raise_on_error=True, inner_cycles=1):
+        o = _opts(precision, rel_tol, max_cycles, nu1, nu2, warm_start, fixed_cycles, use_graph, inner_cycles)
         info = SolveInfo()
         rc = lib().elas_solve(self.h, C.byref(o), C.byref(info))
         if rc != OK and raise_on_error and rc not in (ERR_NOT_CONVERGED,):
@@ -431,12 +427,13 @@ def grid_from_problem(ctx: Context, p: M.Problem, mixed=False, max_levels=0) -> 
 
 
 def _opts(precision=FP64, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False, fixed_cycles=0,
-          use_graph=False):
+          use_graph=False, inner_cycles=1):
     o = SolveOpts()
     lib().elas_solve_opts_default(C.byref(o))
     o.precision, o.rel_tol, o.max_cycles = precision, rel_tol, max_cycles
     o.nu1, o.nu2, o.warm_start, o.fixed_cycles = nu1, nu2, int(warm_start), fixed_cycles
     o.use_graph = int(use_graph)
+    o.inner_cycles = int(inner_cycles)
     return o
 
 

@@ -256,3 +256,14 @@ def test_autotuned_launch_shapes_do_not_change_results(E, ctx):
     assert np.array_equal(ub, g.displacement())
     assert before["rel_history"] == after["rel_history"]
     g.close()
+
+
+def test_two_inner_fp32_cycles_per_refinement_step(E, ctx):
+    p = CASES["polycrystal"]()
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    one = g.solve(precision=E.MIXED, rel_tol=1e-8)
+    two = g.solve(precision=E.MIXED, rel_tol=1e-8, inner_cycles=2)
+    assert two["status"] == 0 and two["cycles"] < one["cycles"]
+    ref, _ = MG.solve(p, tol=1e-8, max_cycles=300)
+    assert rel_err(g.displacement(), ref) < 1e-7
+    g.close()
