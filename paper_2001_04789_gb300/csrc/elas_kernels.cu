@@ -205,18 +205,18 @@ __global__ void __launch_bounds__(kBlock) k_apply_int(Lv<T> L, const T* __restri
     for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
 }
 
+// Edge and corner nodes: one warp per node, lanes 0-2 evaluate its three rows.
 template <typename T, int KIND>
-__global__ void k_apply_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= L.nbnd) return;
-    const int p = L.bnodes[t];
+__global__ void __launch_bounds__(kBlock) k_apply_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= L.nbnd || lane >= 3) return;
+    const int p = L.bnodes[w];
     int c[3];
     coords_of(p, L.n, c);
     const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-    int types[3];
-    T v[3];
-    boundary_rows_all<T, KIND>(L, u, ni, types, v);
-    for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
+    UField<T> uf{u, L.N, L.n[0], L.n[1]};
+    out[lane * L.N + p] = boundary_row<T, KIND>(L, uf, ni, lane, row_type(L, ni, lane));
 }
 
 // r = f - load - A u on one node's rows (load = t + w x d, the equilibrating load);
@@ -277,17 +277,24 @@ __global__ void __launch_bounds__(kBlock) k_residual_bnd(Lv<T> L, const T* __res
                                                         NullInfo nf, const double* __restrict__ lam,
                                                         TR* __restrict__ r, double* __restrict__ partials) {
     if (L.active && *L.active == 0) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (t < L.nbnd) {
-        const int p = L.bnodes[t];
+    if (w < L.nbnd) {
+        const int p = L.bnodes[w];
         int c[3];
         coords_of(p, L.n, c);
         const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
         int types[3];
+        for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
+        T val = T(0);
+        if (lane < 3) {
+            UField<T> uf{u, L.N, L.n[0], L.n[1]};
+            val = boundary_row<T, KIND>(L, uf, ni, lane, types[lane]);
+        }
         T v[3];
-        boundary_rows_all<T, KIND>(L, u, ni, types, v);
-        residual_store<T, TR, NORM>(L, f, nf, lam, c, p, types, v, r, acc);
+        for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, i);
+        if (lane == 0) residual_store<T, TR, NORM>(L, f, nf, lam, c, p, types, v, r, acc);
     }
     if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
 }
@@ -335,29 +342,39 @@ __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* _
     for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + d[i];
 }
 
-// Red-black smoother, boundary-plane nodes (one thread per listed node).
+// Red-black smoother, edge and corner nodes: one warp per node; lanes 0-8 compute
+// the diagonal block entries, lanes 9-11 the rows, lane 0 solves and writes.
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
                                                           const T* __restrict__ f, int colour, NullInfo nf,
                                                           const double* __restrict__ lam) {
     if (L.active && *L.active == 0) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= L.nbnd) return;
-    const int p = L.bnodes[t];
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= L.nbnd) return;
+    const int p = L.bnodes[w];
     const int N = L.N;
     int c[3];
     coords_of(p, L.n, c);
     if (((c[0] + c[1] + c[2]) & 1) != colour) {
-        uo[p] = u[p];
-        uo[N + p] = u[N + p];
-        uo[2 * N + p] = u[2 * N + p];
+        if (lane < 3) uo[lane * N + p] = u[lane * N + p];
         return;
     }
     const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
     int types[3];
-    T v[3];
-    boundary_rows_all<T, KIND>(L, u, ni, types, v);
-    T r[3], B[3][3], d[3];
+    for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
+    T val = T(0);
+    if (lane < 9) {
+        val = boundary_block_entry<T, KIND>(L, ni, types, lane / 3, lane % 3);
+    } else if (lane < 12) {
+        UField<T> uf{u, N, L.n[0], L.n[1]};
+        val = boundary_row<T, KIND>(L, uf, ni, lane - 9, types[lane - 9]);
+    }
+    T B[3][3], v[3];
+    for (int q = 0; q < 9; ++q) B[q / 3][q % 3] = __shfl_sync(0xffffffffu, val, q);
+    for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, 9 + i);
+    if (lane != 0) return;
+    T r[3], d[3];
     for (int i = 0; i < 3; ++i) {
         if (types[i] == ROW_DIRICHLET) {
             r[i] = T(0);
@@ -367,7 +384,6 @@ __global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __r
             r[i] = fi - v[i];
         }
     }
-    boundary_block<T, KIND>(L, ni, types, B);
     solve3(B, r, d);
     for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
 }
@@ -1138,8 +1154,8 @@ void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
     launch_faces_apply<T, 2>(L, u, out, s);
     if (L.nbnd) {
         count_launch();
-        if (L.K == 2) k_apply_bnd<T, 2><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u, out);
-        else k_apply_bnd<T, 21><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u, out);
+        if (L.K == 2) k_apply_bnd<T, 2><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u, out);
+        else k_apply_bnd<T, 21><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u, out);
     }
 }
 
@@ -1150,7 +1166,7 @@ void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf,
     if (nf) nfv = *nf;
     const size_t ni = interior_count(L);
     const int nbi = ni ? blocks_for(ni) : 0;
-    const int nbb = L.nbnd ? blocks_for(L.nbnd) : 0;
+    const int nbb = L.nbnd ? blocks_for((size_t)L.nbnd * 32) : 0;
     int off = nbi;
     off += launch_faces_residual<T, TR, 0>(L, u, f, nfv, lam, r, partials ? partials + (size_t)off * kPartialStride : nullptr, s);
     off += launch_faces_residual<T, TR, 1>(L, u, f, nfv, lam, r, partials ? partials + (size_t)off * kPartialStride : nullptr, s);
@@ -1316,8 +1332,8 @@ void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int 
     launch_faces_sweep<T, 2>(L, u_in, u_out, f, colour, nfv, lam, s);
     if (L.nbnd) {
         count_launch();
-        if (L.K == 2) k_half_sweep_bnd<T, 2><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
-        else k_half_sweep_bnd<T, 21><<<blocks_for(L.nbnd), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+        if (L.K == 2) k_half_sweep_bnd<T, 2><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+        else k_half_sweep_bnd<T, 21><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
     }
 }
 
