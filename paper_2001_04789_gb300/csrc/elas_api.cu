@@ -756,7 +756,14 @@ int elas_grid_create(elas_ctx c, const elas_grid_desc* d, elas_grid* out) {
         v.N = v.n[0] * v.n[1] * v.n[2];
         if ((rc = level_alloc(g, v, d->mixed != 0))) break;
     }
-    const size_t nparts = (size_t)((g->lv[0].N + kBlock - 1) / kBlock) * kPartialStride + 64;
+    // reduction blocks of one residual launch set: interior + faces (each at most one
+    // block per 256 nodes) + edges/corners (one warp per node)
+    size_t maxblocks = 0;
+    for (auto& v : g->lv) {
+        const size_t nb = 2 * (size_t)((v.N + kBlock - 1) / kBlock) + ((size_t)v.nbnd * 32 + kBlock - 1) / kBlock + 8;
+        maxblocks = nb > maxblocks ? nb : maxblocks;
+    }
+    const size_t nparts = maxblocks * kPartialStride + 64;
     if (!rc) rc = galloc(g, &g->partials, nparts);
     if (!rc) rc = galloc(g, &g->status, 64);
     if (!rc) rc = galloc(g, &g->G, 36);
