@@ -635,23 +635,21 @@ __device__ __forceinline__ double null_vec(const NullInfo& nf, int q, int c, con
 
 // Equilibrating load at a non-Dirichlet row from its rigid-motion form a = (t, w):
 // t_c + (w x d)_c, d = x - ctr.  (sum_q lam_q W_q = t + w x d with t, w = basis lam.)
+// The load is a small correction (the incompatible part of the right-hand side), so
+// it is evaluated in FP32 in every kernel, including the FP64 residual: its FP32
+// rounding is ~1e-7 of a term that is itself far below the residual tolerance.
 template <typename T>
 __device__ __forceinline__ T rigid_load(const NullInfo& nf, const double* __restrict__ a, int comp, const int c[3]) {
-    const T* at = sizeof(T) == 8 ? (const T*)a : (const T*)(a + kLoadFloatOffset);
-    T d0, d1, d2;
-    if (sizeof(T) == 8) {
-        d0 = T(nf.off[0]) + T(nf.h[0]) * T(c[0]);
-        d1 = T(nf.off[1]) + T(nf.h[1]) * T(c[1]);
-        d2 = T(nf.off[2]) + T(nf.h[2]) * T(c[2]);
-    } else {
-        d0 = T(nf.off32[0]) + T(nf.h32[0]) * T(c[0]);
-        d1 = T(nf.off32[1]) + T(nf.h32[1]) * T(c[1]);
-        d2 = T(nf.off32[2]) + T(nf.h32[2]) * T(c[2]);
-    }
-    const T w0 = at[3], w1 = at[4], w2 = at[5];
-    if (comp == 0) return at[0] + (w1 * d2 - w2 * d1);
-    if (comp == 1) return at[1] + (w2 * d0 - w0 * d2);
-    return at[2] + (w0 * d1 - w1 * d0);
+    const float* at = (const float*)(a + kLoadFloatOffset);
+    const float d0 = nf.off32[0] + nf.h32[0] * float(c[0]);
+    const float d1 = nf.off32[1] + nf.h32[1] * float(c[1]);
+    const float d2 = nf.off32[2] + nf.h32[2] * float(c[2]);
+    const float w0 = at[3], w1 = at[4], w2 = at[5];
+    float v;
+    if (comp == 0) v = at[0] + (w1 * d2 - w2 * d1);
+    else if (comp == 1) v = at[1] + (w2 * d0 - w0 * d2);
+    else v = at[2] + (w0 * d1 - w1 * d0);
+    return T(v);
 }
 
 // sum_q coef[q] W_q(c): the equilibrating load at a non-Dirichlet row.

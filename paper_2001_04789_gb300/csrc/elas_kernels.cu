@@ -220,13 +220,14 @@ __global__ void __launch_bounds__(kBlock) k_apply_bnd(Lv<T> L, const T* __restri
 }
 
 // r = f - load - A u on one node's rows (load = t + w x d, the equilibrating load);
-// accumulates sum r^2 and the six rigid-motion moments sum r, sum d x r.
+// accumulates sum r^2 (FP64) and the six rigid-motion moments sum r, sum d x r (FP32:
+// they only steer the equilibrating load).
 template <typename T, typename TR, bool NORM>
 __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restrict__ f, const NullInfo& nf,
                                                const double* __restrict__ load, const int c[3], int p,
                                                const int types[3], const T v[3], TR* __restrict__ r,
                                                double acc[7]) {
-    double rr[3];
+    T rr[3];
     for (int i = 0; i < 3; ++i) {
         T ri = T(0);
         if (types[i] != ROW_DIRICHLET) {
@@ -234,21 +235,22 @@ __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restri
             if (load) fi -= rigid_load<T>(nf, load, i, c);
             ri = fi - v[i];
         }
-        rr[i] = (double)ri;
+        rr[i] = ri;
         r[i * L.N + p] = (TR)ri;
     }
     if (NORM) {
-        acc[0] += rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+        acc[0] += (double)(rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2]);
         if (nf.m > 0) {
-            const double d0 = nf.lo[0] + nf.h[0] * c[0] - nf.ctr[0];
-            const double d1 = nf.lo[1] + nf.h[1] * c[1] - nf.ctr[1];
-            const double d2 = nf.lo[2] + nf.h[2] * c[2] - nf.ctr[2];
-            acc[1] += rr[0];
-            acc[2] += rr[1];
-            acc[3] += rr[2];
-            acc[4] += d1 * rr[2] - d2 * rr[1];
-            acc[5] += d2 * rr[0] - d0 * rr[2];
-            acc[6] += d0 * rr[1] - d1 * rr[0];
+            const float d0 = nf.off32[0] + nf.h32[0] * float(c[0]);
+            const float d1 = nf.off32[1] + nf.h32[1] * float(c[1]);
+            const float d2 = nf.off32[2] + nf.h32[2] * float(c[2]);
+            const float r0 = (float)rr[0], r1 = (float)rr[1], r2 = (float)rr[2];
+            acc[1] += r0;
+            acc[2] += r1;
+            acc[3] += r2;
+            acc[4] += d1 * r2 - d2 * r1;
+            acc[5] += d2 * r0 - d0 * r2;
+            acc[6] += d0 * r1 - d1 * r0;
         }
     }
 }
