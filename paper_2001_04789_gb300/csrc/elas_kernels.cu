@@ -220,8 +220,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_bnd(Lv<T> L, const T* __restri
 }
 
 // r = f - load - A u on one node's rows (load = t + w x d, the equilibrating load);
-// accumulates sum r^2 (FP64) and the six rigid-motion moments sum r, sum d x r (FP32:
-// they only steer the equilibrating load).
+// accumulates sum r^2 and the six rigid-motion moments sum r, sum d x r.
 template <typename T, typename TR, bool NORM>
 __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restrict__ f, const NullInfo& nf,
                                                const double* __restrict__ load, const int c[3], int p,
@@ -239,12 +238,14 @@ __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restri
         r[i * L.N + p] = (TR)ri;
     }
     if (NORM) {
-        acc[0] += (double)(rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2]);
+        const double r0 = (double)rr[0], r1 = (double)rr[1], r2 = (double)rr[2];
+        acc[0] += r0 * r0 + r1 * r1 + r2 * r2;
         if (nf.m > 0) {
-            const float d0 = nf.off32[0] + nf.h32[0] * float(c[0]);
-            const float d1 = nf.off32[1] + nf.h32[1] * float(c[1]);
-            const float d2 = nf.off32[2] + nf.h32[2] * float(c[2]);
-            const float r0 = (float)rr[0], r1 = (float)rr[1], r2 = (float)rr[2];
+            // FP64: the moments of r cancel strongly (they measure the small incompatible
+            // part), so they are summed in full precision
+            const double d0 = nf.off[0] + nf.h[0] * c[0];
+            const double d1 = nf.off[1] + nf.h[1] * c[1];
+            const double d2 = nf.off[2] + nf.h[2] * c[2];
             acc[1] += r0;
             acc[2] += r1;
             acc[3] += r2;
