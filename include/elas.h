@@ -204,6 +204,27 @@ int  elas_op_rhs(elas_grid g, double* f_out);
 /* Exact solve of the coarsest level (dense FP64 inverse built at setup). */
 int  elas_op_bottom(elas_grid g, int precision, const void* f, void* u);
 
+/* The residual of elas_op_residual, for callers that cannot allocate device memory
+ * while they run: a host that has handed all of its memory to another runtime, code
+ * running between the phases of a memory pool it does not own, or an embedding that
+ * forbids cudaMalloc on its hot path.  This call allocates nothing: no cudaMalloc or
+ * cudaFree, no allocator callback, no library routine that allocates.  Its reduction
+ * scratch is one file-scope device array of ELAS_NOALLOC_SCRATCH_DOUBLES doubles that
+ * every GPU loading this library holds until the process exits.  (The paper has no
+ * counterpart; this is an interface for such callers only.)
+ *   - Same arguments and results as elas_op_residual (device pointers u, f, r of the
+ *     named level; *sumsq receives sum r^2).  The grid's own buffers are not used.
+ *   - A level whose reduction needs more blocks than the array holds is rejected with
+ *     ELAS_ERR_INVALID_ARG (about 60 million nodes with the default size).
+ *   - The first call on a device looks up the array's device address with that device
+ *     current; make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; every slot a
+ *     call reads is written earlier in the same call, so nothing needs clearing, but
+ *     calls that overlap on the GPU (other streams, other host threads) race. */
+#define ELAS_NOALLOC_SCRATCH_DOUBLES (1 << 21)
+int  elas_op_residual_noalloc(elas_grid g, int level, int precision, const void* u, const void* f,
+                              void* r, double* sumsq);
+
 /* ---- measurement -------------------------------------------------------------
  * With profiling enabled, every finest-level launch of the smoother and of the
  * residual inside elas_solve is bracketed by CUDA events on the context's stream;

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <string>
 #include <deque>
+#include <mutex>
 #include <map>
 #include <vector>
 
@@ -1073,6 +1074,59 @@ int elas_op_residual(elas_grid g, int level, int precision, const void* u, const
     rc = read_status(g, st, 1);
     if (rc) return rc;
     if (sumsq) *sumsq = st[0];
+    return ELAS_OK;
+}
+
+// ---- residual without allocation: reduction scratch in a file-scope device array ----
+static __device__ __align__(256) double g_noalloc_scratch[ELAS_NOALLOC_SCRATCH_DOUBLES];
+
+// Device address of the scratch array, looked up once per device with that device
+// current (a host-side use of the symbol itself would not be a device address).
+static double* noalloc_scratch(elas_ctx c) {
+    static std::mutex mu;
+    static std::map<int, double*> addr;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = addr.find(c->device);
+    if (it != addr.end()) return it->second;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return nullptr;
+    if (cur != c->device && cudaSetDevice(c->device) != cudaSuccess) return nullptr;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (cur != c->device) cudaSetDevice(cur);
+    if (e != cudaSuccess || !p) return nullptr;
+    addr[c->device] = (double*)p;
+    return (double*)p;
+}
+
+int elas_op_residual_noalloc(elas_grid g, int level, int precision, const void* u, const void* f, void* r,
+                             double* sumsq) {
+    int rc = check_level(g, level, precision);
+    if (rc) return rc;
+    elas_ctx c = g->ctx;
+    Level& v = g->lv[level];
+    // blocks of one residual launch set (interior, faces, edges), as sized at grid creation
+    const size_t nb_max =
+        2 * (size_t)((v.N + kBlock - 1) / kBlock) + ((size_t)v.nbnd * 32 + kBlock - 1) / kBlock + 8;
+    if (nb_max * kPartialStride + 8 > (size_t)ELAS_NOALLOC_SCRATCH_DOUBLES)
+        return set_err(c, ELAS_ERR_INVALID_ARG, "level too large for the no-allocation residual's static scratch");
+    double* scratch = noalloc_scratch(c);
+    if (!scratch) return set_err(c, ELAS_ERR_DEVICE, "cudaGetSymbolAddress of the static scratch failed");
+    double* out = scratch + (ELAS_NOALLOC_SCRATCH_DOUBLES - 8);   // the final sum's slot
+    int nb = 0;
+    if (precision == 0)
+        launch_residual<double, double>(v.L64, (const double*)u, (const double*)f, nullptr, nullptr, (double*)r,
+                                        scratch, &nb, c->stream);
+    else
+        launch_residual<float, float>(v.L32, (const float*)u, (const float*)f, nullptr, nullptr, (float*)r, scratch,
+                                      &nb, c->stream);
+    CHECK_LAUNCH(c);
+    launch_sum_partials(scratch, nb, 1, out, c->stream);
+    CHECK_LAUNCH(c);
+    double h = 0.0;
+    CUDA_TRY(c, cudaMemcpyAsync(&h, out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (sumsq) *sumsq = h;
     return ELAS_OK;
 }
 

@@ -105,6 +105,7 @@ def lib():
         "elas_query_residual": (ip, [vp, dp, dp]),
         "elas_op_apply": (ip, [vp, ip, ip, vp, vp]),
         "elas_op_residual": (ip, [vp, ip, ip, vp, vp, vp, dp]),
+        "elas_op_residual_noalloc": (ip, [vp, ip, ip, vp, vp, vp, dp]),
         "elas_op_sweep": (ip, [vp, ip, ip, vp, vp]),
         "elas_op_restrict": (ip, [vp, ip, ip, vp, vp]),
         "elas_op_prolong_add": (ip, [vp, ip, ip, vp, vp]),
@@ -340,6 +341,14 @@ class Grid:
         ss = C.c_double()
         self.ctx.check(lib().elas_op_residual(self.h, level, precision, _ptr(u), _ptr(f), _ptr(r), C.byref(ss)))
         return r, ss.value
+
+    def op_residual_noalloc(self, level, precision, u, f, r):
+        """elas_op_residual without any allocation: the caller passes the output r;
+        the reduction uses the library's static device scratch."""
+        ss = C.c_double()
+        self.ctx.check(lib().elas_op_residual_noalloc(self.h, level, precision, _ptr(u), _ptr(f), _ptr(r),
+                                                      C.byref(ss)))
+        return ss.value
 
     def op_sweep(self, level, precision, u, f):
         self.ctx.check(lib().elas_op_sweep(self.h, level, precision, _ptr(u), _ptr(f)))
