@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e and the CPU baseline")
     ap.add_argument("--inner", type=int, default=2, help="FP32 V-cycles per FP64 refinement step")
+    ap.add_argument("--graph", action="store_true", help="replay refinement steps as a CUDA graph")
     return ap.parse_args()
 
 
@@ -275,7 +276,8 @@ def main():
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        info = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner)
+        info = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner,
+                       use_graph=args.graph)
         b.record(stream)
         per.append((a, b))
         if info["status"] != 0:

@@ -146,7 +146,8 @@ typedef struct {
     int    nu1, nu2;      /* pre / post smoothing sweeps (one sweep = red + black) */
     int    warm_start;    /* 1 = start from the current displacement              */
     int    fixed_cycles;  /* > 0: run exactly this many cycles, ignore rel_tol     */
-    int    use_graph;     /* reserved (batched solves always use a CUDA graph)     */
+    int    use_graph;     /* mixed: replay refinement steps as a captured CUDA graph
+                             with device-side stopping (batched solves always do)  */
     int    inner_cycles;  /* mixed: FP32 V-cycles per FP64 refinement step (>= 1)  */
 } elas_solve_opts;
 

@@ -914,6 +914,7 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
     const bool mixed = opts->precision == ELAS_PRECISION_MIXED;
     if (mixed && !g->desc.mixed) return set_err(c, ELAS_ERR_STATE, "grid was created without the FP32 hierarchy");
     if (g->desc.max_levels == 1) return set_err(c, ELAS_ERR_STATE, "grid has no multigrid hierarchy (AMR level)");
+    if (mixed && opts->use_graph) return elas_batch_solve(&g, 1, opts, info);   // graph replay, one member
     const auto t0 = std::chrono::steady_clock::now();
     int rc = setup(g);
     if (rc) return rc;
@@ -1253,15 +1254,17 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
     if (!grids || n < 0 || !opts || !info) return ELAS_ERR_INVALID_ARG;
     if (n == 0) return ELAS_OK;
     elas_ctx c = grids[0]->ctx;
-    bool batched = opts->precision == ELAS_PRECISION_MIXED && n > 1;
+    bool batched = opts->precision == ELAS_PRECISION_MIXED && (n > 1 || opts->use_graph);
     for (int i = 0; i < n; ++i) {
         if (!grids[i]) return ELAS_ERR_INVALID_ARG;
         if (grids[i]->ctx != c || !grids[i]->desc.mixed || grids[i]->desc.max_levels == 1) batched = false;
     }
     if (!batched) {
         int worst = ELAS_OK;
+        elas_solve_opts one = *opts;
+        one.use_graph = 0;
         for (int i = 0; i < n; ++i) {
-            const int rc = elas_solve(grids[i], opts, &info[i]);
+            const int rc = elas_solve(grids[i], &one, &info[i]);
             if (rc != ELAS_OK && worst == ELAS_OK) worst = rc;
         }
         return worst;

@@ -267,3 +267,14 @@ def test_two_inner_fp32_cycles_per_refinement_step(E, ctx):
     ref, _ = MG.solve(p, tol=1e-8, max_cycles=300)
     assert rel_err(g.displacement(), ref) < 1e-7
     g.close()
+
+
+def test_graph_replayed_mixed_solve_equals_direct_solve(E, ctx):
+    p = CASES["polycrystal"]()
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    direct = g.solve(precision=E.MIXED, rel_tol=1e-8, inner_cycles=2)
+    ud = g.displacement()
+    graph = g.solve(precision=E.MIXED, rel_tol=1e-8, inner_cycles=2, use_graph=True)
+    assert graph["cycles"] == direct["cycles"]
+    assert np.abs(g.displacement() - ud).max() <= 1e-14 * np.abs(ud).max()
+    g.close()
