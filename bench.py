@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip e2e and the CPU baseline")
     ap.add_argument("--inner", type=int, default=2, help="FP32 V-cycles per FP64 refinement step")
     ap.add_argument("--graph", action="store_true", help="replay refinement steps as a CUDA graph")
+    ap.add_argument("--half", action="store_true", help="FP16 moduli in the FP32 V-cycle")
     return ap.parse_args()
 
 
@@ -244,7 +245,7 @@ def main():
     N = p.n[0] * p.n[1] * p.n[2]
     K = p.moduli_kind
     ctx = E.Context(local)
-    g = E.grid_from_problem(ctx, p, mixed=True)
+    g = E.grid_from_problem(ctx, p, mixed=True, half_moduli=args.half)
     stream = ctx.stream
 
     # launch-shape autotuning of the smoother (per level), then warm-up solves
@@ -360,7 +361,8 @@ def main():
         "config": {"workload": f"polycrystal {args.n}^3 nodes ({N} nodes, {3 * N} DOF), {args.grains} grains, "
                                "rotated cubic C11=1.68 C12=1.21 C44=0.75, GB width 4h, u_x=-+0.5e-3 on x faces, "
                                "traction-free elsewhere; V(2,2) red-black block GS",
-                   "precision": f"FP32 V-cycle x{args.inner} inside FP64 iterative refinement",
+                   "precision": f"FP32 V-cycle x{args.inner} inside FP64 iterative refinement"
+                                + (", FP16 moduli in the V-cycle" if args.half else ""),
                    "inputs": "larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
         "cycles": info["cycles"], "rel_residual": info["rel_residual"], "rel_residual_fp64_check": rel64,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},

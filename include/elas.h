@@ -104,6 +104,8 @@ typedef struct {
     int    mixed;         /* 1 = also allocate the FP32 hierarchy            */
     int    max_levels;    /* 0 = coarsen automatically; 1 = this level only (AMR
                              fine levels: smoothed, never solved on their own)  */
+    int    half_moduli;   /* mixed grids: the FP32 V-cycle reads FP16 moduli (half
+                             the bytes); the FP64 refinement keeps FP64 moduli   */
 } elas_grid_desc;
 
 /* Create a grid and its multigrid hierarchy (Section 3.1: levels below 0,

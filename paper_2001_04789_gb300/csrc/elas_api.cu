@@ -82,6 +82,7 @@ struct Level {
     Lv<float> L32;
     double *mod64 = nullptr, *u = nullptr, *ua = nullptr, *f = nullptr, *r = nullptr, *divc = nullptr;
     float *mod32 = nullptr, *u32 = nullptr, *ua32 = nullptr, *f32 = nullptr, *r32 = nullptr;
+    __half* mod16 = nullptr;   // FP16 moduli of the FP32 V-cycle (half_moduli grids)
     int* bnd = nullptr;   // boundary-plane nodes of this level
     int nbnd = 0;
     NullInfo nf{};
@@ -190,6 +191,7 @@ void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int 
     L.nbnd = 0;
     L.divc = nullptr;
     L.active = nullptr;
+    L.modh = nullptr;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -426,7 +428,8 @@ int setup(elas_grid g) {
     if (g->desc.mixed) {
         for (int l = 0; l < nl; ++l) {
             Level& v = g->lv[l];
-            launch_to_float(v.mod64, v.mod32, (size_t)g->K * v.N, s);
+            if (v.mod16) launch_to_half(v.mod64, v.mod16, (size_t)g->K * v.N, s);
+            else launch_to_float(v.mod64, v.mod32, (size_t)g->K * v.N, s);
             CHECK_LAUNCH(c);
         }
     }
@@ -566,7 +569,11 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     if ((rc = galloc(g, &v.f, 3 * N))) return rc;
     if ((rc = galloc(g, &v.r, 3 * N))) return rc;
     if (mixed) {
-        if ((rc = galloc(g, &v.mod32, (size_t)g->K * N))) return rc;
+        if (g->desc.half_moduli) {
+            if ((rc = galloc(g, &v.mod16, (size_t)g->K * N))) return rc;
+        } else if ((rc = galloc(g, &v.mod32, (size_t)g->K * N))) {
+            return rc;
+        }
         if ((rc = galloc(g, &v.u32, 3 * N))) return rc;
         if ((rc = galloc(g, &v.ua32, 3 * N))) return rc;
         if ((rc = galloc(g, &v.f32, 3 * N))) return rc;
@@ -612,6 +619,7 @@ void refresh_lv(elas_grid g) {
         v.L64.bnodes = v.L32.bnodes = v.bnd;
         v.L64.nbnd = v.L32.nbnd = v.nbnd;
         v.L64.divc = v.divc;
+        v.L32.modh = v.mod16;
         v.nf = null_space(g->desc, v.n, h, g->bc_type);
     }
 }
@@ -719,7 +727,7 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
     for (auto& n : level_dims(*d)) {
         const size_t N = (size_t)n[0] * n[1] * n[2];
         total += N * 8 * (K + 12 + (K == 21 ? 18 : 0));
-        if (d->mixed) total += N * 4 * (K + 12);
+        if (d->mixed) total += N * ((d->half_moduli ? 2 : 4) * K + 48);
     }
     const size_t N0 = (size_t)d->n[0] * d->n[1] * d->n[2];
     total += N0 * 8 * 9;   // eigenstrain + body force when given

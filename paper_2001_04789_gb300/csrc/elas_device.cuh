@@ -14,6 +14,7 @@
 // direction l the first derivative D_l is one-sided and second order.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,7 +39,16 @@ struct Lv {
     const T* __restrict__ divc;
     // optional per-grid flag of a batched solve: kernels of a converged member return at once
     const int* __restrict__ active;
+    // optional FP16 copy of the moduli read by FP32 kernels instead of `mod`
+    const __half* __restrict__ modh;
 };
+
+// Moduli plane entry idx (plane * N + node): from the FP16 copy when a FP32 level has one.
+template <typename T>
+__device__ __forceinline__ T modv(const Lv<T>& L, int idx) {
+    if (sizeof(T) == 4 && L.modh) return T(__half2float(L.modh[idx]));
+    return L.mod[idx];
+}
 
 // ---- Voigt helpers ----------------------------------------------------------
 __host__ __device__ constexpr int voigt(int i, int j) { return i == j ? i : 6 - i - j; }
@@ -53,15 +63,15 @@ __host__ __device__ constexpr int pair_index(int j, int l) {  // (0,1)->2 (0,2)-
 template <typename T, int KIND>
 __device__ __forceinline__ T Cm(const Lv<T>& L, int q, int i, int j, int k, int l) {
     if (KIND == 2) {
-        const T lam = L.mod[q];
-        const T mu = L.mod[L.N + q];
+        const T lam = modv(L, q);
+        const T mu = modv(L, L.N + q);
         T v = T(0);
         if (i == j && k == l) v += lam;
         if (i == k && j == l) v += mu;
         if (i == l && j == k) v += mu;
         return v;
     } else {
-        return L.mod[upper(voigt(i, j), voigt(k, l)) * L.N + q];
+        return modv(L, upper(voigt(i, j), voigt(k, l)) * L.N + q);
     }
 }
 
@@ -301,14 +311,12 @@ __device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restric
     for (int i = 0; i < 3; ++i) out[i] = T(0);
     if (KIND == 2) {
         // isotropic: C_ijkl = lam d_ij d_kl + mu (d_ik d_jl + d_il d_jk)
-        const T* lamp = L.mod;
-        const T* mup = L.mod + N;
-        const T lam = lamp[p], mu = mup[p];
+        const T lam = modv(L, p), mu = modv(L, N + p);
         T dlam[3], dmu[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            dlam[j] = (lamp[qp[j]] - lamp[qm[j]]) * L.inv2h[j];
-            dmu[j] = (mup[qp[j]] - mup[qm[j]]) * L.inv2h[j];
+            dlam[j] = (modv(L, qp[j]) - modv(L, qm[j])) * L.inv2h[j];
+            dmu[j] = (modv(L, N + qp[j]) - modv(L, N + qm[j])) * L.inv2h[j];
         }
         const T div = G[0][0] + G[1][1] + G[2][2];
 #pragma unroll
@@ -325,7 +333,6 @@ __device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restric
             out[i] = t1 + (lam + mu) * graddiv + mu * lap;
         }
     } else {
-        const T* m = L.mod;
         // second derivatives grouped by Voigt pair b = (k,l):
         // S[j][b] = d_j d_b u  (diagonal b) or d_j d_l u_k + d_j d_k u_l (shear b)
         T S[3][6];
@@ -357,13 +364,13 @@ __device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restric
                     // term 1: (d_j C_(ij)V) e_V
 #pragma unroll
                     for (int V = 0; V < 6; ++V) {
-                        const T* cp = m + upper(I, V) * N;
-                        acc += (cp[qp[j]] - cp[qm[j]]) * L.inv2h[j] * e[V];
+                        const int base = upper(I, V) * N;
+                        acc += (modv(L, base + qp[j]) - modv(L, base + qm[j])) * L.inv2h[j] * e[V];
                     }
                 }
                 // term 2: C_(ij)b S_jb
 #pragma unroll
-                for (int b = 0; b < 6; ++b) acc += m[upper(I, b) * N + p] * S[j][b];
+                for (int b = 0; b < 6; ++b) acc += modv(L, upper(I, b) * N + p) * S[j][b];
             }
             out[i] = acc;
         }

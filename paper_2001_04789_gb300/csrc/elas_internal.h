@@ -69,6 +69,7 @@ template <typename T>
 void launch_restrict_moduli(const Lv<T>& Lf, const Lv<T>& Lc, const T* mf, T* mc, cudaStream_t s);
 
 void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s);
+void launch_to_half(const double* in, __half* out, size_t n, cudaStream_t s);
 // M_iV = sum_j d_j C_(ij)V (18 planes) of a general-moduli FP64 level (setup)
 void launch_divc(const Lv<double>& L, double* M, cudaStream_t s);
 void launch_add_correction(const Lv<double>& L, double* u, const float* e, cudaStream_t s);

@@ -652,6 +652,11 @@ __global__ void k_divc(Lv<T> L, T* __restrict__ M) {
         }
 }
 
+__global__ void k_to_half(const double* __restrict__ in, __half* __restrict__ out, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __double2half(in[i]);
+}
+
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
@@ -1364,6 +1369,11 @@ void launch_restrict_moduli(const Lv<T>& Lf, const Lv<T>& Lc, const T* mf, T* mc
 void launch_divc(const Lv<double>& L, double* M, cudaStream_t s) {
     count_launch();
     k_divc<double><<<blocks_for(L.N), kBlock, 0, s>>>(L, M);
+}
+
+void launch_to_half(const double* in, __half* out, size_t n, cudaStream_t s) {
+    count_launch();
+    k_to_half<<<blocks_for(n), kBlock, 0, s>>>(in, out, n);
 }
 
 void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s) {

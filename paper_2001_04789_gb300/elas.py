@@ -35,7 +35,7 @@ class ElasError(RuntimeError):
 class GridDesc(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("periodic", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("moduli_kind", C.c_int), ("mixed", C.c_int),
-                ("max_levels", C.c_int)]
+                ("max_levels", C.c_int), ("half_moduli", C.c_int)]
 
 
 class AmrLevelDesc(C.Structure):
@@ -214,9 +214,10 @@ class Context:
             self.h = None
 
 
-def desc_for(problem: M.Problem, mixed=False, max_levels=0):
+def desc_for(problem: M.Problem, mixed=False, max_levels=0, half_moduli=False):
     d = GridDesc()
     d.max_levels = int(max_levels)
+    d.half_moduli = int(bool(half_moduli))
     for k in range(3):
         d.n[k] = int(problem.n[k])
         d.periodic[k] = int(bool(problem.periodic[k]))
@@ -398,9 +399,9 @@ def autotune_load(text):
     return lib().elas_autotune_load(text.encode())
 
 
-def grid_from_problem(ctx: Context, p: M.Problem, mixed=False, max_levels=0) -> Grid:
+def grid_from_problem(ctx: Context, p: M.Problem, mixed=False, max_levels=0, half_moduli=False) -> Grid:
     """Create a grid and load a Problem's moduli, loads and boundary conditions."""
-    g = Grid(ctx, desc_for(p, mixed, max_levels))
+    g = Grid(ctx, desc_for(p, mixed, max_levels, half_moduli))
     g.set_moduli(p.moduli)
     if p.eigenstrain is not None:
         g.set_eigenstrain(p.eigenstrain)

@@ -278,3 +278,15 @@ def test_graph_replayed_mixed_solve_equals_direct_solve(E, ctx):
     assert graph["cycles"] == direct["cycles"]
     assert np.abs(g.displacement() - ud).max() <= 1e-14 * np.abs(ud).max()
     g.close()
+
+
+@pytest.mark.parametrize("case", ["polycrystal", "eshelby", "periodic_iso"])
+def test_half_moduli_v_cycle_reaches_the_oracle_solution(E, ctx, case):
+    """FP16 moduli only precondition: the FP64 refinement still reaches the oracle."""
+    p = CASES[case]()
+    g = E.grid_from_problem(ctx, p, mixed=True, half_moduli=True)
+    info = g.solve(precision=E.MIXED, rel_tol=1e-8, inner_cycles=2)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+    ref, _ = MG.solve(p, tol=1e-8, max_cycles=300)
+    assert rel_err(g.displacement(), ref) < 1e-7
+    g.close()
