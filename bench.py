@@ -291,9 +291,19 @@ def main():
     elapsed = ev0.elapsed_time(ev1) / 1000.0
     launches = E.launch_count() - launches0
     lat = sorted(a.elapsed_time(b) for a, b in per)
-    prof = {name: ctx.profile_read(cls) for name, cls in
-            [("sweep32", E.PROF_SWEEP32_L0), ("resid64", E.PROF_RESID64_L0), ("resid32", E.PROF_RESID32_L0)]}
+    prof_classes = [("sweep32", E.PROF_SWEEP32_L0), ("resid64", E.PROF_RESID64_L0), ("resid32", E.PROF_RESID32_L0)]
+    prof = {name: ctx.profile_read(cls) for name, cls in prof_classes}
     ctx.profile(False)
+    prof_source = "timed region"
+    if not any(cnt for _, cnt in prof.values()):
+        # graph replays record no per-kernel events: time the same kernels in one
+        # eager solve after the timed region (same launch shapes, same buffers)
+        ctx.profile(True)
+        g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner)
+        torch.cuda.synchronize()
+        prof = {name: ctx.profile_read(cls) for name, cls in prof_classes}
+        ctx.profile(False)
+        prof_source = "one eager solve after the timed graph replays"
     value, elapsed = whole_job_value(elapsed, args.steps, dist)
     rel64, _ = g.query_residual()
 
@@ -343,7 +353,9 @@ def main():
             key = {"sweep32": "sweep32", "resid64": "resid64_mixed", "resid32": "resid32"}[name]
             kernels[name] = {"launches": cnt_k, "total_ms": ms_k, "avg_ms": avg * 1e3,
                              "alg_GBs": alg_bytes_per_node(key, K) * N / avg / 1e9,
-                             "share_of_timed": ms_k / (elapsed * 1000.0 / world)}
+                             "share_of_timed": (ms_k / (elapsed * 1000.0 / world)
+                                                if prof_source == "timed region" else None)}
+    roof["events_from"] = prof_source
 
     cpu = None
     if not args.quick and not args.no_cpu_baseline and world == 1:

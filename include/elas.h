@@ -244,12 +244,17 @@ int  elas_profile_read(elas_ctx ctx, int kernel_class, double* total_ms, long lo
 unsigned long long elas_launch_count(void);
 
 /* ---- autotuner ---------------------------------------------------------------
- * The interior smoother has several launch shapes (threads per block x minimum
- * resident blocks per SM, which bounds registers per thread).  elas_autotune
+ * The interior smoother has several launch shapes: 0-4 are one thread per x-pair
+ * of interior nodes with (threads per block, minimum resident blocks per SM) =
+ * (256,1) (256,2) (256,3) (256,4) (128,8), the second number bounding registers per
+ * thread; 5 and 6 stage moduli and displacement planes of a 32 x 16 (resp. 32 x 8)
+ * tile in shared memory and march through z (FP32 levels with FP32 moduli only;
+ * identical arithmetic, so every shape gives bitwise-equal results).  elas_autotune
  * times each shape on every level of the grid, in FP32 (mixed grids) and FP64,
  * and keeps the fastest per (level dimensions, moduli kind, precision) in a
  * process-wide table used by every later launch.  times_ms (optional) receives
- * the FP32 timings of the finest level, one per shape.  The table can be saved
+ * the FP32 timings of the finest level, one per shape (-1 where a shape does not
+ * apply).  The table can be saved
  * and restored as text (one "nx ny nz kind bytes divc shape" line per entry). */
 int  elas_autotune(elas_grid g, float* times_ms, int ntimes);
 int  elas_autotune_dump(char* buf, int cap);   /* returns the text length */

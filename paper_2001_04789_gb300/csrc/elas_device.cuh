@@ -50,6 +50,24 @@ __device__ __forceinline__ T modv(const Lv<T>& L, int idx) {
     return L.mod[idx];
 }
 
+// ---- rounded arithmetic the compiler never contracts -----------------------------
+// The interior stencil, its diagonal block and the 3x3 solve spell out every
+// multiply-add with these, so the result does not depend on how the compiler fuses
+// operations in a given kernel: every launch shape of the smoother computes
+// identical bits.
+template <typename T> __device__ __forceinline__ T xadd(T a, T b);
+template <typename T> __device__ __forceinline__ T xsub(T a, T b);
+template <typename T> __device__ __forceinline__ T xmul(T a, T b);
+template <typename T> __device__ __forceinline__ T xfma(T a, T b, T c);   // a * b + c, one rounding
+template <> __device__ __forceinline__ float xadd(float a, float b) { return __fadd_rn(a, b); }
+template <> __device__ __forceinline__ float xsub(float a, float b) { return __fsub_rn(a, b); }
+template <> __device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+template <> __device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // ---- Voigt helpers ----------------------------------------------------------
 __host__ __device__ constexpr int voigt(int i, int j) { return i == j ? i : 6 - i - j; }
 __host__ __device__ constexpr int upper(int a, int b) {
@@ -267,70 +285,56 @@ __device__ __forceinline__ T boundary_row(const Lv<T>& L, const U& u, const Node
 
 // ---- interior fast path ------------------------------------------------------------
 // All three rows of D_H u at a node that lies on no boundary plane.
-template <typename T, int KIND, bool HAS_M = false>
-__device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restrict__ u,
-                                              int x, int y, int z, T out[3]) {
-    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int N = L.N;
-    int X[3] = {x - 1, x, x + 1}, Y[3] = {y - 1, y, y + 1}, Z[3] = {z - 1, z, z + 1};
-    if (L.per[0]) { if (X[0] < 0) X[0] += nx; if (X[2] >= nx) X[2] -= nx; }
-    if (L.per[1]) { if (Y[0] < 0) Y[0] += ny; if (Y[2] >= ny) Y[2] -= ny; }
-    if (L.per[2]) { if (Z[0] < 0) Z[0] += nz; if (Z[2] >= nz) Z[2] -= nz; }
-    const int Ys[3] = {Y[0] * nx, Y[1] * nx, Y[2] * nx};
-    const int Zs[3] = {Z[0] * nx * ny, Z[1] * nx * ny, Z[2] * nx * ny};
-#define IDX(dx, dy, dz) (X[(dx) + 1] + Ys[(dy) + 1] + Zs[(dz) + 1])
-    const int p = IDX(0, 0, 0);
-    const int qp[3] = {IDX(1, 0, 0), IDX(0, 1, 0), IDX(0, 0, 1)};
-    const int qm[3] = {IDX(-1, 0, 0), IDX(0, -1, 0), IDX(0, 0, -1)};
-    // pair (j,l) corner indices: ++, +-, -+, --
-    const int cr[3][4] = {
-        {IDX(0, 1, 1), IDX(0, 1, -1), IDX(0, -1, 1), IDX(0, -1, -1)},   // pair (1,2)
-        {IDX(1, 0, 1), IDX(1, 0, -1), IDX(-1, 0, 1), IDX(-1, 0, -1)},   // pair (0,2)
-        {IDX(1, 1, 0), IDX(1, -1, 0), IDX(-1, 1, 0), IDX(-1, -1, 0)}};  // pair (0,1)
-#undef IDX
+// All three rows of D_H u at a node on no boundary plane, through accessors:
+// ua(k, dx, dy, dz) = u_k at the offset node, ca(c, dx, dy, dz) = moduli plane c there
+// (offsets are compile-time after unrolling; p = linear index for the optional
+// precomputed modulus divergence).
+template <typename T, int KIND, bool HAS_M, class UA, class CA>
+__device__ __forceinline__ void interior_rows_core(const Lv<T>& L, const UA& ua, const CA& ca, int p, T out[3]) {
     T G[3][3];      // du_k/dx_l
     T Hd[3][3];     // d2u_k/dx_j2
     T Hm[3][3];     // mixed: Hm[k][pair]
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const T* uk = u + k * N;
-        const T u0 = uk[p];
+        const T u0 = ua(k, 0, 0, 0);
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
-            const T up = uk[qp[l]], um = uk[qm[l]];
-            G[k][l] = (up - um) * L.inv2h[l];
-            Hd[k][l] = (up - T(2) * u0 + um) * L.invh2[l];
+            const T up = ua(k, l == 0, l == 1, l == 2), um = ua(k, -(l == 0), -(l == 1), -(l == 2));
+            G[k][l] = xmul(xsub(up, um), L.inv2h[l]);
+            Hd[k][l] = xmul(xadd(xfma(T(-2), u0, up), um), L.invh2[l]);
         }
-#pragma unroll
-        for (int pr = 0; pr < 3; ++pr)
-            Hm[k][pr] = (uk[cr[pr][0]] - uk[cr[pr][1]] - uk[cr[pr][2]] + uk[cr[pr][3]]) * L.inv4hh[pr];
+        auto mixed = [&](T pp, T pm, T mp, T mm, T s) { return xmul(xadd(xsub(xsub(pp, pm), mp), mm), s); };
+        Hm[k][0] = mixed(ua(k, 0, 1, 1), ua(k, 0, 1, -1), ua(k, 0, -1, 1), ua(k, 0, -1, -1), L.inv4hh[0]);
+        Hm[k][1] = mixed(ua(k, 1, 0, 1), ua(k, 1, 0, -1), ua(k, -1, 0, 1), ua(k, -1, 0, -1), L.inv4hh[1]);
+        Hm[k][2] = mixed(ua(k, 1, 1, 0), ua(k, 1, -1, 0), ua(k, -1, 1, 0), ua(k, -1, -1, 0), L.inv4hh[2]);
     }
     // engineering strain of the gradient, Voigt order
-    const T e[6] = {G[0][0], G[1][1], G[2][2], G[1][2] + G[2][1], G[0][2] + G[2][0], G[0][1] + G[1][0]};
+    const T e[6] = {G[0][0], G[1][1], G[2][2], xadd(G[1][2], G[2][1]), xadd(G[0][2], G[2][0]),
+                    xadd(G[0][1], G[1][0])};
 #pragma unroll
     for (int i = 0; i < 3; ++i) out[i] = T(0);
     if (KIND == 2) {
         // isotropic: C_ijkl = lam d_ij d_kl + mu (d_ik d_jl + d_il d_jk)
-        const T lam = modv(L, p), mu = modv(L, N + p);
+        const T lam = ca(0, 0, 0, 0), mu = ca(1, 0, 0, 0);
         T dlam[3], dmu[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            dlam[j] = (modv(L, qp[j]) - modv(L, qm[j])) * L.inv2h[j];
-            dmu[j] = (modv(L, N + qp[j]) - modv(L, N + qm[j])) * L.inv2h[j];
+            dlam[j] = xmul(xsub(ca(0, j == 0, j == 1, j == 2), ca(0, -(j == 0), -(j == 1), -(j == 2))), L.inv2h[j]);
+            dmu[j] = xmul(xsub(ca(1, j == 0, j == 1, j == 2), ca(1, -(j == 0), -(j == 1), -(j == 2))), L.inv2h[j]);
         }
-        const T div = G[0][0] + G[1][1] + G[2][2];
+        const T div = xadd(xadd(G[0][0], G[1][1]), G[2][2]);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             // (d_j C_ijkl) G_kl = dlam_i div + dmu_j (G_ij + G_ji)
-            T t1 = dlam[i] * div;
+            T t1 = xmul(dlam[i], div);
 #pragma unroll
-            for (int j = 0; j < 3; ++j) t1 += dmu[j] * (G[i][j] + G[j][i]);
+            for (int j = 0; j < 3; ++j) t1 = xfma(dmu[j], xadd(G[i][j], G[j][i]), t1);
             // C_ijkl H_k,jl = lam d_i(div) + mu (lap u_i + d_i div)
-            T lap = Hd[i][0] + Hd[i][1] + Hd[i][2];
-            T graddiv = T(0);
+            const T lap = xadd(xadd(Hd[i][0], Hd[i][1]), Hd[i][2]);
+            T graddiv = (i == 0) ? Hd[0][0] : Hm[0][pair_index(i, 0)];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) graddiv += (k == i) ? Hd[k][k] : Hm[k][pair_index(i, k)];
-            out[i] = t1 + (lam + mu) * graddiv + mu * lap;
+            for (int k = 1; k < 3; ++k) graddiv = xadd(graddiv, (k == i) ? Hd[k][k] : Hm[k][pair_index(i, k)]);
+            out[i] = xfma(mu, lap, xfma(xadd(lam, mu), graddiv, t1));
         }
     } else {
         // second derivatives grouped by Voigt pair b = (k,l):
@@ -346,7 +350,7 @@ __device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restric
                 const int l = (b == 5) ? 1 : 2;
                 const T hkl = (j == l) ? Hd[k][j] : Hm[k][pair_index(j, l)];
                 const T hlk = (j == k) ? Hd[l][j] : Hm[l][pair_index(j, k)];
-                S[j][b] = hkl + hlk;
+                S[j][b] = xadd(hkl, hlk);
             }
         }
 #pragma unroll
@@ -355,7 +359,7 @@ __device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restric
             if (HAS_M) {
                 // term 1: M_iV e_V
 #pragma unroll
-                for (int V = 0; V < 6; ++V) acc += L.divc[(i * 6 + V) * N + p] * e[V];
+                for (int V = 0; V < 6; ++V) acc = xfma(L.divc[(i * 6 + V) * L.N + p], e[V], acc);
             }
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -364,17 +368,36 @@ __device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restric
                     // term 1: (d_j C_(ij)V) e_V
 #pragma unroll
                     for (int V = 0; V < 6; ++V) {
-                        const int base = upper(I, V) * N;
-                        acc += (modv(L, base + qp[j]) - modv(L, base + qm[j])) * L.inv2h[j] * e[V];
+                        const int cmp = upper(I, V);
+                        const T dC = xmul(xsub(ca(cmp, j == 0, j == 1, j == 2), ca(cmp, -(j == 0), -(j == 1), -(j == 2))),
+                                          L.inv2h[j]);
+                        acc = xfma(dC, e[V], acc);
                     }
                 }
                 // term 2: C_(ij)b S_jb
 #pragma unroll
-                for (int b = 0; b < 6; ++b) acc += modv(L, upper(I, b) * N + p) * S[j][b];
+                for (int b = 0; b < 6; ++b) acc = xfma(ca(upper(I, b), 0, 0, 0), S[j][b], acc);
             }
             out[i] = acc;
         }
     }
+}
+
+
+template <typename T, int KIND, bool HAS_M = false>
+__device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restrict__ u,
+                                              int x, int y, int z, T out[3]) {
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int N = L.N;
+    int X[3] = {x - 1, x, x + 1}, Y[3] = {y - 1, y, y + 1}, Z[3] = {z - 1, z, z + 1};
+    if (L.per[0]) { if (X[0] < 0) X[0] += nx; if (X[2] >= nx) X[2] -= nx; }
+    if (L.per[1]) { if (Y[0] < 0) Y[0] += ny; if (Y[2] >= ny) Y[2] -= ny; }
+    if (L.per[2]) { if (Z[0] < 0) Z[0] += nz; if (Z[2] >= nz) Z[2] -= nz; }
+    const int Ys[3] = {Y[0] * nx, Y[1] * nx, Y[2] * nx};
+    const int Zs[3] = {Z[0] * nx * ny, Z[1] * nx * ny, Z[2] * nx * ny};
+    auto ua = [&](int k, int dx, int dy, int dz) { return u[k * N + X[dx + 1] + Ys[dy + 1] + Zs[dz + 1]]; };
+    auto ca = [&](int c, int dx, int dy, int dz) { return modv(L, c * N + X[dx + 1] + Ys[dy + 1] + Zs[dz + 1]); };
+    interior_rows_core<T, KIND, HAS_M>(L, ua, ca, X[1] + Ys[1] + Zs[1], out);
 }
 
 // Diagonal 3x3 block of an interior node: B_ik = -2 sum_j C_ijkj / h_j^2.
@@ -387,7 +410,33 @@ __device__ __forceinline__ void interior_block(const Lv<T>& L, int p, T B[3][3])
             T acc = T(0);
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                if (Cnz<T, KIND>(i, j, k, j)) acc += Cm<T, KIND>(L, p, i, j, k, j) * (T(-2) * L.invh2[j]);
+                if (Cnz<T, KIND>(i, j, k, j)) acc = xfma(Cm<T, KIND>(L, p, i, j, k, j), T(-2) * L.invh2[j], acc);
+            B[i][k] = acc;
+        }
+}
+
+// The same block through a centre-moduli accessor ca(c, 0, 0, 0).
+template <typename T, int KIND, class CA>
+__device__ __forceinline__ void interior_block_acc(const Lv<T>& L, const CA& ca, T B[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T acc = T(0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                T c;
+                if (KIND == 2) {
+                    c = T(0);
+                    if (i == j && k == j) c = xadd(c, ca(0, 0, 0, 0));
+                    if (i == k) c = xadd(c, ca(1, 0, 0, 0));
+                    if (i == j && j == k) c = xadd(c, ca(1, 0, 0, 0));
+                    if (!Cnz<T, KIND>(i, j, k, j)) continue;
+                } else {
+                    c = ca(upper(voigt(i, j), voigt(k, j)), 0, 0, 0);
+                }
+                acc = xfma(c, T(-2) * L.invh2[j], acc);
+            }
             B[i][k] = acc;
         }
 }
@@ -582,21 +631,22 @@ __device__ __forceinline__ void face_node(const Lv<T>& L, const T* __restrict__ 
 // Solve B d = r for a 3x3 block (explicit inverse by cofactors).
 template <typename T>
 __device__ __forceinline__ void solve3(const T B[3][3], const T r[3], T d[3]) {
-    const T c00 = B[1][1] * B[2][2] - B[1][2] * B[2][1];
-    const T c01 = B[1][2] * B[2][0] - B[1][0] * B[2][2];
-    const T c02 = B[1][0] * B[2][1] - B[1][1] * B[2][0];
-    const T det = B[0][0] * c00 + B[0][1] * c01 + B[0][2] * c02;
+    auto cof = [](T a, T b, T c, T e) { return xsub(xmul(a, b), xmul(c, e)); };   // a b - c e
+    const T c00 = cof(B[1][1], B[2][2], B[1][2], B[2][1]);
+    const T c01 = cof(B[1][2], B[2][0], B[1][0], B[2][2]);
+    const T c02 = cof(B[1][0], B[2][1], B[1][1], B[2][0]);
+    const T det = xfma(B[0][2], c02, xfma(B[0][1], c01, xmul(B[0][0], c00)));
     const T id = T(1) / det;
-    const T i00 = c00 * id, i10 = c01 * id, i20 = c02 * id;
-    const T i01 = (B[0][2] * B[2][1] - B[0][1] * B[2][2]) * id;
-    const T i11 = (B[0][0] * B[2][2] - B[0][2] * B[2][0]) * id;
-    const T i21 = (B[0][1] * B[2][0] - B[0][0] * B[2][1]) * id;
-    const T i02 = (B[0][1] * B[1][2] - B[0][2] * B[1][1]) * id;
-    const T i12 = (B[0][2] * B[1][0] - B[0][0] * B[1][2]) * id;
-    const T i22 = (B[0][0] * B[1][1] - B[0][1] * B[1][0]) * id;
-    d[0] = i00 * r[0] + i01 * r[1] + i02 * r[2];
-    d[1] = i10 * r[0] + i11 * r[1] + i12 * r[2];
-    d[2] = i20 * r[0] + i21 * r[1] + i22 * r[2];
+    const T i00 = xmul(c00, id), i10 = xmul(c01, id), i20 = xmul(c02, id);
+    const T i01 = xmul(cof(B[0][2], B[2][1], B[0][1], B[2][2]), id);
+    const T i11 = xmul(cof(B[0][0], B[2][2], B[0][2], B[2][0]), id);
+    const T i21 = xmul(cof(B[0][1], B[2][0], B[0][0], B[2][1]), id);
+    const T i02 = xmul(cof(B[0][1], B[1][2], B[0][2], B[1][1]), id);
+    const T i12 = xmul(cof(B[0][2], B[1][0], B[0][0], B[1][2]), id);
+    const T i22 = xmul(cof(B[0][0], B[1][1], B[0][1], B[1][0]), id);
+    d[0] = xfma(i02, r[2], xfma(i01, r[1], xmul(i00, r[0])));
+    d[1] = xfma(i12, r[2], xfma(i11, r[1], xmul(i10, r[0])));
+    d[2] = xfma(i22, r[2], xfma(i21, r[1], xmul(i20, r[0])));
 }
 
 // ---- rigid-body modes and the equilibrating load -------------------------------------
@@ -648,14 +698,14 @@ __device__ __forceinline__ double null_vec(const NullInfo& nf, int q, int c, con
 template <typename T>
 __device__ __forceinline__ T rigid_load(const NullInfo& nf, const double* __restrict__ a, int comp, const int c[3]) {
     const float* at = (const float*)(a + kLoadFloatOffset);
-    const float d0 = nf.off32[0] + nf.h32[0] * float(c[0]);
-    const float d1 = nf.off32[1] + nf.h32[1] * float(c[1]);
-    const float d2 = nf.off32[2] + nf.h32[2] * float(c[2]);
+    const float d0 = xfma(nf.h32[0], float(c[0]), nf.off32[0]);
+    const float d1 = xfma(nf.h32[1], float(c[1]), nf.off32[1]);
+    const float d2 = xfma(nf.h32[2], float(c[2]), nf.off32[2]);
     const float w0 = at[3], w1 = at[4], w2 = at[5];
     float v;
-    if (comp == 0) v = at[0] + (w1 * d2 - w2 * d1);
-    else if (comp == 1) v = at[1] + (w2 * d0 - w0 * d2);
-    else v = at[2] + (w0 * d1 - w1 * d0);
+    if (comp == 0) v = xadd(at[0], xsub(xmul(w1, d2), xmul(w2, d1)));
+    else if (comp == 1) v = xadd(at[1], xsub(xmul(w2, d0), xmul(w0, d2)));
+    else v = xadd(at[2], xsub(xmul(w0, d1), xmul(w1, d0)));
     return T(v);
 }
 

@@ -31,7 +31,7 @@ void count_launch(int n = 1);
 
 // Interior smoother launch variants (block size, minimum blocks per SM) and the
 // autotuner that picks one per level shape and precision.
-constexpr int kNumSweepVariants = 5;
+constexpr int kNumSweepVariants = 7;
 constexpr int kDefaultSweepVariant = 0;
 template <typename T>
 int tune_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, cudaStream_t s, float* ms_out);

@@ -337,12 +337,170 @@ __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* _
     const int c[3] = {xa, y, z};
     for (int i = 0; i < 3; ++i) {
         T fi = f[i * N + p];
-        if (lam) fi -= rigid_load<T>(nf, lam, i, c);
-        r[i] = fi - v[i];
+        if (lam) fi = xsub(fi, rigid_load<T>(nf, lam, i, c));
+        r[i] = xsub(fi, v[i]);
     }
     interior_block<T, KIND>(L, p, B);
     solve3(B, r, d);
-    for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + d[i];
+    for (int i = 0; i < 3; ++i) uo[i * N + p] = xadd(u[i * N + p], d[i]);
+}
+
+// ---- shared-memory tiled FP32 interior smoother --------------------------------------
+// A block owns a 32 x TY tile of interior (x, y) nodes and marches through a chunk of
+// interior z planes.  Moduli planes with a one-node x/y halo rotate through three shared
+// buffers and displacement planes through four; plane z+2 streams in (cp.async) while
+// plane z is computed, and the moduli of plane z-1 that the z-derivative needs are
+// copied to registers before their buffer is refilled.  Each warp covers 16 x-pairs of
+// two neighbouring rows: their active nodes have opposite x parity, so with an even row
+// stride every shared load of the warp falls on 32 distinct banks.  The arithmetic is
+// the same inlined stencil as the untiled kernel (same operations, same order).
+constexpr int kTileX = 32;             // interior nodes per tile row
+constexpr int kTileS = kTileX + 2;     // shared row stride (with halo), even
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int KIND, int TY>
+struct TiledShape {
+    static constexpr int KP = (KIND == 2) ? 2 : 21;
+    static constexpr int R = TY + 2;                   // rows with halo
+    static constexpr int PLANE = R * kTileS;           // one component of one plane
+    static constexpr int CPL = KP * PLANE;             // floats per moduli plane
+    static constexpr int UPL = 3 * PLANE;              // floats per displacement plane
+    static constexpr int NPOS = (PLANE + 16 * TY - 1) / (16 * TY);   // positions per thread
+    static constexpr size_t SMEM = sizeof(float) * (3 * CPL + 4 * UPL);
+};
+
+template <int KIND, int TY>
+__global__ void __launch_bounds__(16 * TY, (TY <= 8) ? 2 : 1)
+    k_half_sweep_tiled(Lv<float> L, const float* __restrict__ u, float* __restrict__ uo,
+                       const float* __restrict__ f, int colour, NullInfo nf, const double* __restrict__ lam,
+                       int zlen) {
+    using S = TiledShape<KIND, TY>;
+    constexpr int KP = S::KP, R = S::R, PLANE = S::PLANE, CPL = S::CPL, UPL = S::UPL, NPOS = S::NPOS;
+    constexpr int NT = 16 * TY;
+    extern __shared__ __align__(16) float sm[];
+    float* const Cs = sm;                  // [3][KP][R][kTileS]
+    float* const Us = sm + 3 * CPL;        // [4][3][R][kTileS]
+    if (L.active && *L.active == 0) return;
+    int lo[3], cnt[3];
+    interior_box(L, lo, cnt);
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2], N = L.N;
+    const int xt0 = lo[0] + kTileX * blockIdx.x;
+    const int yt0 = lo[1] + TY * blockIdx.y;
+    const int z0 = lo[2] + zlen * blockIdx.z;
+    const int zend = min(z0 + zlen, lo[2] + cnt[2]);
+    if (z0 >= zend) return;
+    const int xend = lo[0] + cnt[0], yend = lo[1] + cnt[1];
+
+    // plane positions (row, column) this thread copies: in-plane global offset or -1
+    int goff[NPOS];
+#pragma unroll
+    for (int j = 0; j < NPOS; ++j) {
+        const int pos = threadIdx.x + NT * j;
+        goff[j] = -1;
+        if (pos < PLANE) {
+            int x = xt0 - 1 + pos % kTileS, y = yt0 - 1 + pos / kTileS;
+            if (x <= xend && y <= yend) {
+                if (x < 0) x += nx;
+                if (x >= nx) x -= nx;
+                if (y < 0) y += ny;
+                if (y >= ny) y -= ny;
+                goff[j] = x + nx * y;
+            }
+        }
+    }
+    auto plane_base = [&](int z) -> int {
+        if (z < 0) z += nz;
+        if (z >= nz) z -= nz;
+        return z * nx * ny;
+    };
+    // enqueue moduli and displacement of plane z into ring slot j (moduli: j % 3, u: j % 4)
+    auto load_plane = [&](int z, int j) {
+        const int zb = plane_base(z);
+        float* cd = Cs + (j % 3) * CPL;
+        float* ud = Us + (j & 3) * UPL;
+#pragma unroll
+        for (int q = 0; q < NPOS; ++q) {
+            const int pos = threadIdx.x + NT * q;
+            if (goff[q] < 0) continue;
+            const float* cs = L.mod + zb + goff[q];
+#pragma unroll 7
+            for (int c = 0; c < KP; ++c) cp_async4(cd + c * PLANE + pos, cs + (size_t)c * N);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cp_async4(ud + k * PLANE + pos, u + (size_t)k * N + zb + goff[q]);
+        }
+        cp_async_commit();
+    };
+
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int y = yt0 + ty;
+    const int x0 = xt0 + 2 * tx;
+    const int yl = ty + 1;
+
+    // prologue: planes z0-1, z0, z0+1 in slots 0, 1, 2
+    load_plane(z0 - 1, 0);
+    load_plane(z0, 1);
+    load_plane(z0 + 1, 2);
+
+    for (int z = z0; z < zend; ++z) {
+        const int j = z - z0 + 1;          // ring index of the current plane
+        const int xa = x0 + ((x0 + y + z + colour) & 1);
+        const int xi = (xa == x0) ? x0 + 1 : x0;
+        const int xla = xa - xt0 + 1, xli = xi - xt0 + 1;
+        cp_async_wait_all();
+        __syncthreads();
+        // moduli of plane z-1 at the active node, before its slot is refilled
+        float cprev[KP];
+        {
+            const float* cb = Cs + ((j + 2) % 3) * CPL + yl * kTileS + xla;
+#pragma unroll
+            for (int c = 0; c < KP; ++c) cprev[c] = cb[c * PLANE];
+        }
+        __syncthreads();
+        if (z + 2 <= zend) load_plane(z + 2, j + 2);
+
+        const float* const Cz = Cs + (j % 3) * CPL + yl * kTileS;
+        const float* const Cn = Cs + ((j + 1) % 3) * CPL + yl * kTileS + xla;
+        const float* const Um = Us + ((j + 3) & 3) * UPL + yl * kTileS + xla;
+        const float* const U0 = Us + (j & 3) * UPL + yl * kTileS;
+        const float* const Up = Us + ((j + 1) & 3) * UPL + yl * kTileS + xla;
+        const int row = nx * (y + ny * z);
+        if (y < yend && xi < xend) {
+            const int q = xi + row;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) uo[(size_t)k * N + q] = U0[k * PLANE + xli];
+        }
+        if (y < yend && xa < xend) {
+            auto ua = [&](int k, int dx, int dy, int dz) -> float {
+                const float* b = dz < 0 ? Um : (dz > 0 ? Up : U0 + xla);
+                return b[k * PLANE + dy * kTileS + dx];
+            };
+            auto ca = [&](int c, int dx, int dy, int dz) -> float {
+                if (dz < 0) return cprev[c];
+                if (dz > 0) return Cn[c * PLANE];
+                return Cz[c * PLANE + dy * kTileS + xla + dx];
+            };
+            const int p = xa + row;
+            float v[3];
+            interior_rows_core<float, KIND, false>(L, ua, ca, p, v);
+            float r[3], B[3][3], d[3];
+            const int c3[3] = {xa, y, z};
+            for (int i = 0; i < 3; ++i) {
+                float fi = f[(size_t)i * N + p];
+                if (lam) fi = xsub(fi, rigid_load<float>(nf, lam, i, c3));
+                r[i] = xsub(fi, v[i]);
+            }
+            interior_block_acc<float, KIND>(L, ca, B);
+            solve3(B, r, d);
+            for (int i = 0; i < 3; ++i) uo[(size_t)i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
+        }
+    }
+    cp_async_wait_all();
 }
 
 // Red-black smoother, edge and corner nodes: one warp per node; lanes 0-8 compute
@@ -1208,7 +1366,11 @@ void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf,
 // ---- launch variants of the interior smoother and their tuning table -----------------
 // (threads per block, minimum resident blocks per SM) pairs; the second number
 // bounds the registers per thread and so trades registers for resident warps.
-static const int kSweepVariants[kNumSweepVariants][2] = {{256, 1}, {256, 2}, {256, 3}, {256, 4}, {128, 8}};
+// Variants 5 and 6 are the shared-memory tiled kernel (32 x 16 and 32 x 8 tiles, FP32
+// levels with FP32 moduli only); their pair holds (threads, resident blocks per SM).
+static const int kSweepVariants[kNumSweepVariants][2] = {{256, 1}, {256, 2}, {256, 3}, {256, 4}, {128, 8},
+                                                         {256, 1}, {128, 2}};
+constexpr int kFirstTiledVariant = 5;
 
 static std::mutex g_tune_mu;
 static std::map<std::array<int, 6>, int> g_tune;
@@ -1266,9 +1428,72 @@ int tune_table_load(const char* text) {
     return count;
 }
 
+static int sm_count() {
+    static int n = [] {
+        int dev = 0, c = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        return c > 0 ? c : 1;
+    }();
+    return n;
+}
+
+// z planes per block of the tiled smoother: the chunking with the fewest plane steps
+// per SM, counting whole waves of resident blocks and two prologue planes per block.
+static int tiled_zlen(int columns, int nzi, int per_sm) {
+    const long slots = (long)sm_count() * per_sm;
+    int best = nzi;
+    long best_cost = -1;
+    for (int zc = 1; zc <= nzi; ++zc) {
+        const int zl = (nzi + zc - 1) / zc;
+        if ((nzi + zl - 1) / zl != zc) continue;
+        const long blocks = (long)columns * zc;
+        const long cost = ((blocks + slots - 1) / slots) * (zl + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = zl;
+        }
+    }
+    return best;
+}
+
+template <int KIND, int TY>
+static void launch_tiled(const Lv<float>& L, const float* u_in, float* u_out, const float* f, int colour,
+                         const NullInfo& nfv, const double* lam, cudaStream_t s) {
+    using S = TiledShape<KIND, TY>;
+    static const bool attr = [] {
+        cudaFuncSetAttribute(k_half_sweep_tiled<KIND, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)S::SMEM);
+        return true;
+    }();
+    (void)attr;
+    int cnt[3];
+    for (int d = 0; d < 3; ++d) cnt[d] = L.per[d] ? L.n[d] : L.n[d] - 2;
+    const int gx = (cnt[0] + kTileX - 1) / kTileX, gy = (cnt[1] + TY - 1) / TY;
+    const int zl = tiled_zlen(gx * gy, cnt[2], TY <= 8 ? 2 : 1);
+    const dim3 grid(gx, gy, (cnt[2] + zl - 1) / zl);
+    k_half_sweep_tiled<KIND, TY><<<grid, 16 * TY, S::SMEM, s>>>(L, u_in, u_out, f, colour, nfv, lam, zl);
+}
+
+// The tiled kernel reads FP32 moduli planes directly: not for FP64 levels, FP16 moduli
+// or the precomputed modulus divergence.
+template <typename T>
+static bool variant_ok(const Lv<T>& L, int v) {
+    if (v < kFirstTiledVariant) return true;
+    return sizeof(T) == 4 && !L.modh && !L.divc;
+}
+
 template <typename T, int KIND, bool HM>
 void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
                        const NullInfo& nfv, const double* lam, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4 && !HM) {
+        if (v >= kFirstTiledVariant && variant_ok(L, v)) {
+            if (v == kFirstTiledVariant) launch_tiled<KIND, 16>(L, u_in, u_out, f, colour, nfv, lam, s);
+            else launch_tiled<KIND, 8>(L, u_in, u_out, f, colour, nfv, lam, s);
+            return;
+        }
+    }
+    if (v >= kFirstTiledVariant) v = kDefaultSweepVariant;
     const int bs = kSweepVariants[v][0];
     const int nb = (int)((np + bs - 1) / bs);
     switch (v) {
@@ -1293,6 +1518,10 @@ int tune_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, cudaStream_t
     int best = kDefaultSweepVariant;
     float best_ms = 1e30f;
     for (int v = 0; v < kNumSweepVariants; ++v) {
+        if (!variant_ok(L, v)) {
+            if (ms_out) ms_out[v] = -1.f;
+            continue;
+        }
         auto run = [&]() {
             if (L.K == 2) sweep_int_variant<T, 2, false>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
             else if (L.divc) sweep_int_variant<T, 21, true>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);

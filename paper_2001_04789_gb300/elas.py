@@ -377,15 +377,21 @@ class Grid:
 
     def autotune(self):
         """Pick the fastest smoother launch shape per level; returns the finest
-        level's FP32 timings (ms) per shape."""
-        t = (C.c_float * 8)()
-        self.ctx.check(lib().elas_autotune(self.h, t, 8))
-        return list(t[:5])
+        level's FP32 timings (ms) per shape, -1 for a shape that does not apply."""
+        t = (C.c_float * NUM_SWEEP_VARIANTS)()
+        self.ctx.check(lib().elas_autotune(self.h, t, NUM_SWEEP_VARIANTS))
+        return list(t)
 
     def close(self):
         if getattr(self, "h", None):
             lib().elas_grid_destroy(self.h)
             self.h = None
+
+
+# interior smoother launch shapes: 0-4 untiled (threads, min blocks per SM) = (256,1),
+# (256,2), (256,3), (256,4), (128,8); 5-6 shared-memory tiled, 32x16 and 32x8 tiles
+NUM_SWEEP_VARIANTS = 7
+TILED_VARIANTS = (5, 6)
 
 
 def autotune_dump():

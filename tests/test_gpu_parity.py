@@ -250,7 +250,7 @@ def test_autotuned_launch_shapes_do_not_change_results(E, ctx):
     before = g.solve(precision=E.MIXED, rel_tol=0.0, fixed_cycles=3)
     ub = g.displacement()
     times = g.autotune()
-    assert len(times) == 5 and all(t > 0 for t in times)
+    assert len(times) == E.NUM_SWEEP_VARIANTS and all(t > 0 for t in times)
     assert len(E.autotune_dump().strip().splitlines()) >= 1
     after = g.solve(precision=E.MIXED, rel_tol=0.0, fixed_cycles=3)
     assert np.array_equal(ub, g.displacement())
@@ -289,4 +289,64 @@ def test_half_moduli_v_cycle_reaches_the_oracle_solution(E, ctx, case):
     assert info["status"] == 0 and info["rel_residual"] <= 1e-8
     ref, _ = MG.solve(p, tol=1e-8, max_cycles=300)
     assert rel_err(g.displacement(), ref) < 1e-7
+    g.close()
+
+
+def force_variant(E, p, v):
+    """Tuning-table entries that pin interior smoother shape v on every FP32 level."""
+    n = list(p.n)
+    lines = []
+    for _ in range(12):
+        lines.append(f"{n[0]} {n[1]} {n[2]} {21 if p.moduli_kind == M.MODULI_GEN21 else 2} 4 0 {v}")
+        if min(n) < 5:
+            break
+        n = [(m - 1) // 2 + 1 if not per else m // 2 for m, per in zip(n, p.periodic)]
+    assert E.autotune_load("\n".join(lines)) == len(lines)
+
+
+TILE_CASES = {
+    # interior 68 x 35 x 21: two full 32-wide tiles and a ragged one, ragged rows, z chunks
+    "gen21_ragged": lambda: mixed_bc_problem(n=(70, 37, 23), kind=M.MODULI_GEN21),
+    "iso_ragged": lambda: mixed_bc_problem(n=(41, 19, 13), kind=M.MODULI_ISO),
+    "periodic_iso": lambda: periodic_problem(32),
+    "polycrystal": lambda: M.polycrystal(33, grains=5, seed=2),
+}
+
+
+@pytest.mark.parametrize("case", list(TILE_CASES))
+def test_tiled_smoother_is_bitwise_equal_to_untiled(E, ctx, case):
+    """The shared-memory tiled interior half-sweep runs the same arithmetic as the
+    one-thread-per-pair kernel: a sweep from the same state gives identical bits."""
+    p = TILE_CASES[case]()
+    g = E.grid_from_problem(ctx, p, mixed=True, max_levels=1)
+    rng = np.random.default_rng(5)
+    u = rng.normal(size=(3,) + g.shape)
+    f = rng.normal(size=(3,) + g.shape) * 100
+    out = {}
+    for v in range(E.NUM_SWEEP_VARIANTS):
+        force_variant(E, p, v)
+        u32 = dev(u, torch.float32)
+        g.op_sweep(0, E.MIXED, u32, dev(f, torch.float32))
+        out[v] = u32.cpu().numpy()
+    for v in range(1, E.NUM_SWEEP_VARIANTS):
+        assert np.array_equal(out[v], out[0]), f"shape {v}"
+    force_variant(E, p, 0)
+    g.close()
+
+
+@pytest.mark.parametrize("case", ["periodic_iso", "polycrystal"])
+def test_tiled_smoother_mixed_solve_matches(E, ctx, case):
+    """Whole mixed solves (equilibrating load included on the periodic cell) with the
+    tiled smoother on every FP32 level repeat the untiled residual history exactly."""
+    p = TILE_CASES[case]()
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    hist = {}
+    for v in (0,) + E.TILED_VARIANTS:
+        force_variant(E, p, v)
+        info = g.solve(precision=E.MIXED, rel_tol=0.0, fixed_cycles=4, inner_cycles=2)
+        hist[v] = (info["rel_history"], g.displacement())
+    for v in E.TILED_VARIANTS:
+        assert hist[v][0] == hist[0][0]
+        assert np.array_equal(hist[v][1], hist[0][1])
+    force_variant(E, p, 0)
     g.close()
