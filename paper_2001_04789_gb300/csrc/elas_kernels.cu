@@ -256,64 +256,53 @@ __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restri
     }
 }
 
+// Residual bodies: one interior node per thread, one edge/corner node per warp, one
+// face node per thread; each adds its node's contributions to the thread's sums.
 template <typename T, typename TR, int KIND, bool NORM, bool HM>
-__global__ void __launch_bounds__(kBlock) k_residual_int(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
-                                                        NullInfo nf, const double* __restrict__ lam,
-                                                        TR* __restrict__ r, double* __restrict__ partials) {
-    if (L.active && *L.active == 0) return;
+__device__ __forceinline__ void residual_int_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
+                                                  const NullInfo& nf, const double* __restrict__ lam,
+                                                  TR* __restrict__ r, int t, double acc[7]) {
     int lo[3], cnt[3];
     interior_box(L, lo, cnt);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (t < cnt[0] * cnt[1] * cnt[2]) {
-        const int c[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
-        T v[3];
-        interior_rows<T, KIND, HM>(L, u, c[0], c[1], c[2], v);
-        const int types[3] = {ROW_INTERIOR, ROW_INTERIOR, ROW_INTERIOR};
-        residual_store<T, TR, NORM>(L, f, nf, lam, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
-    }
-    if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
+    if (t >= cnt[0] * cnt[1] * cnt[2]) return;
+    const int c[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
+    T v[3];
+    interior_rows<T, KIND, HM>(L, u, c[0], c[1], c[2], v);
+    const int types[3] = {ROW_INTERIOR, ROW_INTERIOR, ROW_INTERIOR};
+    residual_store<T, TR, NORM>(L, f, nf, lam, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
 }
 
 template <typename T, typename TR, int KIND, bool NORM>
-__global__ void __launch_bounds__(kBlock) k_residual_bnd(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
-                                                        NullInfo nf, const double* __restrict__ lam,
-                                                        TR* __restrict__ r, double* __restrict__ partials) {
-    if (L.active && *L.active == 0) return;
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (w < L.nbnd) {
-        const int p = L.bnodes[w];
-        int c[3];
-        coords_of(p, L.n, c);
-        const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-        int types[3];
-        for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
-        T val = T(0);
-        if (lane < 3) {
-            UField<T> uf{u, L.N, L.n[0], L.n[1]};
-            val = boundary_row<T, KIND>(L, uf, ni, lane, types[lane]);
-        }
-        T v[3];
-        for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, i);
-        if (lane == 0) residual_store<T, TR, NORM>(L, f, nf, lam, c, p, types, v, r, acc);
+__device__ __forceinline__ void residual_bnd_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
+                                                  const NullInfo& nf, const double* __restrict__ lam,
+                                                  TR* __restrict__ r, int w, int lane, double acc[7]) {
+    if (w >= L.nbnd) return;   // whole warp
+    const int p = L.bnodes[w];
+    int c[3];
+    coords_of(p, L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    int types[3];
+    for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
+    T val = T(0);
+    if (lane < 3) {
+        UField<T> uf{u, L.N, L.n[0], L.n[1]};
+        val = boundary_row<T, KIND>(L, uf, ni, lane, types[lane]);
     }
-    if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
+    T v[3];
+    for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, i);
+    if (lane == 0) residual_store<T, TR, NORM>(L, f, nf, lam, c, p, types, v, r, acc);
 }
 
 // Red-black smoother, interior nodes: each thread owns the x-pair (x0, x0+1) of the
 // interior box, updates the one of the active colour and copies the other; every
 // row uses the values from before the half-sweep (Jacobi within the colour).
-template <typename T, int KIND, bool HM, int BS, int MINB>
-__global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
-                                                          const T* __restrict__ f, int colour, NullInfo nf,
-                                                          const double* __restrict__ lam) {
-    if (L.active && *L.active == 0) return;
+template <typename T, int KIND, bool HM>
+__device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restrict__ u, T* __restrict__ uo,
+                                                const T* __restrict__ f, int colour, const NullInfo& nf,
+                                                const double* __restrict__ lam, int t) {
     int lo[3], cnt[3];
     interior_box(L, lo, cnt);
     const int npair = (cnt[0] + 1) >> 1;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= npair * cnt[1] * cnt[2]) return;
     const int m = t % npair;
     const int yz = t / npair;
@@ -506,13 +495,10 @@ __global__ void __launch_bounds__(16 * TY, (TY <= 8) ? 2 : 1)
 // Red-black smoother, edge and corner nodes: one warp per node; lanes 0-8 compute
 // the diagonal block entries, lanes 9-11 the rows, lane 0 solves and writes.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
-                                                          const T* __restrict__ f, int colour, NullInfo nf,
-                                                          const double* __restrict__ lam) {
-    if (L.active && *L.active == 0) return;
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= L.nbnd) return;
+__device__ __forceinline__ void sweep_bnd_body(const Lv<T>& L, const T* __restrict__ u, T* __restrict__ uo,
+                                               const T* __restrict__ f, int colour, const NullInfo& nf,
+                                               const double* __restrict__ lam, int w, int lane) {
+    if (w >= L.nbnd) return;   // whole warp
     const int p = L.bnodes[w];
     const int N = L.N;
     int c[3];
@@ -547,6 +533,15 @@ __global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __r
     }
     solve3(B, r, d);
     for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
+                                                          const T* __restrict__ f, int colour, NullInfo nf,
+                                                          const double* __restrict__ lam) {
+    if (L.active && *L.active == 0) return;
+    sweep_bnd_body<T, KIND>(L, u, uo, f, colour, nf, lam, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                            threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -602,29 +597,24 @@ __global__ void __launch_bounds__(kBlock) k_apply_face(Lv<T> L, const T* __restr
 }
 
 template <typename T, typename TR, int KIND, int A, bool NORM>
-__global__ void __launch_bounds__(kBlock) k_residual_face(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
-                                                         NullInfo nf, const double* __restrict__ load,
-                                                         TR* __restrict__ r, double* __restrict__ partials) {
-    if (L.active && *L.active == 0) return;
+__device__ __forceinline__ void residual_face_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
+                                                   const NullInfo& nf, const double* __restrict__ load,
+                                                   TR* __restrict__ r, int t, double acc[7]) {
     int c[3], side;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (face_coords<T, A>(L, blockIdx.x * blockDim.x + threadIdx.x, c, side)) {
-        int types[3];
-        face_types<T, A>(L, side, types);
-        T v[3], B[3][3];
-        face_node<T, KIND, A>(L, u, c, side, types, v, B, false);
-        residual_store<T, TR, NORM>(L, f, nf, load, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
-    }
-    if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
+    if (!face_coords<T, A>(L, t, c, side)) return;
+    int types[3];
+    face_types<T, A>(L, side, types);
+    T v[3], B[3][3];
+    face_node<T, KIND, A>(L, u, c, side, types, v, B, false);
+    residual_store<T, TR, NORM>(L, f, nf, load, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
 }
 
 template <typename T, int KIND, int A>
-__global__ void __launch_bounds__(kBlock) k_half_sweep_face(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
-                                                           const T* __restrict__ f, int colour, NullInfo nf,
-                                                           const double* __restrict__ load) {
-    if (L.active && *L.active == 0) return;
+__device__ __forceinline__ void sweep_face_body(const Lv<T>& L, const T* __restrict__ u, T* __restrict__ uo,
+                                                const T* __restrict__ f, int colour, const NullInfo& nf,
+                                                const double* __restrict__ load, int t) {
     int c[3], side;
-    if (!face_coords<T, A>(L, blockIdx.x * blockDim.x + threadIdx.x, c, side)) return;
+    if (!face_coords<T, A>(L, t, c, side)) return;
     const int N = L.N;
     const int p = lin(L, c[0], c[1], c[2]);
     if (((c[0] + c[1] + c[2]) & 1) != colour) {
@@ -650,12 +640,73 @@ __global__ void __launch_bounds__(kBlock) k_half_sweep_face(Lv<T> L, const T* __
     for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
 }
 
+template <typename T, int KIND, int A>
+__global__ void __launch_bounds__(kBlock) k_half_sweep_face(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
+                                                           const T* __restrict__ f, int colour, NullInfo nf,
+                                                           const double* __restrict__ load) {
+    if (L.active && *L.active == 0) return;
+    sweep_face_body<T, KIND, A>(L, u, uo, f, colour, nf, load, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 template <typename T, int A>
 inline size_t face_count(const Lv<T>& L) {
     if (L.per[A]) return 0;
     int nf, ns;
     face_extent<T, A>(L, nf, ns);
     return (size_t)2 * nf * ns;
+}
+
+// ---- one launch per half-sweep / residual ---------------------------------------------
+// The grid's first blocks take the edge and corner nodes (a warp each), then the face
+// nodes of directions 0, 1, 2 (a thread each), then the interior.  The boundary blocks
+// are few and latency-bound; issued first, they run alongside the interior blocks
+// instead of as four short launches of their own.  Block ranges are uniform per block.
+struct BndSegs {
+    int e, f0, f1, f2;   // one past the last block of the edge, x-, y- and z-face ranges
+};
+
+template <typename T>
+inline BndSegs bnd_segs(const Lv<T>& L, int bs) {
+    auto nb = [bs](size_t n) { return (int)((n + bs - 1) / bs); };
+    BndSegs g;
+    g.e = nb((size_t)L.nbnd * 32);
+    g.f0 = g.e + nb(face_count<T, 0>(L));
+    g.f1 = g.f0 + nb(face_count<T, 1>(L));
+    g.f2 = g.f1 + nb(face_count<T, 2>(L));
+    return g;
+}
+
+// Red-black smoother, all nodes of one colour (see the bodies above for each kind).
+template <typename T, int KIND, bool HM, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
+                                                          const T* __restrict__ f, int colour, NullInfo nf,
+                                                          const double* __restrict__ lam, BndSegs sg) {
+    if (L.active && *L.active == 0) return;
+    const int b = blockIdx.x, tid = threadIdx.x;
+    if (b < sg.f2) {
+        if (b < sg.e) sweep_bnd_body<T, KIND>(L, u, uo, f, colour, nf, lam, (b * BS + tid) >> 5, tid & 31);
+        else if (b < sg.f0) sweep_face_body<T, KIND, 0>(L, u, uo, f, colour, nf, lam, (b - sg.e) * BS + tid);
+        else if (b < sg.f1) sweep_face_body<T, KIND, 1>(L, u, uo, f, colour, nf, lam, (b - sg.f0) * BS + tid);
+        else sweep_face_body<T, KIND, 2>(L, u, uo, f, colour, nf, lam, (b - sg.f1) * BS + tid);
+        return;
+    }
+    sweep_pair_body<T, KIND, HM>(L, u, uo, f, colour, nf, lam, (b - sg.f2) * BS + tid);
+}
+
+// r = f - load - A u on every node; block partials of sum r^2 and the rigid moments.
+template <typename T, typename TR, int KIND, bool NORM, bool HM>
+__global__ void __launch_bounds__(kBlock) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
+                                                    NullInfo nf, const double* __restrict__ lam,
+                                                    TR* __restrict__ r, double* __restrict__ partials, BndSegs sg) {
+    if (L.active && *L.active == 0) return;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int b = blockIdx.x, tid = threadIdx.x;
+    if (b < sg.e) residual_bnd_body<T, TR, KIND, NORM>(L, u, f, nf, lam, r, (b * kBlock + tid) >> 5, tid & 31, acc);
+    else if (b < sg.f0) residual_face_body<T, TR, KIND, 0, NORM>(L, u, f, nf, lam, r, (b - sg.e) * kBlock + tid, acc);
+    else if (b < sg.f1) residual_face_body<T, TR, KIND, 1, NORM>(L, u, f, nf, lam, r, (b - sg.f0) * kBlock + tid, acc);
+    else if (b < sg.f2) residual_face_body<T, TR, KIND, 2, NORM>(L, u, f, nf, lam, r, (b - sg.f1) * kBlock + tid, acc);
+    else residual_int_body<T, TR, KIND, NORM, HM>(L, u, f, nf, lam, r, (b - sg.f2) * kBlock + tid, acc);
+    if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -1279,23 +1330,6 @@ void launch_faces_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
     else k_apply_face<T, 21, A><<<blocks_for(n), kBlock, 0, s>>>(L, u, out);
 }
 
-template <typename T, typename TR, int A>
-int launch_faces_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo& nfv, const double* load, TR* r,
-                          double* partials, cudaStream_t s) {
-    const size_t n = face_count<T, A>(L);
-    if (!n) return 0;
-    const int nb = blocks_for(n);
-    count_launch();
-    if (partials) {
-        if (L.K == 2) k_residual_face<T, TR, 2, A, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, load, r, partials);
-        else k_residual_face<T, TR, 21, A, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, load, r, partials);
-    } else {
-        if (L.K == 2) k_residual_face<T, TR, 2, A, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, load, r, nullptr);
-        else k_residual_face<T, TR, 21, A, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, load, r, nullptr);
-    }
-    return nb;
-}
-
 template <typename T, int A>
 void launch_faces_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour, const NullInfo& nfv,
                         const double* load, cudaStream_t s) {
@@ -1330,36 +1364,19 @@ void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf,
                      double* partials, int* nblocks, cudaStream_t s) {
     NullInfo nfv{};
     if (nf) nfv = *nf;
-    const size_t ni = interior_count(L);
-    const int nbi = ni ? blocks_for(ni) : 0;
-    const int nbb = L.nbnd ? blocks_for((size_t)L.nbnd * 32) : 0;
-    int off = nbi;
-    off += launch_faces_residual<T, TR, 0>(L, u, f, nfv, lam, r, partials ? partials + (size_t)off * kPartialStride : nullptr, s);
-    off += launch_faces_residual<T, TR, 1>(L, u, f, nfv, lam, r, partials ? partials + (size_t)off * kPartialStride : nullptr, s);
-    off += launch_faces_residual<T, TR, 2>(L, u, f, nfv, lam, r, partials ? partials + (size_t)off * kPartialStride : nullptr, s);
-    if (nblocks) *nblocks = off + nbb;
-    double* pb = partials ? partials + (size_t)off * kPartialStride : nullptr;
-    if (nbi) {
-        count_launch();
-        if (partials) {
-            if (L.K == 2) k_residual_int<T, TR, 2, true, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
-            else if (L.divc) k_residual_int<T, TR, 21, true, true><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
-            else k_residual_int<T, TR, 21, true, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials);
-        } else {
-            if (L.K == 2) k_residual_int<T, TR, 2, false, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
-            else if (L.divc) k_residual_int<T, TR, 21, false, true><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
-            else k_residual_int<T, TR, 21, false, false><<<nbi, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
-        }
-    }
-    if (nbb) {
-        count_launch();
-        if (partials) {
-            if (L.K == 2) k_residual_bnd<T, TR, 2, true><<<nbb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, pb);
-            else k_residual_bnd<T, TR, 21, true><<<nbb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, pb);
-        } else {
-            if (L.K == 2) k_residual_bnd<T, TR, 2, false><<<nbb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
-            else k_residual_bnd<T, TR, 21, false><<<nbb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr);
-        }
+    const BndSegs sg = bnd_segs(L, kBlock);
+    const int nb = sg.f2 + blocks_for(interior_count(L));
+    if (nblocks) *nblocks = nb;
+    if (!nb) return;
+    count_launch();
+    if (partials) {
+        if (L.K == 2) k_residual<T, TR, 2, true, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
+        else if (L.divc) k_residual<T, TR, 21, true, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
+        else k_residual<T, TR, 21, true, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
+    } else {
+        if (L.K == 2) k_residual<T, TR, 2, false, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
+        else if (L.divc) k_residual<T, TR, 21, false, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
+        else k_residual<T, TR, 21, false, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
     }
 }
 
@@ -1483,25 +1500,49 @@ static bool variant_ok(const Lv<T>& L, int v) {
     return sizeof(T) == 4 && !L.modh && !L.divc;
 }
 
+// Edge, corner and face nodes of a half-sweep as launches of their own (with the tiled
+// interior kernel, whose grid is three-dimensional).
+template <typename T>
+static void launch_boundary_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
+                                  const NullInfo& nfv, const double* lam, cudaStream_t s) {
+    launch_faces_sweep<T, 0>(L, u_in, u_out, f, colour, nfv, lam, s);
+    launch_faces_sweep<T, 1>(L, u_in, u_out, f, colour, nfv, lam, s);
+    launch_faces_sweep<T, 2>(L, u_in, u_out, f, colour, nfv, lam, s);
+    if (L.nbnd) {
+        count_launch();
+        if (L.K == 2) k_half_sweep_bnd<T, 2><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+        else k_half_sweep_bnd<T, 21><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
+    }
+}
+
+// One half-sweep with interior shape v: the untiled shapes take every node in one
+// launch; the tiled ones launch the boundary nodes separately.
 template <typename T, int KIND, bool HM>
 void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
                        const NullInfo& nfv, const double* lam, cudaStream_t s) {
     if constexpr (sizeof(T) == 4 && !HM) {
         if (v >= kFirstTiledVariant && variant_ok(L, v)) {
-            if (v == kFirstTiledVariant) launch_tiled<KIND, 16>(L, u_in, u_out, f, colour, nfv, lam, s);
-            else launch_tiled<KIND, 8>(L, u_in, u_out, f, colour, nfv, lam, s);
+            if (np) {
+                count_launch();
+                if (v == kFirstTiledVariant) launch_tiled<KIND, 16>(L, u_in, u_out, f, colour, nfv, lam, s);
+                else launch_tiled<KIND, 8>(L, u_in, u_out, f, colour, nfv, lam, s);
+            }
+            launch_boundary_sweep(L, u_in, u_out, f, colour, nfv, lam, s);
             return;
         }
     }
     if (v >= kFirstTiledVariant) v = kDefaultSweepVariant;
     const int bs = kSweepVariants[v][0];
-    const int nb = (int)((np + bs - 1) / bs);
+    const BndSegs sg = bnd_segs(L, bs);
+    const int nb = sg.f2 + (int)((np + bs - 1) / bs);
+    if (!nb) return;
+    count_launch();
     switch (v) {
-        case 0: k_half_sweep_int<T, KIND, HM, 256, 1><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
-        case 1: k_half_sweep_int<T, KIND, HM, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
-        case 2: k_half_sweep_int<T, KIND, HM, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
-        case 3: k_half_sweep_int<T, KIND, HM, 256, 4><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
-        default: k_half_sweep_int<T, KIND, HM, 128, 8><<<nb, 128, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam); break;
+        case 0: k_half_sweep_int<T, KIND, HM, 256, 1><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+        case 1: k_half_sweep_int<T, KIND, HM, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+        case 2: k_half_sweep_int<T, KIND, HM, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+        case 3: k_half_sweep_int<T, KIND, HM, 256, 4><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+        default: k_half_sweep_int<T, KIND, HM, 128, 8><<<nb, 128, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
     }
 }
 
@@ -1557,21 +1598,10 @@ void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int 
     NullInfo nfv{};
     if (nf) nfv = *nf;
     const size_t np = interior_pairs(L);
-    if (np) {
-        count_launch();
-        const int v = sweep_variant_for(L);
-        if (L.K == 2) sweep_int_variant<T, 2, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-        else if (L.divc) sweep_int_variant<T, 21, true>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-        else sweep_int_variant<T, 21, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-    }
-    launch_faces_sweep<T, 0>(L, u_in, u_out, f, colour, nfv, lam, s);
-    launch_faces_sweep<T, 1>(L, u_in, u_out, f, colour, nfv, lam, s);
-    launch_faces_sweep<T, 2>(L, u_in, u_out, f, colour, nfv, lam, s);
-    if (L.nbnd) {
-        count_launch();
-        if (L.K == 2) k_half_sweep_bnd<T, 2><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
-        else k_half_sweep_bnd<T, 21><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
-    }
+    const int v = sweep_variant_for(L);
+    if (L.K == 2) sweep_int_variant<T, 2, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+    else if (L.divc) sweep_int_variant<T, 21, true>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+    else sweep_int_variant<T, 21, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
 }
 
 template <typename T>
