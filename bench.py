@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e and the CPU baseline")
-    ap.add_argument("--inner", type=int, default=2, help="FP32 V-cycles per FP64 refinement step")
+    ap.add_argument("--inner", type=int, default=3, help="FP32 V-cycles per FP64 refinement step")
     ap.add_argument("--graph", action="store_true", help="replay refinement steps as a CUDA graph")
     ap.add_argument("--half", action="store_true", help="FP16 moduli in the FP32 V-cycle")
     return ap.parse_args()

@@ -1,6 +1,6 @@
 """Builds the sm_103a shared library ``libelas_gb300.so`` in place with nvcc.
 
-The two translation units compile in parallel; nothing here needs a GPU, so the
+The translation units compile in parallel; nothing here needs a GPU, so the
 same build runs on a CPU-only machine (cross-compilation) and on the GPU host.
 """
 import os
@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libelas_gb300.so")
-SOURCES = ["elas_kernels.cu", "elas_api.cu"]
+SOURCES = ["elas_sweep_f32.cu", "elas_sweep_f64.cu", "elas_residual.cu", "elas_kernels.cu", "elas_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -192,6 +192,7 @@ void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int 
     L.divc = nullptr;
     L.active = nullptr;
     L.modh = nullptr;
+    L.mlay = kModPlanes;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -428,8 +429,8 @@ int setup(elas_grid g) {
     if (g->desc.mixed) {
         for (int l = 0; l < nl; ++l) {
             Level& v = g->lv[l];
-            if (v.mod16) launch_to_half(v.mod64, v.mod16, (size_t)g->K * v.N, s);
-            else launch_to_float(v.mod64, v.mod32, (size_t)g->K * v.N, s);
+            if (v.mod16) launch_moduli_copy(v.mod64, v.mod16, v.N, g->K, s);
+            else launch_moduli_copy(v.mod64, v.mod32, v.N, g->K, s);
             CHECK_LAUNCH(c);
         }
     }
@@ -570,8 +571,8 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     if ((rc = galloc(g, &v.r, 3 * N))) return rc;
     if (mixed) {
         if (g->desc.half_moduli) {
-            if ((rc = galloc(g, &v.mod16, (size_t)g->K * N))) return rc;
-        } else if ((rc = galloc(g, &v.mod32, (size_t)g->K * N))) {
+            if ((rc = galloc(g, &v.mod16, moduli_copy_entries(v.N, g->K, true)))) return rc;
+        } else if ((rc = galloc(g, &v.mod32, moduli_copy_entries(v.N, g->K, false)))) {
             return rc;
         }
         if ((rc = galloc(g, &v.u32, 3 * N))) return rc;
@@ -581,6 +582,7 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     }
     v.L64.mod = v.mod64;
     v.L32.mod = v.mod32;
+    v.L32.mlay = v.mod16 ? kModRecords : (v.mod32 ? kModBlocked : kModPlanes);
     // list of the nodes on two or three boundary planes (face nodes are enumerated
     // arithmetically by the face kernels)
     std::vector<int> b;
@@ -620,6 +622,7 @@ void refresh_lv(elas_grid g) {
         v.L64.nbnd = v.L32.nbnd = v.nbnd;
         v.L64.divc = v.divc;
         v.L32.modh = v.mod16;
+        v.L32.mlay = v.mod16 ? kModRecords : (v.mod32 ? kModBlocked : kModPlanes);
         v.nf = null_space(g->desc, v.n, h, g->bc_type);
     }
 }
@@ -727,7 +730,7 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
     for (auto& n : level_dims(*d)) {
         const size_t N = (size_t)n[0] * n[1] * n[2];
         total += N * 8 * (K + 12 + (K == 21 ? 18 : 0));
-        if (d->mixed) total += N * ((d->half_moduli ? 2 : 4) * K + 48);
+        if (d->mixed) total += (d->half_moduli ? 2 : 4) * moduli_copy_entries((int)N, K, d->half_moduli) + N * 48;
     }
     const size_t N0 = (size_t)d->n[0] * d->n[1] * d->n[2];
     total += N0 * 8 * 9;   // eigenstrain + body force when given
@@ -744,7 +747,7 @@ int elas_grid_create(elas_ctx c, const elas_grid_desc* d, elas_grid* out) {
         if (!(d->hi[k] > d->lo[k])) return set_err(c, ELAS_ERR_INVALID_ARG, "empty domain");
     }
     const double N0 = (double)d->n[0] * d->n[1] * d->n[2];
-    if (N0 * d->moduli_kind >= 2147483647.0 || 3.0 * N0 >= 2147483647.0)
+    if (N0 * mod_record(d->moduli_kind) >= 2147483647.0 || 3.0 * N0 >= 2147483647.0)
         return set_err(c, ELAS_ERR_INVALID_ARG, "grid too large for 32-bit plane indexing");
     cudaSetDevice(c->device);
     elas_grid g = new elas_grid_s();

@@ -28,7 +28,11 @@ struct Lv {
     int n[3];
     int per[3];
     int N;
-    int K;                 // moduli planes: 2 (lambda, mu) or 21 (Voigt upper triangle)
+    int K;                 // moduli components: 2 (lambda, mu) or 21 (Voigt upper triangle)
+    // moduli layout: kModPlanes = one plane per component (FP64 levels); kModBlocked =
+    // planes per block of 32 consecutive nodes (FP32 copies); kModRecords = node-major
+    // records (FP16 copies)
+    int mlay;
     signed char bc[6][3];  // boundary type per (face, component); 0 on periodic faces
     T h[3], inv2h[3], invh[3], invh2[3], inv4hh[3];   // inv4hh[d] for the pair != d
     const T* __restrict__ mod;
@@ -43,11 +47,50 @@ struct Lv {
     const __half* __restrict__ modh;
 };
 
-// Moduli plane entry idx (plane * N + node): from the FP16 copy when a FP32 level has one.
+// Moduli layouts.  Planes: component c of node q at c * N + q.  Blocked (FP32 copies):
+// the nodes are cut into blocks of 32 consecutive linear indices and each block stores
+// its K components as K runs of 32, so c of q sits at (q / 32) * 32 K + 32 c + q % 32: a
+// warp's loads of one component stay as contiguous as in planes, while the K components
+// of a node are compile-time offsets (multiples of 128 bytes) from one address.
+// Records (FP16 copies): node-major, lambda, mu or the 21 components padded to 24, so a
+// node costs one address and three 16-byte loads.
+enum : int { kModPlanes = 0, kModBlocked = 1, kModRecords = 2 };
+__host__ __device__ constexpr int mod_record(int K) { return K == 2 ? 2 : 24; }
+__host__ __device__ inline size_t blocked_index(int K, int c, int q) {
+    return (size_t)(q >> 5) * (32 * K) + 32 * c + (q & 31);
+}
+
+// Moduli component c of node q in the level's layout.
 template <typename T>
-__device__ __forceinline__ T modv(const Lv<T>& L, int idx) {
-    if (sizeof(T) == 4 && L.modh) return T(__half2float(L.modh[idx]));
-    return L.mod[idx];
+__device__ __forceinline__ T modc(const Lv<T>& L, int c, int q) {
+    if (sizeof(T) == 4) {
+        if (L.mlay == kModRecords) return T(__half2float(L.modh[(size_t)q * mod_record(L.K) + c]));
+        if (L.mlay == kModBlocked) return L.mod[blocked_index(L.K, c, q)];
+    }
+    return L.mod[(size_t)c * L.N + q];
+}
+
+// Component c of node q from a blocked FP32 copy (c is a compile-time constant in the
+// unrolled stencil: the address of q is computed once, the components are offsets).
+template <int KIND>
+__device__ __forceinline__ float blk_float(const float* __restrict__ mod, int q, int c) {
+    constexpr int K = KIND == 2 ? 2 : 21;
+    return __ldg(mod + (size_t)(q >> 5) * (32 * K) + (q & 31) + 32 * c);
+}
+
+// Component c of node q's FP16 record, read as aligned 16-byte pieces shared by repeated
+// calls (the selects fold away for constant c).
+template <int KIND>
+__device__ __forceinline__ float rec_half(const __half* __restrict__ mod, int q, int c) {
+    unsigned w;
+    if (KIND == 2) {
+        w = __ldg(reinterpret_cast<const unsigned*>(mod) + q);
+    } else {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(mod) + (size_t)q * 3 + (c >> 3));
+        const int k = (c & 7) >> 1;
+        w = k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+    }
+    return __half2float(__ushort_as_half((unsigned short)((c & 1) ? (w >> 16) : (w & 0xffffu))));
 }
 
 // ---- rounded arithmetic the compiler never contracts -----------------------------
@@ -81,15 +124,15 @@ __host__ __device__ constexpr int pair_index(int j, int l) {  // (0,1)->2 (0,2)-
 template <typename T, int KIND>
 __device__ __forceinline__ T Cm(const Lv<T>& L, int q, int i, int j, int k, int l) {
     if (KIND == 2) {
-        const T lam = modv(L, q);
-        const T mu = modv(L, L.N + q);
+        const T lam = modc(L, 0, q);
+        const T mu = modc(L, 1, q);
         T v = T(0);
         if (i == j && k == l) v += lam;
         if (i == k && j == l) v += mu;
         if (i == l && j == k) v += mu;
         return v;
     } else {
-        return modv(L, upper(voigt(i, j), voigt(k, l)) * L.N + q);
+        return modc(L, upper(voigt(i, j), voigt(k, l)), q);
     }
 }
 
@@ -353,40 +396,50 @@ __device__ __forceinline__ void interior_rows_core(const Lv<T>& L, const UA& ua,
                 S[j][b] = xadd(hkl, hlk);
             }
         }
+        T acc[3] = {T(0), T(0), T(0)};
+        if (HAS_M) {
+            // term 1: M_iV e_V
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            T acc = T(0);
-            if (HAS_M) {
-                // term 1: M_iV e_V
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int V = 0; V < 6; ++V) acc = xfma(L.divc[(i * 6 + V) * L.N + p], e[V], acc);
-            }
+                for (int V = 0; V < 6; ++V) acc[i] = xfma(L.divc[(i * 6 + V) * L.N + p], e[V], acc[i]);
+        }
+        // term 2: C_(ij)b S_jb, centre moduli
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const int I = voigt(i, j);
-                if (!HAS_M) {
-                    // term 1: (d_j C_(ij)V) e_V
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int b = 0; b < 6; ++b) acc[i] = xfma(ca(upper(voigt(i, j), b), 0, 0, 0), S[j][b], acc[i]);
+        if (!HAS_M) {
+            // term 1: (d_j C_(ij)V) e_V, one direction at a time (the two neighbour
+            // records of direction j are live only within its iteration)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int I = voigt(i, j);
 #pragma unroll
                     for (int V = 0; V < 6; ++V) {
                         const int cmp = upper(I, V);
                         const T dC = xmul(xsub(ca(cmp, j == 0, j == 1, j == 2), ca(cmp, -(j == 0), -(j == 1), -(j == 2))),
                                           L.inv2h[j]);
-                        acc = xfma(dC, e[V], acc);
+                        acc[i] = xfma(dC, e[V], acc[i]);
                     }
                 }
-                // term 2: C_(ij)b S_jb
-#pragma unroll
-                for (int b = 0; b < 6; ++b) acc = xfma(ca(upper(I, b), 0, 0, 0), S[j][b], acc);
-            }
-            out[i] = acc;
         }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) out[i] = acc[i];
     }
 }
 
 
-template <typename T, int KIND, bool HAS_M = false>
-__device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restrict__ u,
-                                              int x, int y, int z, T out[3]) {
+// Calls body(ua, ca, p) with the accessors of the interior node (x, y, z): displacement
+// planes, and the moduli in the level's layout (FP64 planes; FP32 or FP16 node records,
+// MH selecting FP16).  Periodic directions wrap.
+template <typename T, int KIND, bool MH, class F>
+__device__ __forceinline__ void with_interior(const Lv<T>& L, const T* __restrict__ u, int x, int y, int z,
+                                              F&& body) {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     const int N = L.N;
     int X[3] = {x - 1, x, x + 1}, Y[3] = {y - 1, y, y + 1}, Z[3] = {z - 1, z, z + 1};
@@ -396,8 +449,33 @@ __device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restric
     const int Ys[3] = {Y[0] * nx, Y[1] * nx, Y[2] * nx};
     const int Zs[3] = {Z[0] * nx * ny, Z[1] * nx * ny, Z[2] * nx * ny};
     auto ua = [&](int k, int dx, int dy, int dz) { return u[k * N + X[dx + 1] + Ys[dy + 1] + Zs[dz + 1]]; };
-    auto ca = [&](int c, int dx, int dy, int dz) { return modv(L, c * N + X[dx + 1] + Ys[dy + 1] + Zs[dz + 1]); };
-    interior_rows_core<T, KIND, HAS_M>(L, ua, ca, X[1] + Ys[1] + Zs[1], out);
+    const int p = X[1] + Ys[1] + Zs[1];
+    if constexpr (sizeof(T) == 4) {
+        auto ca = [&](int c, int dx, int dy, int dz) -> T {
+            const int q = X[dx + 1] + Ys[dy + 1] + Zs[dz + 1];
+            if constexpr (MH) return rec_half<KIND>(L.modh, q, c);
+            else return blk_float<KIND>(L.mod, q, c);
+        };
+        body(ua, ca, p);
+    } else {
+        auto ca = [&](int c, int dx, int dy, int dz) -> T {
+            return L.mod[(size_t)c * N + X[dx + 1] + Ys[dy + 1] + Zs[dz + 1]];
+        };
+        body(ua, ca, p);
+    }
+}
+
+// All three rows of D_H u at an interior node, in any moduli layout.
+template <typename T, int KIND, bool HAS_M = false>
+__device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restrict__ u,
+                                              int x, int y, int z, T out[3]) {
+    auto body = [&](const auto& ua, const auto& ca, int p) { interior_rows_core<T, KIND, HAS_M>(L, ua, ca, p, out); };
+    if constexpr (sizeof(T) == 4) {
+        if (L.modh) with_interior<T, KIND, true>(L, u, x, y, z, body);
+        else with_interior<T, KIND, false>(L, u, x, y, z, body);
+    } else {
+        with_interior<T, KIND, false>(L, u, x, y, z, body);
+    }
 }
 
 // Diagonal 3x3 block of an interior node: B_ik = -2 sum_j C_ijkj / h_j^2.

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <array>
+
 #include "elas_device.cuh"
 
 namespace elas {
@@ -35,6 +37,8 @@ constexpr int kNumSweepVariants = 7;
 constexpr int kDefaultSweepVariant = 0;
 template <typename T>
 int tune_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, cudaStream_t s, float* ms_out);
+int tune_lookup(const std::array<int, 6>& key, int fallback);   // key: nx ny nz K bytes divc
+void tune_store(const std::array<int, 6>& key, int variant);
 int tune_table_dump(char* buf, int cap);
 int tune_table_load(const char* text);
 
@@ -68,8 +72,11 @@ void launch_prolong_add(const Lv<T>& Lf, const Lv<T>& Lc, const T* ec, T* u, cud
 template <typename T>
 void launch_restrict_moduli(const Lv<T>& Lf, const Lv<T>& Lc, const T* mf, T* mc, cudaStream_t s);
 
-void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s);
-void launch_to_half(const double* in, __half* out, size_t n, cudaStream_t s);
+// FP64 moduli planes (K x N) -> the FP32 blocked copy or the FP16 node records of an FP32
+// level (entries to allocate: moduli_copy_entries).
+size_t moduli_copy_entries(int N, int K, bool half);
+void launch_moduli_copy(const double* in, float* out, int N, int K, cudaStream_t s);
+void launch_moduli_copy(const double* in, __half* out, int N, int K, cudaStream_t s);
 // M_iV = sum_j d_j C_(ij)V (18 planes) of a general-moduli FP64 level (setup)
 void launch_divc(const Lv<double>& L, double* M, cudaStream_t s);
 void launch_add_correction(const Lv<double>& L, double* u, const float* e, cudaStream_t s);

@@ -1,20 +1,13 @@
-// CUDA kernels of the matrix-free multigrid path (sm_103a).
-//
-// One thread per node (per node pair in the smoother).  Fields are structure of
-// arrays, so every warp reads and writes contiguous x-runs of each plane; the
-// stencil's neighbour reuse is served by L1/L2.  Reductions are deterministic:
-// warp shuffles, one partial per block, then a single-block fixed-order sum.
-#include <cuda_runtime.h>
-#include <stdint.h>
-#include <stdio.h>
-#include <string.h>
-
+// Launchers of the multigrid kernels other than the residual and the smoother
+// (right-hand side, operator, transfers, bottom solve, reductions, AMR), the launch
+// counter and the smoother's tuning table.
 #include <array>
 #include <map>
 #include <mutex>
 #include <string>
 
-#include "elas_internal.h"
+#define ELAS_KERNELS_TU
+#include "elas_kernels.cuh"
 
 namespace elas {
 
@@ -22,1291 +15,6 @@ static unsigned long long g_launches = 0;
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 void count_launch(int n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
 
-namespace {
-
-inline int blocks_for(size_t n) { return (int)((n + kBlock - 1) / kBlock); }
-
-__device__ __forceinline__ void coords_of(int p, const int n[3], int c[3]) {
-    c[0] = p % n[0];
-    const int r = p / n[0];
-    c[1] = r % n[1];
-    c[2] = r / n[1];
-}
-
-// Block-wide sum of `width` doubles per thread into partials[blockIdx * kPartialStride + w].
-template <int MAXW>
-__device__ __forceinline__ void block_reduce_store(double (&v)[MAXW], int width, double* partials) {
-    __shared__ double sm[kBlock / 32][MAXW];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int w = 0; w < MAXW; ++w) {
-        if (w >= width) break;
-        double x = v[w];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) sm[warp][w] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-#pragma unroll
-        for (int w = 0; w < MAXW; ++w) {
-            if (w >= width) break;
-            double x = (lane < kBlock / 32) ? sm[lane][w] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) partials[blockIdx.x * kPartialStride + w] = x;
-        }
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ T face_datum(const BoundaryData& bd, int f, int c, int p, int N) {
-    return bd.face[f] ? T(bd.face[f][c * N + p]) : T(bd.uniform[f][c]);
-}
-
-// ---------------------------------------------------------------------------
-// right-hand side (setup, FP64)
-// ---------------------------------------------------------------------------
-template <int KIND>
-__global__ void k_rhs(Lv<double> L, RhsInputs in, BoundaryData bd, double* __restrict__ f) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.N) return;
-    int c[3];
-    coords_of(p, L.n, c);
-    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-    const int N = L.N;
-    auto eps = [&](int k, int l, int q) -> double {
-        return in.eps0 ? in.eps0[voigt(k, l) * N + q] : 0.0;
-    };
-    for (int i = 0; i < 3; ++i) {
-        const int t = row_type(L, ni, i);
-        double v = 0.0;
-        if (t == ROW_INTERIOR || t == ROW_TRACTION) {
-            if (in.body) v -= in.body[i * N + p];
-            for (int j = 0; j < 3; ++j) {
-                if (ni.side[j] != 0) continue;
-                int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
-                cp[j] = wrapc(L, j, c[j] + 1);
-                cm[j] = wrapc(L, j, c[j] - 1);
-                const int qp = lin(L, cp[0], cp[1], cp[2]), qm = lin(L, cm[0], cm[1], cm[2]);
-                for (int k = 0; k < 3; ++k)
-                    for (int l = 0; l < 3; ++l) {
-                        const double C0 = (KIND == 2) ? Cm<double, 2>(L, p, i, j, k, l) : Cm<double, 21>(L, p, i, j, k, l);
-                        const double Cp = (KIND == 2) ? Cm<double, 2>(L, qp, i, j, k, l) : Cm<double, 21>(L, qp, i, j, k, l);
-                        const double Cn = (KIND == 2) ? Cm<double, 2>(L, qm, i, j, k, l) : Cm<double, 21>(L, qm, i, j, k, l);
-                        const double ebar = in.has_mean_strain ? in.mean_strain[voigt(k, l)] : 0.0;
-                        v += (Cp - Cn) * L.inv2h[j] * (eps(k, l, p) - ebar) +
-                             C0 * (eps(k, l, qp) - eps(k, l, qm)) * L.inv2h[j];
-                    }
-            }
-            if (t == ROW_TRACTION) {
-                for (int a = 0; a < 3; ++a) {
-                    if (ni.side[a] == 0) continue;
-                    const int fc = 2 * a + (ni.side[a] > 0 ? 1 : 0);
-                    const double s = ni.side[a];
-                    int cn[3] = {c[0], c[1], c[2]};
-                    cn[a] -= ni.side[a];
-                    const int qn = lin(L, cn[0], cn[1], cn[2]);
-                    double acc = 0.0;
-                    for (int k = 0; k < 3; ++k)
-                        for (int l = 0; l < 3; ++l) {
-                            const double Ca = (KIND == 2) ? Cm<double, 2>(L, p, i, a, k, l) : Cm<double, 21>(L, p, i, a, k, l);
-                            const double Cb = (KIND == 2) ? Cm<double, 2>(L, qn, i, a, k, l) : Cm<double, 21>(L, qn, i, a, k, l);
-                            acc += 0.5 * (Ca + Cb) * 0.5 * (eps(k, l, p) + eps(k, l, qn));
-                        }
-                    v -= (2.0 * L.invh[a]) * (face_datum<double>(bd, fc, i, p, N) + s * acc);
-                }
-            }
-        } else if (t == ROW_NEUMANN) {
-            for (int a = 0; a < 3; ++a) {
-                if (ni.side[a] == 0) continue;
-                const int fc = 2 * a + (ni.side[a] > 0 ? 1 : 0);
-                if (L.bc[fc][i] != ROW_NEUMANN) continue;
-                const double C = (KIND == 2) ? Cm<double, 2>(L, p, i, a, i, a) : Cm<double, 21>(L, p, i, a, i, a);
-                v += -(2.0 * L.invh[a]) * C * face_datum<double>(bd, fc, i, p, N);
-            }
-        }
-        f[i * N + p] = v;
-    }
-}
-
-__global__ void k_dirichlet(Lv<double> L, BoundaryData bd, double* __restrict__ u, int keep_free) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.N) return;
-    int c[3];
-    coords_of(p, L.n, c);
-    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-    for (int i = 0; i < 3; ++i) {
-        const int t = row_type(L, ni, i);
-        if (t == ROW_DIRICHLET) {
-            // lowest-numbered Dirichlet face of this node wins
-            double v = 0.0;
-            for (int f = 5; f >= 0; --f) {
-                const int d = f / 2;
-                const int on = (f % 2 == 0) ? (ni.side[d] < 0) : (ni.side[d] > 0);
-                if (on && L.bc[f][i] == ROW_DIRICHLET) v = face_datum<double>(bd, f, i, p, L.N);
-            }
-            u[i * L.N + p] = v;
-        } else if (!keep_free) {
-            u[i * L.N + p] = 0.0;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// operator, residual, smoother.  Each comes as an interior kernel over the box of
-// nodes on no boundary plane (the fast stencil, no divergence) and a boundary
-// kernel over the level's list of boundary-plane nodes (generic rows).
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void interior_box(const Lv<T>& L, int lo[3], int cnt[3]) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        lo[d] = L.per[d] ? 0 : 1;
-        cnt[d] = L.per[d] ? L.n[d] : L.n[d] - 2;
-    }
-}
-
-template <typename T>
-__host__ __device__ inline size_t interior_count(const Lv<T>& L) {
-    size_t c = 1;
-    for (int d = 0; d < 3; ++d) c *= (size_t)(L.per[d] ? L.n[d] : L.n[d] - 2);
-    return c;
-}
-
-template <typename T>
-__host__ __device__ inline size_t interior_pairs(const Lv<T>& L) {
-    const int cx = L.per[0] ? L.n[0] : L.n[0] - 2;
-    const int cy = L.per[1] ? L.n[1] : L.n[1] - 2;
-    const int cz = L.per[2] ? L.n[2] : L.n[2] - 2;
-    return (size_t)((cx + 1) / 2) * cy * cz;
-}
-
-template <typename T, int KIND>
-__device__ __forceinline__ void boundary_rows_all(const Lv<T>& L, const T* __restrict__ u, const NodeInfo& ni,
-                                                  int types[3], T out[3]) {
-    UField<T> uf{u, L.N, L.n[0], L.n[1]};
-    for (int i = 0; i < 3; ++i) {
-        types[i] = row_type(L, ni, i);
-        out[i] = boundary_row<T, KIND>(L, uf, ni, i, types[i]);
-    }
-}
-
-template <typename T, int KIND, bool HM>
-__global__ void __launch_bounds__(kBlock) k_apply_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
-    int lo[3], cnt[3];
-    interior_box(L, lo, cnt);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt[0] * cnt[1] * cnt[2]) return;
-    const int x = lo[0] + t % cnt[0], y = lo[1] + (t / cnt[0]) % cnt[1], z = lo[2] + t / (cnt[0] * cnt[1]);
-    T v[3];
-    interior_rows<T, KIND, HM>(L, u, x, y, z, v);
-    const int p = lin(L, x, y, z);
-    for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
-}
-
-// Edge and corner nodes: one warp per node, lanes 0-2 evaluate its three rows.
-template <typename T, int KIND>
-__global__ void __launch_bounds__(kBlock) k_apply_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= L.nbnd || lane >= 3) return;
-    const int p = L.bnodes[w];
-    int c[3];
-    coords_of(p, L.n, c);
-    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-    UField<T> uf{u, L.N, L.n[0], L.n[1]};
-    out[lane * L.N + p] = boundary_row<T, KIND>(L, uf, ni, lane, row_type(L, ni, lane));
-}
-
-// r = f - load - A u on one node's rows (load = t + w x d, the equilibrating load);
-// accumulates sum r^2 and the six rigid-motion moments sum r, sum d x r.
-template <typename T, typename TR, bool NORM>
-__device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restrict__ f, const NullInfo& nf,
-                                               const double* __restrict__ load, const int c[3], int p,
-                                               const int types[3], const T v[3], TR* __restrict__ r,
-                                               double acc[7]) {
-    T rr[3];
-    for (int i = 0; i < 3; ++i) {
-        T ri = T(0);
-        if (types[i] != ROW_DIRICHLET) {
-            T fi = f[i * L.N + p];
-            if (load) fi -= rigid_load<T>(nf, load, i, c);
-            ri = fi - v[i];
-        }
-        rr[i] = ri;
-        r[i * L.N + p] = (TR)ri;
-    }
-    if (NORM) {
-        const double r0 = (double)rr[0], r1 = (double)rr[1], r2 = (double)rr[2];
-        acc[0] += r0 * r0 + r1 * r1 + r2 * r2;
-        if (nf.m > 0) {
-            // FP64: the moments of r cancel strongly (they measure the small incompatible
-            // part), so they are summed in full precision
-            const double d0 = nf.off[0] + nf.h[0] * c[0];
-            const double d1 = nf.off[1] + nf.h[1] * c[1];
-            const double d2 = nf.off[2] + nf.h[2] * c[2];
-            acc[1] += r0;
-            acc[2] += r1;
-            acc[3] += r2;
-            acc[4] += d1 * r2 - d2 * r1;
-            acc[5] += d2 * r0 - d0 * r2;
-            acc[6] += d0 * r1 - d1 * r0;
-        }
-    }
-}
-
-// Residual bodies: one interior node per thread, one edge/corner node per warp, one
-// face node per thread; each adds its node's contributions to the thread's sums.
-template <typename T, typename TR, int KIND, bool NORM, bool HM>
-__device__ __forceinline__ void residual_int_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
-                                                  const NullInfo& nf, const double* __restrict__ lam,
-                                                  TR* __restrict__ r, int t, double acc[7]) {
-    int lo[3], cnt[3];
-    interior_box(L, lo, cnt);
-    if (t >= cnt[0] * cnt[1] * cnt[2]) return;
-    const int c[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
-    T v[3];
-    interior_rows<T, KIND, HM>(L, u, c[0], c[1], c[2], v);
-    const int types[3] = {ROW_INTERIOR, ROW_INTERIOR, ROW_INTERIOR};
-    residual_store<T, TR, NORM>(L, f, nf, lam, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
-}
-
-template <typename T, typename TR, int KIND, bool NORM>
-__device__ __forceinline__ void residual_bnd_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
-                                                  const NullInfo& nf, const double* __restrict__ lam,
-                                                  TR* __restrict__ r, int w, int lane, double acc[7]) {
-    if (w >= L.nbnd) return;   // whole warp
-    const int p = L.bnodes[w];
-    int c[3];
-    coords_of(p, L.n, c);
-    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-    int types[3];
-    for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
-    T val = T(0);
-    if (lane < 3) {
-        UField<T> uf{u, L.N, L.n[0], L.n[1]};
-        val = boundary_row<T, KIND>(L, uf, ni, lane, types[lane]);
-    }
-    T v[3];
-    for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, i);
-    if (lane == 0) residual_store<T, TR, NORM>(L, f, nf, lam, c, p, types, v, r, acc);
-}
-
-// Red-black smoother, interior nodes: each thread owns the x-pair (x0, x0+1) of the
-// interior box, updates the one of the active colour and copies the other; every
-// row uses the values from before the half-sweep (Jacobi within the colour).
-template <typename T, int KIND, bool HM>
-__device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restrict__ u, T* __restrict__ uo,
-                                                const T* __restrict__ f, int colour, const NullInfo& nf,
-                                                const double* __restrict__ lam, int t) {
-    int lo[3], cnt[3];
-    interior_box(L, lo, cnt);
-    const int npair = (cnt[0] + 1) >> 1;
-    if (t >= npair * cnt[1] * cnt[2]) return;
-    const int m = t % npair;
-    const int yz = t / npair;
-    const int y = lo[1] + yz % cnt[1], z = lo[2] + yz / cnt[1];
-    const int x0 = lo[0] + 2 * m;
-    const int xend = lo[0] + cnt[0];          // one past the last interior x
-    const int xa = x0 + ((x0 + y + z + colour) & 1);
-    const int xi = (xa == x0) ? x0 + 1 : x0;
-    const int N = L.N;
-    if (xi < xend) {
-        const int q = lin(L, xi, y, z);
-        uo[q] = u[q];
-        uo[N + q] = u[N + q];
-        uo[2 * N + q] = u[2 * N + q];
-    }
-    if (xa >= xend) return;
-    const int p = lin(L, xa, y, z);
-    T v[3];
-    interior_rows<T, KIND, HM>(L, u, xa, y, z, v);
-    T r[3], B[3][3], d[3];
-    const int c[3] = {xa, y, z};
-    for (int i = 0; i < 3; ++i) {
-        T fi = f[i * N + p];
-        if (lam) fi = xsub(fi, rigid_load<T>(nf, lam, i, c));
-        r[i] = xsub(fi, v[i]);
-    }
-    interior_block<T, KIND>(L, p, B);
-    solve3(B, r, d);
-    for (int i = 0; i < 3; ++i) uo[i * N + p] = xadd(u[i * N + p], d[i]);
-}
-
-// ---- shared-memory tiled FP32 interior smoother --------------------------------------
-// A block owns a 32 x TY tile of interior (x, y) nodes and marches through a chunk of
-// interior z planes.  Moduli planes with a one-node x/y halo rotate through three shared
-// buffers and displacement planes through four; plane z+2 streams in (cp.async) while
-// plane z is computed, and the moduli of plane z-1 that the z-derivative needs are
-// copied to registers before their buffer is refilled.  Each warp covers 16 x-pairs of
-// two neighbouring rows: their active nodes have opposite x parity, so with an even row
-// stride every shared load of the warp falls on 32 distinct banks.  The arithmetic is
-// the same inlined stencil as the untiled kernel (same operations, same order).
-constexpr int kTileX = 32;             // interior nodes per tile row
-constexpr int kTileS = kTileX + 2;     // shared row stride (with halo), even
-
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-template <int KIND, int TY>
-struct TiledShape {
-    static constexpr int KP = (KIND == 2) ? 2 : 21;
-    static constexpr int R = TY + 2;                   // rows with halo
-    static constexpr int PLANE = R * kTileS;           // one component of one plane
-    static constexpr int CPL = KP * PLANE;             // floats per moduli plane
-    static constexpr int UPL = 3 * PLANE;              // floats per displacement plane
-    static constexpr int NPOS = (PLANE + 16 * TY - 1) / (16 * TY);   // positions per thread
-    static constexpr size_t SMEM = sizeof(float) * (3 * CPL + 4 * UPL);
-};
-
-template <int KIND, int TY>
-__global__ void __launch_bounds__(16 * TY, (TY <= 8) ? 2 : 1)
-    k_half_sweep_tiled(Lv<float> L, const float* __restrict__ u, float* __restrict__ uo,
-                       const float* __restrict__ f, int colour, NullInfo nf, const double* __restrict__ lam,
-                       int zlen) {
-    using S = TiledShape<KIND, TY>;
-    constexpr int KP = S::KP, R = S::R, PLANE = S::PLANE, CPL = S::CPL, UPL = S::UPL, NPOS = S::NPOS;
-    constexpr int NT = 16 * TY;
-    extern __shared__ __align__(16) float sm[];
-    float* const Cs = sm;                  // [3][KP][R][kTileS]
-    float* const Us = sm + 3 * CPL;        // [4][3][R][kTileS]
-    if (L.active && *L.active == 0) return;
-    int lo[3], cnt[3];
-    interior_box(L, lo, cnt);
-    const int nx = L.n[0], ny = L.n[1], nz = L.n[2], N = L.N;
-    const int xt0 = lo[0] + kTileX * blockIdx.x;
-    const int yt0 = lo[1] + TY * blockIdx.y;
-    const int z0 = lo[2] + zlen * blockIdx.z;
-    const int zend = min(z0 + zlen, lo[2] + cnt[2]);
-    if (z0 >= zend) return;
-    const int xend = lo[0] + cnt[0], yend = lo[1] + cnt[1];
-
-    // plane positions (row, column) this thread copies: in-plane global offset or -1
-    int goff[NPOS];
-#pragma unroll
-    for (int j = 0; j < NPOS; ++j) {
-        const int pos = threadIdx.x + NT * j;
-        goff[j] = -1;
-        if (pos < PLANE) {
-            int x = xt0 - 1 + pos % kTileS, y = yt0 - 1 + pos / kTileS;
-            if (x <= xend && y <= yend) {
-                if (x < 0) x += nx;
-                if (x >= nx) x -= nx;
-                if (y < 0) y += ny;
-                if (y >= ny) y -= ny;
-                goff[j] = x + nx * y;
-            }
-        }
-    }
-    auto plane_base = [&](int z) -> int {
-        if (z < 0) z += nz;
-        if (z >= nz) z -= nz;
-        return z * nx * ny;
-    };
-    // enqueue moduli and displacement of plane z into ring slot j (moduli: j % 3, u: j % 4)
-    auto load_plane = [&](int z, int j) {
-        const int zb = plane_base(z);
-        float* cd = Cs + (j % 3) * CPL;
-        float* ud = Us + (j & 3) * UPL;
-#pragma unroll
-        for (int q = 0; q < NPOS; ++q) {
-            const int pos = threadIdx.x + NT * q;
-            if (goff[q] < 0) continue;
-            const float* cs = L.mod + zb + goff[q];
-#pragma unroll 7
-            for (int c = 0; c < KP; ++c) cp_async4(cd + c * PLANE + pos, cs + (size_t)c * N);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) cp_async4(ud + k * PLANE + pos, u + (size_t)k * N + zb + goff[q]);
-        }
-        cp_async_commit();
-    };
-
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int y = yt0 + ty;
-    const int x0 = xt0 + 2 * tx;
-    const int yl = ty + 1;
-
-    // prologue: planes z0-1, z0, z0+1 in slots 0, 1, 2
-    load_plane(z0 - 1, 0);
-    load_plane(z0, 1);
-    load_plane(z0 + 1, 2);
-
-    for (int z = z0; z < zend; ++z) {
-        const int j = z - z0 + 1;          // ring index of the current plane
-        const int xa = x0 + ((x0 + y + z + colour) & 1);
-        const int xi = (xa == x0) ? x0 + 1 : x0;
-        const int xla = xa - xt0 + 1, xli = xi - xt0 + 1;
-        cp_async_wait_all();
-        __syncthreads();
-        // moduli of plane z-1 at the active node, before its slot is refilled
-        float cprev[KP];
-        {
-            const float* cb = Cs + ((j + 2) % 3) * CPL + yl * kTileS + xla;
-#pragma unroll
-            for (int c = 0; c < KP; ++c) cprev[c] = cb[c * PLANE];
-        }
-        __syncthreads();
-        if (z + 2 <= zend) load_plane(z + 2, j + 2);
-
-        const float* const Cz = Cs + (j % 3) * CPL + yl * kTileS;
-        const float* const Cn = Cs + ((j + 1) % 3) * CPL + yl * kTileS + xla;
-        const float* const Um = Us + ((j + 3) & 3) * UPL + yl * kTileS + xla;
-        const float* const U0 = Us + (j & 3) * UPL + yl * kTileS;
-        const float* const Up = Us + ((j + 1) & 3) * UPL + yl * kTileS + xla;
-        const int row = nx * (y + ny * z);
-        if (y < yend && xi < xend) {
-            const int q = xi + row;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) uo[(size_t)k * N + q] = U0[k * PLANE + xli];
-        }
-        if (y < yend && xa < xend) {
-            auto ua = [&](int k, int dx, int dy, int dz) -> float {
-                const float* b = dz < 0 ? Um : (dz > 0 ? Up : U0 + xla);
-                return b[k * PLANE + dy * kTileS + dx];
-            };
-            auto ca = [&](int c, int dx, int dy, int dz) -> float {
-                if (dz < 0) return cprev[c];
-                if (dz > 0) return Cn[c * PLANE];
-                return Cz[c * PLANE + dy * kTileS + xla + dx];
-            };
-            const int p = xa + row;
-            float v[3];
-            interior_rows_core<float, KIND, false>(L, ua, ca, p, v);
-            float r[3], B[3][3], d[3];
-            const int c3[3] = {xa, y, z};
-            for (int i = 0; i < 3; ++i) {
-                float fi = f[(size_t)i * N + p];
-                if (lam) fi = xsub(fi, rigid_load<float>(nf, lam, i, c3));
-                r[i] = xsub(fi, v[i]);
-            }
-            interior_block_acc<float, KIND>(L, ca, B);
-            solve3(B, r, d);
-            for (int i = 0; i < 3; ++i) uo[(size_t)i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
-        }
-    }
-    cp_async_wait_all();
-}
-
-// Red-black smoother, edge and corner nodes: one warp per node; lanes 0-8 compute
-// the diagonal block entries, lanes 9-11 the rows, lane 0 solves and writes.
-template <typename T, int KIND>
-__device__ __forceinline__ void sweep_bnd_body(const Lv<T>& L, const T* __restrict__ u, T* __restrict__ uo,
-                                               const T* __restrict__ f, int colour, const NullInfo& nf,
-                                               const double* __restrict__ lam, int w, int lane) {
-    if (w >= L.nbnd) return;   // whole warp
-    const int p = L.bnodes[w];
-    const int N = L.N;
-    int c[3];
-    coords_of(p, L.n, c);
-    if (((c[0] + c[1] + c[2]) & 1) != colour) {
-        if (lane < 3) uo[lane * N + p] = u[lane * N + p];
-        return;
-    }
-    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-    int types[3];
-    for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
-    T val = T(0);
-    if (lane < 9) {
-        val = boundary_block_entry<T, KIND>(L, ni, types, lane / 3, lane % 3);
-    } else if (lane < 12) {
-        UField<T> uf{u, N, L.n[0], L.n[1]};
-        val = boundary_row<T, KIND>(L, uf, ni, lane - 9, types[lane - 9]);
-    }
-    T B[3][3], v[3];
-    for (int q = 0; q < 9; ++q) B[q / 3][q % 3] = __shfl_sync(0xffffffffu, val, q);
-    for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, 9 + i);
-    if (lane != 0) return;
-    T r[3], d[3];
-    for (int i = 0; i < 3; ++i) {
-        if (types[i] == ROW_DIRICHLET) {
-            r[i] = T(0);
-        } else {
-            T fi = f[i * N + p];
-            if (lam) fi -= rigid_load<T>(nf, lam, i, c);
-            r[i] = fi - v[i];
-        }
-    }
-    solve3(B, r, d);
-    for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
-}
-
-template <typename T, int KIND>
-__global__ void __launch_bounds__(kBlock) k_half_sweep_bnd(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
-                                                          const T* __restrict__ f, int colour, NullInfo nf,
-                                                          const double* __restrict__ lam) {
-    if (L.active && *L.active == 0) return;
-    sweep_bnd_body<T, KIND>(L, u, uo, f, colour, nf, lam, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                            threadIdx.x & 31);
-}
-
-// ---------------------------------------------------------------------------
-// face nodes: nodes on exactly one boundary plane, enumerated per direction A
-// (both sides): thread -> (side, slow tangential, fast tangential)
-// ---------------------------------------------------------------------------
-template <typename T, int A>
-__host__ __device__ inline void face_extent(const Lv<T>& L, int& n_fast, int& n_slow) {
-    constexpr int ta = A == 0 ? 1 : 0;
-    constexpr int tb = A == 2 ? 1 : 2;
-    n_fast = L.per[ta] ? L.n[ta] : L.n[ta] - 2;
-    n_slow = L.per[tb] ? L.n[tb] : L.n[tb] - 2;
-}
-
-template <typename T, int A>
-__device__ __forceinline__ bool face_coords(const Lv<T>& L, int t, int c[3], int& side) {
-    constexpr int ta = A == 0 ? 1 : 0;
-    constexpr int tb = A == 2 ? 1 : 2;
-    int nf, ns;
-    face_extent<T, A>(L, nf, ns);
-    if (t >= 2 * nf * ns) return false;
-    const int i_fast = t % nf;
-    const int rest = t / nf;
-    const int i_slow = rest % ns;
-    const int sd = rest / ns;
-    c[ta] = (L.per[ta] ? 0 : 1) + i_fast;
-    c[tb] = (L.per[tb] ? 0 : 1) + i_slow;
-    c[A] = sd == 0 ? 0 : L.n[A] - 1;
-    side = sd == 0 ? -1 : 1;
-    return true;
-}
-
-template <typename T, int A>
-__device__ __forceinline__ void face_types(const Lv<T>& L, int side, int types[3]) {
-    const int f = 2 * A + (side > 0 ? 1 : 0);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const int t = L.bc[f][i];
-        types[i] = t == ROW_DIRICHLET ? ROW_DIRICHLET : (t == ROW_NEUMANN ? ROW_NEUMANN : ROW_TRACTION);
-    }
-}
-
-template <typename T, int KIND, int A>
-__global__ void __launch_bounds__(kBlock) k_apply_face(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
-    int c[3], side;
-    if (!face_coords<T, A>(L, blockIdx.x * blockDim.x + threadIdx.x, c, side)) return;
-    int types[3];
-    face_types<T, A>(L, side, types);
-    T v[3], B[3][3];
-    face_node<T, KIND, A>(L, u, c, side, types, v, B, false);
-    const int p = lin(L, c[0], c[1], c[2]);
-    for (int i = 0; i < 3; ++i) out[i * L.N + p] = v[i];
-}
-
-template <typename T, typename TR, int KIND, int A, bool NORM>
-__device__ __forceinline__ void residual_face_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
-                                                   const NullInfo& nf, const double* __restrict__ load,
-                                                   TR* __restrict__ r, int t, double acc[7]) {
-    int c[3], side;
-    if (!face_coords<T, A>(L, t, c, side)) return;
-    int types[3];
-    face_types<T, A>(L, side, types);
-    T v[3], B[3][3];
-    face_node<T, KIND, A>(L, u, c, side, types, v, B, false);
-    residual_store<T, TR, NORM>(L, f, nf, load, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
-}
-
-template <typename T, int KIND, int A>
-__device__ __forceinline__ void sweep_face_body(const Lv<T>& L, const T* __restrict__ u, T* __restrict__ uo,
-                                                const T* __restrict__ f, int colour, const NullInfo& nf,
-                                                const double* __restrict__ load, int t) {
-    int c[3], side;
-    if (!face_coords<T, A>(L, t, c, side)) return;
-    const int N = L.N;
-    const int p = lin(L, c[0], c[1], c[2]);
-    if (((c[0] + c[1] + c[2]) & 1) != colour) {
-        uo[p] = u[p];
-        uo[N + p] = u[N + p];
-        uo[2 * N + p] = u[2 * N + p];
-        return;
-    }
-    int types[3];
-    face_types<T, A>(L, side, types);
-    T v[3], B[3][3], r[3], d[3];
-    face_node<T, KIND, A>(L, u, c, side, types, v, B, true);
-    for (int i = 0; i < 3; ++i) {
-        if (types[i] == ROW_DIRICHLET) {
-            r[i] = T(0);
-        } else {
-            T fi = f[i * N + p];
-            if (load) fi -= rigid_load<T>(nf, load, i, c);
-            r[i] = fi - v[i];
-        }
-    }
-    solve3(B, r, d);
-    for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
-}
-
-template <typename T, int KIND, int A>
-__global__ void __launch_bounds__(kBlock) k_half_sweep_face(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
-                                                           const T* __restrict__ f, int colour, NullInfo nf,
-                                                           const double* __restrict__ load) {
-    if (L.active && *L.active == 0) return;
-    sweep_face_body<T, KIND, A>(L, u, uo, f, colour, nf, load, blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-template <typename T, int A>
-inline size_t face_count(const Lv<T>& L) {
-    if (L.per[A]) return 0;
-    int nf, ns;
-    face_extent<T, A>(L, nf, ns);
-    return (size_t)2 * nf * ns;
-}
-
-// ---- one launch per half-sweep / residual ---------------------------------------------
-// The grid's first blocks take the edge and corner nodes (a warp each), then the face
-// nodes of directions 0, 1, 2 (a thread each), then the interior.  The boundary blocks
-// are few and latency-bound; issued first, they run alongside the interior blocks
-// instead of as four short launches of their own.  Block ranges are uniform per block.
-struct BndSegs {
-    int e, f0, f1, f2;   // one past the last block of the edge, x-, y- and z-face ranges
-};
-
-template <typename T>
-inline BndSegs bnd_segs(const Lv<T>& L, int bs) {
-    auto nb = [bs](size_t n) { return (int)((n + bs - 1) / bs); };
-    BndSegs g;
-    g.e = nb((size_t)L.nbnd * 32);
-    g.f0 = g.e + nb(face_count<T, 0>(L));
-    g.f1 = g.f0 + nb(face_count<T, 1>(L));
-    g.f2 = g.f1 + nb(face_count<T, 2>(L));
-    return g;
-}
-
-// Red-black smoother, all nodes of one colour (see the bodies above for each kind).
-template <typename T, int KIND, bool HM, int BS, int MINB>
-__global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
-                                                          const T* __restrict__ f, int colour, NullInfo nf,
-                                                          const double* __restrict__ lam, BndSegs sg) {
-    if (L.active && *L.active == 0) return;
-    const int b = blockIdx.x, tid = threadIdx.x;
-    if (b < sg.f2) {
-        if (b < sg.e) sweep_bnd_body<T, KIND>(L, u, uo, f, colour, nf, lam, (b * BS + tid) >> 5, tid & 31);
-        else if (b < sg.f0) sweep_face_body<T, KIND, 0>(L, u, uo, f, colour, nf, lam, (b - sg.e) * BS + tid);
-        else if (b < sg.f1) sweep_face_body<T, KIND, 1>(L, u, uo, f, colour, nf, lam, (b - sg.f0) * BS + tid);
-        else sweep_face_body<T, KIND, 2>(L, u, uo, f, colour, nf, lam, (b - sg.f1) * BS + tid);
-        return;
-    }
-    sweep_pair_body<T, KIND, HM>(L, u, uo, f, colour, nf, lam, (b - sg.f2) * BS + tid);
-}
-
-// r = f - load - A u on every node; block partials of sum r^2 and the rigid moments.
-template <typename T, typename TR, int KIND, bool NORM, bool HM>
-__global__ void __launch_bounds__(kBlock) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
-                                                    NullInfo nf, const double* __restrict__ lam,
-                                                    TR* __restrict__ r, double* __restrict__ partials, BndSegs sg) {
-    if (L.active && *L.active == 0) return;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    const int b = blockIdx.x, tid = threadIdx.x;
-    if (b < sg.e) residual_bnd_body<T, TR, KIND, NORM>(L, u, f, nf, lam, r, (b * kBlock + tid) >> 5, tid & 31, acc);
-    else if (b < sg.f0) residual_face_body<T, TR, KIND, 0, NORM>(L, u, f, nf, lam, r, (b - sg.e) * kBlock + tid, acc);
-    else if (b < sg.f1) residual_face_body<T, TR, KIND, 1, NORM>(L, u, f, nf, lam, r, (b - sg.f0) * kBlock + tid, acc);
-    else if (b < sg.f2) residual_face_body<T, TR, KIND, 2, NORM>(L, u, f, nf, lam, r, (b - sg.f1) * kBlock + tid, acc);
-    else residual_int_body<T, TR, KIND, NORM, HM>(L, u, f, nf, lam, r, (b - sg.f2) * kBlock + tid, acc);
-    if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
-}
-
-// ---------------------------------------------------------------------------
-// transfers (Section 3.2)
-// ---------------------------------------------------------------------------
-// weights of fine offsets -1, 0, +1 for coarse index I in one direction
-template <typename T>
-__device__ __forceinline__ void restrict_weights(const Lv<T>& Lc, int d, int I, T w[3]) {
-    if (!Lc.per[d] && I == 0) { w[0] = T(0); w[1] = T(0.5); w[2] = T(0.5); return; }
-    if (!Lc.per[d] && I == Lc.n[d] - 1) { w[0] = T(0.5); w[1] = T(0.5); w[2] = T(0); return; }
-    w[0] = T(0.25); w[1] = T(0.5); w[2] = T(0.25);
-}
-
-template <typename T>
-__global__ void k_restrict(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ r, T* __restrict__ fc, NullInfo nf,
-                           const double* __restrict__ dlam) {
-    if (Lf.active && *Lf.active == 0) return;
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= Lc.N) return;
-    int C[3];
-    coords_of(P, Lc.n, C);
-    const NodeInfo nic = node_info(Lc, C[0], C[1], C[2]);
-    T wx[3], wy[3], wz[3];
-    restrict_weights(Lc, 0, C[0], wx);
-    restrict_weights(Lc, 1, C[1], wy);
-    restrict_weights(Lc, 2, C[2], wz);
-    T acc[3] = {T(0), T(0), T(0)};
-    const bool corr = dlam != nullptr;
-    for (int dz = -1; dz <= 1; ++dz) {
-        if (wz[dz + 1] == T(0)) continue;
-        const int fz = wrapc(Lf, 2, 2 * C[2] + dz);
-        for (int dy = -1; dy <= 1; ++dy) {
-            if (wy[dy + 1] == T(0)) continue;
-            const int fy = wrapc(Lf, 1, 2 * C[1] + dy);
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (wx[dx + 1] == T(0)) continue;
-                const int fx = wrapc(Lf, 0, 2 * C[0] + dx);
-                const T w = wx[dx + 1] * wy[dy + 1] * wz[dz + 1];
-                const int q = lin(Lf, fx, fy, fz);
-                const int cf[3] = {fx, fy, fz};
-                NodeInfo nif;
-                if (corr) nif = node_info(Lf, fx, fy, fz);
-                for (int i = 0; i < 3; ++i) {
-                    T v = r[i * Lf.N + q];
-                    if (corr && row_type(Lf, nif, i) != ROW_DIRICHLET) v -= rigid_load<T>(nf, dlam, i, cf);
-                    acc[i] += w * v;
-                }
-            }
-        }
-    }
-    for (int i = 0; i < 3; ++i)
-        fc[i * Lc.N + P] = (row_type(Lc, nic, i) == ROW_DIRICHLET) ? T(0) : acc[i];
-}
-
-template <typename T>
-__global__ void k_prolong_add(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ ec, T* __restrict__ u) {
-    if (Lf.active && *Lf.active == 0) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= Lf.N) return;
-    int c[3];
-    coords_of(p, Lf.n, c);
-    const NodeInfo ni = node_info(Lf, c[0], c[1], c[2]);
-    int lo[3], hi[3];
-    T wl[3], wh[3];
-    for (int d = 0; d < 3; ++d) {
-        if ((c[d] & 1) == 0) {
-            lo[d] = hi[d] = c[d] >> 1;
-            wl[d] = T(1);
-            wh[d] = T(0);
-        } else {
-            lo[d] = c[d] >> 1;
-            hi[d] = lo[d] + 1;
-            if (Lc.per[d] && hi[d] >= Lc.n[d]) hi[d] -= Lc.n[d];
-            wl[d] = T(0.5);
-            wh[d] = T(0.5);
-        }
-    }
-    for (int i = 0; i < 3; ++i) {
-        if (row_type(Lf, ni, i) == ROW_DIRICHLET) continue;
-        const T* e = ec + i * Lc.N;
-        T v = T(0);
-        for (int bz = 0; bz < 2; ++bz) {
-            const T wzv = bz ? wh[2] : wl[2];
-            if (wzv == T(0)) continue;
-            const int cz = bz ? hi[2] : lo[2];
-            for (int by = 0; by < 2; ++by) {
-                const T wyv = by ? wh[1] : wl[1];
-                if (wyv == T(0)) continue;
-                const int cy = by ? hi[1] : lo[1];
-                for (int bx = 0; bx < 2; ++bx) {
-                    const T wxv = bx ? wh[0] : wl[0];
-                    if (wxv == T(0)) continue;
-                    const int cx = bx ? hi[0] : lo[0];
-                    v += wxv * wyv * wzv * e[lin(Lc, cx, cy, cz)];
-                }
-            }
-        }
-        u[i * Lf.N + p] += v;
-    }
-}
-
-template <typename T>
-__global__ void k_restrict_moduli(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ mf, T* __restrict__ mc) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= Lc.N) return;
-    int C[3];
-    coords_of(P, Lc.n, C);
-    T wx[3], wy[3], wz[3];
-    restrict_weights(Lc, 0, C[0], wx);
-    restrict_weights(Lc, 1, C[1], wy);
-    restrict_weights(Lc, 2, C[2], wz);
-    for (int k = 0; k < Lf.K; ++k) {
-        T acc = T(0);
-        for (int dz = -1; dz <= 1; ++dz) {
-            if (wz[dz + 1] == T(0)) continue;
-            const int fz = wrapc(Lf, 2, 2 * C[2] + dz);
-            for (int dy = -1; dy <= 1; ++dy) {
-                if (wy[dy + 1] == T(0)) continue;
-                const int fy = wrapc(Lf, 1, 2 * C[1] + dy);
-                for (int dx = -1; dx <= 1; ++dx) {
-                    if (wx[dx + 1] == T(0)) continue;
-                    const int fx = wrapc(Lf, 0, 2 * C[0] + dx);
-                    acc += wx[dx + 1] * wy[dy + 1] * wz[dz + 1] * mf[k * Lf.N + lin(Lf, fx, fy, fz)];
-                }
-            }
-        }
-        mc[k * Lc.N + P] = acc;
-    }
-}
-
-// M_iV = sum_j (C_(ij)V(p+e_j) - C_(ij)V(p-e_j)) / 2h_j at interior nodes, 0 elsewhere.
-template <typename T>
-__global__ void k_divc(Lv<T> L, T* __restrict__ M) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.N) return;
-    int c[3];
-    coords_of(p, L.n, c);
-    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-    for (int i = 0; i < 3; ++i)
-        for (int V = 0; V < 6; ++V) {
-            T acc = T(0);
-            if (!ni.boundary) {
-                for (int j = 0; j < 3; ++j) {
-                    int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
-                    cp[j] = wrapc(L, j, c[j] + 1);
-                    cm[j] = wrapc(L, j, c[j] - 1);
-                    const T* cc = L.mod + upper(voigt(i, j), V) * L.N;
-                    acc += (cc[lin(L, cp[0], cp[1], cp[2])] - cc[lin(L, cm[0], cm[1], cm[2])]) * L.inv2h[j];
-                }
-            }
-            M[(i * 6 + V) * L.N + p] = acc;
-        }
-}
-
-__global__ void k_to_half(const double* __restrict__ in, __half* __restrict__ out, size_t n) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = __double2half(in[i]);
-}
-
-__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)in[i];
-}
-
-template <typename TE>
-__global__ void k_add_correction(Lv<double> L, double* __restrict__ u, const TE* __restrict__ e) {
-    if (L.active && *L.active == 0) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.N) return;
-    int c[3];
-    coords_of(p, L.n, c);
-    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-    for (int i = 0; i < 3; ++i)
-        if (row_type(L, ni, i) != ROW_DIRICHLET) u[i * L.N + p] += (double)e[i * L.N + p];
-}
-
-// ---------------------------------------------------------------------------
-// bottom solve
-// ---------------------------------------------------------------------------
-template <int KIND>
-__global__ void k_bottom_assemble(Lv<double> L, const int* __restrict__ dofs, int nfree, NullInfo nf,
-                                  double* __restrict__ A) {
-    const int ntot = nfree + nf.m;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)ntot * ntot) return;
-    const int row = (int)(t / ntot), col = (int)(t % ntot);
-    double v = 0.0;
-    if (row < nfree && col < nfree) {
-        const int ir = dofs[row] / L.N, pr = dofs[row] % L.N;
-        const int ic = dofs[col] / L.N, pc = dofs[col] % L.N;
-        int c[3];
-        coords_of(pr, L.n, c);
-        const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-        const int type = row_type(L, ni, ir);
-        UProbe<double> e{ic, {0, 0, 0}};
-        coords_of(pc, L.n, e.c0);
-        v = boundary_row<double, KIND>(L, e, ni, ir, type == ROW_INTERIOR ? ROW_TRACTION : type);
-    } else if (row < nfree && col >= nfree) {
-        const int ir = dofs[row] / L.N, pr = dofs[row] % L.N;
-        int c[3];
-        coords_of(pr, L.n, c);
-        v = null_vec(nf, col - nfree, ir, c);
-    } else if (row >= nfree && col < nfree) {
-        const int ic = dofs[col] / L.N, pc = dofs[col] % L.N;
-        int c[3];
-        coords_of(pc, L.n, c);
-        v = null_vec(nf, row - nfree, ic, c);
-    }
-    A[t] = v;
-}
-
-// Gauss-Jordan inversion with partial pivoting, one block.
-__global__ void k_invert(double* __restrict__ A, double* __restrict__ X, int n, int* singular) {
-    __shared__ int piv;
-    __shared__ double pval;
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) X[i] = ((i / n) == (i % n)) ? 1.0 : 0.0;
-    __syncthreads();
-    for (int col = 0; col < n; ++col) {
-        if (threadIdx.x == 0) {
-            int best = col;
-            double bv = fabs(A[col * n + col]);
-            for (int r = col + 1; r < n; ++r) {
-                const double v = fabs(A[r * n + col]);
-                if (v > bv) { bv = v; best = r; }
-            }
-            piv = best;
-            pval = A[best * n + col];
-            if (bv == 0.0) *singular = 1;
-        }
-        __syncthreads();
-        if (pval == 0.0) return;
-        if (piv != col) {
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                double a = A[col * n + k]; A[col * n + k] = A[piv * n + k]; A[piv * n + k] = a;
-                double x = X[col * n + k]; X[col * n + k] = X[piv * n + k]; X[piv * n + k] = x;
-            }
-        }
-        __syncthreads();
-        const double inv = 1.0 / pval;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            A[col * n + k] *= inv;
-            X[col * n + k] *= inv;
-        }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-            const int r = idx / n, k = idx % n;
-            if (r == col) continue;
-            const double fct = A[r * n + col];
-            if (k == col) continue;
-            A[r * n + k] -= fct * A[col * n + k];
-            X[r * n + k] -= fct * X[col * n + k];
-        }
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            if (r == col) continue;
-            const double fct = A[r * n + col];
-            X[r * n + col] -= fct * X[col * n + col];
-            A[r * n + col] = 0.0;
-        }
-        __syncthreads();
-    }
-}
-
-template <typename T>
-__global__ void k_bottom_gather(Lv<T> L, const int* __restrict__ dofs, int nfree, int ntot, const T* __restrict__ f,
-                                double* __restrict__ b) {
-    if (L.active && *L.active == 0) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ntot) return;
-    b[i] = i < nfree ? (double)f[dofs[i]] : 0.0;
-}
-
-template <typename T>
-__global__ void k_bottom_matvec(Lv<T> L, const int* __restrict__ dofs, int nfree, int ntot,
-                                const double* __restrict__ Ainv, const double* __restrict__ b, T* __restrict__ u) {
-    if (L.active && *L.active == 0) return;
-    const int row = blockIdx.x;
-    if (row >= nfree) return;
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < ntot; k += blockDim.x) acc += Ainv[(size_t)row * ntot + k] * b[k];
-    __shared__ double sm[kBlock / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) s += sm[w];
-        u[dofs[row]] = (T)s;
-    }
-}
-
-template <typename T>
-__global__ void k_zero(T* __restrict__ a, size_t n) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = T(0);
-}
-
-// ---------------------------------------------------------------------------
-// reductions
-// ---------------------------------------------------------------------------
-// Deterministic sum of the residual partials; with free rigid modes also
-//   W^T r = basis^T mom,  dlam = G^-1 W^T r,  lam += dlam,
-//   a_lam = basis lam, a_dlam = basis dlam (the loads as t + w x d),
-//   ||r - dlam.W||^2 = ||r||^2 - 2 dlam.W^T r + dlam^T G dlam.
-__global__ void k_finalize(const double* __restrict__ partials, int nblocks, NullInfo nf,
-                           const double* __restrict__ Ginv, const double* __restrict__ G,
-                           double* __restrict__ lam, double* __restrict__ dlam, double* __restrict__ alam,
-                           double* __restrict__ adlam, double* __restrict__ out, int update_lam, BatchFlags bf) {
-    if (bf.active && *bf.active == 0) return;
-    __shared__ double sm[kBlock][7];
-    const int width = nf.m > 0 ? 7 : 1;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-        for (int w = 0; w < width; ++w) acc[w] += partials[b * kPartialStride + w];
-    for (int w = 0; w < 7; ++w) sm[threadIdx.x][w] = acc[w];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int w = 0; w < width; ++w) sm[threadIdx.x][w] += sm[threadIdx.x + s][w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        double ss = sm[0][0];
-        if (nf.m > 0) {
-            double wtr[6], d[6];
-            for (int q = 0; q < nf.m; ++q) {
-                double v = 0.0;
-                for (int mo = 0; mo < 6; ++mo) v += nf.basis[mo][q] * sm[0][1 + mo];
-                wtr[q] = v;
-            }
-            for (int q = 0; q < nf.m; ++q) {
-                double v = 0.0;
-                for (int k = 0; k < nf.m; ++k) v += Ginv[q * nf.m + k] * wtr[k];
-                d[q] = v;
-            }
-            double c1 = 0.0, c2 = 0.0;
-            for (int q = 0; q < nf.m; ++q) {
-                c1 += d[q] * wtr[q];
-                for (int k = 0; k < nf.m; ++k) c2 += d[q] * G[q * nf.m + k] * d[k];
-            }
-            ss = ss - 2.0 * c1 + c2;
-            if (ss < 0.0) ss = 0.0;
-            for (int q = 0; q < nf.m; ++q) {
-                dlam[q] = d[q];
-                if (update_lam) lam[q] += d[q];
-            }
-            for (int mo = 0; mo < 6; ++mo) {
-                double a = 0.0, b = 0.0;
-                for (int q = 0; q < nf.m; ++q) {
-                    a += nf.basis[mo][q] * lam[q];
-                    b += nf.basis[mo][q] * d[q];
-                }
-                alam[mo] = a;
-                adlam[mo] = b;
-                ((float*)(alam + kLoadFloatOffset))[mo] = (float)a;
-                ((float*)(adlam + kLoadFloatOffset))[mo] = (float)b;
-            }
-        }
-        out[0] = ss;
-        if (bf.active) {
-            // batched solve: record the relative residual, stop this member when done
-            const double rel = bf.r0 > 0.0 ? sqrt(ss) / bf.r0 : 0.0;
-            const int k = *bf.count;
-            if (k < bf.hist_len) bf.hist[k] = rel;
-            *bf.count = k + 1;
-            if (!(rel > bf.tol) || k >= bf.max_cycles || !isfinite(rel)) *bf.active = 0;
-        }
-    }
-}
-
-__global__ void k_null_dots(Lv<double> L, NullInfo nf, const double* __restrict__ u, double* __restrict__ partials,
-                            int gram) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    int width = gram ? nf.m * nf.m : nf.m;
-    if (p < L.N) {
-        int c[3];
-        coords_of(p, L.n, c);
-        const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-        for (int i = 0; i < 3; ++i) {
-            if (row_type(L, ni, i) == ROW_DIRICHLET) continue;
-            if (gram) {
-                // only the upper triangle fits 7 slots for m <= 3; the host calls this
-                // once per row q for larger m (see launch_null_dots)
-            } else {
-                for (int q = 0; q < nf.m; ++q) acc[q] += null_vec(nf, q, i, c) * u[i * L.N + p];
-            }
-        }
-    }
-    block_reduce_store<7>(acc, width > 7 ? 7 : width, partials);
-}
-
-// W^T W row by row: column q0 of the Gram matrix
-__global__ void k_null_gram_row(Lv<double> L, NullInfo nf, int q0, double* __restrict__ partials) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (p < L.N) {
-        int c[3];
-        coords_of(p, L.n, c);
-        const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-        for (int i = 0; i < 3; ++i) {
-            if (row_type(L, ni, i) == ROW_DIRICHLET) continue;
-            const double w0 = null_vec(nf, q0, i, c);
-            for (int q = 0; q < nf.m; ++q) acc[q] += w0 * null_vec(nf, q, i, c);
-        }
-    }
-    block_reduce_store<7>(acc, nf.m, partials);
-}
-
-__global__ void k_sum_partials(const double* __restrict__ partials, int nblocks, int width, double* __restrict__ out) {
-    __shared__ double sm[kBlock][7];
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-        for (int w = 0; w < width; ++w) acc[w] += partials[b * kPartialStride + w];
-    for (int w = 0; w < 7; ++w) sm[threadIdx.x][w] = acc[w];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int w = 0; w < width; ++w) sm[threadIdx.x][w] += sm[threadIdx.x + s][w];
-        __syncthreads();
-    }
-    if (threadIdx.x < width) out[threadIdx.x] = sm[0][threadIdx.x];
-}
-
-__global__ void k_remove_null(Lv<double> L, NullInfo nf, const double* __restrict__ Ginv,
-                              const double* __restrict__ wtu, double* __restrict__ u) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.N) return;
-    double coef[6];
-    for (int q = 0; q < nf.m; ++q) {
-        double v = 0.0;
-        for (int k = 0; k < nf.m; ++k) v += Ginv[q * nf.m + k] * wtu[k];
-        coef[q] = v;
-    }
-    int c[3];
-    coords_of(p, L.n, c);
-    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-    for (int i = 0; i < 3; ++i)
-        if (row_type(L, ni, i) != ROW_DIRICHLET) u[i * L.N + p] -= null_combo(nf, coef, i, c);
-}
-
-
-// ---------------------------------------------------------------------------
-// block-structured AMR transfers (reflux-free coarse/fine treatment)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool amr_is_ghost(const AmrBox& b, const int n[3], const int c[3]) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        if (b.ghost[2 * d] && c[d] == 0) return true;
-        if (b.ghost[2 * d + 1] && c[d] == n[d] - 1) return true;
-    }
-    return false;
-}
-
-__global__ void k_amr_interp(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc, const double* __restrict__ cf,
-                             double* __restrict__ ff, int mode) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= Lf.N) return;
-    int c[3];
-    coords_of(p, Lf.n, c);
-    const bool ghost = amr_is_ghost(bf, Lf.n, c);
-    if ((mode == 0) != ghost) return;
-    int i0[3], i1[3];
-    double w1[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int g = bf.grid_lo[d] + c[d];
-        i0[d] = g / 2 - bc.grid_lo[d];
-        i1[d] = (g + 1) / 2 - bc.grid_lo[d];
-        w1[d] = (g & 1) ? 0.5 : 0.0;
-    }
-    const NodeInfo ni = node_info(Lf, c[0], c[1], c[2]);
-    for (int k = 0; k < 3; ++k) {
-        if (mode == 1 && row_type(Lf, ni, k) == ROW_DIRICHLET) continue;
-        const double* e = cf + (size_t)k * Lc.N;
-        double v = 0.0;
-        for (int bz = 0; bz < 2; ++bz) {
-            const double wz = bz ? w1[2] : 1.0 - w1[2];
-            if (wz == 0.0) continue;
-            for (int by = 0; by < 2; ++by) {
-                const double wy = by ? w1[1] : 1.0 - w1[1];
-                if (wy == 0.0) continue;
-                for (int bx = 0; bx < 2; ++bx) {
-                    const double wx = bx ? w1[0] : 1.0 - w1[0];
-                    if (wx == 0.0) continue;
-                    v += wx * wy * wz *
-                         e[lin(Lc, bx ? i1[0] : i0[0], by ? i1[1] : i0[1], bz ? i1[2] : i0[2])];
-                }
-            }
-        }
-        if (mode == 0) ff[(size_t)k * Lf.N + p] = v;
-        else ff[(size_t)k * Lf.N + p] += v;
-    }
-}
-
-// covered coarse box (in coarse local coordinates): coarse global I with 2I in [valid_lo, valid_hi]
-__device__ __forceinline__ void amr_cov_box(const AmrBox& bf, const AmrBox& bc, int lo[3], int cnt[3]) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int a = (bf.valid_lo[d] + 1) / 2, b = bf.valid_hi[d] / 2;
-        lo[d] = a - bc.grid_lo[d];
-        cnt[d] = b - a + 1;
-    }
-}
-
-__global__ void k_amr_inject(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc, const double* __restrict__ ffield,
-                             double* __restrict__ cfield) {
-    int lo[3], cnt[3];
-    amr_cov_box(bf, bc, lo, cnt);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt[0] * cnt[1] * cnt[2]) return;
-    const int cc[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
-    int fc[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) fc[d] = 2 * (bc.grid_lo[d] + cc[d]) - bf.grid_lo[d];
-    const int pc = lin(Lc, cc[0], cc[1], cc[2]), pf = lin(Lf, fc[0], fc[1], fc[2]);
-    for (int k = 0; k < 3; ++k) cfield[(size_t)k * Lc.N + pc] = ffield[(size_t)k * Lf.N + pf];
-}
-
-__global__ void k_amr_restrict(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc, const double* __restrict__ ffield,
-                               double* __restrict__ cfield, int K, int zero_dirichlet) {
-    int lo[3], cnt[3];
-    amr_cov_box(bf, bc, lo, cnt);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt[0] * cnt[1] * cnt[2]) return;
-    const int cc[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
-    double w[3][3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int fcg = 2 * (bc.grid_lo[d] + cc[d]);
-        double ww[3];
-        if (fcg == 0) { ww[0] = 0.0; ww[1] = 0.5; ww[2] = 0.5; }
-        else if (fcg == bf.count[d] - 1) { ww[0] = 0.5; ww[1] = 0.5; ww[2] = 0.0; }
-        else { ww[0] = 0.25; ww[1] = 0.5; ww[2] = 0.25; }
-        double sum = 0.0;
-        for (int o = -1; o <= 1; ++o) {
-            const int g = fcg + o;
-            if (g < bf.valid_lo[d] || g > bf.valid_hi[d]) ww[o + 1] = 0.0;
-            sum += ww[o + 1];
-        }
-        for (int o = 0; o < 3; ++o) w[d][o] = ww[o] / sum;
-    }
-    const NodeInfo nic = node_info(Lc, cc[0], cc[1], cc[2]);
-    const int pc = lin(Lc, cc[0], cc[1], cc[2]);
-    for (int k = 0; k < K; ++k) {
-        double acc = 0.0;
-        for (int oz = -1; oz <= 1; ++oz) {
-            if (w[2][oz + 1] == 0.0) continue;
-            for (int oy = -1; oy <= 1; ++oy) {
-                if (w[1][oy + 1] == 0.0) continue;
-                for (int ox = -1; ox <= 1; ++ox) {
-                    if (w[0][ox + 1] == 0.0) continue;
-                    const int fx = 2 * (bc.grid_lo[0] + cc[0]) + ox - bf.grid_lo[0];
-                    const int fy = 2 * (bc.grid_lo[1] + cc[1]) + oy - bf.grid_lo[1];
-                    const int fz = 2 * (bc.grid_lo[2] + cc[2]) + oz - bf.grid_lo[2];
-                    acc += w[0][ox + 1] * w[1][oy + 1] * w[2][oz + 1] * ffield[(size_t)k * Lf.N + lin(Lf, fx, fy, fz)];
-                }
-            }
-        }
-        if (zero_dirichlet && k < 3 && row_type(Lc, nic, k) == ROW_DIRICHLET) acc = 0.0;
-        cfield[(size_t)k * Lc.N + pc] = acc;
-    }
-}
-
-__global__ void k_amr_norm(Lv<double> L, AmrBox b, AmrBox cov, int has_cov, const double* __restrict__ res,
-                           double* __restrict__ partials) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (p < L.N) {
-        int c[3];
-        coords_of(p, L.n, c);
-        bool skip = amr_is_ghost(b, L.n, c);
-        if (!skip && has_cov) {
-            bool in = true;
-            for (int d = 0; d < 3; ++d) {
-                const int g2 = 2 * (b.grid_lo[d] + c[d]);
-                in &= (g2 >= cov.valid_lo[d] && g2 <= cov.valid_hi[d]);
-            }
-            skip = in;
-        }
-        if (!skip)
-            for (int k = 0; k < 3; ++k) {
-                const double r = res[(size_t)k * L.N + p];
-                acc[0] += r * r;
-            }
-    }
-    block_reduce_store<7>(acc, 1, partials);
-}
-
-__global__ void k_amr_add(Lv<double> L, AmrBox b, double* __restrict__ u, const double* __restrict__ cor) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.N) return;
-    int c[3];
-    coords_of(p, L.n, c);
-    if (amr_is_ghost(b, L.n, c)) return;
-    for (int k = 0; k < 3; ++k) u[(size_t)k * L.N + p] += cor[(size_t)k * L.N + p];
-}
-
-}  // namespace
 
 // ---------------------------------------------------------------------------
 // launchers
@@ -1319,25 +27,6 @@ void launch_rhs(const Lv<double>& L, const RhsInputs& in, const BoundaryData& bd
 void launch_dirichlet(const Lv<double>& L, const BoundaryData& bd, double* u, int keep_free, cudaStream_t s) {
     count_launch();
     k_dirichlet<<<blocks_for(L.N), kBlock, 0, s>>>(L, bd, u, keep_free);
-}
-
-template <typename T, int A>
-void launch_faces_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
-    const size_t n = face_count<T, A>(L);
-    if (!n) return;
-    count_launch();
-    if (L.K == 2) k_apply_face<T, 2, A><<<blocks_for(n), kBlock, 0, s>>>(L, u, out);
-    else k_apply_face<T, 21, A><<<blocks_for(n), kBlock, 0, s>>>(L, u, out);
-}
-
-template <typename T, int A>
-void launch_faces_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour, const NullInfo& nfv,
-                        const double* load, cudaStream_t s) {
-    const size_t n = face_count<T, A>(L);
-    if (!n) return;
-    count_launch();
-    if (L.K == 2) k_half_sweep_face<T, 2, A><<<blocks_for(n), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, load);
-    else k_half_sweep_face<T, 21, A><<<blocks_for(n), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, load);
 }
 
 template <typename T>
@@ -1359,55 +48,19 @@ void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
     }
 }
 
-template <typename T, typename TR>
-void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf, const double* lam, TR* r,
-                     double* partials, int* nblocks, cudaStream_t s) {
-    NullInfo nfv{};
-    if (nf) nfv = *nf;
-    const BndSegs sg = bnd_segs(L, kBlock);
-    const int nb = sg.f2 + blocks_for(interior_count(L));
-    if (nblocks) *nblocks = nb;
-    if (!nb) return;
-    count_launch();
-    if (partials) {
-        if (L.K == 2) k_residual<T, TR, 2, true, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
-        else if (L.divc) k_residual<T, TR, 21, true, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
-        else k_residual<T, TR, 21, true, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
-    } else {
-        if (L.K == 2) k_residual<T, TR, 2, false, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
-        else if (L.divc) k_residual<T, TR, 21, false, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
-        else k_residual<T, TR, 21, false, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
-    }
-}
-
-// ---- launch variants of the interior smoother and their tuning table -----------------
-// (threads per block, minimum resident blocks per SM) pairs; the second number
-// bounds the registers per thread and so trades registers for resident warps.
-// Variants 5 and 6 are the shared-memory tiled kernel (32 x 16 and 32 x 8 tiles, FP32
-// levels with FP32 moduli only); their pair holds (threads, resident blocks per SM).
-static const int kSweepVariants[kNumSweepVariants][2] = {{256, 1}, {256, 2}, {256, 3}, {256, 4}, {128, 8},
-                                                         {256, 1}, {128, 2}};
-constexpr int kFirstTiledVariant = 5;
-
+// ---- tuning table of the interior smoother (shared by all translation units) -----------
 static std::mutex g_tune_mu;
 static std::map<std::array<int, 6>, int> g_tune;
 
-template <typename T>
-static std::array<int, 6> tune_key(const Lv<T>& L) {
-    return {L.n[0], L.n[1], L.n[2], L.K, (int)sizeof(T), L.divc ? 1 : 0};
+int tune_lookup(const std::array<int, 6>& key, int fallback) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    return it == g_tune.end() ? fallback : it->second;
 }
 
-template <typename T>
-int sweep_variant_for(const Lv<T>& L) {
+void tune_store(const std::array<int, 6>& key, int v) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(tune_key(L));
-    return it == g_tune.end() ? kDefaultSweepVariant : it->second;
-}
-
-template <typename T>
-void set_sweep_variant(const Lv<T>& L, int v) {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[tune_key(L)] = v;
+    g_tune[key] = v;
 }
 
 int tune_table_dump(char* buf, int cap) {
@@ -1445,164 +98,6 @@ int tune_table_load(const char* text) {
     return count;
 }
 
-static int sm_count() {
-    static int n = [] {
-        int dev = 0, c = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-        return c > 0 ? c : 1;
-    }();
-    return n;
-}
-
-// z planes per block of the tiled smoother: the chunking with the fewest plane steps
-// per SM, counting whole waves of resident blocks and two prologue planes per block.
-static int tiled_zlen(int columns, int nzi, int per_sm) {
-    const long slots = (long)sm_count() * per_sm;
-    int best = nzi;
-    long best_cost = -1;
-    for (int zc = 1; zc <= nzi; ++zc) {
-        const int zl = (nzi + zc - 1) / zc;
-        if ((nzi + zl - 1) / zl != zc) continue;
-        const long blocks = (long)columns * zc;
-        const long cost = ((blocks + slots - 1) / slots) * (zl + 2);
-        if (best_cost < 0 || cost < best_cost) {
-            best_cost = cost;
-            best = zl;
-        }
-    }
-    return best;
-}
-
-template <int KIND, int TY>
-static void launch_tiled(const Lv<float>& L, const float* u_in, float* u_out, const float* f, int colour,
-                         const NullInfo& nfv, const double* lam, cudaStream_t s) {
-    using S = TiledShape<KIND, TY>;
-    static const bool attr = [] {
-        cudaFuncSetAttribute(k_half_sweep_tiled<KIND, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)S::SMEM);
-        return true;
-    }();
-    (void)attr;
-    int cnt[3];
-    for (int d = 0; d < 3; ++d) cnt[d] = L.per[d] ? L.n[d] : L.n[d] - 2;
-    const int gx = (cnt[0] + kTileX - 1) / kTileX, gy = (cnt[1] + TY - 1) / TY;
-    const int zl = tiled_zlen(gx * gy, cnt[2], TY <= 8 ? 2 : 1);
-    const dim3 grid(gx, gy, (cnt[2] + zl - 1) / zl);
-    k_half_sweep_tiled<KIND, TY><<<grid, 16 * TY, S::SMEM, s>>>(L, u_in, u_out, f, colour, nfv, lam, zl);
-}
-
-// The tiled kernel reads FP32 moduli planes directly: not for FP64 levels, FP16 moduli
-// or the precomputed modulus divergence.
-template <typename T>
-static bool variant_ok(const Lv<T>& L, int v) {
-    if (v < kFirstTiledVariant) return true;
-    return sizeof(T) == 4 && !L.modh && !L.divc;
-}
-
-// Edge, corner and face nodes of a half-sweep as launches of their own (with the tiled
-// interior kernel, whose grid is three-dimensional).
-template <typename T>
-static void launch_boundary_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
-                                  const NullInfo& nfv, const double* lam, cudaStream_t s) {
-    launch_faces_sweep<T, 0>(L, u_in, u_out, f, colour, nfv, lam, s);
-    launch_faces_sweep<T, 1>(L, u_in, u_out, f, colour, nfv, lam, s);
-    launch_faces_sweep<T, 2>(L, u_in, u_out, f, colour, nfv, lam, s);
-    if (L.nbnd) {
-        count_launch();
-        if (L.K == 2) k_half_sweep_bnd<T, 2><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
-        else k_half_sweep_bnd<T, 21><<<blocks_for((size_t)L.nbnd * 32), kBlock, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam);
-    }
-}
-
-// One half-sweep with interior shape v: the untiled shapes take every node in one
-// launch; the tiled ones launch the boundary nodes separately.
-template <typename T, int KIND, bool HM>
-void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
-                       const NullInfo& nfv, const double* lam, cudaStream_t s) {
-    if constexpr (sizeof(T) == 4 && !HM) {
-        if (v >= kFirstTiledVariant && variant_ok(L, v)) {
-            if (np) {
-                count_launch();
-                if (v == kFirstTiledVariant) launch_tiled<KIND, 16>(L, u_in, u_out, f, colour, nfv, lam, s);
-                else launch_tiled<KIND, 8>(L, u_in, u_out, f, colour, nfv, lam, s);
-            }
-            launch_boundary_sweep(L, u_in, u_out, f, colour, nfv, lam, s);
-            return;
-        }
-    }
-    if (v >= kFirstTiledVariant) v = kDefaultSweepVariant;
-    const int bs = kSweepVariants[v][0];
-    const BndSegs sg = bnd_segs(L, bs);
-    const int nb = sg.f2 + (int)((np + bs - 1) / bs);
-    if (!nb) return;
-    count_launch();
-    switch (v) {
-        case 0: k_half_sweep_int<T, KIND, HM, 256, 1><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-        case 1: k_half_sweep_int<T, KIND, HM, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-        case 2: k_half_sweep_int<T, KIND, HM, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-        case 3: k_half_sweep_int<T, KIND, HM, 256, 4><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-        default: k_half_sweep_int<T, KIND, HM, 128, 8><<<nb, 128, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-    }
-}
-
-// Time every variant of the interior half-sweep on one level (buffers as given) and
-// keep the fastest in the tuning table.  Returns the chosen variant.
-template <typename T>
-int tune_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, cudaStream_t s, float* ms_out) {
-    const size_t np = interior_pairs(L);
-    if (!np) return kDefaultSweepVariant;
-    NullInfo nfv{};
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    int best = kDefaultSweepVariant;
-    float best_ms = 1e30f;
-    for (int v = 0; v < kNumSweepVariants; ++v) {
-        if (!variant_ok(L, v)) {
-            if (ms_out) ms_out[v] = -1.f;
-            continue;
-        }
-        auto run = [&]() {
-            if (L.K == 2) sweep_int_variant<T, 2, false>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
-            else if (L.divc) sweep_int_variant<T, 21, true>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
-            else sweep_int_variant<T, 21, false>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
-        };
-        run();
-        cudaEventRecord(a, s);
-        const int reps = 5;
-        for (int r = 0; r < reps; ++r) run();
-        cudaEventRecord(b, s);
-        cudaEventSynchronize(b);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        ms /= reps;
-        if (ms_out) ms_out[v] = ms;
-        if (cudaGetLastError() == cudaSuccess && ms < best_ms) {
-            best_ms = ms;
-            best = v;
-        }
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    set_sweep_variant(L, best);
-    return best;
-}
-
-template int tune_sweep<float>(const Lv<float>&, const float*, float*, const float*, cudaStream_t, float*);
-template int tune_sweep<double>(const Lv<double>&, const double*, double*, const double*, cudaStream_t, float*);
-
-template <typename T>
-void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour, const NullInfo* nf,
-                       const double* lam, cudaStream_t s) {
-    NullInfo nfv{};
-    if (nf) nfv = *nf;
-    const size_t np = interior_pairs(L);
-    const int v = sweep_variant_for(L);
-    if (L.K == 2) sweep_int_variant<T, 2, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-    else if (L.divc) sweep_int_variant<T, 21, true>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-    else sweep_int_variant<T, 21, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-}
 
 template <typename T>
 void launch_restrict(const Lv<T>& Lf, const Lv<T>& Lc, const T* r, T* fc, const NullInfo* nf, const double* dlam,
@@ -1630,14 +125,18 @@ void launch_divc(const Lv<double>& L, double* M, cudaStream_t s) {
     k_divc<double><<<blocks_for(L.N), kBlock, 0, s>>>(L, M);
 }
 
-void launch_to_half(const double* in, __half* out, size_t n, cudaStream_t s) {
-    count_launch();
-    k_to_half<<<blocks_for(n), kBlock, 0, s>>>(in, out, n);
+size_t moduli_copy_entries(int N, int K, bool half) {
+    return half ? (size_t)N * mod_record(K) : (size_t)((N + 31) / 32) * 32 * K;
 }
 
-void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s) {
+void launch_moduli_copy(const double* in, float* out, int N, int K, cudaStream_t s) {
     count_launch();
-    k_to_float<<<blocks_for(n), kBlock, 0, s>>>(in, out, n);
+    k_to_moduli_copy<float><<<blocks_for(moduli_copy_entries(N, K, false)), kBlock, 0, s>>>(in, out, N, K);
+}
+
+void launch_moduli_copy(const double* in, __half* out, int N, int K, cudaStream_t s) {
+    count_launch();
+    k_to_moduli_copy<__half><<<blocks_for(moduli_copy_entries(N, K, true)), kBlock, 0, s>>>(in, out, N, K);
 }
 
 void launch_add_correction(const Lv<double>& L, double* u, const float* e, cudaStream_t s) {
@@ -1753,16 +252,6 @@ void launch_amr_add(const Lv<double>& L, const AmrBox& b, double* u, const doubl
 // explicit instantiations
 template void launch_apply<double>(const Lv<double>&, const double*, double*, cudaStream_t);
 template void launch_apply<float>(const Lv<float>&, const float*, float*, cudaStream_t);
-template void launch_residual<double, double>(const Lv<double>&, const double*, const double*, const NullInfo*,
-                                              const double*, double*, double*, int*, cudaStream_t);
-template void launch_residual<double, float>(const Lv<double>&, const double*, const double*, const NullInfo*,
-                                             const double*, float*, double*, int*, cudaStream_t);
-template void launch_residual<float, float>(const Lv<float>&, const float*, const float*, const NullInfo*,
-                                            const double*, float*, double*, int*, cudaStream_t);
-template void launch_half_sweep<double>(const Lv<double>&, const double*, double*, const double*, int,
-                                        const NullInfo*, const double*, cudaStream_t);
-template void launch_half_sweep<float>(const Lv<float>&, const float*, float*, const float*, int, const NullInfo*,
-                                       const double*, cudaStream_t);
 template void launch_restrict<double>(const Lv<double>&, const Lv<double>&, const double*, double*, const NullInfo*,
                                       const double*, cudaStream_t);
 template void launch_restrict<float>(const Lv<float>&, const Lv<float>&, const float*, float*, const NullInfo*,

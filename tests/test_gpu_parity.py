@@ -250,7 +250,9 @@ def test_autotuned_launch_shapes_do_not_change_results(E, ctx):
     before = g.solve(precision=E.MIXED, rel_tol=0.0, fixed_cycles=3)
     ub = g.displacement()
     times = g.autotune()
-    assert len(times) == E.NUM_SWEEP_VARIANTS and all(t > 0 for t in times)
+    # the untiled shapes always apply; a tiled one reports -1 where it does not
+    assert len(times) == E.NUM_SWEEP_VARIANTS and all(t > 0 for t in times[:5])
+    assert all(t > 0 or t == -1 for t in times)
     assert len(E.autotune_dump().strip().splitlines()) >= 1
     after = g.solve(precision=E.MIXED, rel_tol=0.0, fixed_cycles=3)
     assert np.array_equal(ub, g.displacement())
