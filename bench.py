@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 METRIC = "Solves/s at 1e-8 rel. residual, mixed vs FP64; stencil HBM GB/s; p99 latency"
 UNIT = "solves/s"
 FALLBACK_HBM_GBS = 6800.0
+# DRAM read + write bytes per node of one finest-level FP32 half-sweep launch, per
+# smoother shape (autotuner index), from one ncu capture of that shape on the 129^3
+# polycrystal; scaled by the node count to the benchmarked grid.
+SWEEP32_TRAFFIC_B_PER_NODE = {1: 145.4, 2: 153.2}
 # nominal FP64 vector throughput of the part (1.25 TFLOP/s dense FP64)
 NOMINAL_FP64_TFLOPS = 1.25
 
@@ -343,8 +347,14 @@ def main():
     else:
         bpn = alg_bytes_per_node(dom, K)
         achieved = bpn * N / avg_s / 1e9
+        traffic = None
+        if dom == "sweep32" and K == 21:
+            key = f"{p.n[0]} {p.n[1]} {p.n[2]} 21 4 0 "
+            shape = [int(l.split()[-1]) for l in E.autotune_dump().splitlines() if l.startswith(key)]
+            if shape and shape[0] in SWEEP32_TRAFFIC_B_PER_NODE:
+                traffic = SWEEP32_TRAFFIC_B_PER_NODE[shape[0]] * N
         roof = {"kernel": f"{dom} (finest level)", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                 "peak_source": f"{peak_kind} copy bandwidth", "launches": cnt, "avg_ms": avg_s * 1e3}
     kernels = {}
     for name, (ms_k, cnt_k) in prof.items():

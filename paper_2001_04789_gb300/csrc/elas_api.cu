@@ -85,6 +85,8 @@ struct Level {
     __half* mod16 = nullptr;   // FP16 moduli of the FP32 V-cycle (half_moduli grids)
     int* bnd = nullptr;   // boundary-plane nodes of this level
     int nbnd = 0;
+    double* bcoef64 = nullptr;   // edge and corner row coefficients (kEdgeCoef per node)
+    float* bcoef32 = nullptr;
     NullInfo nf{};
 };
 
@@ -193,6 +195,7 @@ void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int 
     L.active = nullptr;
     L.modh = nullptr;
     L.mlay = kModPlanes;
+    L.bcoef = nullptr;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -434,6 +437,14 @@ int setup(elas_grid g) {
             CHECK_LAUNCH(c);
         }
     }
+    // coefficients of the edge and corner rows (they depend on moduli and boundary types)
+    for (int l = 0; l < nl; ++l) {
+        Level& v = g->lv[l];
+        if (!v.nbnd) continue;
+        launch_edge_coef<double>(v.L64, v.bcoef64, s);
+        if (v.bcoef32) launch_edge_coef<float>(v.L32, v.bcoef32, s);
+        CHECK_LAUNCH(c);
+    }
     // equilibrating load of the finest level: G = W^T W, Ginv
     Level& L0 = g->lv[0];
     const int m = L0.nf.m;
@@ -553,9 +564,9 @@ int remove_rigid(elas_grid g) {
     int nb = 0;
     launch_null_dots(L0.L64, L0.nf, L0.u, g->partials, &nb, 0, c->stream);
     CHECK_LAUNCH(c);
-    launch_sum_partials(g->partials, nb, L0.nf.m, g->status + 8, c->stream);
+    launch_sum_partials(g->partials, nb, 6, g->status + 8, c->stream);
     CHECK_LAUNCH(c);
-    launch_remove_null(L0.L64, L0.nf, g->Ginv, g->status + 8, L0.u, c->stream);
+    launch_remove_null(L0.L64, L0.nf, g->Ginv, g->status + 8, g->status + 16, L0.u, c->stream);
     CHECK_LAUNCH(c);
     return ELAS_OK;
 }
@@ -597,6 +608,8 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     v.nbnd = (int)b.size();
     if (v.nbnd) {
         if ((rc = galloc(g, &v.bnd, b.size()))) return rc;
+        if ((rc = galloc(g, &v.bcoef64, b.size() * kEdgeCoef))) return rc;
+        if (mixed && (rc = galloc(g, &v.bcoef32, b.size() * kEdgeCoef))) return rc;
         elas_ctx c = g->ctx;
         CUDA_TRY(c, cudaMemcpyAsync(v.bnd, b.data(), sizeof(int) * b.size(), cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -619,6 +632,8 @@ void refresh_lv(elas_grid g) {
         v.L64.mod = v.mod64;
         v.L32.mod = v.mod32;
         v.L64.bnodes = v.L32.bnodes = v.bnd;
+        v.L64.bcoef = v.bcoef64;
+        v.L32.bcoef = v.bcoef32;
         v.L64.nbnd = v.L32.nbnd = v.nbnd;
         v.L64.divc = v.divc;
         v.L32.modh = v.mod16;
@@ -731,6 +746,7 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
         const size_t N = (size_t)n[0] * n[1] * n[2];
         total += N * 8 * (K + 12 + (K == 21 ? 18 : 0));
         if (d->mixed) total += (d->half_moduli ? 2 : 4) * moduli_copy_entries((int)N, K, d->half_moduli) + N * 48;
+        total += (size_t)4 * (n[0] + n[1] + n[2]) * kEdgeCoef * (d->mixed ? 12 : 8);   // edge rows
     }
     const size_t N0 = (size_t)d->n[0] * d->n[1] * d->n[2];
     total += N0 * 8 * 9;   // eigenstrain + body force when given

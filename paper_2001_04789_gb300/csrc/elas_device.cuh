@@ -45,7 +45,16 @@ struct Lv {
     const int* __restrict__ active;
     // optional FP16 copy of the moduli read by FP32 kernels instead of `mod`
     const __half* __restrict__ modh;
+    // optional coefficients of the edge and corner rows: for bnodes[w], kEdgeCoef entries
+    // [row i][slot][component k] (see edge_slot_node), so a row is a 27-slot dot product
+    const T* __restrict__ bcoef;
 };
+
+// Edge and corner rows reach 3 nodes per direction: c-1, c, c+1 where the node is not on a
+// boundary plane of that direction (wrapped when periodic), c, c+s, c+2s (s inward) where
+// it is.  Slot t0 + 3 t1 + 9 t2 names one of the 27; the slot of the node itself is
+// edge_center_slot.  Coefficients per node: 3 rows x 27 slots x 3 components.
+constexpr int kEdgeCoef = 243;
 
 // Moduli layouts.  Planes: component c of node q at c * N + q.  Blocked (FP32 copies):
 // the nodes are cut into blocks of 32 consecutive linear indices and each block stores
@@ -186,6 +195,26 @@ __device__ __forceinline__ int row_type(const Lv<T>& L, const NodeInfo& ni, int 
 template <typename T>
 __device__ __forceinline__ int lin(const Lv<T>& L, int x, int y, int z) {
     return x + L.n[0] * (y + L.n[1] * z);
+}
+
+// Node coordinates of slot `slot` of a boundary node (see kEdgeCoef).
+template <typename T>
+__device__ __forceinline__ void edge_slot_node(const Lv<T>& L, const NodeInfo& ni, int slot, int a[3]) {
+    const int t[3] = {slot % 3, (slot / 3) % 3, slot / 9};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (ni.side[d] == 0) {
+            int v = ni.c[d] + t[d] - 1;
+            if (L.per[d]) v = v < 0 ? v + L.n[d] : (v >= L.n[d] ? v - L.n[d] : v);
+            a[d] = v;
+        } else {
+            a[d] = ni.c[d] - ni.side[d] * t[d];
+        }
+    }
+}
+
+__device__ __forceinline__ int edge_center_slot(const NodeInfo& ni) {
+    return (ni.side[0] == 0 ? 1 : 0) + 3 * (ni.side[1] == 0 ? 1 : 0) + 9 * (ni.side[2] == 0 ? 1 : 0);
 }
 
 // Coordinate c + s e_d with periodic wrap.
@@ -785,14 +814,6 @@ __device__ __forceinline__ T rigid_load(const NullInfo& nf, const double* __rest
     else if (comp == 1) v = xadd(at[1], xsub(xmul(w2, d0), xmul(w0, d2)));
     else v = xadd(at[2], xsub(xmul(w0, d1), xmul(w1, d0)));
     return T(v);
-}
-
-// sum_q coef[q] W_q(c): the equilibrating load at a non-Dirichlet row.
-__device__ __forceinline__ double null_combo(const NullInfo& nf, const double* coef, int c, const int xyz[3]) {
-    double v = 0.0;
-#pragma unroll 1
-    for (int q = 0; q < nf.m; ++q) v += coef[q] * null_vec(nf, q, c, xyz);
-    return v;
 }
 
 }  // namespace elas

@@ -75,6 +75,9 @@ void launch_restrict_moduli(const Lv<T>& Lf, const Lv<T>& Lc, const T* mf, T* mc
 // FP64 moduli planes (K x N) -> the FP32 blocked copy or the FP16 node records of an FP32
 // level (entries to allocate: moduli_copy_entries).
 size_t moduli_copy_entries(int N, int K, bool half);
+// Coefficients of the level's edge and corner rows (L.nbnd x kEdgeCoef) into out.
+template <typename T>
+void launch_edge_coef(const Lv<T>& L, T* out, cudaStream_t s);
 void launch_moduli_copy(const double* in, float* out, int N, int K, cudaStream_t s);
 void launch_moduli_copy(const double* in, __half* out, int N, int K, cudaStream_t s);
 // M_iV = sum_j d_j C_(ij)V (18 planes) of a general-moduli FP64 level (setup)
@@ -107,13 +110,17 @@ void launch_finalize(const double* partials, int nblocks, const NullInfo& nf, co
                      const double* G, double* lam, double* dlam, double* alam, double* adlam, double* out,
                      int update_lam, cudaStream_t s, BatchFlags bflags = BatchFlags{});
 
-// W^T u partials (and W^T W at setup when gram != 0).
+// Block partials of the six raw rigid-motion moments of u (sum u, sum d x u over the
+// non-Dirichlet rows); with gram = q + 1, column q of W^T W (setup).
 void launch_null_dots(const Lv<double>& L, const NullInfo& nf, const double* u, double* partials,
                       int* nblocks, int gram, cudaStream_t s);
 void launch_sum_partials(const double* partials, int nblocks, int width, double* out, cudaStream_t s);
-// u -= sum_q coef[q] W_q, coef = Ginv (W^T u) computed on the device
-void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* Ginv, const double* wtu,
-                        double* u, cudaStream_t s);
+// u -= sum_q coef[q] W_q with coef = Ginv (W^T u), from the six raw moments of u
+// (sum u, sum d x u; launch_null_dots + launch_sum_partials with width 6): the motion
+// (t, w) = basis coef is formed on the device in `motion` (6 doubles), then
+// u -= t + w x d on the non-Dirichlet rows.
+void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* Ginv, const double* moment,
+                        double* motion, double* u, cudaStream_t s);
 
 // ---- block-structured AMR transfers ------------------------------------------------
 // Placement of one AMR level's grid in its level's global node index space.

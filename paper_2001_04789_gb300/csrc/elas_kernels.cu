@@ -125,6 +125,17 @@ void launch_divc(const Lv<double>& L, double* M, cudaStream_t s) {
     k_divc<double><<<blocks_for(L.N), kBlock, 0, s>>>(L, M);
 }
 
+template <typename T>
+void launch_edge_coef(const Lv<T>& L, T* out, cudaStream_t s) {
+    const size_t n = (size_t)L.nbnd * kEdgeCoef;
+    if (!n) return;
+    count_launch();
+    if (L.K == 2) k_edge_coef<T, 2><<<blocks_for(n), kBlock, 0, s>>>(L, out);
+    else k_edge_coef<T, 21><<<blocks_for(n), kBlock, 0, s>>>(L, out);
+}
+template void launch_edge_coef<double>(const Lv<double>&, double*, cudaStream_t);
+template void launch_edge_coef<float>(const Lv<float>&, float*, cudaStream_t);
+
 size_t moduli_copy_entries(int N, int K, bool half) {
     return half ? (size_t)N * mod_record(K) : (size_t)((N + 31) / 32) * 32 * K;
 }
@@ -182,7 +193,7 @@ void launch_finalize(const double* partials, int nblocks, const NullInfo& nf, co
                      double* lam, double* dlam, double* alam, double* adlam, double* out, int update_lam,
                      cudaStream_t s, BatchFlags bflags) {
     count_launch();
-    k_finalize<<<1, kBlock, 0, s>>>(partials, nblocks, nf, Ginv, G, lam, dlam, alam, adlam, out, update_lam, bflags);
+    k_finalize<<<1, kSumThreads, 0, s>>>(partials, nblocks, nf, Ginv, G, lam, dlam, alam, adlam, out, update_lam, bflags);
 }
 
 void launch_null_dots(const Lv<double>& L, const NullInfo& nf, const double* u, double* partials, int* nblocks,
@@ -201,13 +212,14 @@ void launch_null_dots(const Lv<double>& L, const NullInfo& nf, const double* u, 
 
 void launch_sum_partials(const double* partials, int nblocks, int width, double* out, cudaStream_t s) {
     count_launch();
-    k_sum_partials<<<1, kBlock, 0, s>>>(partials, nblocks, width, out);
+    k_sum_partials<<<1, kSumThreads, 0, s>>>(partials, nblocks, width, out);
 }
 
-void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* Ginv, const double* wtu, double* u,
-                        cudaStream_t s) {
-    count_launch();
-    k_remove_null<<<blocks_for(L.N), kBlock, 0, s>>>(L, nf, Ginv, wtu, u);
+void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* Ginv, const double* moment,
+                        double* motion, double* u, cudaStream_t s) {
+    count_launch(2);
+    k_null_motion<<<1, 32, 0, s>>>(nf, Ginv, moment, motion);
+    k_remove_null<<<blocks_for(L.N), kBlock, 0, s>>>(L, nf, motion, u);
 }
 
 void launch_amr_interp(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,

@@ -53,6 +53,48 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[MAXW], int width,
     }
 }
 
+// Fixed-order sum of the 7-wide block partials by one block of kSumThreads threads:
+// each thread keeps four records in flight per step (the loads are independent, so the
+// sum is limited by bandwidth rather than by one load's latency), then a warp-shuffle
+// tree and a second one over the warps.  The result lands in sm[0][0..6].
+constexpr int kSumThreads = 512;
+__device__ __forceinline__ void sum_partials_block(const double* __restrict__ partials, int nblocks,
+                                                   double (&sm)[kSumThreads / 32][7]) {
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int b0 = threadIdx.x; b0 < nblocks; b0 += 4 * kSumThreads) {
+        double v[4][7];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int b = b0 + k * kSumThreads;
+#pragma unroll
+            for (int w = 0; w < 7; ++w) v[k][w] = b < nblocks ? partials[(size_t)b * kPartialStride + w] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int w = 0; w < 7; ++w) acc[w] += v[k][w];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int w = 0; w < 7; ++w) {
+        double x = acc[w];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sm[warp][w] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int w = 0; w < 7; ++w) {
+            double x = lane < kSumThreads / 32 ? sm[lane][w] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) sm[0][w] = x;
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __device__ __forceinline__ T face_datum(const BoundaryData& bd, int f, int c, int p, int N) {
     return bd.face[f] ? T(bd.face[f][c * N + p]) : T(bd.uniform[f][c]);
@@ -268,6 +310,34 @@ __device__ __forceinline__ void residual_int_body(const Lv<T>& L, const T* __res
     residual_store<T, TR, NORM>(L, f, nf, lam, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
 }
 
+// Rows of an edge or corner node from its stored coefficients (L.bcoef): lanes 0-26 take
+// one slot each (three displacement loads, nine multiply-adds), then a fixed shuffle
+// tree sums the lanes.  Every lane returns the three rows.
+template <typename T>
+__device__ __forceinline__ void edge_rows_coef(const Lv<T>& L, const T* __restrict__ u, const NodeInfo& ni,
+                                               const T* __restrict__ cf, int lane, T v[3]) {
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    if (lane < 27) {
+        int a[3];
+        edge_slot_node(L, ni, lane, a);
+        const int q = lin(L, a[0], a[1], a[2]);
+        const T u0 = u[q], u1 = u[L.N + q], u2 = u[2 * L.N + q];
+        const T* c0 = cf + 3 * lane;
+        s0 = xfma(c0[2], u2, xfma(c0[1], u1, xmul(c0[0], u0)));
+        s1 = xfma(c0[83], u2, xfma(c0[82], u1, xmul(c0[81], u0)));
+        s2 = xfma(c0[164], u2, xfma(c0[163], u1, xmul(c0[162], u0)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 = xadd(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+        s1 = xadd(s1, __shfl_xor_sync(0xffffffffu, s1, o));
+        s2 = xadd(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+    }
+    v[0] = s0;
+    v[1] = s1;
+    v[2] = s2;
+}
+
 template <typename T, typename TR, int KIND, bool NORM>
 __device__ __forceinline__ void residual_bnd_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
                                                   const NullInfo& nf, const double* __restrict__ lam,
@@ -279,13 +349,17 @@ __device__ __forceinline__ void residual_bnd_body(const Lv<T>& L, const T* __res
     const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
     int types[3];
     for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
-    T val = T(0);
-    if (lane < 3) {
-        UField<T> uf{u, L.N, L.n[0], L.n[1]};
-        val = boundary_row<T, KIND>(L, uf, ni, lane, types[lane]);
-    }
     T v[3];
-    for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, i);
+    if (L.bcoef) {
+        edge_rows_coef<T>(L, u, ni, L.bcoef + (size_t)w * kEdgeCoef, lane, v);
+    } else {
+        T val = T(0);
+        if (lane < 3) {
+            UField<T> uf{u, L.N, L.n[0], L.n[1]};
+            val = boundary_row<T, KIND>(L, uf, ni, lane, types[lane]);
+        }
+        for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, i);
+    }
     if (lane == 0) residual_store<T, TR, NORM>(L, f, nf, lam, c, p, types, v, r, acc);
 }
 
@@ -513,17 +587,27 @@ __device__ __forceinline__ void sweep_bnd_body(const Lv<T>& L, const T* __restri
     const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
     int types[3];
     for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
-    T val = T(0);
-    if (lane < 9) {
-        val = boundary_block_entry<T, KIND>(L, ni, types, lane / 3, lane % 3);
-    } else if (lane < 12) {
-        UField<T> uf{u, N, L.n[0], L.n[1]};
-        val = boundary_row<T, KIND>(L, uf, ni, lane - 9, types[lane - 9]);
-    }
     T B[3][3], v[3];
-    for (int q = 0; q < 9; ++q) B[q / 3][q % 3] = __shfl_sync(0xffffffffu, val, q);
-    for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, 9 + i);
-    if (lane != 0) return;
+    if (L.bcoef) {
+        // stored rows; the diagonal block is the node's own slot
+        const T* cf = L.bcoef + (size_t)w * kEdgeCoef;
+        edge_rows_coef<T>(L, u, ni, cf, lane, v);
+        if (lane != 0) return;
+        const int cs = edge_center_slot(ni);
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) B[i][k] = cf[81 * i + 3 * cs + k];
+    } else {
+        T val = T(0);
+        if (lane < 9) {
+            val = boundary_block_entry<T, KIND>(L, ni, types, lane / 3, lane % 3);
+        } else if (lane < 12) {
+            UField<T> uf{u, N, L.n[0], L.n[1]};
+            val = boundary_row<T, KIND>(L, uf, ni, lane - 9, types[lane - 9]);
+        }
+        for (int q = 0; q < 9; ++q) B[q / 3][q % 3] = __shfl_sync(0xffffffffu, val, q);
+        for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, 9 + i);
+        if (lane != 0) return;
+    }
     T r[3], d[3];
     for (int i = 0; i < 3; ++i) {
         if (types[i] == ROW_DIRICHLET) {
@@ -657,6 +741,24 @@ inline size_t face_count(const Lv<T>& L) {
     int nf, ns;
     face_extent<T, A>(L, nf, ns);
     return (size_t)2 * nf * ns;
+}
+
+// Coefficients of the edge and corner rows: entry e = (w, i, slot, k) is row i of node
+// bnodes[w] applied to the unit vector of component k at the slot's node, i.e. the
+// operator's matrix entry (the generic rows are linear in u).  Setup only.
+template <typename T, int KIND>
+__global__ void k_edge_coef(Lv<T> L, T* __restrict__ out) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)L.nbnd * kEdgeCoef) return;
+    const int w = (int)(e / kEdgeCoef), rem = (int)(e % kEdgeCoef);
+    const int i = rem / 81, slot = (rem % 81) / 3, k = rem % 3;
+    int c[3];
+    coords_of(L.bnodes[w], L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    UProbe<T> probe;
+    probe.kk = k;
+    edge_slot_node(L, ni, slot, probe.c0);
+    out[e] = boundary_row<T, KIND>(L, probe, ni, i, row_type(L, ni, i));
 }
 
 // ---- one launch per half-sweep / residual ---------------------------------------------
@@ -1032,18 +1134,8 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, Nul
                            double* __restrict__ lam, double* __restrict__ dlam, double* __restrict__ alam,
                            double* __restrict__ adlam, double* __restrict__ out, int update_lam, BatchFlags bf) {
     if (bf.active && *bf.active == 0) return;
-    __shared__ double sm[kBlock][7];
-    const int width = nf.m > 0 ? 7 : 1;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-        for (int w = 0; w < width; ++w) acc[w] += partials[b * kPartialStride + w];
-    for (int w = 0; w < 7; ++w) sm[threadIdx.x][w] = acc[w];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int w = 0; w < width; ++w) sm[threadIdx.x][w] += sm[threadIdx.x + s][w];
-        __syncthreads();
-    }
+    __shared__ double sm[kSumThreads / 32][7];
+    sum_partials_block(partials, nblocks, sm);
     if (threadIdx.x == 0) {
         double ss = sm[0][0];
         if (nf.m > 0) {
@@ -1104,17 +1196,23 @@ __global__ void k_null_dots(Lv<double> L, NullInfo nf, const double* __restrict_
         int c[3];
         coords_of(p, L.n, c);
         const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
-        for (int i = 0; i < 3; ++i) {
-            if (row_type(L, ni, i) == ROW_DIRICHLET) continue;
-            if (gram) {
-                // only the upper triangle fits 7 slots for m <= 3; the host calls this
-                // once per row q for larger m (see launch_null_dots)
-            } else {
-                for (int q = 0; q < nf.m; ++q) acc[q] += null_vec(nf, q, i, c) * u[i * L.N + p];
-            }
-        }
+        // the six raw rigid-motion moments of u over its non-Dirichlet rows: sum u and
+        // sum d x u (d = x - ctr); W_q . u = sum_mode basis[mode][q] * moment[mode]
+        double um[3];
+        for (int i = 0; i < 3; ++i) um[i] = row_type(L, ni, i) == ROW_DIRICHLET ? 0.0 : u[i * L.N + p];
+        const double d0 = nf.off[0] + nf.h[0] * c[0];
+        const double d1 = nf.off[1] + nf.h[1] * c[1];
+        const double d2 = nf.off[2] + nf.h[2] * c[2];
+        acc[0] = um[0];
+        acc[1] = um[1];
+        acc[2] = um[2];
+        acc[3] = d1 * um[2] - d2 * um[1];
+        acc[4] = d2 * um[0] - d0 * um[2];
+        acc[5] = d0 * um[1] - d1 * um[0];
     }
-    block_reduce_store<7>(acc, width > 7 ? 7 : width, partials);
+    (void)gram;
+    (void)width;
+    block_reduce_store<7>(acc, 6, partials);
 }
 #endif
 
@@ -1139,37 +1237,49 @@ __global__ void k_null_gram_row(Lv<double> L, NullInfo nf, int q0, double* __res
 
 #ifdef ELAS_KERNELS_TU
 __global__ void k_sum_partials(const double* __restrict__ partials, int nblocks, int width, double* __restrict__ out) {
-    __shared__ double sm[kBlock][7];
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-        for (int w = 0; w < width; ++w) acc[w] += partials[b * kPartialStride + w];
-    for (int w = 0; w < 7; ++w) sm[threadIdx.x][w] = acc[w];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int w = 0; w < width; ++w) sm[threadIdx.x][w] += sm[threadIdx.x + s][w];
-        __syncthreads();
-    }
+    __shared__ double sm[kSumThreads / 32][7];
+    sum_partials_block(partials, nblocks, sm);
     if (threadIdx.x < width) out[threadIdx.x] = sm[0][threadIdx.x];
 }
 #endif
 
 #ifdef ELAS_KERNELS_TU
-__global__ void k_remove_null(Lv<double> L, NullInfo nf, const double* __restrict__ Ginv,
-                              const double* __restrict__ wtu, double* __restrict__ u) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.N) return;
-    double coef[6];
+// From the raw moments: W^T u = basis^T moment, coef = G^-1 W^T u, and the rigid motion
+// (t, w) = basis coef that sum_q coef_q W_q equals (one thread).
+__global__ void k_null_motion(NullInfo nf, const double* __restrict__ Ginv, const double* __restrict__ moment,
+                              double* __restrict__ motion) {
+    if (threadIdx.x != 0) return;
+    double wtu[6], coef[6];
+    for (int q = 0; q < nf.m; ++q) {
+        double v = 0.0;
+        for (int mo = 0; mo < 6; ++mo) v += nf.basis[mo][q] * moment[mo];
+        wtu[q] = v;
+    }
     for (int q = 0; q < nf.m; ++q) {
         double v = 0.0;
         for (int k = 0; k < nf.m; ++k) v += Ginv[q * nf.m + k] * wtu[k];
         coef[q] = v;
     }
+    for (int mo = 0; mo < 6; ++mo) {
+        double v = 0.0;
+        for (int q = 0; q < nf.m; ++q) v += nf.basis[mo][q] * coef[q];
+        motion[mo] = v;
+    }
+}
+
+// u -= t + w x d on the non-Dirichlet rows (the rigid part of u).
+__global__ void k_remove_null(Lv<double> L, NullInfo nf, const double* __restrict__ motion, double* __restrict__ u) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
     int c[3];
     coords_of(p, L.n, c);
     const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    const double d[3] = {nf.off[0] + nf.h[0] * c[0], nf.off[1] + nf.h[1] * c[1], nf.off[2] + nf.h[2] * c[2]};
+    const double w[3] = {motion[3], motion[4], motion[5]};
+    const double r[3] = {motion[0] + (w[1] * d[2] - w[2] * d[1]), motion[1] + (w[2] * d[0] - w[0] * d[2]),
+                         motion[2] + (w[0] * d[1] - w[1] * d[0])};
     for (int i = 0; i < 3; ++i)
-        if (row_type(L, ni, i) != ROW_DIRICHLET) u[i * L.N + p] -= null_combo(nf, coef, i, c);
+        if (row_type(L, ni, i) != ROW_DIRICHLET) u[i * L.N + p] -= r[i];
 }
 #endif
 
