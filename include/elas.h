@@ -247,7 +247,8 @@ unsigned long long elas_launch_count(void);
  * The interior smoother has several launch shapes: 0-4 are one thread per x-pair
  * of interior nodes with (threads per block, minimum resident blocks per SM) =
  * (256,1) (256,2) (256,3) (256,4) (128,8), the second number bounding registers per
- * thread; 5 and 6 stage moduli and displacement planes of a 32 x 16 (resp. 32 x 8)
+ * thread (levels with FP16 moduli use shapes 1 and 2 only); 5 and 6 stage moduli and
+ * displacement planes of a 32 x 16 (resp. 32 x 8)
  * tile in shared memory and march through z (FP32 levels with FP32 moduli only;
  * identical arithmetic, so every shape gives bitwise-equal results).  elas_autotune
  * times each shape on every level of the grid, in FP32 (mixed grids) and FP64,

@@ -45,8 +45,9 @@ struct Lv {
     const int* __restrict__ active;
     // optional FP16 copy of the moduli read by FP32 kernels instead of `mod`
     const __half* __restrict__ modh;
-    // optional coefficients of the edge and corner rows: for bnodes[w], kEdgeCoef entries
-    // [row i][slot][component k] (see edge_slot_node), so a row is a 27-slot dot product
+    // coefficients of the edge and corner rows: for bnodes[w], kEdgeCoef entries
+    // [row i][slot][component k] (see edge_slot_node), so a row is a 27-slot dot product;
+    // set up with the moduli, required by the smoother and the residual
     const T* __restrict__ bcoef;
 };
 

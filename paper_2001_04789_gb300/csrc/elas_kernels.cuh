@@ -296,7 +296,7 @@ __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restri
 
 // Residual bodies: one interior node per thread, one edge/corner node per warp, one
 // face node per thread; each adds its node's contributions to the thread's sums.
-template <typename T, typename TR, int KIND, bool NORM, bool HM>
+template <typename T, typename TR, int KIND, bool NORM, bool HM, bool MH>
 __device__ __forceinline__ void residual_int_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
                                                   const NullInfo& nf, const double* __restrict__ lam,
                                                   TR* __restrict__ r, int t, double acc[7]) {
@@ -305,7 +305,9 @@ __device__ __forceinline__ void residual_int_body(const Lv<T>& L, const T* __res
     if (t >= cnt[0] * cnt[1] * cnt[2]) return;
     const int c[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
     T v[3];
-    interior_rows<T, KIND, HM>(L, u, c[0], c[1], c[2], v);
+    with_interior<T, KIND, MH>(L, u, c[0], c[1], c[2], [&](const auto& ua, const auto& ca, int p) {
+        interior_rows_core<T, KIND, HM>(L, ua, ca, p, v);
+    });
     const int types[3] = {ROW_INTERIOR, ROW_INTERIOR, ROW_INTERIOR};
     residual_store<T, TR, NORM>(L, f, nf, lam, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
 }
@@ -350,23 +352,14 @@ __device__ __forceinline__ void residual_bnd_body(const Lv<T>& L, const T* __res
     int types[3];
     for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
     T v[3];
-    if (L.bcoef) {
-        edge_rows_coef<T>(L, u, ni, L.bcoef + (size_t)w * kEdgeCoef, lane, v);
-    } else {
-        T val = T(0);
-        if (lane < 3) {
-            UField<T> uf{u, L.N, L.n[0], L.n[1]};
-            val = boundary_row<T, KIND>(L, uf, ni, lane, types[lane]);
-        }
-        for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, i);
-    }
+    edge_rows_coef<T>(L, u, ni, L.bcoef + (size_t)w * kEdgeCoef, lane, v);
     if (lane == 0) residual_store<T, TR, NORM>(L, f, nf, lam, c, p, types, v, r, acc);
 }
 
 // Red-black smoother, interior nodes: each thread owns the x-pair (x0, x0+1) of the
 // interior box, updates the one of the active colour and copies the other; every
 // row uses the values from before the half-sweep (Jacobi within the colour).
-template <typename T, int KIND, bool HM>
+template <typename T, int KIND, bool HM, bool MH>
 __device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restrict__ u, T* __restrict__ uo,
                                                 const T* __restrict__ f, int colour, const NullInfo& nf,
                                                 const double* __restrict__ lam, int t) {
@@ -402,12 +395,7 @@ __device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restr
         solve3(B, r, d);
         for (int i = 0; i < 3; ++i) uo[i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
     };
-    if constexpr (sizeof(T) == 4) {
-        if (L.modh) with_interior<T, KIND, true>(L, u, xa, y, z, body);
-        else with_interior<T, KIND, false>(L, u, xa, y, z, body);
-    } else {
-        with_interior<T, KIND, false>(L, u, xa, y, z, body);
-    }
+    with_interior<T, KIND, MH>(L, u, xa, y, z, body);
 }
 
 // ---- shared-memory tiled FP32 interior smoother --------------------------------------
@@ -446,7 +434,7 @@ __global__ void __launch_bounds__(16 * TY, (TY <= 8) ? 2 : 1)
                        const float* __restrict__ f, int colour, NullInfo nf, const double* __restrict__ lam,
                        int zlen) {
     using S = TiledShape<KIND, TY>;
-    constexpr int KP = S::KP, R = S::R, PLANE = S::PLANE, CPL = S::CPL, UPL = S::UPL, NPOS = S::NPOS;
+    constexpr int KP = S::KP, PLANE = S::PLANE, CPL = S::CPL, UPL = S::UPL, NPOS = S::NPOS;
     constexpr int NT = 16 * TY;
     extern __shared__ __align__(16) float sm[];
     float* const Cs = sm;                  // [3][KP][R][kTileS]
@@ -587,27 +575,14 @@ __device__ __forceinline__ void sweep_bnd_body(const Lv<T>& L, const T* __restri
     const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
     int types[3];
     for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
+    // stored rows (L.bcoef, set up with the moduli); the diagonal block is the node's own slot
     T B[3][3], v[3];
-    if (L.bcoef) {
-        // stored rows; the diagonal block is the node's own slot
-        const T* cf = L.bcoef + (size_t)w * kEdgeCoef;
-        edge_rows_coef<T>(L, u, ni, cf, lane, v);
-        if (lane != 0) return;
-        const int cs = edge_center_slot(ni);
-        for (int i = 0; i < 3; ++i)
-            for (int k = 0; k < 3; ++k) B[i][k] = cf[81 * i + 3 * cs + k];
-    } else {
-        T val = T(0);
-        if (lane < 9) {
-            val = boundary_block_entry<T, KIND>(L, ni, types, lane / 3, lane % 3);
-        } else if (lane < 12) {
-            UField<T> uf{u, N, L.n[0], L.n[1]};
-            val = boundary_row<T, KIND>(L, uf, ni, lane - 9, types[lane - 9]);
-        }
-        for (int q = 0; q < 9; ++q) B[q / 3][q % 3] = __shfl_sync(0xffffffffu, val, q);
-        for (int i = 0; i < 3; ++i) v[i] = __shfl_sync(0xffffffffu, val, 9 + i);
-        if (lane != 0) return;
-    }
+    const T* cf = L.bcoef + (size_t)w * kEdgeCoef;
+    edge_rows_coef<T>(L, u, ni, cf, lane, v);
+    if (lane != 0) return;
+    const int cs = edge_center_slot(ni);
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) B[i][k] = cf[81 * i + 3 * cs + k];
     T r[3], d[3];
     for (int i = 0; i < 3; ++i) {
         if (types[i] == ROW_DIRICHLET) {
@@ -782,7 +757,7 @@ inline BndSegs bnd_segs(const Lv<T>& L, int bs) {
 }
 
 // Red-black smoother, all nodes of one colour (see the bodies above for each kind).
-template <typename T, int KIND, bool HM, int BS, int MINB>
+template <typename T, int KIND, bool HM, bool MH, int BS, int MINB>
 __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
                                                           const T* __restrict__ f, int colour, NullInfo nf,
                                                           const double* __restrict__ lam, BndSegs sg) {
@@ -795,11 +770,11 @@ __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* _
         else sweep_face_body<T, KIND, 2>(L, u, uo, f, colour, nf, lam, (b - sg.f1) * BS + tid);
         return;
     }
-    sweep_pair_body<T, KIND, HM>(L, u, uo, f, colour, nf, lam, (b - sg.f2) * BS + tid);
+    sweep_pair_body<T, KIND, HM, MH>(L, u, uo, f, colour, nf, lam, (b - sg.f2) * BS + tid);
 }
 
 // r = f - load - A u on every node; block partials of sum r^2 and the rigid moments.
-template <typename T, typename TR, int KIND, bool NORM, bool HM>
+template <typename T, typename TR, int KIND, bool NORM, bool HM, bool MH>
 __global__ void __launch_bounds__(kBlock) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                                     NullInfo nf, const double* __restrict__ lam,
                                                     TR* __restrict__ r, double* __restrict__ partials, BndSegs sg) {
@@ -810,7 +785,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(Lv<T> L, const T* __restric
     else if (b < sg.f0) residual_face_body<T, TR, KIND, 0, NORM>(L, u, f, nf, lam, r, (b - sg.e) * kBlock + tid, acc);
     else if (b < sg.f1) residual_face_body<T, TR, KIND, 1, NORM>(L, u, f, nf, lam, r, (b - sg.f0) * kBlock + tid, acc);
     else if (b < sg.f2) residual_face_body<T, TR, KIND, 2, NORM>(L, u, f, nf, lam, r, (b - sg.f1) * kBlock + tid, acc);
-    else residual_int_body<T, TR, KIND, NORM, HM>(L, u, f, nf, lam, r, (b - sg.f2) * kBlock + tid, acc);
+    else residual_int_body<T, TR, KIND, NORM, HM, MH>(L, u, f, nf, lam, r, (b - sg.f2) * kBlock + tid, acc);
     if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
 }
 
@@ -1191,7 +1166,6 @@ __global__ void k_null_dots(Lv<double> L, NullInfo nf, const double* __restrict_
                             int gram) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    int width = gram ? nf.m * nf.m : nf.m;
     if (p < L.N) {
         int c[3];
         coords_of(p, L.n, c);
@@ -1211,7 +1185,6 @@ __global__ void k_null_dots(Lv<double> L, NullInfo nf, const double* __restrict_
         acc[5] = d0 * um[1] - d1 * um[0];
     }
     (void)gram;
-    (void)width;
     block_reduce_store<7>(acc, 6, partials);
 }
 #endif

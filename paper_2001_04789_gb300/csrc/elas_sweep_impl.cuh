@@ -1,5 +1,6 @@
 // Launch shapes of the red-black smoother, their autotuner and the half-sweep launcher.
-// Instantiated once per precision (elas_sweep_f32.cu, elas_sweep_f64.cu).
+// Instantiated per precision (elas_sweep_f32.cu, elas_sweep_f64.cu); the FP32 isotropic
+// instances compile in elas_sweep_f32_iso.cu.
 #pragma once
 #include <array>
 
@@ -61,7 +62,7 @@ static int tiled_zlen(int columns, int nzi, int per_sm) {
 }
 
 template <int KIND, int TY>
-static void launch_tiled(const Lv<float>& L, const float* u_in, float* u_out, const float* f, int colour,
+void launch_tiled(const Lv<float>& L, const float* u_in, float* u_out, const float* f, int colour,
                          const NullInfo& nfv, const double* lam, cudaStream_t s) {
     using S = TiledShape<KIND, TY>;
     static const bool attr = [] {
@@ -82,6 +83,7 @@ static void launch_tiled(const Lv<float>& L, const float* u_in, float* u_out, co
 // FP16 moduli.
 template <typename T>
 static bool variant_ok(const Lv<T>& L, int v) {
+    if (sizeof(T) == 4 && L.modh) return v == 1 || v == 2;   // FP16 records: two shapes
     if (v < kFirstTiledVariant) return true;
     return sizeof(T) == 4 && L.mlay == kModBlocked && !L.divc;
 }
@@ -103,10 +105,10 @@ static void launch_boundary_sweep(const Lv<T>& L, const T* u_in, T* u_out, const
 
 // One half-sweep with interior shape v: the untiled shapes take every node in one
 // launch; the tiled ones launch the boundary nodes separately.
-template <typename T, int KIND, bool HM>
+template <typename T, int KIND, bool HM, bool MH>
 void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
                        const NullInfo& nfv, const double* lam, cudaStream_t s) {
-    if constexpr (sizeof(T) == 4 && !HM) {
+    if constexpr (sizeof(T) == 4 && !HM && !MH) {
         if (v >= kFirstTiledVariant && variant_ok(L, v)) {
             if (np) {
                 count_launch();
@@ -117,18 +119,46 @@ void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out
             return;
         }
     }
-    if (v >= kFirstTiledVariant) v = kDefaultSweepVariant;
-    const int bs = kSweepVariants[v][0];
-    const BndSegs sg = bnd_segs(L, bs);
-    const int nb = sg.f2 + (int)((np + bs - 1) / bs);
-    if (!nb) return;
-    count_launch();
-    switch (v) {
-        case 0: k_half_sweep_int<T, KIND, HM, 256, 1><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-        case 1: k_half_sweep_int<T, KIND, HM, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-        case 2: k_half_sweep_int<T, KIND, HM, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-        case 3: k_half_sweep_int<T, KIND, HM, 256, 4><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-        default: k_half_sweep_int<T, KIND, HM, 128, 8><<<nb, 128, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+    if (v >= kFirstTiledVariant || !variant_ok(L, v)) v = kDefaultSweepVariant;
+    if constexpr (MH) {
+        // FP16 records: shapes (256,2) and (256,3) only
+        const int bs = 256;
+        const BndSegs sg = bnd_segs(L, bs);
+        const int nb = sg.f2 + (int)((np + bs - 1) / bs);
+        if (!nb) return;
+        count_launch();
+        if (v == 1) k_half_sweep_int<T, KIND, HM, true, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg);
+        else k_half_sweep_int<T, KIND, HM, true, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg);
+    } else {
+        const int bs = kSweepVariants[v][0];
+        const BndSegs sg = bnd_segs(L, bs);
+        const int nb = sg.f2 + (int)((np + bs - 1) / bs);
+        if (!nb) return;
+        count_launch();
+        switch (v) {
+            case 0: k_half_sweep_int<T, KIND, HM, false, 256, 1><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+            case 1: k_half_sweep_int<T, KIND, HM, false, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+            case 2: k_half_sweep_int<T, KIND, HM, false, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+            case 3: k_half_sweep_int<T, KIND, HM, false, 256, 4><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+            default: k_half_sweep_int<T, KIND, HM, false, 128, 8><<<nb, 128, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+        }
+    }
+}
+
+// Moduli kind -> kernel instance.
+template <typename T>
+static void dispatch_sweep(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
+                           const NullInfo& nfv, const double* lam, cudaStream_t s) {
+    if constexpr (sizeof(T) == 8) {
+        // FP64 levels of general moduli always carry the divergence
+        if (L.K == 2) sweep_int_variant<T, 2, false, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        else sweep_int_variant<T, 21, true, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+    } else if (L.modh) {
+        if (L.K == 2) sweep_int_variant<T, 2, false, true>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        else sweep_int_variant<T, 21, false, true>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+    } else {
+        if (L.K == 2) sweep_int_variant<T, 2, false, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        else sweep_int_variant<T, 21, false, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
     }
 }
 
@@ -150,9 +180,7 @@ int tune_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, cudaStream_t
             continue;
         }
         auto run = [&]() {
-            if (L.K == 2) sweep_int_variant<T, 2, false>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
-            else if (L.divc) sweep_int_variant<T, 21, true>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
-            else sweep_int_variant<T, 21, false>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
+            dispatch_sweep<T>(v, np, L, u_in, u_out, f, 0, nfv, nullptr, s);
         };
         run();
         cudaEventRecord(a, s);
@@ -183,9 +211,7 @@ void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int 
     if (nf) nfv = *nf;
     const size_t np = interior_pairs(L);
     const int v = sweep_variant_for(L);
-    if (L.K == 2) sweep_int_variant<T, 2, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-    else if (L.divc) sweep_int_variant<T, 21, true>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-    else sweep_int_variant<T, 21, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+    dispatch_sweep<T>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
 }
 
 }  // namespace elas

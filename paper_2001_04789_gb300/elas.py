@@ -389,8 +389,10 @@ class Grid:
 
 
 # interior smoother launch shapes: 0-4 untiled (threads, min blocks per SM) = (256,1),
-# (256,2), (256,3), (256,4), (128,8); 5-6 shared-memory tiled, 32x16 and 32x8 tiles
+# (256,2), (256,3), (256,4), (128,8); 5-6 shared-memory tiled, 32x16 and 32x8 tiles.
+# Levels with FP16 moduli use shapes 1 and 2 only (the others report -1 when tuned).
 NUM_SWEEP_VARIANTS = 7
+UNTILED_VARIANTS = tuple(range(5))
 TILED_VARIANTS = (5, 6)
 
 
