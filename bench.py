@@ -31,7 +31,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM read + write bytes per node of one finest-level FP32 half-sweep launch, per
 # smoother shape (autotuner index), from one ncu capture of that shape on the 129^3
 # polycrystal; scaled by the node count to the benchmarked grid.
-SWEEP32_TRAFFIC_B_PER_NODE = {1: 145.4, 2: 153.2}
+SWEEP32_TRAFFIC_B_PER_NODE = {1: 144.2, 2: 151.7}
 # nominal FP64 vector throughput of the part (1.25 TFLOP/s dense FP64)
 NOMINAL_FP64_TFLOPS = 1.25
 
