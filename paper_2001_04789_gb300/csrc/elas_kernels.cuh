@@ -774,11 +774,12 @@ __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* _
 }
 
 // r = f - load - A u on every node; block partials of sum r^2 and the rigid moments.
-// Two resident blocks per SM (at most 128 registers): the FP64 instance is bound by the
-// FP64 pipe and needs the warps to keep it busy (one block at 180 registers ran 15%
-// slower).
+// Resident blocks per SM: two for FP64 (at most 128 registers; the FP64 instance is bound
+// by the FP64 pipe and needs the warps to keep it busy, one block at 180 registers ran
+// 15% slower), three for FP32 (80 registers with a few spills: 0.97 -> 0.79 ms at 257^3,
+// the same latency-for-registers trade as the smoother's (256,3) shape).
 template <typename T, typename TR, int KIND, bool NORM, bool HM, bool MH>
-__global__ void __launch_bounds__(kBlock, 2) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                                     NullInfo nf, const double* __restrict__ lam,
                                                     TR* __restrict__ r, double* __restrict__ partials, BndSegs sg) {
     if (L.active && *L.active == 0) return;
