@@ -117,6 +117,7 @@ struct elas_grid_s {
     bool moduli_set = false;
     bool dirty = true;         // moduli or boundary types changed: rebuild everything
     bool rhs_dirty = true;     // only loads / boundary data changed: rebuild the right-hand side
+    bool gram_valid = false;   // W^T W of the finest level (depends on boundary types, not moduli)
     std::vector<std::pair<void*, size_t>> allocs;
 };
 
@@ -448,7 +449,7 @@ int setup(elas_grid g) {
     // equilibrating load of the finest level: G = W^T W, Ginv
     Level& L0 = g->lv[0];
     const int m = L0.nf.m;
-    if (m > 0) {
+    if (m > 0 && !g->gram_valid) {
         std::vector<double> Gh(m * m), Gi(m * m);
         for (int q = 0; q < m; ++q) {
             int nb = 0;
@@ -465,6 +466,7 @@ int setup(elas_grid g) {
         CUDA_TRY(c, cudaMemcpyAsync(g->G, Gh.data(), sizeof(double) * m * m, cudaMemcpyHostToDevice, s));
         CUDA_TRY(c, cudaMemcpyAsync(g->Ginv, Gi.data(), sizeof(double) * m * m, cudaMemcpyHostToDevice, s));
         CUDA_TRY(c, cudaStreamSynchronize(s));
+        g->gram_valid = true;
     }
     // bottom: dense inverse of the coarsest operator (bordered when singular)
     if (g->ntot > 0) {
@@ -901,6 +903,7 @@ int elas_set_bc(elas_grid g, int face, int comp, int type, double value) {
     if (changed) g->dirty = true;
     else g->rhs_dirty = true;
     if (changed) {
+        g->gram_valid = false;
         refresh_lv(g);
         return rebuild_bottom_dofs(g);
     }

@@ -114,12 +114,15 @@ __global__ void k_rhs(Lv<double> L, RhsInputs in, BoundaryData bd, double* __res
     auto eps = [&](int k, int l, int q) -> double {
         return in.eps0 ? in.eps0[voigt(k, l) * N + q] : 0.0;
     };
+    // with no eigenstrain and no mean strain the source terms vanish: only body force and
+    // boundary data remain
+    const bool source = in.eps0 || in.has_mean_strain;
     for (int i = 0; i < 3; ++i) {
         const int t = row_type(L, ni, i);
         double v = 0.0;
         if (t == ROW_INTERIOR || t == ROW_TRACTION) {
             if (in.body) v -= in.body[i * N + p];
-            for (int j = 0; j < 3; ++j) {
+            for (int j = 0; j < 3 && source; ++j) {
                 if (ni.side[j] != 0) continue;
                 int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
                 cp[j] = wrapc(L, j, c[j] + 1);
@@ -144,7 +147,7 @@ __global__ void k_rhs(Lv<double> L, RhsInputs in, BoundaryData bd, double* __res
                     cn[a] -= ni.side[a];
                     const int qn = lin(L, cn[0], cn[1], cn[2]);
                     double acc = 0.0;
-                    for (int k = 0; k < 3; ++k)
+                    for (int k = 0; k < 3 && in.eps0; ++k)
                         for (int l = 0; l < 3; ++l) {
                             const double Ca = (KIND == 2) ? Cm<double, 2>(L, p, i, a, k, l) : Cm<double, 21>(L, p, i, a, k, l);
                             const double Cb = (KIND == 2) ? Cm<double, 2>(L, qn, i, a, k, l) : Cm<double, 21>(L, qn, i, a, k, l);
@@ -1019,16 +1022,40 @@ __global__ void k_invert(double* __restrict__ A, double* __restrict__ X, int n, 
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) X[i] = ((i / n) == (i % n)) ? 1.0 : 0.0;
     __syncthreads();
     for (int col = 0; col < n; ++col) {
-        if (threadIdx.x == 0) {
-            int best = col;
-            double bv = fabs(A[col * n + col]);
-            for (int r = col + 1; r < n; ++r) {
+        // pivot: the first row of largest |A[r][col]|, r >= col (block-wide argmax; ties
+        // go to the lower row, as in a sequential scan)
+        {
+            __shared__ double wv[32];
+            __shared__ int wr[32];
+            double bv = -1.0;
+            int br = n;
+            for (int r = col + threadIdx.x; r < n; r += blockDim.x) {
                 const double v = fabs(A[r * n + col]);
-                if (v > bv) { bv = v; best = r; }
+                if (v > bv) { bv = v; br = r; }
             }
-            piv = best;
-            pval = A[best * n + col];
-            if (bv == 0.0) *singular = 1;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+                const int orr = __shfl_down_sync(0xffffffffu, br, o);
+                if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+            }
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (lane == 0) { wv[warp] = bv; wr[warp] = br; }
+            __syncthreads();
+            if (warp == 0) {
+                const int nw = (blockDim.x + 31) >> 5;
+                bv = lane < nw ? wv[lane] : -1.0;
+                br = lane < nw ? wr[lane] : n;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+                    const int orr = __shfl_down_sync(0xffffffffu, br, o);
+                    if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+                }
+                if (lane == 0) {
+                    piv = br;
+                    pval = A[br * n + col];
+                    if (bv == 0.0) *singular = 1;
+                }
+            }
         }
         __syncthreads();
         if (pval == 0.0) return;
