@@ -474,7 +474,7 @@ int setup(elas_grid g) {
         launch_bottom_assemble(B.L64, g->dofs, g->nfree, B.nf, g->Awork, s);
         CHECK_LAUNCH(c);
         CUDA_TRY(c, cudaMemsetAsync(g->flag, 0, sizeof(int), s));
-        launch_invert(g->Awork, g->Ainv, g->ntot, g->flag, s);
+        launch_invert(g->Awork, g->Ainv, g->ntot, g->bwork, g->flag, s);
         CHECK_LAUNCH(c);
         int flag = 0;
         CUDA_TRY(c, cudaMemcpyAsync(&flag, g->flag, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -89,7 +89,7 @@ void launch_add_correction64(const Lv<double>& L, double* u, const double* e, cu
 // columns of the free rigid modes), its inverse, and the solve.
 void launch_bottom_assemble(const Lv<double>& L, const int* dofs, int nfree, const NullInfo& nf,
                             double* A, cudaStream_t s);
-void launch_invert(double* A, double* Ainv, int n, int* singular_flag, cudaStream_t s);
+void launch_invert(double* A, double* Ainv, int n, double* fcol, int* singular_flag, cudaStream_t s);  // fcol: n doubles of scratch
 template <typename T>
 void launch_bottom_solve(const Lv<T>& L, const int* dofs, int nfree, int ntot, const double* Ainv,
                          const T* f, T* u, double* work, cudaStream_t s);

@@ -169,10 +169,15 @@ void launch_bottom_assemble(const Lv<double>& L, const int* dofs, int nfree, con
     else { count_launch(); k_bottom_assemble<21><<<nb, kBlock, 0, s>>>(L, dofs, nfree, nf, A); }
 }
 
-void launch_invert(double* A, double* Ainv, int n, int* singular_flag, cudaStream_t s) {
+void launch_invert(double* A, double* Ainv, int n, double* fcol, int* singular_flag, cudaStream_t s) {
     if (n == 0) return;
-    count_launch();
-    k_invert<<<1, 1024, 0, s>>>(A, Ainv, n, singular_flag);
+    const int nb = blocks_for((size_t)n * n);
+    count_launch(1 + 2 * n);
+    k_gj_init<<<nb, kBlock, 0, s>>>(Ainv, n);
+    for (int col = 0; col < n; ++col) {
+        k_gj_pivot<<<1, 1024, 0, s>>>(A, Ainv, n, col, fcol, singular_flag);
+        k_gj_eliminate<<<nb, kBlock, 0, s>>>(A, Ainv, n, col, fcol, singular_flag);
+    }
 }
 
 template <typename T>

@@ -1014,80 +1014,84 @@ __global__ void k_bottom_assemble(Lv<double> L, const int* __restrict__ dofs, in
     A[t] = v;
 }
 
-// Gauss-Jordan inversion with partial pivoting, one block.
 #ifdef ELAS_KERNELS_TU
-__global__ void k_invert(double* __restrict__ A, double* __restrict__ X, int n, int* singular) {
+// Gauss-Jordan inverse with partial pivoting, X = A^-1 (A is destroyed), one pivot column
+// per pair of launches so that the O(n^3) elimination spreads over every SM: the pivot
+// launch (one block) picks the first row of largest |A[r][col]|, swaps it up, scales the
+// pivot row and saves column col in fcol; the elimination launch updates all other rows.
+// A zero pivot sets *singular and every later launch returns at once.
+__global__ void k_gj_init(double* __restrict__ X, int n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (size_t)n * n) X[i] = ((int)(i / n) == (int)(i % n)) ? 1.0 : 0.0;
+}
+
+__global__ void k_gj_pivot(double* __restrict__ A, double* __restrict__ X, int n, int col,
+                           double* __restrict__ fcol, int* __restrict__ singular) {
     __shared__ int piv;
     __shared__ double pval;
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) X[i] = ((i / n) == (i % n)) ? 1.0 : 0.0;
+    __shared__ double wv[32];
+    __shared__ int wr[32];
+    if (*singular) return;
+    double bv = -1.0;
+    int br = n;
+    for (int r = col + threadIdx.x; r < n; r += blockDim.x) {
+        const double v = fabs(A[(size_t)r * n + col]);
+        if (v > bv) { bv = v; br = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_down_sync(0xffffffffu, br, o);
+        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { wv[warp] = bv; wr[warp] = br; }
     __syncthreads();
-    for (int col = 0; col < n; ++col) {
-        // pivot: the first row of largest |A[r][col]|, r >= col (block-wide argmax; ties
-        // go to the lower row, as in a sequential scan)
-        {
-            __shared__ double wv[32];
-            __shared__ int wr[32];
-            double bv = -1.0;
-            int br = n;
-            for (int r = col + threadIdx.x; r < n; r += blockDim.x) {
-                const double v = fabs(A[r * n + col]);
-                if (v > bv) { bv = v; br = r; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-                const int orr = __shfl_down_sync(0xffffffffu, br, o);
-                if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-            }
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) { wv[warp] = bv; wr[warp] = br; }
-            __syncthreads();
-            if (warp == 0) {
-                const int nw = (blockDim.x + 31) >> 5;
-                bv = lane < nw ? wv[lane] : -1.0;
-                br = lane < nw ? wr[lane] : n;
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double ov = __shfl_down_sync(0xffffffffu, bv, o);
-                    const int orr = __shfl_down_sync(0xffffffffu, br, o);
-                    if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-                }
-                if (lane == 0) {
-                    piv = br;
-                    pval = A[br * n + col];
-                    if (bv == 0.0) *singular = 1;
-                }
-            }
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        bv = lane < nw ? wv[lane] : -1.0;
+        br = lane < nw ? wr[lane] : n;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const int orr = __shfl_down_sync(0xffffffffu, br, o);
+            if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
         }
-        __syncthreads();
-        if (pval == 0.0) return;
-        if (piv != col) {
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
-                double a = A[col * n + k]; A[col * n + k] = A[piv * n + k]; A[piv * n + k] = a;
-                double x = X[col * n + k]; X[col * n + k] = X[piv * n + k]; X[piv * n + k] = x;
-            }
+        if (lane == 0) {
+            piv = br;
+            pval = A[(size_t)br * n + col];
+            if (bv == 0.0) *singular = 1;
         }
-        __syncthreads();
-        const double inv = 1.0 / pval;
+    }
+    __syncthreads();
+    if (pval == 0.0) return;
+    if (piv != col) {
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            A[col * n + k] *= inv;
-            X[col * n + k] *= inv;
+            double a = A[(size_t)col * n + k]; A[(size_t)col * n + k] = A[(size_t)piv * n + k]; A[(size_t)piv * n + k] = a;
+            double x = X[(size_t)col * n + k]; X[(size_t)col * n + k] = X[(size_t)piv * n + k]; X[(size_t)piv * n + k] = x;
         }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-            const int r = idx / n, k = idx % n;
-            if (r == col) continue;
-            const double fct = A[r * n + col];
-            if (k == col) continue;
-            A[r * n + k] -= fct * A[col * n + k];
-            X[r * n + k] -= fct * X[col * n + k];
-        }
-        __syncthreads();
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            if (r == col) continue;
-            const double fct = A[r * n + col];
-            X[r * n + col] -= fct * X[col * n + col];
-            A[r * n + col] = 0.0;
-        }
-        __syncthreads();
+    }
+    __syncthreads();
+    const double inv = 1.0 / pval;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        A[(size_t)col * n + k] *= inv;
+        X[(size_t)col * n + k] *= inv;
+    }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) fcol[r] = A[(size_t)r * n + col];
+}
+
+__global__ void k_gj_eliminate(double* __restrict__ A, double* __restrict__ X, int n, int col,
+                               const double* __restrict__ fcol, const int* __restrict__ singular) {
+    if (*singular) return;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n * n) return;
+    const int r = (int)(idx / n), k = (int)(idx % n);
+    if (r == col) return;
+    const double fct = fcol[r];
+    if (k != col) {
+        A[idx] -= fct * A[(size_t)col * n + k];
+        X[idx] -= fct * X[(size_t)col * n + k];
+    } else {
+        X[idx] -= fct * X[(size_t)col * n + col];
+        A[idx] = 0.0;
     }
 }
 #endif
