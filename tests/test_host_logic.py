@@ -1,0 +1,49 @@
+"""Host-side logic of the C library that needs no GPU: the smoother's tuning table
+(text round trip, rejection of unknown launch shapes) and the HBM estimate used for
+admission by the serving loop."""
+import pytest
+
+from paper_2001_04789_gb300 import microstructure as M
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def E():
+    from paper_2001_04789_gb300 import build as B
+    try:
+        B.build()
+    except RuntimeError as e:       # no nvcc on this machine
+        pytest.skip(str(e))
+    from paper_2001_04789_gb300 import elas
+    return elas
+
+
+def test_tuning_table_round_trip_and_unknown_shapes(E):
+    bad = E.NUM_SWEEP_VARIANTS          # one past the last launch shape
+    text = f"41 43 47 21 4 0 2\n23 29 31 2 8 1 1\n19 19 19 21 4 0 {bad}\n"
+    assert E.autotune_load(text) == 2   # the unknown shape is refused
+    dump = E.autotune_dump()
+    lines = set(dump.strip().splitlines())
+    assert "41 43 47 21 4 0 2" in lines and "23 29 31 2 8 1 1" in lines
+    assert not any(l.startswith("19 19 19 21 4 0") for l in lines)
+    # the dump reads back entry for entry
+    assert E.autotune_load(dump) == len(lines)
+    assert set(E.autotune_dump().strip().splitlines()) == lines
+
+
+def test_hbm_estimate_orders_precisions_and_sizes(E):
+    est = lambda p, **kw: E.lib().elas_grid_bytes_estimate(E.desc_for(p, **kw))
+    small = M.polycrystal(33, grains=3, seed=0)
+    fp64 = est(small)
+    mixed = est(small, mixed=True)
+    half = est(small, mixed=True, half_moduli=True)
+    assert fp64 < half < mixed
+    # FP64 general moduli: 21 planes + 18 divergence planes + 12 field planes per node,
+    # summed over a hierarchy of about 8/7 of the finest level, plus 9 input planes
+    # (eigenstrain, body force) and the edge-row coefficients
+    n0 = 33 ** 3
+    assert 8 * 51 * n0 <= fp64 <= 8 * 51 * n0 * 1.5
+    big = M.polycrystal(65, grains=3, seed=0)
+    ratio = est(big, mixed=True) / mixed
+    assert 7.0 < ratio < 9.0            # node count grows 7.6x from 33^3 to 65^3
