@@ -508,22 +508,8 @@ __device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restric
     }
 }
 
-// Diagonal 3x3 block of an interior node: B_ik = -2 sum_j C_ijkj / h_j^2.
-template <typename T, int KIND>
-__device__ __forceinline__ void interior_block(const Lv<T>& L, int p, T B[3][3]) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            T acc = T(0);
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                if (Cnz<T, KIND>(i, j, k, j)) acc = xfma(Cm<T, KIND>(L, p, i, j, k, j), T(-2) * L.invh2[j], acc);
-            B[i][k] = acc;
-        }
-}
-
-// The same block through a centre-moduli accessor ca(c, 0, 0, 0).
+// Diagonal 3x3 block of an interior node, B_ik = -2 sum_j C_ijkj / h_j^2, from the
+// centre-moduli accessor ca(c, 0, 0, 0).
 template <typename T, int KIND, class CA>
 __device__ __forceinline__ void interior_block_acc(const Lv<T>& L, const CA& ca, T B[3][3]) {
 #pragma unroll
@@ -547,67 +533,6 @@ __device__ __forceinline__ void interior_block_acc(const Lv<T>& L, const CA& ca,
             }
             B[i][k] = acc;
         }
-}
-
-// Diagonal 3x3 block of a boundary node, B_ik = d(A u)_i / d u_k at the node itself:
-// the product-rule terms contribute C_ijkj (-2/h_j^2) and (d_j C_ijkl) c_l, the
-// half-cell terms -(2/h_a) s_a Cbar_iakl (s_a/h_a for l = a, c_l/2 otherwise), with
-// c_l = -+3/(2 h_l) the node's weight in its one-sided derivative of direction l.
-template <typename T, int KIND>
-__device__ __noinline__ T boundary_block_entry(const Lv<T>& L, const NodeInfo& ni, const int types[3], int i, int k) {
-    const int* c = ni.c;
-    const int p = lin(L, c[0], c[1], c[2]);
-    T cl[3];
-    for (int l = 0; l < 3; ++l)
-        cl[l] = ni.side[l] < 0 ? T(-1.5) * L.invh[l] : (ni.side[l] > 0 ? T(1.5) * L.invh[l] : T(0));
-    if (types[i] == ROW_DIRICHLET) return (i == k) ? T(1) : T(0);
-    if (types[i] == ROW_NEUMANN) {
-        if (i != k) return T(0);
-        T acc = T(0);
-        for (int a = 0; a < 3; ++a) {
-            if (ni.side[a] == 0) continue;
-            const int f = 2 * a + (ni.side[a] > 0 ? 1 : 0);
-            if (L.bc[f][i] != ROW_NEUMANN) continue;
-            acc += -(T(2) * L.invh[a]) * Cm<T, KIND>(L, p, i, a, i, a) * T(ni.side[a]) * cl[a];
-        }
-        return acc;
-    }
-    T acc = T(0);
-    for (int j = 0; j < 3; ++j) {
-        if (ni.side[j] != 0) continue;
-        int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
-        cp[j] = wrapc(L, j, c[j] + 1);
-        cm[j] = wrapc(L, j, c[j] - 1);
-        const int qp = lin(L, cp[0], cp[1], cp[2]), qm = lin(L, cm[0], cm[1], cm[2]);
-        for (int l = 0; l < 3; ++l) {
-            if (!Cnz<T, KIND>(i, j, k, l)) continue;
-            if (cl[l] != T(0))
-                acc += (Cm<T, KIND>(L, qp, i, j, k, l) - Cm<T, KIND>(L, qm, i, j, k, l)) * L.inv2h[j] * cl[l];
-            if (l == j) acc += Cm<T, KIND>(L, p, i, j, k, j) * (T(-2) * L.invh2[j]);
-        }
-    }
-    for (int a = 0; a < 3; ++a) {
-        if (ni.side[a] == 0) continue;
-        const T s = T(ni.side[a]);
-        int cn[3] = {c[0], c[1], c[2]};
-        cn[a] = c[a] - ni.side[a];
-        const int qn = lin(L, cn[0], cn[1], cn[2]);
-        for (int l = 0; l < 3; ++l) {
-            if (!Cnz<T, KIND>(i, a, k, l)) continue;
-            const T coef = (l == a) ? s * L.invh[a] : T(0.5) * cl[l];
-            if (coef == T(0)) continue;
-            const T Cbar = T(0.5) * (Cm<T, KIND>(L, p, i, a, k, l) + Cm<T, KIND>(L, qn, i, a, k, l));
-            acc += -(T(2) * L.invh[a]) * s * Cbar * coef;
-        }
-    }
-    return acc;
-}
-
-// Diagonal 3x3 block of a boundary node (entries as above).
-template <typename T, int KIND>
-__device__ __noinline__ void boundary_block(const Lv<T>& L, const NodeInfo& ni, const int types[3], T B[3][3]) {
-    for (int i = 0; i < 3; ++i)
-        for (int k = 0; k < 3; ++k) B[i][k] = boundary_block_entry<T, KIND>(L, ni, types, i, k);
 }
 
 // ---- face-node fast path ------------------------------------------------------------

@@ -223,16 +223,6 @@ __host__ __device__ inline size_t interior_pairs(const Lv<T>& L) {
     return (size_t)((cx + 1) / 2) * cy * cz;
 }
 
-template <typename T, int KIND>
-__device__ __forceinline__ void boundary_rows_all(const Lv<T>& L, const T* __restrict__ u, const NodeInfo& ni,
-                                                  int types[3], T out[3]) {
-    UField<T> uf{u, L.N, L.n[0], L.n[1]};
-    for (int i = 0; i < 3; ++i) {
-        types[i] = row_type(L, ni, i);
-        out[i] = boundary_row<T, KIND>(L, uf, ni, i, types[i]);
-    }
-}
-
 template <typename T, int KIND, bool HM>
 __global__ void __launch_bounds__(kBlock) k_apply_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ out) {
     int lo[3], cnt[3];
