@@ -155,3 +155,51 @@ def test_composite_solution_approaches_uniform_fine_solution():
     err_amr = np.abs(ul - uf[(slice(None),) + sl]).max()
     err_coarse = np.abs(uc - uf[:, ::2, ::2, ::2]).max()
     assert err_amr < 0.5 * err_coarse, (err_amr, err_coarse)
+
+
+# --------------------------------------------------------------------------
+# restriction to covered coarse nodes: truncated, renormalised weights
+# --------------------------------------------------------------------------
+
+def _box(grid_lo, n, valid_lo=None, valid_hi=None):
+    from types import SimpleNamespace
+    return SimpleNamespace(grid_lo=grid_lo, valid_lo=valid_lo, valid_hi=valid_hi,
+                           problem=SimpleNamespace(n=n))
+
+
+def test_restriction_weights_truncated_and_renormalised_by_hand():
+    """Section 3.2's R_mn at covered coarse nodes, weights worked out by hand: the
+    single-grid (1/4, 1/2, 1/4) (interior) and (1/2, 1/2) (domain boundary) weights,
+    cut to the valid fine nodes and scaled to sum to one."""
+    fine = _box((3, 3, 3), (11, 11, 11), (4, 4, 4), (12, 12, 12))   # 17 fine nodes per direction
+    w = lambda gc: A._restrict_weights_1d(gc, fine, 0, 17)
+    assert w(2) == pytest.approx({0: 2 / 3, 1: 1 / 3})          # footprint 3, 4, 5; 3 is a ghost
+    assert w(4) == pytest.approx({-1: 0.25, 0: 0.5, 1: 0.25})
+    assert w(6) == pytest.approx({-1: 1 / 3, 0: 2 / 3})
+    edge = _box((0, 0, 0), (10, 10, 10), (0, 0, 0), (8, 8, 8))     # valid box on the low domain face
+    we = lambda gc: A._restrict_weights_1d(gc, edge, 1, 17)
+    assert we(0) == pytest.approx({0: 0.5, 1: 0.5})                 # domain boundary node, untouched
+    assert we(4) == pytest.approx({-1: 1 / 3, 0: 2 / 3})            # fine node 9 is outside the box
+
+
+def test_restriction_of_a_point_value_and_of_a_constant():
+    fine = _box((3, 3, 3), (11, 11, 11), (4, 4, 4), (12, 12, 12))
+    coarse = _box((0, 0, 0), (9, 9, 9))
+    # a unit value at fine global node (x, y, z) = (4, 5, 12) reaches coarse (2, 2, 6) with
+    # 2/3 * 1/3 * 2/3 and coarse (2, 3, 6) with 2/3 * 1/4 * 2/3; nothing else
+    fres = np.zeros((1, 11, 11, 11))
+    fres[0, 12 - 3, 5 - 3, 4 - 3] = 1.0
+    cres = np.full((1, 9, 9, 9), -7.0)
+    A.restrict_field(fine, fres, coarse, cres, (17, 17, 17))
+    expect = np.full((1, 9, 9, 9), -7.0)
+    expect[0, 2:7, 2:7, 2:7] = 0.0                                  # every covered node is written
+    expect[0, 6, 2, 2] = 4 / 27
+    expect[0, 6, 3, 2] = 1 / 9
+    assert np.allclose(cres, expect, rtol=0, atol=1e-15)
+    # renormalised weights conserve constants on every covered node, including the
+    # truncated ones next to the coarse/fine boundary
+    fres = np.full((2, 11, 11, 11), 5.0)
+    cres = np.zeros((2, 9, 9, 9))
+    A.restrict_field(fine, fres, coarse, cres, (17, 17, 17))
+    assert np.allclose(cres[:, 2:7, 2:7, 2:7], 5.0, rtol=0, atol=1e-14)
+    assert np.all(cres[:, :2] == 0) and np.all(cres[:, 7:] == 0)

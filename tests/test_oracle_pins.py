@@ -520,3 +520,98 @@ def test_rotation_invariance_of_moduli():
     T = M.rotate_tensor(cub, R)
     assert np.allclose(T, np.transpose(T, (2, 3, 0, 1)))
     assert np.allclose(T, np.transpose(T, (1, 0, 2, 3)))
+
+
+# --------------------------------------------------------------------------
+# mean strain of a periodic cell: laminate closed form
+# --------------------------------------------------------------------------
+
+def laminate_closed_form(C0, ebar, a, x_a, alpha, beta):
+    """Continuum fluctuation of a periodic laminate under the mean strain ebar.
+
+    Moduli C(x) = C0 / (alpha + beta cos(2 pi x_a)) vary along direction a only, so
+    the fluctuation u~ depends on x_a alone.  Equilibrium makes the traction on the
+    layer planes, sigma_ia = C_iakl (ebar_kl + u~_k,a delta_la), uniform; with
+    A_ik = C0_iaka and b_i = C0_iakl ebar_kl (tensor ebar, shears not doubled) and
+    a zero-mean u~_,a this gives u~_,a = (beta / alpha) cos(2 pi x_a) A^-1 b, hence
+    u~ = (beta / alpha) sin(2 pi x_a) / (2 pi) A^-1 b; the homogenised traction is
+    sigma_ia = b_i / alpha."""
+    E = np.array([[ebar[0], ebar[5], ebar[4]], [ebar[5], ebar[1], ebar[3]], [ebar[4], ebar[3], ebar[2]]])
+    A = C0[:, a, :, a]
+    b = np.einsum("ikl,kl->i", C0[:, a, :, :], E)
+    amp = np.linalg.solve(A, b) * beta / alpha
+    return np.einsum("k,...->k...", amp, np.sin(2 * np.pi * x_a) / (2 * np.pi)), b / alpha
+
+
+def laminate_problem(n, a, kind, C0, ebar, alpha, beta):
+    p = M.Problem(n=n, periodic=(True, True, True))
+    X, Y, Z = p.coords()
+    xa = (X, Y, Z)[a]
+    scale = 1.0 / (alpha + beta * np.cos(2 * np.pi * xa))
+    if kind == M.MODULI_ISO:
+        lam = C0[0, 0, 1, 1]
+        mu = C0[0, 1, 0, 1]
+        p.moduli_kind = M.MODULI_ISO
+        p.moduli = np.stack([lam * scale, mu * scale])
+    else:
+        p.moduli_kind = M.MODULI_GEN21
+        p.moduli = M.tensor_to_upper21(C0)[:, None, None, None] * scale[None]
+    p.mean_strain = np.asarray(ebar, dtype=float)
+    p.bc = []
+    return p, xa
+
+
+@pytest.mark.parametrize("a,kind", [(0, M.MODULI_ISO), (2, M.MODULI_GEN21), (1, M.MODULI_GEN21)])
+def test_periodic_laminate_mean_strain_matches_closed_form(a, kind):
+    """Pins the mean-strain part of the right-hand side (u = ebar x + u~, Section
+    2.1.1 product rule) against the laminate closed form: the solved fluctuation
+    converges to it at second order, with the right sign and the tensor (not
+    engineering) shear components, for normal and shear mean strains."""
+    if kind == M.MODULI_ISO:
+        lam, mu = M.lame(1.0, 0.3)
+        C0 = iso_tensor(float(lam), float(mu))
+    else:
+        rng = np.random.default_rng(11)
+        C0 = M.voigt_to_tensor(M.cubic_voigt(1.68, 1.21, 0.75))
+        C0 = M.rotate_tensor(C0, M.random_rotation(rng))
+    ebar = np.array([0.7, -0.4, 0.25, 0.5, -0.35, 0.6]) * 1e-3
+    alpha, beta = 1.0, 0.5
+    errs = []
+    for na in (16, 32, 64):
+        n = [8, 8, 8]
+        n[a] = na
+        p, xa = laminate_problem(tuple(n), a, kind, C0, ebar, alpha, beta)
+        u, info = MG.solve(p, tol=1e-12, max_cycles=200)
+        assert info.converged
+        ue, _ = laminate_closed_form(C0, ebar, a, xa, alpha, beta)
+        # the fluctuation is defined up to a translation: compare zero-mean fields
+        u = u - u.mean(axis=(1, 2, 3), keepdims=True)
+        errs.append(np.abs(u - ue).max() / np.abs(ue).max())
+    assert errs[-1] < 2e-3, errs
+    orders = [np.log2(errs[k] / errs[k + 1]) for k in range(len(errs) - 1)]
+    assert all(1.8 < o < 2.2 for o in orders), (errs, orders)
+
+
+def test_periodic_laminate_homogenised_traction():
+    """The mean traction on the layer planes of the discrete solution (central
+    differences of u = ebar x + u~) equals the closed-form homogenised traction
+    b / alpha to second order."""
+    lam, mu = M.lame(1.0, 0.3)
+    C0 = iso_tensor(float(lam), float(mu))
+    ebar = np.array([0.7, -0.4, 0.25, 0.5, -0.35, 0.6]) * 1e-3
+    alpha, beta = 1.0, 0.5
+    p, xa = laminate_problem((64, 8, 8), 0, M.MODULI_ISO, C0, ebar, alpha, beta)
+    u, info = MG.solve(p, tol=1e-12, max_cycles=200)
+    _, t_exact = laminate_closed_form(C0, ebar, 0, xa, alpha, beta)
+    h = p.h[0]
+    E = np.array([[ebar[0], ebar[5], ebar[4]], [ebar[5], ebar[1], ebar[3]], [ebar[4], ebar[3], ebar[2]]])
+    # strain = ebar + sym grad u~ (u~ varies along x only)
+    dux = (np.roll(u, -1, axis=3) - np.roll(u, 1, axis=3)) / (2 * h)
+    eps = np.broadcast_to(E[:, :, None, None, None], (3, 3) + u.shape[1:]).copy()
+    for k in range(3):
+        eps[k, 0] += 0.5 * dux[k]
+        eps[0, k] += 0.5 * dux[k]
+    scale = 1.0 / (alpha + beta * np.cos(2 * np.pi * xa))
+    sig_x = np.einsum("ikl,kl...->i...", C0[:, 0], eps) * scale[None]
+    t_num = sig_x.mean(axis=(1, 2, 3))
+    assert np.allclose(t_num, t_exact, rtol=2e-3, atol=2e-3 * np.abs(t_exact).max()), (t_num, t_exact)
