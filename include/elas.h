@@ -217,8 +217,12 @@ int  elas_op_bottom(elas_grid g, int precision, const void* f, void* u);
  * counterpart; this is an interface for such callers only.)
  *   - Same arguments and results as elas_op_residual (device pointers u, f, r of the
  *     named level; *sumsq receives sum r^2).  The grid's own buffers are not used.
+ *   - The grid must be set up: after new moduli, boundary types or loads the set-up
+ *     (which may allocate) runs in the next solve or elas_op_residual; until then this
+ *     call returns ELAS_ERR_STATE and does nothing.
  *   - A level whose reduction needs more blocks than the array holds is rejected with
- *     ELAS_ERR_INVALID_ARG (about 60 million nodes with the default size).
+ *     ELAS_ERR_INVALID_ARG (levels above about 33 million nodes with the default size:
+ *     the bound counts two blocks of 256 per 256 nodes, covering the boundary blocks).
  *   - The first call on a device looks up the array's device address with that device
  *     current; make that first call before any stream capture.
  *   - All calls share the array and it keeps the last call's contents; every slot a
@@ -239,6 +243,12 @@ int  elas_op_residual_noalloc(elas_grid g, int level, int precision, const void*
 #define ELAS_PROF_RESID64_L0 2   /* FP64 residual + norms, finest level           */
 #define ELAS_PROF_RESID32_L0 3   /* FP32 residual, finest level (mixed path)      */
 #define ELAS_PROF_CLASSES    4
+/* ALU peak of the device, measured: a launch of independent fused multiply-add chains
+ * on every SM (FP64 for precision 0, FP32 for precision 1), sized to about 20 ms, best
+ * of three timed with CUDA events; *tflops receives FLOP/s / 1e12 (an FMA counts two).
+ * The roofline of a kernel bound by arithmetic is stated against this number.  Allocates
+ * and frees a 2 KB device buffer and a stream of its own. */
+int  elas_measure_fma_peak(int device, int precision, double* tflops);
 int  elas_profile_enable(elas_ctx ctx, int enable);
 int  elas_profile_read(elas_ctx ctx, int kernel_class, double* total_ms, long long* launches);
 unsigned long long elas_launch_count(void);
@@ -299,8 +309,10 @@ int  elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts,
  * free slots (at most max_active), advances every active request by one
  * refinement step (FP64 residual, FP32 V-cycle, FP64 update; mixed precision,
  * grids created with mixed = 1), all members' kernels interleaved on parallel
- * streams, and retires the ones that reached their tolerance.  A grid must not be
- * submitted again before its request has been polled as done.  Results are the
+ * streams, and retires the ones that reached their tolerance.  elas_server_submit
+ * refuses (ELAS_ERR_STATE) a grid that already has a waiting or active request.  A
+ * request whose set-up fails at admission (e.g. no moduli set) takes no slot: it
+ * retires at once and polls as done with that error in info->status.  Results are the
  * same as a lone elas_solve with the same options (same kernels in the same
  * order per grid). */
 typedef struct elas_server_s* elas_server;
@@ -310,7 +322,8 @@ int  elas_server_submit(elas_server s, elas_grid g, const elas_solve_opts* opts,
 /* One step; *active and *waiting receive the counts after it. */
 int  elas_server_step(elas_server s, int* active, int* waiting);
 /* 1 when the request is done (info filled, latency from submit to retirement in
- * seconds), 0 while pending, negative on error. */
+ * seconds; info->status is negative if it failed), 0 while pending or unknown,
+ * negative on a bad argument. */
 int  elas_server_poll(elas_server s, long long ticket, elas_solve_info* info, double* latency_s);
 
 #ifdef __cplusplus

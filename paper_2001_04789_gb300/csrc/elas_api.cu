@@ -2,6 +2,7 @@
 // FP64 and mixed-precision solves, single-operation entry points.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -1132,9 +1133,14 @@ static double* noalloc_scratch(elas_ctx c) {
 
 int elas_op_residual_noalloc(elas_grid g, int level, int precision, const void* u, const void* f, void* r,
                              double* sumsq) {
+    if (!g) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = g->ctx;
+    // the grid's set-up (after new moduli, boundary types or loads) may allocate, so this
+    // entry point refuses to run it
+    if (g->dirty || g->rhs_dirty)
+        return set_err(c, ELAS_ERR_STATE, "grid set-up pending: call a solve or elas_op_residual first");
     int rc = check_level(g, level, precision);
     if (rc) return rc;
-    elas_ctx c = g->ctx;
     Level& v = g->lv[level];
     // blocks of one residual launch set (interior, faces, edges), as sized at grid creation
     const size_t nb_max =
@@ -1231,6 +1237,39 @@ int elas_op_bottom(elas_grid g, int precision, const void* f, void* u) {
     return ELAS_OK;
 }
 
+int elas_measure_fma_peak(int device, int precision, double* tflops) {
+    if (!tflops || (precision != 0 && precision != 1)) return ELAS_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return ELAS_ERR_DEVICE;
+    cudaStream_t s = nullptr;
+    void* out = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return ELAS_ERR_DEVICE;
+    if (cudaMalloc(&out, 256 * sizeof(double)) != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return ELAS_ERR_DEVICE;
+    }
+    // size the launch to about 20 ms from a short probe, then keep the best of three
+    float ms = 0.f;
+    int iters = precision == 0 ? 256 : 4096;
+    double flops = measure_fma_flops(precision, iters, &ms, out, s);
+    if (ms > 0.f) {
+        const double scale = 20.0 / ms;
+        const double it = scale * iters;
+        iters = it > 2e8 ? 200000000 : (it < 4 ? 4 : (int)it);
+        iters -= iters % 4;
+    }
+    double best = 0.0;
+    for (int r = 0; r < 4; ++r) {
+        flops = measure_fma_flops(precision, iters, &ms, out, s);
+        if (r > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+    }
+    const cudaError_t e = cudaGetLastError();
+    cudaFree(out);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return ELAS_ERR_DEVICE;
+    *tflops = best;
+    return ELAS_OK;
+}
+
 int elas_profile_enable(elas_ctx c, int enable) {
     if (!c) return ELAS_ERR_INVALID_ARG;
     cudaStreamSynchronize(c->stream);
@@ -1280,6 +1319,13 @@ int elas_autotune(elas_grid g, float* times_ms, int ntimes) {
 int elas_autotune_dump(char* buf, int cap) { return tune_table_dump(buf, cap); }
 int elas_autotune_load(const char* text) { return text ? tune_table_load(text) : 0; }
 
+}  // extern "C"
+namespace {
+int batch_run(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_info* info, void* mem,
+              std::chrono::steady_clock::time_point t0);
+}  // namespace
+extern "C" {
+
 int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_info* info) {
     if (!grids || n < 0 || !opts || !info) return ELAS_ERR_INVALID_ARG;
     if (n == 0) return ELAS_OK;
@@ -1306,12 +1352,30 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
         const int rc = setup(grids[i]);
         if (rc) return rc;
     }
-    cudaStream_t main = c->stream;
-    // per-member flags, counters and histories
-    const size_t hist_len = ELAS_HISTORY;
-    const size_t bytes = n * (2 * sizeof(int)) + 256 + n * hist_len * sizeof(double);
+    // per-member flags, counters and histories; every exit of the run clears the members'
+    // flag pointers and frees them
+    const size_t bytes = n * (2 * sizeof(int)) + 256 + n * (size_t)ELAS_HISTORY * sizeof(double);
     void* mem = ctx_alloc(c, bytes);
     if (!mem) return set_err(c, ELAS_ERR_ALLOC, "batch work arrays: allocation failed");
+    const int rc = batch_run(grids, n, opts, info, mem, t0);
+    for (int i = 0; i < n; ++i)
+        for (auto& v : grids[i]->lv) {
+            v.L64.active = nullptr;
+            v.L32.active = nullptr;
+        }
+    cudaStreamSynchronize(c->stream);
+    ctx_free(c, mem, bytes);
+    return rc;
+}
+
+}  // extern "C"
+
+namespace {
+int batch_run(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_info* info, void* mem,
+              std::chrono::steady_clock::time_point t0) {
+    elas_ctx c = grids[0]->ctx;
+    cudaStream_t main = c->stream;
+    const size_t hist_len = ELAS_HISTORY;
     int* flags = (int*)mem;
     int* counts = flags + n;
     double* hist = (double*)((char*)mem + (((size_t)2 * n * sizeof(int) + 255) & ~size_t(255)));
@@ -1403,15 +1467,7 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     cudaEventDestroy(fork);
-    for (int i = 0; i < n; ++i)
-        for (auto& v : grids[i]->lv) {
-            v.L64.active = nullptr;
-            v.L32.active = nullptr;
-        }
-    if (rc) {
-        ctx_free(c, mem, bytes);
-        return rc;
-    }
+    if (rc) return rc;
     std::vector<double> h_hist((size_t)n * hist_len);
     CUDA_TRY(c, cudaMemcpyAsync(h_counts.data(), counts, sizeof(int) * n, cudaMemcpyDeviceToHost, main));
     CUDA_TRY(c, cudaMemcpyAsync(h_hist.data(), hist, sizeof(double) * n * hist_len, cudaMemcpyDeviceToHost, main));
@@ -1434,12 +1490,10 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
         info[i].status = ok ? ELAS_OK : ELAS_ERR_NOT_CONVERGED;
         if (!ok && worst == ELAS_OK) worst = ELAS_ERR_NOT_CONVERGED;
     }
-    ctx_free(c, mem, bytes);
     if (worst) set_err(c, worst, "a batch member did not reach the tolerance");
     return worst;
 }
-
-}  // extern "C"
+}  // namespace
 
 // ======================================================================================
 // block-structured AMR: composite reflux-free cycle
@@ -1770,6 +1824,11 @@ int elas_server_submit(elas_server s, elas_grid g, const elas_solve_opts* opts, 
     if (!s || !g || !opts || !ticket) return ELAS_ERR_INVALID_ARG;
     if (g->ctx != s->ctx || !g->desc.mixed || g->desc.max_levels == 1)
         return set_err(s->ctx, ELAS_ERR_INVALID_ARG, "server requests need grids of its context with mixed = 1");
+    // one request per grid at a time: two would share its residual partials, levels and flags
+    for (const auto& w : s->waiting)
+        if (w.g == g) return set_err(s->ctx, ELAS_ERR_STATE, "grid already has a waiting request");
+    for (const auto& a : s->active)
+        if (a.g == g) return set_err(s->ctx, ELAS_ERR_STATE, "grid already has an active request");
     ServerReq r;
     r.ticket = s->next++;
     r.g = g;
@@ -1785,15 +1844,23 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
     elas_ctx c = s->ctx;
     cudaSetDevice(c->device);
     cudaStream_t main = c->stream;
-    // admit
+    // admit: set the grid up first; a request whose set-up fails retires at once with
+    // that error as its status and takes no slot
     while (!s->waiting.empty() && !s->free_slots.empty()) {
         ServerReq r = s->waiting.front();
         s->waiting.pop_front();
+        elas_grid g = r.g;
+        const int rc = setup(g);
+        if (rc) {
+            ServerDone d{};
+            d.info.status = rc;
+            d.latency = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_submit).count();
+            d.info.seconds = d.latency;
+            s->done[r.ticket] = d;
+            continue;
+        }
         r.slot = s->free_slots.back();
         s->free_slots.pop_back();
-        elas_grid g = r.g;
-        int rc = setup(g);
-        if (rc) return rc;
         Level& L0 = g->lv[0];
         launch_dirichlet(L0.L64, boundary_data(g), L0.u, r.opts.warm_start ? 1 : 0, main);
         cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, main);

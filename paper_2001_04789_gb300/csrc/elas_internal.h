@@ -122,6 +122,11 @@ void launch_sum_partials(const double* partials, int nblocks, int width, double*
 void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* Ginv, const double* moment,
                         double* motion, double* u, cudaStream_t s);
 
+// ALU peak microbenchmark: one launch of independent FMA chains on every SM (precision 0 =
+// FP64, 1 = FP32); returns the FLOPs of the launch and its device time in *ms.  out: a
+// device buffer of 256 elements (never written in practice).
+double measure_fma_flops(int precision, int iters, float* ms, void* out, cudaStream_t s);
+
 // ---- block-structured AMR transfers ------------------------------------------------
 // Placement of one AMR level's grid in its level's global node index space.
 struct AmrBox {

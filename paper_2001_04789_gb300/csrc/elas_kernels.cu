@@ -266,6 +266,49 @@ void launch_amr_add(const Lv<double>& L, const AmrBox& b, double* u, const doubl
     k_amr_add<<<blocks_for(L.N), kBlock, 0, s>>>(L, b, u, cor);
 }
 
+// ---- ALU peak: independent FMA chains ------------------------------------------------
+// Each thread runs kFmaChains independent chains x <- x b + a (b < 1, so the values stay
+// bounded) for iters rounds, unrolled by four; nothing else is issued in the loop but
+// its counter.  The sum is stored only under a condition the inputs never meet, so the
+// chains cannot be removed.  FLOPs per launch: 2 kFmaChains iters x threads.
+constexpr int kFmaChains = 16;
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_chain(T a, T b, int iters, T* __restrict__ out) {
+    T x[kFmaChains];
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) x[j] = a + T(j) * T(1e-3) + T(threadIdx.x) * T(1e-6);
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < kFmaChains; ++j) x[j] = fma(x[j], b, a);
+    }
+    T sum = T(0);
+#pragma unroll
+    for (int j = 0; j < kFmaChains; ++j) sum += x[j];
+    if (sum == T(-12345)) out[threadIdx.x] = sum;
+}
+
+double measure_fma_flops(int precision, int iters, float* ms, void* out, cudaStream_t s) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 8, threads = 256;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    count_launch();
+    cudaEventRecord(e0, s);
+    if (precision == 0) k_fma_chain<double><<<blocks, threads, 0, s>>>(0.5, 0.999, iters, (double*)out);
+    else k_fma_chain<float><<<blocks, threads, 0, s>>>(0.5f, 0.999f, iters, (float*)out);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    *ms = 0.f;
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return 2.0 * kFmaChains * (double)iters * blocks * threads;
+}
+
 // explicit instantiations
 template void launch_apply<double>(const Lv<double>&, const double*, double*, cudaStream_t);
 template void launch_apply<float>(const Lv<float>&, const float*, float*, cudaStream_t);

@@ -126,6 +126,7 @@ def lib():
         "elas_amr_solve": (ip, [vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "elas_profile_read": (ip, [vp, ip, dp, C.POINTER(C.c_longlong)]),
         "elas_launch_count": (C.c_ulonglong, []),
+        "elas_measure_fma_peak": (ip, [ip, ip, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -140,6 +141,15 @@ PROF_SWEEP64_L0, PROF_SWEEP32_L0, PROF_RESID64_L0, PROF_RESID32_L0 = 0, 1, 2, 3
 
 def launch_count():
     return int(lib().elas_launch_count())
+
+
+def measure_fma_peak(device=0, precision=FP64):
+    """Measured FMA throughput of the device in TFLOP/s (FP64 or FP32 chains)."""
+    t = C.c_double()
+    rc = lib().elas_measure_fma_peak(device, precision, C.byref(t))
+    if rc != OK:
+        raise ElasError(rc, "FMA peak measurement failed")
+    return t.value
 
 
 def exported_symbols():
@@ -192,6 +202,13 @@ class Context:
 
     def error(self):
         return lib().elas_last_error(self.h).decode()
+
+    def after_current(self, *tensors):
+        """Order the context's stream after torch's current stream when any argument is
+        a device tensor: inputs are usually produced by asynchronous kernels on the
+        current stream, and the library reads them on its own stream."""
+        if any(getattr(t, "is_cuda", False) for t in tensors):
+            self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
 
     def check(self, rc):
         if rc not in (OK,):
@@ -253,11 +270,13 @@ class Grid:
         self.ctx.check(lib().elas_set_moduli(self.h, _ptr(a), HOST))
 
     def set_moduli_from(self, tensor):
+        self.ctx.after_current(tensor)
         """Moduli from a torch tensor: pinned host memory or device memory."""
         space = DEVICE if tensor.is_cuda else HOST
         self.ctx.check(lib().elas_set_moduli(self.h, _ptr(tensor), space))
 
     def displacement_into(self, tensor):
+        self.ctx.after_current(tensor)
         """Copy the displacement into a torch tensor (pinned host or device)."""
         space = DEVICE if tensor.is_cuda else HOST
         self.ctx.check(lib().elas_get_displacement(self.h, _ptr(tensor), space))
@@ -334,11 +353,13 @@ class Grid:
 
     def op_apply(self, level, precision, u):
         out = self.ctx.torch.empty_like(u)
+        self.ctx.after_current(u, out)
         self.ctx.check(lib().elas_op_apply(self.h, level, precision, _ptr(u), _ptr(out)))
         return out
 
     def op_residual(self, level, precision, u, f):
         r = self.ctx.torch.empty_like(u)
+        self.ctx.after_current(u, f, r)
         ss = C.c_double()
         self.ctx.check(lib().elas_op_residual(self.h, level, precision, _ptr(u), _ptr(f), _ptr(r), C.byref(ss)))
         return r, ss.value
@@ -347,31 +368,37 @@ class Grid:
         """elas_op_residual without any allocation: the caller passes the output r;
         the reduction uses the library's static device scratch."""
         ss = C.c_double()
+        self.ctx.after_current(u, f, r)
         self.ctx.check(lib().elas_op_residual_noalloc(self.h, level, precision, _ptr(u), _ptr(f), _ptr(r),
                                                       C.byref(ss)))
         return ss.value
 
     def op_sweep(self, level, precision, u, f):
+        self.ctx.after_current(u, f)
         self.ctx.check(lib().elas_op_sweep(self.h, level, precision, _ptr(u), _ptr(f)))
         return u
 
     def op_restrict(self, level, precision, r):
         nc = self.level_dims(level + 1)
         fc = self.ctx.torch.empty((3, nc[2], nc[1], nc[0]), dtype=r.dtype, device=r.device)
+        self.ctx.after_current(r, fc)
         self.ctx.check(lib().elas_op_restrict(self.h, level, precision, _ptr(r), _ptr(fc)))
         return fc
 
     def op_prolong_add(self, level, precision, ec, u):
+        self.ctx.after_current(ec, u)
         self.ctx.check(lib().elas_op_prolong_add(self.h, level, precision, _ptr(ec), _ptr(u)))
         return u
 
     def op_rhs(self):
         f = self.ctx.torch.empty((3,) + self.shape, dtype=self.ctx.torch.float64, device=f"cuda:{self.ctx.device}")
+        self.ctx.after_current(f)
         self.ctx.check(lib().elas_op_rhs(self.h, _ptr(f)))
         return f
 
     def op_bottom(self, precision, f):
         u = self.ctx.torch.empty_like(f)
+        self.ctx.after_current(f, u)
         self.ctx.check(lib().elas_op_bottom(self.h, precision, _ptr(f), _ptr(u)))
         return u
 

@@ -352,3 +352,22 @@ def test_tiled_smoother_mixed_solve_matches(E, ctx, case):
         assert np.array_equal(hist[v][1], hist[0][1])
     force_variant(E, p, 0)
     g.close()
+
+
+def test_inputs_written_by_async_kernels_on_the_current_stream(E, ctx):
+    """Device inputs produced by kernels still queued on torch's current stream are
+    read only after those kernels: the binding orders the library's stream after it."""
+    p = mixed_bc_problem()
+    g = E.grid_from_problem(ctx, p)
+    rng = np.random.default_rng(5)
+    u_host = rng.normal(size=(3,) + g.shape)
+    u_sync = dev(u_host)
+    ref = g.op_apply(0, E.FP64, u_sync).cpu().numpy()
+    torch.cuda.synchronize()
+    x = torch.full((4096, 4096), 1.0 / 4096, device="cuda:0")
+    for _ in range(12):            # a queue of long kernels ahead of the input's producer
+        x = x @ x
+    u_async = torch.as_tensor(u_host, device="cuda:0") + x[0, 0] * 0.0
+    out = g.op_apply(0, E.FP64, u_async).cpu().numpy()
+    assert np.array_equal(out, ref)
+    g.close()
