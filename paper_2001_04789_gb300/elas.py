@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libelas_gb300.so")
 OK = 0
 ERR_NOT_CONVERGED = -3
 ERR_DIVERGED = -4
+ERR_STATE = -7
 HOST, DEVICE = 0, 1
 FP64, MIXED = 0, 1
 HISTORY = 128

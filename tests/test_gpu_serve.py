@@ -69,3 +69,34 @@ def test_request_loop_completes_short_stream(E):
     assert out["completed"] > 0
     assert out["converged"] == out["completed"]
     assert out["latency_ms"]["p99"] >= out["latency_ms"]["p50"] > 0
+
+
+def test_duplicate_submission_refused_and_failed_setup_retires(E):
+    """A grid with a request still waiting or active is refused; a request whose set-up
+    fails at admission (no moduli) polls as done with that error and frees its slot for
+    the next request."""
+    ctx = E.Context(0)
+    good = E.grid_from_problem(ctx, M.eshelby_sphere(17), mixed=True)
+    bare = E.Grid(ctx, E.desc_for(M.eshelby_sphere(17), mixed=True))     # moduli never set
+    server = E.Server(ctx, max_active=1)
+    t_bad = server.submit(bare, rel_tol=1e-8)
+    t_good = server.submit(good, rel_tol=1e-8)
+    with pytest.raises(E.ElasError) as err:
+        server.submit(good, rel_tol=1e-8)
+    assert err.value.code == E.ERR_STATE
+    results = {}
+    for _ in range(500):
+        server.step()
+        for t in (t_bad, t_good):
+            if t not in results:
+                r = server.poll(t)
+                if r is not None:
+                    results[t] = r[0]
+        if len(results) == 2:
+            break
+    assert results[t_bad]["status"] == E.ERR_STATE
+    assert results[t_good]["status"] == 0 and results[t_good]["rel_residual"] <= 1e-8
+    server.close()
+    good.close()
+    bare.close()
+    ctx.close()
