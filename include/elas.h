@@ -74,6 +74,20 @@ extern "C" {
 #define ELAS_PRECISION_FP64  0   /* every level in FP64 */
 #define ELAS_PRECISION_MIXED 1   /* FP32 V-cycle inside FP64 iterative refinement */
 
+/* Smoothers (Section 3.1 smooths with Jacobi iterations; the default here is red-black).
+ * One sweep of each: ELAS_SMOOTH_RB, red then black nodes ((i+j+k) even first), each
+ * colour updated from the values before it (u <- u + B^-1 r with B the node's 3x3
+ * diagonal block); ELAS_SMOOTH_GS8, the eight colours (i mod 2) + 2 (j mod 2) + 4 (k mod 2)
+ * in that order, likewise (block Gauss-Seidel on interior rows, whose stencil never
+ * joins two nodes of one colour); ELAS_SMOOTH_JACOBI, u <- u + omega B^-1 r on every node. */
+#define ELAS_SMOOTH_RB     0
+#define ELAS_SMOOTH_GS8    1
+#define ELAS_SMOOTH_JACOBI 2
+/* Cycles: V, or F (Section 3.1, the paper's runs): the coarse-grid correction of a level
+ * is an F-cycle on the next level followed by a V-cycle from its result. */
+#define ELAS_CYCLE_V 0
+#define ELAS_CYCLE_F 1
+
 typedef struct elas_ctx_s*  elas_ctx;
 typedef struct elas_grid_s* elas_grid;
 
@@ -151,6 +165,10 @@ typedef struct {
     int    use_graph;     /* mixed: replay refinement steps as a captured CUDA graph
                              with device-side stopping (batched solves always do)  */
     int    inner_cycles;  /* mixed: FP32 V-cycles per FP64 refinement step (>= 1)  */
+    int    smoother;      /* ELAS_SMOOTH_RB (default), ELAS_SMOOTH_GS8 or
+                             ELAS_SMOOTH_JACOBI; nu1, nu2 count its sweeps         */
+    int    cycle;         /* ELAS_CYCLE_V (default) or ELAS_CYCLE_F                 */
+    double omega;         /* damping of ELAS_SMOOTH_JACOBI, in (0, 1] (default 2/3) */
 } elas_solve_opts;
 
 #define ELAS_HISTORY 128
@@ -195,6 +213,9 @@ int  elas_op_residual(elas_grid g, int level, int precision, const void* u, cons
                       void* r, double* sumsq);
 /* One red-black sweep (red then black, Jacobi within a colour), in place on u. */
 int  elas_op_sweep(elas_grid g, int level, int precision, void* u, const void* f);
+/* One sweep of the given smoother (ELAS_SMOOTH_*; omega for Jacobi), in place on u. */
+int  elas_op_smooth(elas_grid g, int level, int precision, int smoother, double omega, void* u,
+                    const void* f);
 /* fc = R r: volume-weighted full weighting to level+1 (Section 3.2); 0 on
  * Dirichlet rows of the coarse level. */
 int  elas_op_restrict(elas_grid g, int level, int precision, const void* r, void* fc);

@@ -31,6 +31,22 @@ purpose (each is listed in the design notes):
 * convergence test: the residual after the pre-smoothing of a cycle, relative to
   the residual of the Dirichlet-only initial field; when it is at or below the
   tolerance the solve stops with that field.
+
+Options beside the default (the comparison with the paper's own cycle):
+
+* smoother "gs8": eight colours (i mod 2, j mod 2, k mod 2), swept in the order
+  c = (i mod 2) + 2 (j mod 2) + 4 (k mod 2), each colour Jacobi within itself.  No
+  two nodes of one colour are neighbours in the 19-point interior stencil, so on
+  interior rows this is block Gauss-Seidel in the colour ordering;
+* smoother "jacobi": damped nodal block Jacobi, u <- u + omega B^-1 r on every node
+  at once.  The paper smooths with Jacobi iterations (Section 3.1) and states no
+  weight; the reading is omega = 2/3, the usual damping of Jacobi as a smoother;
+* cycle "F" (Section 3.1: the paper's runs use F-cycles only): the coarse-grid
+  correction of level l is an F-cycle on level l + 1 from zero followed by a
+  V-cycle on level l + 1 from that result; the coarsest level is solved exactly.
+  The paper's schedule, two Jacobi iterations per smoothing operation and four
+  smoothing operations per level, is read as F(4, 4) with Jacobi: four iterations
+  before and four after each coarse-grid correction.
 """
 from __future__ import annotations
 
@@ -198,9 +214,44 @@ def half_sweep(L: LevelData, u, f, colour):
     u += np.where(L.colour == colour, delta, 0.0)
 
 
-def sweep(L, u, f):
-    half_sweep(L, u, f, 0)
-    half_sweep(L, u, f, 1)
+def colour8(shape):
+    """Eight-colour index (i mod 2) + 2 (j mod 2) + 4 (k mod 2) of every node."""
+    k, j, i = np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+    return (i % 2) + 2 * (j % 2) + 4 * (k % 2)
+
+
+def colour_pass(L: LevelData, u, f, mask, omega=1.0):
+    """u_p <- u_p + omega B_p^-1 r_p on the nodes of `mask`, every row evaluated with
+    the values from before the pass."""
+    r = S.residual(L.level, u, f, L.types)
+    delta = np.einsum("...ik,k...->i...", L.Binv, r)
+    u += np.where(mask, omega * delta, 0.0)
+
+
+@dataclasses.dataclass(frozen=True)
+class Smoother:
+    """Smoother of the cycle: "rb" (red-black, the default), "gs8" (eight colours) or
+    "jacobi" (damped block Jacobi with weight omega).  One sweep is red + black, the
+    eight colours, or one Jacobi iteration."""
+    kind: str = "rb"
+    omega: float = 2.0 / 3.0
+
+
+RB = Smoother()
+
+
+def sweep(L, u, f, sm: Smoother = RB):
+    if sm.kind == "rb":
+        half_sweep(L, u, f, 0)
+        half_sweep(L, u, f, 1)
+    elif sm.kind == "gs8":
+        c8 = colour8(L.level.shape)
+        for c in range(8):
+            colour_pass(L, u, f, c8 == c)
+    elif sm.kind == "jacobi":
+        colour_pass(L, u, f, np.ones(L.level.shape, dtype=bool), sm.omega)
+    else:
+        raise ValueError(sm.kind)
 
 
 def bottom_solve(L: LevelData, f):
@@ -220,22 +271,25 @@ def bottom_solve(L: LevelData, f):
     return e
 
 
-def vcycle(levels, l, u, f, nu1, nu2):
+def vcycle(levels, l, u, f, nu1, nu2, sm: Smoother = RB, cycle="V"):
+    """One cycle on level l from the current u: nu1 sweeps, the coarse-grid correction
+    (of the V or F kind), nu2 sweeps; the coarsest level is solved exactly."""
     L = levels[l]
     if l == len(levels) - 1:
         u[...] = bottom_solve(L, f)
         return
     for _ in range(nu1):
-        sweep(L, u, f)
+        sweep(L, u, f, sm)
     r = S.residual(L.level, u, f, L.types)
-    correct(levels, l, u, r, nu1, nu2)
+    correct(levels, l, u, r, nu1, nu2, sm, cycle)
     for _ in range(nu2):
-        sweep(L, u, f)
+        sweep(L, u, f, sm)
 
 
-def correct(levels, l, u, r, nu1, nu2):
-    """Coarse-grid correction: restrict r, cycle on the next level from zero, add the
-    interpolated correction on non-Dirichlet rows."""
+def correct(levels, l, u, r, nu1, nu2, sm: Smoother = RB, cycle="V"):
+    """Coarse-grid correction: restrict r, cycle on the next level from zero (for an F
+    cycle: an F-cycle, then a V-cycle from its result), add the interpolated
+    correction on non-Dirichlet rows."""
     L = levels[l]
     if l == len(levels) - 1:
         # a single-level hierarchy: the correction is the exact (bordered) solve
@@ -245,7 +299,11 @@ def correct(levels, l, u, r, nu1, nu2):
     Lc = levels[l + 1]
     fc = np.where(Lc.types == DIRICHLET, 0.0, fc)
     uc = np.zeros_like(fc)
-    vcycle(levels, l + 1, uc, fc, nu1, nu2)
+    if cycle == "F":
+        vcycle(levels, l + 1, uc, fc, nu1, nu2, sm, "F")
+        vcycle(levels, l + 1, uc, fc, nu1, nu2, sm, "V")
+    else:
+        vcycle(levels, l + 1, uc, fc, nu1, nu2, sm, "V")
     u += np.where(L.types == DIRICHLET, 0.0, prolong(uc, L.level))
 
 
@@ -274,9 +332,10 @@ def equilibrate(null, r, lam):
 
 
 def solve(problem: Problem, tol=1e-8, max_cycles=100, nu1=2, nu2=2, u0=None, levels=None,
-          f=None, fixed_cycles=None):
-    """FP64 V(nu1, nu2) solve.  Returns (u, info).  With ``fixed_cycles`` the solve runs
-    exactly that many coarse-grid corrections and stops after the next pre-smoothing."""
+          f=None, fixed_cycles=None, smoother: Smoother = RB, cycle="V"):
+    """FP64 V(nu1, nu2) (or F(nu1, nu2)) solve.  Returns (u, info).  With
+    ``fixed_cycles`` the solve runs exactly that many coarse-grid corrections and stops
+    after the next pre-smoothing."""
     if levels is None:
         levels = build_hierarchy(S.level_from_problem(problem))
     L0 = levels[0]
@@ -294,7 +353,7 @@ def solve(problem: Problem, tol=1e-8, max_cycles=100, nu1=2, nu2=2, u0=None, lev
     while True:
         feff = f - np.einsum("p,p...->...", lam, L0.null) if lam.size else f
         for _ in range(nu1):
-            sweep(L0, u, feff)
+            sweep(L0, u, feff, smoother)
         r = S.residual(L0.level, u, feff, L0.types)
         r, lam = equilibrate(L0.null, r, lam)
         rel = norm2(r) / r0 if r0 > 0 else 0.0
@@ -309,9 +368,9 @@ def solve(problem: Problem, tol=1e-8, max_cycles=100, nu1=2, nu2=2, u0=None, lev
             converged = rel <= tol
             break
         feff = f - np.einsum("p,p...->...", lam, L0.null) if lam.size else f
-        correct(levels, 0, u, r, nu1, nu2)
+        correct(levels, 0, u, r, nu1, nu2, smoother, cycle)
         for _ in range(nu2):
-            sweep(L0, u, feff)
+            sweep(L0, u, feff, smoother)
         cycles += 1
     u = remove_rigid(L0.null, u)
     return u, SolveInfo(cycles, hist, hist[-1], converged, lam, r0)

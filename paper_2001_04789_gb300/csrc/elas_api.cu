@@ -84,6 +84,7 @@ struct Level {
     double *mod64 = nullptr, *u = nullptr, *ua = nullptr, *f = nullptr, *r = nullptr, *divc = nullptr;
     float *mod32 = nullptr, *u32 = nullptr, *ua32 = nullptr, *f32 = nullptr, *r32 = nullptr;
     __half* mod16 = nullptr;   // FP16 moduli of the FP32 V-cycle (half_moduli grids)
+    bool split = false;        // mod32 holds colour-split records with the divergence
     int* bnd = nullptr;   // boundary-plane nodes of this level
     int nbnd = 0;
     double* bcoef64 = nullptr;   // edge and corner row coefficients (kEdgeCoef per node)
@@ -119,6 +120,10 @@ struct elas_grid_s {
     bool dirty = true;         // moduli or boundary types changed: rebuild everything
     bool rhs_dirty = true;     // only loads / boundary data changed: rebuild the right-hand side
     bool gram_valid = false;   // W^T W of the finest level (depends on boundary types, not moduli)
+    // smoother and cycle of the solve in progress (from its options)
+    int smoother = ELAS_SMOOTH_RB;
+    int cycle = ELAS_CYCLE_V;
+    double omega = 2.0 / 3.0;
     std::vector<std::pair<void*, size_t>> allocs;
 };
 
@@ -198,6 +203,8 @@ void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int 
     L.modh = nullptr;
     L.mlay = kModPlanes;
     L.bcoef = nullptr;
+    L.msplit1 = 0;
+    L.omega = (T)1;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -435,6 +442,7 @@ int setup(elas_grid g) {
         for (int l = 0; l < nl; ++l) {
             Level& v = g->lv[l];
             if (v.mod16) launch_moduli_copy(v.mod64, v.mod16, v.N, g->K, s);
+            else if (v.split) launch_moduli_split(v.mod64, v.divc, v.mod32, v.N, s);
             else launch_moduli_copy(v.mod64, v.mod32, v.N, g->K, s);
             CHECK_LAUNCH(c);
         }
@@ -517,25 +525,44 @@ struct Fields<float> {
     static const Lv<float>& L(Level& v) { return v.L32; }
 };
 
+// `sweeps` sweeps of a smoother on level l, in place on u (ping-pong through ua): red-black
+// (two passes a sweep), eight colours (eight passes) or damped Jacobi (one pass).
 template <typename T>
-void smooth(elas_grid g, int l, int sweeps, const NullInfo* nf, const double* lam) {
+void smooth_with(elas_grid g, int l, int sweeps, int kind, double omega, T* u, T* ua, const T* f, const NullInfo* nf,
+                 const double* lam) {
     Level& v = g->lv[l];
     elas_ctx c = g->ctx;
     cudaStream_t s = c->stream;
     const int cls = sizeof(T) == 8 ? ELAS_PROF_SWEEP64_L0 : ELAS_PROF_SWEEP32_L0;
-    for (int k = 0; k < sweeps; ++k) {
-        size_t e = l == 0 ? prof_begin(c, cls) : (size_t)-1;
-        launch_half_sweep<T>(Fields<T>::L(v), Fields<T>::u(v), Fields<T>::ua(v), Fields<T>::f(v), 0, nf, lam, s);
-        prof_end(c, e);
-        e = l == 0 ? prof_begin(c, cls) : (size_t)-1;
-        launch_half_sweep<T>(Fields<T>::L(v), Fields<T>::ua(v), Fields<T>::u(v), Fields<T>::f(v), 1, nf, lam, s);
+    Lv<T> L = Fields<T>::L(v);
+    L.omega = (T)omega;
+    int passes = 0, first = 0;
+    if (kind == ELAS_SMOOTH_GS8) passes = 8, first = 2;
+    else if (kind == ELAS_SMOOTH_JACOBI) passes = 1, first = kJacobiColour;
+    else passes = 2, first = 0;
+    const int total = sweeps * passes;
+    for (int k = 0; k < total; ++k) {
+        const int colour = kind == ELAS_SMOOTH_JACOBI ? kJacobiColour : first + k % passes;
+        const size_t e = l == 0 ? prof_begin(c, cls) : (size_t)-1;
+        if (k % 2 == 0) launch_half_sweep<T>(L, u, ua, f, colour, nf, lam, s);
+        else launch_half_sweep<T>(L, ua, u, f, colour, nf, lam, s);
         prof_end(c, e);
     }
+    if (total % 2) cudaMemcpyAsync(u, ua, sizeof(T) * 3 * (size_t)v.N, cudaMemcpyDeviceToDevice, s);
 }
 
-// Correction cycle on level l >= 1 (or l = 0 of the FP32 cycle): u_l from zero.
 template <typename T>
-void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const double* dlam0, bool zero_init = true) {
+void smooth(elas_grid g, int l, int sweeps, const NullInfo* nf, const double* lam) {
+    Level& v = g->lv[l];
+    smooth_with<T>(g, l, sweeps, g->smoother, g->omega, Fields<T>::u(v), Fields<T>::ua(v), Fields<T>::f(v), nf, lam);
+}
+
+// Correction cycle on level l >= 1 (or l = 0 of the FP32 cycle): u_l from zero (or from
+// its current value).  cycle: ELAS_CYCLE_V, or ELAS_CYCLE_F, whose coarse-grid correction
+// is an F-cycle on the next level followed by a V-cycle from its result (Section 3.1).
+template <typename T>
+void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const double* dlam0, bool zero_init = true,
+            int cycle = ELAS_CYCLE_V) {
     Level& v = g->lv[l];
     cudaStream_t s = g->ctx->stream;
     const int nl = (int)g->lv.size();
@@ -555,7 +582,12 @@ void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const dou
     prof_end(g->ctx, e);
     Level& w = g->lv[l + 1];
     launch_restrict<T>(Fields<T>::L(v), Fields<T>::L(w), Fields<T>::r(v), Fields<T>::f(w), nullptr, nullptr, s);
-    vcycle<T>(g, l + 1, nu1, nu2, nullptr, nullptr);
+    if (cycle == ELAS_CYCLE_F) {
+        vcycle<T>(g, l + 1, nu1, nu2, nullptr, nullptr, true, ELAS_CYCLE_F);
+        vcycle<T>(g, l + 1, nu1, nu2, nullptr, nullptr, false, ELAS_CYCLE_V);
+    } else {
+        vcycle<T>(g, l + 1, nu1, nu2, nullptr, nullptr);
+    }
     launch_prolong_add<T>(Fields<T>::L(v), Fields<T>::L(w), Fields<T>::u(w), Fields<T>::u(v), s);
     smooth<T>(g, l, nu2, nf, lam);
 }
@@ -584,8 +616,11 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     if ((rc = galloc(g, &v.f, 3 * N))) return rc;
     if ((rc = galloc(g, &v.r, 3 * N))) return rc;
     if (mixed) {
+        v.split = !g->desc.half_moduli && split_layout_applies(v.n, g->K);
         if (g->desc.half_moduli) {
             if ((rc = galloc(g, &v.mod16, moduli_copy_entries(v.N, g->K, true)))) return rc;
+        } else if (v.split) {
+            if ((rc = galloc(g, &v.mod32, split_entries(v.N)))) return rc;
         } else if ((rc = galloc(g, &v.mod32, moduli_copy_entries(v.N, g->K, false)))) {
             return rc;
         }
@@ -596,7 +631,8 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     }
     v.L64.mod = v.mod64;
     v.L32.mod = v.mod32;
-    v.L32.mlay = v.mod16 ? kModRecords : (v.mod32 ? kModBlocked : kModPlanes);
+    v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
+    v.L32.msplit1 = v.split ? split_half_entries((v.N + 1) / 2) : 0;
     // list of the nodes on two or three boundary planes (face nodes are enumerated
     // arithmetically by the face kernels)
     std::vector<int> b;
@@ -640,7 +676,8 @@ void refresh_lv(elas_grid g) {
         v.L64.nbnd = v.L32.nbnd = v.nbnd;
         v.L64.divc = v.divc;
         v.L32.modh = v.mod16;
-        v.L32.mlay = v.mod16 ? kModRecords : (v.mod32 ? kModBlocked : kModPlanes);
+        v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
+        v.L32.msplit1 = v.split ? split_half_entries((v.N + 1) / 2) : 0;
         v.nf = null_space(g->desc, v.n, h, g->bc_type);
     }
 }
@@ -748,7 +785,11 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
     for (auto& n : level_dims(*d)) {
         const size_t N = (size_t)n[0] * n[1] * n[2];
         total += N * 8 * (K + 12 + (K == 21 ? 18 : 0));
-        if (d->mixed) total += (d->half_moduli ? 2 : 4) * moduli_copy_entries((int)N, K, d->half_moduli) + N * 48;
+        if (d->mixed) {
+            const bool split = !d->half_moduli && split_layout_applies(n.data(), K);
+            total += (d->half_moduli ? 2 : 4) * (split ? split_entries((int)N) : moduli_copy_entries((int)N, K, d->half_moduli)) +
+                     N * 48;
+        }
         total += (size_t)4 * (n[0] + n[1] + n[2]) * kEdgeCoef * (d->mixed ? 12 : 8);   // edge rows
     }
     const size_t N0 = (size_t)d->n[0] * d->n[1] * d->n[2];
@@ -935,7 +976,24 @@ void elas_solve_opts_default(elas_solve_opts* o) {
     o->fixed_cycles = 0;
     o->use_graph = 0;
     o->inner_cycles = 1;
+    o->smoother = ELAS_SMOOTH_RB;
+    o->cycle = ELAS_CYCLE_V;
+    o->omega = 2.0 / 3.0;
 }
+
+namespace {
+// Take the smoother and cycle of a solve's options onto the grid (checked).
+int take_cycle_opts(elas_grid g, const elas_solve_opts* o) {
+    if (o->smoother < ELAS_SMOOTH_RB || o->smoother > ELAS_SMOOTH_JACOBI || (o->cycle != ELAS_CYCLE_V && o->cycle != ELAS_CYCLE_F))
+        return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "unknown smoother or cycle");
+    if (o->smoother == ELAS_SMOOTH_JACOBI && !(o->omega > 0.0 && o->omega <= 1.0))
+        return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "Jacobi damping must lie in (0, 1]");
+    g->smoother = o->smoother;
+    g->cycle = o->cycle;
+    g->omega = o->omega;
+    return ELAS_OK;
+}
+}  // namespace
 
 int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) {
     if (!g || !opts || !info) return ELAS_ERR_INVALID_ARG;
@@ -947,7 +1005,9 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
     if (g->desc.max_levels == 1) return set_err(c, ELAS_ERR_STATE, "grid has no multigrid hierarchy (AMR level)");
     if (mixed && opts->use_graph) return elas_batch_solve(&g, 1, opts, info);   // graph replay, one member
     const auto t0 = std::chrono::steady_clock::now();
-    int rc = setup(g);
+    int rc = take_cycle_opts(g, opts);
+    if (rc) return rc;
+    rc = setup(g);
     if (rc) return rc;
     cudaStream_t s = c->stream;
     Level& L0 = g->lv[0];
@@ -1004,13 +1064,18 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
         } else if (!mixed) {
             Level& L1 = g->lv[1];
             launch_restrict<double>(L0.L64, L1.L64, L0.r, L1.f, nf0, dload, s);
-            vcycle<double>(g, 1, nu1, nu2, nullptr, nullptr);
+            if (g->cycle == ELAS_CYCLE_F) {
+                vcycle<double>(g, 1, nu1, nu2, nullptr, nullptr, true, ELAS_CYCLE_F);
+                vcycle<double>(g, 1, nu1, nu2, nullptr, nullptr, false, ELAS_CYCLE_V);
+            } else {
+                vcycle<double>(g, 1, nu1, nu2, nullptr, nullptr);
+            }
             launch_prolong_add<double>(L0.L64, L1.L64, L1.u, L0.u, s);
             smooth<double>(g, 0, nu2, nf0, load);
         } else {
             // FP32 V-cycles on the correction equation, the first from zero
             const int inner = opts->inner_cycles > 1 ? opts->inner_cycles : 1;
-            for (int k = 0; k < inner; ++k) vcycle<float>(g, 0, nu1, nu2, nf0, dload, k == 0);
+            for (int k = 0; k < inner; ++k) vcycle<float>(g, 0, nu1, nu2, nf0, dload, k == 0, g->cycle);
             launch_add_correction(L0.L64, L0.u, L0.u32, s);
         }
         CHECK_LAUNCH(c);
@@ -1184,6 +1249,19 @@ int elas_op_sweep(elas_grid g, int level, int precision, void* u, const void* f)
     return ELAS_OK;
 }
 
+int elas_op_smooth(elas_grid g, int level, int precision, int smoother, double omega, void* u, const void* f) {
+    int rc = check_level(g, level, precision);
+    if (rc) return rc;
+    if (smoother < ELAS_SMOOTH_RB || smoother > ELAS_SMOOTH_JACOBI)
+        return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "unknown smoother");
+    Level& v = g->lv[level];
+    if (precision == 0) smooth_with<double>(g, level, 1, smoother, omega, (double*)u, v.ua, (const double*)f, nullptr, nullptr);
+    else smooth_with<float>(g, level, 1, smoother, omega, (float*)u, v.ua32, (const float*)f, nullptr, nullptr);
+    CHECK_LAUNCH(g->ctx);
+    CUDA_TRY(g->ctx, cudaStreamSynchronize(g->ctx->stream));
+    return ELAS_OK;
+}
+
 int elas_op_restrict(elas_grid g, int level, int precision, const void* r, void* fc) {
     int rc = check_level(g, level, precision);
     if (rc) return rc;
@@ -1349,7 +1427,8 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
     const auto t0 = std::chrono::steady_clock::now();
     for (int i = 0; i < n; ++i) {
         std::memset(&info[i], 0, sizeof(info[i]));
-        const int rc = setup(grids[i]);
+        int rc = take_cycle_opts(grids[i], opts);
+        if (!rc) rc = setup(grids[i]);
         if (rc) return rc;
     }
     // per-member flags, counters and histories; every exit of the run clears the members'
@@ -1431,7 +1510,7 @@ int batch_run(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_i
             launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1,
                             c->stream, bfl);
             for (int k = 0; k < (opts->inner_cycles > 1 ? opts->inner_cycles : 1); ++k)
-                vcycle<float>(g, 0, nu1, nu2, nf0, nf0 ? g->adlam : nullptr, k == 0);
+                vcycle<float>(g, 0, nu1, nu2, nf0, nf0 ? g->adlam : nullptr, k == 0, opts->cycle);
             launch_add_correction(L0.L64, L0.u, L0.u32, c->stream);
         }
     }
@@ -1699,6 +1778,9 @@ int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* inf
         CHECK_LAUNCH(c);
     }
     for (auto g : a->g) {
+        // the composite cycle smooths with the red-black smoother in V-cycles
+        g->smoother = ELAS_SMOOTH_RB;
+        g->cycle = ELAS_CYCLE_V;
         int rc = setup(g);
         if (rc) return rc;
     }
@@ -1850,7 +1932,8 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
         ServerReq r = s->waiting.front();
         s->waiting.pop_front();
         elas_grid g = r.g;
-        const int rc = setup(g);
+        int rc = take_cycle_opts(g, &r.opts);
+        if (!rc) rc = setup(g);
         if (rc) {
             ServerDone d{};
             d.info.status = rc;
@@ -1904,7 +1987,7 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
             launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1,
                             c->stream, bfl);
             for (int k = 0; k < (r.opts.inner_cycles > 1 ? r.opts.inner_cycles : 1); ++k)
-                vcycle<float>(g, 0, r.opts.nu1, r.opts.nu2, nf0, nf0 ? g->adlam : nullptr, k == 0);
+                vcycle<float>(g, 0, r.opts.nu1, r.opts.nu2, nf0, nf0 ? g->adlam : nullptr, k == 0, r.opts.cycle);
             launch_add_correction(L0.L64, L0.u, L0.u32, c->stream);
         }
         c->stream = main;

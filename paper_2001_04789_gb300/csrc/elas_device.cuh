@@ -49,7 +49,21 @@ struct Lv {
     // [row i][slot][component k] (see edge_slot_node), so a row is a 27-slot dot product;
     // set up with the moduli, required by the smoother and the residual
     const T* __restrict__ bcoef;
+    // colour-split layout (kModSplit): offset, in elements, of the odd-index half
+    size_t msplit1;
+    // damping of the Jacobi smoother (colour kJacobiColour); the other smoothers ignore it
+    T omega;
 };
+
+// Which nodes one smoother pass updates.  Colours 0 and 1: red-black, (i + j + k) mod 2;
+// 2..9: the eight colours (i mod 2) + 2 (j mod 2) + 4 (k mod 2), offset by 2;
+// kJacobiColour: every node (damped block Jacobi).
+constexpr int kJacobiColour = 10;
+__host__ __device__ __forceinline__ bool sweep_active(int colour, int x, int y, int z) {
+    if (colour < 2) return ((x + y + z) & 1) == colour;
+    if (colour < kJacobiColour) return ((x & 1) | ((y & 1) << 1) | ((z & 1) << 2)) == colour - 2;
+    return true;
+}
 
 // Edge and corner rows reach 3 nodes per direction: c-1, c, c+1 where the node is not on a
 // boundary plane of that direction (wrapped when periodic), c, c+s, c+2s (s inward) where
@@ -64,11 +78,21 @@ constexpr int kEdgeCoef = 243;
 // of a node are compile-time offsets (multiples of 128 bytes) from one address.
 // Records (FP16 copies): node-major, lambda, mu or the 21 components padded to 24, so a
 // node costs one address and three 16-byte loads.
-enum : int { kModPlanes = 0, kModBlocked = 1, kModRecords = 2 };
+// Colour split (FP32 copies of general moduli on levels with odd nx and ny): there the
+// parity of the linear index q equals the red-black colour (i + j + k) mod 2, so the even
+// and the odd q form the two colours.  Each colour is stored blocked as above, with
+// kSplitK components per node: the 21 moduli followed by the 18 entries of the modulus
+// divergence M_iV = sum_j d_j C_(ij)V (i * 6 + V).  Component c of node q sits at
+// (q & 1) * msplit1 + blocked_index(kSplitK, c, q >> 1).  A half-sweep then reads only its
+// colour's records, contiguous for a warp, and no neighbour moduli at all.
+enum : int { kModPlanes = 0, kModBlocked = 1, kModRecords = 2, kModSplit = 3 };
+constexpr int kSplitK = 39;
 __host__ __device__ constexpr int mod_record(int K) { return K == 2 ? 2 : 24; }
 __host__ __device__ inline size_t blocked_index(int K, int c, int q) {
     return (size_t)(q >> 5) * (32 * K) + 32 * c + (q & 31);
 }
+// Elements of one colour half of the split layout (count nodes, blocks of 32).
+__host__ __device__ inline size_t split_half_entries(int count) { return (size_t)((count + 31) / 32) * 32 * kSplitK; }
 
 // Moduli component c of node q in the level's layout.
 template <typename T>
@@ -76,6 +100,7 @@ __device__ __forceinline__ T modc(const Lv<T>& L, int c, int q) {
     if (sizeof(T) == 4) {
         if (L.mlay == kModRecords) return T(__half2float(L.modh[(size_t)q * mod_record(L.K) + c]));
         if (L.mlay == kModBlocked) return L.mod[blocked_index(L.K, c, q)];
+        if (L.mlay == kModSplit) return L.mod[(q & 1) * L.msplit1 + blocked_index(kSplitK, c, q >> 1)];
     }
     return L.mod[(size_t)c * L.N + q];
 }
@@ -427,12 +452,12 @@ __device__ __forceinline__ void interior_rows_core(const Lv<T>& L, const UA& ua,
             }
         }
         T acc[3] = {T(0), T(0), T(0)};
-        if (HAS_M) {
-            // term 1: M_iV e_V
+        if constexpr (HAS_M) {
+            // term 1: M_iV e_V, the divergence as components 21 + i * 6 + V of the accessor
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int V = 0; V < 6; ++V) acc[i] = xfma(L.divc[(i * 6 + V) * L.N + p], e[V], acc[i]);
+                for (int V = 0; V < 6; ++V) acc[i] = xfma(ca(21 + i * 6 + V, 0, 0, 0), e[V], acc[i]);
         }
         // term 2: C_(ij)b S_jb, centre moduli
 #pragma unroll
@@ -441,7 +466,7 @@ __device__ __forceinline__ void interior_rows_core(const Lv<T>& L, const UA& ua,
             for (int j = 0; j < 3; ++j)
 #pragma unroll
                 for (int b = 0; b < 6; ++b) acc[i] = xfma(ca(upper(voigt(i, j), b), 0, 0, 0), S[j][b], acc[i]);
-        if (!HAS_M) {
+        if constexpr (!HAS_M) {
             // term 1: (d_j C_(ij)V) e_V, one direction at a time (the two neighbour
             // records of direction j are live only within its iteration)
 #pragma unroll
@@ -464,10 +489,15 @@ __device__ __forceinline__ void interior_rows_core(const Lv<T>& L, const UA& ua,
 }
 
 
+// Moduli layouts of the interior accessor (template argument ML): FP64 planes or FP32
+// blocks, FP16 node records, FP32 colour split (centre node only).
+enum : int { kMlDefault = 0, kMlHalf = 1, kMlSplit = 2 };
+
 // Calls body(ua, ca, p) with the accessors of the interior node (x, y, z): displacement
-// planes, and the moduli in the level's layout (FP64 planes; FP32 or FP16 node records,
-// MH selecting FP16).  Periodic directions wrap.
-template <typename T, int KIND, bool MH, class F>
+// planes, and the moduli in the level's layout (ML, above).  Components from 21 on are
+// the modulus divergence: FP64 planes in L.divc, or the split records' tail.  Periodic
+// directions wrap.
+template <typename T, int KIND, int ML, class F>
 __device__ __forceinline__ void with_interior(const Lv<T>& L, const T* __restrict__ u, int x, int y, int z,
                                               F&& body) {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
@@ -480,16 +510,24 @@ __device__ __forceinline__ void with_interior(const Lv<T>& L, const T* __restric
     const int Zs[3] = {Z[0] * nx * ny, Z[1] * nx * ny, Z[2] * nx * ny};
     auto ua = [&](int k, int dx, int dy, int dz) { return u[k * N + X[dx + 1] + Ys[dy + 1] + Zs[dz + 1]]; };
     const int p = X[1] + Ys[1] + Zs[1];
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && ML == kMlSplit) {
+        // centre records only (the divergence replaces the neighbour moduli)
+        const float* cb = (const float*)L.mod + (p & 1) * L.msplit1 + (size_t)((p >> 1) >> 5) * (32 * kSplitK) +
+                          ((p >> 1) & 31);
+        auto ca = [&](int c, int, int, int) -> T { return __ldg(cb + 32 * c); };
+        body(ua, ca, p);
+    } else if constexpr (sizeof(T) == 4) {
         auto ca = [&](int c, int dx, int dy, int dz) -> T {
             const int q = X[dx + 1] + Ys[dy + 1] + Zs[dz + 1];
-            if constexpr (MH) return rec_half<KIND>(L.modh, q, c);
+            if constexpr (ML == kMlHalf) return rec_half<KIND>(L.modh, q, c);
             else return blk_float<KIND>(L.mod, q, c);
         };
         body(ua, ca, p);
     } else {
         auto ca = [&](int c, int dx, int dy, int dz) -> T {
-            return L.mod[(size_t)c * N + X[dx + 1] + Ys[dy + 1] + Zs[dz + 1]];
+            const int q = X[dx + 1] + Ys[dy + 1] + Zs[dz + 1];
+            if (c >= 21) return L.divc[(size_t)(c - 21) * N + q];
+            return L.mod[(size_t)c * N + q];
         };
         body(ua, ca, p);
     }
@@ -499,12 +537,19 @@ __device__ __forceinline__ void with_interior(const Lv<T>& L, const T* __restric
 template <typename T, int KIND, bool HAS_M = false>
 __device__ __forceinline__ void interior_rows(const Lv<T>& L, const T* __restrict__ u,
                                               int x, int y, int z, T out[3]) {
+    if constexpr (sizeof(T) == 4) {
+        if (KIND == 21 && L.mlay == kModSplit) {
+            auto body = [&](const auto& ua, const auto& ca, int p) { interior_rows_core<T, KIND, true>(L, ua, ca, p, out); };
+            with_interior<T, KIND, kMlSplit>(L, u, x, y, z, body);
+            return;
+        }
+    }
     auto body = [&](const auto& ua, const auto& ca, int p) { interior_rows_core<T, KIND, HAS_M>(L, ua, ca, p, out); };
     if constexpr (sizeof(T) == 4) {
-        if (L.modh) with_interior<T, KIND, true>(L, u, x, y, z, body);
-        else with_interior<T, KIND, false>(L, u, x, y, z, body);
+        if (L.modh) with_interior<T, KIND, kMlHalf>(L, u, x, y, z, body);
+        else with_interior<T, KIND, kMlDefault>(L, u, x, y, z, body);
     } else {
-        with_interior<T, KIND, false>(L, u, x, y, z, body);
+        with_interior<T, KIND, kMlDefault>(L, u, x, y, z, body);
     }
 }
 

@@ -79,6 +79,12 @@ size_t moduli_copy_entries(int N, int K, bool half);
 template <typename T>
 void launch_edge_coef(const Lv<T>& L, T* out, cudaStream_t s);
 void launch_moduli_copy(const double* in, float* out, int N, int K, cudaStream_t s);
+// Colour-split FP32 records (moduli + divergence, kModSplit) of a general-moduli level with
+// odd nx and ny: whether a level takes them, their element count, and the copy from the
+// FP64 moduli and divergence planes.
+bool split_layout_applies(const int n[3], int K);
+size_t split_entries(int N);
+void launch_moduli_split(const double* mod, const double* divc, float* out, int N, cudaStream_t s);
 void launch_moduli_copy(const double* in, __half* out, int N, int K, cudaStream_t s);
 // M_iV = sum_j d_j C_(ij)V (18 planes) of a general-moduli FP64 level (setup)
 void launch_divc(const Lv<double>& L, double* M, cudaStream_t s);

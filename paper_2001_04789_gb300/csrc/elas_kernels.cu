@@ -145,6 +145,31 @@ void launch_moduli_copy(const double* in, float* out, int N, int K, cudaStream_t
     k_to_moduli_copy<float><<<blocks_for(moduli_copy_entries(N, K, false)), kBlock, 0, s>>>(in, out, N, K);
 }
 
+// FP64 moduli (21 planes) and divergence (18 planes) -> the FP32 colour-split records.
+__global__ void k_to_moduli_split(const double* __restrict__ mod, const double* __restrict__ divc,
+                                  float* __restrict__ out, int N, size_t half1, size_t total) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int h = i >= half1 ? 1 : 0;
+    const size_t r = h ? i - half1 : i;
+    const size_t blk = r / (32 * (size_t)kSplitK), rr = r % (32 * (size_t)kSplitK);
+    const int c = (int)(rr / 32);
+    const long long q = 2 * (long long)(blk * 32 + rr % 32) + h;
+    double v = 0.0;
+    if (q < N) v = c < 21 ? mod[(size_t)c * N + q] : divc[(size_t)(c - 21) * N + q];
+    out[i] = (float)v;
+}
+
+bool split_layout_applies(const int n[3], int K) { return K == 21 && (n[0] & 1) && (n[1] & 1); }
+
+size_t split_entries(int N) { return split_half_entries((N + 1) / 2) + split_half_entries(N / 2); }
+
+void launch_moduli_split(const double* mod, const double* divc, float* out, int N, cudaStream_t s) {
+    const size_t total = split_entries(N);
+    count_launch();
+    k_to_moduli_split<<<blocks_for(total), kBlock, 0, s>>>(mod, divc, out, N, split_half_entries((N + 1) / 2), total);
+}
+
 void launch_moduli_copy(const double* in, __half* out, int N, int K, cudaStream_t s) {
     count_launch();
     k_to_moduli_copy<__half><<<blocks_for(moduli_copy_entries(N, K, true)), kBlock, 0, s>>>(in, out, N, K);

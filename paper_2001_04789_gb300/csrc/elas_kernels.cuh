@@ -289,7 +289,7 @@ __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restri
 
 // Residual bodies: one interior node per thread, one edge/corner node per warp, one
 // face node per thread; each adds its node's contributions to the thread's sums.
-template <typename T, typename TR, int KIND, bool NORM, bool HM, bool MH>
+template <typename T, typename TR, int KIND, bool NORM, bool HM, int ML>
 __device__ __forceinline__ void residual_int_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
                                                   const NullInfo& nf, const double* __restrict__ lam,
                                                   TR* __restrict__ r, int t, double acc[7]) {
@@ -298,7 +298,7 @@ __device__ __forceinline__ void residual_int_body(const Lv<T>& L, const T* __res
     if (t >= cnt[0] * cnt[1] * cnt[2]) return;
     const int c[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
     T v[3];
-    with_interior<T, KIND, MH>(L, u, c[0], c[1], c[2], [&](const auto& ua, const auto& ca, int p) {
+    with_interior<T, KIND, ML>(L, u, c[0], c[1], c[2], [&](const auto& ua, const auto& ca, int p) {
         interior_rows_core<T, KIND, HM>(L, ua, ca, p, v);
     });
     const int types[3] = {ROW_INTERIOR, ROW_INTERIOR, ROW_INTERIOR};
@@ -352,7 +352,7 @@ __device__ __forceinline__ void residual_bnd_body(const Lv<T>& L, const T* __res
 // Red-black smoother, interior nodes: each thread owns the x-pair (x0, x0+1) of the
 // interior box, updates the one of the active colour and copies the other; every
 // row uses the values from before the half-sweep (Jacobi within the colour).
-template <typename T, int KIND, bool HM, bool MH>
+template <typename T, int KIND, bool HM, int ML>
 __device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restrict__ u, T* __restrict__ uo,
                                                 const T* __restrict__ f, int colour, const NullInfo& nf,
                                                 const double* __restrict__ lam, int t) {
@@ -365,30 +365,45 @@ __device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restr
     const int y = lo[1] + yz % cnt[1], z = lo[2] + yz / cnt[1];
     const int x0 = lo[0] + 2 * m;
     const int xend = lo[0] + cnt[0];          // one past the last interior x
-    const int xa = x0 + ((x0 + y + z + colour) & 1);
-    const int xi = (xa == x0) ? x0 + 1 : x0;
     const int N = L.N;
-    if (xi < xend) {
-        const int q = lin(L, xi, y, z);
+    auto copy = [&](int x) {
+        const int q = lin(L, x, y, z);
         uo[q] = u[q];
         uo[N + q] = u[N + q];
         uo[2 * N + q] = u[2 * N + q];
-    }
-    if (xa >= xend) return;
-    const int c[3] = {xa, y, z};
-    auto body = [&](const auto& ua, const auto& ca, int p) {
-        T v[3], r[3], B[3][3], d[3];
-        interior_rows_core<T, KIND, HM>(L, ua, ca, p, v);
-        for (int i = 0; i < 3; ++i) {
-            T fi = f[i * N + p];
-            if (lam) fi = xsub(fi, rigid_load<T>(nf, lam, i, c));
-            r[i] = xsub(fi, v[i]);
-        }
-        interior_block_acc<T, KIND>(L, ca, B);
-        solve3(B, r, d);
-        for (int i = 0; i < 3; ++i) uo[i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
     };
-    with_interior<T, KIND, MH>(L, u, xa, y, z, body);
+    auto update = [&](int x) {
+        const int c[3] = {x, y, z};
+        auto body = [&](const auto& ua, const auto& ca, int p) {
+            T v[3], r[3], B[3][3], d[3];
+            interior_rows_core<T, KIND, HM>(L, ua, ca, p, v);
+            for (int i = 0; i < 3; ++i) {
+                T fi = f[i * N + p];
+                if (lam) fi = xsub(fi, rigid_load<T>(nf, lam, i, c));
+                r[i] = xsub(fi, v[i]);
+            }
+            interior_block_acc<T, KIND>(L, ca, B);
+            solve3(B, r, d);
+            if (colour == kJacobiColour)
+                for (int i = 0; i < 3; ++i) d[i] = xmul(L.omega, d[i]);
+            for (int i = 0; i < 3; ++i) uo[i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
+        };
+        with_interior<T, KIND, ML>(L, u, x, y, z, body);
+    };
+    if (colour < 2) {
+        // red-black: exactly one node of the pair is active
+        const int xa = x0 + ((x0 + y + z + colour) & 1);
+        const int xi = (xa == x0) ? x0 + 1 : x0;
+        if (xi < xend) copy(xi);
+        if (xa < xend) update(xa);
+        return;
+    }
+    // eight colours or Jacobi: each node of the pair in turn
+#pragma unroll 1
+    for (int x = x0; x < x0 + 2 && x < xend; ++x) {
+        if (sweep_active(colour, x, y, z)) update(x);
+        else copy(x);
+    }
 }
 
 // ---- shared-memory tiled FP32 interior smoother --------------------------------------
@@ -561,7 +576,7 @@ __device__ __forceinline__ void sweep_bnd_body(const Lv<T>& L, const T* __restri
     const int N = L.N;
     int c[3];
     coords_of(p, L.n, c);
-    if (((c[0] + c[1] + c[2]) & 1) != colour) {
+    if (!sweep_active(colour, c[0], c[1], c[2])) {
         if (lane < 3) uo[lane * N + p] = u[lane * N + p];
         return;
     }
@@ -587,6 +602,8 @@ __device__ __forceinline__ void sweep_bnd_body(const Lv<T>& L, const T* __restri
         }
     }
     solve3(B, r, d);
+    if (colour == kJacobiColour)
+        for (int i = 0; i < 3; ++i) d[i] *= L.omega;
     for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
 }
 
@@ -672,7 +689,7 @@ __device__ __forceinline__ void sweep_face_body(const Lv<T>& L, const T* __restr
     if (!face_coords<T, A>(L, t, c, side)) return;
     const int N = L.N;
     const int p = lin(L, c[0], c[1], c[2]);
-    if (((c[0] + c[1] + c[2]) & 1) != colour) {
+    if (!sweep_active(colour, c[0], c[1], c[2])) {
         uo[p] = u[p];
         uo[N + p] = u[N + p];
         uo[2 * N + p] = u[2 * N + p];
@@ -692,6 +709,8 @@ __device__ __forceinline__ void sweep_face_body(const Lv<T>& L, const T* __restr
         }
     }
     solve3(B, r, d);
+    if (colour == kJacobiColour)
+        for (int i = 0; i < 3; ++i) d[i] *= L.omega;
     for (int i = 0; i < 3; ++i) uo[i * N + p] = u[i * N + p] + (types[i] == ROW_DIRICHLET ? T(0) : d[i]);
 }
 
@@ -750,7 +769,7 @@ inline BndSegs bnd_segs(const Lv<T>& L, int bs) {
 }
 
 // Red-black smoother, all nodes of one colour (see the bodies above for each kind).
-template <typename T, int KIND, bool HM, bool MH, int BS, int MINB>
+template <typename T, int KIND, bool HM, int ML, int BS, int MINB>
 __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* __restrict__ u, T* __restrict__ uo,
                                                           const T* __restrict__ f, int colour, NullInfo nf,
                                                           const double* __restrict__ lam, BndSegs sg) {
@@ -763,7 +782,7 @@ __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* _
         else sweep_face_body<T, KIND, 2>(L, u, uo, f, colour, nf, lam, (b - sg.f1) * BS + tid);
         return;
     }
-    sweep_pair_body<T, KIND, HM, MH>(L, u, uo, f, colour, nf, lam, (b - sg.f2) * BS + tid);
+    sweep_pair_body<T, KIND, HM, ML>(L, u, uo, f, colour, nf, lam, (b - sg.f2) * BS + tid);
 }
 
 // r = f - load - A u on every node; block partials of sum r^2 and the rigid moments.
@@ -771,7 +790,7 @@ __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* _
 // by the FP64 pipe and needs the warps to keep it busy, one block at 180 registers ran
 // 15% slower), three for FP32 (80 registers with a few spills: 0.97 -> 0.79 ms at 257^3,
 // the same latency-for-registers trade as the smoother's (256,3) shape).
-template <typename T, typename TR, int KIND, bool NORM, bool HM, bool MH>
+template <typename T, typename TR, int KIND, bool NORM, bool HM, int ML>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                                     NullInfo nf, const double* __restrict__ lam,
                                                     TR* __restrict__ r, double* __restrict__ partials, BndSegs sg) {
@@ -782,7 +801,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) k_residual(Lv<
     else if (b < sg.f0) residual_face_body<T, TR, KIND, 0, NORM>(L, u, f, nf, lam, r, (b - sg.e) * kBlock + tid, acc);
     else if (b < sg.f1) residual_face_body<T, TR, KIND, 1, NORM>(L, u, f, nf, lam, r, (b - sg.f0) * kBlock + tid, acc);
     else if (b < sg.f2) residual_face_body<T, TR, KIND, 2, NORM>(L, u, f, nf, lam, r, (b - sg.f1) * kBlock + tid, acc);
-    else residual_int_body<T, TR, KIND, NORM, HM, MH>(L, u, f, nf, lam, r, (b - sg.f2) * kBlock + tid, acc);
+    else residual_int_body<T, TR, KIND, NORM, HM, ML>(L, u, f, nf, lam, r, (b - sg.f2) * kBlock + tid, acc);
     if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
 }
 

@@ -19,26 +19,34 @@ void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf,
     // their moduli as FP32 blocks or FP16 records
     if constexpr (sizeof(T) == 8) {
         if (L.K == 21 && L.divc) {
-            if (partials) k_residual<T, TR, 21, true, true, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
-            else k_residual<T, TR, 21, false, true, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
+            if (partials) k_residual<T, TR, 21, true, true, kMlDefault><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
+            else k_residual<T, TR, 21, false, true, kMlDefault><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
+            return;
+        }
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (L.K == 21 && L.mlay == kModSplit) {
+            // colour-split records with the divergence
+            if (partials) k_residual<T, TR, 21, true, true, kMlSplit><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
+            else k_residual<T, TR, 21, false, true, kMlSplit><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
             return;
         }
     }
     if (L.modh) {
         if (partials) {
-            if (L.K == 2) k_residual<T, TR, 2, true, false, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
-            else k_residual<T, TR, 21, true, false, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
+            if (L.K == 2) k_residual<T, TR, 2, true, false, kMlHalf><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
+            else k_residual<T, TR, 21, true, false, kMlHalf><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
         } else {
-            if (L.K == 2) k_residual<T, TR, 2, false, false, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
-            else k_residual<T, TR, 21, false, false, true><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
+            if (L.K == 2) k_residual<T, TR, 2, false, false, kMlHalf><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
+            else k_residual<T, TR, 21, false, false, kMlHalf><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
         }
     } else {
         if (partials) {
-            if (L.K == 2) k_residual<T, TR, 2, true, false, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
-            else k_residual<T, TR, 21, true, false, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
+            if (L.K == 2) k_residual<T, TR, 2, true, false, kMlDefault><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
+            else k_residual<T, TR, 21, true, false, kMlDefault><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, partials, sg);
         } else {
-            if (L.K == 2) k_residual<T, TR, 2, false, false, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
-            else k_residual<T, TR, 21, false, false, false><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
+            if (L.K == 2) k_residual<T, TR, 2, false, false, kMlDefault><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
+            else k_residual<T, TR, 21, false, false, kMlDefault><<<nb, kBlock, 0, s>>>(L, u, f, nfv, lam, r, nullptr, sg);
         }
     }
 }

@@ -1,15 +1,18 @@
 // Red-black smoother launchers and autotuner, FP32 levels.  The kernel instances compile
 // in the companion units: FP16-moduli shapes (elas_sweep_f32_h.cu), isotropic moduli
-// (elas_sweep_f32_iso.cu) and the shared-memory tiled kernel (elas_sweep_f32_tiled.cu).
+// (elas_sweep_f32_iso.cu), colour-split moduli (elas_sweep_f32_split.cu) and the
+// shared-memory tiled kernel (elas_sweep_f32_tiled.cu).
 #include "elas_sweep_impl.cuh"
 
 namespace elas {
 
-extern template void sweep_int_variant<float, 2, false, false>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
+extern template void sweep_int_variant<float, 2, false, kMlDefault>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
                                                 const NullInfo&, const double*, cudaStream_t);
-extern template void sweep_int_variant<float, 2, false, true>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
+extern template void sweep_int_variant<float, 2, false, kMlHalf>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
                                                 const NullInfo&, const double*, cudaStream_t);
-extern template void sweep_int_variant<float, 21, false, true>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
+extern template void sweep_int_variant<float, 21, false, kMlHalf>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
+                                                const NullInfo&, const double*, cudaStream_t);
+extern template void sweep_int_variant<float, 21, true, kMlSplit>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
                                                 const NullInfo&, const double*, cudaStream_t);
 extern template void launch_tiled<21, 16>(const Lv<float>&, const float*, float*, const float*, int, const NullInfo&, const double*,
                                   cudaStream_t);

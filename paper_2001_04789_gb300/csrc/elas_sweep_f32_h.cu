@@ -3,9 +3,9 @@
 
 namespace elas {
 
-template void sweep_int_variant<float, 2, false, true>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
+template void sweep_int_variant<float, 2, false, kMlHalf>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
                                                 const NullInfo&, const double*, cudaStream_t);
-template void sweep_int_variant<float, 21, false, true>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
+template void sweep_int_variant<float, 21, false, kMlHalf>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
                                                 const NullInfo&, const double*, cudaStream_t);
 
 }  // namespace elas

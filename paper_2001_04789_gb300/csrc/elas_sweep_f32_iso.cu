@@ -8,7 +8,7 @@ extern template void launch_tiled<2, 16>(const Lv<float>&, const float*, float*,
                                   cudaStream_t);
 extern template void launch_tiled<2, 8>(const Lv<float>&, const float*, float*, const float*, int, const NullInfo&, const double*,
                                   cudaStream_t);
-template void sweep_int_variant<float, 2, false, false>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
+template void sweep_int_variant<float, 2, false, kMlDefault>(int, size_t, const Lv<float>&, const float*, float*, const float*, int,
                                                 const NullInfo&, const double*, cudaStream_t);
 
 }  // namespace elas

@@ -17,9 +17,11 @@ static const int kSweepVariants[kNumSweepVariants][2] = {{256, 1}, {256, 2}, {25
                                                          {256, 1}, {128, 2}};
 constexpr int kFirstTiledVariant = 5;
 
+// Tuning key: level dimensions, moduli kind, precision and the moduli source (1: FP64
+// levels with the precomputed divergence, 2: FP32 colour-split records, 0: otherwise).
 template <typename T>
 static std::array<int, 6> tune_key(const Lv<T>& L) {
-    return {L.n[0], L.n[1], L.n[2], L.K, (int)sizeof(T), L.divc ? 1 : 0};
+    return {L.n[0], L.n[1], L.n[2], L.K, (int)sizeof(T), L.divc ? 1 : (L.mlay == kModSplit ? 2 : 0)};
 }
 
 template <typename T>
@@ -84,6 +86,7 @@ void launch_tiled(const Lv<float>& L, const float* u_in, float* u_out, const flo
 template <typename T>
 static bool variant_ok(const Lv<T>& L, int v) {
     if (sizeof(T) == 4 && L.modh) return v == 1 || v == 2;   // FP16 records: two shapes
+    if (sizeof(T) == 4 && L.mlay == kModSplit) return v < kFirstTiledVariant;   // untiled shapes
     if (v < kFirstTiledVariant) return true;
     return sizeof(T) == 4 && L.mlay == kModBlocked && !L.divc;
 }
@@ -105,11 +108,11 @@ static void launch_boundary_sweep(const Lv<T>& L, const T* u_in, T* u_out, const
 
 // One half-sweep with interior shape v: the untiled shapes take every node in one
 // launch; the tiled ones launch the boundary nodes separately.
-template <typename T, int KIND, bool HM, bool MH>
+template <typename T, int KIND, bool HM, int MH>
 void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
                        const NullInfo& nfv, const double* lam, cudaStream_t s) {
-    if constexpr (sizeof(T) == 4 && !HM && !MH) {
-        if (v >= kFirstTiledVariant && variant_ok(L, v)) {
+    if constexpr (sizeof(T) == 4 && !HM && MH == kMlDefault) {
+        if (v >= kFirstTiledVariant && variant_ok(L, v) && colour < 2) {   // tiled: red-black only
             if (np) {
                 count_launch();
                 if (v == kFirstTiledVariant) launch_tiled<KIND, 16>(L, u_in, u_out, f, colour, nfv, lam, s);
@@ -120,15 +123,15 @@ void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out
         }
     }
     if (v >= kFirstTiledVariant || !variant_ok(L, v)) v = kDefaultSweepVariant;
-    if constexpr (MH) {
+    if constexpr (MH == kMlHalf) {
         // FP16 records: shapes (256,2) and (256,3) only
         const int bs = 256;
         const BndSegs sg = bnd_segs(L, bs);
         const int nb = sg.f2 + (int)((np + bs - 1) / bs);
         if (!nb) return;
         count_launch();
-        if (v == 1) k_half_sweep_int<T, KIND, HM, true, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg);
-        else k_half_sweep_int<T, KIND, HM, true, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg);
+        if (v == 1) k_half_sweep_int<T, KIND, HM, kMlHalf, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg);
+        else k_half_sweep_int<T, KIND, HM, kMlHalf, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg);
     } else {
         const int bs = kSweepVariants[v][0];
         const BndSegs sg = bnd_segs(L, bs);
@@ -136,11 +139,11 @@ void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out
         if (!nb) return;
         count_launch();
         switch (v) {
-            case 0: k_half_sweep_int<T, KIND, HM, false, 256, 1><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-            case 1: k_half_sweep_int<T, KIND, HM, false, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-            case 2: k_half_sweep_int<T, KIND, HM, false, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-            case 3: k_half_sweep_int<T, KIND, HM, false, 256, 4><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
-            default: k_half_sweep_int<T, KIND, HM, false, 128, 8><<<nb, 128, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+            case 0: k_half_sweep_int<T, KIND, HM, MH, 256, 1><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+            case 1: k_half_sweep_int<T, KIND, HM, MH, 256, 2><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+            case 2: k_half_sweep_int<T, KIND, HM, MH, 256, 3><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+            case 3: k_half_sweep_int<T, KIND, HM, MH, 256, 4><<<nb, 256, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
+            default: k_half_sweep_int<T, KIND, HM, MH, 128, 8><<<nb, 128, 0, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg); break;
         }
     }
 }
@@ -151,14 +154,17 @@ static void dispatch_sweep(int v, size_t np, const Lv<T>& L, const T* u_in, T* u
                            const NullInfo& nfv, const double* lam, cudaStream_t s) {
     if constexpr (sizeof(T) == 8) {
         // FP64 levels of general moduli always carry the divergence
-        if (L.K == 2) sweep_int_variant<T, 2, false, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-        else sweep_int_variant<T, 21, true, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        if (L.K == 2) sweep_int_variant<T, 2, false, kMlDefault>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        else sweep_int_variant<T, 21, true, kMlDefault>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
     } else if (L.modh) {
-        if (L.K == 2) sweep_int_variant<T, 2, false, true>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-        else sweep_int_variant<T, 21, false, true>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        if (L.K == 2) sweep_int_variant<T, 2, false, kMlHalf>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        else sweep_int_variant<T, 21, false, kMlHalf>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+    } else if (L.K == 21 && L.mlay == kModSplit) {
+        // colour-split records with the divergence: centre moduli only
+        sweep_int_variant<T, 21, true, kMlSplit>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
     } else {
-        if (L.K == 2) sweep_int_variant<T, 2, false, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
-        else sweep_int_variant<T, 21, false, false>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        if (L.K == 2) sweep_int_variant<T, 2, false, kMlDefault>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
+        else sweep_int_variant<T, 21, false, kMlDefault>(v, np, L, u_in, u_out, f, colour, nfv, lam, s);
     }
 }
 

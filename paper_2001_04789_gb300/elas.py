@@ -24,6 +24,8 @@ ERR_DIVERGED = -4
 ERR_STATE = -7
 HOST, DEVICE = 0, 1
 FP64, MIXED = 0, 1
+SMOOTH_RB, SMOOTH_GS8, SMOOTH_JACOBI = 0, 1, 2
+CYCLE_V, CYCLE_F = 0, 1
 HISTORY = 128
 
 
@@ -47,7 +49,8 @@ class AmrLevelDesc(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("rel_tol", C.c_double), ("max_cycles", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("warm_start", C.c_int),
-                ("fixed_cycles", C.c_int), ("use_graph", C.c_int), ("inner_cycles", C.c_int)]
+                ("fixed_cycles", C.c_int), ("use_graph", C.c_int), ("inner_cycles", C.c_int),
+                ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -108,6 +111,7 @@ def lib():
         "elas_op_residual": (ip, [vp, ip, ip, vp, vp, vp, dp]),
         "elas_op_residual_noalloc": (ip, [vp, ip, ip, vp, vp, vp, dp]),
         "elas_op_sweep": (ip, [vp, ip, ip, vp, vp]),
+        "elas_op_smooth": (ip, [vp, ip, ip, ip, C.c_double, vp, vp]),
         "elas_op_restrict": (ip, [vp, ip, ip, vp, vp]),
         "elas_op_prolong_add": (ip, [vp, ip, ip, vp, vp]),
         "elas_op_rhs": (ip, [vp, vp]),
@@ -313,8 +317,10 @@ class Grid:
 
     # -- solve -------------------------------------------------------------------
     def solve(self, precision=FP64, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False,
-              fixed_cycles=0, use_graph=False, raise_on_error=True, inner_cycles=1):
-        o = _opts(precision, rel_tol, max_cycles, nu1, nu2, warm_start, fixed_cycles, use_graph, inner_cycles)
+              fixed_cycles=0, use_graph=False, raise_on_error=True, inner_cycles=1, smoother=None, cycle=None,
+              omega=None):
+        o = _opts(precision, rel_tol, max_cycles, nu1, nu2, warm_start, fixed_cycles, use_graph, inner_cycles,
+                  smoother, cycle, omega)
         info = SolveInfo()
         rc = lib().elas_solve(self.h, C.byref(o), C.byref(info))
         if rc != OK and raise_on_error and rc not in (ERR_NOT_CONVERGED,):
@@ -377,6 +383,12 @@ class Grid:
     def op_sweep(self, level, precision, u, f):
         self.ctx.after_current(u, f)
         self.ctx.check(lib().elas_op_sweep(self.h, level, precision, _ptr(u), _ptr(f)))
+        return u
+
+    def op_smooth(self, level, precision, smoother, u, f, omega=2.0 / 3.0):
+        """One sweep of the given smoother (SMOOTH_RB, SMOOTH_GS8, SMOOTH_JACOBI), in place."""
+        self.ctx.after_current(u, f)
+        self.ctx.check(lib().elas_op_smooth(self.h, level, precision, smoother, omega, _ptr(u), _ptr(f)))
         return u
 
     def op_restrict(self, level, precision, r):
@@ -473,13 +485,19 @@ def grid_from_problem(ctx: Context, p: M.Problem, mixed=False, max_levels=0, hal
 
 
 def _opts(precision=FP64, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False, fixed_cycles=0,
-          use_graph=False, inner_cycles=1):
+          use_graph=False, inner_cycles=1, smoother=None, cycle=None, omega=None):
     o = SolveOpts()
     lib().elas_solve_opts_default(C.byref(o))
     o.precision, o.rel_tol, o.max_cycles = precision, rel_tol, max_cycles
     o.nu1, o.nu2, o.warm_start, o.fixed_cycles = nu1, nu2, int(warm_start), fixed_cycles
     o.use_graph = int(use_graph)
     o.inner_cycles = int(inner_cycles)
+    if smoother is not None:
+        o.smoother = int(smoother)
+    if cycle is not None:
+        o.cycle = int(cycle)
+    if omega is not None:
+        o.omega = float(omega)
     return o
 
 

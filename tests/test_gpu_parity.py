@@ -295,11 +295,15 @@ def test_half_moduli_v_cycle_reaches_the_oracle_solution(E, ctx, case):
 
 
 def force_variant(E, p, v):
-    """Tuning-table entries that pin interior smoother shape v on every FP32 level."""
+    """Tuning-table entries that pin interior smoother shape v on every FP32 level (keys
+    of blocked and of colour-split moduli; a shape that does not apply to a level falls
+    back to shape 0 there)."""
     n = list(p.n)
     lines = []
     for _ in range(12):
-        lines.append(f"{n[0]} {n[1]} {n[2]} {21 if p.moduli_kind == M.MODULI_GEN21 else 2} 4 0 {v}")
+        k = 21 if p.moduli_kind == M.MODULI_GEN21 else 2
+        lines.append(f"{n[0]} {n[1]} {n[2]} {k} 4 0 {v}")
+        lines.append(f"{n[0]} {n[1]} {n[2]} {k} 4 2 {v}")
         if min(n) < 5:
             break
         n = [(m - 1) // 2 + 1 if not per else m // 2 for m, per in zip(n, p.periodic)]

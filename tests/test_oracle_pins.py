@@ -615,3 +615,112 @@ def test_periodic_laminate_homogenised_traction():
     sig_x = np.einsum("ikl,kl...->i...", C0[:, 0], eps) * scale[None]
     t_num = sig_x.mean(axis=(1, 2, 3))
     assert np.allclose(t_num, t_exact, rtol=2e-3, atol=2e-3 * np.abs(t_exact).max()), (t_num, t_exact)
+
+
+# --------------------------------------------------------------------------
+# the paper's own cycle: eight-colour Gauss-Seidel, damped Jacobi, F-cycles
+# --------------------------------------------------------------------------
+
+def _periodic_varied(n=8, seed=2):
+    rng = np.random.default_rng(seed)
+    p = make_problem((n, n, n), M.MODULI_GEN21, C_tensor=random_general_C(rng), periodic=(True, True, True))
+    X, Y, Z = p.coords()
+    p.moduli = p.moduli * (1.0 + 0.3 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * (Y + Z)))[None]
+    p.bc = []
+    return p
+
+
+def test_eight_colour_sweep_is_block_gauss_seidel_in_colour_order():
+    """On a periodic grid of even size no two nodes of one colour share a stencil, so
+    one eight-colour sweep must equal block Gauss-Seidel in colour order, written as
+    x_new = (D + L)^-1 (f - U x_old) with D, L, U from the assembled matrix permuted
+    colour by colour."""
+    p = _periodic_varied()
+    L = MG.build_hierarchy(S.level_from_problem(p))[0]
+    free, A = MG.assemble_dense(L.level, L.types)
+    assert free.all()
+    rng = np.random.default_rng(3)
+    u = rng.normal(size=(3,) + L.level.shape)
+    f = rng.normal(size=(3,) + L.level.shape) * 50
+    c8 = np.broadcast_to(MG.colour8(L.level.shape)[None], u.shape).reshape(-1)
+    order = np.argsort(c8, kind="stable")
+    Ap = A[np.ix_(order, order)]
+    cp = c8[order]
+    lower = cp[:, None] > cp[None, :]
+    same = cp[:, None] == cp[None, :]
+    DL = np.where(lower | same, Ap, 0.0)
+    U = np.where(~(lower | same), Ap, 0.0)
+    x_old = u.reshape(-1)[order]
+    x_new = np.linalg.solve(DL, f.reshape(-1)[order] - U @ x_old)
+    expect = np.empty_like(x_new)
+    expect[order] = x_new
+    MG.sweep(L, u, f, MG.Smoother("gs8"))
+    assert np.allclose(u.reshape(-1), expect, rtol=0, atol=1e-11 * np.abs(expect).max())
+
+
+def test_jacobi_sweep_is_damped_block_splitting():
+    """One damped Jacobi sweep equals u + omega D^-1 (f - A u) with D the 3x3 node
+    blocks of the assembled matrix (Dirichlet rows included as identity)."""
+    p = make_problem((5, 4, 5), M.MODULI_GEN21, C_tensor=random_general_C(np.random.default_rng(4)),
+                     bc=[[(M.TRACTION, 0.0)] * 3 if f_ != 4 else [(M.DIRICHLET, 0.0)] * 3 for f_ in range(6)])
+    L = MG.build_hierarchy(S.level_from_problem(p))[0]
+    n = L.level.shape
+    N = n[0] * n[1] * n[2]
+    A = np.zeros((3 * N, 3 * N))
+    for col in range(3 * N):
+        e = np.zeros(3 * N)
+        e[col] = 1.0
+        A[:, col] = S.apply(L.level, e.reshape((3,) + n), L.types).reshape(-1)
+    rng = np.random.default_rng(6)
+    u = rng.normal(size=(3,) + n)
+    f = rng.normal(size=(3,) + n)
+    f = np.where(L.types == M.DIRICHLET, 0.0, f)
+    omega = 0.6
+    r = np.where(L.types.reshape(-1) == M.DIRICHLET, 0.0, f.reshape(-1) - A @ u.reshape(-1))
+    expect = u.reshape(-1).copy()
+    for q in range(N):
+        idx = [q, N + q, 2 * N + q]
+        expect[idx] += omega * np.linalg.solve(A[np.ix_(idx, idx)], r[idx])
+    MG.sweep(L, u, f, MG.Smoother("jacobi", omega))
+    assert np.allclose(u.reshape(-1), expect, rtol=0, atol=1e-12 * np.abs(expect).max())
+
+
+def test_f_cycle_is_its_definition_on_three_levels():
+    """With three levels the F-cycle's correction of level 1 is V(1) from zero, then V(1)
+    from that result (the level-1 F-cycle ends in the exact coarsest solve); written
+    out with the V-cycle, one F-cycle must give the same field."""
+    p = M.polycrystal(17, grains=4, seed=7)
+    levels = MG.build_hierarchy(S.level_from_problem(p))
+    assert len(levels) == 3
+    L0, L1 = levels[0], levels[1]
+    rng = np.random.default_rng(8)
+    f = np.where(L0.types == M.DIRICHLET, 0.0, rng.normal(size=(3,) + L0.level.shape))
+    uF = np.zeros_like(f)
+    MG.vcycle(levels, 0, uF, f, 2, 2, MG.RB, "F")
+    u = np.zeros_like(f)
+    for _ in range(2):
+        MG.sweep(L0, u, f)
+    r = S.residual(L0.level, u, f, L0.types)
+    fc = np.where(L1.types == M.DIRICHLET, 0.0, MG.restrict(r, L0.level))
+    e = np.zeros_like(fc)
+    MG.vcycle(levels, 1, e, fc, 2, 2)
+    MG.vcycle(levels, 1, e, fc, 2, 2)
+    u += np.where(L0.types == M.DIRICHLET, 0.0, MG.prolong(e, L0.level))
+    for _ in range(2):
+        MG.sweep(L0, u, f)
+    assert np.allclose(uF, u, rtol=0, atol=1e-14 * np.abs(u).max())
+
+
+@pytest.mark.parametrize("sm,cycle,nu", [("gs8", "V", 2), ("jacobi", "F", 4), ("rb", "F", 2)])
+def test_other_smoothers_and_cycles_reach_the_dense_solution(sm, cycle, nu):
+    p = M.eshelby_sphere(9)
+    levels = MG.build_hierarchy(S.level_from_problem(p))
+    L = levels[0]
+    free, A = MG.assemble_dense(L.level, L.types)
+    f = S.rhs(L.level, p)
+    u_ref = np.zeros_like(f)
+    u_ref[free] = np.linalg.solve(A, f[free])
+    u, info = MG.solve(p, tol=1e-13, max_cycles=200, nu1=nu, nu2=nu, levels=levels,
+                       smoother=MG.Smoother(sm), cycle=cycle)
+    assert info.converged
+    assert np.abs(u - u_ref).max() <= 1e-10 * np.abs(u_ref).max()
