@@ -197,6 +197,13 @@ int  elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info)
  * periodic grid with mean strain). */
 int  elas_get_displacement(elas_grid g, double* out, int memspace);
 int  elas_set_displacement(elas_grid g, const double* in, int memspace);
+/* Stress of the current displacement of the finest level (the stress of Eq. 1c):
+ * sigma = C : (grad u + E - eps0), E the mean strain of a periodic grid (else 0), eps0 the
+ * eigenstrain (if set); first derivatives central, one-sided second order on the
+ * boundary planes of a non-periodic direction.  out: 6 x N doubles, tensor components
+ * 11, 22, 33, 23, 31, 12 (HOST or DEVICE per memspace; a HOST call allocates and frees a
+ * 6 x N device buffer through the context's allocator). */
+int  elas_get_stress(elas_grid g, double* out, int memspace);
 /* FP64 residual of the current displacement: ||r||_2 / ||r_0||_2 and ||r||_2. */
 int  elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2);
 

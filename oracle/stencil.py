@@ -10,7 +10,9 @@ Test infrastructure (see the package docstring).  Follows Section 2.1:
 * the product-rule split of Section 2.1.1:
   D(u)_i = C_ijkl,j (u_k,l - eps0_kl) + C_ijkl (u_k,lj - eps0_kl,j);
 * the homogeneous / inhomogeneous split D_H(u) = D(u) - D(0), with the solution
-  of D_H(u) = -(D(0) + b) (Section 2.1.1).
+  of D_H(u) = -(D(0) + b) (Section 2.1.1);
+* the stress output sigma = C (grad u - eps0) of Eq. (1c), with the operator's first
+  differences.
 
 Readings where the paper is silent (each is listed in the design notes):
 
@@ -431,3 +433,35 @@ def block_diagonal(level: Level, types=None):
             B[i, k] = np.where(types[i] == NEUMANN, ne[i, k], B[i, k])
             B[i, k] = np.where(types[i] == DIRICHLET, 1.0 if i == k else 0.0, B[i, k])
     return B
+
+
+# --------------------------------------------------------------------------
+# stress (output)
+# --------------------------------------------------------------------------
+
+def stress(level: Level, u, eps0=None, ebar=None):
+    """Stress sigma = C : (grad u + ebar - eps0) at every node, the quantity whose normal
+    component the traction condition Eq. (1c) prescribes.  Returns the six tensor
+    components 11, 22, 33, 23, 31, 12 (shape (6, nz, ny, nx)).
+
+    grad u uses the operator's first derivatives: central, one-sided second order on
+    the boundary planes of a non-periodic direction.  ebar is the mean strain of a
+    periodic cell (u is then the fluctuation u~ of u = ebar x + u~), eps0 the
+    eigenstrain field (6 tensor components), both optional."""
+    sh = level.shape
+    g = [[grad_boundary(u[k], l, level) for l in range(3)] for k in range(3)]
+    eps = np.zeros((6,) + sh)
+    for a, (k, l) in enumerate(((0, 0), (1, 1), (2, 2), (1, 2), (2, 0), (0, 1))):
+        eps[a] = 0.5 * (g[k][l] + g[l][k])
+        if ebar is not None:
+            eps[a] += ebar[a]
+        if eps0 is not None:
+            eps[a] -= eps0[a]
+    out = np.zeros((6,) + sh)
+    for a, (i, j) in enumerate(((0, 0), (1, 1), (2, 2), (1, 2), (2, 0), (0, 1))):
+        for k, l in itertools.product(range(3), repeat=2):
+            C = modulus(level, i, j, k, l)
+            if C is None:
+                continue
+            out[a] += C * eps[VOIGT[k][l]]
+    return out

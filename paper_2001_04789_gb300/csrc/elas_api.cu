@@ -1108,6 +1108,33 @@ int elas_get_displacement(elas_grid g, double* out, int memspace) {
     return ELAS_OK;
 }
 
+int elas_get_stress(elas_grid g, double* out, int memspace) {
+    if (!g || !out) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = g->ctx;
+    cudaSetDevice(c->device);
+    if (!g->moduli_set) return set_err(c, ELAS_ERR_STATE, "moduli not set");
+    Level& L0 = g->lv[0];
+    const size_t count = (size_t)6 * L0.N;
+    double* dst = (double*)out;
+    void* tmp = nullptr;
+    if (memspace == ELAS_HOST) {
+        tmp = ctx_alloc(c, sizeof(double) * count);
+        if (!tmp) return set_err(c, ELAS_ERR_ALLOC, "stress output buffer: allocation failed");
+        dst = (double*)tmp;
+    }
+    MeanStrain ms{};
+    if (g->has_mean)
+        for (int k = 0; k < 6; ++k) ms.e[k] = g->mean[k];
+    launch_stress(L0.L64, L0.u, g->eps0, ms, dst, c->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && tmp)
+        e = cudaMemcpyAsync(out, tmp, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (tmp) ctx_free(c, tmp, sizeof(double) * count);
+    if (e != cudaSuccess) return set_err(c, ELAS_ERR_DEVICE, std::string("stress: ") + cudaGetErrorString(e));
+    return ELAS_OK;
+}
+
 int elas_set_displacement(elas_grid g, const double* in, int memspace) {
     if (!g || !in) return ELAS_ERR_INVALID_ARG;
     return copy_in(g->ctx, g->lv[0].u, in, (size_t)3 * g->lv[0].N, memspace);

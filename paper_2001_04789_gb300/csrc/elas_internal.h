@@ -33,7 +33,7 @@ void count_launch(int n = 1);
 
 // Interior smoother launch variants (block size, minimum blocks per SM) and the
 // autotuner that picks one per level shape and precision.
-constexpr int kNumSweepVariants = 7;
+constexpr int kNumSweepVariants = 9;
 constexpr int kDefaultSweepVariant = 0;
 template <typename T>
 int tune_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, cudaStream_t s, float* ms_out);
@@ -127,6 +127,14 @@ void launch_sum_partials(const double* partials, int nblocks, int width, double*
 // u -= t + w x d on the non-Dirichlet rows.
 void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* Ginv, const double* moment,
                         double* motion, double* u, cudaStream_t s);
+
+// Stress sigma = C : (grad u + mean - eps0) of an FP64 level, 6 x N (11 22 33 23 31 12);
+// eps0 optional (6 x N), mean the mean strain of a periodic cell (zero otherwise).
+struct MeanStrain {
+    double e[6];
+};
+void launch_stress(const Lv<double>& L, const double* u, const double* eps0, const MeanStrain& mean, double* out,
+                   cudaStream_t s);
 
 // ALU peak microbenchmark: one launch of independent FMA chains on every SM (precision 0 =
 // FP64, 1 = FP32); returns the FLOPs of the launch and its device time in *ms.  out: a

@@ -291,6 +291,46 @@ void launch_amr_add(const Lv<double>& L, const AmrBox& b, double* u, const doubl
     k_amr_add<<<blocks_for(L.N), kBlock, 0, s>>>(L, b, u, cor);
 }
 
+// ---- stress output ------------------------------------------------------------------
+// sigma = C : (grad u + ebar - eps0) at every node (Eq. 1c's stress), six tensor
+// components 11 22 33 23 31 12; first derivatives central, one-sided second order on the
+// boundary planes of a non-periodic direction (the operator's own differences).
+template <int KIND>
+__global__ void k_stress(Lv<double> L, const double* __restrict__ u, const double* __restrict__ eps0, MeanStrain mean,
+                         double* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
+    int c[3];
+    coords_of(p, L.n, c);
+    UField<double> uf{u, L.N, L.n[0], L.n[1]};
+    double G[3][3];
+    for (int k = 0; k < 3; ++k) {
+        auto uk = [&](const int a[3]) { return uf.at(k, a); };
+        for (int l = 0; l < 3; ++l) G[k][l] = deriv_c(L, uk, c, l);
+    }
+    double e[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+            const int v = voigt(k, l);
+            e[k][l] = 0.5 * (G[k][l] + G[l][k]) + mean.e[v] - (eps0 ? eps0[(size_t)v * L.N + p] : 0.0);
+        }
+    const int I[6] = {0, 1, 2, 1, 2, 0}, J[6] = {0, 1, 2, 2, 0, 1};
+    for (int a = 0; a < 6; ++a) {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l)
+                if (Cnz<double, KIND>(I[a], J[a], k, l)) s += Cm<double, KIND>(L, p, I[a], J[a], k, l) * e[k][l];
+        out[(size_t)a * L.N + p] = s;
+    }
+}
+
+void launch_stress(const Lv<double>& L, const double* u, const double* eps0, const MeanStrain& mean, double* out,
+                   cudaStream_t s) {
+    count_launch();
+    if (L.K == 2) k_stress<2><<<blocks_for(L.N), kBlock, 0, s>>>(L, u, eps0, mean, out);
+    else k_stress<21><<<blocks_for(L.N), kBlock, 0, s>>>(L, u, eps0, mean, out);
+}
+
 // ---- ALU peak: independent FMA chains ------------------------------------------------
 // Each thread runs kFmaChains independent chains x <- x b + a (b < 1, so the values stay
 // bounded) for iters rounds, unrolled by four; nothing else is issued in the loop but

@@ -785,6 +785,137 @@ __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* _
     sweep_pair_body<T, KIND, HM, ML>(L, u, uo, f, colour, nf, lam, (b - sg.f2) * BS + tid);
 }
 
+// ---- z-marching tiled half-sweep of colour-split FP32 levels ---------------------------
+// A block owns a 32 x TY tile of interior (x, y) nodes and a chunk of interior z planes.
+// Only the displacement is staged: its planes, with a one-node x/y halo, rotate through
+// four shared buffers (cp.async, plane z+2 streaming in while plane z is computed), so
+// each displacement value comes from DRAM once per half-sweep and the 57 stencil reads of
+// a node are shared-memory loads at compile-time offsets.  The moduli and their
+// divergence are the active node's own colour-split records, read once from global
+// memory.  Each warp covers 16 x-pairs of two neighbouring rows (active nodes of
+// opposite x parity: conflict-free shared loads).  The first blocks of the launch take
+// the edge, corner and face nodes, as in k_half_sweep_int.  Same stencil, same order of
+// operations as the untiled kernel: identical bits.
+template <int TY>
+struct SplitTile {
+    static constexpr int R = TY + 2;                   // rows with halo
+    static constexpr int PLANE = R * kTileS;           // one component of one plane
+    static constexpr int UPL = 3 * PLANE;              // floats per displacement plane
+    static constexpr int NT = 16 * TY;
+    static constexpr int NPOS = (PLANE + NT - 1) / NT; // positions per thread
+    static constexpr size_t SMEM = sizeof(float) * 4 * UPL;
+};
+
+template <int TY, int MINB>
+__global__ void __launch_bounds__(16 * TY, MINB)
+    k_half_sweep_tiled_split(Lv<float> L, const float* __restrict__ u, float* __restrict__ uo,
+                             const float* __restrict__ f, int colour, NullInfo nf, const double* __restrict__ lam,
+                             BndSegs sg, int gx, int gy, int zlen) {
+    using S = SplitTile<TY>;
+    constexpr int PLANE = S::PLANE, UPL = S::UPL, NPOS = S::NPOS, NT = S::NT;
+    extern __shared__ __align__(16) float sm[];
+    if (L.active && *L.active == 0) return;
+    const int b = blockIdx.x, tid = threadIdx.x;
+    if (b < sg.f2) {
+        if (b < sg.e) sweep_bnd_body<float, 21>(L, u, uo, f, colour, nf, lam, (b * NT + tid) >> 5, tid & 31);
+        else if (b < sg.f0) sweep_face_body<float, 21, 0>(L, u, uo, f, colour, nf, lam, (b - sg.e) * NT + tid);
+        else if (b < sg.f1) sweep_face_body<float, 21, 1>(L, u, uo, f, colour, nf, lam, (b - sg.f0) * NT + tid);
+        else sweep_face_body<float, 21, 2>(L, u, uo, f, colour, nf, lam, (b - sg.f1) * NT + tid);
+        return;
+    }
+    const int t = b - sg.f2;
+    const int bx = t % gx, by = (t / gx) % gy, bz = t / (gx * gy);
+    int lo[3], cnt[3];
+    interior_box(L, lo, cnt);
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2], N = L.N;
+    const int xt0 = lo[0] + kTileX * bx;
+    const int yt0 = lo[1] + TY * by;
+    const int z0 = lo[2] + zlen * bz;
+    const int zend = min(z0 + zlen, lo[2] + cnt[2]);
+    if (z0 >= zend) return;
+    const int xend = lo[0] + cnt[0], yend = lo[1] + cnt[1];
+
+    // in-plane global offset of each shared position this thread copies, or -1
+    int goff[NPOS];
+#pragma unroll
+    for (int j = 0; j < NPOS; ++j) {
+        const int pos = tid + NT * j;
+        goff[j] = -1;
+        if (pos < PLANE) {
+            int x = xt0 - 1 + pos % kTileS, y = yt0 - 1 + pos / kTileS;
+            if (x <= xend && y <= yend) {
+                if (x < 0) x += nx;
+                if (x >= nx) x -= nx;
+                if (y < 0) y += ny;
+                if (y >= ny) y -= ny;
+                goff[j] = x + nx * y;
+            }
+        }
+    }
+    auto load_plane = [&](int z, int j) {
+        if (z < 0) z += nz;
+        if (z >= nz) z -= nz;
+        const int zb = z * nx * ny;
+        float* ud = sm + (j & 3) * UPL;
+#pragma unroll
+        for (int q = 0; q < NPOS; ++q) {
+            if (goff[q] < 0) continue;
+            const int pos = tid + NT * q;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cp_async4(ud + k * PLANE + pos, u + (size_t)k * N + zb + goff[q]);
+        }
+        cp_async_commit();
+    };
+
+    const int tx = tid & 15, ty = tid >> 4;
+    const int y = yt0 + ty;
+    const int x0 = xt0 + 2 * tx;
+    const int yl = ty + 1;
+    load_plane(z0 - 1, 0);
+    load_plane(z0, 1);
+    load_plane(z0 + 1, 2);
+    for (int z = z0; z < zend; ++z) {
+        const int j = z - z0 + 1;          // ring slot of plane z
+        cp_async_wait_all();
+        __syncthreads();
+        if (z + 2 <= zend) load_plane(z + 2, j + 2);   // into the slot of plane z - 2
+        const int xa = x0 + ((x0 + y + z + colour) & 1);
+        const int xi = (xa == x0) ? x0 + 1 : x0;
+        const int xla = xa - xt0 + 1, xli = xi - xt0 + 1;
+        const float* const Um = sm + ((j + 3) & 3) * UPL + yl * kTileS + xla;
+        const float* const U0 = sm + (j & 3) * UPL + yl * kTileS;
+        const float* const Up = sm + ((j + 1) & 3) * UPL + yl * kTileS + xla;
+        const int row = nx * (y + ny * z);
+        if (y < yend && xi < xend) {
+            const int q = xi + row;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) uo[(size_t)k * N + q] = U0[k * PLANE + xli];
+        }
+        if (y < yend && xa < xend) {
+            const int p = xa + row;
+            const float* cb = L.mod + (p & 1) * L.msplit1 + (size_t)((p >> 1) >> 5) * (32 * kSplitK) + ((p >> 1) & 31);
+            auto ua = [&](int k, int dx, int dy, int dz) -> float {
+                const float* bp = dz < 0 ? Um : (dz > 0 ? Up : U0 + xla);
+                return bp[k * PLANE + dy * kTileS + dx];
+            };
+            auto ca = [&](int c, int, int, int) -> float { return __ldg(cb + 32 * c); };
+            float v[3];
+            interior_rows_core<float, 21, true>(L, ua, ca, p, v);
+            float r[3], B[3][3], d[3];
+            const int c3[3] = {xa, y, z};
+            for (int i = 0; i < 3; ++i) {
+                float fi = f[(size_t)i * N + p];
+                if (lam) fi = xsub(fi, rigid_load<float>(nf, lam, i, c3));
+                r[i] = xsub(fi, v[i]);
+            }
+            interior_block_acc<float, 21>(L, ca, B);
+            solve3(B, r, d);
+            for (int i = 0; i < 3; ++i) uo[(size_t)i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
+        }
+    }
+    cp_async_wait_all();
+}
+
 // r = f - load - A u on every node; block partials of sum r^2 and the rigid moments.
 // Resident blocks per SM: two for FP64 (at most 128 registers; the FP64 instance is bound
 // by the FP64 pipe and needs the warps to keep it busy, one block at 180 registers ran

@@ -12,10 +12,13 @@ namespace elas {
 // (threads per block, minimum resident blocks per SM) pairs; the second number
 // bounds the registers per thread and so trades registers for resident warps.
 // Variants 5 and 6 are the shared-memory tiled kernel (32 x 16 and 32 x 8 tiles, FP32
-// levels with FP32 moduli only); their pair holds (threads, resident blocks per SM).
+// levels with blocked FP32 moduli only); 7 and 8 the z-marching tiled kernel of
+// colour-split levels (32 x 16 and 32 x 8 tiles, displacement staged); their pair holds
+// (threads, resident blocks per SM).
 static const int kSweepVariants[kNumSweepVariants][2] = {{256, 1}, {256, 2}, {256, 3}, {256, 4}, {128, 8},
-                                                         {256, 1}, {128, 2}};
+                                                         {256, 1}, {128, 2}, {256, 2}, {128, 4}};
 constexpr int kFirstTiledVariant = 5;
+constexpr int kFirstSplitTiledVariant = 7;
 
 // Tuning key: level dimensions, moduli kind, precision and the moduli source (1: FP64
 // levels with the precomputed divergence, 2: FP32 colour-split records, 0: otherwise).
@@ -81,12 +84,29 @@ void launch_tiled(const Lv<float>& L, const float* u_in, float* u_out, const flo
     k_half_sweep_tiled<KIND, TY><<<grid, 16 * TY, S::SMEM, s>>>(L, u_in, u_out, f, colour, nfv, lam, zl);
 }
 
+template <int TY, int MINB>
+void launch_tiled_split(const Lv<float>& L, const float* u_in, float* u_out, const float* f, int colour,
+                        const NullInfo& nfv, const double* lam, cudaStream_t s) {
+    using S = SplitTile<TY>;
+    int cnt[3];
+    for (int d = 0; d < 3; ++d) cnt[d] = L.per[d] ? L.n[d] : L.n[d] - 2;
+    const int gx = (cnt[0] + kTileX - 1) / kTileX, gy = (cnt[1] + TY - 1) / TY;
+    const int zl = cnt[2] > 0 ? tiled_zlen(gx * gy, cnt[2], MINB) : 1;
+    const int gz = cnt[2] > 0 ? (cnt[2] + zl - 1) / zl : 0;
+    const BndSegs sg = bnd_segs(L, S::NT);
+    const int nb = sg.f2 + gx * gy * gz;
+    if (!nb) return;
+    count_launch();
+    k_half_sweep_tiled_split<TY, MINB><<<nb, S::NT, S::SMEM, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg, gx, gy, zl);
+}
+
 // The tiled kernel reads the blocked FP32 moduli copy directly: not for FP64 levels or
 // FP16 moduli.
 template <typename T>
 static bool variant_ok(const Lv<T>& L, int v) {
     if (sizeof(T) == 4 && L.modh) return v == 1 || v == 2;   // FP16 records: two shapes
-    if (sizeof(T) == 4 && L.mlay == kModSplit) return v < kFirstTiledVariant;   // untiled shapes
+    if (sizeof(T) == 4 && L.mlay == kModSplit) return v < kFirstTiledVariant || v >= kFirstSplitTiledVariant;
+    if (v >= kFirstSplitTiledVariant) return false;
     if (v < kFirstTiledVariant) return true;
     return sizeof(T) == 4 && L.mlay == kModBlocked && !L.divc;
 }
@@ -119,6 +139,13 @@ void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out
                 else launch_tiled<KIND, 8>(L, u_in, u_out, f, colour, nfv, lam, s);
             }
             launch_boundary_sweep(L, u_in, u_out, f, colour, nfv, lam, s);
+            return;
+        }
+    }
+    if constexpr (sizeof(T) == 4 && MH == kMlSplit) {
+        if (v >= kFirstSplitTiledVariant && variant_ok(L, v) && colour < 2) {   // red-black only
+            if (v == kFirstSplitTiledVariant) launch_tiled_split<16, 2>(L, u_in, u_out, f, colour, nfv, lam, s);
+            else launch_tiled_split<8, 4>(L, u_in, u_out, f, colour, nfv, lam, s);
             return;
         }
     }

@@ -106,6 +106,7 @@ def lib():
         "elas_solve": (ip, [vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "elas_get_displacement": (ip, [vp, vp, ip]),
         "elas_set_displacement": (ip, [vp, vp, ip]),
+        "elas_get_stress": (ip, [vp, vp, ip]),
         "elas_query_residual": (ip, [vp, dp, dp]),
         "elas_op_apply": (ip, [vp, ip, ip, vp, vp]),
         "elas_op_residual": (ip, [vp, ip, ip, vp, vp, vp, dp]),
@@ -336,6 +337,12 @@ class Grid:
         a = self._host(u, 3 * self.N)
         self.ctx.check(lib().elas_set_displacement(self.h, _ptr(a), HOST))
 
+    def stress(self):
+        """Stress of the current displacement, (6, nz, ny, nx): 11, 22, 33, 23, 31, 12."""
+        out = np.empty((6,) + self.shape)
+        self.ctx.check(lib().elas_get_stress(self.h, _ptr(out), HOST))
+        return out
+
     def query_residual(self):
         rel, ab = C.c_double(), C.c_double()
         self.ctx.check(lib().elas_query_residual(self.h, C.byref(rel), C.byref(ab)))
@@ -429,11 +436,14 @@ class Grid:
 
 
 # interior smoother launch shapes: 0-4 untiled (threads, min blocks per SM) = (256,1),
-# (256,2), (256,3), (256,4), (128,8); 5-6 shared-memory tiled, 32x16 and 32x8 tiles.
+# (256,2), (256,3), (256,4), (128,8); 5-6 shared-memory tiled, 32x16 and 32x8 tiles
+# (blocked FP32 moduli); 7-8 z-marching tiled with staged displacement, 32x16 and 32x8
+# tiles (colour-split FP32 moduli).
 # Levels with FP16 moduli use shapes 1 and 2 only (the others report -1 when tuned).
-NUM_SWEEP_VARIANTS = 7
+NUM_SWEEP_VARIANTS = 9
 UNTILED_VARIANTS = tuple(range(5))
 TILED_VARIANTS = (5, 6)
+SPLIT_TILED_VARIANTS = (7, 8)
 
 
 def autotune_dump():

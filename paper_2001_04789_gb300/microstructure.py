@@ -178,6 +178,33 @@ def eshelby_sphere(n=33, radius=0.2, width_cells=3.0, E_matrix=1.0, E_incl=2.0, 
     return p
 
 
+def eshelby_ellipsoid(n=129, half_width=4.0, axes=(1.0, 0.75, 0.5), E=210.0, nu=0.3, eps_star=1e-3,
+                      width=0.1):
+    """Ellipsoidal Eshelby inclusion of Section 4.1: an 8 x 8 x 8 box (half width 4) with
+    u = 0 on all faces, homogeneous moduli E = 210, nu = 0.3, and the dilatational
+    eigenstrain eps_star I inside the ellipsoid with semi-axes (1, 0.75, 0.5), blended by
+    the error-function profile of width 0.1.  The indicator as printed is garbled; the
+    reading taken: eta = 1 inside, A = diag(a_i^-2) and the argument
+    (x^T A x - 1) / (2 width |A x|), so that eta = 1/2 on the sharp ellipsoid."""
+    from scipy.special import erf
+    p = Problem(n=(n, n, n), lo=(-half_width,) * 3, hi=(half_width,) * 3, name=f"eshelby_ellipsoid_{n}")
+    X, Y, Z = p.coords()
+    a = np.asarray(axes, dtype=float)
+    q = (X / a[0]) ** 2 + (Y / a[1]) ** 2 + (Z / a[2]) ** 2
+    ax = np.sqrt((X / a[0] ** 2) ** 2 + (Y / a[1] ** 2) ** 2 + (Z / a[2] ** 2) ** 2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        arg = np.where(ax > 0, (q - 1.0) / (2.0 * width * np.maximum(ax, 1e-300)), -np.inf)
+    eta = 0.5 * (1.0 - erf(arg))
+    lam, mu = lame(np.full(X.shape, E), nu)
+    p.moduli_kind = MODULI_ISO
+    p.moduli = np.stack([lam, mu])
+    eps = np.zeros((6,) + X.shape)
+    eps[0] = eps[1] = eps[2] = eps_star * eta
+    p.eigenstrain = eps
+    p.bc = all_faces(DIRICHLET, 0.0)
+    return p
+
+
 def polycrystal(n=257, grains=20, seed=0, c11=1.68, c12=1.21, c44=0.75, width_cells=4.0,
                 strain=1e-3):
     """Voronoi polycrystal (Section 4.3 analogue): rotated cubic grains blended by the

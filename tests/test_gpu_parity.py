@@ -316,6 +316,8 @@ TILE_CASES = {
     "iso_ragged": lambda: mixed_bc_problem(n=(41, 19, 13), kind=M.MODULI_ISO),
     "periodic_iso": lambda: periodic_problem(32),
     "polycrystal": lambda: M.polycrystal(33, grains=5, seed=2),
+    # odd nx, ny: colour-split moduli; interior 67 x 35 x 21 (ragged tiles, z chunks)
+    "split_ragged": lambda: mixed_bc_problem(n=(69, 37, 23), kind=M.MODULI_GEN21),
 }
 
 
@@ -347,11 +349,11 @@ def test_tiled_smoother_mixed_solve_matches(E, ctx, case):
     p = TILE_CASES[case]()
     g = E.grid_from_problem(ctx, p, mixed=True)
     hist = {}
-    for v in (0,) + E.TILED_VARIANTS:
+    for v in (0,) + E.TILED_VARIANTS + E.SPLIT_TILED_VARIANTS:
         force_variant(E, p, v)
         info = g.solve(precision=E.MIXED, rel_tol=0.0, fixed_cycles=4, inner_cycles=2)
         hist[v] = (info["rel_history"], g.displacement())
-    for v in E.TILED_VARIANTS:
+    for v in E.TILED_VARIANTS + E.SPLIT_TILED_VARIANTS:
         assert hist[v][0] == hist[0][0]
         assert np.array_equal(hist[v][1], hist[0][1])
     force_variant(E, p, 0)

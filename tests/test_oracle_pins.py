@@ -724,3 +724,103 @@ def test_other_smoothers_and_cycles_reach_the_dense_solution(sm, cycle, nu):
                        smoother=MG.Smoother(sm), cycle=cycle)
     assert info.converged
     assert np.abs(u - u_ref).max() <= 1e-10 * np.abs(u_ref).max()
+
+
+# --------------------------------------------------------------------------
+# stress output
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", [M.MODULI_ISO, M.MODULI_GEN21])
+def test_stress_exact_for_quadratic_u_affine_moduli_and_eigenstrain(kind):
+    """Central and one-sided second-order first differences are exact on quadratics, so
+    the stress output equals C(x) : (grad u - eps0) evaluated analytically, on every
+    node including faces, edges and corners."""
+    rng = np.random.default_rng(21)
+    p = M.Problem(n=(6, 5, 7), lo=(0.1, -0.2, 0.3), hi=(1.0, 0.6, 1.4))
+    X, Y, Z = p.coords()
+    u, grad, _ = quadratic_field(rng, X, Y, Z)
+    e0 = rng.normal(size=6) * 1e-3
+    eps0 = np.zeros((6,) + X.shape)
+    for a in range(6):
+        eps0[a] = e0[a] * (1 + 0.5 * X - 0.3 * Z)
+    if kind == M.MODULI_ISO:
+        lam = 1.0 + 0.2 * X + 0.1 * Y
+        mu = 0.7 - 0.1 * Z + 0.05 * X
+        p.moduli_kind = M.MODULI_ISO
+        p.moduli = np.stack([lam, mu])
+        T = iso_tensor(lam, mu)
+    else:
+        T0 = random_general_C(rng)
+        w = 1.0 + 0.3 * X - 0.2 * Y + 0.1 * Z
+        p.moduli_kind = M.MODULI_GEN21
+        p.moduli = M.tensor_to_upper21(T0)[:, None, None, None] * w[None]
+        T = T0[..., None, None, None] * w
+    p.bc = M.all_faces(M.TRACTION, 0.0)
+    lev = S.level_from_problem(p)
+    got = S.stress(lev, u, eps0=eps0)
+    E0 = np.zeros((3, 3) + X.shape)
+    for a, (k, l) in enumerate(((0, 0), (1, 1), (2, 2), (1, 2), (2, 0), (0, 1))):
+        E0[k, l] = E0[l, k] = eps0[a]
+    strain = 0.5 * (grad + np.swapaxes(grad, 0, 1)) - E0
+    sig = np.einsum("ijkl...,kl...->ij...", T, strain)
+    expect = np.stack([sig[0, 0], sig[1, 1], sig[2, 2], sig[1, 2], sig[2, 0], sig[0, 1]])
+    assert np.allclose(got, expect, rtol=0, atol=1e-11 * np.abs(expect).max())
+
+
+def test_stress_inside_eshelby_sphere_converges_to_closed_form():
+    """Inside a spherical inhomogeneity with a dilatational eigenstrain the strain is
+    uniform, A I with A = 3 K_i eps* / (3 K_i + 4 mu_m), and the stress hydrostatic,
+    3 K_i (A - eps*) I (Eshelby's solution); with the closed form as Dirichlet data the
+    stress near the centre approaches it as the grid and interface width shrink."""
+    errs = []
+    for n in (17, 33):
+        p = M.eshelby_sphere(n, radius=0.2)
+        X, Y, Z = p.coords()
+        ue, r = eshelby_sphere_closed_form(X, Y, Z, 0.2, 1e-3, 2.0, 1.0, 0.3)
+        p.dirichlet_values = ue
+        u, info = MG.solve(p, tol=1e-11, max_cycles=80)
+        lev = S.level_from_problem(p)
+        sig = S.stress(lev, u, eps0=p.eigenstrain)
+        lam_i, mu_i = M.lame(2.0, 0.3)
+        _, mu_m = M.lame(1.0, 0.3)
+        K_i = lam_i + 2.0 * mu_i / 3.0
+        A = 3 * K_i * 1e-3 / (3 * K_i + 4 * mu_m)
+        s_exact = 3 * K_i * (A - 1e-3)
+        core = r <= 0.08
+        errs.append(max(np.abs(sig[a][core] - s_exact).max() for a in range(3)) / abs(s_exact))
+        assert max(np.abs(sig[a][core]).max() for a in range(3, 6)) < 0.05 * abs(s_exact)
+    # first order in h (the interface is 3h wide on a sphere of radius 3.2 - 6.4 h); a
+    # dropped or sign-flipped eigenstrain would be off by the whole stress
+    assert errs[1] < 0.6 * errs[0] and errs[1] < 0.25, errs
+
+
+def test_eshelby_tensor_helper_sphere_limit_and_identities():
+    """The ellipsoid closed form used to validate the stress: its sphere limit is
+    S_1111 = (7 - 5 nu) / (15 (1 - nu)), S_1122 = (5 nu - 1) / (15 (1 - nu)), and the
+    integrals satisfy I_1 + I_2 + I_3 = 4 pi and 3 I_11 + I_12 + I_13 = 4 pi / a_1^2."""
+    import eshelby_closed_form as EC
+    nu = 0.3
+    S = EC.normal_eshelby_block((0.7, 0.7, 0.7), nu)
+    assert np.isclose(S[0, 0], (7 - 5 * nu) / (15 * (1 - nu)), rtol=1e-7)
+    assert np.isclose(S[0, 1], (5 * nu - 1) / (15 * (1 - nu)), rtol=1e-7)
+    a = (1.0, 0.75, 0.5)
+    I, Iij = EC.eshelby_integrals(a)
+    assert np.isclose(I.sum(), 4 * np.pi, rtol=1e-8)
+    for i in range(3):
+        assert np.isclose(3 * Iij[i, i] + sum(Iij[i, j] for j in range(3) if j != i), 4 * np.pi / a[i] ** 2,
+                          rtol=1e-8)
+
+
+def test_ellipsoid_indicator_reading():
+    """The Section 4.1 indicator as read: 1 at the centre, 1/2 on the sharp ellipsoid,
+    0 far outside, and the eigenstrain dilatational."""
+    p = M.eshelby_ellipsoid(33)
+    X, Y, Z = p.coords()
+    e = p.eigenstrain[0] / 1e-3
+    c = p.n[0] // 2
+    assert e[c, c, c] == pytest.approx(1.0)
+    assert e[0, 0, 0] == pytest.approx(0.0, abs=1e-12)
+    q = (X / 1.0) ** 2 + (Y / 0.75) ** 2 + (Z / 0.5) ** 2
+    on = np.isclose(q, 1.0, atol=1e-12)
+    assert on.any() and np.allclose(e[on], 0.5)
+    assert np.array_equal(p.eigenstrain[0], p.eigenstrain[2]) and not p.eigenstrain[3:].any()
