@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--inner", type=int, default=3, help="FP32 V-cycles per FP64 refinement step")
     ap.add_argument("--graph", action="store_true", help="replay refinement steps as a CUDA graph")
     ap.add_argument("--half", action="store_true", help="FP16 moduli in the FP32 V-cycle")
+    ap.add_argument("--cycle", default="V", choices=["V", "F"], help="multigrid cycle of the FP32 correction")
+    ap.add_argument("--smoother", default="rb", choices=["rb", "gs8", "jacobi"])
+    ap.add_argument("--nu", type=int, default=2, help="pre- and post-smoothing sweeps")
     return ap.parse_args()
 
 
@@ -313,8 +316,10 @@ def main():
 
     # launch-shape autotuning of the smoother (per level), then warm-up solves
     tune_ms = g.autotune()
+    cyc = {"cycle": {"V": E.CYCLE_V, "F": E.CYCLE_F}[args.cycle], "nu1": args.nu, "nu2": args.nu,
+           "smoother": {"rb": E.SMOOTH_RB, "gs8": E.SMOOTH_GS8, "jacobi": E.SMOOTH_JACOBI}[args.smoother]}
     for _ in range(args.warmup):
-        info = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner)
+        info = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner, **cyc)
     # FP64 reference solve of the same problem
     fp64_times, fp64_info = [], None
     for _ in range(args.fp64_steps):
@@ -341,7 +346,7 @@ def main():
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         info = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner,
-                       use_graph=args.graph)
+                       use_graph=args.graph, **cyc)
         b.record(stream)
         per.append((a, b))
         if info["status"] != 0:
@@ -362,7 +367,7 @@ def main():
         # graph replays record no per-kernel events: time the same kernels in one
         # eager solve after the timed region (same launch shapes, same buffers)
         ctx.profile(True)
-        g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner)
+        g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner, **cyc)
         torch.cuda.synchronize()
         prof = {name: ctx.profile_read(cls) for name, cls in prof_classes}
         ctx.profile(False)
@@ -379,7 +384,7 @@ def main():
         t = time.perf_counter()
         for _ in range(args.e2e_steps):
             g.set_moduli_from(host_mod)
-            info_e = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner)
+            info_e = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=200, inner_cycles=args.inner, **cyc)
             g.displacement_into(host_u)
         torch.cuda.synchronize()
         te = time.perf_counter() - t
@@ -479,9 +484,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"polycrystal {args.n}^3 nodes ({N} nodes, {3 * N} DOF), {args.grains} grains, "
                                "rotated cubic C11=1.68 C12=1.21 C44=0.75, GB width 4h, u_x=-+0.5e-3 on x faces, "
-                               "traction-free elsewhere; V(2,2) red-black block GS",
-                   "precision": f"FP32 V-cycle x{args.inner} inside FP64 iterative refinement"
-                                + (", FP16 moduli in the V-cycle" if args.half else ""),
+                               "traction-free elsewhere",
+                   "precision": f"FP32 {args.cycle}({args.nu},{args.nu}) {args.smoother} cycle x{args.inner} "
+                                "inside FP64 iterative refinement" + (", FP16 moduli in the V-cycle" if args.half else ""),
                    "inputs": "larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
         "cycles": info["cycles"], "rel_residual": info["rel_residual"], "rel_residual_fp64_check": rel64,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},

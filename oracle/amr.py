@@ -28,6 +28,15 @@ Reading of Section 3.2 and Appendix A taken here (listed in the design notes):
   interpolated coarse correction on all valid fine nodes, set the ghosts from it,
   and relax again; finally add the corrections and inject fine values into covered
   coarse nodes.
+
+Reading R2 (``reading="R2"``), the other reading of Section 3.2 ("N + 1 ghost
+nodes" with N = 1): fine grids carry two ghost layers on each coarse/fine face.  The
+inner layer is relaxed with the valid nodes (it is the epsilon-neighbourhood of the
+valid region); only the outer layer is a Dirichlet boundary filled by interpolation.
+Every covered coarse node then has its whole restriction footprint among relaxed
+fine nodes, so residuals, moduli and the solution itself pass down by the untruncated
+full-weighting restriction (no injection).  Covered Dirichlet coarse rows keep their
+boundary values.
 """
 from __future__ import annotations
 
@@ -46,9 +55,12 @@ class AmrData:
     L: MG.LevelData              # smoother data of the level's grid
     f: np.ndarray
     levels0: list = None         # level 0 only: its multigrid hierarchy
-    ghost_mask: np.ndarray = None
+    ghost_mask: np.ndarray = None   # Dirichlet ghost nodes (filled by interpolation)
     valid_mask: np.ndarray = None
     covered: np.ndarray = None   # nodes covered by the next finer level
+    relax_mask: np.ndarray = None   # relaxed nodes: valid (R1), valid + inner ghost layer (R2)
+    relax_spec: object = None       # the spec with its valid box grown to the relaxed nodes
+    reading: str = "R1"
 
 
 def _single_level(level):
@@ -63,7 +75,17 @@ def _coords_1d(spec, d):
     return spec.grid_lo[d] + np.arange(spec.problem.n[d])
 
 
-def coarse_moduli(specs):
+def relaxed_spec(sp, reading):
+    """The spec with its valid box grown to the nodes that are relaxed: the valid box
+    itself (R1), or the valid box and the inner ghost layer of each coarse/fine face (R2)."""
+    if reading == "R1" or sp.level == 0:
+        return sp
+    lo = tuple(sp.valid_lo[d] - (1 if sp.ghost[2 * d] else 0) for d in range(3))
+    hi = tuple(sp.valid_hi[d] + (1 if sp.ghost[2 * d + 1] else 0) for d in range(3))
+    return dataclasses.replace(sp, valid_lo=lo, valid_hi=hi)
+
+
+def coarse_moduli(specs, reading="R1"):
     """Operator equivalence across AMR levels (Section 3.1): a covered coarse node
     takes the restriction of the finer level's moduli, exactly as the multigrid
     levels below 0 take restricted moduli.  Returns one moduli array per level."""
@@ -71,13 +93,15 @@ def coarse_moduli(specs):
     n0 = specs[0].problem.n
     for l in range(len(specs) - 1, 0, -1):
         counts = tuple((n0[d] - 1) * 2 ** l + 1 for d in range(3))
-        restrict_field(specs[l], mods[l], specs[l - 1], mods[l - 1], counts)
+        restrict_field(relaxed_spec(specs[l], reading), mods[l], specs[l - 1], mods[l - 1], counts)
     return mods
 
 
-def build(specs):
+def build(specs, reading="R1"):
+    if reading not in ("R1", "R2"):
+        raise ValueError(reading)
     out = []
-    mods = coarse_moduli(specs)
+    mods = coarse_moduli(specs, reading)
     specs = [dataclasses.replace(sp, problem=dataclasses.replace(sp.problem, moduli=mod))
              for sp, mod in zip(specs, mods)]
     for sp in specs:
@@ -89,14 +113,19 @@ def build(specs):
             levels0 = None
             Ld = _single_level(lev)
         f = S.rhs(lev, sp.problem)
-        valid = np.ones(lev.shape, dtype=bool)
-        for d in range(3):
-            g = _coords_1d(sp, d)
-            ok = (g >= sp.valid_lo[d]) & (g <= sp.valid_hi[d])
-            shape = [1, 1, 1]
-            shape[2 - d] = -1
-            valid &= ok.reshape(shape)
-        out.append(AmrData(sp, Ld, f, levels0, ~valid, valid))
+        rsp = relaxed_spec(sp, reading)
+        masks = []
+        for box in (sp, rsp):
+            m = np.ones(lev.shape, dtype=bool)
+            for d in range(3):
+                g = _coords_1d(sp, d)
+                ok = (g >= box.valid_lo[d]) & (g <= box.valid_hi[d])
+                shape = [1, 1, 1]
+                shape[2 - d] = -1
+                m &= ok.reshape(shape)
+            masks.append(m)
+        valid, relax = masks
+        out.append(AmrData(sp, Ld, f, levels0, ~relax, valid, relax_mask=relax, relax_spec=rsp, reading=reading))
     for l in range(len(out) - 1):
         c, fn = out[l], out[l + 1]
         cov = np.ones(c.L.level.shape, dtype=bool)
@@ -167,10 +196,22 @@ def _restrict_weights_1d(gc, fine_spec, d, n_level_fine):
 
 
 def restrict_residual(fine: AmrData, fres, coarse: AmrData, cres, n_level_fine):
-    """R_mn at covered coarse nodes: weights truncated to valid fine nodes, renormalised
-    (applied direction by direction: the weights are a tensor product)."""
-    restrict_field(fine.spec, fres, coarse.spec, cres, n_level_fine)
+    """R_mn at covered coarse nodes: weights truncated to relaxed fine nodes (the valid
+    ones in R1) and renormalised (applied direction by direction: the weights are a
+    tensor product)."""
+    restrict_field(fine.relax_spec, fres, coarse.spec, cres, n_level_fine)
     cres[:] = np.where(coarse.L.types == DIRICHLET, 0.0, cres)
+
+
+def sync_covered(fine: AmrData, ffield, coarse: AmrData, cfield, n_level_fine):
+    """Covered coarse nodes from the fine solution: injection (R1), or the full-weighting
+    restriction over the relaxed fine nodes on non-Dirichlet coarse rows (R2)."""
+    if fine.reading == "R1":
+        inject(fine, ffield, coarse, cfield)
+        return
+    tmp = cfield.copy()
+    restrict_field(fine.relax_spec, ffield, coarse.spec, tmp, n_level_fine)
+    cfield[:] = np.where(coarse.L.types == DIRICHLET, cfield, tmp)
 
 
 def restrict_field(sp, fres, csp, cres, n_level_fine):
@@ -211,7 +252,7 @@ def composite_residual(data, u):
     res = []
     for l in range(nl):
         r = S.residual(data[l].L.level, u[l], data[l].f, data[l].L.types)
-        r = np.where(data[l].valid_mask[None], r, 0.0)
+        r = np.where(data[l].relax_mask[None], r, 0.0)
         res.append(r)
     for l in range(nl - 1, 0, -1):
         restrict_residual(data[l], res[l], data[l - 1], res[l - 1], counts[l])
@@ -231,8 +272,9 @@ def initial_state(data):
     for d in data:
         uD = S.dirichlet_values(d.L.level)
         u.append(np.where(d.ghost_mask[None], 0.0, uD))
+    counts = fine_level_counts(data)
     for l in range(len(data) - 1, 0, -1):
-        inject(data[l], u[l], data[l - 1], u[l - 1])
+        sync_covered(data[l], u[l], data[l - 1], u[l - 1], counts[l])
     return u
 
 
@@ -248,7 +290,7 @@ def cycle(data, u, nu1=2, nu2=2):
         for _ in range(nu1):
             MG.sweep(Ld, cor[l], res[l])
         rr = S.residual(Ld.level, cor[l], res[l], Ld.types)
-        res_pass[l] = np.where(data[l].valid_mask[None], rr, 0.0)
+        res_pass[l] = np.where(data[l].relax_mask[None], rr, 0.0)
         restrict_residual(data[l], res_pass[l], data[l - 1], res_pass[l - 1], counts[l])
         if l - 1 > 0:
             res[l - 1] = np.where(data[l - 1].covered[None], res_pass[l - 1], res[l - 1])
@@ -259,19 +301,19 @@ def cycle(data, u, nu1=2, nu2=2):
         Ld = data[l].L
         interp = interpolate(data[l - 1], cor[l - 1], data[l])
         nonD = Ld.types != DIRICHLET
-        cor[l] = np.where(data[l].valid_mask[None] & nonD, cor[l] + interp, cor[l])
+        cor[l] = np.where(data[l].relax_mask[None] & nonD, cor[l] + interp, cor[l])
         cor[l] = np.where(data[l].ghost_mask[None], interp, cor[l])
         for _ in range(nu2):
             MG.sweep(Ld, cor[l], res[l])
     for l in range(nl):
         u[l] += np.where(data[l].ghost_mask[None], 0.0, cor[l])
     for l in range(nl - 1, 0, -1):
-        inject(data[l], u[l], data[l - 1], u[l - 1])
+        sync_covered(data[l], u[l], data[l - 1], u[l - 1], counts[l])
 
 
-def solve(specs, tol=1e-8, max_cycles=100, nu1=2, nu2=2, data=None, fixed_cycles=None):
+def solve(specs, tol=1e-8, max_cycles=100, nu1=2, nu2=2, data=None, fixed_cycles=None, reading="R1"):
     if data is None:
-        data = build(specs)
+        data = build(specs, reading)
     u = initial_state(data)
     r0 = composite_norm(data, composite_residual(data, u))
     hist = []

@@ -787,12 +787,13 @@ __global__ void __launch_bounds__(BS, MINB) k_half_sweep_int(Lv<T> L, const T* _
 
 // ---- z-marching tiled half-sweep of colour-split FP32 levels ---------------------------
 // A block owns a 32 x TY tile of interior (x, y) nodes and a chunk of interior z planes.
-// Only the displacement is staged: its planes, with a one-node x/y halo, rotate through
-// four shared buffers (cp.async, plane z+2 streaming in while plane z is computed), so
-// each displacement value comes from DRAM once per half-sweep and the 57 stencil reads of
-// a node are shared-memory loads at compile-time offsets.  The moduli and their
-// divergence are the active node's own colour-split records, read once from global
-// memory.  Each warp covers 16 x-pairs of two neighbouring rows (active nodes of
+// Every global read is an asynchronous copy issued one plane ahead (cp.async): the
+// displacement planes, with a one-node x/y halo, rotate through four shared buffers
+// (plane z+2 streams in while plane z is computed), and the active nodes' colour-split
+// records (21 moduli + 18 divergence entries) and right-hand sides of plane z+1 fill the
+// other half of a double buffer.  So each value comes from DRAM once per half-sweep and
+// the stencil reads only shared memory, the 57 displacement reads at compile-time
+// offsets.  Each warp covers 16 x-pairs of two neighbouring rows (active nodes of
 // opposite x parity: conflict-free shared loads).  The first blocks of the launch take
 // the edge, corner and face nodes, as in k_half_sweep_int.  Same stencil, same order of
 // operations as the untiled kernel: identical bits.
@@ -803,7 +804,9 @@ struct SplitTile {
     static constexpr int UPL = 3 * PLANE;              // floats per displacement plane
     static constexpr int NT = 16 * TY;
     static constexpr int NPOS = (PLANE + NT - 1) / NT; // positions per thread
-    static constexpr size_t SMEM = sizeof(float) * 4 * UPL;
+    static constexpr int REC = kSplitK * NT;           // floats of one plane's records
+    static constexpr int FRH = 3 * NT;                 // floats of one plane's right-hand sides
+    static constexpr size_t SMEM = sizeof(float) * (4 * UPL + 2 * REC + 2 * FRH);
 };
 
 template <int TY, int MINB>
@@ -812,8 +815,11 @@ __global__ void __launch_bounds__(16 * TY, MINB)
                              const float* __restrict__ f, int colour, NullInfo nf, const double* __restrict__ lam,
                              BndSegs sg, int gx, int gy, int zlen) {
     using S = SplitTile<TY>;
-    constexpr int PLANE = S::PLANE, UPL = S::UPL, NPOS = S::NPOS, NT = S::NT;
+    constexpr int PLANE = S::PLANE, UPL = S::UPL, NPOS = S::NPOS, NT = S::NT, REC = S::REC, FRH = S::FRH;
     extern __shared__ __align__(16) float sm[];
+    float* const Us = sm;                          // [4][3][R][kTileS]
+    float* const Rs = sm + 4 * UPL;                // [2][kSplitK][NT]
+    float* const Fs = Rs + 2 * REC;                // [2][3][NT]
     if (L.active && *L.active == 0) return;
     const int b = blockIdx.x, tid = threadIdx.x;
     if (b < sg.f2) {
@@ -852,11 +858,17 @@ __global__ void __launch_bounds__(16 * TY, MINB)
             }
         }
     }
-    auto load_plane = [&](int z, int j) {
+    const int tx = tid & 15, ty = tid >> 4;
+    const int y = yt0 + ty;
+    const int x0 = xt0 + 2 * tx;
+    const int yl = ty + 1;
+    auto active_x = [&](int z) { return x0 + ((x0 + y + z + colour) & 1); };
+    // displacement plane z into ring slot j & 3
+    auto load_u = [&](int z, int j) {
         if (z < 0) z += nz;
         if (z >= nz) z -= nz;
         const int zb = z * nx * ny;
-        float* ud = sm + (j & 3) * UPL;
+        float* ud = Us + (j & 3) * UPL;
 #pragma unroll
         for (int q = 0; q < NPOS; ++q) {
             if (goff[q] < 0) continue;
@@ -864,27 +876,40 @@ __global__ void __launch_bounds__(16 * TY, MINB)
 #pragma unroll
             for (int k = 0; k < 3; ++k) cp_async4(ud + k * PLANE + pos, u + (size_t)k * N + zb + goff[q]);
         }
-        cp_async_commit();
     };
-
-    const int tx = tid & 15, ty = tid >> 4;
-    const int y = yt0 + ty;
-    const int x0 = xt0 + 2 * tx;
-    const int yl = ty + 1;
-    load_plane(z0 - 1, 0);
-    load_plane(z0, 1);
-    load_plane(z0 + 1, 2);
+    // this thread's active node of plane z: its record and right-hand side into buffer z & 1
+    auto load_node = [&](int z) {
+        const int xa = active_x(z);
+        if (y >= yend || xa >= xend) return;
+        const int p = xa + nx * (y + ny * z);
+        const float* cb = L.mod + (p & 1) * L.msplit1 + (size_t)((p >> 1) >> 5) * (32 * kSplitK) + ((p >> 1) & 31);
+        float* rd = Rs + (z & 1) * REC + tid;
+#pragma unroll
+        for (int c = 0; c < kSplitK; ++c) cp_async4(rd + c * NT, cb + 32 * c);
+        float* fd = Fs + (z & 1) * FRH + tid;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cp_async4(fd + k * NT, f + (size_t)k * N + p);
+    };
+    load_u(z0 - 1, 0);
+    load_u(z0, 1);
+    load_u(z0 + 1, 2);
+    load_node(z0);
+    cp_async_commit();
     for (int z = z0; z < zend; ++z) {
         const int j = z - z0 + 1;          // ring slot of plane z
         cp_async_wait_all();
         __syncthreads();
-        if (z + 2 <= zend) load_plane(z + 2, j + 2);   // into the slot of plane z - 2
-        const int xa = x0 + ((x0 + y + z + colour) & 1);
+        // one plane ahead: displacement plane z+2 (into the slot of plane z-2) and the
+        // records of plane z+1 (into the buffer of plane z-1)
+        if (z + 2 <= zend) load_u(z + 2, j + 2);
+        if (z + 1 < zend) load_node(z + 1);
+        cp_async_commit();
+        const int xa = active_x(z);
         const int xi = (xa == x0) ? x0 + 1 : x0;
         const int xla = xa - xt0 + 1, xli = xi - xt0 + 1;
-        const float* const Um = sm + ((j + 3) & 3) * UPL + yl * kTileS + xla;
-        const float* const U0 = sm + (j & 3) * UPL + yl * kTileS;
-        const float* const Up = sm + ((j + 1) & 3) * UPL + yl * kTileS + xla;
+        const float* const Um = Us + ((j + 3) & 3) * UPL + yl * kTileS + xla;
+        const float* const U0 = Us + (j & 3) * UPL + yl * kTileS;
+        const float* const Up = Us + ((j + 1) & 3) * UPL + yl * kTileS + xla;
         const int row = nx * (y + ny * z);
         if (y < yend && xi < xend) {
             const int q = xi + row;
@@ -893,18 +918,19 @@ __global__ void __launch_bounds__(16 * TY, MINB)
         }
         if (y < yend && xa < xend) {
             const int p = xa + row;
-            const float* cb = L.mod + (p & 1) * L.msplit1 + (size_t)((p >> 1) >> 5) * (32 * kSplitK) + ((p >> 1) & 31);
+            const float* rb = Rs + (z & 1) * REC + tid;
+            const float* fb = Fs + (z & 1) * FRH + tid;
             auto ua = [&](int k, int dx, int dy, int dz) -> float {
                 const float* bp = dz < 0 ? Um : (dz > 0 ? Up : U0 + xla);
                 return bp[k * PLANE + dy * kTileS + dx];
             };
-            auto ca = [&](int c, int, int, int) -> float { return __ldg(cb + 32 * c); };
+            auto ca = [&](int c, int, int, int) -> float { return rb[c * NT]; };
             float v[3];
             interior_rows_core<float, 21, true>(L, ua, ca, p, v);
             float r[3], B[3][3], d[3];
             const int c3[3] = {xa, y, z};
             for (int i = 0; i < 3; ++i) {
-                float fi = f[(size_t)i * N + p];
+                float fi = fb[i * NT];
                 if (lam) fi = xsub(fi, rigid_load<float>(nf, lam, i, c3));
                 r[i] = xsub(fi, v[i]);
             }

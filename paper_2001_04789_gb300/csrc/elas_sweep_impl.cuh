@@ -16,7 +16,7 @@ namespace elas {
 // colour-split levels (32 x 16 and 32 x 8 tiles, displacement staged); their pair holds
 // (threads, resident blocks per SM).
 static const int kSweepVariants[kNumSweepVariants][2] = {{256, 1}, {256, 2}, {256, 3}, {256, 4}, {128, 8},
-                                                         {256, 1}, {128, 2}, {256, 2}, {128, 4}};
+                                                         {256, 1}, {128, 2}, {256, 1}, {128, 3}};
 constexpr int kFirstTiledVariant = 5;
 constexpr int kFirstSplitTiledVariant = 7;
 
@@ -96,6 +96,12 @@ void launch_tiled_split(const Lv<float>& L, const float* u_in, float* u_out, con
     const BndSegs sg = bnd_segs(L, S::NT);
     const int nb = sg.f2 + gx * gy * gz;
     if (!nb) return;
+    static const bool attr = [] {
+        cudaFuncSetAttribute(k_half_sweep_tiled_split<TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)S::SMEM);
+        return true;
+    }();
+    (void)attr;
     count_launch();
     k_half_sweep_tiled_split<TY, MINB><<<nb, S::NT, S::SMEM, s>>>(L, u_in, u_out, f, colour, nfv, lam, sg, gx, gy, zl);
 }
@@ -144,8 +150,8 @@ void sweep_int_variant(int v, size_t np, const Lv<T>& L, const T* u_in, T* u_out
     }
     if constexpr (sizeof(T) == 4 && MH == kMlSplit) {
         if (v >= kFirstSplitTiledVariant && variant_ok(L, v) && colour < 2) {   // red-black only
-            if (v == kFirstSplitTiledVariant) launch_tiled_split<16, 2>(L, u_in, u_out, f, colour, nfv, lam, s);
-            else launch_tiled_split<8, 4>(L, u_in, u_out, f, colour, nfv, lam, s);
+            if (v == kFirstSplitTiledVariant) launch_tiled_split<16, 1>(L, u_in, u_out, f, colour, nfv, lam, s);
+            else launch_tiled_split<8, 3>(L, u_in, u_out, f, colour, nfv, lam, s);
             return;
         }
     }

@@ -331,10 +331,11 @@ def _tag_box(phi, h, thresh, block, parent_lo, parent_hi, n_level):
     return tuple(int(v) for v in lo_f), tuple(int(v) for v in hi_f)
 
 
-def amr_layout(make_box_problem, base_n, nlevels, indicator, thresh=0.1, block=32):
+def amr_layout(make_box_problem, base_n, nlevels, indicator, thresh=0.1, block=32, ghost_layers=1):
     """Build the AMR levels of a unit-cube workload.  ``make_box_problem(n3, lo3, hi3)``
     returns the workload's Problem on a node box; ``indicator(X, Y, Z)`` is the field
-    whose gradient tags cells for refinement."""
+    whose gradient tags cells for refinement.  Fine grids carry ``ghost_layers`` node
+    layers beyond each coarse/fine face (1 for reading R1, 2 for reading R2)."""
     base = make_box_problem((base_n,) * 3, (0.0,) * 3, (1.0,) * 3)
     levels = [AmrLevel(0, 1.0 / (base_n - 1), (0, 0, 0), (base_n - 1,) * 3, (0, 0, 0),
                        (False,) * 6, base)]
@@ -354,8 +355,8 @@ def amr_layout(make_box_problem, base_n, nlevels, indicator, thresh=0.1, block=3
         for f in range(6):
             d = f // 2
             ghost.append(vlo[d] > 0 if f % 2 == 0 else vhi[d] < n_level - 1)
-        glo = tuple(vlo[d] - (1 if ghost[2 * d] else 0) for d in range(3))
-        ghi = tuple(vhi[d] + (1 if ghost[2 * d + 1] else 0) for d in range(3))
+        glo = tuple(vlo[d] - (ghost_layers if ghost[2 * d] else 0) for d in range(3))
+        ghi = tuple(vhi[d] + (ghost_layers if ghost[2 * d + 1] else 0) for d in range(3))
         n3 = tuple(ghi[d] - glo[d] + 1 for d in range(3))
         lo3 = tuple(glo[d] * h for d in range(3))
         hi3 = tuple(ghi[d] * h for d in range(3))
@@ -365,11 +366,11 @@ def amr_layout(make_box_problem, base_n, nlevels, indicator, thresh=0.1, block=3
     return levels
 
 
-def amr_penny_crack(base_n=65, nlevels=3, block=32, thresh=0.1, width=3.0 / 256, **kw):
+def amr_penny_crack(base_n=65, nlevels=3, block=32, thresh=0.1, width=3.0 / 256, ghost_layers=1, **kw):
     """Penny crack on a 3-level layout, ratio 2 (laterally clamped z grips)."""
     mk = lambda n3, lo3, hi3: penny_crack(width=width, clamp_lateral=True, box=(n3, lo3, hi3), **kw)
     ind = lambda X, Y, Z: crack_indicator(X, Y, Z, width=width)
-    return amr_layout(mk, base_n, nlevels, ind, thresh, block)
+    return amr_layout(mk, base_n, nlevels, ind, thresh, block, ghost_layers)
 
 
 def ellipsoid_rve(n, seed, nu=0.3, width_cells=3.0, strain_norm=1e-3):

@@ -203,3 +203,93 @@ def test_restriction_of_a_point_value_and_of_a_constant():
     A.restrict_field(fine, fres, coarse, cres, (17, 17, 17))
     assert np.allclose(cres[:, 2:7, 2:7, 2:7], 5.0, rtol=0, atol=1e-14)
     assert np.all(cres[:, :2] == 0) and np.all(cres[:, 7:] == 0)
+
+
+# --------------------------------------------------------------------------
+# reading R2: N + 1 = 2 ghost layers, inner layer relaxed, full weighting
+# --------------------------------------------------------------------------
+
+def test_r2_restriction_weights_are_untruncated_at_the_coarse_fine_boundary():
+    """In R2 the inner ghost layer is relaxed, so a covered coarse node on the
+    coarse/fine boundary restricts with the full (1/4, 1/2, 1/4) footprint."""
+    from types import SimpleNamespace
+    sp = SimpleNamespace(level=1, grid_lo=(2, 2, 2), valid_lo=(4, 4, 4), valid_hi=(12, 12, 12),
+                         ghost=(True,) * 6, problem=SimpleNamespace(n=(13, 13, 13)))
+    import dataclasses as dc
+
+    @dc.dataclass
+    class Spec:
+        level: int
+        grid_lo: tuple
+        valid_lo: tuple
+        valid_hi: tuple
+        ghost: tuple
+        problem: object
+    spec = Spec(sp.level, sp.grid_lo, sp.valid_lo, sp.valid_hi, sp.ghost, sp.problem)
+    rsp = A.relaxed_spec(spec, "R2")
+    assert rsp.valid_lo == (3, 3, 3) and rsp.valid_hi == (13, 13, 13)
+    assert A._restrict_weights_1d(2, rsp, 0, 17) == pytest.approx({-1: 0.25, 0: 0.5, 1: 0.25})
+    assert A.relaxed_spec(spec, "R1") is spec
+
+
+def test_r2_composite_solve_reproduces_affine_field_exactly():
+    G = np.array([[1.0, 0.3, -0.2], [0.1, -0.5, 0.4], [0.2, 0.0, 0.7]]) * 1e-3
+    b = np.array([1e-4, -2e-4, 3e-4])
+
+    def field(p):
+        X, Y, Z = p.coords()
+        x = [X, Y, Z]
+        return np.stack([sum(G[k, l] * x[l] for l in range(3)) + b[k] for k in range(3)])
+
+    def mk(n3, lo3, hi3):
+        p = M.Problem(n=tuple(n3), lo=tuple(lo3), hi=tuple(hi3))
+        X, _, _ = p.coords()
+        lam, mu = M.lame(np.ones(X.shape), 0.3)
+        p.moduli_kind = M.MODULI_ISO
+        p.moduli = np.stack([lam, mu])
+        p.bc = M.all_faces(M.DIRICHLET, 0.0)
+        p.face_values = {f_: field(p) for f_ in range(6)}
+        return p
+
+    ind = lambda X, Y, Z: np.exp(-((X - 0.4) ** 2 + (Y - 0.6) ** 2 + (Z - 0.5) ** 2) / 0.02)
+    specs = M.amr_layout(mk, 17, 3, ind, thresh=0.15, block=8, ghost_layers=2)
+    assert len(specs) == 3
+    u, info = A.solve(specs, tol=1e-12, max_cycles=60, reading="R2")
+    assert info["converged"]
+    for sp, ul in zip(specs, u):
+        assert np.abs(ul - field(sp.problem)).max() < 1e-11
+
+
+def test_r2_is_closer_to_the_uniform_fine_solution_than_r1():
+    """Both readings on the same smooth problem: the R2 composite solution lies closer
+    to the uniform fine-grid solution than R1's, and both far below the coarse error."""
+    from oracle import multigrid as MG
+
+    def mk(n3, lo3, hi3):
+        p = M.Problem(n=tuple(n3), lo=tuple(lo3), hi=tuple(hi3))
+        X, Y, Z = p.coords()
+        g = np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) / 0.01)
+        lam, mu = M.lame(1.0 + 0.8 * g, 0.3)
+        p.moduli_kind = M.MODULI_ISO
+        p.moduli = np.stack([lam, mu])
+        e = np.zeros((6,) + X.shape)
+        e[0] = e[1] = e[2] = 1e-3 * g
+        p.eigenstrain = e
+        p.bc = M.all_faces(M.DIRICHLET, 0.0)
+        return p
+
+    ind = lambda X, Y, Z: np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2) / 0.01)
+    uf, _ = MG.solve(mk((33, 33, 33), (0, 0, 0), (1, 1, 1)), tol=1e-11, max_cycles=80)
+    uc, _ = MG.solve(mk((17, 17, 17), (0, 0, 0), (1, 1, 1)), tol=1e-11, max_cycles=80)
+    err = {}
+    for reading, layers in (("R1", 1), ("R2", 2)):
+        specs = M.amr_layout(mk, 17, 2, ind, thresh=0.05, block=8, ghost_layers=layers)
+        u, info = A.solve(specs, tol=1e-11, max_cycles=80, reading=reading)
+        assert info["converged"]
+        sp = specs[1]
+        sl = tuple(slice(sp.valid_lo[d], sp.valid_hi[d] + 1) for d in (2, 1, 0))
+        ul = u[1][(slice(None),) + tuple(slice(sp.valid_lo[d] - sp.grid_lo[d], sp.valid_hi[d] - sp.grid_lo[d] + 1)
+                                         for d in (2, 1, 0))]
+        err[reading] = np.abs(ul - uf[(slice(None),) + sl]).max()
+    err_coarse = np.abs(uc - uf[:, ::2, ::2, ::2]).max()
+    assert err["R2"] < err["R1"] < 0.5 * err_coarse, (err, err_coarse)
