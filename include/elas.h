@@ -322,6 +322,20 @@ typedef struct {
     int ghost[6];
 } elas_amr_level;
 int  elas_amr_create(elas_grid* grids, const elas_amr_level* levels, int nlevels, elas_amr* out);
+/* Which reading of the reflux-free treatment (Section 3.2) the composite cycle uses.
+ * ELAS_AMR_R1 (default): valid fine nodes include the coarse/fine boundary, one ghost
+ * layer (Dirichlet, interpolated), covered coarse nodes take the coincident fine value,
+ * fine residuals and moduli pass down with the restriction weights truncated to valid
+ * nodes and renormalised.  ELAS_AMR_R2 (the "N + 1 ghost nodes" of Section 3.2, N = 1):
+ * fine grids carry two ghost layers on each coarse/fine face (grid_lo two nodes before
+ * valid_lo there); the inner layer is relaxed with the valid nodes, the outer one is the
+ * interpolated Dirichlet layer; residuals, moduli and the solution pass down by the
+ * untruncated full-weighting restriction (covered Dirichlet coarse rows keep their
+ * values).  ELAS_ERR_INVALID_ARG if a grid lacks the second layer.  The composite norm
+ * counts valid fine rows and uncovered coarse rows in both readings. */
+#define ELAS_AMR_R1 1
+#define ELAS_AMR_R2 2
+int  elas_amr_set_reading(elas_amr a, int reading);
 int  elas_amr_destroy(elas_amr a);
 int  elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* info);
 

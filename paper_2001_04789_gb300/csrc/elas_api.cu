@@ -1606,7 +1606,9 @@ int batch_run(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_i
 // ======================================================================================
 struct elas_amr_s {
     std::vector<elas_grid> g;
-    std::vector<AmrBox> box;
+    std::vector<AmrBox> box;    // valid boxes
+    std::vector<AmrBox> rbox;   // relaxed boxes: the valid box (R1), grown by the inner ghost layer (R2)
+    int reading = ELAS_AMR_R1;
     std::vector<double*> res, rpass, cor, cora, tmp;
     std::vector<std::pair<void*, size_t>> allocs;
     double* partials = nullptr;
@@ -1644,10 +1646,20 @@ int amr_composite_residual(elas_amr a) {
         launch_residual<double, double>(v.L64, v.u, v.f, nullptr, nullptr, a->res[l], nullptr, nullptr, s);
     }
     for (int l = nl - 1; l >= 1; --l)
-        launch_amr_restrict(a->g[l]->lv[0].L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->res[l],
+        launch_amr_restrict(a->g[l]->lv[0].L64, a->rbox[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->res[l],
                             a->res[l - 1], 3, 1, s);
     CHECK_LAUNCH(c);
     return ELAS_OK;
+}
+
+// Covered coarse nodes from the fine solution: injection (R1), or the full-weighting
+// restriction over the relaxed fine nodes, Dirichlet rows kept (R2).
+void amr_sync(elas_amr a, int l, const double* ffield, double* cfield) {
+    cudaStream_t s = a->g[0]->ctx->stream;
+    const Lv<double>& Lf = a->g[l]->lv[0].L64;
+    const Lv<double>& Lc = a->g[l - 1]->lv[0].L64;
+    if (a->reading == ELAS_AMR_R2) launch_amr_restrict(Lf, a->rbox[l], Lc, a->box[l - 1], ffield, cfield, 3, 2, s);
+    else launch_amr_inject(Lf, a->box[l], Lc, a->box[l - 1], ffield, cfield, s);
 }
 
 int amr_norm(elas_amr a, double* out) {
@@ -1683,8 +1695,8 @@ void amr_cycle(elas_amr a, int nu1, int nu2) {
             smooth<double>(gl, 0, nu1, nullptr, nullptr);
             launch_residual<double, double>(v.L64, v.u, v.f, nullptr, nullptr, a->rpass[l], nullptr, nullptr, s);
         }
-        launch_amr_restrict(v.L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->rpass[l], a->rpass[l - 1], 3, 1,
-                            s);
+        launch_amr_restrict(v.L64, a->rbox[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->rpass[l], a->rpass[l - 1], 3,
+                            1, s);
         if (l - 1 >= 1)
             cudaMemcpyAsync(a->res[l - 1], a->rpass[l - 1], sizeof(double) * 3 * (size_t)a->g[l - 1]->lv[0].N,
                             cudaMemcpyDeviceToDevice, s);
@@ -1704,9 +1716,7 @@ void amr_cycle(elas_amr a, int nu1, int nu2) {
         smooth<double>(gl, 0, nu2, nullptr, nullptr);
     }
     for (int l = 0; l < nl; ++l) launch_amr_add(a->g[l]->lv[0].L64, a->box[l], a->g[l]->lv[0].u, a->cor[l], s);
-    for (int l = nl - 1; l >= 1; --l)
-        launch_amr_inject(a->g[l]->lv[0].L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->g[l]->lv[0].u,
-                          a->g[l - 1]->lv[0].u, s);
+    for (int l = nl - 1; l >= 1; --l) amr_sync(a, l, a->g[l]->lv[0].u, a->g[l - 1]->lv[0].u);
 }
 
 }  // namespace
@@ -1742,6 +1752,7 @@ int elas_amr_create(elas_grid* grids, const elas_amr_level* levels, int nlevels,
         for (int f = 0; f < 6; ++f) b.ghost[f] = levels[l].ghost[f];
         a->g.push_back(g);
         a->box.push_back(b);
+        a->rbox.push_back(b);
         parts += (size_t)((g->lv[0].N + kBlock - 1) / kBlock) * kPartialStride;
     }
     auto alloc = [&](double** p, size_t count) -> int {
@@ -1773,6 +1784,33 @@ int elas_amr_create(elas_grid* grids, const elas_amr_level* levels, int nlevels,
     return ELAS_OK;
 }
 
+int elas_amr_set_reading(elas_amr a, int reading) {
+    if (!a) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = a->g[0]->ctx;
+    if (reading != ELAS_AMR_R1 && reading != ELAS_AMR_R2) return set_err(c, ELAS_ERR_INVALID_ARG, "unknown AMR reading");
+    const int nl = (int)a->g.size();
+    for (int l = 0; l < nl; ++l) {
+        AmrBox rb = a->box[l];
+        if (reading == ELAS_AMR_R2 && l > 0) {
+            for (int d = 0; d < 3; ++d) {
+                const int glo = rb.grid_lo[d], ghi = glo + a->g[l]->desc.n[d] - 1;
+                if (rb.ghost[2 * d]) {
+                    if (rb.valid_lo[d] - glo < 2) return set_err(c, ELAS_ERR_INVALID_ARG, "reading R2 needs two ghost layers");
+                    rb.valid_lo[d] -= 1;
+                }
+                if (rb.ghost[2 * d + 1]) {
+                    if (ghi - rb.valid_hi[d] < 2) return set_err(c, ELAS_ERR_INVALID_ARG, "reading R2 needs two ghost layers");
+                    rb.valid_hi[d] += 1;
+                }
+            }
+        }
+        a->rbox[l] = rb;
+    }
+    a->reading = reading;
+    for (auto g : a->g) g->dirty = true;   // covered coarse moduli follow the reading
+    return ELAS_OK;
+}
+
 int elas_amr_destroy(elas_amr a) {
     if (!a) return ELAS_ERR_INVALID_ARG;
     if (!a->g.empty()) {
@@ -1798,7 +1836,7 @@ int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* inf
     if (dirty) {
         for (int l = nl - 1; l >= 1; --l) {
             if (!a->g[l]->moduli_set || !a->g[l - 1]->moduli_set) return set_err(c, ELAS_ERR_STATE, "moduli not set");
-            launch_amr_restrict(a->g[l]->lv[0].L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1],
+            launch_amr_restrict(a->g[l]->lv[0].L64, a->rbox[l], a->g[l - 1]->lv[0].L64, a->box[l - 1],
                                 a->g[l]->lv[0].mod64, a->g[l - 1]->lv[0].mod64, a->g[l]->K, 0, s);
             a->g[l - 1]->dirty = true;
         }
@@ -1813,9 +1851,7 @@ int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* inf
     }
     if (a->g[0]->lv[0].nf.m > 0) return set_err(c, ELAS_ERR_STATE, "AMR solve needs a problem without free rigid modes");
     for (int l = 0; l < nl; ++l) launch_dirichlet(a->g[l]->lv[0].L64, boundary_data(a->g[l]), a->g[l]->lv[0].u, 0, s);
-    for (int l = nl - 1; l >= 1; --l)
-        launch_amr_inject(a->g[l]->lv[0].L64, a->box[l], a->g[l - 1]->lv[0].L64, a->box[l - 1], a->g[l]->lv[0].u,
-                          a->g[l - 1]->lv[0].u, s);
+    for (int l = nl - 1; l >= 1; --l) amr_sync(a, l, a->g[l]->lv[0].u, a->g[l - 1]->lv[0].u);
     int rc = amr_composite_residual(a);
     if (rc) return rc;
     double r0 = 0.0;

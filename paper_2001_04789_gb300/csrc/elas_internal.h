@@ -157,8 +157,9 @@ void launch_amr_interp(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>&
 // covered coarse nodes := coincident fine values
 void launch_amr_inject(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
                        const double* ffield, double* cfield, cudaStream_t s);
-// covered coarse nodes := renormalised restriction of a K-plane fine field
-// (zero on coarse Dirichlet rows when zero_dirichlet)
+// covered coarse nodes := renormalised restriction of a K-plane fine field over the fine
+// box's valid nodes; on coarse Dirichlet rows: zero (zero_dirichlet 1), kept (2), or the
+// restricted value (0)
 void launch_amr_restrict(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
                          const double* ffield, double* cfield, int K, int zero_dirichlet, cudaStream_t s);
 // partials of sum res^2 over valid nodes not covered by the next level (cov may be null)

@@ -372,7 +372,9 @@ __device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restr
         uo[N + q] = u[N + q];
         uo[2 * N + q] = u[2 * N + q];
     };
-    auto update = [&](int x) {
+    // copy_dx: 0, or the x offset (+-1) of an inactive pair partner to copy alongside, so
+    // that the warp's two stores to a row meet in the same sectors at the same time
+    auto update = [&](int x, int copy_dx) {
         const int c[3] = {x, y, z};
         auto body = [&](const auto& ua, const auto& ca, int p) {
             T v[3], r[3], B[3][3], d[3];
@@ -386,22 +388,27 @@ __device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restr
             solve3(B, r, d);
             if (colour == kJacobiColour)
                 for (int i = 0; i < 3; ++i) d[i] = xmul(L.omega, d[i]);
-            for (int i = 0; i < 3; ++i) uo[i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
+            for (int i = 0; i < 3; ++i) {
+                if (copy_dx > 0) uo[i * N + p + 1] = ua(i, 1, 0, 0);
+                else if (copy_dx < 0) uo[i * N + p - 1] = ua(i, -1, 0, 0);
+                uo[i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
+            }
         };
         with_interior<T, KIND, ML>(L, u, x, y, z, body);
     };
     if (colour < 2) {
-        // red-black: exactly one node of the pair is active
+        // red-black: exactly one node of the pair is active; its partner is copied in
+        // the same stores
         const int xa = x0 + ((x0 + y + z + colour) & 1);
         const int xi = (xa == x0) ? x0 + 1 : x0;
-        if (xi < xend) copy(xi);
-        if (xa < xend) update(xa);
+        if (xa < xend) update(xa, xi < xend ? xi - xa : 0);
+        else if (xi < xend) copy(xi);
         return;
     }
     // eight colours or Jacobi: each node of the pair in turn
 #pragma unroll 1
     for (int x = x0; x < x0 + 2 && x < xend; ++x) {
-        if (sweep_active(colour, x, y, z)) update(x);
+        if (sweep_active(colour, x, y, z)) update(x, 0);
         else copy(x);
     }
 }
@@ -911,13 +918,14 @@ __global__ void __launch_bounds__(16 * TY, MINB)
         const float* const U0 = Us + (j & 3) * UPL + yl * kTileS;
         const float* const Up = Us + ((j + 1) & 3) * UPL + yl * kTileS + xla;
         const int row = nx * (y + ny * z);
-        if (y < yend && xi < xend) {
+        if (y < yend && xi < xend && xa >= xend) {
             const int q = xi + row;
 #pragma unroll
             for (int k = 0; k < 3; ++k) uo[(size_t)k * N + q] = U0[k * PLANE + xli];
         }
         if (y < yend && xa < xend) {
             const int p = xa + row;
+            const bool cp = xi < xend;
             const float* rb = Rs + (z & 1) * REC + tid;
             const float* fb = Fs + (z & 1) * FRH + tid;
             auto ua = [&](int k, int dx, int dy, int dz) -> float {
@@ -936,7 +944,10 @@ __global__ void __launch_bounds__(16 * TY, MINB)
             }
             interior_block_acc<float, 21>(L, ca, B);
             solve3(B, r, d);
-            for (int i = 0; i < 3; ++i) uo[(size_t)i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
+            for (int i = 0; i < 3; ++i) {
+                if (cp) uo[(size_t)i * N + xi + row] = U0[i * PLANE + xli];
+                uo[(size_t)i * N + p] = xadd(ua(i, 0, 0, 0), d[i]);
+            }
         }
     }
     cp_async_wait_all();
@@ -1580,7 +1591,10 @@ __global__ void k_amr_restrict(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox b
                 }
             }
         }
-        if (zero_dirichlet && k < 3 && row_type(Lc, nic, k) == ROW_DIRICHLET) acc = 0.0;
+        if (k < 3 && row_type(Lc, nic, k) == ROW_DIRICHLET) {
+            if (zero_dirichlet == 1) acc = 0.0;
+            else if (zero_dirichlet == 2) continue;   // keep the coarse boundary value
+        }
         cfield[(size_t)k * Lc.N + pc] = acc;
     }
 }
@@ -1594,7 +1608,12 @@ __global__ void k_amr_norm(Lv<double> L, AmrBox b, AmrBox cov, int has_cov, cons
     if (p < L.N) {
         int c[3];
         coords_of(p, L.n, c);
-        bool skip = amr_is_ghost(b, L.n, c);
+        // valid nodes only (ghost layers, relaxed or not, are not composite equations)
+        bool skip = false;
+        for (int d = 0; d < 3; ++d) {
+            const int g = b.grid_lo[d] + c[d];
+            skip |= (g < b.valid_lo[d] || g > b.valid_hi[d]);
+        }
         if (!skip && has_cov) {
             bool in = true;
             for (int d = 0; d < 3; ++d) {

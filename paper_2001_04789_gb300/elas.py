@@ -129,6 +129,7 @@ def lib():
         "elas_server_step": (ip, [vp, C.POINTER(ip), C.POINTER(ip)]),
         "elas_server_poll": (ip, [vp, C.c_longlong, C.POINTER(SolveInfo), dp]),
         "elas_amr_destroy": (ip, [vp]),
+        "elas_amr_set_reading": (ip, [vp, ip]),
         "elas_amr_solve": (ip, [vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "elas_profile_read": (ip, [vp, ip, dp, C.POINTER(C.c_longlong)]),
         "elas_launch_count": (C.c_ulonglong, []),
@@ -516,7 +517,7 @@ class Amr:
     (``microstructure.AmrLevel`` list): one grid per level, level 0 with its
     multigrid hierarchy, finer levels smoothed only."""
 
-    def __init__(self, ctx: Context, specs):
+    def __init__(self, ctx: Context, specs, reading="R1"):
         self.ctx = ctx
         self.specs = specs
         self.grids = [grid_from_problem(ctx, sp.problem, max_levels=0 if sp.level == 0 else 1) for sp in specs]
@@ -532,6 +533,7 @@ class Amr:
         h = C.c_void_p()
         ctx.check(lib().elas_amr_create(arr, descs, len(specs), C.byref(h)))
         self.h = h
+        ctx.check(lib().elas_amr_set_reading(self.h, {"R1": 1, "R2": 2}[reading]))
 
     def solve(self, rel_tol=1e-8, max_cycles=200, nu1=2, nu2=2, fixed_cycles=0, raise_on_error=True):
         info = SolveInfo()

@@ -95,3 +95,35 @@ def test_amr_affine_field_is_exact(E, ctx):
                                     for d in (2, 1, 0))
         assert np.abs(ul[sl] - ue[sl]).max() < 1e-11
     amr.close()
+
+
+def r2_layouts():
+    return {
+        "crack2_r2": lambda: M.amr_penny_crack(base_n=17, nlevels=2, block=8, width=3.0 / 32, ghost_layers=2),
+        "crack3_r2": lambda: M.amr_penny_crack(base_n=17, nlevels=3, block=8, width=3.0 / 64, ghost_layers=2),
+    }
+
+
+@pytest.mark.parametrize("name", list(r2_layouts()))
+def test_amr_r2_fixed_cycles_match_oracle(E, ctx, name):
+    """Reading R2 (two ghost layers, inner relaxed, full-weighting restriction) on the
+    GPU against the oracle's R2 cycle: every level's valid and inner-ghost nodes."""
+    specs = r2_layouts()[name]()
+    amr = E.Amr(ctx, specs, reading="R2")
+    info = amr.solve(fixed_cycles=3)
+    got = amr.displacements()
+    ref, rinfo = A.solve(specs, fixed_cycles=3, reading="R2")
+    for l, (g, r) in enumerate(zip(got, ref)):
+        sp = specs[l]
+        grow = [(1 if sp.ghost[2 * d] else 0, 1 if sp.ghost[2 * d + 1] else 0) if l > 0 else (0, 0) for d in range(3)]
+        sl = (slice(None),) + tuple(slice(sp.valid_lo[d] - grow[d][0] - sp.grid_lo[d],
+                                          sp.valid_hi[d] + grow[d][1] - sp.grid_lo[d] + 1) for d in (2, 1, 0))
+        assert rel_err(g[sl], r[sl]) < 1e-9, (name, l)
+    assert np.allclose(info["rel_history"], rinfo["rel_history"], rtol=1e-7)
+    amr.close()
+
+
+def test_amr_r2_needs_two_ghost_layers(E, ctx):
+    specs = layouts()["crack2"]()
+    with pytest.raises(E.ElasError):
+        E.Amr(ctx, specs, reading="R2")
