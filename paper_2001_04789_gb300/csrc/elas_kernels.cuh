@@ -372,8 +372,7 @@ __device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restr
         uo[N + q] = u[N + q];
         uo[2 * N + q] = u[2 * N + q];
     };
-    // copy_dx: 0, or the x offset (+-1) of an inactive pair partner to copy alongside, so
-    // that the warp's two stores to a row meet in the same sectors at the same time
+    // copy_dx: 0, or the x offset (+-1) of an inactive pair partner to copy with the update
     auto update = [&](int x, int copy_dx) {
         const int c[3] = {x, y, z};
         auto body = [&](const auto& ua, const auto& ca, int p) {
@@ -397,12 +396,12 @@ __device__ __forceinline__ void sweep_pair_body(const Lv<T>& L, const T* __restr
         with_interior<T, KIND, ML>(L, u, x, y, z, body);
     };
     if (colour < 2) {
-        // red-black: exactly one node of the pair is active; its partner is copied in
-        // the same stores
+        // red-black: exactly one node of the pair is active (the partner's copy goes
+        // first: storing it beside the update measured slower)
         const int xa = x0 + ((x0 + y + z + colour) & 1);
         const int xi = (xa == x0) ? x0 + 1 : x0;
-        if (xa < xend) update(xa, xi < xend ? xi - xa : 0);
-        else if (xi < xend) copy(xi);
+        if (xi < xend) copy(xi);
+        if (xa < xend) update(xa, 0);
         return;
     }
     // eight colours or Jacobi: each node of the pair in turn
