@@ -340,8 +340,18 @@ int  elas_amr_destroy(elas_amr a);
 int  elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* info);
 
 /* ---- batches ---------------------------------------------------------------
- * Solve n independent grids of the same context, all in flight at once on the
- * context's stream (one launch per phase covers every grid).  info has n entries. */
+ * Solve n independent grids of the same context (mixed precision), all in flight at
+ * once on the context's stream.  When every grid has one moduli kind and one FP32
+ * moduli layout (and the red-black smoother is chosen), each phase of the cycle -- a
+ * half-sweep of one level, a residual, a restriction, a prolongation, the bottom solve,
+ * the load update, the FP64 correction -- is ONE launch over a device work list of the
+ * members taking part (a block finds its member by binary search over block offsets),
+ * so launches per refinement step depend on the number of levels, not of members.  Two
+ * refinement steps are captured as a CUDA graph once per batch composition and options
+ * (cached on the context until a member is destroyed, set up anew, or gets new loads)
+ * and replayed until every member has stopped on its own tolerance (device-side flags).
+ * Other batches run each member's own launches as parallel graph branches.  Every member
+ * computes exactly what its lone elas_solve computes.  info has n entries. */
 int  elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts,
                       elas_solve_info* info);
 

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <string>
 #include <deque>
+#include <functional>
 #include <mutex>
 #include <map>
 #include <vector>
@@ -38,6 +39,7 @@ struct elas_ctx_s {
     long long prof_count[ELAS_PROF_CLASSES] = {0, 0, 0, 0};
     std::vector<cudaStream_t> branch;        // streams of the batched graph's branches
     std::vector<cudaEvent_t> branch_ev;
+    struct BatchPlan* plan = nullptr;         // the batched engine's last plan and graph
 };
 
 namespace {
@@ -120,6 +122,7 @@ struct elas_grid_s {
     bool dirty = true;         // moduli or boundary types changed: rebuild everything
     bool rhs_dirty = true;     // only loads / boundary data changed: rebuild the right-hand side
     bool gram_valid = false;   // W^T W of the finest level (depends on boundary types, not moduli)
+    unsigned long long gen = 0;   // full set-ups so far (a cached batch plan checks it)
     // smoother and cycle of the solve in progress (from its options)
     int smoother = ELAS_SMOOTH_RB;
     int cycle = ELAS_CYCLE_V;
@@ -496,6 +499,7 @@ int setup(elas_grid g) {
     }
     g->dirty = false;
     g->rhs_dirty = false;
+    ++g->gen;
     return ELAS_OK;
 }
 
@@ -728,6 +732,14 @@ int copy_in(elas_ctx c, double* dst, const double* src, size_t count, int memspa
 
 }  // namespace
 
+namespace {
+void plan_free(elas_ctx c, BatchPlan* p);
+bool plan_has_member(const BatchPlan* p, elas_grid g);
+bool batch_engine_applies(elas_grid* grids, int n, const elas_solve_opts* o);
+int batch_engine(elas_grid* grids, int n, const elas_solve_opts* o, elas_solve_info* info,
+                 std::chrono::steady_clock::time_point t0);
+}  // namespace
+
 // ======================================================================================
 // C ABI
 // ======================================================================================
@@ -766,6 +778,8 @@ int elas_ctx_create(elas_ctx* out, int device, size_t hbm_budget_bytes, const el
 int elas_ctx_destroy(elas_ctx c) {
     if (!c) return ELAS_ERR_INVALID_ARG;
     cudaStreamSynchronize(c->stream);
+    plan_free(c, c->plan);
+    c->plan = nullptr;
     for (auto e : c->pool) cudaEventDestroy(e);
     for (auto st : c->branch) cudaStreamDestroy(st);
     for (auto e : c->branch_ev) cudaEventDestroy(e);
@@ -867,6 +881,10 @@ int elas_grid_destroy(elas_grid g) {
     if (!g) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = g->ctx;
     cudaStreamSynchronize(c->stream);
+    if (plan_has_member(c->plan, g)) {
+        plan_free(c, c->plan);
+        c->plan = nullptr;
+    }
     for (auto& a : g->allocs) ctx_free(c, a.first, a.second);
     cudaStreamSynchronize(c->stream);
     delete g;
@@ -1458,6 +1476,15 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
         if (!rc) rc = setup(grids[i]);
         if (rc) return rc;
     }
+    if (batch_engine_applies(grids, n, opts)) {
+        const int rc = batch_engine(grids, n, opts, info, t0);
+        for (int i = 0; i < n; ++i)
+            for (auto& v : grids[i]->lv) {
+                v.L64.active = nullptr;
+                v.L32.active = nullptr;
+            }
+        return rc;
+    }
     // per-member flags, counters and histories; every exit of the run clears the members'
     // flag pointers and frees them
     const size_t bytes = n * (2 * sizeof(int)) + 256 + n * (size_t)ELAS_HISTORY * sizeof(double);
@@ -1475,6 +1502,359 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
 }
 
 }  // extern "C"
+
+// ---- batched engine: per-phase launches over a work list, one captured graph per plan ----
+struct BatchPlan {
+    std::vector<elas_grid> members;
+    std::vector<unsigned long long> gen;
+    std::vector<double> r0;
+    int nu1 = 0, nu2 = 0, inner = 1, cycle = 0, max_cycles = 0, fixed = 0;
+    double tol = 0.0;
+    void* mem = nullptr;
+    size_t bytes = 0;
+    int* flags = nullptr;
+    int* counts = nullptr;
+    double* hist = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long per_replay = 0;
+    int steps_per_replay = 2;
+};
+
+namespace {
+
+bool plan_has_member(const BatchPlan* p, elas_grid g) {
+    if (!p) return false;
+    for (auto m : p->members)
+        if (m == g) return true;
+    return false;
+}
+
+void plan_free(elas_ctx c, BatchPlan* p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->mem) ctx_free(c, p->mem, p->bytes);
+    delete p;
+}
+
+// Task arrays of the plan: host bytes laid out as in the device arena.
+struct Arena {
+    std::vector<char> host;
+    size_t push(const void* data, size_t bytes) {
+        const size_t off = (host.size() + 255) & ~size_t(255);
+        host.resize(off + bytes);
+        std::memcpy(host.data() + off, data, bytes);
+        return off;
+    }
+};
+struct PhaseRef {   // a phase before upload: arena offsets of its tasks and offsets
+    BatchPhase ph;
+    size_t tasks_off = 0, starts_off = 0;
+};
+
+template <typename Task>
+PhaseRef make_phase(Arena& ar, int kind, const std::vector<Task>& tasks, int K, int ml, int colour = 0) {
+    PhaseRef r;
+    r.ph.kind = kind;
+    r.ph.n = (int)tasks.size();
+    r.ph.K = K;
+    r.ph.ml = ml;
+    r.ph.colour = colour;
+    if (tasks.empty()) return r;
+    std::vector<int> starts(tasks.size() + 1, 0);
+    for (size_t i = 0; i < tasks.size(); ++i) starts[i + 1] = starts[i] + batch_task_blocks(kind, &tasks[i]);
+    r.ph.blocks = starts.back();
+    r.tasks_off = ar.push(tasks.data(), sizeof(Task) * tasks.size());
+    r.starts_off = ar.push(starts.data(), sizeof(int) * starts.size());
+    return r;
+}
+
+// Whether the grids can share the per-phase kernels: mixed, one moduli kind and one FP32
+// moduli layout on every level, the red-black smoother.
+bool batch_engine_applies(elas_grid* grids, int n, const elas_solve_opts* o) {
+    if (o->smoother != ELAS_SMOOTH_RB) return false;
+    const int K = grids[0]->K;
+    const int ml = grids[0]->lv[0].L32.mlay;
+    for (int i = 0; i < n; ++i) {
+        elas_grid g = grids[i];
+        if (g->K != K || g->desc.half_moduli || !g->desc.mixed) return false;
+        for (auto& v : g->lv)
+            if (v.L32.mlay != ml) return false;
+    }
+    return ml == kModBlocked || ml == kModSplit;
+}
+
+bool plan_matches(const BatchPlan* p, elas_grid* grids, int n, const elas_solve_opts* o) {
+    if (!p || (int)p->members.size() != n) return false;
+    if (p->nu1 != o->nu1 || p->nu2 != o->nu2 || p->inner != (o->inner_cycles > 1 ? o->inner_cycles : 1) ||
+        p->cycle != o->cycle || p->tol != o->rel_tol ||
+        p->max_cycles != (o->fixed_cycles > 0 ? o->fixed_cycles : o->max_cycles) || p->fixed != o->fixed_cycles)
+        return false;
+    for (int i = 0; i < n; ++i)
+        if (p->members[i] != grids[i] || p->gen[i] != grids[i]->gen || p->r0[i] != grids[i]->r0) return false;
+    return true;
+}
+
+// Build the task arrays of one refinement step of every member (FP64 residual, the
+// load update and convergence test, `inner` FP32 V-cycles level by level, the FP64
+// correction), upload them, and capture two steps as a graph.
+int plan_build(elas_grid* grids, int n, const elas_solve_opts* o, BatchPlan** out) {
+    elas_ctx c = grids[0]->ctx;
+    BatchPlan* p = new BatchPlan();
+    p->nu1 = o->nu1;
+    p->nu2 = o->nu2;
+    p->inner = o->inner_cycles > 1 ? o->inner_cycles : 1;
+    p->cycle = o->cycle;
+    p->tol = o->rel_tol;
+    p->fixed = o->fixed_cycles;
+    p->max_cycles = o->fixed_cycles > 0 ? o->fixed_cycles : o->max_cycles;
+    const int H = ELAS_HISTORY;
+    const size_t flag_bytes = ((size_t)2 * n * sizeof(int) + 255) & ~size_t(255);
+    const size_t hist_bytes = ((size_t)n * H * sizeof(double) + 255) & ~size_t(255);
+    const int K = grids[0]->K;
+    const int ml = grids[0]->lv[0].L32.mlay == kModSplit ? kMlSplit : kMlDefault;
+    int depth = 0;
+    for (int i = 0; i < n; ++i) depth = std::max(depth, (int)grids[i]->lv.size());
+    // flags live at the start of the arena; the tasks point at them through each level's
+    // active pointer, so the arena's device address is needed first: allocate for the
+    // task bytes measured on a dry build, then build for real
+    Arena ar;
+    std::vector<PhaseRef> phases;
+    auto build = [&](char* dev_base) {
+        ar.host.assign(flag_bytes + hist_bytes, 0);
+        phases.clear();
+        int* flags = (int*)dev_base;
+        int* counts = flags + n;
+        double* hist = (double*)(dev_base + flag_bytes);
+        for (int i = 0; i < n; ++i)
+            for (auto& v : grids[i]->lv) v.L64.active = v.L32.active = flags + i;
+        NullInfo none{};
+        // FP64 residual (written as FP32 into the level-0 right-hand side) and finalize
+        std::vector<ResidTask<double, float>> r64;
+        std::vector<FinalizeTask> fin;
+        std::vector<CorrTask> corr;
+        for (int i = 0; i < n; ++i) {
+            elas_grid g = grids[i];
+            Level& L0 = g->lv[0];
+            const bool rm = L0.nf.m > 0;
+            ResidTask<double, float> t{L0.L64, L0.u, L0.f, rm ? L0.nf : none, rm ? g->alam : nullptr, L0.f32, g->partials};
+            r64.push_back(t);
+            FinalizeTask ft{};
+            ft.partials = g->partials;
+            ft.nblocks = batch_task_blocks(kPhaseResid64, &t);
+            ft.nf = L0.nf;
+            ft.Ginv = g->Ginv;
+            ft.G = g->G;
+            ft.lam = g->lam;
+            ft.dlam = g->dlam;
+            ft.alam = g->alam;
+            ft.adlam = g->adlam;
+            ft.out = g->status;
+            ft.bf = BatchFlags{flags + i, counts + i, hist + (size_t)i * H, H, g->r0, o->rel_tol, p->max_cycles};
+            fin.push_back(ft);
+            corr.push_back(CorrTask{L0.L64, L0.u, L0.u32});
+        }
+        const PhaseRef ph_r64 = make_phase(ar, kPhaseResid64, r64, K, ml);
+        PhaseRef ph_fin;
+        ph_fin.ph.kind = kPhaseFinalize;
+        ph_fin.ph.n = n;
+        ph_fin.ph.blocks = n;
+        ph_fin.tasks_off = ar.push(fin.data(), sizeof(FinalizeTask) * fin.size());
+        const PhaseRef ph_corr = make_phase(ar, kPhaseCorr, corr, K, ml);
+        // per-depth task arrays of the FP32 V-cycle
+        struct Depth {
+            PhaseRef zero, red, black, res, restr, prol, bzero, gather, matvec;
+        };
+        std::vector<Depth> D(depth);
+        for (int d = 0; d < depth; ++d) {
+            std::vector<ZeroTask<float>> zv, zb;
+            std::vector<SweepTask<float>> sr, sb;
+            std::vector<ResidTask<float, float>> rs;
+            std::vector<RestrictTask<float>> re;
+            std::vector<ProlongTask<float>> pr;
+            std::vector<BottomTask<float>> bt;
+            for (int i = 0; i < n; ++i) {
+                elas_grid g = grids[i];
+                const int nl = (int)g->lv.size();
+                if (d >= nl) continue;
+                Level& v = g->lv[d];
+                const size_t n3 = (size_t)3 * v.N;
+                const bool rm = d == 0 && g->lv[0].nf.m > 0;
+                const NullInfo& nf = rm ? g->lv[0].nf : none;
+                const double* lam = rm ? g->adlam : nullptr;
+                if (d == nl - 1) {
+                    zb.push_back(ZeroTask<float>{v.u32, n3, flags + i});
+                    bt.push_back(BottomTask<float>{v.L32, g->dofs, g->nfree, g->ntot, g->Ainv, v.f32, v.u32, g->bwork});
+                    continue;
+                }
+                Level& w = g->lv[d + 1];
+                zv.push_back(ZeroTask<float>{v.u32, n3, flags + i});
+                sr.push_back(SweepTask<float>{v.L32, v.u32, v.ua32, v.f32, nf, lam});
+                sb.push_back(SweepTask<float>{v.L32, v.ua32, v.u32, v.f32, nf, lam});
+                rs.push_back(ResidTask<float, float>{v.L32, v.u32, v.f32, nf, lam, v.r32, nullptr});
+                re.push_back(RestrictTask<float>{v.L32, w.L32, v.r32, w.f32, none, nullptr});
+                pr.push_back(ProlongTask<float>{v.L32, w.L32, w.u32, v.u32});
+            }
+            D[d].zero = make_phase(ar, kPhaseZero, zv, K, ml);
+            D[d].red = make_phase(ar, kPhaseSweep, sr, K, ml, 0);
+            D[d].black = make_phase(ar, kPhaseSweep, sb, K, ml, 1);
+            D[d].res = make_phase(ar, kPhaseResid32, rs, K, ml);
+            D[d].restr = make_phase(ar, kPhaseRestrict, re, K, ml);
+            D[d].prol = make_phase(ar, kPhaseProlong, pr, K, ml);
+            D[d].bzero = make_phase(ar, kPhaseZero, zb, K, ml);
+            D[d].gather = make_phase(ar, kPhaseGather, bt, K, ml);
+            D[d].matvec = make_phase(ar, kPhaseMatvec, bt, K, ml);
+        }
+        // one refinement step as a sequence of phases
+        auto smooth = [&](int d, int sweeps) {
+            for (int k = 0; k < sweeps; ++k) {
+                phases.push_back(D[d].red);
+                phases.push_back(D[d].black);
+            }
+        };
+        // the FP32 cycle of depth d (V, or F: the next depth's correction F then V)
+        std::function<void(int, bool, int)> cyc = [&](int d, bool zero, int kind) {
+            if (d >= depth) return;
+            phases.push_back(D[d].bzero);
+            phases.push_back(D[d].gather);
+            phases.push_back(D[d].matvec);
+            if (zero) phases.push_back(D[d].zero);
+            smooth(d, o->nu1);
+            phases.push_back(D[d].res);
+            phases.push_back(D[d].restr);
+            if (kind == ELAS_CYCLE_F) {
+                cyc(d + 1, true, ELAS_CYCLE_F);
+                cyc(d + 1, false, ELAS_CYCLE_V);
+            } else {
+                cyc(d + 1, true, ELAS_CYCLE_V);
+            }
+            phases.push_back(D[d].prol);
+            smooth(d, o->nu2);
+        };
+        phases.push_back(ph_r64);
+        phases.push_back(ph_fin);
+        for (int k = 0; k < p->inner; ++k) cyc(0, k == 0, o->cycle);
+        phases.push_back(ph_corr);
+    };
+    build(nullptr);
+    p->bytes = ar.host.size();
+    p->mem = ctx_alloc(c, p->bytes);
+    if (!p->mem) {
+        delete p;
+        return set_err(c, ELAS_ERR_ALLOC, "batch plan: allocation failed");
+    }
+    build((char*)p->mem);
+    p->flags = (int*)p->mem;
+    p->counts = p->flags + n;
+    p->hist = (double*)((char*)p->mem + flag_bytes);
+    for (int i = 0; i < n; ++i) {
+        p->members.push_back(grids[i]);
+        p->gen.push_back(grids[i]->gen);
+        p->r0.push_back(grids[i]->r0);
+    }
+    cudaStream_t main = c->stream;
+    cudaError_t ce = cudaMemcpyAsync(p->mem, ar.host.data(), p->bytes, cudaMemcpyHostToDevice, main);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(main);
+    // capture two refinement steps
+    const unsigned long long l0 = launch_count();
+    if (ce == cudaSuccess) ce = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        for (int rep = 0; rep < p->steps_per_replay; ++rep)
+            for (auto& r : phases) {
+                BatchPhase ph = r.ph;
+                ph.tasks = (const char*)p->mem + r.tasks_off;
+                ph.starts = (const int*)((const char*)p->mem + r.starts_off);
+                batch_phase_launch(ph, main);
+            }
+        ce = cudaStreamEndCapture(main, &p->graph);
+    }
+    p->per_replay = launch_count() - l0;
+    count_launch(-(int)p->per_replay);
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (ce != cudaSuccess) {
+        plan_free(c, p);
+        return set_err(c, ELAS_ERR_DEVICE, std::string("batch plan graph: ") + cudaGetErrorString(ce));
+    }
+    *out = p;
+    return ELAS_OK;
+}
+
+// Run a batch through the engine: per-call initial state, graph replays until every
+// member stops, results.
+int batch_engine(elas_grid* grids, int n, const elas_solve_opts* o, elas_solve_info* info,
+                 std::chrono::steady_clock::time_point t0) {
+    elas_ctx c = grids[0]->ctx;
+    cudaStream_t main = c->stream;
+    const bool prof = c->profile;
+    c->profile = false;
+    if (!plan_matches(c->plan, grids, n, o)) {
+        plan_free(c, c->plan);
+        c->plan = nullptr;
+        int rc = plan_build(grids, n, o, &c->plan);
+        if (rc) {
+            c->profile = prof;
+            return rc;
+        }
+    }
+    BatchPlan* p = c->plan;
+    for (int i = 0; i < n; ++i)
+        for (auto& v : grids[i]->lv) v.L64.active = v.L32.active = p->flags + i;
+    std::vector<int> h_flags(n, 1), h_counts(n, 0);
+    CUDA_TRY(c, cudaMemcpyAsync(p->flags, h_flags.data(), sizeof(int) * n, cudaMemcpyHostToDevice, main));
+    CUDA_TRY(c, cudaMemcpyAsync(p->counts, h_counts.data(), sizeof(int) * n, cudaMemcpyHostToDevice, main));
+    for (int i = 0; i < n; ++i) {
+        elas_grid g = grids[i];
+        Level& L0 = g->lv[0];
+        launch_dirichlet(L0.L64, boundary_data(g), L0.u, o->warm_start ? 1 : 0, main);
+        cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, main);
+        cudaMemsetAsync(g->alam, 0, sizeof(double) * kLoadDoubles, main);
+        cudaMemsetAsync(g->adlam, 0, sizeof(double) * kLoadDoubles, main);
+    }
+    CHECK_LAUNCH(c);
+    const int max_replays = p->max_cycles / p->steps_per_replay + 2;
+    cudaError_t ce = cudaSuccess;
+    for (int r = 0; r < max_replays; ++r) {
+        ce = cudaGraphLaunch(p->exec, main);
+        if (ce != cudaSuccess) break;
+        count_launch((int)p->per_replay);
+        cudaMemcpyAsync(h_flags.data(), p->flags, sizeof(int) * n, cudaMemcpyDeviceToHost, main);
+        ce = cudaStreamSynchronize(main);
+        if (ce != cudaSuccess) break;
+        bool any = false;
+        for (int i = 0; i < n; ++i) any |= h_flags[i] != 0;
+        if (!any) break;
+    }
+    c->profile = prof;
+    if (ce != cudaSuccess) return set_err(c, ELAS_ERR_DEVICE, std::string("batch replay: ") + cudaGetErrorString(ce));
+    const int H = ELAS_HISTORY;
+    std::vector<double> h_hist((size_t)n * H);
+    CUDA_TRY(c, cudaMemcpyAsync(h_counts.data(), p->counts, sizeof(int) * n, cudaMemcpyDeviceToHost, main));
+    CUDA_TRY(c, cudaMemcpyAsync(h_hist.data(), p->hist, sizeof(double) * n * H, cudaMemcpyDeviceToHost, main));
+    for (int i = 0; i < n; ++i) {
+        const int rr = remove_rigid(grids[i]);
+        if (rr) return rr;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(main));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int worst = ELAS_OK;
+    for (int i = 0; i < n; ++i) {
+        const int cnt = h_counts[i] < H ? h_counts[i] : H;
+        for (int k = 0; k < cnt; ++k) info[i].rel_history[k] = h_hist[(size_t)i * H + k];
+        info[i].cycles = h_counts[i] > 0 ? h_counts[i] - 1 : 0;
+        info[i].rel_residual = cnt > 0 ? h_hist[(size_t)i * H + cnt - 1] : 0.0;
+        info[i].r0 = grids[i]->r0;
+        info[i].nlam = grids[i]->lv[0].nf.m;
+        info[i].seconds = secs;
+        const bool ok = o->fixed_cycles > 0 ? true : info[i].rel_residual <= o->rel_tol;
+        info[i].status = ok ? ELAS_OK : ELAS_ERR_NOT_CONVERGED;
+        if (!ok && worst == ELAS_OK) worst = ELAS_ERR_NOT_CONVERGED;
+    }
+    if (worst) set_err(c, worst, "a batch member did not reach the tolerance");
+    return worst;
+}
+
+}  // namespace
 
 namespace {
 int batch_run(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_info* info, void* mem,

@@ -136,6 +136,98 @@ struct MeanStrain {
 void launch_stress(const Lv<double>& L, const double* u, const double* eps0, const MeanStrain& mean, double* out,
                    cudaStream_t s);
 
+// ---- batched engine: one launch per phase over a work list of members ------------------
+// Each phase (a half-sweep of one level, a residual, a restriction, ...) of a batch of
+// grids is one launch.  Its tasks (one per member taking part) sit in device memory with
+// their block offsets; a block finds its task by binary search over the offsets and runs
+// the same per-node code as the single-grid kernels on that member's level, so every
+// member computes exactly what it computes alone.
+enum : int {
+    kPhaseSweep = 0,      // SweepTask<float>: half-sweep (colour in the phase)
+    kPhaseResid32 = 1,    // ResidTask<float, float>: FP32 residual, no norm
+    kPhaseResid64 = 2,    // ResidTask<double, float>: FP64 residual written as FP32, with partials
+    kPhaseRestrict = 3,   // RestrictTask<float>
+    kPhaseProlong = 4,    // ProlongTask<float>
+    kPhaseZero = 5,       // ZeroTask<float>
+    kPhaseGather = 6,     // BottomTask<float>: right-hand side of the bottom solve
+    kPhaseMatvec = 7,     // BottomTask<float>: dense inverse times it
+    kPhaseFinalize = 8,   // FinalizeTask
+    kPhaseCorr = 9,       // CorrTask: FP64 u += FP32 e
+};
+template <typename T>
+struct SweepTask {
+    Lv<T> L;
+    const T* u;
+    T* uo;
+    const T* f;
+    NullInfo nf;
+    const double* lam;
+};
+template <typename T, typename TR>
+struct ResidTask {
+    Lv<T> L;
+    const T* u;
+    const T* f;
+    NullInfo nf;
+    const double* lam;
+    TR* r;
+    double* partials;
+};
+template <typename T>
+struct RestrictTask {
+    Lv<T> Lf, Lc;
+    const T* r;
+    T* fc;
+    NullInfo nf;
+    const double* dlam;
+};
+template <typename T>
+struct ProlongTask {
+    Lv<T> Lf, Lc;
+    const T* ec;
+    T* u;
+};
+template <typename T>
+struct ZeroTask {
+    T* a;
+    size_t n;
+    const int* active;
+};
+template <typename T>
+struct BottomTask {
+    Lv<T> L;
+    const int* dofs;
+    int nfree, ntot;
+    const double* Ainv;
+    const T* f;
+    T* u;
+    double* work;
+};
+struct FinalizeTask {
+    const double* partials;
+    int nblocks;
+    NullInfo nf;
+    const double *Ginv, *G;
+    double *lam, *dlam, *alam, *adlam, *out;
+    BatchFlags bf;
+};
+struct CorrTask {
+    Lv<double> L;
+    double* u;
+    const float* e;
+};
+// A phase ready to launch: kind, member count, tasks and block offsets in device memory
+// (n + 1 offsets), total blocks, the half-sweep colour and the moduli variant of the
+// sweep and residual kernels (moduli kind 2 or 21 and layout kMl*).
+struct BatchPhase {
+    int kind = 0, n = 0, blocks = 0, colour = 0, K = 2, ml = 0;
+    const void* tasks = nullptr;
+    const int* starts = nullptr;
+};
+// Blocks one task of a phase takes (the member's own block partition).
+int batch_task_blocks(int kind, const void* task);
+void batch_phase_launch(const BatchPhase& ph, cudaStream_t s);
+
 // ALU peak microbenchmark: one launch of independent FMA chains on every SM (precision 0 =
 // FP64, 1 = FP32); returns the FLOPs of the launch and its device time in *ms.  out: a
 // device buffer of 256 elements (never written in practice).

@@ -27,9 +27,9 @@ __device__ __forceinline__ void coords_of(int p, const int n[3], int c[3]) {
     c[2] = r / n[1];
 }
 
-// Block-wide sum of `width` doubles per thread into partials[blockIdx * kPartialStride + w].
+// Block-wide sum of `width` doubles per thread into partials[bid * kPartialStride + w].
 template <int MAXW>
-__device__ __forceinline__ void block_reduce_store(double (&v)[MAXW], int width, double* partials) {
+__device__ __forceinline__ void block_reduce_store_at(double (&v)[MAXW], int width, double* partials, int bid) {
     __shared__ double sm[kBlock / 32][MAXW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -48,9 +48,14 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[MAXW], int width,
             double x = (lane < kBlock / 32) ? sm[lane][w] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) partials[blockIdx.x * kPartialStride + w] = x;
+            if (lane == 0) partials[(size_t)bid * kPartialStride + w] = x;
         }
     }
+}
+
+template <int MAXW>
+__device__ __forceinline__ void block_reduce_store(double (&v)[MAXW], int width, double* partials) {
+    block_reduce_store_at<MAXW>(v, width, partials, blockIdx.x);
 }
 
 // Fixed-order sum of the 7-wide block partials by one block of kSumThreads threads:
@@ -729,7 +734,7 @@ __global__ void __launch_bounds__(kBlock) k_half_sweep_face(Lv<T> L, const T* __
 }
 
 template <typename T, int A>
-inline size_t face_count(const Lv<T>& L) {
+__host__ __device__ inline size_t face_count(const Lv<T>& L) {
     if (L.per[A]) return 0;
     int nf, ns;
     face_extent<T, A>(L, nf, ns);
@@ -764,13 +769,12 @@ struct BndSegs {
 };
 
 template <typename T>
-inline BndSegs bnd_segs(const Lv<T>& L, int bs) {
-    auto nb = [bs](size_t n) { return (int)((n + bs - 1) / bs); };
+__host__ __device__ inline BndSegs bnd_segs(const Lv<T>& L, int bs) {
     BndSegs g;
-    g.e = nb((size_t)L.nbnd * 32);
-    g.f0 = g.e + nb(face_count<T, 0>(L));
-    g.f1 = g.f0 + nb(face_count<T, 1>(L));
-    g.f2 = g.f1 + nb(face_count<T, 2>(L));
+    g.e = (int)(((size_t)L.nbnd * 32 + bs - 1) / bs);
+    g.f0 = g.e + (int)((face_count<T, 0>(L) + bs - 1) / bs);
+    g.f1 = g.f0 + (int)((face_count<T, 1>(L) + bs - 1) / bs);
+    g.f2 = g.f1 + (int)((face_count<T, 2>(L) + bs - 1) / bs);
     return g;
 }
 
@@ -984,10 +988,9 @@ __device__ __forceinline__ void restrict_weights(const Lv<T>& Lc, int d, int I, 
 }
 
 template <typename T>
-__global__ void k_restrict(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ r, T* __restrict__ fc, NullInfo nf,
-                           const double* __restrict__ dlam) {
-    if (Lf.active && *Lf.active == 0) return;
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void restrict_body(const Lv<T>& Lf, const Lv<T>& Lc, const T* __restrict__ r,
+                                              T* __restrict__ fc, const NullInfo& nf, const double* __restrict__ dlam,
+                                              int P) {
     if (P >= Lc.N) return;
     int C[3];
     coords_of(P, Lc.n, C);
@@ -1025,9 +1028,15 @@ __global__ void k_restrict(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ r, T* __res
 }
 
 template <typename T>
-__global__ void k_prolong_add(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ ec, T* __restrict__ u) {
+__global__ void k_restrict(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ r, T* __restrict__ fc, NullInfo nf,
+                           const double* __restrict__ dlam) {
     if (Lf.active && *Lf.active == 0) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    restrict_body<T>(Lf, Lc, r, fc, nf, dlam, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_body(const Lv<T>& Lf, const Lv<T>& Lc, const T* __restrict__ ec,
+                                             T* __restrict__ u, int p) {
     if (p >= Lf.N) return;
     int c[3];
     coords_of(p, Lf.n, c);
@@ -1069,6 +1078,12 @@ __global__ void k_prolong_add(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ ec, T* _
         }
         u[i * Lf.N + p] += v;
     }
+}
+
+template <typename T>
+__global__ void k_prolong_add(Lv<T> Lf, Lv<T> Lc, const T* __restrict__ ec, T* __restrict__ u) {
+    if (Lf.active && *Lf.active == 0) return;
+    prolong_body<T>(Lf, Lc, ec, u, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename T>
@@ -1144,15 +1159,20 @@ __global__ void k_to_moduli_copy(const double* __restrict__ in, TO* __restrict__
 }
 
 template <typename TE>
-__global__ void k_add_correction(Lv<double> L, double* __restrict__ u, const TE* __restrict__ e) {
-    if (L.active && *L.active == 0) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void add_correction_body(const Lv<double>& L, double* __restrict__ u,
+                                                    const TE* __restrict__ e, int p) {
     if (p >= L.N) return;
     int c[3];
     coords_of(p, L.n, c);
     const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
     for (int i = 0; i < 3; ++i)
         if (row_type(L, ni, i) != ROW_DIRICHLET) u[i * L.N + p] += (double)e[i * L.N + p];
+}
+
+template <typename TE>
+__global__ void k_add_correction(Lv<double> L, double* __restrict__ u, const TE* __restrict__ e) {
+    if (L.active && *L.active == 0) return;
+    add_correction_body<TE>(L, u, e, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1281,11 +1301,11 @@ __global__ void k_bottom_gather(Lv<T> L, const int* __restrict__ dofs, int nfree
     b[i] = i < nfree ? (double)f[dofs[i]] : 0.0;
 }
 
+// Row `row` of the bottom solve: u[dofs[row]] = sum_k Ainv[row][k] b[k] (a whole block).
 template <typename T>
-__global__ void k_bottom_matvec(Lv<T> L, const int* __restrict__ dofs, int nfree, int ntot,
-                                const double* __restrict__ Ainv, const double* __restrict__ b, T* __restrict__ u) {
-    if (L.active && *L.active == 0) return;
-    const int row = blockIdx.x;
+__device__ __forceinline__ void bottom_matvec_body(const int* __restrict__ dofs, int nfree, int ntot,
+                                                   const double* __restrict__ Ainv, const double* __restrict__ b,
+                                                   T* __restrict__ u, int row) {
     if (row >= nfree) return;
     double acc = 0.0;
     for (int k = threadIdx.x; k < ntot; k += blockDim.x) acc += Ainv[(size_t)row * ntot + k] * b[k];
@@ -1302,6 +1322,13 @@ __global__ void k_bottom_matvec(Lv<T> L, const int* __restrict__ dofs, int nfree
 }
 
 template <typename T>
+__global__ void k_bottom_matvec(Lv<T> L, const int* __restrict__ dofs, int nfree, int ntot,
+                                const double* __restrict__ Ainv, const double* __restrict__ b, T* __restrict__ u) {
+    if (L.active && *L.active == 0) return;
+    bottom_matvec_body<T>(dofs, nfree, ntot, Ainv, b, u, blockIdx.x);
+}
+
+template <typename T>
 __global__ void k_zero(T* __restrict__ a, size_t n) {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = T(0);
@@ -1314,12 +1341,11 @@ __global__ void k_zero(T* __restrict__ a, size_t n) {
 //   W^T r = basis^T mom,  dlam = G^-1 W^T r,  lam += dlam,
 //   a_lam = basis lam, a_dlam = basis dlam (the loads as t + w x d),
 //   ||r - dlam.W||^2 = ||r||^2 - 2 dlam.W^T r + dlam^T G dlam.
-#ifdef ELAS_KERNELS_TU
-__global__ void k_finalize(const double* __restrict__ partials, int nblocks, NullInfo nf,
-                           const double* __restrict__ Ginv, const double* __restrict__ G,
-                           double* __restrict__ lam, double* __restrict__ dlam, double* __restrict__ alam,
-                           double* __restrict__ adlam, double* __restrict__ out, int update_lam, BatchFlags bf) {
-    if (bf.active && *bf.active == 0) return;
+__device__ __forceinline__ void finalize_body(const double* __restrict__ partials, int nblocks, const NullInfo& nf,
+                                              const double* __restrict__ Ginv, const double* __restrict__ G,
+                                              double* __restrict__ lam, double* __restrict__ dlam,
+                                              double* __restrict__ alam, double* __restrict__ adlam,
+                                              double* __restrict__ out, int update_lam, const BatchFlags& bf) {
     __shared__ double sm[kSumThreads / 32][7];
     sum_partials_block(partials, nblocks, sm);
     if (threadIdx.x == 0) {
@@ -1369,6 +1395,15 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, Nul
             if (!(rel > bf.tol) || k >= bf.max_cycles || !isfinite(rel)) *bf.active = 0;
         }
     }
+}
+
+#ifdef ELAS_KERNELS_TU
+__global__ void k_finalize(const double* __restrict__ partials, int nblocks, NullInfo nf,
+                           const double* __restrict__ Ginv, const double* __restrict__ G,
+                           double* __restrict__ lam, double* __restrict__ dlam, double* __restrict__ alam,
+                           double* __restrict__ adlam, double* __restrict__ out, int update_lam, BatchFlags bf) {
+    if (bf.active && *bf.active == 0) return;
+    finalize_body(partials, nblocks, nf, Ginv, G, lam, dlam, alam, adlam, out, update_lam, bf);
 }
 #endif
 

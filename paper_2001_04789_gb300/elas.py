@@ -555,16 +555,17 @@ class Amr:
 
 
 def batch_solve(grids, precision=MIXED, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False,
-                fixed_cycles=0, raise_on_error=True):
-    """Solve every grid of one context together: one CUDA graph replays a few
-    refinement steps of all members as parallel branches; members stop on their
-    own tolerance.  Returns one info dict per grid."""
+                fixed_cycles=0, raise_on_error=True, inner_cycles=1, cycle=None):
+    """Solve every grid of one context together: one launch per phase of the cycle covers
+    every member (grids of one moduli kind and layout; otherwise the members' own launches
+    run as parallel branches), a captured CUDA graph replays refinement steps, and members
+    stop on their own tolerance.  Returns one info dict per grid."""
     if not grids:
         return []
     n = len(grids)
     arr = (C.c_void_p * n)(*[g.h for g in grids])
     infos = (SolveInfo * n)()
-    o = _opts(precision, rel_tol, max_cycles, nu1, nu2, warm_start, fixed_cycles)
+    o = _opts(precision, rel_tol, max_cycles, nu1, nu2, warm_start, fixed_cycles, False, inner_cycles, None, cycle)
     rc = lib().elas_batch_solve(arr, n, C.byref(o), infos)
     if rc != OK and raise_on_error and rc != ERR_NOT_CONVERGED:
         raise ElasError(rc, grids[0].ctx.error())

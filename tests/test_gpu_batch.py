@@ -69,3 +69,66 @@ def test_batch_warm_start_from_converged_members_stops_at_once(E, ctx):
     assert all(i["cycles"] == 0 for i in infos)
     for g in grids:
         g.close()
+
+
+# --------------------------------------------------------------------------
+# the per-phase engine: batches of one moduli kind and FP32 layout
+# --------------------------------------------------------------------------
+
+def iso_members():
+    return [M.ellipsoid_rve(17, seed=1), M.ellipsoid_rve(33, seed=2), M.eshelby_sphere(17),
+            M.penny_crack(17, width=3.0 / 16, clamp_lateral=True), M.ellipsoid_rve(33, seed=7)]
+
+
+def gen_members():
+    from test_gpu_parity import mixed_bc_problem
+    return [M.polycrystal(17, grains=4, seed=5), M.polycrystal(33, grains=5, seed=6), mixed_bc_problem()]
+
+
+@pytest.mark.parametrize("family", ["iso", "gen21_split"])
+@pytest.mark.parametrize("cycle", [0, 1])
+def test_engine_members_are_bitwise_their_lone_solves(E, ctx, family, cycle):
+    """One launch per phase over all members: each member runs exactly the kernels of
+    its lone solve, so results and residual histories are identical bit for bit."""
+    probs = iso_members() if family == "iso" else gen_members()
+    grids = [E.grid_from_problem(ctx, p, mixed=True) for p in probs]
+    infos = E.batch_solve(grids, precision=E.MIXED, rel_tol=1e-8, max_cycles=100, inner_cycles=2, cycle=cycle)
+    batch_u = [g.displacement() for g in grids]
+    for g, info, ub in zip(grids, infos, batch_u):
+        assert info["status"] == 0
+        alone = g.solve(precision=E.MIXED, rel_tol=1e-8, max_cycles=100, inner_cycles=2, cycle=cycle)
+        assert np.array_equal(g.displacement(), ub)
+        assert alone["rel_history"] == info["rel_history"] and alone["cycles"] == info["cycles"]
+    for g in grids:
+        g.close()
+
+
+def test_engine_launches_do_not_grow_with_member_count(E, ctx):
+    """Launches per refinement step depend on the levels, not on how many members."""
+    counts = {}
+    for m in (2, 6):
+        grids = [E.grid_from_problem(ctx, M.ellipsoid_rve(33, seed=10 + i), mixed=True) for i in range(m)]
+        E.batch_solve(grids, precision=E.MIXED, rel_tol=0.0, fixed_cycles=2)       # plan and graph
+        l0 = E.launch_count()
+        E.batch_solve(grids, precision=E.MIXED, rel_tol=0.0, fixed_cycles=2)
+        counts[m] = E.launch_count() - l0
+        for g in grids:
+            g.close()
+    # the per-call initial state is per member (3 launches each); the replayed steps are not
+    assert counts[6] - counts[2] <= 4 * 3, counts
+
+
+def test_engine_plan_follows_new_loads(E, ctx):
+    """A cached plan is rebuilt when a member's loads (and so its r0) change."""
+    probs = iso_members()[:3]
+    grids = [E.grid_from_problem(ctx, p, mixed=True) for p in probs]
+    E.batch_solve(grids, precision=E.MIXED, rel_tol=1e-8)
+    p2 = M.ellipsoid_rve(17, seed=1)
+    p2.mean_strain = -2.0 * p2.mean_strain
+    grids[0].set_mean_strain(p2.mean_strain)
+    infos = E.batch_solve(grids, precision=E.MIXED, rel_tol=1e-8)
+    ub = grids[0].displacement()
+    alone = grids[0].solve(precision=E.MIXED, rel_tol=1e-8)
+    assert np.array_equal(grids[0].displacement(), ub) and alone["cycles"] == infos[0]["cycles"]
+    for g in grids:
+        g.close()
