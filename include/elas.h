@@ -371,6 +371,12 @@ typedef struct elas_server_s* elas_server;
 int  elas_server_create(elas_ctx ctx, int max_active, elas_server* out);
 int  elas_server_destroy(elas_server s);
 int  elas_server_submit(elas_server s, elas_grid g, const elas_solve_opts* opts, long long* ticket);
+/* A composite AMR solve as a request (Section 3.2; FP64 composite cycles, reading as set
+ * on the elas_amr): admitted into a free slot like a grid request; each server step runs
+ * one composite cycle of it, interleaved with the other requests, and it retires at
+ * opts->rel_tol (composite norm) or max_cycles.  warm_start keeps the levels' current
+ * displacements.  Results are the same as elas_amr_solve's (same kernels, same order). */
+int  elas_server_submit_amr(elas_server s, elas_amr a, const elas_solve_opts* opts, long long* ticket);
 /* One step; *active and *waiting receive the counts after it. */
 int  elas_server_step(elas_server s, int* active, int* waiting);
 /* 1 when the request is done (info filled, latency from submit to retirement in

@@ -2042,7 +2042,8 @@ void amr_sync(elas_amr a, int l, const double* ffield, double* cfield) {
     else launch_amr_inject(Lf, a->box[l], Lc, a->box[l - 1], ffield, cfield, s);
 }
 
-int amr_norm(elas_amr a, double* out) {
+// Sum of the squared composite residual into g[0]->status[0] (enqueued only).
+int amr_norm_enqueue(elas_amr a) {
     const int nl = (int)a->g.size();
     elas_ctx c = a->g[0]->ctx;
     cudaStream_t s = c->stream;
@@ -2052,8 +2053,14 @@ int amr_norm(elas_amr a, double* out) {
                                a->partials + (size_t)off * kPartialStride, s);
     launch_sum_partials(a->partials, off, 1, a->g[0]->status, s);
     CHECK_LAUNCH(c);
+    return ELAS_OK;
+}
+
+int amr_norm(elas_amr a, double* out) {
+    int rc = amr_norm_enqueue(a);
+    if (rc) return rc;
     double st[1];
-    int rc = read_status(a->g[0], st, 1);
+    rc = read_status(a->g[0], st, 1);
     if (rc) return rc;
     *out = std::sqrt(st[0]);
     return ELAS_OK;
@@ -2203,13 +2210,15 @@ int elas_amr_destroy(elas_amr a) {
     return ELAS_OK;
 }
 
-int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* info) {
-    if (!a || !opts || !info) return ELAS_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+// Set-up of a composite solve: covered coarse moduli (after changes), every level's
+// set-up, the initial state (Dirichlet data; the free values kept for a warm start) and
+// the covered coarse nodes from the fine ones.
+int amr_prepare(elas_amr a, bool warm) {
     const int nl = (int)a->g.size();
     elas_ctx c = a->g[0]->ctx;
-    cudaSetDevice(c->device);
-    std::memset(info, 0, sizeof(*info));
-    const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = c->stream;
     bool dirty = false;
     for (auto g : a->g) dirty |= g->dirty;
@@ -2230,9 +2239,26 @@ int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* inf
         if (rc) return rc;
     }
     if (a->g[0]->lv[0].nf.m > 0) return set_err(c, ELAS_ERR_STATE, "AMR solve needs a problem without free rigid modes");
-    for (int l = 0; l < nl; ++l) launch_dirichlet(a->g[l]->lv[0].L64, boundary_data(a->g[l]), a->g[l]->lv[0].u, 0, s);
+    for (int l = 0; l < nl; ++l)
+        launch_dirichlet(a->g[l]->lv[0].L64, boundary_data(a->g[l]), a->g[l]->lv[0].u, warm ? 1 : 0, s);
     for (int l = nl - 1; l >= 1; --l) amr_sync(a, l, a->g[l]->lv[0].u, a->g[l - 1]->lv[0].u);
-    int rc = amr_composite_residual(a);
+    CHECK_LAUNCH(c);
+    return ELAS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* info) {
+    if (!a || !opts || !info) return ELAS_ERR_INVALID_ARG;
+    elas_ctx c = a->g[0]->ctx;
+    cudaSetDevice(c->device);
+    std::memset(info, 0, sizeof(*info));
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = c->stream;
+    int rc = amr_prepare(a, opts->warm_start != 0);
+    if (rc) return rc;
+    rc = amr_composite_residual(a);
     if (rc) return rc;
     double r0 = 0.0;
     if ((rc = amr_norm(a, &r0))) return rc;
@@ -2286,9 +2312,15 @@ namespace {
 struct ServerReq {
     long long ticket;
     elas_grid g;
+    elas_amr a = nullptr;       // composite AMR request (g = its level-0 grid)
     elas_solve_opts opts;
     int slot = -1;
     std::chrono::steady_clock::time_point t_submit;
+    // AMR requests: convergence is followed on the host
+    bool started = false;
+    int cycles = 0;
+    double r0 = 0.0;
+    std::vector<double> hist;
 };
 struct ServerDone {
     elas_solve_info info;
@@ -2310,6 +2342,7 @@ struct elas_server_s {
     void* mem = nullptr;
     size_t bytes = 0;
     std::vector<int> h_flags, h_counts;
+    double* h_norm = nullptr;   // pinned: the composite residual norms of AMR requests, per slot
 };
 
 extern "C" {
@@ -2331,6 +2364,11 @@ int elas_server_create(elas_ctx c, int max_active, elas_server* out) {
     for (int i = max_active - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->h_flags.assign(max_active, 0);
     s->h_counts.assign(max_active, 0);
+    if (cudaMallocHost(&s->h_norm, sizeof(double) * max_active) != cudaSuccess) {
+        ctx_free(c, s->mem, s->bytes);
+        delete s;
+        return set_err(c, ELAS_ERR_DEVICE, "server: pinned host buffer");
+    }
     *out = s;
     return ELAS_OK;
 }
@@ -2341,7 +2379,26 @@ int elas_server_destroy(elas_server s) {
     for (auto& r : s->active)
         for (auto& v : r.g->lv) v.L64.active = v.L32.active = nullptr;
     ctx_free(s->ctx, s->mem, s->bytes);
+    if (s->h_norm) cudaFreeHost(s->h_norm);
     delete s;
+    return ELAS_OK;
+}
+
+int elas_server_submit_amr(elas_server s, elas_amr a, const elas_solve_opts* opts, long long* ticket) {
+    if (!s || !a || !opts || !ticket) return ELAS_ERR_INVALID_ARG;
+    if (a->g[0]->ctx != s->ctx) return set_err(s->ctx, ELAS_ERR_INVALID_ARG, "AMR request of another context");
+    for (const auto& w : s->waiting)
+        if (w.a == a) return set_err(s->ctx, ELAS_ERR_STATE, "composite solve already has a waiting request");
+    for (const auto& r : s->active)
+        if (r.a == a) return set_err(s->ctx, ELAS_ERR_STATE, "composite solve already has an active request");
+    ServerReq r;
+    r.ticket = s->next++;
+    r.g = a->g[0];
+    r.a = a;
+    r.opts = *opts;
+    r.t_submit = std::chrono::steady_clock::now();
+    s->waiting.push_back(r);
+    *ticket = r.ticket;
     return ELAS_OK;
 }
 
@@ -2375,8 +2432,13 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
         ServerReq r = s->waiting.front();
         s->waiting.pop_front();
         elas_grid g = r.g;
-        int rc = take_cycle_opts(g, &r.opts);
-        if (!rc) rc = setup(g);
+        int rc = ELAS_OK;
+        if (r.a) {
+            rc = amr_prepare(r.a, r.opts.warm_start != 0);
+        } else {
+            rc = take_cycle_opts(g, &r.opts);
+            if (!rc) rc = setup(g);
+        }
         if (rc) {
             ServerDone d{};
             d.info.status = rc;
@@ -2387,6 +2449,10 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
         }
         r.slot = s->free_slots.back();
         s->free_slots.pop_back();
+        if (r.a) {
+            s->active.push_back(r);
+            continue;
+        }
         Level& L0 = g->lv[0];
         launch_dirichlet(L0.L64, boundary_data(g), L0.u, r.opts.warm_start ? 1 : 0, main);
         cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, main);
@@ -2420,6 +2486,15 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
             elas_grid g = r.g;
             Level& L0 = g->lv[0];
             c->stream = c->branch[k % S];
+            if (r.a) {
+                // one composite cycle (the first step only evaluates the initial residual),
+                // then the composite residual and its norm
+                if (r.started) amr_cycle(r.a, r.opts.nu1, r.opts.nu2);
+                amr_composite_residual(r.a);
+                amr_norm_enqueue(r.a);
+                cudaMemcpyAsync(s->h_norm + r.slot, g->status, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+                continue;
+            }
             const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
             int nb = 0;
             launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, nf0 ? g->alam : nullptr, L0.f32, g->partials, &nb,
@@ -2447,6 +2522,37 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
         // retire
         std::vector<ServerReq> keep;
         for (auto& r : s->active) {
+            if (r.a) {
+                const double nr = std::sqrt(s->h_norm[r.slot]);
+                if (!r.started) {
+                    r.started = true;
+                    r.r0 = nr;
+                } else {
+                    ++r.cycles;
+                }
+                const double rel = r.r0 > 0 ? nr / r.r0 : 0.0;
+                r.hist.push_back(rel);
+                const int maxc = r.opts.fixed_cycles > 0 ? r.opts.fixed_cycles : r.opts.max_cycles;
+                const bool bad = !std::isfinite(rel) || rel > 1e12;
+                const bool stop = bad || r.cycles >= maxc || (r.opts.fixed_cycles <= 0 && rel <= r.opts.rel_tol);
+                if (!stop) {
+                    keep.push_back(r);
+                    continue;
+                }
+                ServerDone d{};
+                const int cnt = (int)r.hist.size() < ELAS_HISTORY ? (int)r.hist.size() : ELAS_HISTORY;
+                for (int k = 0; k < cnt; ++k) d.info.rel_history[k] = r.hist[k];
+                d.info.cycles = r.cycles;
+                d.info.rel_residual = rel;
+                d.info.r0 = r.r0;
+                const bool ok = r.opts.fixed_cycles > 0 || rel <= r.opts.rel_tol;
+                d.info.status = bad ? ELAS_ERR_DIVERGED : (ok ? ELAS_OK : ELAS_ERR_NOT_CONVERGED);
+                d.latency = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_submit).count();
+                d.info.seconds = d.latency;
+                s->done[r.ticket] = d;
+                s->free_slots.push_back(r.slot);
+                continue;
+            }
             if (s->h_flags[r.slot]) {
                 keep.push_back(r);
                 continue;

@@ -126,6 +126,7 @@ def lib():
         "elas_autotune_load": (ip, [C.c_char_p]),
         "elas_server_destroy": (ip, [vp]),
         "elas_server_submit": (ip, [vp, vp, C.POINTER(SolveOpts), C.POINTER(C.c_longlong)]),
+        "elas_server_submit_amr": (ip, [vp, vp, C.POINTER(SolveOpts), C.POINTER(C.c_longlong)]),
         "elas_server_step": (ip, [vp, C.POINTER(ip), C.POINTER(ip)]),
         "elas_server_poll": (ip, [vp, C.c_longlong, C.POINTER(SolveInfo), dp]),
         "elas_amr_destroy": (ip, [vp]),
@@ -584,6 +585,12 @@ class Server:
     def submit(self, grid: Grid, **kw):
         t = C.c_longlong()
         self.ctx.check(lib().elas_server_submit(self.h, grid.h, C.byref(_opts(MIXED, **kw)), C.byref(t)))
+        return t.value
+
+    def submit_amr(self, amr, **kw):
+        """A composite AMR solve (an ``Amr``) as a request: one composite cycle per step."""
+        t = C.c_longlong()
+        self.ctx.check(lib().elas_server_submit_amr(self.h, amr.h, C.byref(_opts(FP64, **kw)), C.byref(t)))
         return t.value
 
     def step(self):

@@ -160,14 +160,19 @@ def iso_to_upper21(lam, mu):
 # --------------------------------------------------------------------------
 
 def eshelby_sphere(n=33, radius=0.2, width_cells=3.0, E_matrix=1.0, E_incl=2.0, nu=0.3,
-                   eps_star=1e-3, centre=(0.5, 0.5, 0.5)):
+                   eps_star=1e-3, centre=(0.5, 0.5, 0.5), box=None, width=None):
     """Spherical Eshelby inhomogeneity on the unit cube (Section 4.1 analogue):
-    tanh-blended isotropic moduli, eigenstrain eps_star * phi * I, u = 0 on all faces."""
-    p = Problem(n=(n, n, n), name=f"eshelby_sphere_{n}")
+    tanh-blended isotropic moduli, eigenstrain eps_star * phi * I, u = 0 on all faces.
+    ``box = (n3, lo3, hi3)`` evaluates the same fields on a sub-box (AMR levels); the
+    profile width is then ``width`` (physical), else width_cells node spacings."""
+    if box is None:
+        p = Problem(n=(n, n, n), name=f"eshelby_sphere_{n}")
+    else:
+        p = Problem(n=tuple(box[0]), lo=tuple(box[1]), hi=tuple(box[2]), name="eshelby_sphere_box")
     X, Y, Z = p.coords()
-    h = p.h[0]
+    w = width if width is not None else width_cells * p.h[0]
     r = np.sqrt((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2)
-    phi = tanh_profile(r - radius, width_cells * h)
+    phi = tanh_profile(r - radius, w)
     lam, mu = lame(E_matrix * (1.0 - phi) + E_incl * phi, nu)
     p.moduli_kind = MODULI_ISO
     p.moduli = np.stack([lam, mu])
@@ -206,18 +211,22 @@ def eshelby_ellipsoid(n=129, half_width=4.0, axes=(1.0, 0.75, 0.5), E=210.0, nu=
 
 
 def polycrystal(n=257, grains=20, seed=0, c11=1.68, c12=1.21, c44=0.75, width_cells=4.0,
-                strain=1e-3):
+                strain=1e-3, box=None, width=None, clamp=False):
     """Voronoi polycrystal (Section 4.3 analogue): rotated cubic grains blended by the
     linear mixture rule over tanh grain-boundary profiles; u_x = -+strain/2 on the x
-    faces, zero shear traction there, traction-free y and z faces."""
+    faces, zero shear traction there, traction-free y and z faces (with ``clamp`` the
+    x faces hold u_y = u_z = 0 too, leaving no rigid modes).  ``box = (n3, lo3, hi3)``
+    evaluates the same grains on a sub-box (AMR levels), profile width ``width``."""
     rng = np.random.default_rng(seed)
-    p = Problem(n=(n, n, n), name=f"polycrystal_{n}_{grains}g")
+    if box is None:
+        p = Problem(n=(n, n, n), name=f"polycrystal_{n}_{grains}g")
+    else:
+        p = Problem(n=tuple(box[0]), lo=tuple(box[1]), hi=tuple(box[2]), name="polycrystal_box")
     centres = rng.random((grains, 3))
     rots = [random_rotation(rng) for _ in range(grains)]
     base = voigt_to_tensor(cubic_voigt(c11, c12, c44))
     grain_c = np.stack([tensor_to_upper21(rotate_tensor(base, R)) for R in rots])
-    h = p.h[0]
-    w = width_cells * h
+    w = width if width is not None else width_cells * p.h[0]
     X, Y, Z = p.coords()
     shape = X.shape
     # distance-squared to every centre, one z-slab at a time to bound memory
@@ -243,8 +252,9 @@ def polycrystal(n=257, grains=20, seed=0, c11=1.68, c12=1.21, c44=0.75, width_ce
     p.moduli_kind = MODULI_GEN21
     p.moduli = C
     bc = all_faces(TRACTION, 0.0)
-    bc[0] = [(DIRICHLET, -0.5 * strain), (TRACTION, 0.0), (TRACTION, 0.0)]
-    bc[1] = [(DIRICHLET, +0.5 * strain), (TRACTION, 0.0), (TRACTION, 0.0)]
+    lat = DIRICHLET if clamp else TRACTION
+    bc[0] = [(DIRICHLET, -0.5 * strain), (lat, 0.0), (lat, 0.0)]
+    bc[1] = [(DIRICHLET, +0.5 * strain), (lat, 0.0), (lat, 0.0)]
     p.bc = bc
     return p
 
@@ -371,6 +381,26 @@ def amr_penny_crack(base_n=65, nlevels=3, block=32, thresh=0.1, width=3.0 / 256,
     mk = lambda n3, lo3, hi3: penny_crack(width=width, clamp_lateral=True, box=(n3, lo3, hi3), **kw)
     ind = lambda X, Y, Z: crack_indicator(X, Y, Z, width=width)
     return amr_layout(mk, base_n, nlevels, ind, thresh, block, ghost_layers)
+
+
+def amr_request_layout(kind, base_n, nlevels=2, block=32, seed=0, ghost_layers=1):
+    """Two-level (by default) AMR layouts of the served microstructures: an Eshelby
+    sphere, a laterally clamped penny crack and a clamped polycrystal, each refined where
+    its indicator varies fast; profile widths fixed in physical units (3 or 4 spacings of
+    the finest level)."""
+    hf = 1.0 / ((base_n - 1) * 2 ** (nlevels - 1))
+    if kind == "sphere":
+        w = 3.0 * hf
+        mk = lambda n3, lo3, hi3: eshelby_sphere(box=(n3, lo3, hi3), width=w)
+        r = lambda X, Y, Z: np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+        ind = lambda X, Y, Z: tanh_profile(r(X, Y, Z) - 0.2, w)
+        return amr_layout(mk, base_n, nlevels, ind, 0.1, block, ghost_layers)
+    if kind == "crack":
+        return amr_penny_crack(base_n, nlevels, block, 0.1, width=3.0 * hf, ghost_layers=ghost_layers)
+    w = 4.0 * hf
+    mk = lambda n3, lo3, hi3: polycrystal(grains=12, seed=seed, box=(n3, lo3, hi3), width=w, clamp=True)
+    ind = lambda X, Y, Z: mk(X.shape[::-1], (X.min(), Y.min(), Z.min()), (X.max(), Y.max(), Z.max())).moduli[0] / 1.68
+    return amr_layout(mk, base_n, nlevels, ind, 0.1, block, ghost_layers)
 
 
 def ellipsoid_rve(n, seed, nu=0.3, width_cells=3.0, strain_norm=1e-3):

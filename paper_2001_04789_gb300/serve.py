@@ -1,15 +1,19 @@
 """Request loop around the native continuous-batching engine (elas_server_*).
 
 Requests arrive as a Poisson stream.  Each names a microstructure (Eshelby
-sphere, penny crack or polycrystal at one of several sizes) and a load scale.
-Hierarchies stay resident on the device between requests, up to an HBM budget
-(least recently used idle grids are evicted to admit a new one), and every solve
-is warm-started from the previous displacement of the same microstructure.  A
-request waits while its grid is busy with an earlier request; otherwise it is
-submitted at once and joins the batch at the next refinement step.
+sphere, penny crack or polycrystal) at one of several sizes, either on one grid
+(mixed precision) or as a two-level block-structured AMR layout (composite FP64
+cycles, one per server step), and a load scale.  Hierarchies stay resident on
+the device between requests, up to an HBM budget (least recently used idle ones
+are evicted to admit a new one), and every solve is warm-started from the
+previous displacement of the same microstructure.  A request waits while its
+hierarchy is busy with an earlier request; otherwise it is submitted at once and
+joins the batch at the next step.  Admission is bounded: an arrival that finds
+``max_queue`` requests already waiting is refused (and counted), so the reported
+latencies are those of a load the device sustains.
 
 ``python -m paper_2001_04789_gb300.serve --seconds 20`` prints one JSON line with
-completed solves, solves/s and p50/p99 latency measured from arrival.
+completed and refused requests, solves/s and p50/p99 latency from arrival.
 """
 from __future__ import annotations
 
@@ -44,14 +48,24 @@ def scale_loads(grid, problem, s):
         grid.set_eigenstrain(s * problem.eigenstrain)
 
 
+def amr_bytes(specs):
+    """Device bytes of a composite solve: each level's grid plus five work fields."""
+    total = 0
+    for sp in specs:
+        d = E.desc_for(sp.problem, mixed=False, max_levels=0 if sp.level == 0 else 1)
+        total += E.lib().elas_grid_bytes_estimate(d) + 5 * 3 * 8 * int(np.prod(sp.problem.n))
+    return total
+
+
 class ResidentCache:
-    """Grids kept on the device, keyed by microstructure id, evicted LRU when the
-    context's HBM budget would be exceeded."""
+    """Hierarchies kept on the device, keyed by microstructure id: a single grid
+    (value (grid, problem)) or a composite AMR solve (value (amr, specs)); evicted LRU
+    when the context's HBM budget would be exceeded."""
 
     def __init__(self, ctx, budget):
         self.ctx = ctx
         self.budget = budget
-        self.grids = collections.OrderedDict()     # id -> (grid, problem)
+        self.grids = collections.OrderedDict()     # id -> (grid or amr, problem or specs)
         self.busy = set()
 
     def get(self, mid, factory):
@@ -59,14 +73,15 @@ class ResidentCache:
             self.grids.move_to_end(mid)
             return self.grids[mid]
         p = factory()
-        need = E.lib().elas_grid_bytes_estimate(E.desc_for(p, mixed=True))
+        amr = isinstance(p, list)
+        need = amr_bytes(p) if amr else E.lib().elas_grid_bytes_estimate(E.desc_for(p, mixed=True))
         while self.ctx.bytes_in_use() + need > self.budget:
             victim = next((k for k in self.grids if k not in self.busy), None)
             if victim is None:
                 return None
             g, _ = self.grids.pop(victim)
             g.close()
-        g = E.grid_from_problem(self.ctx, p, mixed=True)
+        g = E.Amr(self.ctx, p) if amr else E.grid_from_problem(self.ctx, p, mixed=True)
         self.grids[mid] = (g, p)
         return self.grids[mid]
 
@@ -76,16 +91,34 @@ class ResidentCache:
         self.grids.clear()
 
 
+def make_entry(mid):
+    kind, n, seed = mid
+    if kind.startswith("amr_"):
+        return M.amr_request_layout(kind[4:], n, seed=seed)
+    return make_problem(kind, n, seed=seed)
+
+
+def scale_entry(g, p, sc):
+    if isinstance(p, list):
+        for grid, sp in zip(g.grids, p):
+            scale_loads(grid, sp.problem, sc)
+    else:
+        scale_loads(g, p, sc)
+
+
 def run(seconds=20.0, rate=200.0, sizes=(65, 129), kinds=("sphere", "crack", "polycrystal"),
-        variants=2, budget=150 << 30, max_active=16, seed=0, rel_tol=1e-8, device=0):
+        variants=2, budget=150 << 30, max_active=16, seed=0, rel_tol=1e-8, device=0,
+        amr_kinds=(), amr_sizes=(65,), max_queue=None):
     rng = np.random.default_rng(seed)
     ctx = E.Context(device, budget_bytes=budget)
     server = E.Server(ctx, max_active=max_active)
     cache = ResidentCache(ctx, budget)
     catalogue = [(k, n, v) for k in kinds for n in sizes for v in range(variants)]
+    catalogue += [("amr_" + k, n, v) for k in amr_kinds for n in amr_sizes for v in range(variants)]
     pending = collections.deque()          # (arrival, mid, scale) waiting for a free grid
     inflight = {}                          # ticket -> (arrival, mid)
     latencies, results = [], []
+    refused = 0
     t0 = time.perf_counter()
     next_arrival = rng.exponential(1.0 / rate)
     steps = 0
@@ -94,7 +127,11 @@ def run(seconds=20.0, rate=200.0, sizes=(65, 129), kinds=("sphere", "crack", "po
         now = time.perf_counter() - t0
         while next_arrival <= now and next_arrival < seconds:
             mid = catalogue[int(rng.integers(len(catalogue)))]
-            pending.append((next_arrival, mid, float(rng.uniform(0.5, 1.5))))
+            sc = float(rng.uniform(0.5, 1.5))
+            if max_queue is not None and len(pending) >= max_queue:
+                refused += 1
+            else:
+                pending.append((next_arrival, mid, sc))
             next_arrival += rng.exponential(1.0 / rate)
         # submit every pending request whose grid is resident and idle
         keep = collections.deque()
@@ -102,13 +139,16 @@ def run(seconds=20.0, rate=200.0, sizes=(65, 129), kinds=("sphere", "crack", "po
             if mid in cache.busy:
                 keep.append((arr, mid, sc))
                 continue
-            entry = cache.get(mid, lambda mid=mid: make_problem(mid[0], mid[1], seed=mid[2]))
+            entry = cache.get(mid, lambda mid=mid: make_entry(mid))
             if entry is None:
                 keep.append((arr, mid, sc))
                 continue
             g, p = entry
-            scale_loads(g, p, sc)
-            t = server.submit(g, rel_tol=rel_tol, max_cycles=200, warm_start=True)
+            scale_entry(g, p, sc)
+            if isinstance(p, list):
+                t = server.submit_amr(g, rel_tol=rel_tol, max_cycles=200, warm_start=True)
+            else:
+                t = server.submit(g, rel_tol=rel_tol, max_cycles=200, warm_start=True)
             inflight[t] = (arr, mid)
             cache.busy.add(mid)
         pending = keep
@@ -135,12 +175,14 @@ def run(seconds=20.0, rate=200.0, sizes=(65, 129), kinds=("sphere", "crack", "po
     ctx.close()
     lat = np.sort(np.array(latencies)) if latencies else np.array([np.nan])
     return {
-        "completed": len(results), "seconds": elapsed, "solves_per_s": len(results) / elapsed,
+        "completed": len(results), "refused": refused, "max_queue": max_queue,
+        "seconds": elapsed, "solves_per_s": len(results) / elapsed,
         "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
         "rate": rate, "steps": steps, "mean_active": active_sum / max(steps, 1),
         "converged": sum(1 for r in results if r["status"] == 0),
         "mean_cycles": float(np.mean([r["cycles"] for r in results])) if results else None,
-        "sizes": list(sizes), "kinds": list(kinds), "max_active": max_active,
+        "sizes": list(sizes), "kinds": list(kinds), "amr_kinds": list(amr_kinds), "amr_sizes": list(amr_sizes),
+        "max_active": max_active,
     }
 
 
@@ -150,9 +192,15 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--sizes", default="65,129")
     ap.add_argument("--max-active", type=int, default=16)
+    ap.add_argument("--amr", default="", help="AMR request kinds, e.g. sphere,crack,polycrystal")
+    ap.add_argument("--amr-sizes", default="65", help="base node counts of the AMR requests")
+    ap.add_argument("--kinds", default="sphere,crack,polycrystal", help="single-grid request kinds")
+    ap.add_argument("--max-queue", type=int, default=None, help="refuse arrivals beyond this many waiting")
     a = ap.parse_args()
     out = run(seconds=a.seconds, rate=a.rate, sizes=tuple(int(v) for v in a.sizes.split(",")),
-              max_active=a.max_active)
+              max_active=a.max_active, kinds=tuple(k for k in a.kinds.split(",") if k),
+              amr_kinds=tuple(k for k in a.amr.split(",") if k),
+              amr_sizes=tuple(int(v) for v in a.amr_sizes.split(",")), max_queue=a.max_queue)
     print(json.dumps(out), flush=True)
 
 

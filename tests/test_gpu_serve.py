@@ -100,3 +100,49 @@ def test_duplicate_submission_refused_and_failed_setup_retires(E):
     good.close()
     bare.close()
     ctx.close()
+
+
+def test_amr_request_is_the_same_alone_and_in_the_mix(E):
+    """A composite AMR solve served as a request (one composite cycle per step, beside
+    single-grid requests) gives the same cycles and the same bits as elas_amr_solve."""
+    from paper_2001_04789_gb300 import microstructure as M2
+    ctx = E.Context(0)
+    specs = M2.amr_penny_crack(base_n=17, nlevels=2, block=8, width=3.0 / 32)
+    amr = E.Amr(ctx, specs)
+    alone = amr.solve(rel_tol=1e-8)
+    u_alone = amr.displacements()
+    grids = [E.grid_from_problem(ctx, p, mixed=True) for p in problems()[:2]]
+    server = E.Server(ctx, max_active=3)
+    tickets = {server.submit(grids[0], rel_tol=1e-8): "g0", server.submit_amr(amr, rel_tol=1e-8): "amr",
+               server.submit(grids[1], rel_tol=1e-8): "g1"}
+    done = {}
+    for _ in range(1000):
+        server.step()
+        for t, name in list(tickets.items()):
+            r = server.poll(t)
+            if r is not None:
+                done[name] = r[0]
+                del tickets[t]
+        if not tickets:
+            break
+    assert done["amr"]["status"] == 0 and done["amr"]["cycles"] == alone["cycles"]
+    assert np.allclose(done["amr"]["rel_history"], alone["rel_history"], rtol=1e-12)
+    for ua, ub in zip(u_alone, amr.displacements()):
+        assert np.array_equal(ua, ub)
+    server.close()
+    amr.close()
+    for g in grids:
+        g.close()
+    ctx.close()
+
+
+def test_request_loop_with_amr_requests_and_bounded_admission(E):
+    """The request loop serves two-level AMR requests beside single-grid ones and refuses
+    arrivals beyond its queue bound; every served solve converges."""
+    from paper_2001_04789_gb300 import serve
+    out = serve.run(seconds=2.0, rate=60.0, sizes=(17,), kinds=("sphere", "polycrystal"),
+                    amr_kinds=("sphere", "crack", "polycrystal"), amr_sizes=(17,), max_active=4,
+                    budget=8 << 30, max_queue=6)
+    assert out["completed"] > 0 and out["converged"] == out["completed"]
+    assert out["refused"] >= 0 and out["max_queue"] == 6
+    assert out["latency_ms"]["p99"] >= out["latency_ms"]["p50"] > 0
