@@ -1548,9 +1548,9 @@ struct Arena {
         return off;
     }
 };
-struct PhaseRef {   // a phase before upload: arena offsets of its tasks and offsets
+struct PhaseRef {   // a phase before upload: arena offsets of its tasks and block map
     BatchPhase ph;
-    size_t tasks_off = 0, starts_off = 0;
+    size_t tasks_off = 0, bmap_off = 0;
 };
 
 template <typename Task>
@@ -1562,11 +1562,14 @@ PhaseRef make_phase(Arena& ar, int kind, const std::vector<Task>& tasks, int K, 
     r.ph.ml = ml;
     r.ph.colour = colour;
     if (tasks.empty()) return r;
-    std::vector<int> starts(tasks.size() + 1, 0);
-    for (size_t i = 0; i < tasks.size(); ++i) starts[i + 1] = starts[i] + batch_task_blocks(kind, &tasks[i]);
-    r.ph.blocks = starts.back();
+    std::vector<int2> bmap;
+    for (size_t i = 0; i < tasks.size(); ++i) {
+        const int nb = batch_task_blocks(kind, &tasks[i]);
+        for (int b = 0; b < nb; ++b) bmap.push_back(make_int2((int)i, b));
+    }
+    r.ph.blocks = (int)bmap.size();
     r.tasks_off = ar.push(tasks.data(), sizeof(Task) * tasks.size());
-    r.starts_off = ar.push(starts.data(), sizeof(int) * starts.size());
+    r.bmap_off = ar.push(bmap.data(), sizeof(int2) * bmap.size());
     return r;
 }
 
@@ -1764,7 +1767,7 @@ int plan_build(elas_grid* grids, int n, const elas_solve_opts* o, BatchPlan** ou
             for (auto& r : phases) {
                 BatchPhase ph = r.ph;
                 ph.tasks = (const char*)p->mem + r.tasks_off;
-                ph.starts = (const int*)((const char*)p->mem + r.starts_off);
+                ph.bmap = (const int2*)((const char*)p->mem + r.bmap_off);
                 batch_phase_launch(ph, main);
             }
         ce = cudaStreamEndCapture(main, &p->graph);

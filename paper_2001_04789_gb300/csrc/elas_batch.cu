@@ -1,8 +1,9 @@
 // Batched engine: one launch per phase of a multigrid cycle covers every member of a
-// batch of grids.  A phase's tasks (one per member taking part) and their block offsets
-// live in device memory; each block finds its task by binary search over the offsets and
-// runs the same per-node code as the single-grid kernels on that member's level, with the
-// member's own block partition, so each member's result is identical to its lone solve.
+// batch of grids.  A phase's tasks (one per member taking part) and its block map (the
+// task and the block within it, for every block of the launch) live in device memory;
+// each block loads its task into shared memory and runs the same per-node code as the
+// single-grid kernels on that member's level, with the member's own block partition, so
+// each member's result is identical to its lone solve.
 // Converged members (their active flag cleared on the device) skip their blocks.
 #include "elas_kernels.cuh"
 
@@ -11,27 +12,28 @@ namespace {
 
 constexpr int kBatchBlock = 256;
 
-// Task of block b: the largest i with starts[i] <= b (starts[0] = 0, n + 1 entries).
-__device__ __forceinline__ int find_task(const int* __restrict__ starts, int n, int b) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (starts[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ bool inactive(const int* a) { return a && *a == 0; }
 
+// The block's task, copied into shared memory by the whole block (so that the level's
+// fields are read at shared-memory latency), and the block's index within its task,
+// both from the phase's block map (one (task, local block) pair per block).
+template <typename Task>
+__device__ __forceinline__ int load_task(const Task* __restrict__ tasks, const int2* __restrict__ bmap, Task& dst) {
+    const int2 m = bmap[blockIdx.x];
+    const int* src = reinterpret_cast<const int*>(tasks + m.x);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(Task) / sizeof(int)); k += blockDim.x) d[k] = src[k];
+    __syncthreads();
+    return m.y;
+}
+
 template <int KIND, bool HM, int ML>
-__global__ void __launch_bounds__(kBatchBlock, 2)
-    k_batch_sweep(const SweepTask<float>* __restrict__ tasks, const int* __restrict__ starts, int n, int colour) {
-    const int i = find_task(starts, n, blockIdx.x);
-    const SweepTask<float>& t = tasks[i];
+__global__ void __launch_bounds__(kBatchBlock, 3)
+    k_batch_sweep(const SweepTask<float>* __restrict__ tasks, const int2* __restrict__ bmap, int colour) {
+    __shared__ __align__(16) SweepTask<float> t;
+    const int b = load_task(tasks, bmap, t), tid = threadIdx.x;
     const Lv<float>& L = t.L;
     if (inactive(L.active)) return;
-    const int b = blockIdx.x - starts[i], tid = threadIdx.x;
     const BndSegs sg = bnd_segs(L, kBatchBlock);
     if (b < sg.f2) {
         if (b < sg.e) sweep_bnd_body<float, KIND>(L, t.u, t.uo, t.f, colour, t.nf, t.lam, (b * kBatchBlock + tid) >> 5, tid & 31);
@@ -45,13 +47,12 @@ __global__ void __launch_bounds__(kBatchBlock, 2)
 
 template <typename T, typename TR, int KIND, bool NORM, bool HM, int ML>
 __global__ void __launch_bounds__(kBatchBlock, sizeof(T) == 4 ? 3 : 2)
-    k_batch_resid(const ResidTask<T, TR>* __restrict__ tasks, const int* __restrict__ starts, int n) {
-    const int i = find_task(starts, n, blockIdx.x);
-    const ResidTask<T, TR>& t = tasks[i];
+    k_batch_resid(const ResidTask<T, TR>* __restrict__ tasks, const int2* __restrict__ bmap) {
+    __shared__ __align__(16) ResidTask<T, TR> t;
+    const int b = load_task(tasks, bmap, t), tid = threadIdx.x;
     const Lv<T>& L = t.L;
     if (inactive(L.active)) return;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    const int b = blockIdx.x - starts[i], tid = threadIdx.x;
     const BndSegs sg = bnd_segs(L, kBlock);
     if (b < sg.e) residual_bnd_body<T, TR, KIND, NORM>(L, t.u, t.f, t.nf, t.lam, t.r, (b * kBlock + tid) >> 5, tid & 31, acc);
     else if (b < sg.f0) residual_face_body<T, TR, KIND, 0, NORM>(L, t.u, t.f, t.nf, t.lam, t.r, (b - sg.e) * kBlock + tid, acc);
@@ -61,41 +62,41 @@ __global__ void __launch_bounds__(kBatchBlock, sizeof(T) == 4 ? 3 : 2)
     if (NORM) block_reduce_store_at<7>(acc, t.nf.m > 0 ? 7 : 1, t.partials, b);
 }
 
-__global__ void k_batch_restrict(const RestrictTask<float>* __restrict__ tasks, const int* __restrict__ starts, int n) {
-    const int i = find_task(starts, n, blockIdx.x);
-    const RestrictTask<float>& t = tasks[i];
+__global__ void k_batch_restrict(const RestrictTask<float>* __restrict__ tasks, const int2* __restrict__ bmap) {
+    __shared__ __align__(16) RestrictTask<float> t;
+    const int b = load_task(tasks, bmap, t);
     if (inactive(t.Lf.active)) return;
-    restrict_body<float>(t.Lf, t.Lc, t.r, t.fc, t.nf, t.dlam, (blockIdx.x - starts[i]) * kBlock + threadIdx.x);
+    restrict_body<float>(t.Lf, t.Lc, t.r, t.fc, t.nf, t.dlam, b * kBlock + threadIdx.x);
 }
 
-__global__ void k_batch_prolong(const ProlongTask<float>* __restrict__ tasks, const int* __restrict__ starts, int n) {
-    const int i = find_task(starts, n, blockIdx.x);
-    const ProlongTask<float>& t = tasks[i];
+__global__ void k_batch_prolong(const ProlongTask<float>* __restrict__ tasks, const int2* __restrict__ bmap) {
+    __shared__ __align__(16) ProlongTask<float> t;
+    const int b = load_task(tasks, bmap, t);
     if (inactive(t.Lf.active)) return;
-    prolong_body<float>(t.Lf, t.Lc, t.ec, t.u, (blockIdx.x - starts[i]) * kBlock + threadIdx.x);
+    prolong_body<float>(t.Lf, t.Lc, t.ec, t.u, b * kBlock + threadIdx.x);
 }
 
-__global__ void k_batch_zero(const ZeroTask<float>* __restrict__ tasks, const int* __restrict__ starts, int n) {
-    const int i = find_task(starts, n, blockIdx.x);
-    const ZeroTask<float>& t = tasks[i];
+__global__ void k_batch_zero(const ZeroTask<float>* __restrict__ tasks, const int2* __restrict__ bmap) {
+    const int2 m = bmap[blockIdx.x];
+    const ZeroTask<float>& t = tasks[m.x];
     if (inactive(t.active)) return;
-    const size_t k = (size_t)(blockIdx.x - starts[i]) * kBlock + threadIdx.x;
+    const size_t k = (size_t)m.y * kBlock + threadIdx.x;
     if (k < t.n) t.a[k] = 0.f;
 }
 
-__global__ void k_batch_gather(const BottomTask<float>* __restrict__ tasks, const int* __restrict__ starts, int n) {
-    const int i = find_task(starts, n, blockIdx.x);
-    const BottomTask<float>& t = tasks[i];
+__global__ void k_batch_gather(const BottomTask<float>* __restrict__ tasks, const int2* __restrict__ bmap) {
+    const int2 m = bmap[blockIdx.x];
+    const BottomTask<float>& t = tasks[m.x];
     if (inactive(t.L.active)) return;
-    const int k = (blockIdx.x - starts[i]) * kBlock + threadIdx.x;
+    const int k = m.y * kBlock + threadIdx.x;
     if (k < t.ntot) t.work[k] = k < t.nfree ? (double)t.f[t.dofs[k]] : 0.0;
 }
 
-__global__ void k_batch_matvec(const BottomTask<float>* __restrict__ tasks, const int* __restrict__ starts, int n) {
-    const int i = find_task(starts, n, blockIdx.x);
-    const BottomTask<float>& t = tasks[i];
+__global__ void k_batch_matvec(const BottomTask<float>* __restrict__ tasks, const int2* __restrict__ bmap) {
+    const int2 m = bmap[blockIdx.x];
+    const BottomTask<float>& t = tasks[m.x];
     if (inactive(t.L.active)) return;
-    bottom_matvec_body<float>(t.dofs, t.nfree, t.ntot, t.Ainv, t.work, t.u, blockIdx.x - starts[i]);
+    bottom_matvec_body<float>(t.dofs, t.nfree, t.ntot, t.Ainv, t.work, t.u, m.y);
 }
 
 __global__ void k_batch_finalize(const FinalizeTask* __restrict__ tasks, int n) {
@@ -104,31 +105,30 @@ __global__ void k_batch_finalize(const FinalizeTask* __restrict__ tasks, int n) 
     finalize_body(t.partials, t.nblocks, t.nf, t.Ginv, t.G, t.lam, t.dlam, t.alam, t.adlam, t.out, 1, t.bf);
 }
 
-__global__ void k_batch_corr(const CorrTask* __restrict__ tasks, const int* __restrict__ starts, int n) {
-    const int i = find_task(starts, n, blockIdx.x);
-    const CorrTask& t = tasks[i];
+__global__ void k_batch_corr(const CorrTask* __restrict__ tasks, const int2* __restrict__ bmap) {
+    __shared__ __align__(16) CorrTask t;
+    const int b = load_task(tasks, bmap, t);
     if (inactive(t.L.active)) return;
-    add_correction_body<float>(t.L, t.u, t.e, (blockIdx.x - starts[i]) * kBlock + threadIdx.x);
+    add_correction_body<float>(t.L, t.u, t.e, b * kBlock + threadIdx.x);
 }
 
 template <int KIND, bool HM, int ML>
 void sweep_launch(const BatchPhase& ph, cudaStream_t s) {
-    k_batch_sweep<KIND, HM, ML><<<ph.blocks, kBatchBlock, 0, s>>>((const SweepTask<float>*)ph.tasks, ph.starts, ph.n,
-                                                                   ph.colour);
+    k_batch_sweep<KIND, HM, ML><<<ph.blocks, kBatchBlock, 0, s>>>((const SweepTask<float>*)ph.tasks, ph.bmap, ph.colour);
 }
 
 template <typename T, typename TR, bool NORM>
 void resid_launch(const BatchPhase& ph, cudaStream_t s) {
     const auto* t = (const ResidTask<T, TR>*)ph.tasks;
     if (sizeof(T) == 8) {
-        if (ph.K == 21) k_batch_resid<T, TR, 21, NORM, true, kMlDefault><<<ph.blocks, kBlock, 0, s>>>(t, ph.starts, ph.n);
-        else k_batch_resid<T, TR, 2, NORM, false, kMlDefault><<<ph.blocks, kBlock, 0, s>>>(t, ph.starts, ph.n);
+        if (ph.K == 21) k_batch_resid<T, TR, 21, NORM, true, kMlDefault><<<ph.blocks, kBlock, 0, s>>>(t, ph.bmap);
+        else k_batch_resid<T, TR, 2, NORM, false, kMlDefault><<<ph.blocks, kBlock, 0, s>>>(t, ph.bmap);
     } else if (ph.ml == kMlSplit) {
-        k_batch_resid<T, TR, 21, NORM, true, kMlSplit><<<ph.blocks, kBlock, 0, s>>>(t, ph.starts, ph.n);
+        k_batch_resid<T, TR, 21, NORM, true, kMlSplit><<<ph.blocks, kBlock, 0, s>>>(t, ph.bmap);
     } else if (ph.K == 21) {
-        k_batch_resid<T, TR, 21, NORM, false, kMlDefault><<<ph.blocks, kBlock, 0, s>>>(t, ph.starts, ph.n);
+        k_batch_resid<T, TR, 21, NORM, false, kMlDefault><<<ph.blocks, kBlock, 0, s>>>(t, ph.bmap);
     } else {
-        k_batch_resid<T, TR, 2, NORM, false, kMlDefault><<<ph.blocks, kBlock, 0, s>>>(t, ph.starts, ph.n);
+        k_batch_resid<T, TR, 2, NORM, false, kMlDefault><<<ph.blocks, kBlock, 0, s>>>(t, ph.bmap);
     }
 }
 
@@ -171,13 +171,13 @@ void batch_phase_launch(const BatchPhase& ph, cudaStream_t s) {
             break;
         case kPhaseResid32: resid_launch<float, float, false>(ph, s); break;
         case kPhaseResid64: resid_launch<double, float, true>(ph, s); break;
-        case kPhaseRestrict: k_batch_restrict<<<ph.blocks, kBlock, 0, s>>>((const RestrictTask<float>*)ph.tasks, ph.starts, ph.n); break;
-        case kPhaseProlong: k_batch_prolong<<<ph.blocks, kBlock, 0, s>>>((const ProlongTask<float>*)ph.tasks, ph.starts, ph.n); break;
-        case kPhaseZero: k_batch_zero<<<ph.blocks, kBlock, 0, s>>>((const ZeroTask<float>*)ph.tasks, ph.starts, ph.n); break;
-        case kPhaseGather: k_batch_gather<<<ph.blocks, kBlock, 0, s>>>((const BottomTask<float>*)ph.tasks, ph.starts, ph.n); break;
-        case kPhaseMatvec: k_batch_matvec<<<ph.blocks, kBlock, 0, s>>>((const BottomTask<float>*)ph.tasks, ph.starts, ph.n); break;
+        case kPhaseRestrict: k_batch_restrict<<<ph.blocks, kBlock, 0, s>>>((const RestrictTask<float>*)ph.tasks, ph.bmap); break;
+        case kPhaseProlong: k_batch_prolong<<<ph.blocks, kBlock, 0, s>>>((const ProlongTask<float>*)ph.tasks, ph.bmap); break;
+        case kPhaseZero: k_batch_zero<<<ph.blocks, kBlock, 0, s>>>((const ZeroTask<float>*)ph.tasks, ph.bmap); break;
+        case kPhaseGather: k_batch_gather<<<ph.blocks, kBlock, 0, s>>>((const BottomTask<float>*)ph.tasks, ph.bmap); break;
+        case kPhaseMatvec: k_batch_matvec<<<ph.blocks, kBlock, 0, s>>>((const BottomTask<float>*)ph.tasks, ph.bmap); break;
         case kPhaseFinalize: k_batch_finalize<<<ph.n, kSumThreads, 0, s>>>((const FinalizeTask*)ph.tasks, ph.n); break;
-        case kPhaseCorr: k_batch_corr<<<ph.blocks, kBlock, 0, s>>>((const CorrTask*)ph.tasks, ph.starts, ph.n); break;
+        case kPhaseCorr: k_batch_corr<<<ph.blocks, kBlock, 0, s>>>((const CorrTask*)ph.tasks, ph.bmap); break;
     }
 }
 

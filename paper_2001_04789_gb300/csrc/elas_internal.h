@@ -216,13 +216,14 @@ struct CorrTask {
     double* u;
     const float* e;
 };
-// A phase ready to launch: kind, member count, tasks and block offsets in device memory
-// (n + 1 offsets), total blocks, the half-sweep colour and the moduli variant of the
-// sweep and residual kernels (moduli kind 2 or 21 and layout kMl*).
+// A phase ready to launch: kind, member count, tasks and the block map in device memory
+// (for every block of the launch: its task and its block index within that task), total
+// blocks, the half-sweep colour and the moduli variant of the sweep and residual kernels
+// (moduli kind 2 or 21 and layout kMl*).
 struct BatchPhase {
     int kind = 0, n = 0, blocks = 0, colour = 0, K = 2, ml = 0;
     const void* tasks = nullptr;
-    const int* starts = nullptr;
+    const int2* bmap = nullptr;
 };
 // Blocks one task of a phase takes (the member's own block partition).
 int batch_task_blocks(int kind, const void* task);

@@ -1,0 +1,71 @@
+"""Time one finest-level kernel of the polycrystal workload through the C ABI.
+
+``python -m paper_2001_04789_gb300.kernel_timing --n 129 --kernel sweep32 --shape 3``
+builds the n^3 polycrystal grid (finest level only), pins the smoother's launch shape
+(autotuner index) for that level, runs ``--reps`` launches of the chosen kernel on
+random fields, and prints one JSON line with the mean device time per launch (CUDA
+events on the library's stream) and the algorithmic and issued bandwidth.  Kernels:
+``sweep32`` (one FP32 red-black sweep = two half-sweep launches), ``resid32`` (FP32
+residual), ``resid64`` (FP64 residual).  It is also the small profiling target for
+ncu captures of these kernels.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=129)
+    ap.add_argument("--kernel", default="sweep32", choices=["sweep32", "resid32", "resid64"])
+    ap.add_argument("--shape", type=int, default=3, help="smoother launch shape (autotuner index)")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--grains", type=int, default=10)
+    a = ap.parse_args()
+    import torch
+    from . import build as B
+    B.build()
+    from . import elas as E
+    from . import microstructure as M
+    p = M.polycrystal(a.n, grains=a.grains, seed=0)
+    ctx = E.Context(0)
+    g = E.grid_from_problem(ctx, p, mixed=True, max_levels=1)
+    for flag in (0, 1, 2):
+        E.autotune_load(f"{a.n} {a.n} {a.n} 21 4 {flag} {a.shape}")
+    rng = np.random.default_rng(0)
+    dt = torch.float64 if a.kernel == "resid64" else torch.float32
+    prec = E.FP64 if a.kernel == "resid64" else E.MIXED
+    u = torch.as_tensor(rng.normal(size=(3,) + g.shape) * 1e-3, dtype=dt, device="cuda:0")
+    f = torch.as_tensor(rng.normal(size=(3,) + g.shape), dtype=dt, device="cuda:0")
+    torch.cuda.synchronize()
+
+    def once():
+        if a.kernel == "sweep32":
+            g.op_sweep(0, prec, u, f)
+        else:
+            g.op_residual(0, prec, u, f)
+
+    once()
+    s = ctx.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(a.reps):
+        once()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    N = int(np.prod(p.n))
+    launches = 2 if a.kernel == "sweep32" else 1
+    alg = {"sweep32": 120.0, "resid32": 120.0, "resid64": 240.0}[a.kernel]   # bytes per node per pass
+    print(json.dumps({"kernel": a.kernel, "n": a.n, "nodes": N, "shape": a.shape, "reps": a.reps,
+                      "ms_per_launch": ms / launches, "ms_per_pass": ms,
+                      "alg_GBs": alg * N / (ms * 1e-3) / 1e9}), flush=True)
+    g.close()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
