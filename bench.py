@@ -28,10 +28,11 @@ sys.path.insert(0, ROOT)
 METRIC = "Solves/s at 1e-8 rel. residual, mixed vs FP64; stencil HBM GB/s; p99 latency"
 UNIT = "solves/s"
 FALLBACK_HBM_GBS = 6800.0
-# DRAM read + write bytes per node of one finest-level FP32 half-sweep launch, per
-# smoother shape (autotuner index), from one ncu capture of that shape on the 129^3
-# polycrystal; scaled by the node count to the benchmarked grid.
-SWEEP32_TRAFFIC_B_PER_NODE = {1: 144.2, 2: 151.7}
+# DRAM read + write bytes per node of one finest-level FP32 half-sweep launch (colour-split
+# moduli), per smoother shape (autotuner index), from one ncu capture of that shape on the
+# 129^3 polycrystal (profiles/sweep32_split_polycrystal129.md); scaled by the node count to
+# the benchmarked grid.
+SWEEP32_TRAFFIC_B_PER_NODE = {3: 201.6}
 
 
 def parse():
@@ -84,13 +85,14 @@ def alg_bytes_per_node(cls, K):
     return 4 * K + 12 + 12 + 12
 
 
-# Bytes the kernels are designed to move per node and launch (what the code issues):
-# an FP32 half-sweep with blocked moduli reads every node's moduli (its active colour's
-# stencils touch both colours), all of u, f of the active rows, and writes every row of
-# the output (active rows updated, the others copied).
+# Bytes the kernels are designed to move per node and launch (what the code issues): an
+# FP32 half-sweep of general moduli in the colour-split layout reads its colour's records
+# (39 floats per active node, half the nodes), all of u and f's lines (the active rows'
+# values interleave with the others'), and writes every row of the output (active rows
+# updated, the others copied); with isotropic moduli every node's two moduli are read.
 def issued_bytes_per_node(cls, K):
     if cls == "sweep32":
-        return 4 * K + 12 + 6 + 12
+        return (39 * 4 / 2 if K == 21 else 4 * K) + 12 + 12 + 12
     return alg_bytes_per_node(cls, K)
 
 
@@ -417,7 +419,7 @@ def main():
         achieved = bpn * N / avg_s / 1e9
         traffic = None
         if dom == "sweep32" and K == 21:
-            key = f"{p.n[0]} {p.n[1]} {p.n[2]} 21 4 0 "
+            key = f"{p.n[0]} {p.n[1]} {p.n[2]} 21 4 2 "
             shape = [int(l.split()[-1]) for l in E.autotune_dump().splitlines() if l.startswith(key)]
             if shape and shape[0] in SWEEP32_TRAFFIC_B_PER_NODE:
                 traffic = SWEEP32_TRAFFIC_B_PER_NODE[shape[0]] * N

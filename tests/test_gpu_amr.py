@@ -127,3 +127,24 @@ def test_amr_r2_needs_two_ghost_layers(E, ctx):
     specs = layouts()["crack2"]()
     with pytest.raises(E.ElasError):
         E.Amr(ctx, specs, reading="R2")
+
+
+def test_amr_config3_at_stated_size_matches_oracle(E, ctx):
+    """The penny-crack layout at its stated size (base 65^3, three levels, 32-cell blocks;
+    levels of 65^3, 129 x 129 x 67 and 195 x 195 x 67 nodes): one composite cycle on the
+    GPU against the oracle's on every level's valid nodes, then a converged GPU solve."""
+    specs = M.amr_penny_crack(base_n=65, nlevels=3, block=32)
+    assert len(specs) == 3
+    amr = E.Amr(ctx, specs)
+    info = amr.solve(fixed_cycles=1)
+    got = amr.displacements()
+    ref, rinfo = A.solve(specs, fixed_cycles=1)
+    for l, (g, r) in enumerate(zip(got, ref)):
+        sp = specs[l]
+        sl = (slice(None),) + tuple(slice(sp.valid_lo[d] - sp.grid_lo[d], sp.valid_hi[d] - sp.grid_lo[d] + 1)
+                                    for d in (2, 1, 0))
+        assert rel_err(g[sl], r[sl]) < 1e-9, l
+    assert np.allclose(info["rel_history"], rinfo["rel_history"], rtol=1e-7)
+    full = amr.solve(rel_tol=1e-8, max_cycles=200)
+    assert full["status"] == 0 and full["rel_residual"] <= 1e-8
+    amr.close()
