@@ -311,9 +311,13 @@ int  elas_autotune_load(const char* text);     /* returns the entries read */
  * work arrays only.  Covered coarse moduli are replaced by the restriction of the
  * finer level's (operator equivalence across levels).  Solve: the composite cycle
  * (ghosts by trilinear interpolation of the coarser level, covered coarse nodes by
- * injection, restricted fine residuals on covered nodes, level-0 V-cycle); FP64;
- * the problem must have no free rigid modes.  Level solutions are read with
- * elas_get_displacement on each grid. */
+ * injection, restricted fine residuals on covered nodes, level-0 V-cycle); the
+ * problem must have no free rigid modes.  opts->precision ELAS_PRECISION_FP64: FP64
+ * composite cycles; ELAS_PRECISION_MIXED (every level's grid created with mixed = 1):
+ * each refinement step casts the FP64 composite residual to FP32, runs one composite
+ * correction cycle in FP32 (FP32 fine-level smoothing, FP32 level-0 V-cycle) and adds the
+ * corrections to the FP64 levels; convergence is tested on the FP64 composite residual.
+ * Level solutions are read with elas_get_displacement on each grid. */
 typedef struct elas_amr_s* elas_amr;
 typedef struct {
     int grid_lo[3];
@@ -371,11 +375,13 @@ typedef struct elas_server_s* elas_server;
 int  elas_server_create(elas_ctx ctx, int max_active, elas_server* out);
 int  elas_server_destroy(elas_server s);
 int  elas_server_submit(elas_server s, elas_grid g, const elas_solve_opts* opts, long long* ticket);
-/* A composite AMR solve as a request (Section 3.2; FP64 composite cycles, reading as set
- * on the elas_amr): admitted into a free slot like a grid request; each server step runs
- * one composite cycle of it, interleaved with the other requests, and it retires at
- * opts->rel_tol (composite norm) or max_cycles.  warm_start keeps the levels' current
- * displacements.  Results are the same as elas_amr_solve's (same kernels, same order). */
+/* A composite AMR solve as a request (Section 3.2, reading as set on the elas_amr):
+ * admitted into a free slot like a grid request; each server step runs one composite
+ * cycle of it (FP64, or for opts->precision ELAS_PRECISION_MIXED one FP32 correction cycle
+ * on the FP64 composite residual, as in elas_amr_solve), interleaved with the other
+ * requests, and it retires at opts->rel_tol (composite norm) or max_cycles.  warm_start
+ * keeps the levels' current displacements.  Results are the same as elas_amr_solve's
+ * (same kernels, same order). */
 int  elas_server_submit_amr(elas_server s, elas_amr a, const elas_solve_opts* opts, long long* ticket);
 /* One step; *active and *waiting receive the counts after it. */
 int  elas_server_step(elas_server s, int* active, int* waiting);

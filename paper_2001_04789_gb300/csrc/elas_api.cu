@@ -1993,6 +1993,7 @@ struct elas_amr_s {
     std::vector<AmrBox> rbox;   // relaxed boxes: the valid box (R1), grown by the inner ghost layer (R2)
     int reading = ELAS_AMR_R1;
     std::vector<double*> res, rpass, cor, cora, tmp;
+    std::vector<float*> res32, rpass32, cor32, cora32, tmp32;   // mixed solves (allocated on first use)
     std::vector<std::pair<void*, size_t>> allocs;
     double* partials = nullptr;
     size_t npart = 0;
@@ -2066,6 +2067,88 @@ int amr_norm(elas_amr a, double* out) {
     rc = read_status(a->g[0], st, 1);
     if (rc) return rc;
     *out = std::sqrt(st[0]);
+    return ELAS_OK;
+}
+
+struct LevelSwap32 {
+    Level& v;
+    float *u, *ua, *f, *r;
+    LevelSwap32(Level& lv, float* nu, float* nua, float* nf, float* nr)
+        : v(lv), u(lv.u32), ua(lv.ua32), f(lv.f32), r(lv.r32) {
+        v.u32 = nu;
+        v.ua32 = nua;
+        v.f32 = nf;
+        v.r32 = nr;
+    }
+    ~LevelSwap32() {
+        v.u32 = u;
+        v.ua32 = ua;
+        v.f32 = f;
+        v.r32 = r;
+    }
+};
+
+// The composite correction cycle of a mixed solve in FP32 (the same steps as amr_cycle,
+// on FP32 copies of the residuals, corrections and moduli); the corrections are left in
+// cor32 for the FP64 update.
+void amr_cycle32(elas_amr a, int nu1, int nu2) {
+    const int nl = (int)a->g.size();
+    cudaStream_t s = a->g[0]->ctx->stream;
+    for (int l = 0; l < nl; ++l) {
+        const size_t bytes = sizeof(float) * 3 * (size_t)a->g[l]->lv[0].N;
+        cudaMemcpyAsync(a->rpass32[l], a->res32[l], bytes, cudaMemcpyDeviceToDevice, s);
+    }
+    for (int l = nl - 1; l >= 1; --l) {
+        elas_grid gl = a->g[l];
+        Level& v = gl->lv[0];
+        cudaMemsetAsync(a->cor32[l], 0, sizeof(float) * 3 * (size_t)v.N, s);
+        {
+            LevelSwap32 sw(v, a->cor32[l], a->cora32[l], a->res32[l], a->tmp32[l]);
+            smooth<float>(gl, 0, nu1, nullptr, nullptr);
+            launch_residual<float, float>(v.L32, v.u32, v.f32, nullptr, nullptr, a->rpass32[l], nullptr, nullptr, s);
+        }
+        launch_amr_restrict<float>(v.L32, a->rbox[l], a->g[l - 1]->lv[0].L32, a->box[l - 1], a->rpass32[l],
+                                   a->rpass32[l - 1], 3, 1, s);
+        if (l - 1 >= 1)
+            cudaMemcpyAsync(a->res32[l - 1], a->rpass32[l - 1], sizeof(float) * 3 * (size_t)a->g[l - 1]->lv[0].N,
+                            cudaMemcpyDeviceToDevice, s);
+    }
+    {
+        Level& v0 = a->g[0]->lv[0];
+        LevelSwap32 sw(v0, a->cor32[0], a->cora32[0], nl > 1 ? a->rpass32[0] : a->res32[0], a->tmp32[0]);
+        vcycle<float>(a->g[0], 0, nu1, nu2, nullptr, nullptr);
+    }
+    for (int l = 1; l < nl; ++l) {
+        elas_grid gl = a->g[l];
+        Level& v = gl->lv[0];
+        const Lv<float>& Lc = a->g[l - 1]->lv[0].L32;
+        launch_amr_interp<float>(v.L32, a->box[l], Lc, a->box[l - 1], a->cor32[l - 1], a->cor32[l], 1, s);
+        launch_amr_interp<float>(v.L32, a->box[l], Lc, a->box[l - 1], a->cor32[l - 1], a->cor32[l], 0, s);
+        LevelSwap32 sw(v, a->cor32[l], a->cora32[l], a->res32[l], a->tmp32[l]);
+        smooth<float>(gl, 0, nu2, nullptr, nullptr);
+    }
+}
+
+// FP32 work arrays of the mixed composite solve (once).
+int amr_alloc32(elas_amr a) {
+    if (!a->res32.empty()) return ELAS_OK;
+    elas_ctx c = a->g[0]->ctx;
+    for (auto g : a->g)
+        if (!g->desc.mixed) return set_err(c, ELAS_ERR_STATE, "mixed AMR solve needs every level created with mixed = 1");
+    for (auto g : a->g) {
+        const size_t bytes = sizeof(float) * 3 * (size_t)g->lv[0].N;
+        float* p[5];
+        for (int k = 0; k < 5; ++k) {
+            p[k] = (float*)ctx_alloc(c, bytes);
+            if (!p[k]) return set_err(c, ELAS_ERR_ALLOC, "AMR FP32 work arrays: allocation failed");
+            a->allocs.push_back({p[k], bytes});
+        }
+        a->res32.push_back(p[0]);
+        a->rpass32.push_back(p[1]);
+        a->cor32.push_back(p[2]);
+        a->cora32.push_back(p[3]);
+        a->tmp32.push_back(p[4]);
+    }
     return ELAS_OK;
 }
 
@@ -2259,7 +2342,11 @@ int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* inf
     std::memset(info, 0, sizeof(*info));
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = c->stream;
-    int rc = amr_prepare(a, opts->warm_start != 0);
+    const bool mixed = opts->precision == ELAS_PRECISION_MIXED;
+    const int nl = (int)a->g.size();
+    int rc = mixed ? amr_alloc32(a) : ELAS_OK;
+    if (rc) return rc;
+    rc = amr_prepare(a, opts->warm_start != 0);
     if (rc) return rc;
     rc = amr_composite_residual(a);
     if (rc) return rc;
@@ -2292,7 +2379,17 @@ int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* inf
                 break;
             }
         }
-        amr_cycle(a, nu1, nu2);
+        if (mixed) {
+            // FP32 composite cycle on the FP64 composite residual, FP64 update
+            for (int l = 0; l < nl; ++l)
+                launch_cast<float, double>(a->res32[l], a->res[l], (size_t)3 * a->g[l]->lv[0].N, s);
+            amr_cycle32(a, nu1, nu2);
+            for (int l = 0; l < nl; ++l)
+                launch_amr_add<double, float>(a->g[l]->lv[0].L64, a->box[l], a->g[l]->lv[0].u, a->cor32[l], s);
+            for (int l = nl - 1; l >= 1; --l) amr_sync(a, l, a->g[l]->lv[0].u, a->g[l - 1]->lv[0].u);
+        } else {
+            amr_cycle(a, nu1, nu2);
+        }
         CHECK_LAUNCH(c);
         ++cycles;
     }
@@ -2437,7 +2534,8 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
         elas_grid g = r.g;
         int rc = ELAS_OK;
         if (r.a) {
-            rc = amr_prepare(r.a, r.opts.warm_start != 0);
+            if (r.opts.precision == ELAS_PRECISION_MIXED) rc = amr_alloc32(r.a);
+            if (!rc) rc = amr_prepare(r.a, r.opts.warm_start != 0);
         } else {
             rc = take_cycle_opts(g, &r.opts);
             if (!rc) rc = setup(g);
@@ -2491,8 +2589,23 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
             c->stream = c->branch[k % S];
             if (r.a) {
                 // one composite cycle (the first step only evaluates the initial residual),
-                // then the composite residual and its norm
-                if (r.started) amr_cycle(r.a, r.opts.nu1, r.opts.nu2);
+                // then the composite residual and its norm; mixed: the FP32 correction cycle
+                // on the FP64 residual, as elas_amr_solve does
+                if (r.started) {
+                    if (r.opts.precision == ELAS_PRECISION_MIXED) {
+                        elas_amr a = r.a;
+                        const int nl = (int)a->g.size();
+                        for (int l = 0; l < nl; ++l)
+                            launch_cast<float, double>(a->res32[l], a->res[l], (size_t)3 * a->g[l]->lv[0].N, c->stream);
+                        amr_cycle32(a, r.opts.nu1, r.opts.nu2);
+                        for (int l = 0; l < nl; ++l)
+                            launch_amr_add<double, float>(a->g[l]->lv[0].L64, a->box[l], a->g[l]->lv[0].u, a->cor32[l],
+                                                          c->stream);
+                        for (int l = nl - 1; l >= 1; --l) amr_sync(a, l, a->g[l]->lv[0].u, a->g[l - 1]->lv[0].u);
+                    } else {
+                        amr_cycle(r.a, r.opts.nu1, r.opts.nu2);
+                    }
+                }
                 amr_composite_residual(r.a);
                 amr_norm_enqueue(r.a);
                 cudaMemcpyAsync(s->h_norm + r.slot, g->status, sizeof(double), cudaMemcpyDeviceToHost, c->stream);

@@ -245,20 +245,26 @@ struct AmrBox {
 };
 
 // mode 0: ghost nodes := I(coarse); mode 1: valid non-Dirichlet nodes += I(coarse)
-void launch_amr_interp(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
-                       const double* cfield, double* ffield, int mode, cudaStream_t s);
+template <typename T>
+void launch_amr_interp(const Lv<T>& Lf, const AmrBox& bf, const Lv<T>& Lc, const AmrBox& bc, const T* cfield,
+                       T* ffield, int mode, cudaStream_t s);
 // covered coarse nodes := coincident fine values
 void launch_amr_inject(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
                        const double* ffield, double* cfield, cudaStream_t s);
 // covered coarse nodes := renormalised restriction of a K-plane fine field over the fine
 // box's valid nodes; on coarse Dirichlet rows: zero (zero_dirichlet 1), kept (2), or the
 // restricted value (0)
-void launch_amr_restrict(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
-                         const double* ffield, double* cfield, int K, int zero_dirichlet, cudaStream_t s);
+template <typename T>
+void launch_amr_restrict(const Lv<T>& Lf, const AmrBox& bf, const Lv<T>& Lc, const AmrBox& bc, const T* ffield,
+                         T* cfield, int K, int zero_dirichlet, cudaStream_t s);
 // partials of sum res^2 over valid nodes not covered by the next level (cov may be null)
 int launch_amr_norm(const Lv<double>& L, const AmrBox& b, const AmrBox* cov, const double* res, double* partials,
                     cudaStream_t s);
 // u += cor on every node that is not a ghost
-void launch_amr_add(const Lv<double>& L, const AmrBox& b, double* u, const double* cor, cudaStream_t s);
+template <typename TU, typename TC>
+void launch_amr_add(const Lv<TU>& L, const AmrBox& b, TU* u, const TC* cor, cudaStream_t s);
+// a := (TO) b over n elements
+template <typename TO, typename TI>
+void launch_cast(TO* a, const TI* b, size_t n, cudaStream_t s);
 
 }  // namespace elas

@@ -252,10 +252,11 @@ void launch_remove_null(const Lv<double>& L, const NullInfo& nf, const double* G
     k_remove_null<<<blocks_for(L.N), kBlock, 0, s>>>(L, nf, motion, u);
 }
 
-void launch_amr_interp(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
-                       const double* cfield, double* ffield, int mode, cudaStream_t s) {
+template <typename T>
+void launch_amr_interp(const Lv<T>& Lf, const AmrBox& bf, const Lv<T>& Lc, const AmrBox& bc, const T* cfield,
+                       T* ffield, int mode, cudaStream_t s) {
     count_launch();
-    k_amr_interp<<<blocks_for(Lf.N), kBlock, 0, s>>>(Lf, bf, Lc, bc, cfield, ffield, mode);
+    k_amr_interp<T><<<blocks_for(Lf.N), kBlock, 0, s>>>(Lf, bf, Lc, bc, cfield, ffield, mode);
 }
 
 static size_t amr_cov_count(const AmrBox& bf) {
@@ -270,10 +271,12 @@ void launch_amr_inject(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>&
     k_amr_inject<<<blocks_for(amr_cov_count(bf)), kBlock, 0, s>>>(Lf, bf, Lc, bc, ffield, cfield);
 }
 
-void launch_amr_restrict(const Lv<double>& Lf, const AmrBox& bf, const Lv<double>& Lc, const AmrBox& bc,
-                         const double* ffield, double* cfield, int K, int zero_dirichlet, cudaStream_t s) {
+template <typename T>
+void launch_amr_restrict(const Lv<T>& Lf, const AmrBox& bf, const Lv<T>& Lc, const AmrBox& bc, const T* ffield,
+                         T* cfield, int K, int zero_dirichlet, cudaStream_t s) {
     count_launch();
-    k_amr_restrict<<<blocks_for(amr_cov_count(bf)), kBlock, 0, s>>>(Lf, bf, Lc, bc, ffield, cfield, K, zero_dirichlet);
+    k_amr_restrict<T><<<blocks_for(amr_cov_count(bf)), kBlock, 0, s>>>(Lf, bf, Lc, bc, ffield, cfield, K,
+                                                                       zero_dirichlet);
 }
 
 int launch_amr_norm(const Lv<double>& L, const AmrBox& b, const AmrBox* cov, const double* res, double* partials,
@@ -286,10 +289,30 @@ int launch_amr_norm(const Lv<double>& L, const AmrBox& b, const AmrBox* cov, con
     return nb;
 }
 
-void launch_amr_add(const Lv<double>& L, const AmrBox& b, double* u, const double* cor, cudaStream_t s) {
+template <typename TU, typename TC>
+void launch_amr_add(const Lv<TU>& L, const AmrBox& b, TU* u, const TC* cor, cudaStream_t s) {
     count_launch();
-    k_amr_add<<<blocks_for(L.N), kBlock, 0, s>>>(L, b, u, cor);
+    k_amr_add<TU, TC><<<blocks_for(L.N), kBlock, 0, s>>>(L, b, u, cor);
 }
+
+template <typename TO, typename TI>
+void launch_cast(TO* a, const TI* b, size_t n, cudaStream_t s) {
+    count_launch();
+    k_cast<TO, TI><<<blocks_for(n), kBlock, 0, s>>>(a, b, n);
+}
+
+template void launch_amr_interp<double>(const Lv<double>&, const AmrBox&, const Lv<double>&, const AmrBox&,
+                                        const double*, double*, int, cudaStream_t);
+template void launch_amr_interp<float>(const Lv<float>&, const AmrBox&, const Lv<float>&, const AmrBox&,
+                                       const float*, float*, int, cudaStream_t);
+template void launch_amr_restrict<double>(const Lv<double>&, const AmrBox&, const Lv<double>&, const AmrBox&,
+                                          const double*, double*, int, int, cudaStream_t);
+template void launch_amr_restrict<float>(const Lv<float>&, const AmrBox&, const Lv<float>&, const AmrBox&,
+                                         const float*, float*, int, int, cudaStream_t);
+template void launch_amr_add<double, double>(const Lv<double>&, const AmrBox&, double*, const double*, cudaStream_t);
+template void launch_amr_add<double, float>(const Lv<double>&, const AmrBox&, double*, const float*, cudaStream_t);
+template void launch_amr_add<float, float>(const Lv<float>&, const AmrBox&, float*, const float*, cudaStream_t);
+template void launch_cast<float, double>(float*, const double*, size_t, cudaStream_t);
 
 // ---- stress output ------------------------------------------------------------------
 // sigma = C : (grad u + ebar - eps0) at every node (Eq. 1c's stress), six tensor

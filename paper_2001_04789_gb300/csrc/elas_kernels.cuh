@@ -1516,8 +1516,9 @@ __device__ __forceinline__ bool amr_is_ghost(const AmrBox& b, const int n[3], co
 }
 
 #ifdef ELAS_KERNELS_TU
-__global__ void k_amr_interp(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc, const double* __restrict__ cf,
-                             double* __restrict__ ff, int mode) {
+template <typename T>
+__global__ void k_amr_interp(Lv<T> Lf, AmrBox bf, Lv<T> Lc, AmrBox bc, const T* __restrict__ cf,
+                             T* __restrict__ ff, int mode) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= Lf.N) return;
     int c[3];
@@ -1536,7 +1537,7 @@ __global__ void k_amr_interp(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc,
     const NodeInfo ni = node_info(Lf, c[0], c[1], c[2]);
     for (int k = 0; k < 3; ++k) {
         if (mode == 1 && row_type(Lf, ni, k) == ROW_DIRICHLET) continue;
-        const double* e = cf + (size_t)k * Lc.N;
+        const T* e = cf + (size_t)k * Lc.N;
         double v = 0.0;
         for (int bz = 0; bz < 2; ++bz) {
             const double wz = bz ? w1[2] : 1.0 - w1[2];
@@ -1552,8 +1553,8 @@ __global__ void k_amr_interp(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc,
                 }
             }
         }
-        if (mode == 0) ff[(size_t)k * Lf.N + p] = v;
-        else ff[(size_t)k * Lf.N + p] += v;
+        if (mode == 0) ff[(size_t)k * Lf.N + p] = (T)v;
+        else ff[(size_t)k * Lf.N + p] += (T)v;
     }
 }
 #endif
@@ -1585,8 +1586,9 @@ __global__ void k_amr_inject(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc,
 #endif
 
 #ifdef ELAS_KERNELS_TU
-__global__ void k_amr_restrict(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox bc, const double* __restrict__ ffield,
-                               double* __restrict__ cfield, int K, int zero_dirichlet) {
+template <typename T>
+__global__ void k_amr_restrict(Lv<T> Lf, AmrBox bf, Lv<T> Lc, AmrBox bc, const T* __restrict__ ffield,
+                               T* __restrict__ cfield, int K, int zero_dirichlet) {
     int lo[3], cnt[3];
     amr_cov_box(bf, bc, lo, cnt);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1621,7 +1623,7 @@ __global__ void k_amr_restrict(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox b
                     const int fx = 2 * (bc.grid_lo[0] + cc[0]) + ox - bf.grid_lo[0];
                     const int fy = 2 * (bc.grid_lo[1] + cc[1]) + oy - bf.grid_lo[1];
                     const int fz = 2 * (bc.grid_lo[2] + cc[2]) + oz - bf.grid_lo[2];
-                    acc += w[0][ox + 1] * w[1][oy + 1] * w[2][oz + 1] * ffield[(size_t)k * Lf.N + lin(Lf, fx, fy, fz)];
+                    acc += w[0][ox + 1] * w[1][oy + 1] * w[2][oz + 1] * (double)ffield[(size_t)k * Lf.N + lin(Lf, fx, fy, fz)];
                 }
             }
         }
@@ -1629,7 +1631,7 @@ __global__ void k_amr_restrict(Lv<double> Lf, AmrBox bf, Lv<double> Lc, AmrBox b
             if (zero_dirichlet == 1) acc = 0.0;
             else if (zero_dirichlet == 2) continue;   // keep the coarse boundary value
         }
-        cfield[(size_t)k * Lc.N + pc] = acc;
+        cfield[(size_t)k * Lc.N + pc] = (T)acc;
     }
 }
 #endif
@@ -1667,13 +1669,21 @@ __global__ void k_amr_norm(Lv<double> L, AmrBox b, AmrBox cov, int has_cov, cons
 #endif
 
 #ifdef ELAS_KERNELS_TU
-__global__ void k_amr_add(Lv<double> L, AmrBox b, double* __restrict__ u, const double* __restrict__ cor) {
+template <typename TU, typename TC>
+__global__ void k_amr_add(Lv<TU> L, AmrBox b, TU* __restrict__ u, const TC* __restrict__ cor) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= L.N) return;
     int c[3];
     coords_of(p, L.n, c);
     if (amr_is_ghost(b, L.n, c)) return;
-    for (int k = 0; k < 3; ++k) u[(size_t)k * L.N + p] += cor[(size_t)k * L.N + p];
+    for (int k = 0; k < 3; ++k) u[(size_t)k * L.N + p] += (TU)cor[(size_t)k * L.N + p];
+}
+
+// a := (TO) b, n elements
+template <typename TO, typename TI>
+__global__ void k_cast(TO* __restrict__ a, const TI* __restrict__ b, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (TO)b[i];
 }
 #endif
 

@@ -518,10 +518,11 @@ class Amr:
     (``microstructure.AmrLevel`` list): one grid per level, level 0 with its
     multigrid hierarchy, finer levels smoothed only."""
 
-    def __init__(self, ctx: Context, specs, reading="R1"):
+    def __init__(self, ctx: Context, specs, reading="R1", mixed=False):
         self.ctx = ctx
         self.specs = specs
-        self.grids = [grid_from_problem(ctx, sp.problem, max_levels=0 if sp.level == 0 else 1) for sp in specs]
+        self.grids = [grid_from_problem(ctx, sp.problem, mixed=mixed, max_levels=0 if sp.level == 0 else 1)
+                      for sp in specs]
         descs = (AmrLevelDesc * len(specs))()
         for i, sp in enumerate(specs):
             for d in range(3):
@@ -536,9 +537,10 @@ class Amr:
         self.h = h
         ctx.check(lib().elas_amr_set_reading(self.h, {"R1": 1, "R2": 2}[reading]))
 
-    def solve(self, rel_tol=1e-8, max_cycles=200, nu1=2, nu2=2, fixed_cycles=0, raise_on_error=True):
+    def solve(self, rel_tol=1e-8, max_cycles=200, nu1=2, nu2=2, fixed_cycles=0, raise_on_error=True,
+              precision=FP64):
         info = SolveInfo()
-        rc = lib().elas_amr_solve(self.h, C.byref(_opts(FP64, rel_tol, max_cycles, nu1, nu2, False, fixed_cycles)),
+        rc = lib().elas_amr_solve(self.h, C.byref(_opts(precision, rel_tol, max_cycles, nu1, nu2, False, fixed_cycles)),
                                   C.byref(info))
         if rc != OK and raise_on_error and rc != ERR_NOT_CONVERGED:
             raise ElasError(rc, self.ctx.error())
@@ -587,10 +589,11 @@ class Server:
         self.ctx.check(lib().elas_server_submit(self.h, grid.h, C.byref(_opts(MIXED, **kw)), C.byref(t)))
         return t.value
 
-    def submit_amr(self, amr, **kw):
-        """A composite AMR solve (an ``Amr``) as a request: one composite cycle per step."""
+    def submit_amr(self, amr, precision=FP64, **kw):
+        """A composite AMR solve (an ``Amr``) as a request: one composite cycle per step
+        (MIXED: an FP32 correction cycle on the FP64 composite residual)."""
         t = C.c_longlong()
-        self.ctx.check(lib().elas_server_submit_amr(self.h, amr.h, C.byref(_opts(FP64, **kw)), C.byref(t)))
+        self.ctx.check(lib().elas_server_submit_amr(self.h, amr.h, C.byref(_opts(precision, **kw)), C.byref(t)))
         return t.value
 
     def step(self):

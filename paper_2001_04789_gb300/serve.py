@@ -81,7 +81,7 @@ class ResidentCache:
                 return None
             g, _ = self.grids.pop(victim)
             g.close()
-        g = E.Amr(self.ctx, p) if amr else E.grid_from_problem(self.ctx, p, mixed=True)
+        g = E.Amr(self.ctx, p, mixed=True) if amr else E.grid_from_problem(self.ctx, p, mixed=True)
         self.grids[mid] = (g, p)
         return self.grids[mid]
 
@@ -108,7 +108,7 @@ def scale_entry(g, p, sc):
 
 def run(seconds=20.0, rate=200.0, sizes=(65, 129), kinds=("sphere", "crack", "polycrystal"),
         variants=2, budget=150 << 30, max_active=16, seed=0, rel_tol=1e-8, device=0,
-        amr_kinds=(), amr_sizes=(65,), max_queue=None):
+        amr_kinds=(), amr_sizes=(65,), max_queue=None, prewarm=False):
     rng = np.random.default_rng(seed)
     ctx = E.Context(device, budget_bytes=budget)
     server = E.Server(ctx, max_active=max_active)
@@ -119,6 +119,14 @@ def run(seconds=20.0, rate=200.0, sizes=(65, 129), kinds=("sphere", "crack", "po
     inflight = {}                          # ticket -> (arrival, mid)
     latencies, results = [], []
     refused = 0
+    t_prewarm = 0.0
+    if prewarm:
+        # resident hierarchies: every microstructure of the catalogue is generated and set
+        # up on the device before the stream starts (as far as the budget allows)
+        t = time.perf_counter()
+        for mid in catalogue:
+            cache.get(mid, lambda mid=mid: make_entry(mid))
+        t_prewarm = time.perf_counter() - t
     t0 = time.perf_counter()
     next_arrival = rng.exponential(1.0 / rate)
     steps = 0
@@ -146,7 +154,7 @@ def run(seconds=20.0, rate=200.0, sizes=(65, 129), kinds=("sphere", "crack", "po
             g, p = entry
             scale_entry(g, p, sc)
             if isinstance(p, list):
-                t = server.submit_amr(g, rel_tol=rel_tol, max_cycles=200, warm_start=True)
+                t = server.submit_amr(g, precision=E.MIXED, rel_tol=rel_tol, max_cycles=200, warm_start=True)
             else:
                 t = server.submit(g, rel_tol=rel_tol, max_cycles=200, warm_start=True)
             inflight[t] = (arr, mid)
@@ -176,6 +184,7 @@ def run(seconds=20.0, rate=200.0, sizes=(65, 129), kinds=("sphere", "crack", "po
     lat = np.sort(np.array(latencies)) if latencies else np.array([np.nan])
     return {
         "completed": len(results), "refused": refused, "max_queue": max_queue,
+        "prewarm_seconds": t_prewarm,
         "seconds": elapsed, "solves_per_s": len(results) / elapsed,
         "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3)},
         "rate": rate, "steps": steps, "mean_active": active_sum / max(steps, 1),
@@ -196,11 +205,13 @@ def main():
     ap.add_argument("--amr-sizes", default="65", help="base node counts of the AMR requests")
     ap.add_argument("--kinds", default="sphere,crack,polycrystal", help="single-grid request kinds")
     ap.add_argument("--max-queue", type=int, default=None, help="refuse arrivals beyond this many waiting")
+    ap.add_argument("--prewarm", action="store_true", help="create every hierarchy before the stream starts")
     a = ap.parse_args()
     out = run(seconds=a.seconds, rate=a.rate, sizes=tuple(int(v) for v in a.sizes.split(",")),
               max_active=a.max_active, kinds=tuple(k for k in a.kinds.split(",") if k),
               amr_kinds=tuple(k for k in a.amr.split(",") if k),
-              amr_sizes=tuple(int(v) for v in a.amr_sizes.split(",")), max_queue=a.max_queue)
+              amr_sizes=tuple(int(v) for v in a.amr_sizes.split(",")), max_queue=a.max_queue,
+              prewarm=a.prewarm)
     print(json.dumps(out), flush=True)
 
 

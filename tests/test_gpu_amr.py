@@ -148,3 +148,34 @@ def test_amr_config3_at_stated_size_matches_oracle(E, ctx):
     full = amr.solve(rel_tol=1e-8, max_cycles=200)
     assert full["status"] == 0 and full["rel_residual"] <= 1e-8
     amr.close()
+
+
+@pytest.mark.parametrize("reading,name", [("R1", "crack2"), ("R1", "crack3"), ("R2", "crack2_r2")])
+def test_amr_mixed_composite_solve_reaches_the_oracle(E, ctx, reading, name):
+    """FP32 composite cycles inside FP64 refinement: at a relative composite residual of
+    1e-8 (checked in FP64) every level is within 1e-7 of the oracle's FP64 solution."""
+    specs = (layouts() if reading == "R1" else r2_layouts())[name]()
+    amr = E.Amr(ctx, specs, reading=reading, mixed=True)
+    info = amr.solve(rel_tol=1e-8, max_cycles=200, precision=E.MIXED)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+    ref, rinfo = A.solve(specs, tol=1e-8, max_cycles=200, reading=reading)
+    for l, (g, r) in enumerate(zip(amr.displacements(), ref)):
+        sp = specs[l]
+        sl = (slice(None),) + tuple(slice(sp.valid_lo[d] - sp.grid_lo[d], sp.valid_hi[d] - sp.grid_lo[d] + 1)
+                                    for d in (2, 1, 0))
+        assert rel_err(g[sl], r[sl]) < 1e-7, (name, l)
+    amr.close()
+
+
+def test_amr_config3_at_stated_size_mixed(E, ctx):
+    """Config 3 in mixed precision: converges to 1e-8 (FP64 composite norm) and agrees
+    with the FP64 composite solve of the same layout."""
+    specs = M.amr_penny_crack(base_n=65, nlevels=3, block=32)
+    amr = E.Amr(ctx, specs, mixed=True)
+    i64 = amr.solve(rel_tol=1e-9, max_cycles=200)
+    u64 = amr.displacements()
+    imx = amr.solve(rel_tol=1e-8, max_cycles=200, precision=E.MIXED)
+    assert i64["status"] == 0 and imx["status"] == 0 and imx["rel_residual"] <= 1e-8
+    for l, (a_, b_) in enumerate(zip(amr.displacements(), u64)):
+        assert rel_err(a_, b_) < 1e-6, l
+    amr.close()

@@ -146,3 +146,33 @@ def test_request_loop_with_amr_requests_and_bounded_admission(E):
     assert out["completed"] > 0 and out["converged"] == out["completed"]
     assert out["refused"] >= 0 and out["max_queue"] == 6
     assert out["latency_ms"]["p99"] >= out["latency_ms"]["p50"] > 0
+
+
+def test_mixed_amr_request_is_the_same_alone_and_in_the_mix(E):
+    from paper_2001_04789_gb300 import microstructure as M2
+    ctx = E.Context(0)
+    specs = M2.amr_penny_crack(base_n=17, nlevels=2, block=8, width=3.0 / 32)
+    amr = E.Amr(ctx, specs, mixed=True)
+    alone = amr.solve(rel_tol=1e-8, precision=E.MIXED)
+    u_alone = amr.displacements()
+    g = E.grid_from_problem(ctx, problems()[0], mixed=True)
+    server = E.Server(ctx, max_active=2)
+    ta = server.submit_amr(amr, precision=E.MIXED, rel_tol=1e-8)
+    tg = server.submit(g, rel_tol=1e-8)
+    done = {}
+    for _ in range(1000):
+        server.step()
+        for t in (ta, tg):
+            if t not in done:
+                r = server.poll(t)
+                if r is not None:
+                    done[t] = r[0]
+        if len(done) == 2:
+            break
+    assert done[ta]["status"] == 0 and done[ta]["cycles"] == alone["cycles"]
+    for ua, ub in zip(u_alone, amr.displacements()):
+        assert np.array_equal(ua, ub)
+    server.close()
+    amr.close()
+    g.close()
+    ctx.close()
