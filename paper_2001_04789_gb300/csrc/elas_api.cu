@@ -208,6 +208,7 @@ void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int 
     L.bcoef = nullptr;
     L.msplit1 = 0;
     L.omega = (T)1;
+    L.xface_list = 0;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -637,17 +638,20 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     v.L32.mod = v.mod32;
     v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
     v.L32.msplit1 = v.split ? split_half_entries((v.N + 1) / 2) : 0;
-    // list of the nodes on two or three boundary planes (face nodes are enumerated
-    // arithmetically by the face kernels)
+    // list of the nodes whose rows are stored as coefficients: the nodes on two or three
+    // boundary planes, and the nodes of the x faces (their stencil neighbours lie nx apart,
+    // so rows evaluated from the fields would read one sector per value); the y and z
+    // face nodes are enumerated arithmetically by the face kernels
     std::vector<int> b;
     const int* per = g->desc.periodic;
     for (int z = 0; z < v.n[2]; ++z)
         for (int y = 0; y < v.n[1]; ++y)
             for (int x = 0; x < v.n[0]; ++x) {
-                const int on = (!per[0] && (x == 0 || x == v.n[0] - 1)) + (!per[1] && (y == 0 || y == v.n[1] - 1)) +
-                               (!per[2] && (z == 0 || z == v.n[2] - 1));
-                if (on >= 2) b.push_back(x + v.n[0] * (y + v.n[1] * z));   // edges and corners
+                const bool xf = !per[0] && (x == 0 || x == v.n[0] - 1);
+                const int on = xf + (!per[1] && (y == 0 || y == v.n[1] - 1)) + (!per[2] && (z == 0 || z == v.n[2] - 1));
+                if (on >= 2 || xf) b.push_back(x + v.n[0] * (y + v.n[1] * z));
             }
+    v.L64.xface_list = v.L32.xface_list = per[0] ? 0 : 1;
     v.nbnd = (int)b.size();
     if (v.nbnd) {
         if ((rc = galloc(g, &v.bnd, b.size()))) return rc;
@@ -678,6 +682,7 @@ void refresh_lv(elas_grid g) {
         v.L64.bcoef = v.bcoef64;
         v.L32.bcoef = v.bcoef32;
         v.L64.nbnd = v.L32.nbnd = v.nbnd;
+        v.L64.xface_list = v.L32.xface_list = g->desc.periodic[0] ? 0 : 1;
         v.L64.divc = v.divc;
         v.L32.modh = v.mod16;
         v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
@@ -804,7 +809,9 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
             total += (d->half_moduli ? 2 : 4) * (split ? split_entries((int)N) : moduli_copy_entries((int)N, K, d->half_moduli)) +
                      N * 48;
         }
-        total += (size_t)4 * (n[0] + n[1] + n[2]) * kEdgeCoef * (d->mixed ? 12 : 8);   // edge rows
+        // stored rows: edges and corners, and the x faces
+        const size_t stored = (size_t)4 * (n[0] + n[1] + n[2]) + (d->periodic[0] ? 0 : (size_t)2 * n[1] * n[2]);
+        total += stored * kEdgeCoef * (d->mixed ? 12 : 8);
     }
     const size_t N0 = (size_t)d->n[0] * d->n[1] * d->n[2];
     total += N0 * 8 * 9;   // eigenstrain + body force when given

@@ -53,6 +53,8 @@ struct Lv {
     size_t msplit1;
     // damping of the Jacobi smoother (colour kJacobiColour); the other smoothers ignore it
     T omega;
+    // 1: the x-face nodes are in bnodes (rows from stored coefficients), not face kernels
+    int xface_list;
 };
 
 // Which nodes one smoother pass updates.  Colours 0 and 1: red-black, (i + j + k) mod 2;
