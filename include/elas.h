@@ -169,7 +169,22 @@ typedef struct {
                              ELAS_SMOOTH_JACOBI; nu1, nu2 count its sweeps         */
     int    cycle;         /* ELAS_CYCLE_V (default) or ELAS_CYCLE_F                 */
     double omega;         /* damping of ELAS_SMOOTH_JACOBI, in (0, 1] (default 2/3) */
+    int    outer_residual;/* mixed: arithmetic of the refinement residual,
+                             ELAS_OUTER_AUTO (default), ELAS_OUTER_FP64 or
+                             ELAS_OUTER_DF                                         */
 } elas_solve_opts;
+
+/* Arithmetic of the refinement residual r = f - D_H(u) of a mixed solve.  FP64: plain
+ * FP64 operations.  DF: double-float, every operation on an unevaluated FP32 pair
+ * hi + lo (about 48 bits; rounding error a few 2^-47 of the operands' magnitudes) on
+ * the FP32 pipes, from double-float copies of u, f and the moduli that the grid keeps
+ * beside the FP64 ones (8 bytes per value); its residual floor lies near 1e-12 of the
+ * load.  AUTO: DF when rel_tol >= 1e-11 or fixed_cycles > 0, else FP64.  The solution
+ * stays an FP64 field either way; info->rel_residual is the norm of the residual so
+ * evaluated. */
+#define ELAS_OUTER_AUTO 0
+#define ELAS_OUTER_FP64 1
+#define ELAS_OUTER_DF   2
 
 #define ELAS_HISTORY 128
 typedef struct {
@@ -215,7 +230,11 @@ int  elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2);
  * product rule, half-cell closure of Eq. 1c), Neumann rows, u itself on
  * Dirichlet rows. */
 int  elas_op_apply(elas_grid g, int level, int precision, const void* u, void* out);
-/* r = f - A u (0 on Dirichlet rows); *sumsq = sum r^2 (FP64 reduction). */
+/* r = f - A u (0 on Dirichlet rows); *sumsq = sum r^2 (FP64 reduction).  precision
+ * ELAS_OP_DF: the refinement residual of a mixed solve, in double-float arithmetic
+ * from FP64 u and f, r written as FP32 (level 0 of a mixed grid with a hierarchy;
+ * sumsq then sums the FP32 values of r). */
+#define ELAS_OP_DF 2
 int  elas_op_residual(elas_grid g, int level, int precision, const void* u, const void* f,
                       void* r, double* sumsq);
 /* One red-black sweep (red then black, Jacobi within a colour), in place on u. */

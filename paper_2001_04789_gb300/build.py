@@ -15,7 +15,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libelas_gb300.so")
 SOURCES = ["elas_sweep_f32.cu", "elas_sweep_f32_iso.cu", "elas_sweep_f32_h.cu", "elas_sweep_f32_tiled.cu",
            "elas_sweep_f32_split.cu", "elas_batch.cu",
-           "elas_sweep_f64.cu", "elas_residual.cu", "elas_residual_f64.cu", "elas_kernels.cu", "elas_api.cu"]
+           "elas_sweep_f64.cu", "elas_residual.cu", "elas_residual_f64.cu", "elas_residual_df.cu", "elas_kernels.cu", "elas_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

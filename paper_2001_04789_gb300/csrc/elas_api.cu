@@ -92,6 +92,9 @@ struct Level {
     double* bcoef64 = nullptr;   // edge and corner row coefficients (kEdgeCoef per node)
     float* bcoef32 = nullptr;
     NullInfo nf{};
+    // double-float copies read by the refinement residual of a mixed solve (finest level of
+    // a mixed grid): moduli (K planes, then the 18 divergence planes), u, f, stored rows
+    dfloat *m2 = nullptr, *u2 = nullptr, *f2 = nullptr, *bc2 = nullptr;
 };
 
 }  // namespace
@@ -123,6 +126,7 @@ struct elas_grid_s {
     bool rhs_dirty = true;     // only loads / boundary data changed: rebuild the right-hand side
     bool gram_valid = false;   // W^T W of the finest level (depends on boundary types, not moduli)
     unsigned long long gen = 0;   // full set-ups so far (a cached batch plan checks it)
+    unsigned long long df_gen = ~0ull;   // set-up whose moduli the double-float copies hold
     // smoother and cycle of the solve in progress (from its options)
     int smoother = ELAS_SMOOTH_RB;
     int cycle = ELAS_CYCLE_V;
@@ -209,6 +213,48 @@ void fill_lv(Lv<T>& L, const int n[3], const int per[3], const double h[3], int 
     L.msplit1 = 0;
     L.omega = (T)1;
     L.xface_list = 0;
+}
+
+// The level seen by the double-float residual: the FP64 view's geometry, boundary types
+// and flags with double-float constants and the double-float planes.
+Lv<dfloat> df_view(const Level& v) {
+    const Lv<double>& S = v.L64;
+    Lv<dfloat> L{};
+    for (int d = 0; d < 3; ++d) {
+        L.n[d] = S.n[d];
+        L.per[d] = S.per[d];
+        L.h[d] = dfloat(S.h[d]);
+        L.inv2h[d] = dfloat(S.inv2h[d]);
+        L.invh[d] = dfloat(S.invh[d]);
+        L.invh2[d] = dfloat(S.invh2[d]);
+        L.inv4hh[d] = dfloat(S.inv4hh[d]);
+    }
+    L.N = S.N;
+    L.K = S.K;
+    L.mlay = kModPlanes;
+    for (int f = 0; f < 6; ++f)
+        for (int c = 0; c < 3; ++c) L.bc[f][c] = S.bc[f][c];
+    L.mod = v.m2;
+    L.bnodes = S.bnodes;
+    L.nbnd = S.nbnd;
+    L.divc = (S.K == 21 && v.divc && v.m2) ? v.m2 + (size_t)21 * v.N : nullptr;
+    L.active = S.active;
+    L.modh = nullptr;
+    L.bcoef = v.bc2;
+    L.msplit1 = 0;
+    L.omega = dfloat(S.omega);
+    L.xface_list = S.xface_list;
+    return L;
+}
+
+// Whether a level keeps its x-face rows as stored coefficients (a warp per node) rather
+// than evaluating them in the face kernels.  Measured per FP32 half-sweep: 257^3 0.53 ->
+// 0.48 ms with the list, 129^3 93.6 -> 91.1 us (best shapes), 65^3 31.1 -> 37.5 us
+// (the 243 coefficients of a face node add a quarter to the level's bytes there), and
+// no difference below: the list is kept on levels of at least 2^20 nodes.
+constexpr size_t kXFaceListMinNodes = size_t(1) << 20;
+bool xface_listed(const int n[3], const int per[3]) {
+    return !per[0] && (size_t)n[0] * n[1] * n[2] >= kXFaceListMinNodes;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -597,6 +643,70 @@ void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const dou
     smooth<T>(g, l, nu2, nf, lam);
 }
 
+// The refinement residual of a mixed solve: double-float (from the grid's double-float
+// copies, kept in step with u by outer_begin and outer_correct) or FP64, both written as
+// FP32 into the FP32 level's right-hand side with FP64 block partials of the norms.
+// The copies are made on the first solve that takes the double-float residual (grids of
+// AMR layouts never do) and refreshed after each full set-up.
+constexpr double kDfMinTol = 1e-11;   // AUTO: below this tolerance the FP64 residual
+bool outer_df(elas_grid g, const elas_solve_opts* o) {
+    if (!g->desc.mixed || g->lv.size() < 2 || o->outer_residual == ELAS_OUTER_FP64) return false;
+    if (o->outer_residual == ELAS_OUTER_DF) return true;
+    return o->fixed_cycles > 0 || o->rel_tol >= kDfMinTol;
+}
+
+// Allocate (once) and fill (after a set-up) the double-float copies of the finest level's
+// moduli, divergence and stored rows; u and f are split at the start of each solve.
+int df_prepare(elas_grid g) {
+    Level& v = g->lv[0];
+    const size_t N = (size_t)v.N;
+    int rc = ELAS_OK;
+    if (!v.m2) {
+        if (!rc) rc = galloc(g, &v.m2, (size_t)(g->K == 21 ? 39 : 2) * N);
+        if (!rc) rc = galloc(g, &v.u2, 3 * N);
+        if (!rc) rc = galloc(g, &v.f2, 3 * N);
+        if (!rc && v.nbnd) rc = galloc(g, &v.bc2, (size_t)v.nbnd * kEdgeCoef);
+        if (rc) return rc;
+        g->df_gen = ~0ull;
+    }
+    if (g->df_gen != g->gen) {
+        elas_ctx c = g->ctx;
+        cudaStream_t s = c->stream;
+        launch_split_df(v.mod64, v.m2, (size_t)g->K * N, s);
+        if (v.divc) launch_split_df(v.divc, v.m2 + 21 * N, 18 * N, s);
+        if (v.bc2) launch_split_df(v.bcoef64, v.bc2, (size_t)v.nbnd * kEdgeCoef, s);
+        CHECK_LAUNCH(c);
+        g->df_gen = g->gen;
+    }
+    return ELAS_OK;
+}
+
+void outer_begin(elas_grid g, bool df, cudaStream_t s) {
+    if (!df) return;
+    Level& L0 = g->lv[0];
+    launch_split_df(L0.u, L0.u2, 3 * (size_t)L0.N, s);
+    launch_split_df(L0.f, L0.f2, 3 * (size_t)L0.N, s);
+}
+
+void outer_residual(elas_grid g, bool df, const NullInfo* nf0, const double* load, int* nb, cudaStream_t s) {
+    Level& L0 = g->lv[0];
+    if (df) launch_residual_df(df_view(L0), L0.u2, L0.f2, nf0, load, L0.f32, g->partials, nb, s);
+    else launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, load, L0.f32, g->partials, nb, s);
+}
+
+void outer_correct(elas_grid g, bool df, cudaStream_t s) {
+    Level& L0 = g->lv[0];
+    if (df) launch_add_correction_df(L0.L64, L0.u, L0.u32, L0.u2, s);
+    else launch_add_correction(L0.L64, L0.u, L0.u32, s);
+}
+
+// Every member of a batch takes the same residual arithmetic.
+bool batch_df(elas_grid* grids, int n, const elas_solve_opts* o) {
+    for (int i = 0; i < n; ++i)
+        if (!outer_df(grids[i], o)) return false;
+    return n > 0;
+}
+
 int remove_rigid(elas_grid g) {
     Level& L0 = g->lv[0];
     if (L0.nf.m == 0) return ELAS_OK;
@@ -639,19 +749,20 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
     v.L32.msplit1 = v.split ? split_half_entries((v.N + 1) / 2) : 0;
     // list of the nodes whose rows are stored as coefficients: the nodes on two or three
-    // boundary planes, and the nodes of the x faces (their stencil neighbours lie nx apart,
-    // so rows evaluated from the fields would read one sector per value); the y and z
-    // face nodes are enumerated arithmetically by the face kernels
+    // boundary planes, and on large levels the nodes of the x faces (their stencil
+    // neighbours lie nx apart, so rows evaluated from the fields read one sector per
+    // value); the other face nodes are enumerated arithmetically by the face kernels
     std::vector<int> b;
     const int* per = g->desc.periodic;
+    const bool xlist = xface_listed(v.n, per);
     for (int z = 0; z < v.n[2]; ++z)
         for (int y = 0; y < v.n[1]; ++y)
             for (int x = 0; x < v.n[0]; ++x) {
                 const bool xf = !per[0] && (x == 0 || x == v.n[0] - 1);
                 const int on = xf + (!per[1] && (y == 0 || y == v.n[1] - 1)) + (!per[2] && (z == 0 || z == v.n[2] - 1));
-                if (on >= 2 || xf) b.push_back(x + v.n[0] * (y + v.n[1] * z));
+                if (on >= 2 || (xf && xlist)) b.push_back(x + v.n[0] * (y + v.n[1] * z));
             }
-    v.L64.xface_list = v.L32.xface_list = per[0] ? 0 : 1;
+    v.L64.xface_list = v.L32.xface_list = xlist ? 1 : 0;
     v.nbnd = (int)b.size();
     if (v.nbnd) {
         if ((rc = galloc(g, &v.bnd, b.size()))) return rc;
@@ -682,7 +793,7 @@ void refresh_lv(elas_grid g) {
         v.L64.bcoef = v.bcoef64;
         v.L32.bcoef = v.bcoef32;
         v.L64.nbnd = v.L32.nbnd = v.nbnd;
-        v.L64.xface_list = v.L32.xface_list = g->desc.periodic[0] ? 0 : 1;
+        v.L64.xface_list = v.L32.xface_list = xface_listed(v.n, g->desc.periodic) ? 1 : 0;
         v.L64.divc = v.divc;
         v.L32.modh = v.mod16;
         v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
@@ -801,7 +912,8 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
     if (!d) return 0;
     const int K = d->moduli_kind;
     size_t total = 0;
-    for (auto& n : level_dims(*d)) {
+    const auto dims = level_dims(*d);
+    for (auto& n : dims) {
         const size_t N = (size_t)n[0] * n[1] * n[2];
         total += N * 8 * (K + 12 + (K == 21 ? 18 : 0));
         if (d->mixed) {
@@ -810,8 +922,10 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
                      N * 48;
         }
         // stored rows: edges and corners, and the x faces
-        const size_t stored = (size_t)4 * (n[0] + n[1] + n[2]) + (d->periodic[0] ? 0 : (size_t)2 * n[1] * n[2]);
+        const size_t stored = (size_t)4 * (n[0] + n[1] + n[2]) + (xface_listed(n.data(), d->periodic) ? (size_t)2 * n[1] * n[2] : 0);
         total += stored * kEdgeCoef * (d->mixed ? 12 : 8);
+        if (d->mixed && d->max_levels != 1 && &n == &dims.front())   // double-float copies of the finest level
+            total += 8 * (N * ((K == 21 ? 39 : 2) + 6) + stored * kEdgeCoef);
     }
     const size_t N0 = (size_t)d->n[0] * d->n[1] * d->n[2];
     total += N0 * 8 * 9;   // eigenstrain + body force when given
@@ -1004,6 +1118,7 @@ void elas_solve_opts_default(elas_solve_opts* o) {
     o->smoother = ELAS_SMOOTH_RB;
     o->cycle = ELAS_CYCLE_V;
     o->omega = 2.0 / 3.0;
+    o->outer_residual = ELAS_OUTER_AUTO;
 }
 
 namespace {
@@ -1013,6 +1128,8 @@ int take_cycle_opts(elas_grid g, const elas_solve_opts* o) {
         return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "unknown smoother or cycle");
     if (o->smoother == ELAS_SMOOTH_JACOBI && !(o->omega > 0.0 && o->omega <= 1.0))
         return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "Jacobi damping must lie in (0, 1]");
+    if (o->outer_residual < ELAS_OUTER_AUTO || o->outer_residual > ELAS_OUTER_DF)
+        return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "unknown outer residual arithmetic");
     g->smoother = o->smoother;
     g->cycle = o->cycle;
     g->omega = o->omega;
@@ -1034,10 +1151,13 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
     if (rc) return rc;
     rc = setup(g);
     if (rc) return rc;
+    if (mixed && outer_df(g, opts) && (rc = df_prepare(g))) return rc;
     cudaStream_t s = c->stream;
     Level& L0 = g->lv[0];
     const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
     launch_dirichlet(L0.L64, boundary_data(g), L0.u, opts->warm_start ? 1 : 0, s);
+    const bool df = mixed && outer_df(g, opts);
+    outer_begin(g, df, s);
     CHECK_LAUNCH(c);
     CUDA_TRY(c, cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, s));
     CUDA_TRY(c, cudaMemsetAsync(g->alam, 0, sizeof(double) * kLoadDoubles, s));
@@ -1056,7 +1176,7 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
         if (!mixed) smooth<double>(g, 0, nu1, nf0, load);
         const size_t ev = prof_begin(c, ELAS_PROF_RESID64_L0);
         if (!mixed) launch_residual<double, double>(L0.L64, L0.u, L0.f, nf0, load, L0.r, g->partials, &nb, s);
-        else launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, load, L0.f32, g->partials, &nb, s);
+        else outer_residual(g, df, nf0, load, &nb, s);
         prof_end(c, ev);
         CHECK_LAUNCH(c);
         launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1, s);
@@ -1101,7 +1221,7 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
             // FP32 V-cycles on the correction equation, the first from zero
             const int inner = opts->inner_cycles > 1 ? opts->inner_cycles : 1;
             for (int k = 0; k < inner; ++k) vcycle<float>(g, 0, nu1, nu2, nf0, dload, k == 0, g->cycle);
-            launch_add_correction(L0.L64, L0.u, L0.u32, s);
+            outer_correct(g, df, s);
         }
         CHECK_LAUNCH(c);
         ++cycles;
@@ -1188,9 +1308,11 @@ int elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2) {
 }
 
 // ---- single operations ----------------------------------------------------------------
-static int check_level(elas_grid g, int level, int precision) {
+static int check_level(elas_grid g, int level, int precision, bool allow_df = false) {
     if (!g) return ELAS_ERR_INVALID_ARG;
     if (level < 0 || level >= (int)g->lv.size()) return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "bad level");
+    if (precision < 0 || precision > (allow_df ? ELAS_OP_DF : 1))
+        return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "bad precision");
     if (precision == 1 && !g->desc.mixed) return set_err(g->ctx, ELAS_ERR_STATE, "no FP32 hierarchy");
     return setup(g);
 }
@@ -1207,11 +1329,22 @@ int elas_op_apply(elas_grid g, int level, int precision, const void* u, void* ou
 }
 
 int elas_op_residual(elas_grid g, int level, int precision, const void* u, const void* f, void* r, double* sumsq) {
-    int rc = check_level(g, level, precision);
+    int rc = check_level(g, level, precision, true);
     if (rc) return rc;
     Level& v = g->lv[level];
     int nb = 0;
-    if (precision == 0)
+    if (precision == ELAS_OP_DF) {
+        // double-float residual of the finest level of a mixed grid (the refinement residual)
+        elas_solve_opts o;
+        elas_solve_opts_default(&o);
+        o.outer_residual = ELAS_OUTER_DF;
+        if (level != 0 || !outer_df(g, &o))
+            return set_err(g->ctx, ELAS_ERR_STATE, "double-float residual: finest level of a mixed grid with a hierarchy only");
+        if ((rc = df_prepare(g))) return rc;
+        launch_split_df((const double*)u, v.u2, 3 * (size_t)v.N, g->ctx->stream);
+        launch_split_df((const double*)f, v.f2, 3 * (size_t)v.N, g->ctx->stream);
+        launch_residual_df(df_view(v), v.u2, v.f2, nullptr, nullptr, (float*)r, g->partials, &nb, g->ctx->stream);
+    } else if (precision == 0)
         launch_residual<double, double>(v.L64, (const double*)u, (const double*)f, nullptr, nullptr, (double*)r,
                                         g->partials, &nb, g->ctx->stream);
     else
@@ -1481,6 +1614,7 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
         std::memset(&info[i], 0, sizeof(info[i]));
         int rc = take_cycle_opts(grids[i], opts);
         if (!rc) rc = setup(grids[i]);
+        if (!rc && outer_df(grids[i], opts)) rc = df_prepare(grids[i]);
         if (rc) return rc;
     }
     if (batch_engine_applies(grids, n, opts)) {
@@ -1516,6 +1650,7 @@ struct BatchPlan {
     std::vector<unsigned long long> gen;
     std::vector<double> r0;
     int nu1 = 0, nu2 = 0, inner = 1, cycle = 0, max_cycles = 0, fixed = 0;
+    bool df = false;   // double-float refinement residual
     double tol = 0.0;
     void* mem = nullptr;
     size_t bytes = 0;
@@ -1599,14 +1734,15 @@ bool plan_matches(const BatchPlan* p, elas_grid* grids, int n, const elas_solve_
     if (!p || (int)p->members.size() != n) return false;
     if (p->nu1 != o->nu1 || p->nu2 != o->nu2 || p->inner != (o->inner_cycles > 1 ? o->inner_cycles : 1) ||
         p->cycle != o->cycle || p->tol != o->rel_tol ||
-        p->max_cycles != (o->fixed_cycles > 0 ? o->fixed_cycles : o->max_cycles) || p->fixed != o->fixed_cycles)
+        p->max_cycles != (o->fixed_cycles > 0 ? o->fixed_cycles : o->max_cycles) || p->fixed != o->fixed_cycles ||
+        p->df != batch_df(grids, n, o))
         return false;
     for (int i = 0; i < n; ++i)
         if (p->members[i] != grids[i] || p->gen[i] != grids[i]->gen || p->r0[i] != grids[i]->r0) return false;
     return true;
 }
 
-// Build the task arrays of one refinement step of every member (FP64 residual, the
+// Build the task arrays of one refinement step of every member (FP64 or double-float residual, the
 // load update and convergence test, `inner` FP32 V-cycles level by level, the FP64
 // correction), upload them, and capture two steps as a graph.
 int plan_build(elas_grid* grids, int n, const elas_solve_opts* o, BatchPlan** out) {
@@ -1619,6 +1755,7 @@ int plan_build(elas_grid* grids, int n, const elas_solve_opts* o, BatchPlan** ou
     p->tol = o->rel_tol;
     p->fixed = o->fixed_cycles;
     p->max_cycles = o->fixed_cycles > 0 ? o->fixed_cycles : o->max_cycles;
+    p->df = batch_df(grids, n, o);
     const int H = ELAS_HISTORY;
     const size_t flag_bytes = ((size_t)2 * n * sizeof(int) + 255) & ~size_t(255);
     const size_t hist_bytes = ((size_t)n * H * sizeof(double) + 255) & ~size_t(255);
@@ -1640,19 +1777,29 @@ int plan_build(elas_grid* grids, int n, const elas_solve_opts* o, BatchPlan** ou
         for (int i = 0; i < n; ++i)
             for (auto& v : grids[i]->lv) v.L64.active = v.L32.active = flags + i;
         NullInfo none{};
-        // FP64 residual (written as FP32 into the level-0 right-hand side) and finalize
+        // FP64 or double-float residual (written as FP32 into the level-0 right-hand side)
+        // and finalize
         std::vector<ResidTask<double, float>> r64;
+        std::vector<ResidTask<dfloat, float>> rdf;
         std::vector<FinalizeTask> fin;
         std::vector<CorrTask> corr;
         for (int i = 0; i < n; ++i) {
             elas_grid g = grids[i];
             Level& L0 = g->lv[0];
             const bool rm = L0.nf.m > 0;
-            ResidTask<double, float> t{L0.L64, L0.u, L0.f, rm ? L0.nf : none, rm ? g->alam : nullptr, L0.f32, g->partials};
-            r64.push_back(t);
             FinalizeTask ft{};
+            if (p->df) {
+                ResidTask<dfloat, float> t{df_view(L0), L0.u2, L0.f2, rm ? L0.nf : none, rm ? g->alam : nullptr,
+                                           L0.f32, g->partials};
+                rdf.push_back(t);
+                ft.nblocks = batch_task_blocks(kPhaseResidDf, &t);
+            } else {
+                ResidTask<double, float> t{L0.L64, L0.u, L0.f, rm ? L0.nf : none, rm ? g->alam : nullptr, L0.f32,
+                                           g->partials};
+                r64.push_back(t);
+                ft.nblocks = batch_task_blocks(kPhaseResid64, &t);
+            }
             ft.partials = g->partials;
-            ft.nblocks = batch_task_blocks(kPhaseResid64, &t);
             ft.nf = L0.nf;
             ft.Ginv = g->Ginv;
             ft.G = g->G;
@@ -1663,9 +1810,9 @@ int plan_build(elas_grid* grids, int n, const elas_solve_opts* o, BatchPlan** ou
             ft.out = g->status;
             ft.bf = BatchFlags{flags + i, counts + i, hist + (size_t)i * H, H, g->r0, o->rel_tol, p->max_cycles};
             fin.push_back(ft);
-            corr.push_back(CorrTask{L0.L64, L0.u, L0.u32});
+            corr.push_back(CorrTask{L0.L64, L0.u, L0.u32, p->df ? L0.u2 : nullptr});
         }
-        const PhaseRef ph_r64 = make_phase(ar, kPhaseResid64, r64, K, ml);
+        const PhaseRef ph_r64 = p->df ? make_phase(ar, kPhaseResidDf, rdf, K, ml) : make_phase(ar, kPhaseResid64, r64, K, ml);
         PhaseRef ph_fin;
         ph_fin.ph.kind = kPhaseFinalize;
         ph_fin.ph.n = n;
@@ -1817,6 +1964,7 @@ int batch_engine(elas_grid* grids, int n, const elas_solve_opts* o, elas_solve_i
         elas_grid g = grids[i];
         Level& L0 = g->lv[0];
         launch_dirichlet(L0.L64, boundary_data(g), L0.u, o->warm_start ? 1 : 0, main);
+        outer_begin(g, p->df, main);
         cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, main);
         cudaMemsetAsync(g->alam, 0, sizeof(double) * kLoadDoubles, main);
         cudaMemsetAsync(g->adlam, 0, sizeof(double) * kLoadDoubles, main);
@@ -1878,10 +2026,12 @@ int batch_run(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_i
     std::vector<int> h_flags(n, 1), h_counts(n, 0);
     CUDA_TRY(c, cudaMemcpyAsync(flags, h_flags.data(), sizeof(int) * n, cudaMemcpyHostToDevice, main));
     CUDA_TRY(c, cudaMemcpyAsync(counts, h_counts.data(), sizeof(int) * n, cudaMemcpyHostToDevice, main));
+    const bool dfb = batch_df(grids, n, opts);
     for (int i = 0; i < n; ++i) {
         elas_grid g = grids[i];
         Level& L0 = g->lv[0];
         launch_dirichlet(L0.L64, boundary_data(g), L0.u, opts->warm_start ? 1 : 0, main);
+        outer_begin(g, dfb, main);
         cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, main);
         cudaMemsetAsync(g->alam, 0, sizeof(double) * kLoadDoubles, main);
         cudaMemsetAsync(g->adlam, 0, sizeof(double) * kLoadDoubles, main);
@@ -1920,15 +2070,14 @@ int batch_run(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_i
             c->stream = c->branch[i % S];
             const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
             int nb = 0;
-            launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, nf0 ? g->alam : nullptr, L0.f32, g->partials, &nb,
-                                           c->stream);
+            outer_residual(g, dfb, nf0, nf0 ? g->alam : nullptr, &nb, c->stream);
             BatchFlags bfl{flags + i, counts + i, hist + (size_t)i * hist_len, (int)hist_len, g->r0, opts->rel_tol,
                            opts->fixed_cycles > 0 ? opts->fixed_cycles : opts->max_cycles};
             launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1,
                             c->stream, bfl);
             for (int k = 0; k < (opts->inner_cycles > 1 ? opts->inner_cycles : 1); ++k)
                 vcycle<float>(g, 0, nu1, nu2, nf0, nf0 ? g->adlam : nullptr, k == 0, opts->cycle);
-            launch_add_correction(L0.L64, L0.u, L0.u32, c->stream);
+            outer_correct(g, dfb, c->stream);
         }
     }
     for (int b = 0; b < S; ++b) {
@@ -2546,6 +2695,7 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
         } else {
             rc = take_cycle_opts(g, &r.opts);
             if (!rc) rc = setup(g);
+            if (!rc && outer_df(g, &r.opts)) rc = df_prepare(g);
         }
         if (rc) {
             ServerDone d{};
@@ -2563,6 +2713,7 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
         }
         Level& L0 = g->lv[0];
         launch_dirichlet(L0.L64, boundary_data(g), L0.u, r.opts.warm_start ? 1 : 0, main);
+        outer_begin(g, outer_df(g, &r.opts), main);
         cudaMemsetAsync(g->lam, 0, sizeof(double) * 8, main);
         cudaMemsetAsync(g->alam, 0, sizeof(double) * kLoadDoubles, main);
         cudaMemsetAsync(g->adlam, 0, sizeof(double) * kLoadDoubles, main);
@@ -2620,8 +2771,7 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
             }
             const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
             int nb = 0;
-            launch_residual<double, float>(L0.L64, L0.u, L0.f, nf0, nf0 ? g->alam : nullptr, L0.f32, g->partials, &nb,
-                                           c->stream);
+            outer_residual(g, outer_df(g, &r.opts), nf0, nf0 ? g->alam : nullptr, &nb, c->stream);
             BatchFlags bfl{s->flags + r.slot, s->counts + r.slot, s->hist + (size_t)r.slot * ELAS_HISTORY,
                            ELAS_HISTORY, g->r0, r.opts.rel_tol,
                            r.opts.fixed_cycles > 0 ? r.opts.fixed_cycles : r.opts.max_cycles};
@@ -2629,7 +2779,7 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
                             c->stream, bfl);
             for (int k = 0; k < (r.opts.inner_cycles > 1 ? r.opts.inner_cycles : 1); ++k)
                 vcycle<float>(g, 0, r.opts.nu1, r.opts.nu2, nf0, nf0 ? g->adlam : nullptr, k == 0, r.opts.cycle);
-            launch_add_correction(L0.L64, L0.u, L0.u32, c->stream);
+            outer_correct(g, outer_df(g, &r.opts), c->stream);
         }
         c->stream = main;
         c->profile = prof;

@@ -109,7 +109,17 @@ __global__ void k_batch_corr(const CorrTask* __restrict__ tasks, const int2* __r
     __shared__ __align__(16) CorrTask t;
     const int b = load_task(tasks, bmap, t);
     if (inactive(t.L.active)) return;
-    add_correction_body<float>(t.L, t.u, t.e, b * kBlock + threadIdx.x);
+    if (t.u2) add_correction_df_body<float>(t.L, t.u, t.e, t.u2, b * kBlock + threadIdx.x);
+    else add_correction_body<float>(t.L, t.u, t.e, b * kBlock + threadIdx.x);
+}
+
+template <int KIND, bool HM>
+__global__ void __launch_bounds__(kBlock, 2)
+    k_batch_resid_df(const ResidTask<dfloat, float>* __restrict__ tasks, const int2* __restrict__ bmap) {
+    __shared__ __align__(16) ResidTask<dfloat, float> t;
+    const int b = load_task(tasks, bmap, t);
+    if (inactive(t.L.active)) return;
+    residual_df_block<KIND, true, HM, kDfNodesPerThread>(t.L, t.u, t.f, t.nf, t.lam, t.r, t.partials, b);
 }
 
 template <int KIND, bool HM, int ML>
@@ -149,6 +159,7 @@ int batch_task_blocks(int kind, const void* task) {
             const auto& t = *(const ResidTask<double, float>*)task;
             return bnd_segs(t.L, kBlock).f2 + nb(interior_count(t.L), kBlock);
         }
+        case kPhaseResidDf: return residual_df_blocks<kDfNodesPerThread>(((const ResidTask<dfloat, float>*)task)->L);
         case kPhaseRestrict: return nb(((const RestrictTask<float>*)task)->Lc.N, kBlock);
         case kPhaseProlong: return nb(((const ProlongTask<float>*)task)->Lf.N, kBlock);
         case kPhaseZero: return nb(((const ZeroTask<float>*)task)->n, kBlock);
@@ -171,6 +182,12 @@ void batch_phase_launch(const BatchPhase& ph, cudaStream_t s) {
             break;
         case kPhaseResid32: resid_launch<float, float, false>(ph, s); break;
         case kPhaseResid64: resid_launch<double, float, true>(ph, s); break;
+        case kPhaseResidDf: {
+            const auto* t = (const ResidTask<dfloat, float>*)ph.tasks;
+            if (ph.K == 21) k_batch_resid_df<21, true><<<ph.blocks, kBlock, 0, s>>>(t, ph.bmap);
+            else k_batch_resid_df<2, false><<<ph.blocks, kBlock, 0, s>>>(t, ph.bmap);
+            break;
+        }
         case kPhaseRestrict: k_batch_restrict<<<ph.blocks, kBlock, 0, s>>>((const RestrictTask<float>*)ph.tasks, ph.bmap); break;
         case kPhaseProlong: k_batch_prolong<<<ph.blocks, kBlock, 0, s>>>((const ProlongTask<float>*)ph.tasks, ph.bmap); break;
         case kPhaseZero: k_batch_zero<<<ph.blocks, kBlock, 0, s>>>((const ZeroTask<float>*)ph.tasks, ph.bmap); break;

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "elas_dfloat.cuh"
+
 namespace elas {
 
 enum : int { ROW_INTERIOR = 0, ROW_DIRICHLET = 1, ROW_TRACTION = 2, ROW_NEUMANN = 3 };
@@ -147,6 +149,10 @@ template <> __device__ __forceinline__ double xadd(double a, double b) { return 
 template <> __device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
 template <> __device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
 template <> __device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <> __device__ __forceinline__ dfloat xadd(dfloat a, dfloat b) { return df_add(a, b); }
+template <> __device__ __forceinline__ dfloat xsub(dfloat a, dfloat b) { return df_sub(a, b); }
+template <> __device__ __forceinline__ dfloat xmul(dfloat a, dfloat b) { return df_mul(a, b); }
+template <> __device__ __forceinline__ dfloat xfma(dfloat a, dfloat b, dfloat c) { return df_fma(a, b, c); }
 
 // ---- Voigt helpers ----------------------------------------------------------
 __host__ __device__ constexpr int voigt(int i, int j) { return i == j ? i : 6 - i - j; }

@@ -56,6 +56,19 @@ template <typename T, typename TR>
 void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf, const double* lam,
                      TR* r, double* partials, int* nblocks, cudaStream_t s);
 
+// The same residual of an FP64 level in double-float arithmetic from double-float copies
+// of u, f, the moduli (with the divergence) and the stored rows (L: the level with those
+// planes), written as FP32; partials (required) as launch_residual's.  Interior threads take
+// kDfNodesPerThread nodes each.
+constexpr int kDfNodesPerThread = 4;
+void launch_residual_df(const Lv<dfloat>& L, const dfloat* u, const dfloat* f, const NullInfo* nf, const double* lam,
+                        float* r, double* partials, int* nblocks, cudaStream_t s);
+int residual_df_block_count(const Lv<dfloat>& L);
+// out[i] = a[i] split into hi + lo (n elements)
+void launch_split_df(const double* a, dfloat* out, size_t n, cudaStream_t s);
+// u += e on the non-Dirichlet rows (as launch_add_correction) and u2 := split(u) everywhere
+void launch_add_correction_df(const Lv<double>& L, double* u, const float* e, dfloat* u2, cudaStream_t s);
+
 // One colour of the red-black block smoother, u_in -> u_out (all nodes written).
 template <typename T>
 void launch_half_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, int colour,
@@ -153,6 +166,7 @@ enum : int {
     kPhaseMatvec = 7,     // BottomTask<float>: dense inverse times it
     kPhaseFinalize = 8,   // FinalizeTask
     kPhaseCorr = 9,       // CorrTask: FP64 u += FP32 e
+    kPhaseResidDf = 10,   // ResidTask<dfloat, float>: double-float residual written as FP32, with partials
 };
 template <typename T>
 struct SweepTask {
@@ -215,6 +229,7 @@ struct CorrTask {
     Lv<double> L;
     double* u;
     const float* e;
+    dfloat* u2;   // non-null: also refresh the double-float copy of u
 };
 // A phase ready to launch: kind, member count, tasks and the block map in device memory
 // (for every block of the launch: its task and its block index within that task), total

@@ -329,9 +329,9 @@ __device__ __forceinline__ void edge_rows_coef(const Lv<T>& L, const T* __restri
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        s0 = xadd(s0, __shfl_xor_sync(0xffffffffu, s0, o));
-        s1 = xadd(s1, __shfl_xor_sync(0xffffffffu, s1, o));
-        s2 = xadd(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+        s0 = xadd(s0, shfl_xor_all(s0, o));
+        s1 = xadd(s1, shfl_xor_all(s1, o));
+        s2 = xadd(s2, shfl_xor_all(s2, o));
     }
     v[0] = s0;
     v[1] = s1;
@@ -955,6 +955,202 @@ __global__ void __launch_bounds__(16 * TY, MINB)
         }
     }
     cp_async_wait_all();
+}
+
+// ---- refinement residual in double-float arithmetic --------------------------------------
+// r = f - load - A u of an FP64 level evaluated on the FP32 pipes: u, f, the moduli with
+// their divergence and the stored rows are double-float planes split from the FP64 ones,
+// every term of the operator is a double-float operation (the same stencil code as the
+// FP64 kernel, instantiated for dfloat), and r is written as FP32 for the correction
+// cycle.  Per block: sum r^2 in FP32 (the stopping test needs a few digits of the norm)
+// and the six rigid moments in double-float (they cancel), stored as FP64 partials in
+// the layout of k_residual.  Interior threads take NPT nodes each, which spreads the
+// block reduction over NPT times more nodes.
+struct DfAcc {
+    float r2;
+    dfloat m[6];
+};
+
+template <bool NORM>
+__device__ __forceinline__ void residual_store_df(const Lv<dfloat>& L, const dfloat* __restrict__ f,
+                                                  const NullInfo& nf, const double* __restrict__ load,
+                                                  const int c[3], int p, const int types[3], const dfloat v[3],
+                                                  float* __restrict__ r, DfAcc& acc) {
+    dfloat rr[3];
+    float rf[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        dfloat ri(0.f, 0.f);
+        if (types[i] != ROW_DIRICHLET) {
+            dfloat fi = f[(size_t)i * L.N + p];
+            if (load) fi = df_sub(fi, dfloat(rigid_load<float>(nf, load, i, c)));
+            ri = df_sub(fi, v[i]);
+        }
+        rr[i] = ri;
+        rf[i] = df_to_float(ri);
+        r[(size_t)i * L.N + p] = rf[i];
+    }
+    if (NORM) {
+        acc.r2 = __fmaf_rn(rf[2], rf[2], __fmaf_rn(rf[1], rf[1], __fmaf_rn(rf[0], rf[0], acc.r2)));
+        if (nf.m > 0) {
+            const float d0 = xfma(nf.h32[0], float(c[0]), nf.off32[0]);
+            const float d1 = xfma(nf.h32[1], float(c[1]), nf.off32[1]);
+            const float d2 = xfma(nf.h32[2], float(c[2]), nf.off32[2]);
+            acc.m[0] = df_add(acc.m[0], rr[0]);
+            acc.m[1] = df_add(acc.m[1], rr[1]);
+            acc.m[2] = df_add(acc.m[2], rr[2]);
+            acc.m[3] = df_add(acc.m[3], df_sub(df_mul(rr[2], d1), df_mul(rr[1], d2)));
+            acc.m[4] = df_add(acc.m[4], df_sub(df_mul(rr[0], d2), df_mul(rr[2], d0)));
+            acc.m[5] = df_add(acc.m[5], df_sub(df_mul(rr[1], d0), df_mul(rr[0], d1)));
+        }
+    }
+}
+
+// Block sum of the accumulators into partials[bid * kPartialStride + 0 .. width)
+__device__ __forceinline__ void block_reduce_store_df(const DfAcc& a, int width, double* partials, int bid) {
+    __shared__ float sr[kBlock / 32];
+    __shared__ dfloat sm[kBlock / 32][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float x = a.r2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = __fadd_rn(x, shfl_xor_all(x, o));
+    if (lane == 0) sr[warp] = x;
+    if (width > 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            dfloat y = a.m[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y = df_add(y, shfl_xor_all(y, o));
+            if (lane == 0) sm[warp][k] = y;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        x = lane < kBlock / 32 ? sr[lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = __fadd_rn(x, shfl_xor_all(x, o));
+        if (lane == 0) partials[(size_t)bid * kPartialStride] = (double)x;
+        if (width > 1) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                dfloat y = lane < kBlock / 32 ? sm[lane][k] : dfloat(0.f, 0.f);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) y = df_add(y, shfl_xor_all(y, o));
+                if (lane == 0) partials[(size_t)bid * kPartialStride + 1 + k] = (double)y.hi + (double)y.lo;
+            }
+        }
+    }
+}
+
+template <int KIND, bool NORM>
+__device__ __forceinline__ void residual_bnd_body_df(const Lv<dfloat>& L, const dfloat* __restrict__ u,
+                                                     const dfloat* __restrict__ f, const NullInfo& nf,
+                                                     const double* __restrict__ lam, float* __restrict__ r, int w,
+                                                     int lane, DfAcc& acc) {
+    if (w >= L.nbnd) return;   // whole warp
+    const int p = L.bnodes[w];
+    int c[3];
+    coords_of(p, L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    int types[3];
+    for (int i = 0; i < 3; ++i) types[i] = row_type(L, ni, i);
+    dfloat v[3];
+    edge_rows_coef<dfloat>(L, u, ni, L.bcoef + (size_t)w * kEdgeCoef, lane, v);
+    if (lane == 0) residual_store_df<NORM>(L, f, nf, lam, c, p, types, v, r, acc);
+}
+
+template <int KIND, int A, bool NORM>
+__device__ __forceinline__ void residual_face_body_df(const Lv<dfloat>& L, const dfloat* __restrict__ u,
+                                                      const dfloat* __restrict__ f, const NullInfo& nf,
+                                                      const double* __restrict__ load, float* __restrict__ r, int t,
+                                                      DfAcc& acc) {
+    int c[3], side;
+    if (!face_coords<dfloat, A>(L, t, c, side)) return;
+    int types[3];
+    face_types<dfloat, A>(L, side, types);
+    dfloat v[3], B[3][3];
+    face_node<dfloat, KIND, A>(L, u, c, side, types, v, B, false);
+    residual_store_df<NORM>(L, f, nf, load, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
+}
+
+template <int KIND, bool NORM, bool HM, int NPT>
+__device__ __forceinline__ void residual_int_body_df(const Lv<dfloat>& L, const dfloat* __restrict__ u,
+                                                     const dfloat* __restrict__ f, const NullInfo& nf,
+                                                     const double* __restrict__ lam, float* __restrict__ r, int b,
+                                                     DfAcc& acc) {
+    int lo[3], cnt[3];
+    interior_box(L, lo, cnt);
+    const int total = cnt[0] * cnt[1] * cnt[2];
+#pragma unroll 1
+    for (int k = 0; k < NPT; ++k) {
+        const int t = (b * NPT + k) * kBlock + (int)threadIdx.x;
+        if (t >= total) break;
+        const int c[3] = {lo[0] + t % cnt[0], lo[1] + (t / cnt[0]) % cnt[1], lo[2] + t / (cnt[0] * cnt[1])};
+        dfloat v[3];
+        with_interior<dfloat, KIND, kMlDefault>(L, u, c[0], c[1], c[2], [&](const auto& ua, const auto& ca, int p) {
+            interior_rows_core<dfloat, KIND, HM>(L, ua, ca, p, v);
+        });
+        const int types[3] = {ROW_INTERIOR, ROW_INTERIOR, ROW_INTERIOR};
+        residual_store_df<NORM>(L, f, nf, lam, c, lin(L, c[0], c[1], c[2]), types, v, r, acc);
+    }
+}
+
+// Blocks of one launch: edge/corner/x-face warps, y- and z-face threads, interior
+// threads of NPT nodes each.
+template <int NPT>
+__host__ __device__ inline int residual_df_blocks(const Lv<dfloat>& L) {
+    const BndSegs sg = bnd_segs(L, kBlock);
+    return sg.f2 + (int)((interior_count(L) + (size_t)kBlock * NPT - 1) / ((size_t)kBlock * NPT));
+}
+
+template <int KIND, bool NORM, bool HM, int NPT>
+__device__ __forceinline__ void residual_df_block(const Lv<dfloat>& L, const dfloat* __restrict__ u,
+                                                  const dfloat* __restrict__ f, const NullInfo& nf,
+                                                  const double* __restrict__ lam, float* __restrict__ r,
+                                                  double* __restrict__ partials, int b) {
+    DfAcc acc;
+    acc.r2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc.m[k] = dfloat(0.f, 0.f);
+    const BndSegs sg = bnd_segs(L, kBlock);
+    const int tid = threadIdx.x;
+    if (b < sg.e) residual_bnd_body_df<KIND, NORM>(L, u, f, nf, lam, r, (b * kBlock + tid) >> 5, tid & 31, acc);
+    else if (b < sg.f0) residual_face_body_df<KIND, 0, NORM>(L, u, f, nf, lam, r, (b - sg.e) * kBlock + tid, acc);
+    else if (b < sg.f1) residual_face_body_df<KIND, 1, NORM>(L, u, f, nf, lam, r, (b - sg.f0) * kBlock + tid, acc);
+    else if (b < sg.f2) residual_face_body_df<KIND, 2, NORM>(L, u, f, nf, lam, r, (b - sg.f1) * kBlock + tid, acc);
+    else residual_int_body_df<KIND, NORM, HM, NPT>(L, u, f, nf, lam, r, b - sg.f2, acc);
+    if (NORM) block_reduce_store_df(acc, nf.m > 0 ? 7 : 1, partials, b);
+}
+
+template <int KIND, bool NORM, bool HM, int NPT>
+__global__ void __launch_bounds__(kBlock, 2) k_residual_df(Lv<dfloat> L, const dfloat* __restrict__ u,
+                                                           const dfloat* __restrict__ f, NullInfo nf,
+                                                           const double* __restrict__ lam, float* __restrict__ r,
+                                                           double* __restrict__ partials) {
+    if (L.active && *L.active == 0) return;
+    residual_df_block<KIND, NORM, HM, NPT>(L, u, f, nf, lam, r, partials, blockIdx.x);
+}
+
+__device__ __forceinline__ dfloat df_split(double v) {
+    const float h = __double2float_rn(v);
+    return dfloat(h, __double2float_rn(v - (double)h));
+}
+
+template <typename TE>
+__device__ __forceinline__ void add_correction_df_body(const Lv<double>& L, double* __restrict__ u,
+                                                       const TE* __restrict__ e, dfloat* __restrict__ u2, int p) {
+    if (p >= L.N) return;
+    int c[3];
+    coords_of(p, L.n, c);
+    const NodeInfo ni = node_info(L, c[0], c[1], c[2]);
+    for (int i = 0; i < 3; ++i) {
+        double x = u[i * L.N + p];
+        if (row_type(L, ni, i) != ROW_DIRICHLET) {
+            x += (double)e[i * L.N + p];
+            u[i * L.N + p] = x;
+        }
+        u2[i * L.N + p] = df_split(x);
+    }
 }
 
 // r = f - load - A u on every node; block partials of sum r^2 and the rigid moments.

@@ -26,6 +26,8 @@ HOST, DEVICE = 0, 1
 FP64, MIXED = 0, 1
 SMOOTH_RB, SMOOTH_GS8, SMOOTH_JACOBI = 0, 1, 2
 CYCLE_V, CYCLE_F = 0, 1
+OUTER_AUTO, OUTER_FP64, OUTER_DF = 0, 1, 2   # arithmetic of a mixed solve's refinement residual
+OP_DF = 2   # op_residual: the refinement residual in double-float arithmetic (FP64 u, f; FP32 r)
 HISTORY = 128
 
 
@@ -50,7 +52,8 @@ class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("rel_tol", C.c_double), ("max_cycles", C.c_int),
                 ("nu1", C.c_int), ("nu2", C.c_int), ("warm_start", C.c_int),
                 ("fixed_cycles", C.c_int), ("use_graph", C.c_int), ("inner_cycles", C.c_int),
-                ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double)]
+                ("smoother", C.c_int), ("cycle", C.c_int), ("omega", C.c_double),
+                ("outer_residual", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -321,9 +324,9 @@ class Grid:
     # -- solve -------------------------------------------------------------------
     def solve(self, precision=FP64, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False,
               fixed_cycles=0, use_graph=False, raise_on_error=True, inner_cycles=1, smoother=None, cycle=None,
-              omega=None):
+              omega=None, outer=None):
         o = _opts(precision, rel_tol, max_cycles, nu1, nu2, warm_start, fixed_cycles, use_graph, inner_cycles,
-                  smoother, cycle, omega)
+                  smoother, cycle, omega, outer)
         info = SolveInfo()
         rc = lib().elas_solve(self.h, C.byref(o), C.byref(info))
         if rc != OK and raise_on_error and rc not in (ERR_NOT_CONVERGED,):
@@ -374,7 +377,9 @@ class Grid:
         return out
 
     def op_residual(self, level, precision, u, f):
-        r = self.ctx.torch.empty_like(u)
+        """r = f - A u and sum r^2; precision OP_DF: double-float from FP64 u, f, r in FP32."""
+        T = self.ctx.torch
+        r = T.empty_like(u, dtype=T.float32) if precision == OP_DF else T.empty_like(u)
         self.ctx.after_current(u, f, r)
         ss = C.c_double()
         self.ctx.check(lib().elas_op_residual(self.h, level, precision, _ptr(u), _ptr(f), _ptr(r), C.byref(ss)))
@@ -497,7 +502,7 @@ def grid_from_problem(ctx: Context, p: M.Problem, mixed=False, max_levels=0, hal
 
 
 def _opts(precision=FP64, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False, fixed_cycles=0,
-          use_graph=False, inner_cycles=1, smoother=None, cycle=None, omega=None):
+          use_graph=False, inner_cycles=1, smoother=None, cycle=None, omega=None, outer=None):
     o = SolveOpts()
     lib().elas_solve_opts_default(C.byref(o))
     o.precision, o.rel_tol, o.max_cycles = precision, rel_tol, max_cycles
@@ -510,6 +515,8 @@ def _opts(precision=FP64, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start
         o.cycle = int(cycle)
     if omega is not None:
         o.omega = float(omega)
+    if outer is not None:
+        o.outer_residual = int(outer)
     return o
 
 
@@ -558,7 +565,7 @@ class Amr:
 
 
 def batch_solve(grids, precision=MIXED, rel_tol=1e-8, max_cycles=100, nu1=2, nu2=2, warm_start=False,
-                fixed_cycles=0, raise_on_error=True, inner_cycles=1, cycle=None):
+                fixed_cycles=0, raise_on_error=True, inner_cycles=1, cycle=None, outer=None):
     """Solve every grid of one context together: one launch per phase of the cycle covers
     every member (grids of one moduli kind and layout; otherwise the members' own launches
     run as parallel branches), a captured CUDA graph replays refinement steps, and members
@@ -568,7 +575,8 @@ def batch_solve(grids, precision=MIXED, rel_tol=1e-8, max_cycles=100, nu1=2, nu2
     n = len(grids)
     arr = (C.c_void_p * n)(*[g.h for g in grids])
     infos = (SolveInfo * n)()
-    o = _opts(precision, rel_tol, max_cycles, nu1, nu2, warm_start, fixed_cycles, False, inner_cycles, None, cycle)
+    o = _opts(precision, rel_tol, max_cycles, nu1, nu2, warm_start, fixed_cycles, False, inner_cycles, None, cycle,
+              None, outer)
     rc = lib().elas_batch_solve(arr, n, C.byref(o), infos)
     if rc != OK and raise_on_error and rc != ERR_NOT_CONVERGED:
         raise ElasError(rc, grids[0].ctx.error())

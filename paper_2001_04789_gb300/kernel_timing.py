@@ -6,7 +6,8 @@ builds the n^3 polycrystal grid (finest level only), pins the smoother's launch 
 random fields, and prints one JSON line with the mean device time per launch (CUDA
 events on the library's stream) and the algorithmic and issued bandwidth.  Kernels:
 ``sweep32`` (one FP32 red-black sweep = two half-sweep launches), ``resid32`` (FP32
-residual), ``resid64`` (FP64 residual).  It is also the small profiling target for
+residual), ``resid64`` (FP64 residual), ``residdf`` (the double-float refinement
+residual; each call also splits u and f into double-float copies, two more launches).  It is also the small profiling target for
 ncu captures of these kernels.
 """
 from __future__ import annotations
@@ -20,7 +21,7 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=129)
-    ap.add_argument("--kernel", default="sweep32", choices=["sweep32", "resid32", "resid64"])
+    ap.add_argument("--kernel", default="sweep32", choices=["sweep32", "resid32", "resid64", "residdf"])
     ap.add_argument("--shape", type=int, default=3, help="smoother launch shape (autotuner index)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--grains", type=int, default=10)
@@ -32,12 +33,13 @@ def main():
     from . import microstructure as M
     p = M.polycrystal(a.n, grains=a.grains, seed=0)
     ctx = E.Context(0)
-    g = E.grid_from_problem(ctx, p, mixed=True, max_levels=1)
+    # the double-float residual belongs to grids with a hierarchy; the others time level 0 alone
+    g = E.grid_from_problem(ctx, p, mixed=True, max_levels=0 if a.kernel == "residdf" else 1)
     for flag in (0, 1, 2):
         E.autotune_load(f"{a.n} {a.n} {a.n} 21 4 {flag} {a.shape}")
     rng = np.random.default_rng(0)
-    dt = torch.float64 if a.kernel == "resid64" else torch.float32
-    prec = E.FP64 if a.kernel == "resid64" else E.MIXED
+    dt = torch.float64 if a.kernel in ("resid64", "residdf") else torch.float32
+    prec = {"resid64": E.FP64, "residdf": E.OP_DF}.get(a.kernel, E.MIXED)
     u = torch.as_tensor(rng.normal(size=(3,) + g.shape) * 1e-3, dtype=dt, device="cuda:0")
     f = torch.as_tensor(rng.normal(size=(3,) + g.shape), dtype=dt, device="cuda:0")
     torch.cuda.synchronize()
@@ -59,7 +61,7 @@ def main():
     ms = e0.elapsed_time(e1) / a.reps
     N = int(np.prod(p.n))
     launches = 2 if a.kernel == "sweep32" else 1
-    alg = {"sweep32": 120.0, "resid32": 120.0, "resid64": 240.0}[a.kernel]   # bytes per node per pass
+    alg = {"sweep32": 120.0, "resid32": 120.0, "resid64": 240.0, "residdf": 240.0}[a.kernel]   # bytes per node per pass
     print(json.dumps({"kernel": a.kernel, "n": a.n, "nodes": N, "shape": a.shape, "reps": a.reps,
                       "ms_per_launch": ms / launches, "ms_per_pass": ms,
                       "alg_GBs": alg * N / (ms * 1e-3) / 1e9}), flush=True)

@@ -43,7 +43,13 @@ def test_hbm_estimate_orders_precisions_and_sizes(E):
     # summed over a hierarchy of about 8/7 of the finest level, plus 9 input planes
     # (eigenstrain, body force) and the edge-row coefficients
     n0 = 33 ** 3
-    assert 8 * 51 * n0 <= fp64 <= 8 * 51 * n0 * 1.5
+    base = 8 * (51 + 9) * n0
+    assert base <= fp64 <= 1.5 * base
     big = M.polycrystal(65, grains=3, seed=0)
     ratio = est(big, mixed=True) / mixed
     assert 7.0 < ratio < 9.0            # node count grows 7.6x from 33^3 to 65^3
+    # levels of 2^20 nodes and more also store their x-face rows (243 coefficients a node)
+    n1 = 129 ** 3
+    large = M.Problem(n=(129, 129, 129), name="descriptor only")
+    large.moduli_kind = M.MODULI_GEN21
+    assert est(large) >= 8 * 60 * n1 + 8 * 243 * 2 * 129 * 129
