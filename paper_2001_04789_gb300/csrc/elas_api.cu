@@ -132,6 +132,20 @@ struct elas_grid_s {
     int cycle = ELAS_CYCLE_V;
     double omega = 2.0 / 3.0;
     std::vector<std::pair<void*, size_t>> allocs;
+    // captured multigrid cycles (see run_cycle), keyed by precision, level, start and cycle
+    // type, valid for the set-up, launch-shape table, options and stream they were
+    // captured with
+    struct CycleGraph {
+        cudaGraphExec_t exec = nullptr;   // null: capture failed, launch directly
+        int launches = 0;
+    };
+    std::map<int, CycleGraph> cyc;
+    unsigned long long cyc_gen = ~0ull, cyc_tune = ~0ull;
+    int cyc_nu1 = -1, cyc_nu2 = -1, cyc_smoother = -1;
+    double cyc_omega = -1.0;
+    const void* cyc_nf = nullptr;
+    const void* cyc_dlam = nullptr;
+    cudaStream_t cyc_stream = nullptr;
 };
 
 namespace {
@@ -611,6 +625,12 @@ void smooth(elas_grid g, int l, int sweeps, const NullInfo* nf, const double* la
 // Correction cycle on level l >= 1 (or l = 0 of the FP32 cycle): u_l from zero (or from
 // its current value).  cycle: ELAS_CYCLE_V, or ELAS_CYCLE_F, whose coarse-grid correction
 // is an F-cycle on the next level followed by a V-cycle from its result (Section 3.1).
+// From the finest level the cycles of the coarser levels run as captured graphs
+// (run_cycle); below it they recurse directly (inside such a capture).
+template <typename T>
+void run_cycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf, const double* dlam, bool zero_init,
+               int cycle);
+
 template <typename T>
 void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const double* dlam0, bool zero_init = true,
             int cycle = ELAS_CYCLE_V) {
@@ -633,14 +653,84 @@ void vcycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf0, const dou
     prof_end(g->ctx, e);
     Level& w = g->lv[l + 1];
     launch_restrict<T>(Fields<T>::L(v), Fields<T>::L(w), Fields<T>::r(v), Fields<T>::f(w), nullptr, nullptr, s);
+    auto descend = l == 0 ? run_cycle<T> : vcycle<T>;
     if (cycle == ELAS_CYCLE_F) {
-        vcycle<T>(g, l + 1, nu1, nu2, nullptr, nullptr, true, ELAS_CYCLE_F);
-        vcycle<T>(g, l + 1, nu1, nu2, nullptr, nullptr, false, ELAS_CYCLE_V);
+        descend(g, l + 1, nu1, nu2, nullptr, nullptr, true, ELAS_CYCLE_F);
+        descend(g, l + 1, nu1, nu2, nullptr, nullptr, false, ELAS_CYCLE_V);
     } else {
-        vcycle<T>(g, l + 1, nu1, nu2, nullptr, nullptr);
+        descend(g, l + 1, nu1, nu2, nullptr, nullptr, true, ELAS_CYCLE_V);
     }
     launch_prolong_add<T>(Fields<T>::L(v), Fields<T>::L(w), Fields<T>::u(w), Fields<T>::u(v), s);
     smooth<T>(g, l, nu2, nf, lam);
+}
+
+void cycle_graphs_free(elas_grid g) {
+    for (auto& kv : g->cyc)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    g->cyc.clear();
+}
+
+// One multigrid cycle from level l (vcycle's arguments), launched from a CUDA graph of
+// its whole launch sequence.  A cycle below the finest level is several dozen launches
+// of small kernels, so launching them one by one costs more host time than the GPU
+// spends on them; the graph of each (precision, level, start, cycle type) is captured
+// on first use and replayed until the set-up, the launch-shape table, the smoothing
+// options or the stream change.  Levels below the finest hold no profiled launches.
+// With a batch's activity flags set, within another capture, or where the stream cannot
+// be captured, the cycle is launched directly.  Replays compute exactly what the direct
+// launches compute.
+template <typename T>
+void run_cycle(elas_grid g, int l, int nu1, int nu2, const NullInfo* nf, const double* dlam, bool zero_init,
+               int cycle) {
+    elas_ctx c = g->ctx;
+    cudaStream_t s = c->stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    if (l == 0 || cs != cudaStreamCaptureStatusNone || g->lv[l].L32.active || g->lv[l].L64.active) {
+        vcycle<T>(g, l, nu1, nu2, nf, dlam, zero_init, cycle);
+        return;
+    }
+    const unsigned long long tv = tune_version();
+    if (g->cyc_gen != g->gen || g->cyc_tune != tv || g->cyc_nu1 != nu1 || g->cyc_nu2 != nu2 ||
+        g->cyc_smoother != g->smoother || g->cyc_omega != g->omega || g->cyc_stream != s ||
+        g->cyc_nf != (const void*)nf || g->cyc_dlam != (const void*)dlam) {
+        cycle_graphs_free(g);
+        g->cyc_gen = g->gen;
+        g->cyc_tune = tv;
+        g->cyc_nu1 = nu1;
+        g->cyc_nu2 = nu2;
+        g->cyc_smoother = g->smoother;
+        g->cyc_omega = g->omega;
+        g->cyc_stream = s;
+        g->cyc_nf = nf;
+        g->cyc_dlam = dlam;
+    }
+    const int key = (sizeof(T) == 8 ? 1 << 16 : 0) | (l << 8) | (zero_init ? 2 : 0) | (cycle == ELAS_CYCLE_F ? 1 : 0);
+    auto it = g->cyc.find(key);
+    if (it == g->cyc.end()) {
+        elas_grid_s::CycleGraph cg;
+        const unsigned long long l0 = launch_count();
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            vcycle<T>(g, l, nu1, nu2, nf, dlam, zero_init, cycle);
+            const cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (e == cudaSuccess && graph && cudaGraphInstantiate(&cg.exec, graph, 0) != cudaSuccess) cg.exec = nullptr;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();   // a refused capture leaves no error behind: launch directly
+        cg.launches = (int)(launch_count() - l0);
+        count_launch(-cg.launches);   // captured, not launched: counted per replay
+        it = g->cyc.emplace(key, cg).first;
+    }
+    if (it->second.exec && cudaGraphLaunch(it->second.exec, s) == cudaSuccess) {
+        count_launch(it->second.launches);
+        return;
+    }
+    cudaGetLastError();
+    vcycle<T>(g, l, nu1, nu2, nf, dlam, zero_init, cycle);
 }
 
 // The refinement residual of a mixed solve: double-float (from the grid's double-float
@@ -1006,6 +1096,7 @@ int elas_grid_destroy(elas_grid g) {
         plan_free(c, c->plan);
         c->plan = nullptr;
     }
+    cycle_graphs_free(g);
     for (auto& a : g->allocs) ctx_free(c, a.first, a.second);
     cudaStreamSynchronize(c->stream);
     delete g;
@@ -1210,10 +1301,10 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
             Level& L1 = g->lv[1];
             launch_restrict<double>(L0.L64, L1.L64, L0.r, L1.f, nf0, dload, s);
             if (g->cycle == ELAS_CYCLE_F) {
-                vcycle<double>(g, 1, nu1, nu2, nullptr, nullptr, true, ELAS_CYCLE_F);
-                vcycle<double>(g, 1, nu1, nu2, nullptr, nullptr, false, ELAS_CYCLE_V);
+                run_cycle<double>(g, 1, nu1, nu2, nullptr, nullptr, true, ELAS_CYCLE_F);
+                run_cycle<double>(g, 1, nu1, nu2, nullptr, nullptr, false, ELAS_CYCLE_V);
             } else {
-                vcycle<double>(g, 1, nu1, nu2, nullptr, nullptr);
+                run_cycle<double>(g, 1, nu1, nu2, nullptr, nullptr, true, ELAS_CYCLE_V);
             }
             launch_prolong_add<double>(L0.L64, L1.L64, L1.u, L0.u, s);
             smooth<double>(g, 0, nu2, nf0, load);

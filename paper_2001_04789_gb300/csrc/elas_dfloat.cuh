@@ -1,16 +1,20 @@
-// Double-float ("double-word") numbers: an unevaluated sum hi + lo of two FP32 values
-// with |lo| <= ulp(hi) / 2, about 48 significant bits.
+// Double-float ("double-word") numbers: an unevaluated sum hi + lo of two FP32 values,
+// about 48 significant bits.
 //
 // GB300's FP64 pipes run at about 1/70 of its FP32 rate (1.06 against 76.8 TFLOP/s
 // measured with independent FMA chains), so the refinement residual of a mixed solve,
 // the one operator application that needs more than FP32 accuracy, is evaluated in
-// this format on the FP32 pipes: an addition costs 11 FP32 operations, a product 7, a
-// multiply-add 15.  The building blocks are the error-free transformations of Knuth
+// this format on the FP32 pipes: an addition costs 8 FP32 operations, a product 4, a
+// multiply-add 12.  The building blocks are the error-free transformations of Knuth
 // (TwoSum) and Dekker (Fast2Sum, and the FMA form of the exact product), combined as
 // the double-word algorithms analysed by Joldes, Muller and Popescu (ACM TOMS 44,
-// 2017): the "sloppy" sum of two double-words and the product through one FMA chain.
-// Their error is bounded by a few units of 2^-47 of the operands' magnitudes (not of
-// the result's): exactly what a residual needs, whose terms cancel to a small sum.
+// 2017): the "sloppy" sum of two double-words and the product through one FMA chain,
+// here without the final renormalisation (Fast2Sum) of each result.  A pair then need
+// not satisfy |lo| <= ulp(hi) / 2, but its lo part stays within a few 2^-24 of the
+// magnitudes of the operands it came from, so every later rounding of a lo term is a
+// few 2^-47 of those magnitudes.  That is the error bound of the whole evaluation: a
+// few units of 2^-47 of the operands' magnitudes (not of the result's), exactly what a
+// residual needs, whose terms cancel to a small sum.
 //
 // Every operation spells out its roundings with the _rn intrinsics, so the compiler
 // never contracts or reorders them.
@@ -47,7 +51,7 @@ __device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
 
 __device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
     const dfloat s = df_two_sum(x.hi, y.hi);
-    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+    return dfloat(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
 
 __device__ __forceinline__ dfloat df_neg(dfloat x) { return dfloat(-x.hi, -x.lo); }
@@ -60,7 +64,7 @@ __device__ __forceinline__ dfloat df_mul(dfloat x, dfloat y) {
     float e = __fmaf_rn(x.hi, y.hi, -p);
     e = __fmaf_rn(x.hi, y.lo, e);
     e = __fmaf_rn(x.lo, y.hi, e);
-    return df_fast_two_sum(p, e);
+    return dfloat(p, e);
 }
 
 // x * y for an FP32 y
@@ -68,17 +72,17 @@ __device__ __forceinline__ dfloat df_mul(dfloat x, float y) {
     const float p = __fmul_rn(x.hi, y);
     float e = __fmaf_rn(x.hi, y, -p);
     e = __fmaf_rn(x.lo, y, e);
-    return df_fast_two_sum(p, e);
+    return dfloat(p, e);
 }
 
-// a * b + c without normalising the product first
+// a * b + c: the product's pair added to c as one sum
 __device__ __forceinline__ dfloat df_fma(dfloat a, dfloat b, dfloat c) {
     const float p = __fmul_rn(a.hi, b.hi);
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
     const dfloat s = df_two_sum(p, c.hi);
-    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+    return dfloat(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
 }
 
 // nearest FP32 value (hi + lo rounded once)

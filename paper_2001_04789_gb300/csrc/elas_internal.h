@@ -41,6 +41,7 @@ int tune_lookup(const std::array<int, 6>& key, int fallback);   // key: nx ny nz
 void tune_store(const std::array<int, 6>& key, int variant);
 int tune_table_dump(char* buf, int cap);
 int tune_table_load(const char* text);
+unsigned long long tune_version();   // changes whenever the table does (captured launches depend on it)
 
 // Launchers (all enqueue on `s`).
 void launch_rhs(const Lv<double>& L, const RhsInputs& in, const BoundaryData& bd, double* f, cudaStream_t s);

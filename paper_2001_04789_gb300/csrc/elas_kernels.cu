@@ -51,6 +51,12 @@ void launch_apply(const Lv<T>& L, const T* u, T* out, cudaStream_t s) {
 // ---- tuning table of the interior smoother (shared by all translation units) -----------
 static std::mutex g_tune_mu;
 static std::map<std::array<int, 6>, int> g_tune;
+static unsigned long long g_tune_version = 0;   // bumped by every change of the table
+
+unsigned long long tune_version() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune_version;
+}
 
 int tune_lookup(const std::array<int, 6>& key, int fallback) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -61,6 +67,7 @@ int tune_lookup(const std::array<int, 6>& key, int fallback) {
 void tune_store(const std::array<int, 6>& key, int v) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = v;
+    ++g_tune_version;
 }
 
 int tune_table_dump(char* buf, int cap) {
@@ -91,6 +98,7 @@ int tune_table_load(const char* text) {
         if (v >= 0 && v < kNumSweepVariants) {
             g_tune[k] = v;
             ++count;
+            ++g_tune_version;
         }
         p += used;
         while (*p == '\n' || *p == ' ') ++p;
