@@ -1131,9 +1131,37 @@ __global__ void __launch_bounds__(kBlock, 2) k_residual_df(Lv<dfloat> L, const d
     residual_df_block<KIND, NORM, HM, NPT>(L, u, f, nf, lam, r, partials, blockIdx.x);
 }
 
+// A double as a double-float pair from its bits alone (no FP64 or conversion instruction:
+// on this GPU those share the narrow FP64 pipe).  IEEE-754 binary64 v = (-1)^s 1.m 2^(e-1023)
+// with a 52-bit m: hi keeps the leading 24 significant bits (truncated), re-biased to the
+// binary32 exponent e - 896; lo is the rest, the next 23 bits below hi's last one, formed
+// as (1.f - 1) 2^(e-896-127-23) by one exact FP32 subtraction.  |v - (hi + lo)| < 2^-46 |v|.
+// |v| below 2^-103 keeps lo = 0 and below 2^-126 gives (0, 0): far under any value of the
+// fields split here (moduli, displacements, loads).
 __device__ __forceinline__ dfloat df_split(double v) {
-    const float h = __double2float_rn(v);
-    return dfloat(h, __double2float_rn(v - (double)h));
+    const unsigned h32 = (unsigned)__double2hiint(v), l32 = (unsigned)__double2loint(v);
+    const int e = (int)((h32 >> 20) & 0x7ffu);
+    if (e < 897) return dfloat(0.f, 0.f);
+    const unsigned hb = (__funnelshift_l(l32, h32, 3) - 0xC0000000u) | (h32 & 0x80000000u);
+    float lo = 0.f;
+    if (e >= 920) {
+        const unsigned base = (hb & 0x7f800000u) - (23u << 23);
+        const float one = __uint_as_float(base);
+        const float lf = __uint_as_float(base | ((l32 >> 6) & 0x7fffffu));
+        lo = __fsub_rn(lf, one);
+        if (h32 & 0x80000000u) lo = -lo;
+    }
+    return dfloat(__uint_as_float(hb), lo);
+}
+
+// An FP32 value as a double from its bits (exact; FP32 subnormals, far below any
+// correction, read as zero), without a conversion instruction.
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned ex = (b >> 23) & 0xffu;
+    if (ex == 0) return 0.0;
+    const unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
 }
 
 template <typename TE>
@@ -1146,7 +1174,7 @@ __device__ __forceinline__ void add_correction_df_body(const Lv<double>& L, doub
     for (int i = 0; i < 3; ++i) {
         double x = u[i * L.N + p];
         if (row_type(L, ni, i) != ROW_DIRICHLET) {
-            x += (double)e[i * L.N + p];
+            x += f2d_bits(e[i * L.N + p]);   // the FP64 update of the refinement, one DADD
             u[i * L.N + p] = x;
         }
         u2[i * L.N + p] = df_split(x);
@@ -1238,42 +1266,36 @@ __device__ __forceinline__ void prolong_body(const Lv<T>& Lf, const Lv<T>& Lc, c
     int c[3];
     coords_of(p, Lf.n, c);
     const NodeInfo ni = node_info(Lf, c[0], c[1], c[2]);
+    // per direction: the coarse nodes below and above (the same node at even fine
+    // coordinates) and their weights 1 / 0 or 1/2 / 1/2; all eight corners are read and
+    // the zero-weight terms add exact zeros, so every thread runs the same instructions
     int lo[3], hi[3];
     T wl[3], wh[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-        if ((c[d] & 1) == 0) {
-            lo[d] = hi[d] = c[d] >> 1;
-            wl[d] = T(1);
-            wh[d] = T(0);
-        } else {
-            lo[d] = c[d] >> 1;
-            hi[d] = lo[d] + 1;
-            if (Lc.per[d] && hi[d] >= Lc.n[d]) hi[d] -= Lc.n[d];
-            wl[d] = T(0.5);
-            wh[d] = T(0.5);
-        }
+        const int odd = c[d] & 1;
+        lo[d] = c[d] >> 1;
+        hi[d] = lo[d] + odd;
+        if (Lc.per[d] && hi[d] >= Lc.n[d]) hi[d] -= Lc.n[d];
+        wl[d] = odd ? T(0.5) : T(1);
+        wh[d] = odd ? T(0.5) : T(0);
     }
+    const int nx = Lc.n[0], nxy = Lc.n[0] * Lc.n[1];
+    const int cz[2] = {lo[2] * nxy, hi[2] * nxy}, cy[2] = {lo[1] * nx, hi[1] * nx}, cx[2] = {lo[0], hi[0]};
+    const T wz[2] = {wl[2], wh[2]}, wy[2] = {wl[1], wh[1]}, wx[2] = {wl[0], wh[0]};
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
         if (row_type(Lf, ni, i) == ROW_DIRICHLET) continue;
-        const T* e = ec + i * Lc.N;
+        const T* e = ec + (size_t)i * Lc.N;
         T v = T(0);
-        for (int bz = 0; bz < 2; ++bz) {
-            const T wzv = bz ? wh[2] : wl[2];
-            if (wzv == T(0)) continue;
-            const int cz = bz ? hi[2] : lo[2];
-            for (int by = 0; by < 2; ++by) {
-                const T wyv = by ? wh[1] : wl[1];
-                if (wyv == T(0)) continue;
-                const int cy = by ? hi[1] : lo[1];
-                for (int bx = 0; bx < 2; ++bx) {
-                    const T wxv = bx ? wh[0] : wl[0];
-                    if (wxv == T(0)) continue;
-                    const int cx = bx ? hi[0] : lo[0];
-                    v += wxv * wyv * wzv * e[lin(Lc, cx, cy, cz)];
-                }
-            }
-        }
-        u[i * Lf.N + p] += v;
+#pragma unroll
+        for (int bz = 0; bz < 2; ++bz)
+#pragma unroll
+            for (int by = 0; by < 2; ++by)
+#pragma unroll
+                for (int bx = 0; bx < 2; ++bx)   // weights are powers of two: exact products
+                    v = xfma(xmul(xmul(wx[bx], wy[by]), wz[bz]), e[cz[bz] + cy[by] + cx[bx]], v);
+        u[(size_t)i * Lf.N + p] = xadd(u[(size_t)i * Lf.N + p], v);
     }
 }
 
