@@ -29,10 +29,11 @@ METRIC = "Solves/s at 1e-8 rel. residual, mixed vs FP64; stencil HBM GB/s; p99 l
 UNIT = "solves/s"
 FALLBACK_HBM_GBS = 6800.0
 # DRAM read + write bytes per node of one finest-level FP32 half-sweep launch (colour-split
-# moduli), per smoother shape (autotuner index), from one ncu capture of that shape on the
-# 129^3 polycrystal (profiles/sweep32_split_polycrystal129.md); scaled by the node count to
-# the benchmarked grid.
-SWEEP32_TRAFFIC_B_PER_NODE = {3: 201.6}
+# moduli, x-face rows stored), per smoother shape (autotuner index), from one ncu capture of
+# that shape on the 129^3 polycrystal (profiles/sweep32_split_polycrystal129.md); scaled by
+# the node count to the benchmarked grid (the x faces' stored rows are 15 B/node of it at
+# 129^3 and half that at 257^3, so at 257^3 this overstates by about 7 B/node).
+SWEEP32_TRAFFIC_B_PER_NODE = {3: 147.4, 4: 148.4}
 
 
 def parse():
@@ -503,6 +504,7 @@ def main():
                                 + (", FP16 moduli in the V-cycle" if args.half else ""),
                    "inputs": "larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
         "cycles": info["cycles"], "rel_residual": info["rel_residual"], "rel_residual_fp64_check": rel64,
+        "rel_residual_inf": info.get("rel_residual_inf"),
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "fp64": {"value": fp64_value, "unit": UNIT, "cycles": fp64_info["cycles"] if fp64_info else None,
                  "seconds": statistics.median(fp64_times) if fp64_times else None},

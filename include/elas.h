@@ -196,6 +196,10 @@ typedef struct {
     double lam[6];                     /* equilibrating-load coefficients             */
     double seconds;                    /* wall time of the solve                      */
     double rel_history[ELAS_HISTORY];  /* relative residual before each correction    */
+    double residual_inf;               /* ||r||_inf of the last residual evaluated (the
+                                          refinement residual's arithmetic); -1 for
+                                          composite AMR solves                          */
+    double rel_residual_inf;           /* the same over ||r_0||_inf                     */
 } elas_solve_info;
 
 void elas_solve_opts_default(elas_solve_opts* o);
@@ -221,6 +225,9 @@ int  elas_set_displacement(elas_grid g, const double* in, int memspace);
 int  elas_get_stress(elas_grid g, double* out, int memspace);
 /* FP64 residual of the current displacement: ||r||_2 / ||r_0||_2 and ||r||_2. */
 int  elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2);
+/* The same residual's max norm: ||r||_inf / ||r_0||_inf and ||r||_inf (largest |r_i|
+ * over all rows and components, the equilibrating load of the last solve applied). */
+int  elas_query_residual_inf(elas_grid g, double* rel_inf, double* abs_inf);
 
 /* ---- single operations of the path, for testing and benchmarking --------------
  * All take DEVICE pointers to FP64 (precision 0) or FP32 (precision 1) arrays of

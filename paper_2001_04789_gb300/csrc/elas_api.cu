@@ -121,6 +121,7 @@ struct elas_grid_s {
     double *G = nullptr, *Ginv = nullptr, *lam = nullptr, *dlam = nullptr, *status = nullptr, *partials = nullptr;
     double *alam = nullptr, *adlam = nullptr;   // loads as rigid motions (t, w)
     double r0 = 0.0;
+    double r0inf = 0.0;   // ||r_0||_inf
     bool moduli_set = false;
     bool dirty = true;         // moduli or boundary types changed: rebuild everything
     bool rhs_dirty = true;     // only loads / boundary data changed: rebuild the right-hand side
@@ -473,10 +474,11 @@ int setup_rhs(elas_grid g) {
         NullInfo none{};
         launch_finalize(g->partials, nb, none, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, g->status, 0, s);
         CHECK_LAUNCH(c);
-        double st[1];
-        int rc = read_status(g, st, 1);
+        double st[2];
+        int rc = read_status(g, st, 2);
         if (rc) return rc;
         g->r0 = std::sqrt(st[0]);
+        g->r0inf = st[1];
     }
     g->rhs_dirty = false;
     return ELAS_OK;
@@ -1259,7 +1261,7 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
     info->nlam = L0.nf.m;
     const int nu1 = opts->nu1 < 0 ? 0 : opts->nu1, nu2 = opts->nu2 < 0 ? 0 : opts->nu2;
     int cycles = 0;
-    double rel = 0.0;
+    double rel = 0.0, rinf = 0.0;
     int status = ELAS_OK;
     int hist = 0;
     for (;;) {
@@ -1272,11 +1274,12 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
         CHECK_LAUNCH(c);
         launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 1, s);
         CHECK_LAUNCH(c);
-        double st[1];
-        rc = read_status(g, st, 1);
+        double st[2];
+        rc = read_status(g, st, 2);
         if (rc) return rc;
         prof_collect(c);
         rel = g->r0 > 0 ? std::sqrt(st[0]) / g->r0 : 0.0;
+        rinf = st[1];
         if (hist < ELAS_HISTORY) info->rel_history[hist++] = rel;
         if (!std::isfinite(rel) || rel > 1e12) {
             status = ELAS_ERR_DIVERGED;
@@ -1328,6 +1331,8 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
     for (int q = 0; q < 6; ++q) info->lam[q] = lam[q];
     info->cycles = cycles;
     info->rel_residual = rel;
+    info->residual_inf = rinf;
+    info->rel_residual_inf = g->r0inf > 0 ? rinf / g->r0inf : 0.0;
     info->status = status;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (status == ELAS_ERR_NOT_CONVERGED) set_err(c, status, "maximum cycles reached above the tolerance");
@@ -1395,6 +1400,28 @@ int elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2) {
     if (rc) return rc;
     if (abs_l2) *abs_l2 = std::sqrt(st[0]);
     if (rel_l2) *rel_l2 = g->r0 > 0 ? std::sqrt(st[0]) / g->r0 : 0.0;
+    return ELAS_OK;
+}
+
+int elas_query_residual_inf(elas_grid g, double* rel_inf, double* abs_inf) {
+    if (!g) return ELAS_ERR_INVALID_ARG;
+    int rc = setup(g);
+    if (rc) return rc;
+    elas_ctx c = g->ctx;
+    Level& L0 = g->lv[0];
+    const NullInfo* nf0 = L0.nf.m > 0 ? &L0.nf : nullptr;
+    int nb = 0;
+    launch_residual<double, double>(L0.L64, L0.u, L0.f, nf0, nf0 ? g->alam : nullptr, L0.r, g->partials, &nb,
+                                    c->stream);
+    CHECK_LAUNCH(c);
+    launch_finalize(g->partials, nb, L0.nf, g->Ginv, g->G, g->lam, g->dlam, g->alam, g->adlam, g->status, 0,
+                    c->stream);
+    CHECK_LAUNCH(c);
+    double st[2];
+    rc = read_status(g, st, 2);
+    if (rc) return rc;
+    if (abs_inf) *abs_inf = st[1];
+    if (rel_inf) *rel_inf = g->r0inf > 0 ? st[1] / g->r0inf : 0.0;
     return ELAS_OK;
 }
 
@@ -2080,6 +2107,9 @@ int batch_engine(elas_grid* grids, int n, const elas_solve_opts* o, elas_solve_i
     std::vector<double> h_hist((size_t)n * H);
     CUDA_TRY(c, cudaMemcpyAsync(h_counts.data(), p->counts, sizeof(int) * n, cudaMemcpyDeviceToHost, main));
     CUDA_TRY(c, cudaMemcpyAsync(h_hist.data(), p->hist, sizeof(double) * n * H, cudaMemcpyDeviceToHost, main));
+    std::vector<double> h_inf(n);
+    for (int i = 0; i < n; ++i)
+        CUDA_TRY(c, cudaMemcpyAsync(&h_inf[i], grids[i]->status + 1, sizeof(double), cudaMemcpyDeviceToHost, main));
     for (int i = 0; i < n; ++i) {
         const int rr = remove_rigid(grids[i]);
         if (rr) return rr;
@@ -2092,6 +2122,8 @@ int batch_engine(elas_grid* grids, int n, const elas_solve_opts* o, elas_solve_i
         for (int k = 0; k < cnt; ++k) info[i].rel_history[k] = h_hist[(size_t)i * H + k];
         info[i].cycles = h_counts[i] > 0 ? h_counts[i] - 1 : 0;
         info[i].rel_residual = cnt > 0 ? h_hist[(size_t)i * H + cnt - 1] : 0.0;
+        info[i].residual_inf = h_inf[i];
+        info[i].rel_residual_inf = grids[i]->r0inf > 0 ? h_inf[i] / grids[i]->r0inf : 0.0;
         info[i].r0 = grids[i]->r0;
         info[i].nlam = grids[i]->lv[0].nf.m;
         info[i].seconds = secs;
@@ -2207,6 +2239,9 @@ int batch_run(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_i
     std::vector<double> h_hist((size_t)n * hist_len);
     CUDA_TRY(c, cudaMemcpyAsync(h_counts.data(), counts, sizeof(int) * n, cudaMemcpyDeviceToHost, main));
     CUDA_TRY(c, cudaMemcpyAsync(h_hist.data(), hist, sizeof(double) * n * hist_len, cudaMemcpyDeviceToHost, main));
+    std::vector<double> h_inf(n);
+    for (int i = 0; i < n; ++i)
+        CUDA_TRY(c, cudaMemcpyAsync(&h_inf[i], grids[i]->status + 1, sizeof(double), cudaMemcpyDeviceToHost, main));
     int worst = ELAS_OK;
     for (int i = 0; i < n; ++i) {
         const int rr = remove_rigid(grids[i]);
@@ -2219,6 +2254,8 @@ int batch_run(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_i
         for (int k = 0; k < cnt; ++k) info[i].rel_history[k] = h_hist[(size_t)i * hist_len + k];
         info[i].cycles = h_counts[i] > 0 ? h_counts[i] - 1 : 0;
         info[i].rel_residual = cnt > 0 ? h_hist[(size_t)i * hist_len + cnt - 1] : 0.0;
+        info[i].residual_inf = h_inf[i];
+        info[i].rel_residual_inf = grids[i]->r0inf > 0 ? h_inf[i] / grids[i]->r0inf : 0.0;
         info[i].r0 = grids[i]->r0;
         info[i].nlam = grids[i]->lv[0].nf.m;
         info[i].seconds = secs;
@@ -2643,6 +2680,8 @@ int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* inf
     CUDA_TRY(c, cudaStreamSynchronize(s));
     info->cycles = cycles;
     info->rel_residual = rel;
+    info->residual_inf = -1.0;   // composite norms: the 2-norm only
+    info->rel_residual_inf = -1.0;
     info->status = status;
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (status == ELAS_ERR_NOT_CONVERGED) set_err(c, status, "maximum cycles reached above the tolerance");
@@ -2908,6 +2947,8 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
                 for (int k = 0; k < cnt; ++k) d.info.rel_history[k] = r.hist[k];
                 d.info.cycles = r.cycles;
                 d.info.rel_residual = rel;
+                d.info.residual_inf = -1.0;   // composite norms: the 2-norm only
+                d.info.rel_residual_inf = -1.0;
                 d.info.r0 = r.r0;
                 const bool ok = r.opts.fixed_cycles > 0 || rel <= r.opts.rel_tol;
                 d.info.status = bad ? ELAS_ERR_DIVERGED : (ok ? ELAS_OK : ELAS_ERR_NOT_CONVERGED);
@@ -2931,7 +2972,11 @@ int elas_server_step(elas_server s, int* n_active, int* n_waiting) {
             if (cnt > 0)
                 CUDA_TRY(c, cudaMemcpyAsync(h.data(), s->hist + (size_t)r.slot * ELAS_HISTORY, sizeof(double) * cnt,
                                             cudaMemcpyDeviceToHost, main));
+            double rinf = 0.0;
+            CUDA_TRY(c, cudaMemcpyAsync(&rinf, g->status + 1, sizeof(double), cudaMemcpyDeviceToHost, main));
             CUDA_TRY(c, cudaStreamSynchronize(main));
+            d.info.residual_inf = rinf;
+            d.info.rel_residual_inf = g->r0inf > 0 ? rinf / g->r0inf : 0.0;
             for (int k = 0; k < cnt; ++k) d.info.rel_history[k] = h[k];
             d.info.cycles = s->h_counts[r.slot] > 0 ? s->h_counts[r.slot] - 1 : 0;
             d.info.rel_residual = cnt > 0 ? h[cnt - 1] : 0.0;

@@ -52,14 +52,14 @@ __global__ void __launch_bounds__(kBatchBlock, sizeof(T) == 4 ? 3 : 2)
     const int b = load_task(tasks, bmap, t), tid = threadIdx.x;
     const Lv<T>& L = t.L;
     if (inactive(L.active)) return;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const BndSegs sg = bnd_segs(L, kBlock);
     if (b < sg.e) residual_bnd_body<T, TR, KIND, NORM>(L, t.u, t.f, t.nf, t.lam, t.r, (b * kBlock + tid) >> 5, tid & 31, acc);
     else if (b < sg.f0) residual_face_body<T, TR, KIND, 0, NORM>(L, t.u, t.f, t.nf, t.lam, t.r, (b - sg.e) * kBlock + tid, acc);
     else if (b < sg.f1) residual_face_body<T, TR, KIND, 1, NORM>(L, t.u, t.f, t.nf, t.lam, t.r, (b - sg.f0) * kBlock + tid, acc);
     else if (b < sg.f2) residual_face_body<T, TR, KIND, 2, NORM>(L, t.u, t.f, t.nf, t.lam, t.r, (b - sg.f1) * kBlock + tid, acc);
     else residual_int_body<T, TR, KIND, NORM, HM, ML>(L, t.u, t.f, t.nf, t.lam, t.r, (b - sg.f2) * kBlock + tid, acc);
-    if (NORM) block_reduce_store_at<7>(acc, t.nf.m > 0 ? 7 : 1, t.partials, b);
+    if (NORM) block_reduce_norms_at(acc, t.nf.m > 0 ? 7 : 1, t.partials, b);
 }
 
 __global__ void k_batch_restrict(const RestrictTask<float>* __restrict__ tasks, const int2* __restrict__ bmap) {

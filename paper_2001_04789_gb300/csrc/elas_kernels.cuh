@@ -58,42 +58,73 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[MAXW], int width,
     block_reduce_store_at<MAXW>(v, width, partials, blockIdx.x);
 }
 
+// Residual norms of a block: the sums v[0 .. width) (sum r^2, the rigid moments) and the
+// maximum v[7] of |r| into partials[bid * kPartialStride + 0 .. width) and [+ 7].
+__device__ __forceinline__ void block_reduce_norms_at(double (&v)[8], int width, double* partials, int bid) {
+    double sums[7];
+#pragma unroll
+    for (int w = 0; w < 7; ++w) sums[w] = v[w];
+    block_reduce_store_at<7>(sums, width, partials, bid);
+    __shared__ double smax[kBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double x = v[7];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    if (lane == 0) smax[warp] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        x = lane < kBlock / 32 ? smax[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+        if (lane == 0) partials[(size_t)bid * kPartialStride + 7] = x;
+    }
+}
+
 // Fixed-order sum of the 7-wide block partials by one block of kSumThreads threads:
 // each thread keeps four records in flight per step (the loads are independent, so the
 // sum is limited by bandwidth rather than by one load's latency), then a warp-shuffle
-// tree and a second one over the warps.  The result lands in sm[0][0..6].
+// tree and a second one over the warps.  The result lands in sm[0][0..6]; sm[0][7] is the
+// maximum of the records' slot 7 (max |r| where a residual wrote them).
 constexpr int kSumThreads = 512;
 __device__ __forceinline__ void sum_partials_block(const double* __restrict__ partials, int nblocks,
-                                                   double (&sm)[kSumThreads / 32][7]) {
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+                                                   double (&sm)[kSumThreads / 32][8]) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int b0 = threadIdx.x; b0 < nblocks; b0 += 4 * kSumThreads) {
-        double v[4][7];
+        double v[4][8];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int b = b0 + k * kSumThreads;
 #pragma unroll
-            for (int w = 0; w < 7; ++w) v[k][w] = b < nblocks ? partials[(size_t)b * kPartialStride + w] : 0.0;
+            for (int w = 0; w < 8; ++w) v[k][w] = b < nblocks ? partials[(size_t)b * kPartialStride + w] : 0.0;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 4; ++k) {
 #pragma unroll
             for (int w = 0; w < 7; ++w) acc[w] += v[k][w];
+            acc[7] = fmax(acc[7], v[k][7]);
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int w = 0; w < 7; ++w) {
+    for (int w = 0; w < 8; ++w) {
         double x = acc[w];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, o);
+            x = w == 7 ? fmax(x, y) : x + y;
+        }
         if (lane == 0) sm[warp][w] = x;
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
-        for (int w = 0; w < 7; ++w) {
+        for (int w = 0; w < 8; ++w) {
             double x = lane < kSumThreads / 32 ? sm[lane][w] : 0.0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                const double y = __shfl_down_sync(0xffffffffu, x, o);
+                x = w == 7 ? fmax(x, y) : x + y;
+            }
             if (lane == 0) sm[0][w] = x;
         }
     }
@@ -261,7 +292,7 @@ template <typename T, typename TR, bool NORM>
 __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restrict__ f, const NullInfo& nf,
                                                const double* __restrict__ load, const int c[3], int p,
                                                const int types[3], const T v[3], TR* __restrict__ r,
-                                               double acc[7]) {
+                                               double acc[8]) {
     T rr[3];
     for (int i = 0; i < 3; ++i) {
         T ri = T(0);
@@ -276,6 +307,7 @@ __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restri
     if (NORM) {
         const double r0 = (double)rr[0], r1 = (double)rr[1], r2 = (double)rr[2];
         acc[0] += r0 * r0 + r1 * r1 + r2 * r2;
+        acc[7] = fmax(acc[7], fmax(fabs(r0), fmax(fabs(r1), fabs(r2))));
         if (nf.m > 0) {
             // FP64: the moments of r cancel strongly (they measure the small incompatible
             // part), so they are summed in full precision
@@ -297,7 +329,7 @@ __device__ __forceinline__ void residual_store(const Lv<T>& L, const T* __restri
 template <typename T, typename TR, int KIND, bool NORM, bool HM, int ML>
 __device__ __forceinline__ void residual_int_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
                                                   const NullInfo& nf, const double* __restrict__ lam,
-                                                  TR* __restrict__ r, int t, double acc[7]) {
+                                                  TR* __restrict__ r, int t, double acc[8]) {
     int lo[3], cnt[3];
     interior_box(L, lo, cnt);
     if (t >= cnt[0] * cnt[1] * cnt[2]) return;
@@ -341,7 +373,7 @@ __device__ __forceinline__ void edge_rows_coef(const Lv<T>& L, const T* __restri
 template <typename T, typename TR, int KIND, bool NORM>
 __device__ __forceinline__ void residual_bnd_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
                                                   const NullInfo& nf, const double* __restrict__ lam,
-                                                  TR* __restrict__ r, int w, int lane, double acc[7]) {
+                                                  TR* __restrict__ r, int w, int lane, double acc[8]) {
     if (w >= L.nbnd) return;   // whole warp
     const int p = L.bnodes[w];
     int c[3];
@@ -682,7 +714,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_face(Lv<T> L, const T* __restr
 template <typename T, typename TR, int KIND, int A, bool NORM>
 __device__ __forceinline__ void residual_face_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
                                                    const NullInfo& nf, const double* __restrict__ load,
-                                                   TR* __restrict__ r, int t, double acc[7]) {
+                                                   TR* __restrict__ r, int t, double acc[8]) {
     int c[3], side;
     if (!face_coords<T, A>(L, t, c, side)) return;
     int types[3];
@@ -967,7 +999,7 @@ __global__ void __launch_bounds__(16 * TY, MINB)
 // the layout of k_residual.  Interior threads take NPT nodes each, which spreads the
 // block reduction over NPT times more nodes.
 struct DfAcc {
-    float r2;
+    float r2, rmax;
     dfloat m[6];
 };
 
@@ -992,6 +1024,7 @@ __device__ __forceinline__ void residual_store_df(const Lv<dfloat>& L, const dfl
     }
     if (NORM) {
         acc.r2 = __fmaf_rn(rf[2], rf[2], __fmaf_rn(rf[1], rf[1], __fmaf_rn(rf[0], rf[0], acc.r2)));
+        acc.rmax = fmaxf(acc.rmax, fmaxf(fabsf(rf[0]), fmaxf(fabsf(rf[1]), fabsf(rf[2]))));
         if (nf.m > 0) {
             const float d0 = xfma(nf.h32[0], float(c[0]), nf.off32[0]);
             const float d1 = xfma(nf.h32[1], float(c[1]), nf.off32[1]);
@@ -1006,15 +1039,22 @@ __device__ __forceinline__ void residual_store_df(const Lv<dfloat>& L, const dfl
     }
 }
 
-// Block sum of the accumulators into partials[bid * kPartialStride + 0 .. width)
+// Block sum of the accumulators into partials[bid * kPartialStride + 0 .. width), and the
+// block's max |r| into [+ 7]
 __device__ __forceinline__ void block_reduce_store_df(const DfAcc& a, int width, double* partials, int bid) {
-    __shared__ float sr[kBlock / 32];
+    __shared__ float sr[kBlock / 32], sx[kBlock / 32];
     __shared__ dfloat sm[kBlock / 32][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float x = a.r2;
+    float x = a.r2, mx = a.rmax;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = __fadd_rn(x, shfl_xor_all(x, o));
-    if (lane == 0) sr[warp] = x;
+    for (int o = 16; o > 0; o >>= 1) {
+        x = __fadd_rn(x, shfl_xor_all(x, o));
+        mx = fmaxf(mx, shfl_xor_all(mx, o));
+    }
+    if (lane == 0) {
+        sr[warp] = x;
+        sx[warp] = mx;
+    }
     if (width > 1) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -1027,9 +1067,16 @@ __device__ __forceinline__ void block_reduce_store_df(const DfAcc& a, int width,
     __syncthreads();
     if (threadIdx.x < 32) {
         x = lane < kBlock / 32 ? sr[lane] : 0.f;
+        mx = lane < kBlock / 32 ? sx[lane] : 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = __fadd_rn(x, shfl_xor_all(x, o));
-        if (lane == 0) partials[(size_t)bid * kPartialStride] = (double)x;
+        for (int o = 16; o > 0; o >>= 1) {
+            x = __fadd_rn(x, shfl_xor_all(x, o));
+            mx = fmaxf(mx, shfl_xor_all(mx, o));
+        }
+        if (lane == 0) {
+            partials[(size_t)bid * kPartialStride] = (double)x;
+            partials[(size_t)bid * kPartialStride + 7] = (double)mx;
+        }
         if (width > 1) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
@@ -1110,6 +1157,7 @@ __device__ __forceinline__ void residual_df_block(const Lv<dfloat>& L, const dfl
                                                   double* __restrict__ partials, int b) {
     DfAcc acc;
     acc.r2 = 0.f;
+    acc.rmax = 0.f;
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc.m[k] = dfloat(0.f, 0.f);
     const BndSegs sg = bnd_segs(L, kBlock);
@@ -1191,14 +1239,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) k_residual(Lv<
                                                     NullInfo nf, const double* __restrict__ lam,
                                                     TR* __restrict__ r, double* __restrict__ partials, BndSegs sg) {
     if (L.active && *L.active == 0) return;
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int b = blockIdx.x, tid = threadIdx.x;
     if (b < sg.e) residual_bnd_body<T, TR, KIND, NORM>(L, u, f, nf, lam, r, (b * kBlock + tid) >> 5, tid & 31, acc);
     else if (b < sg.f0) residual_face_body<T, TR, KIND, 0, NORM>(L, u, f, nf, lam, r, (b - sg.e) * kBlock + tid, acc);
     else if (b < sg.f1) residual_face_body<T, TR, KIND, 1, NORM>(L, u, f, nf, lam, r, (b - sg.f0) * kBlock + tid, acc);
     else if (b < sg.f2) residual_face_body<T, TR, KIND, 2, NORM>(L, u, f, nf, lam, r, (b - sg.f1) * kBlock + tid, acc);
     else residual_int_body<T, TR, KIND, NORM, HM, ML>(L, u, f, nf, lam, r, (b - sg.f2) * kBlock + tid, acc);
-    if (NORM) block_reduce_store<7>(acc, nf.m > 0 ? 7 : 1, partials);
+    if (NORM) block_reduce_norms_at(acc, nf.m > 0 ? 7 : 1, partials, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1565,7 +1613,7 @@ __device__ __forceinline__ void finalize_body(const double* __restrict__ partial
                                               double* __restrict__ lam, double* __restrict__ dlam,
                                               double* __restrict__ alam, double* __restrict__ adlam,
                                               double* __restrict__ out, int update_lam, const BatchFlags& bf) {
-    __shared__ double sm[kSumThreads / 32][7];
+    __shared__ double sm[kSumThreads / 32][8];
     sum_partials_block(partials, nblocks, sm);
     if (threadIdx.x == 0) {
         double ss = sm[0][0];
@@ -1605,6 +1653,7 @@ __device__ __forceinline__ void finalize_body(const double* __restrict__ partial
             }
         }
         out[0] = ss;
+        out[1] = sm[0][7];   // max |r| of the residual as evaluated
         if (bf.active) {
             // batched solve: record the relative residual, stop this member when done
             const double rel = bf.r0 > 0.0 ? sqrt(ss) / bf.r0 : 0.0;
@@ -1675,7 +1724,7 @@ __global__ void k_null_gram_row(Lv<double> L, NullInfo nf, int q0, double* __res
 
 #ifdef ELAS_KERNELS_TU
 __global__ void k_sum_partials(const double* __restrict__ partials, int nblocks, int width, double* __restrict__ out) {
-    __shared__ double sm[kSumThreads / 32][7];
+    __shared__ double sm[kSumThreads / 32][8];
     sum_partials_block(partials, nblocks, sm);
     if (threadIdx.x < width) out[threadIdx.x] = sm[0][threadIdx.x];
 }

@@ -59,13 +59,15 @@ class SolveOpts(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("rel_residual", C.c_double),
                 ("r0", C.c_double), ("nlam", C.c_int), ("lam", C.c_double * 6),
-                ("seconds", C.c_double), ("rel_history", C.c_double * HISTORY)]
+                ("seconds", C.c_double), ("rel_history", C.c_double * HISTORY),
+                ("residual_inf", C.c_double), ("rel_residual_inf", C.c_double)]
 
     def as_dict(self):
         n = min(self.cycles + 1, HISTORY)
         return {"status": self.status, "cycles": self.cycles, "rel_residual": self.rel_residual,
                 "r0": self.r0, "nlam": self.nlam, "lam": list(self.lam[: self.nlam]),
-                "seconds": self.seconds, "rel_history": list(self.rel_history[:n])}
+                "seconds": self.seconds, "rel_history": list(self.rel_history[:n]),
+                "residual_inf": self.residual_inf, "rel_residual_inf": self.rel_residual_inf}
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -111,6 +113,7 @@ def lib():
         "elas_set_displacement": (ip, [vp, vp, ip]),
         "elas_get_stress": (ip, [vp, vp, ip]),
         "elas_query_residual": (ip, [vp, dp, dp]),
+        "elas_query_residual_inf": (ip, [vp, dp, dp]),
         "elas_op_apply": (ip, [vp, ip, ip, vp, vp]),
         "elas_op_residual": (ip, [vp, ip, ip, vp, vp, vp, dp]),
         "elas_op_residual_noalloc": (ip, [vp, ip, ip, vp, vp, vp, dp]),
@@ -351,6 +354,12 @@ class Grid:
     def query_residual(self):
         rel, ab = C.c_double(), C.c_double()
         self.ctx.check(lib().elas_query_residual(self.h, C.byref(rel), C.byref(ab)))
+        return rel.value, ab.value
+
+    def query_residual_inf(self):
+        """Max norm of the FP64 residual: (||r||_inf / ||r_0||_inf, ||r||_inf)."""
+        rel, ab = C.c_double(), C.c_double()
+        self.ctx.check(lib().elas_query_residual_inf(self.h, C.byref(rel), C.byref(ab)))
         return rel.value, ab.value
 
     def levels(self):

@@ -200,6 +200,29 @@ def test_fp64_and_mixed_solves_reach_oracle_solution(E, ctx, case):
     g.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_residual_max_norm_matches_oracle(E, ctx, precision):
+    """||r||_inf of the residual kernels (solve info and query) against the oracle's
+    residual of the returned displacement (all rigid modes held by Dirichlet rows)."""
+    p = CASES["mixed_gen"]()
+    lev = S.level_from_problem(p)
+    f = S.rhs(lev, p)
+    g = E.grid_from_problem(ctx, p, mixed=True)
+    prec = E.FP64 if precision == "fp64" else E.MIXED
+    info = g.solve(precision=prec, rel_tol=1e-7)
+    assert info["status"] == 0 and info["nlam"] == 0
+    ref = np.abs(S.residual(lev, g.displacement(), f)).max()
+    ref0 = np.abs(S.residual(lev, S.dirichlet_values(lev), f)).max()
+    rel_q, abs_q = g.query_residual_inf()
+    assert abs(abs_q - ref) <= 1e-6 * ref + 1e-13 * np.abs(f).max()
+    assert abs(rel_q - ref / ref0) <= 1e-6 * rel_q + 1e-13
+    # the solve's own last evaluation: FP64 (bitwise the query's) or double-float (FP32 output)
+    tol = 0.0 if precision == "fp64" else 1e-6 * abs_q
+    assert abs(info["residual_inf"] - abs_q) <= tol
+    assert info["rel_residual_inf"] > 0
+    g.close()
+
+
 def test_warm_start_from_solution_converges_immediately(E, ctx):
     p = M.eshelby_sphere(17)
     g = E.grid_from_problem(ctx, p, mixed=True)
