@@ -262,14 +262,23 @@ Lv<dfloat> df_view(const Level& v) {
     return L;
 }
 
-// Whether a level keeps its x-face rows as stored coefficients (a warp per node) rather
-// than evaluating them in the face kernels.  Measured per FP32 half-sweep: 257^3 0.53 ->
-// 0.48 ms with the list, 129^3 93.6 -> 91.1 us (best shapes), 65^3 31.1 -> 37.5 us
-// (the 243 coefficients of a face node add a quarter to the level's bytes there), and
-// no difference below: the list is kept on levels of at least 2^20 nodes.
+// Face directions (bit A) whose face nodes take their rows from stored coefficients (a
+// warp per node) rather than from the face kernels.  Large levels list the x faces, whose
+// stencil neighbours lie nx apart (rows evaluated from the fields read one sector per
+// value); measured per FP32 half-sweep: 257^3 0.53 -> 0.48 ms, 129^3 93.6 -> 91.1 us (best
+// shapes), 65^3 31.1 -> 37.5 us (the 243 coefficients of a face node add a quarter to the
+// level's bytes there).  Small levels list every face: their kernels are latency-bound,
+// and a launch without face blocks runs the stored-row and interior code only.
 constexpr size_t kXFaceListMinNodes = size_t(1) << 20;
-bool xface_listed(const int n[3], const int per[3]) {
-    return !per[0] && (size_t)n[0] * n[1] * n[2] >= kXFaceListMinNodes;
+constexpr size_t kAllFacesListMaxNodes = 40000;   // 33^3 and coarser
+int face_list_mask(const int n[3], const int per[3]) {
+    const size_t N = (size_t)n[0] * n[1] * n[2];
+    int m = 0;
+    if (N >= kXFaceListMinNodes) m = 1;
+    else if (N <= kAllFacesListMaxNodes) m = 7;
+    for (int d = 0; d < 3; ++d)
+        if (per[d]) m &= ~(1 << d);
+    return m;
 }
 
 bool coarsenable(const int n[3], const int per[3]) {
@@ -841,20 +850,22 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
     v.L32.msplit1 = v.split ? split_half_entries((v.N + 1) / 2) : 0;
     // list of the nodes whose rows are stored as coefficients: the nodes on two or three
-    // boundary planes, and on large levels the nodes of the x faces (their stencil
-    // neighbours lie nx apart, so rows evaluated from the fields read one sector per
-    // value); the other face nodes are enumerated arithmetically by the face kernels
+    // boundary planes, and the face nodes of the directions in face_list_mask; the other
+    // face nodes are enumerated arithmetically by the face kernels
     std::vector<int> b;
     const int* per = g->desc.periodic;
-    const bool xlist = xface_listed(v.n, per);
+    const int fmask = face_list_mask(v.n, per);
     for (int z = 0; z < v.n[2]; ++z)
         for (int y = 0; y < v.n[1]; ++y)
             for (int x = 0; x < v.n[0]; ++x) {
-                const bool xf = !per[0] && (x == 0 || x == v.n[0] - 1);
-                const int on = xf + (!per[1] && (y == 0 || y == v.n[1] - 1)) + (!per[2] && (z == 0 || z == v.n[2] - 1));
-                if (on >= 2 || (xf && xlist)) b.push_back(x + v.n[0] * (y + v.n[1] * z));
+                const int fx = !per[0] && (x == 0 || x == v.n[0] - 1);
+                const int fy = !per[1] && (y == 0 || y == v.n[1] - 1);
+                const int fz = !per[2] && (z == 0 || z == v.n[2] - 1);
+                const int on = fx + fy + fz;
+                const int dirs = fx | (fy << 1) | (fz << 2);
+                if (on >= 2 || (on == 1 && (dirs & fmask))) b.push_back(x + v.n[0] * (y + v.n[1] * z));
             }
-    v.L64.xface_list = v.L32.xface_list = xlist ? 1 : 0;
+    v.L64.xface_list = v.L32.xface_list = fmask;
     v.nbnd = (int)b.size();
     if (v.nbnd) {
         if ((rc = galloc(g, &v.bnd, b.size()))) return rc;
@@ -885,7 +896,7 @@ void refresh_lv(elas_grid g) {
         v.L64.bcoef = v.bcoef64;
         v.L32.bcoef = v.bcoef32;
         v.L64.nbnd = v.L32.nbnd = v.nbnd;
-        v.L64.xface_list = v.L32.xface_list = xface_listed(v.n, g->desc.periodic) ? 1 : 0;
+        v.L64.xface_list = v.L32.xface_list = face_list_mask(v.n, g->desc.periodic);
         v.L64.divc = v.divc;
         v.L32.modh = v.mod16;
         v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
@@ -1014,7 +1025,9 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
                      N * 48;
         }
         // stored rows: edges and corners, and the x faces
-        const size_t stored = (size_t)4 * (n[0] + n[1] + n[2]) + (xface_listed(n.data(), d->periodic) ? (size_t)2 * n[1] * n[2] : 0);
+        const int fm = face_list_mask(n.data(), d->periodic);
+        const size_t stored = (size_t)4 * (n[0] + n[1] + n[2]) + ((fm & 1) ? (size_t)2 * n[1] * n[2] : 0) +
+                              ((fm & 2) ? (size_t)2 * n[0] * n[2] : 0) + ((fm & 4) ? (size_t)2 * n[0] * n[1] : 0);
         total += stored * kEdgeCoef * (d->mixed ? 12 : 8);
         if (d->mixed && d->max_levels != 1 && &n == &dims.front())   // double-float copies of the finest level
             total += 8 * (N * ((K == 21 ? 39 : 2) + 6) + stored * kEdgeCoef);

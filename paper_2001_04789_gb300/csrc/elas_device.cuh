@@ -55,7 +55,8 @@ struct Lv {
     size_t msplit1;
     // damping of the Jacobi smoother (colour kJacobiColour); the other smoothers ignore it
     T omega;
-    // 1: the x-face nodes are in bnodes (rows from stored coefficients), not face kernels
+    // bit A set: the face nodes of direction A are in bnodes (rows from stored
+    // coefficients), not in the face kernels
     int xface_list;
 };
 

@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(kBlock) k_half_sweep_face(Lv<T> L, const T* __
 template <typename T, int A>
 __host__ __device__ inline size_t face_count(const Lv<T>& L) {
     if (L.per[A]) return 0;
-    if (A == 0 && L.xface_list) return 0;   // x faces go with the stored-coefficient rows
+    if ((L.xface_list >> A) & 1) return 0;   // these faces go with the stored-coefficient rows
     int nf, ns;
     face_extent<T, A>(L, nf, ns);
     return (size_t)2 * nf * ns;

@@ -41,15 +41,17 @@ def test_hbm_estimate_orders_precisions_and_sizes(E):
     assert fp64 < half < mixed
     # FP64 general moduli: 21 planes + 18 divergence planes + 12 field planes per node,
     # summed over a hierarchy of about 8/7 of the finest level, plus 9 input planes
-    # (eigenstrain, body force) and the edge-row coefficients
+    # (eigenstrain, body force) and the stored rows (243 coefficients a node): on levels
+    # of at most 40000 nodes every boundary node's, on levels of 2^20 nodes and more the
+    # edges', corners' and x faces'
     n0 = 33 ** 3
-    base = 8 * (51 + 9) * n0
+    base = 8 * (51 + 9) * n0 + 8 * 243 * 6 * 33 * 33
     assert base <= fp64 <= 1.5 * base
-    big = M.polycrystal(65, grains=3, seed=0)
-    ratio = est(big, mixed=True) / mixed
-    assert 7.0 < ratio < 9.0            # node count grows 7.6x from 33^3 to 65^3
-    # levels of 2^20 nodes and more also store their x-face rows (243 coefficients a node)
     n1 = 129 ** 3
     large = M.Problem(n=(129, 129, 129), name="descriptor only")
     large.moduli_kind = M.MODULI_GEN21
     assert est(large) >= 8 * 60 * n1 + 8 * 243 * 2 * 129 * 129
+    larger = M.Problem(n=(257, 257, 257), name="descriptor only")
+    larger.moduli_kind = M.MODULI_GEN21
+    ratio = est(larger, mixed=True) / est(large, mixed=True)
+    assert 7.0 < ratio < 9.0            # node count grows 7.9x from 129^3 to 257^3
