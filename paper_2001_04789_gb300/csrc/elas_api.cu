@@ -263,19 +263,22 @@ Lv<dfloat> df_view(const Level& v) {
 }
 
 // Face directions (bit A) whose face nodes take their rows from stored coefficients (a
-// warp per node) rather than from the face kernels.  Large levels list the x faces, whose
+// warp per node) rather than from the face kernels.  The face kernels' rows are long
+// latency chains (tens of dependent moduli and displacement loads) and their code
+// dominates the launches of the smaller levels, so every face is listed on levels of up to
+// 300000 nodes (65^3 and coarser); measured V-cycles of a 65^3 hierarchy: 0.87 (faces in
+// face kernels) -> 0.44 ms.  Levels of 2^20 nodes and more list only the x faces, whose
 // stencil neighbours lie nx apart (rows evaluated from the fields read one sector per
-// value); measured per FP32 half-sweep: 257^3 0.53 -> 0.48 ms, 129^3 93.6 -> 91.1 us (best
-// shapes), 65^3 31.1 -> 37.5 us (the 243 coefficients of a face node add a quarter to the
-// level's bytes there).  Small levels list every face: their kernels are latency-bound,
-// and a launch without face blocks runs the stored-row and interior code only.
+// value; 257^3 half-sweep 0.53 -> 0.48 ms): there the 243 coefficients of every face node
+// add to a bandwidth-bound launch (all faces at 129^3: V-cycle of a 129^3 hierarchy
+// 1.37 -> 1.60 ms).
+constexpr size_t kAllFacesListMaxNodes = 300000;
 constexpr size_t kXFaceListMinNodes = size_t(1) << 20;
-constexpr size_t kAllFacesListMaxNodes = 40000;   // 33^3 and coarser
 int face_list_mask(const int n[3], const int per[3]) {
     const size_t N = (size_t)n[0] * n[1] * n[2];
     int m = 0;
-    if (N >= kXFaceListMinNodes) m = 1;
-    else if (N <= kAllFacesListMaxNodes) m = 7;
+    if (N <= kAllFacesListMaxNodes) m = 7;
+    else if (N >= kXFaceListMinNodes) m = 1;
     for (int d = 0; d < 3; ++d)
         if (per[d]) m &= ~(1 << d);
     return m;

@@ -42,7 +42,7 @@ def test_hbm_estimate_orders_precisions_and_sizes(E):
     # FP64 general moduli: 21 planes + 18 divergence planes + 12 field planes per node,
     # summed over a hierarchy of about 8/7 of the finest level, plus 9 input planes
     # (eigenstrain, body force) and the stored rows (243 coefficients a node): on levels
-    # of at most 40000 nodes every boundary node's, on levels of 2^20 nodes and more the
+    # of at most 300000 nodes every boundary node's, on levels of 2^20 nodes and more the
     # edges', corners' and x faces'
     n0 = 33 ** 3
     base = 8 * (51 + 9) * n0 + 8 * 243 * 6 * 33 * 33
