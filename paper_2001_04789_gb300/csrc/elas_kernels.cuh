@@ -330,6 +330,14 @@ template <typename T, typename TR, int KIND, bool NORM, bool HM, int ML>
 __device__ __forceinline__ void residual_int_body(const Lv<T>& L, const T* __restrict__ u, const T* __restrict__ f,
                                                   const NullInfo& nf, const double* __restrict__ lam,
                                                   TR* __restrict__ r, int t, double acc[8]) {
+    if constexpr (ML == kMlSplit) {
+        // warps in pairs over 64 consecutive interior nodes, the first taking the even
+        // offsets and the second the odd ones: within a row a warp's nodes then share a
+        // colour, so each of its record loads is 32 consecutive entries of one colour half
+        // (one 128-byte line) instead of 16 from each half
+        const int w = t >> 5, lane = t & 31;
+        t = ((w >> 1) << 6) + (lane << 1) + (w & 1);
+    }
     int lo[3], cnt[3];
     interior_box(L, lo, cnt);
     if (t >= cnt[0] * cnt[1] * cnt[2]) return;
