@@ -375,7 +375,7 @@ int  elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* in
  * moduli layout (and the red-black smoother is chosen), each phase of the cycle -- a
  * half-sweep of one level, a residual, a restriction, a prolongation, the bottom solve,
  * the load update, the FP64 correction -- is ONE launch over a device work list of the
- * members taking part (a block finds its member by binary search over block offsets),
+ * members taking part (a block reads its member and its block within it from a block map),
  * so launches per refinement step depend on the number of levels, not of members.  Two
  * refinement steps are captured as a CUDA graph once per batch composition and options
  * (cached on the context until a member is destroyed, set up anew, or gets new loads)

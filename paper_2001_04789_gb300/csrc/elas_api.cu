@@ -90,6 +90,10 @@ struct Level {
     int* bnd = nullptr;   // boundary-plane nodes of this level
     int nbnd = 0;
     double* bcoef64 = nullptr;   // edge and corner row coefficients (kEdgeCoef per node)
+    // the FP32 copy's list and coefficients (general moduli on small levels list every
+    // face node there, see face_list_mask)
+    int* bnd32 = nullptr;
+    int nbnd32 = 0;
     float* bcoef32 = nullptr;
     NullInfo nf{};
     // double-float copies read by the refinement residual of a mixed solve (finest level of
@@ -263,21 +267,21 @@ Lv<dfloat> df_view(const Level& v) {
 }
 
 // Face directions (bit A) whose face nodes take their rows from stored coefficients (a
-// warp per node) rather than from the face kernels.  The face kernels' rows are long
-// latency chains (tens of dependent moduli and displacement loads) and their code
-// dominates the launches of the smaller levels, so every face is listed on levels of up to
-// 300000 nodes (65^3 and coarser); measured V-cycles of a 65^3 hierarchy: 0.87 (faces in
-// face kernels) -> 0.44 ms.  Levels of 2^20 nodes and more list only the x faces, whose
-// stencil neighbours lie nx apart (rows evaluated from the fields read one sector per
-// value; 257^3 half-sweep 0.53 -> 0.48 ms): there the 243 coefficients of every face node
-// add to a bandwidth-bound launch (all faces at 129^3: V-cycle of a 129^3 hierarchy
-// 1.37 -> 1.60 ms).
+// warp per node) rather than from the face kernels.  Levels of 2^20 nodes and more list
+// the x faces, whose stencil neighbours lie nx apart (rows evaluated from the fields read
+// one sector per value; 257^3 half-sweep 0.53 -> 0.48 ms).  The FP32 copies of levels of
+// general moduli with up to 300000 nodes (65^3 and coarser) list every face: there the
+// face kernels' rows (tens of dependent moduli and displacement loads, long code) dominate
+// the launches; measured V-cycles of a 65^3 hierarchy 0.87 -> 0.44 ms.  Not so on FP64
+// levels (a stored row is 243 FMAs on the narrow FP64 pipe: 33^3 FP64 solves 133 -> 91
+// per second), with isotropic moduli (two moduli per node make the face rows cheap), nor
+// on 129^3 (the coefficients add to a bandwidth-bound launch: 1.37 -> 1.60 ms).
 constexpr size_t kAllFacesListMaxNodes = 300000;
 constexpr size_t kXFaceListMinNodes = size_t(1) << 20;
-int face_list_mask(const int n[3], const int per[3]) {
+int face_list_mask(const int n[3], const int per[3], bool fp32_general) {
     const size_t N = (size_t)n[0] * n[1] * n[2];
     int m = 0;
-    if (N <= kAllFacesListMaxNodes) m = 7;
+    if (fp32_general && N <= kAllFacesListMaxNodes) m = 7;
     else if (N >= kXFaceListMinNodes) m = 1;
     for (int d = 0; d < 3; ++d)
         if (per[d]) m &= ~(1 << d);
@@ -528,9 +532,8 @@ int setup(elas_grid g) {
     // coefficients of the edge and corner rows (they depend on moduli and boundary types)
     for (int l = 0; l < nl; ++l) {
         Level& v = g->lv[l];
-        if (!v.nbnd) continue;
-        launch_edge_coef<double>(v.L64, v.bcoef64, s);
-        if (v.bcoef32) launch_edge_coef<float>(v.L32, v.bcoef32, s);
+        if (v.nbnd) launch_edge_coef<double>(v.L64, v.bcoef64, s);
+        if (v.nbnd32 && v.bcoef32) launch_edge_coef<float>(v.L32, v.bcoef32, s);
         CHECK_LAUNCH(c);
     }
     // equilibrating load of the finest level: G = W^T W, Ginv
@@ -852,32 +855,51 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     v.L32.mod = v.mod32;
     v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
     v.L32.msplit1 = v.split ? split_half_entries((v.N + 1) / 2) : 0;
-    // list of the nodes whose rows are stored as coefficients: the nodes on two or three
-    // boundary planes, and the face nodes of the directions in face_list_mask; the other
-    // face nodes are enumerated arithmetically by the face kernels
-    std::vector<int> b;
+    // lists of the nodes whose rows are stored as coefficients (the FP64 level's and the
+    // FP32 copy's): the nodes on two or three boundary planes, and the face nodes of the
+    // directions in face_list_mask; the other face nodes are enumerated arithmetically by
+    // the face kernels
     const int* per = g->desc.periodic;
-    const int fmask = face_list_mask(v.n, per);
-    for (int z = 0; z < v.n[2]; ++z)
-        for (int y = 0; y < v.n[1]; ++y)
-            for (int x = 0; x < v.n[0]; ++x) {
-                const int fx = !per[0] && (x == 0 || x == v.n[0] - 1);
-                const int fy = !per[1] && (y == 0 || y == v.n[1] - 1);
-                const int fz = !per[2] && (z == 0 || z == v.n[2] - 1);
-                const int on = fx + fy + fz;
-                const int dirs = fx | (fy << 1) | (fz << 2);
-                if (on >= 2 || (on == 1 && (dirs & fmask))) b.push_back(x + v.n[0] * (y + v.n[1] * z));
-            }
-    v.L64.xface_list = v.L32.xface_list = fmask;
-    v.nbnd = (int)b.size();
+    const int m64 = face_list_mask(v.n, per, false), m32 = face_list_mask(v.n, per, g->K == 21);
+    auto make_list = [&](int fmask) {
+        std::vector<int> b;
+        for (int z = 0; z < v.n[2]; ++z)
+            for (int y = 0; y < v.n[1]; ++y)
+                for (int x = 0; x < v.n[0]; ++x) {
+                    const int fx = !per[0] && (x == 0 || x == v.n[0] - 1);
+                    const int fy = !per[1] && (y == 0 || y == v.n[1] - 1);
+                    const int fz = !per[2] && (z == 0 || z == v.n[2] - 1);
+                    const int on = fx + fy + fz;
+                    const int dirs = fx | (fy << 1) | (fz << 2);
+                    if (on >= 2 || (on == 1 && (dirs & fmask))) b.push_back(x + v.n[0] * (y + v.n[1] * z));
+                }
+        return b;
+    };
+    elas_ctx c = g->ctx;
+    const std::vector<int> b64 = make_list(m64);
+    v.L64.xface_list = m64;
+    v.nbnd = (int)b64.size();
     if (v.nbnd) {
-        if ((rc = galloc(g, &v.bnd, b.size()))) return rc;
-        if ((rc = galloc(g, &v.bcoef64, b.size() * kEdgeCoef))) return rc;
-        if (mixed && (rc = galloc(g, &v.bcoef32, b.size() * kEdgeCoef))) return rc;
-        elas_ctx c = g->ctx;
-        CUDA_TRY(c, cudaMemcpyAsync(v.bnd, b.data(), sizeof(int) * b.size(), cudaMemcpyHostToDevice, c->stream));
-        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if ((rc = galloc(g, &v.bnd, b64.size()))) return rc;
+        if ((rc = galloc(g, &v.bcoef64, b64.size() * kEdgeCoef))) return rc;
+        CUDA_TRY(c, cudaMemcpyAsync(v.bnd, b64.data(), sizeof(int) * b64.size(), cudaMemcpyHostToDevice, c->stream));
     }
+    v.L32.xface_list = m32;
+    if (mixed) {
+        const std::vector<int> b32 = m32 == m64 ? b64 : make_list(m32);
+        v.nbnd32 = (int)b32.size();
+        if (v.nbnd32) {
+            if (m32 == m64) {
+                v.bnd32 = v.bnd;
+            } else {
+                if ((rc = galloc(g, &v.bnd32, b32.size()))) return rc;
+                CUDA_TRY(c, cudaMemcpyAsync(v.bnd32, b32.data(), sizeof(int) * b32.size(), cudaMemcpyHostToDevice,
+                                            c->stream));
+            }
+            if ((rc = galloc(g, &v.bcoef32, b32.size() * kEdgeCoef))) return rc;
+        }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return ELAS_OK;
 }
 
@@ -895,11 +917,14 @@ void refresh_lv(elas_grid g) {
         fill_lv(v.L32, v.n, g->desc.periodic, h, g->K, g->bc_type);
         v.L64.mod = v.mod64;
         v.L32.mod = v.mod32;
-        v.L64.bnodes = v.L32.bnodes = v.bnd;
+        v.L64.bnodes = v.bnd;
+        v.L32.bnodes = v.bnd32;
         v.L64.bcoef = v.bcoef64;
         v.L32.bcoef = v.bcoef32;
-        v.L64.nbnd = v.L32.nbnd = v.nbnd;
-        v.L64.xface_list = v.L32.xface_list = face_list_mask(v.n, g->desc.periodic);
+        v.L64.nbnd = v.nbnd;
+        v.L32.nbnd = v.nbnd32;
+        v.L64.xface_list = face_list_mask(v.n, g->desc.periodic, false);
+        v.L32.xface_list = face_list_mask(v.n, g->desc.periodic, g->K == 21);
         v.L64.divc = v.divc;
         v.L32.modh = v.mod16;
         v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
@@ -1028,10 +1053,13 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
                      N * 48;
         }
         // stored rows: edges and corners, and the x faces
-        const int fm = face_list_mask(n.data(), d->periodic);
-        const size_t stored = (size_t)4 * (n[0] + n[1] + n[2]) + ((fm & 1) ? (size_t)2 * n[1] * n[2] : 0) +
-                              ((fm & 2) ? (size_t)2 * n[0] * n[2] : 0) + ((fm & 4) ? (size_t)2 * n[0] * n[1] : 0);
-        total += stored * kEdgeCoef * (d->mixed ? 12 : 8);
+        auto stored_for = [&](int fm) {
+            return (size_t)4 * (n[0] + n[1] + n[2]) + ((fm & 1) ? (size_t)2 * n[1] * n[2] : 0) +
+                   ((fm & 2) ? (size_t)2 * n[0] * n[2] : 0) + ((fm & 4) ? (size_t)2 * n[0] * n[1] : 0);
+        };
+        const size_t stored = stored_for(face_list_mask(n.data(), d->periodic, false));
+        total += stored * kEdgeCoef * 8;
+        if (d->mixed) total += stored_for(face_list_mask(n.data(), d->periodic, K == 21)) * kEdgeCoef * 4;
         if (d->mixed && d->max_levels != 1 && &n == &dims.front())   // double-float copies of the finest level
             total += 8 * (N * ((K == 21 ? 39 : 2) + 6) + stored * kEdgeCoef);
     }
@@ -1075,7 +1103,8 @@ int elas_grid_create(elas_ctx c, const elas_grid_desc* d, elas_grid* out) {
     // block per 256 nodes) + edges/corners (one warp per node)
     size_t maxblocks = 0;
     for (auto& v : g->lv) {
-        const size_t nb = 2 * (size_t)((v.N + kBlock - 1) / kBlock) + ((size_t)v.nbnd * 32 + kBlock - 1) / kBlock + 8;
+        const size_t nbl = (size_t)(v.nbnd > v.nbnd32 ? v.nbnd : v.nbnd32);
+        const size_t nb = 2 * (size_t)((v.N + kBlock - 1) / kBlock) + (nbl * 32 + kBlock - 1) / kBlock + 8;
         maxblocks = nb > maxblocks ? nb : maxblocks;
     }
     const size_t nparts = maxblocks * kPartialStride + 64;
@@ -1528,7 +1557,7 @@ int elas_op_residual_noalloc(elas_grid g, int level, int precision, const void* 
     Level& v = g->lv[level];
     // blocks of one residual launch set (interior, faces, edges), as sized at grid creation
     const size_t nb_max =
-        2 * (size_t)((v.N + kBlock - 1) / kBlock) + ((size_t)v.nbnd * 32 + kBlock - 1) / kBlock + 8;
+        2 * (size_t)((v.N + kBlock - 1) / kBlock) + ((size_t)(precision == 0 ? v.nbnd : v.nbnd32) * 32 + kBlock - 1) / kBlock + 8;
     if (nb_max * kPartialStride + 8 > (size_t)ELAS_NOALLOC_SCRATCH_DOUBLES)
         return set_err(c, ELAS_ERR_INVALID_ARG, "level too large for the no-allocation residual's static scratch");
     double* scratch = noalloc_scratch(c);

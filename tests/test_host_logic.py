@@ -41,12 +41,13 @@ def test_hbm_estimate_orders_precisions_and_sizes(E):
     assert fp64 < half < mixed
     # FP64 general moduli: 21 planes + 18 divergence planes + 12 field planes per node,
     # summed over a hierarchy of about 8/7 of the finest level, plus 9 input planes
-    # (eigenstrain, body force) and the stored rows (243 coefficients a node): on levels
-    # of at most 300000 nodes every boundary node's, on levels of 2^20 nodes and more the
-    # edges', corners' and x faces'
+    # (eigenstrain, body force) and the stored rows (243 coefficients a node) of the edges
+    # and corners (FP64 levels below 2^20 nodes)
     n0 = 33 ** 3
-    base = 8 * (51 + 9) * n0 + 8 * 243 * 6 * 33 * 33
+    base = 8 * (51 + 9) * n0
     assert base <= fp64 <= 1.5 * base
+    # the FP32 copy of such a level of general moduli also stores every face node's row
+    assert mixed - fp64 >= 4 * 243 * 6 * 31 * 31
     n1 = 129 ** 3
     large = M.Problem(n=(129, 129, 129), name="descriptor only")
     large.moduli_kind = M.MODULI_GEN21
