@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3)
 }
 
 template <typename T, typename TR, int KIND, bool NORM, bool HM, int ML>
-__global__ void __launch_bounds__(kBatchBlock, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kBatchBlock, sizeof(T) == 4 ? 4 : 2)
     k_batch_resid(const ResidTask<T, TR>* __restrict__ tasks, const int2* __restrict__ bmap) {
     __shared__ __align__(16) ResidTask<T, TR> t;
     const int b = load_task(tasks, bmap, t), tid = threadIdx.x;

@@ -1240,10 +1240,11 @@ __device__ __forceinline__ void add_correction_df_body(const Lv<double>& L, doub
 // r = f - load - A u on every node; block partials of sum r^2 and the rigid moments.
 // Resident blocks per SM: two for FP64 (at most 128 registers; the FP64 instance is bound
 // by the FP64 pipe and needs the warps to keep it busy, one block at 180 registers ran
-// 15% slower), three for FP32 (80 registers with a few spills: 0.97 -> 0.79 ms at 257^3,
-// the same latency-for-registers trade as the smoother's (256,3) shape).
+// 15% slower), four for FP32 (64 registers with spills: 0.97 ms at one block, 0.79 at
+// three, 0.74 at four for 257^3 with colour-split records; the same latency-for-registers
+// trade as the smoother's shapes).
 template <typename T, typename TR, int KIND, bool NORM, bool HM, int ML>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 2) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) k_residual(Lv<T> L, const T* __restrict__ u, const T* __restrict__ f,
                                                     NullInfo nf, const double* __restrict__ lam,
                                                     TR* __restrict__ r, double* __restrict__ partials, BndSegs sg) {
     if (L.active && *L.active == 0) return;
