@@ -131,6 +131,42 @@ def test_sweep_matches_oracle(E, ctx, case):
     g.close()
 
 
+@pytest.mark.parametrize("n,sweep", [((71, 69, 67), True), ((103, 103, 99), False)])
+def test_face_row_paths_match_oracle_at_size(E, ctx, n, sweep):
+    """Face rows take different code paths by level size: levels of 300000 to 2^20 nodes
+    evaluate every face row in the face kernels (FP64 and FP32), larger ones take the x
+    faces from stored coefficients and the y and z faces from the face kernels.  One level
+    of each band, general moduli and mixed boundary types: operator rows against the
+    oracle, and one sweep on the first (the oracle's sweep of a million nodes takes
+    minutes)."""
+    p = mixed_bc_problem(n=n)
+    g = E.grid_from_problem(ctx, p, mixed=True, max_levels=1)
+    lev = S.level_from_problem(p)
+    types = S.row_types(lev)
+    rng = np.random.default_rng(7)
+    u = np.where(types == M.DIRICHLET, 0.0, rng.normal(size=(3,) + g.shape))
+    f = np.where(types == M.DIRICHLET, 0.0, rng.normal(size=(3,) + g.shape)) * 100
+    ref = S.apply(lev, u, types)
+    assert rel_err(g.op_apply(0, E.FP64, dev(u)).cpu().numpy(), ref) < 1e-12
+    assert rel_err(g.op_apply(0, E.MIXED, dev(u, torch.float32)).cpu().numpy(), ref) < 2e-5
+    if not sweep:
+        g.close()
+        return
+    B = S.block_diagonal(lev, types)
+    k, j, i = np.meshgrid(*[np.arange(s) for s in lev.shape], indexing="ij")
+    L = MG.LevelData(lev, types, np.linalg.inv(np.moveaxis(B, (0, 1), (-2, -1))), (i + j + k) % 2,
+                     MG.rigid_modes(lev, types))
+    sw = u.copy()
+    MG.sweep(L, sw, f)
+    ud = dev(u)
+    g.op_sweep(0, E.FP64, ud, dev(f))
+    assert rel_err(ud.cpu().numpy(), sw) < 1e-12
+    u32 = dev(u, torch.float32)
+    g.op_sweep(0, E.MIXED, u32, dev(f, torch.float32))
+    assert rel_err(u32.cpu().numpy(), sw) < 5e-5
+    g.close()
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_transfers_match_oracle(E, ctx, case):
     p = CASES[case]()
