@@ -267,21 +267,25 @@ Lv<dfloat> df_view(const Level& v) {
 }
 
 // Face directions (bit A) whose face nodes take their rows from stored coefficients (a
-// warp per node) rather than from the face kernels.  Levels of 2^20 nodes and more list
-// the x faces, whose stencil neighbours lie nx apart (rows evaluated from the fields read
-// one sector per value; 257^3 half-sweep 0.53 -> 0.48 ms).  The FP32 copies of levels of
+// warp per node) rather than from the face kernels; FP32 copies only.  Levels of 2^20
+// nodes and more list the x faces, whose stencil neighbours lie nx apart (rows evaluated
+// from the fields read one sector per value; 257^3 half-sweep 0.53 -> 0.48 ms).  Levels of
 // general moduli with up to 300000 nodes (65^3 and coarser) list every face: there the
 // face kernels' rows (tens of dependent moduli and displacement loads, long code) dominate
-// the launches; measured V-cycles of a 65^3 hierarchy 0.87 -> 0.44 ms.  Not so on FP64
-// levels (a stored row is 243 FMAs on the narrow FP64 pipe: 33^3 FP64 solves 133 -> 91
-// per second), with isotropic moduli (two moduli per node make the face rows cheap), nor
-// on 129^3 (the coefficients add to a bandwidth-bound launch: 1.37 -> 1.60 ms).
+// the launches; measured V-cycles of a 65^3 hierarchy 0.87 -> 0.44 ms.  Not so with
+// isotropic moduli (two moduli per node make the face rows cheap), nor on 129^3 (the
+// coefficients add to a bandwidth-bound launch: 1.37 -> 1.60 ms).  FP64 levels store the
+// edge and corner rows only: a stored row there costs 243 FMAs on the narrow FP64 pipe per
+// application (33^3 FP64 solves 133 -> 91 per second with every face listed) and 243
+// evaluations of the generic row in FP64 at every set-up (the x faces of 257^3: tens of
+// milliseconds per new moduli field).
 constexpr size_t kAllFacesListMaxNodes = 300000;
 constexpr size_t kXFaceListMinNodes = size_t(1) << 20;
-int face_list_mask(const int n[3], const int per[3], bool fp32_general) {
+int face_list_mask(const int n[3], const int per[3], bool fp32, bool general) {
+    if (!fp32) return 0;
     const size_t N = (size_t)n[0] * n[1] * n[2];
     int m = 0;
-    if (fp32_general && N <= kAllFacesListMaxNodes) m = 7;
+    if (general && N <= kAllFacesListMaxNodes) m = 7;
     else if (N >= kXFaceListMinNodes) m = 1;
     for (int d = 0; d < 3; ++d)
         if (per[d]) m &= ~(1 << d);
@@ -860,7 +864,7 @@ int level_alloc(elas_grid g, Level& v, bool mixed) {
     // directions in face_list_mask; the other face nodes are enumerated arithmetically by
     // the face kernels
     const int* per = g->desc.periodic;
-    const int m64 = face_list_mask(v.n, per, false), m32 = face_list_mask(v.n, per, g->K == 21);
+    const int m64 = face_list_mask(v.n, per, false, g->K == 21), m32 = face_list_mask(v.n, per, true, g->K == 21);
     auto make_list = [&](int fmask) {
         std::vector<int> b;
         for (int z = 0; z < v.n[2]; ++z)
@@ -923,8 +927,8 @@ void refresh_lv(elas_grid g) {
         v.L32.bcoef = v.bcoef32;
         v.L64.nbnd = v.nbnd;
         v.L32.nbnd = v.nbnd32;
-        v.L64.xface_list = face_list_mask(v.n, g->desc.periodic, false);
-        v.L32.xface_list = face_list_mask(v.n, g->desc.periodic, g->K == 21);
+        v.L64.xface_list = face_list_mask(v.n, g->desc.periodic, false, g->K == 21);
+        v.L32.xface_list = face_list_mask(v.n, g->desc.periodic, true, g->K == 21);
         v.L64.divc = v.divc;
         v.L32.modh = v.mod16;
         v.L32.mlay = v.mod16 ? kModRecords : (v.split ? kModSplit : (v.mod32 ? kModBlocked : kModPlanes));
@@ -1057,9 +1061,9 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* d) {
             return (size_t)4 * (n[0] + n[1] + n[2]) + ((fm & 1) ? (size_t)2 * n[1] * n[2] : 0) +
                    ((fm & 2) ? (size_t)2 * n[0] * n[2] : 0) + ((fm & 4) ? (size_t)2 * n[0] * n[1] : 0);
         };
-        const size_t stored = stored_for(face_list_mask(n.data(), d->periodic, false));
+        const size_t stored = stored_for(face_list_mask(n.data(), d->periodic, false, K == 21));
         total += stored * kEdgeCoef * 8;
-        if (d->mixed) total += stored_for(face_list_mask(n.data(), d->periodic, K == 21)) * kEdgeCoef * 4;
+        if (d->mixed) total += stored_for(face_list_mask(n.data(), d->periodic, true, K == 21)) * kEdgeCoef * 4;
         if (d->mixed && d->max_levels != 1 && &n == &dims.front())   // double-float copies of the finest level
             total += 8 * (N * ((K == 21 ? 39 : 2) + 6) + stored * kEdgeCoef);
     }
