@@ -61,7 +61,7 @@ void launch_residual(const Lv<T>& L, const T* u, const T* f, const NullInfo* nf,
 // of u, f, the moduli (with the divergence) and the stored rows (L: the level with those
 // planes), written as FP32; partials (required) as launch_residual's.  Interior threads take
 // kDfNodesPerThread nodes each.
-constexpr int kDfNodesPerThread = 4;
+constexpr int kDfNodesPerThread = 8;
 void launch_residual_df(const Lv<dfloat>& L, const dfloat* u, const dfloat* f, const NullInfo* nf, const double* lam,
                         float* r, double* partials, int* nblocks, cudaStream_t s);
 int residual_df_block_count(const Lv<dfloat>& L);
