@@ -767,18 +767,19 @@ bool outer_df(elas_grid g, const elas_solve_opts* o) {
 }
 
 // Allocate (once) and fill (after a set-up) the double-float copies of the finest level's
-// moduli, divergence and stored rows; u and f are split at the start of each solve.
+// moduli, divergence and stored rows; u and f are split at the start of each solve.  Each
+// copy is allocated on its own, so a call after a refused allocation completes the set.
 int df_prepare(elas_grid g) {
     Level& v = g->lv[0];
     const size_t N = (size_t)v.N;
     int rc = ELAS_OK;
-    if (!v.m2) {
-        if (!rc) rc = galloc(g, &v.m2, (size_t)(g->K == 21 ? 39 : 2) * N);
-        if (!rc) rc = galloc(g, &v.u2, 3 * N);
-        if (!rc) rc = galloc(g, &v.f2, 3 * N);
-        if (!rc && v.nbnd) rc = galloc(g, &v.bc2, (size_t)v.nbnd * kEdgeCoef);
-        if (rc) return rc;
+    if (!v.m2 || !v.u2 || !v.f2 || (v.nbnd && !v.bc2)) {
         g->df_gen = ~0ull;
+        if (!v.m2) rc = galloc(g, &v.m2, (size_t)(g->K == 21 ? 39 : 2) * N);
+        if (!rc && !v.u2) rc = galloc(g, &v.u2, 3 * N);
+        if (!rc && !v.f2) rc = galloc(g, &v.f2, 3 * N);
+        if (!rc && v.nbnd && !v.bc2) rc = galloc(g, &v.bc2, (size_t)v.nbnd * kEdgeCoef);
+        if (rc) return rc;
     }
     if (g->df_gen != g->gen) {
         elas_ctx c = g->ctx;
