@@ -142,7 +142,9 @@ size_t elas_grid_bytes_estimate(const elas_grid_desc* desc);
  * stored per point in Section 4.3).  Coarse levels take the restriction of the
  * stored components. */
 int  elas_set_moduli(elas_grid g, const double* comps, int memspace);
-/* Eigenstrain eps0 (Eq. 1a), 6 x N doubles, or NULL for none. */
+/* Eigenstrain eps0 (Eq. 1a), 6 x N doubles, or NULL for none.  The grid copies the
+ * data into its own buffer; clearing with NULL keeps that buffer for the next set
+ * (the same holds for the body force and the face values). */
 int  elas_set_eigenstrain(elas_grid g, const double* eps6, int memspace);
 /* Body force b (Eq. 1a), 3 x N doubles, or NULL for none. */
 int  elas_set_body_force(elas_grid g, const double* b3, int memspace);

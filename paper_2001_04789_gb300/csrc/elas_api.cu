@@ -116,6 +116,7 @@ struct elas_grid_s {
     int bc_type[6][3];
     double bc_val[6][3];
     double* face[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::map<double**, double*> kept;   // buffers of cleared inputs, reused when set again
     // bottom
     int* dofs = nullptr;
     int nfree = 0, ntot = 0;
@@ -1183,17 +1184,26 @@ int elas_set_moduli(elas_grid g, const double* comps, int memspace) {
     return ELAS_OK;
 }
 
+// Set (src non-null) or clear one finest-level input.  A cleared input's buffer stays with
+// the grid and serves the next set of the same input, so clearing and setting again
+// allocates nothing.
 static int set_field(elas_grid g, double** slot, const double* src, size_t count, int memspace) {
+    g->rhs_dirty = true;
     if (!src) {
-        *slot = nullptr;   // memory stays with the grid until destroyed
-        g->rhs_dirty = true;
+        if (*slot) g->kept[slot] = *slot;
+        *slot = nullptr;
         return ELAS_OK;
     }
     if (!*slot) {
-        int rc = galloc(g, slot, count);
-        if (rc) return rc;
+        auto it = g->kept.find(slot);
+        if (it != g->kept.end()) {
+            *slot = it->second;
+            g->kept.erase(it);
+        } else {
+            int rc = galloc(g, slot, count);
+            if (rc) return rc;
+        }
     }
-    g->rhs_dirty = true;
     return copy_in(g->ctx, *slot, src, count, memspace);
 }
 
@@ -1236,15 +1246,7 @@ int elas_set_bc(elas_grid g, int face, int comp, int type, double value) {
 
 int elas_set_face_values(elas_grid g, int face, const double* values, int memspace) {
     if (!g || face < 0 || face > 5) return ELAS_ERR_INVALID_ARG;
-    if (!values) {
-        g->face[face] = nullptr;
-        g->rhs_dirty = true;
-        return ELAS_OK;
-    }
-    double* slot = g->face[face];
-    int rc = set_field(g, &slot, values, (size_t)3 * g->lv[0].N, memspace);
-    g->face[face] = slot;
-    return rc;
+    return set_field(g, &g->face[face], values, (size_t)3 * g->lv[0].N, memspace);
 }
 
 void elas_solve_opts_default(elas_solve_opts* o) {
