@@ -170,6 +170,52 @@ def exported_symbols():
     return [n for n in dir(lib()) if n.startswith("elas_")]
 
 
+def check_field(name, a, dims, dtype, device):
+    """Check a device field argument of a single operation before its pointer goes to the
+    library, whose kernels address 3 x nx x ny x nz elements of it (dims = (nx, ny, nz),
+    the level's nodes) unchecked: a contiguous CUDA tensor on `device`, of element type
+    `dtype` (None: the library refuses the operation before reading it) and of that size."""
+    import torch
+    if not isinstance(a, torch.Tensor) or not a.is_cuda or a.get_device() != device:
+        raise ValueError(f"{name}: a CUDA tensor on device {device} is required")
+    if dtype is not None and a.dtype != dtype:
+        raise ValueError(f"{name}: dtype {a.dtype}, the operation takes {dtype}")
+    if not a.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is required")
+    nx, ny, nz = dims
+    if a.numel() != 3 * nx * ny * nz:
+        raise ValueError(f"{name}: {a.numel()} elements, the level holds 3 x {nx} x {ny} x {nz}")
+    return a
+
+
+def check_buffer(name, a, count, device):
+    """Check a tensor the library copies `count` doubles from or into (host or device
+    memory, by pointer and count alone): a contiguous float64 tensor of exactly that size,
+    on `device` when it is a CUDA tensor."""
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise ValueError(f"{name}: a torch tensor is required")
+    if a.is_cuda and a.get_device() != device:
+        raise ValueError(f"{name}: the tensor is on device {a.get_device()}, the context on {device}")
+    if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != count:
+        raise ValueError(f"{name}: a contiguous float64 tensor of {count} elements is required "
+                         f"({a.dtype}, {a.numel()} elements)")
+    return a
+
+
+def op_dtype(precision, output=False):
+    """Element type of a single operation's fields: FP64, FP32 (MIXED), or for OP_DF FP64
+    inputs and an FP32 output; None for a precision the library refuses."""
+    import torch
+    if precision == FP64:
+        return torch.float64
+    if precision == MIXED:
+        return torch.float32
+    if precision == OP_DF:
+        return torch.float32 if output else torch.float64
+    return None
+
+
 def _ptr(a):
     """Device pointer of a torch tensor, or host pointer of a C-contiguous numpy array."""
     if hasattr(a, "data_ptr"):
@@ -284,14 +330,16 @@ class Grid:
         self.ctx.check(lib().elas_set_moduli(self.h, _ptr(a), HOST))
 
     def set_moduli_from(self, tensor):
-        self.ctx.after_current(tensor)
         """Moduli from a torch tensor: pinned host memory or device memory."""
+        check_buffer("moduli", tensor, self.desc.moduli_kind * self.N, self.ctx.device)
+        self.ctx.after_current(tensor)
         space = DEVICE if tensor.is_cuda else HOST
         self.ctx.check(lib().elas_set_moduli(self.h, _ptr(tensor), space))
 
     def displacement_into(self, tensor):
-        self.ctx.after_current(tensor)
         """Copy the displacement into a torch tensor (pinned host or device)."""
+        check_buffer("displacement", tensor, 3 * self.N, self.ctx.device)
+        self.ctx.after_current(tensor)
         space = DEVICE if tensor.is_cuda else HOST
         self.ctx.check(lib().elas_get_displacement(self.h, _ptr(tensor), space))
         return tensor
@@ -379,7 +427,14 @@ class Grid:
     def _sync(self):
         self.ctx.stream.synchronize()
 
+    def _field(self, name, a, level, dtype):
+        return check_field(name, a, self.level_dims(level), dtype, self.ctx.device)
+
+    def _dtype(self, precision, output=False):
+        return op_dtype(precision, output)
+
     def op_apply(self, level, precision, u):
+        self._field("u", u, level, self._dtype(precision))
         out = self.ctx.torch.empty_like(u)
         self.ctx.after_current(u, out)
         self.ctx.check(lib().elas_op_apply(self.h, level, precision, _ptr(u), _ptr(out)))
@@ -388,6 +443,8 @@ class Grid:
     def op_residual(self, level, precision, u, f):
         """r = f - A u and sum r^2; precision OP_DF: double-float from FP64 u, f, r in FP32."""
         T = self.ctx.torch
+        self._field("u", u, level, self._dtype(precision))
+        self._field("f", f, level, self._dtype(precision))
         r = T.empty_like(u, dtype=T.float32) if precision == OP_DF else T.empty_like(u)
         self.ctx.after_current(u, f, r)
         ss = C.c_double()
@@ -397,6 +454,9 @@ class Grid:
     def op_residual_noalloc(self, level, precision, u, f, r):
         """elas_op_residual without any allocation: the caller passes the output r;
         the reduction uses the library's static device scratch."""
+        self._field("u", u, level, self._dtype(precision))
+        self._field("f", f, level, self._dtype(precision))
+        self._field("r", r, level, self._dtype(precision, output=True))
         ss = C.c_double()
         self.ctx.after_current(u, f, r)
         self.ctx.check(lib().elas_op_residual_noalloc(self.h, level, precision, _ptr(u), _ptr(f), _ptr(r),
@@ -404,17 +464,22 @@ class Grid:
         return ss.value
 
     def op_sweep(self, level, precision, u, f):
+        self._field("u", u, level, self._dtype(precision))
+        self._field("f", f, level, self._dtype(precision))
         self.ctx.after_current(u, f)
         self.ctx.check(lib().elas_op_sweep(self.h, level, precision, _ptr(u), _ptr(f)))
         return u
 
     def op_smooth(self, level, precision, smoother, u, f, omega=2.0 / 3.0):
         """One sweep of the given smoother (SMOOTH_RB, SMOOTH_GS8, SMOOTH_JACOBI), in place."""
+        self._field("u", u, level, self._dtype(precision))
+        self._field("f", f, level, self._dtype(precision))
         self.ctx.after_current(u, f)
         self.ctx.check(lib().elas_op_smooth(self.h, level, precision, smoother, omega, _ptr(u), _ptr(f)))
         return u
 
     def op_restrict(self, level, precision, r):
+        self._field("r", r, level, self._dtype(precision))
         nc = self.level_dims(level + 1)
         fc = self.ctx.torch.empty((3, nc[2], nc[1], nc[0]), dtype=r.dtype, device=r.device)
         self.ctx.after_current(r, fc)
@@ -422,6 +487,8 @@ class Grid:
         return fc
 
     def op_prolong_add(self, level, precision, ec, u):
+        self._field("ec", ec, level + 1, self._dtype(precision))
+        self._field("u", u, level, self._dtype(precision))
         self.ctx.after_current(ec, u)
         self.ctx.check(lib().elas_op_prolong_add(self.h, level, precision, _ptr(ec), _ptr(u)))
         return u
@@ -433,6 +500,7 @@ class Grid:
         return f
 
     def op_bottom(self, precision, f):
+        self._field("f", f, self.levels() - 1, self._dtype(precision))
         u = self.ctx.torch.empty_like(f)
         self.ctx.after_current(f, u)
         self.ctx.check(lib().elas_op_bottom(self.h, precision, _ptr(f), _ptr(u)))

@@ -1,6 +1,6 @@
 """Host-side logic of the C library that needs no GPU: the smoother's tuning table
-(text round trip, rejection of unknown launch shapes) and the HBM estimate used for
-admission by the serving loop."""
+(text round trip, rejection of unknown launch shapes), the HBM estimate used for
+admission by the serving loop, and the binding's checks of single-operation arguments."""
 import pytest
 
 from paper_2001_04789_gb300 import microstructure as M
@@ -56,3 +56,54 @@ def test_hbm_estimate_orders_precisions_and_sizes(E):
     larger.moduli_kind = M.MODULI_GEN21
     ratio = est(larger, mixed=True) / est(large, mixed=True)
     assert 7.0 < ratio < 9.0            # node count grows 7.9x from 129^3 to 257^3
+
+
+class _OnDevice0(torch.Tensor):
+    """A host tensor that reports itself as a CUDA tensor on device 0, so the binding's
+    argument checks can be exercised without a GPU (no pointer reaches the library)."""
+
+    @property
+    def is_cuda(self):
+        return True
+
+    def get_device(self):
+        return 0
+
+
+def test_single_operation_arguments_are_checked_before_the_library(E):
+    """The single-operation wrappers refuse, before any pointer reaches the library, a
+    field argument its kernels would address out of bounds: not a CUDA tensor (a numpy
+    array, a host tensor, another device), the wrong element type, a strided view, or a
+    size other than 3 x the level's nodes."""
+    dims = (5, 4, 3)
+    ok = torch.zeros((3, 3, 4, 5), dtype=torch.float64).as_subclass(_OnDevice0)
+    assert E.check_field("u", ok, dims, torch.float64, 0) is ok
+    assert E.check_field("u", ok, dims, None, 0) is ok        # dtype left to the library
+    bad = {
+        "numpy": torch.zeros(3 * 60, dtype=torch.float64).numpy(),
+        "host": torch.zeros(3 * 60, dtype=torch.float64),
+        "device 1": ok,
+        "dtype": ok.to(torch.float32),
+        "strided": torch.zeros((3, 3, 4, 10), dtype=torch.float64).as_subclass(_OnDevice0)[..., ::2],
+        "short": ok.reshape(-1)[:-1],
+        "long": torch.zeros(3 * 60 + 3, dtype=torch.float64).as_subclass(_OnDevice0),
+    }
+    for what, a in bad.items():
+        device = 1 if what == "device 1" else 0
+        with pytest.raises(ValueError):
+            E.check_field("u", a, dims, torch.float64, device)
+    # whole-grid copies (moduli in, displacement out): float64, contiguous, exact count;
+    # host tensors are copied from host memory, device ones must be on the context's device
+    host = torch.zeros(3 * 60, dtype=torch.float64)
+    assert E.check_buffer("u", host, 180, 0) is host
+    assert E.check_buffer("u", ok.reshape(-1), 180, 0) is not None
+    for a, device in ((host.numpy(), 0), (host.to(torch.float32), 0), (host[:-1], 0),
+                      (torch.zeros((3, 120), dtype=torch.float64)[:, ::2], 0), (ok, 1)):
+        with pytest.raises(ValueError):
+            E.check_buffer("u", a, 180, device)
+    # element types: FP64 and FP32 fields; the double-float residual takes FP64 u and f
+    # and writes FP32 r; a precision the library refuses has none
+    assert E.op_dtype(E.FP64) == torch.float64 and E.op_dtype(E.FP64, output=True) == torch.float64
+    assert E.op_dtype(E.MIXED) == torch.float32
+    assert E.op_dtype(E.OP_DF) == torch.float64 and E.op_dtype(E.OP_DF, output=True) == torch.float32
+    assert E.op_dtype(7) is None
