@@ -233,7 +233,9 @@ int  elas_query_residual_inf(elas_grid g, double* rel_inf, double* abs_inf);
 
 /* ---- single operations of the path, for testing and benchmarking --------------
  * All take DEVICE pointers to FP64 (precision 0) or FP32 (precision 1) arrays of
- * the named level (3 x N_level unless stated) and run on the context's stream. */
+ * the named level (3 x N_level unless stated) and run on the context's stream.  A
+ * NULL grid or array pointer is ELAS_ERR_INVALID_ARG; the arrays' extent and element
+ * type cannot be checked through a raw pointer and are the caller's to get right. */
 
 /* out = A u on every row of `level`: interior and traction rows (Section 2.1.1
  * product rule, half-cell closure of Eq. 1c), Neumann rows, u itself on

@@ -1488,6 +1488,7 @@ static int check_level(elas_grid g, int level, int precision, bool allow_df = fa
 }
 
 int elas_op_apply(elas_grid g, int level, int precision, const void* u, void* out) {
+    if (!g || !u || !out) return ELAS_ERR_INVALID_ARG;
     int rc = check_level(g, level, precision);
     if (rc) return rc;
     Level& v = g->lv[level];
@@ -1499,6 +1500,7 @@ int elas_op_apply(elas_grid g, int level, int precision, const void* u, void* ou
 }
 
 int elas_op_residual(elas_grid g, int level, int precision, const void* u, const void* f, void* r, double* sumsq) {
+    if (!g || !u || !f || !r) return ELAS_ERR_INVALID_ARG;
     int rc = check_level(g, level, precision, true);
     if (rc) return rc;
     Level& v = g->lv[level];
@@ -1553,7 +1555,7 @@ static double* noalloc_scratch(elas_ctx c) {
 
 int elas_op_residual_noalloc(elas_grid g, int level, int precision, const void* u, const void* f, void* r,
                              double* sumsq) {
-    if (!g) return ELAS_ERR_INVALID_ARG;
+    if (!g || !u || !f || !r) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = g->ctx;
     // the grid's set-up (after new moduli, boundary types or loads) may allocate, so this
     // entry point refuses to run it
@@ -1588,6 +1590,7 @@ int elas_op_residual_noalloc(elas_grid g, int level, int precision, const void* 
 }
 
 int elas_op_sweep(elas_grid g, int level, int precision, void* u, const void* f) {
+    if (!g || !u || !f) return ELAS_ERR_INVALID_ARG;
     int rc = check_level(g, level, precision);
     if (rc) return rc;
     Level& v = g->lv[level];
@@ -1605,6 +1608,7 @@ int elas_op_sweep(elas_grid g, int level, int precision, void* u, const void* f)
 }
 
 int elas_op_smooth(elas_grid g, int level, int precision, int smoother, double omega, void* u, const void* f) {
+    if (!g || !u || !f) return ELAS_ERR_INVALID_ARG;
     int rc = check_level(g, level, precision);
     if (rc) return rc;
     if (smoother < ELAS_SMOOTH_RB || smoother > ELAS_SMOOTH_JACOBI)
@@ -1618,6 +1622,7 @@ int elas_op_smooth(elas_grid g, int level, int precision, int smoother, double o
 }
 
 int elas_op_restrict(elas_grid g, int level, int precision, const void* r, void* fc) {
+    if (!g || !r || !fc) return ELAS_ERR_INVALID_ARG;
     int rc = check_level(g, level, precision);
     if (rc) return rc;
     if (level + 1 >= (int)g->lv.size()) return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "no coarser level");
@@ -1633,6 +1638,7 @@ int elas_op_restrict(elas_grid g, int level, int precision, const void* r, void*
 }
 
 int elas_op_prolong_add(elas_grid g, int level, int precision, const void* ec, void* u) {
+    if (!g || !ec || !u) return ELAS_ERR_INVALID_ARG;
     int rc = check_level(g, level, precision);
     if (rc) return rc;
     if (level + 1 >= (int)g->lv.size()) return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "no coarser level");
@@ -1646,6 +1652,7 @@ int elas_op_prolong_add(elas_grid g, int level, int precision, const void* ec, v
 }
 
 int elas_op_rhs(elas_grid g, double* f_out) {
+    if (!g || !f_out) return ELAS_ERR_INVALID_ARG;
     int rc = check_level(g, 0, 0);
     if (rc) return rc;
     CUDA_TRY(g->ctx, cudaMemcpyAsync(f_out, g->lv[0].f, sizeof(double) * 3 * (size_t)g->lv[0].N,
@@ -1655,6 +1662,7 @@ int elas_op_rhs(elas_grid g, double* f_out) {
 }
 
 int elas_op_bottom(elas_grid g, int precision, const void* f, void* u) {
+    if (!g || !f || !u) return ELAS_ERR_INVALID_ARG;
     const int l = (int)g->lv.size() - 1;
     int rc = check_level(g, l, precision);
     if (rc) return rc;

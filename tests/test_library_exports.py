@@ -1,4 +1,5 @@
-"""The C-ABI library loads without a GPU and exports every function elas.h declares."""
+"""The C-ABI library loads without a GPU, exports every function elas.h declares, and
+refuses NULL handles with an error code before touching the device."""
 import os
 import re
 import subprocess
@@ -45,3 +46,53 @@ def test_library_loads_through_ctypes_without_gpu(libpath):
     L = E.lib()
     for n in declared_functions():
         assert hasattr(L, n)
+
+
+_NULL_CALLS = r'''
+import re, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2001_04789_gb300 import elas as E
+L = E.lib()
+text = re.sub(r"/\*.*?\*/", "", open(sys.argv[2]).read(), flags=re.S)
+no_handle = {"elas_measure_fma_peak", "elas_launch_count", "elas_autotune_dump", "elas_autotune_load",
+             "elas_solve_opts_default"}
+for m in re.finditer(r"\n\s*([a-z_ ]+?\**)\s*(elas_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+    ret, name = m.group(1).strip(), m.group(2)
+    if name in no_handle:
+        continue
+    args = []
+    for p in (q.strip() for q in m.group(3).split(",")):
+        if "*" in p or "[" in p or p.split()[0].startswith("elas_"):
+            args.append(None)
+        elif p.startswith("double"):
+            args.append(0.0)
+        else:
+            args.append(0)
+    print(name, ret, getattr(L, name)(*args), flush=True)
+'''
+
+
+def test_every_entry_point_refuses_null_handles_without_a_gpu(libpath):
+    """Each entry point that takes a context, grid, AMR, server or output handle returns
+    ELAS_ERR_INVALID_ARG for NULL ones (zeros for the size queries, a message for the
+    last error) before touching the device: no call dereferences a NULL handle.  Run in a
+    child process, so that a crash fails the test rather than the test run."""
+    import sys
+    r = subprocess.run([sys.executable, "-c", _NULL_CALLS, ROOT, HEADER], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    seen = {}
+    for line in r.stdout.splitlines():
+        name, ret, value = line.split(" ", 2)
+        seen[name] = (ret, value)
+    expected = [n for n in declared_functions()
+                if n not in ("elas_measure_fma_peak", "elas_launch_count", "elas_autotune_dump",
+                             "elas_autotune_load", "elas_solve_opts_default")]
+    assert sorted(seen) == sorted(expected)
+    for name, (ret, value) in seen.items():
+        if ret == "int":
+            assert value == "-1", (name, value)          # ELAS_ERR_INVALID_ARG
+        elif ret == "size_t":
+            assert value == "0", (name, value)
+        else:
+            assert value not in ("None", ""), (name, value)   # elas_last_error: a message
