@@ -1187,39 +1187,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_residual_df(Lv<dfloat> L, const d
     residual_df_block<KIND, NORM, HM, NPT>(L, u, f, nf, lam, r, partials, blockIdx.x);
 }
 
-// A double as a double-float pair from its bits alone (no FP64 or conversion instruction:
-// on this GPU those share the narrow FP64 pipe).  IEEE-754 binary64 v = (-1)^s 1.m 2^(e-1023)
-// with a 52-bit m: hi keeps the leading 24 significant bits (truncated), re-biased to the
-// binary32 exponent e - 896; lo is the rest, the next 23 bits below hi's last one, formed
-// as (1.f - 1) 2^(e-896-127-23) by one exact FP32 subtraction.  |v - (hi + lo)| < 2^-46 |v|.
-// |v| below 2^-103 keeps lo = 0 and below 2^-126 gives (0, 0): far under any value of the
-// fields split here (moduli, displacements, loads).
-__device__ __forceinline__ dfloat df_split(double v) {
-    const unsigned h32 = (unsigned)__double2hiint(v), l32 = (unsigned)__double2loint(v);
-    const int e = (int)((h32 >> 20) & 0x7ffu);
-    if (e < 897) return dfloat(0.f, 0.f);
-    const unsigned hb = (__funnelshift_l(l32, h32, 3) - 0xC0000000u) | (h32 & 0x80000000u);
-    float lo = 0.f;
-    if (e >= 920) {
-        const unsigned base = (hb & 0x7f800000u) - (23u << 23);
-        const float one = __uint_as_float(base);
-        const float lf = __uint_as_float(base | ((l32 >> 6) & 0x7fffffu));
-        lo = __fsub_rn(lf, one);
-        if (h32 & 0x80000000u) lo = -lo;
-    }
-    return dfloat(__uint_as_float(hb), lo);
-}
-
-// An FP32 value as a double from its bits (exact; FP32 subnormals, far below any
-// correction, read as zero), without a conversion instruction.
-__device__ __forceinline__ double f2d_bits(float x) {
-    const unsigned b = __float_as_uint(x);
-    const unsigned ex = (b >> 23) & 0xffu;
-    if (ex == 0) return 0.0;
-    const unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-    return __hiloint2double((int)hi, (int)(b << 29));
-}
-
 template <typename TE>
 __device__ __forceinline__ void add_correction_df_body(const Lv<double>& L, double* __restrict__ u,
                                                        const TE* __restrict__ e, dfloat* __restrict__ u2, int p) {
