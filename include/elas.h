@@ -105,6 +105,8 @@ typedef struct {
  * cudaStream_t (NULL = a stream created and owned by the context). */
 int  elas_ctx_create(elas_ctx* out, int device, size_t hbm_budget_bytes,
                      const elas_allocator* alloc, void* stream);
+/* Destroy the context's servers, AMR layouts and grids first: ELAS_ERR_STATE while a
+ * server of the context is alive. */
 int  elas_ctx_destroy(elas_ctx ctx);
 const char* elas_last_error(elas_ctx ctx);
 /* Bytes currently held by the context. */
@@ -129,6 +131,8 @@ typedef struct {
  * bottom level of at most 6000 unknowns (e.g. n = 2^k m + 1 with small m).  All
  * boundary types default to Dirichlet 0. */
 int  elas_grid_create(elas_ctx ctx, const elas_grid_desc* desc, elas_grid* out);
+/* ELAS_ERR_STATE while a server holds a waiting or active request on the grid (as the
+ * request's grid or a level of its AMR layout); the grid stays valid. */
 int  elas_grid_destroy(elas_grid g);
 /* Number of multigrid levels and the node counts of one of them. */
 int  elas_grid_levels(elas_grid g, int* nlevels);
@@ -370,6 +374,8 @@ int  elas_amr_create(elas_grid* grids, const elas_amr_level* levels, int nlevels
 #define ELAS_AMR_R1 1
 #define ELAS_AMR_R2 2
 int  elas_amr_set_reading(elas_amr a, int reading);
+/* Releases the layout's own buffers (not its grids); ELAS_ERR_STATE while a server holds
+ * a waiting or active request on it. */
 int  elas_amr_destroy(elas_amr a);
 int  elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* info);
 

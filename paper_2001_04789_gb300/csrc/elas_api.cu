@@ -40,7 +40,13 @@ struct elas_ctx_s {
     std::vector<cudaStream_t> branch;        // streams of the batched graph's branches
     std::vector<cudaEvent_t> branch_ev;
     struct BatchPlan* plan = nullptr;         // the batched engine's last plan and graph
+    std::vector<elas_server_s*> servers;      // live servers (their requests hold grids)
 };
+
+// Whether a live server of the context holds a waiting or active request on grid g (as
+// its grid or as a level of its AMR layout) or on AMR layout a; such objects must not be
+// destroyed until the request retires.
+bool server_holds(elas_ctx c, elas_grid g, elas_amr a);
 
 namespace {
 
@@ -1030,6 +1036,7 @@ int elas_ctx_create(elas_ctx* out, int device, size_t hbm_budget_bytes, const el
 
 int elas_ctx_destroy(elas_ctx c) {
     if (!c) return ELAS_ERR_INVALID_ARG;
+    if (!c->servers.empty()) return set_err(c, ELAS_ERR_STATE, "the context has live servers");
     cudaStreamSynchronize(c->stream);
     plan_free(c, c->plan);
     c->plan = nullptr;
@@ -1144,6 +1151,8 @@ int elas_grid_create(elas_ctx c, const elas_grid_desc* d, elas_grid* out) {
 int elas_grid_destroy(elas_grid g) {
     if (!g) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = g->ctx;
+    if (server_holds(c, g, nullptr))
+        return set_err(c, ELAS_ERR_STATE, "grid has a waiting or active server request");
     cudaStreamSynchronize(c->stream);
     if (plan_has_member(c->plan, g)) {
         plan_free(c, c->plan);
@@ -1770,12 +1779,12 @@ extern "C" {
 int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_solve_info* info) {
     if (!grids || n < 0 || !opts || !info) return ELAS_ERR_INVALID_ARG;
     if (n == 0) return ELAS_OK;
+    for (int i = 0; i < n; ++i)
+        if (!grids[i]) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = grids[0]->ctx;
     bool batched = opts->precision == ELAS_PRECISION_MIXED && (n > 1 || opts->use_graph);
-    for (int i = 0; i < n; ++i) {
-        if (!grids[i]) return ELAS_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
         if (grids[i]->ctx != c || !grids[i]->desc.mixed || grids[i]->desc.max_levels == 1) batched = false;
-    }
     if (!batched) {
         int worst = ELAS_OK;
         elas_solve_opts one = *opts;
@@ -2630,6 +2639,8 @@ int elas_amr_set_reading(elas_amr a, int reading) {
 
 int elas_amr_destroy(elas_amr a) {
     if (!a) return ELAS_ERR_INVALID_ARG;
+    if (!a->g.empty() && server_holds(a->g[0]->ctx, nullptr, a))
+        return set_err(a->g[0]->ctx, ELAS_ERR_STATE, "AMR layout has a waiting or active server request");
     if (!a->g.empty()) {
         elas_ctx c = a->g[0]->ctx;
         cudaStreamSynchronize(c->stream);
@@ -2791,6 +2802,25 @@ struct elas_server_s {
     double* h_norm = nullptr;   // pinned: the composite residual norms of AMR requests, per slot
 };
 
+bool server_holds(elas_ctx c, elas_grid g, elas_amr a) {
+    auto holds = [&](const ServerReq& r) {
+        if (a && r.a == a) return true;
+        if (!g) return false;
+        if (r.g == g) return true;
+        if (r.a)
+            for (auto lg : r.a->g)
+                if (lg == g) return true;
+        return false;
+    };
+    for (auto s : c->servers) {
+        for (const auto& r : s->waiting)
+            if (holds(r)) return true;
+        for (const auto& r : s->active)
+            if (holds(r)) return true;
+    }
+    return false;
+}
+
 extern "C" {
 
 int elas_server_create(elas_ctx c, int max_active, elas_server* out) {
@@ -2815,6 +2845,7 @@ int elas_server_create(elas_ctx c, int max_active, elas_server* out) {
         delete s;
         return set_err(c, ELAS_ERR_DEVICE, "server: pinned host buffer");
     }
+    c->servers.push_back(s);
     *out = s;
     return ELAS_OK;
 }
@@ -2826,6 +2857,8 @@ int elas_server_destroy(elas_server s) {
         for (auto& v : r.g->lv) v.L64.active = v.L32.active = nullptr;
     ctx_free(s->ctx, s->mem, s->bytes);
     if (s->h_norm) cudaFreeHost(s->h_norm);
+    auto& sv = s->ctx->servers;
+    sv.erase(std::remove(sv.begin(), sv.end(), s), sv.end());
     delete s;
     return ELAS_OK;
 }
