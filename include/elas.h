@@ -132,7 +132,8 @@ typedef struct {
  * boundary types default to Dirichlet 0. */
 int  elas_grid_create(elas_ctx ctx, const elas_grid_desc* desc, elas_grid* out);
 /* ELAS_ERR_STATE while a server holds a waiting or active request on the grid (as the
- * request's grid or a level of its AMR layout); the grid stays valid. */
+ * request's grid or a level of its AMR layout) or while a live AMR layout holds it as a
+ * level (destroy the layout first); the grid then stays valid. */
 int  elas_grid_destroy(elas_grid g);
 /* Number of multigrid levels and the node counts of one of them. */
 int  elas_grid_levels(elas_grid g, int* nlevels);

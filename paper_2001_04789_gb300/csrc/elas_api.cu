@@ -144,6 +144,7 @@ struct elas_grid_s {
     int cycle = ELAS_CYCLE_V;
     double omega = 2.0 / 3.0;
     std::vector<std::pair<void*, size_t>> allocs;
+    int amr_refs = 0;   // live AMR layouts that hold the grid as a level
     // captured multigrid cycles (see run_cycle), keyed by precision, level, start and cycle
     // type, valid for the set-up, launch-shape table, options and stream they were
     // captured with
@@ -1153,6 +1154,7 @@ int elas_grid_destroy(elas_grid g) {
     elas_ctx c = g->ctx;
     if (server_holds(c, g, nullptr))
         return set_err(c, ELAS_ERR_STATE, "grid has a waiting or active server request");
+    if (g->amr_refs > 0) return set_err(c, ELAS_ERR_STATE, "grid is a level of a live AMR layout");
     cudaStreamSynchronize(c->stream);
     if (plan_has_member(c->plan, g)) {
         plan_free(c, c->plan);
@@ -2350,6 +2352,7 @@ struct elas_amr_s {
     std::vector<std::pair<void*, size_t>> allocs;
     double* partials = nullptr;
     size_t npart = 0;
+    bool holds_refs = false;   // counted in its grids' amr_refs (from a successful create)
 };
 
 namespace {
@@ -2551,9 +2554,11 @@ extern "C" {
 
 int elas_amr_create(elas_grid* grids, const elas_amr_level* levels, int nlevels, elas_amr* out) {
     if (!grids || !levels || nlevels < 1 || !out) return ELAS_ERR_INVALID_ARG;
+    for (int l = 0; l < nlevels; ++l)
+        if (!grids[l]) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = grids[0]->ctx;
     for (int l = 0; l < nlevels; ++l) {
-        if (!grids[l] || grids[l]->ctx != c) return set_err(c, ELAS_ERR_INVALID_ARG, "AMR grids must share a context");
+        if (grids[l]->ctx != c) return set_err(c, ELAS_ERR_INVALID_ARG, "AMR grids must share a context");
         if (grids[l]->K != grids[0]->K) return set_err(c, ELAS_ERR_INVALID_ARG, "AMR levels need one moduli kind");
         if (l > 0 && grids[l]->desc.max_levels != 1)
             return set_err(c, ELAS_ERR_INVALID_ARG, "AMR levels above 0 must be created with max_levels = 1");
@@ -2606,6 +2611,8 @@ int elas_amr_create(elas_grid* grids, const elas_amr_level* levels, int nlevels,
         elas_amr_destroy(a);
         return rc;
     }
+    for (auto g : a->g) ++g->amr_refs;
+    a->holds_refs = true;
     *out = a;
     return ELAS_OK;
 }
@@ -2647,6 +2654,8 @@ int elas_amr_destroy(elas_amr a) {
         for (auto& p : a->allocs) ctx_free(c, p.first, p.second);
         cudaStreamSynchronize(c->stream);
     }
+    if (a->holds_refs)
+        for (auto g : a->g) --g->amr_refs;
     delete a;
     return ELAS_OK;
 }
