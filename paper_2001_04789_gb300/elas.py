@@ -286,8 +286,9 @@ class Context:
         return lib().elas_ctx_bytes_in_use(self.h)
 
     def close(self):
+        """Destroy the context (its servers first: the library refuses while one is alive)."""
         if getattr(self, "h", None):
-            lib().elas_ctx_destroy(self.h)
+            self.check(lib().elas_ctx_destroy(self.h))
             self.h = None
 
 
@@ -514,8 +515,10 @@ class Grid:
         return list(t)
 
     def close(self):
+        """Destroy the grid; refused (ElasError, the grid stays usable) while a server holds a
+        request on it or an AMR layout holds it as a level."""
         if getattr(self, "h", None):
-            lib().elas_grid_destroy(self.h)
+            self.ctx.check(lib().elas_grid_destroy(self.h))
             self.h = None
 
 
@@ -617,9 +620,18 @@ class Amr:
                 descs[i].ghost[f] = int(sp.ghost[f])
         arr = (C.c_void_p * len(specs))(*[g.h for g in self.grids])
         h = C.c_void_p()
-        ctx.check(lib().elas_amr_create(arr, descs, len(specs), C.byref(h)))
+        try:
+            ctx.check(lib().elas_amr_create(arr, descs, len(specs), C.byref(h)))
+        except Exception:
+            for g in self.grids:
+                g.close()
+            raise
         self.h = h
-        ctx.check(lib().elas_amr_set_reading(self.h, {"R1": 1, "R2": 2}[reading]))
+        try:
+            ctx.check(lib().elas_amr_set_reading(self.h, {"R1": 1, "R2": 2}[reading]))
+        except Exception:
+            self.close()          # a refused reading leaves no layout or grids behind
+            raise
 
     def solve(self, rel_tol=1e-8, max_cycles=200, nu1=2, nu2=2, fixed_cycles=0, raise_on_error=True,
               precision=FP64):
@@ -634,8 +646,10 @@ class Amr:
         return [g.displacement() for g in self.grids]
 
     def close(self):
+        """Destroy the layout, then its level grids; refused (ElasError) while a server holds
+        a request on it."""
         if getattr(self, "h", None):
-            lib().elas_amr_destroy(self.h)
+            self.ctx.check(lib().elas_amr_destroy(self.h))
             self.h = None
         for g in self.grids:
             g.close()
