@@ -32,7 +32,8 @@
  *     have no faces.
  *   - memspace: ELAS_HOST for host pointers (copied during the call),
  *     ELAS_DEVICE for device pointers on the context's device (read during the
- *     call only, ordered on the context's stream).
+ *     call only, ordered on the context's stream); any other value is
+ *     ELAS_ERR_INVALID_ARG.
  *   - Every function returns ELAS_OK (0) or a negative error code; the message of
  *     the last error on a context is returned by elas_last_error.
  *   - The library owns all device memory it allocates, through the allocator

@@ -1187,7 +1187,7 @@ size_t elas_grid_bytes(elas_grid g) {
 }
 
 int elas_set_moduli(elas_grid g, const double* comps, int memspace) {
-    if (!g || !comps) return ELAS_ERR_INVALID_ARG;
+    if (!g || !comps || (memspace != ELAS_HOST && memspace != ELAS_DEVICE)) return ELAS_ERR_INVALID_ARG;
     int rc = copy_in(g->ctx, g->lv[0].mod64, comps, (size_t)g->K * g->lv[0].N, memspace);
     if (rc) return rc;
     g->moduli_set = true;
@@ -1199,6 +1199,7 @@ int elas_set_moduli(elas_grid g, const double* comps, int memspace) {
 // the grid and serves the next set of the same input, so clearing and setting again
 // allocates nothing.
 static int set_field(elas_grid g, double** slot, const double* src, size_t count, int memspace) {
+    if (src && memspace != ELAS_HOST && memspace != ELAS_DEVICE) return ELAS_ERR_INVALID_ARG;
     g->rhs_dirty = true;
     if (!src) {
         if (*slot) g->kept[slot] = *slot;
@@ -1404,7 +1405,7 @@ int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) 
 }
 
 int elas_get_displacement(elas_grid g, double* out, int memspace) {
-    if (!g || !out) return ELAS_ERR_INVALID_ARG;
+    if (!g || !out || (memspace != ELAS_HOST && memspace != ELAS_DEVICE)) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = g->ctx;
     CUDA_TRY(c, cudaMemcpyAsync(out, g->lv[0].u, sizeof(double) * 3 * (size_t)g->lv[0].N,
                                 memspace == ELAS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
@@ -1413,7 +1414,7 @@ int elas_get_displacement(elas_grid g, double* out, int memspace) {
 }
 
 int elas_get_stress(elas_grid g, double* out, int memspace) {
-    if (!g || !out) return ELAS_ERR_INVALID_ARG;
+    if (!g || !out || (memspace != ELAS_HOST && memspace != ELAS_DEVICE)) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = g->ctx;
     cudaSetDevice(c->device);
     if (!g->moduli_set) return set_err(c, ELAS_ERR_STATE, "moduli not set");
@@ -1440,7 +1441,7 @@ int elas_get_stress(elas_grid g, double* out, int memspace) {
 }
 
 int elas_set_displacement(elas_grid g, const double* in, int memspace) {
-    if (!g || !in) return ELAS_ERR_INVALID_ARG;
+    if (!g || !in || (memspace != ELAS_HOST && memspace != ELAS_DEVICE)) return ELAS_ERR_INVALID_ARG;
     return copy_in(g->ctx, g->lv[0].u, in, (size_t)3 * g->lv[0].N, memspace);
 }
 
