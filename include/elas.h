@@ -393,7 +393,8 @@ int  elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* in
  * (cached on the context until a member is destroyed, set up anew, or gets new loads)
  * and replayed until every member has stopped on its own tolerance (device-side flags).
  * Other batches run each member's own launches as parallel graph branches.  Every member
- * computes exactly what its lone elas_solve computes.  info has n entries. */
+ * computes exactly what its lone elas_solve computes.  info has n entries.  A grid listed
+ * twice is ELAS_ERR_INVALID_ARG. */
 int  elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts,
                       elas_solve_info* info);
 

@@ -1785,6 +1785,13 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
     for (int i = 0; i < n; ++i)
         if (!grids[i]) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = grids[0]->ctx;
+    {
+        // members share nothing: a grid listed twice would have two solves in its buffers
+        std::vector<elas_grid> sorted(grids, grids + n);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+            return set_err(c, ELAS_ERR_INVALID_ARG, "a grid appears twice in the batch");
+    }
     bool batched = opts->precision == ELAS_PRECISION_MIXED && (n > 1 || opts->use_graph);
     for (int i = 0; i < n; ++i)
         if (grids[i]->ctx != c || !grids[i]->desc.mixed || grids[i]->desc.max_levels == 1) batched = false;
