@@ -2565,6 +2565,9 @@ int elas_amr_create(elas_grid* grids, const elas_amr_level* levels, int nlevels,
     for (int l = 0; l < nlevels; ++l)
         if (!grids[l]) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = grids[0]->ctx;
+    for (int l = 0; l < nlevels; ++l)
+        for (int k = 0; k < l; ++k)
+            if (grids[k] == grids[l]) return set_err(c, ELAS_ERR_INVALID_ARG, "one grid given for two AMR levels");
     for (int l = 0; l < nlevels; ++l) {
         if (grids[l]->ctx != c) return set_err(c, ELAS_ERR_INVALID_ARG, "AMR grids must share a context");
         if (grids[l]->K != grids[0]->K) return set_err(c, ELAS_ERR_INVALID_ARG, "AMR levels need one moduli kind");
