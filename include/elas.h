@@ -409,7 +409,10 @@ int  elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts,
  * request whose set-up fails at admission (e.g. no moduli set) takes no slot: it
  * retires at once and polls as done with that error in info->status.  Results are the
  * same as a lone elas_solve with the same options (same kernels in the same
- * order per grid). */
+ * order per grid).  While a request on a grid (or on an AMR layout holding it) waits or
+ * runs, calls that launch on that grid or change it -- solves, batches, single
+ * operations, setters, residual queries, stress, autotune, destroy -- return
+ * ELAS_ERR_STATE; reading its displacement stays allowed. */
 typedef struct elas_server_s* elas_server;
 int  elas_server_create(elas_ctx ctx, int max_active, elas_server* out);
 int  elas_server_destroy(elas_server s);

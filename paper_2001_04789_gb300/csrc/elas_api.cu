@@ -168,6 +168,15 @@ int set_err(elas_ctx c, int code, const std::string& msg) {
     return code;
 }
 
+// Calls that launch on a grid or change it are refused while a server request holds the
+// grid: an admitted request keeps its per-grid state (activity flags, iterate, loads) in
+// the grid between server steps, and a waiting one is solved from the grid as it will be.
+int refuse_if_served(elas_grid g) {
+    return server_holds(g->ctx, g, nullptr)
+               ? set_err(g->ctx, ELAS_ERR_STATE, "grid has a waiting or active server request")
+               : ELAS_OK;
+}
+
 #define CUDA_TRY(ctx, call)                                                                      \
     do {                                                                                         \
         cudaError_t e_ = (call);                                                                 \
@@ -1188,6 +1197,7 @@ size_t elas_grid_bytes(elas_grid g) {
 
 int elas_set_moduli(elas_grid g, const double* comps, int memspace) {
     if (!g || !comps || (memspace != ELAS_HOST && memspace != ELAS_DEVICE)) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     int rc = copy_in(g->ctx, g->lv[0].mod64, comps, (size_t)g->K * g->lv[0].N, memspace);
     if (rc) return rc;
     g->moduli_set = true;
@@ -1200,6 +1210,7 @@ int elas_set_moduli(elas_grid g, const double* comps, int memspace) {
 // allocates nothing.
 static int set_field(elas_grid g, double** slot, const double* src, size_t count, int memspace) {
     if (src && memspace != ELAS_HOST && memspace != ELAS_DEVICE) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     g->rhs_dirty = true;
     if (!src) {
         if (*slot) g->kept[slot] = *slot;
@@ -1231,6 +1242,7 @@ int elas_set_body_force(elas_grid g, const double* b3, int memspace) {
 
 int elas_set_mean_strain(elas_grid g, const double eps6[6]) {
     if (!g || !eps6) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     if (!(g->desc.periodic[0] && g->desc.periodic[1] && g->desc.periodic[2]))
         return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "mean strain needs a fully periodic grid");
     for (int k = 0; k < 6; ++k) g->mean[k] = eps6[k];
@@ -1241,6 +1253,7 @@ int elas_set_mean_strain(elas_grid g, const double eps6[6]) {
 
 int elas_set_bc(elas_grid g, int face, int comp, int type, double value) {
     if (!g || face < 0 || face > 5 || comp < 0 || comp > 2) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     if (type != ELAS_BC_DIRICHLET && type != ELAS_BC_TRACTION && type != ELAS_BC_NEUMANN)
         return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "unknown boundary type");
     const bool changed = g->bc_type[face][comp] != type;
@@ -1296,6 +1309,7 @@ int take_cycle_opts(elas_grid g, const elas_solve_opts* o) {
 
 int elas_solve(elas_grid g, const elas_solve_opts* opts, elas_solve_info* info) {
     if (!g || !opts || !info) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     elas_ctx c = g->ctx;
     cudaSetDevice(c->device);
     std::memset(info, 0, sizeof(*info));
@@ -1415,6 +1429,7 @@ int elas_get_displacement(elas_grid g, double* out, int memspace) {
 
 int elas_get_stress(elas_grid g, double* out, int memspace) {
     if (!g || !out || (memspace != ELAS_HOST && memspace != ELAS_DEVICE)) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     elas_ctx c = g->ctx;
     cudaSetDevice(c->device);
     if (!g->moduli_set) return set_err(c, ELAS_ERR_STATE, "moduli not set");
@@ -1442,11 +1457,13 @@ int elas_get_stress(elas_grid g, double* out, int memspace) {
 
 int elas_set_displacement(elas_grid g, const double* in, int memspace) {
     if (!g || !in || (memspace != ELAS_HOST && memspace != ELAS_DEVICE)) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     return copy_in(g->ctx, g->lv[0].u, in, (size_t)3 * g->lv[0].N, memspace);
 }
 
 int elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2) {
     if (!g) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     int rc = setup(g);
     if (rc) return rc;
     elas_ctx c = g->ctx;
@@ -1469,6 +1486,7 @@ int elas_query_residual(elas_grid g, double* rel_l2, double* abs_l2) {
 
 int elas_query_residual_inf(elas_grid g, double* rel_inf, double* abs_inf) {
     if (!g) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     int rc = setup(g);
     if (rc) return rc;
     elas_ctx c = g->ctx;
@@ -1492,6 +1510,7 @@ int elas_query_residual_inf(elas_grid g, double* rel_inf, double* abs_inf) {
 // ---- single operations ----------------------------------------------------------------
 static int check_level(elas_grid g, int level, int precision, bool allow_df = false) {
     if (!g) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     if (level < 0 || level >= (int)g->lv.size()) return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "bad level");
     if (precision < 0 || precision > (allow_df ? ELAS_OP_DF : 1))
         return set_err(g->ctx, ELAS_ERR_INVALID_ARG, "bad precision");
@@ -1749,6 +1768,7 @@ unsigned long long elas_launch_count(void) { return elas::launch_count(); }
 
 int elas_autotune(elas_grid g, float* times_ms, int ntimes) {
     if (!g) return ELAS_ERR_INVALID_ARG;
+    if (int rc = refuse_if_served(g)) return rc;
     int rc = setup(g);
     if (rc) return rc;
     elas_ctx c = g->ctx;
@@ -1784,6 +1804,8 @@ int elas_batch_solve(elas_grid* grids, int n, const elas_solve_opts* opts, elas_
     if (n == 0) return ELAS_OK;
     for (int i = 0; i < n; ++i)
         if (!grids[i]) return ELAS_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (int rc = refuse_if_served(grids[i])) return rc;
     elas_ctx c = grids[0]->ctx;
     {
         // members share nothing: a grid listed twice would have two solves in its buffers
@@ -2713,6 +2735,10 @@ extern "C" {
 int elas_amr_solve(elas_amr a, const elas_solve_opts* opts, elas_solve_info* info) {
     if (!a || !opts || !info) return ELAS_ERR_INVALID_ARG;
     elas_ctx c = a->g[0]->ctx;
+    if (server_holds(c, nullptr, a))
+        return set_err(c, ELAS_ERR_STATE, "AMR layout has a waiting or active server request");
+    for (auto lg : a->g)
+        if (int rc = refuse_if_served(lg)) return rc;
     cudaSetDevice(c->device);
     std::memset(info, 0, sizeof(*info));
     const auto t0 = std::chrono::steady_clock::now();
