@@ -1,6 +1,6 @@
 """Host-side logic of the C library that needs no GPU: the smoother's tuning table
 (text round trip, rejection of unknown launch shapes), the HBM estimate used for
-admission by the serving loop, and the binding's checks of single-operation arguments."""
+admission by the serving loop, the binding's checks of single-operation arguments, and the serving loop's resident cache."""
 import pytest
 
 from paper_2001_04789_gb300 import microstructure as M
@@ -107,3 +107,50 @@ def test_single_operation_arguments_are_checked_before_the_library(E):
     assert E.op_dtype(E.MIXED) == torch.float32
     assert E.op_dtype(E.OP_DF) == torch.float64 and E.op_dtype(E.OP_DF, output=True) == torch.float32
     assert E.op_dtype(7) is None
+
+
+def test_resident_cache_evicts_idle_hierarchies_least_recently_used(monkeypatch):
+    """The serving loop's resident cache (host logic only, with stand-ins for the library):
+    a hit moves the entry to the most recent end; admitting an entry that would exceed the
+    HBM budget evicts idle entries, least recently used first, until it fits, and never a
+    busy one; when only busy entries remain the new one waits (None)."""
+    import types
+    from paper_2001_04789_gb300 import serve
+
+    closed = []
+
+    class FakeGrid:
+        def __init__(self, ctx, p):
+            self.ctx, self.p = ctx, p
+            ctx.used += p.bytes
+
+        def close(self):
+            closed.append(self.p.name)
+            self.ctx.used -= self.p.bytes
+
+    class FakeCtx:
+        used = 0
+
+        def bytes_in_use(self):
+            return self.used
+
+    fake_lib = types.SimpleNamespace(elas_grid_bytes_estimate=lambda d: d.bytes)
+    fake_E = types.SimpleNamespace(lib=lambda: fake_lib, desc_for=lambda p, mixed=True: p,
+                                   grid_from_problem=lambda ctx, p, mixed=True: FakeGrid(ctx, p),
+                                   Amr=None)
+    monkeypatch.setattr(serve, "E", fake_E)
+    prob = lambda name, b: types.SimpleNamespace(name=name, bytes=b)
+    ctx = FakeCtx()
+    cache = serve.ResidentCache(ctx, budget=100)
+    for name in "abc":
+        assert cache.get(name, lambda name=name: prob(name, 30)) is not None
+    assert ctx.used == 90 and closed == []
+    cache.get("a", lambda: prob("a", 30))                 # hit: a becomes the most recent
+    cache.busy.add("b")
+    g, _ = cache.get("d", lambda: prob("d", 30))          # needs 30: evicts c (b is busy, a recent)
+    assert closed == ["c"] and list(cache.grids) == ["b", "a", "d"] and ctx.used == 90
+    g, _ = cache.get("e", lambda: prob("e", 40))          # needs 40: evicting a is enough
+    assert closed == ["c", "a"] and list(cache.grids) == ["b", "d", "e"] and ctx.used == 100
+    cache.busy.add("e")
+    assert cache.get("f", lambda: prob("f", 50)) is None   # evicts idle d, then only busy ones: wait
+    assert closed == ["c", "a", "d"] and list(cache.grids) == ["b", "e"] and ctx.used == 70
