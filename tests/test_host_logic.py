@@ -1,6 +1,7 @@
-"""Host-side logic of the C library that needs no GPU: the smoother's tuning table
-(text round trip, rejection of unknown launch shapes), the HBM estimate used for
-admission by the serving loop, the binding's checks of single-operation arguments, and the serving loop's resident cache."""
+"""Host-side logic that needs no GPU: the smoother's tuning table (text round trip,
+rejection of unknown launch shapes), the HBM estimate used for admission by the serving
+loop, the binding's checks of single-operation arguments, and the serving loop's
+resident cache."""
 import pytest
 
 from paper_2001_04789_gb300 import microstructure as M
