@@ -176,3 +176,37 @@ def test_mixed_amr_request_is_the_same_alone_and_in_the_mix(E):
     amr.close()
     g.close()
     ctx.close()
+
+
+def test_a_grid_held_by_a_request_refuses_solves_setters_and_queries(E):
+    """While a request on a grid waits or runs, calls that would launch on the grid or
+    change it are refused with ELAS_ERR_STATE before touching the device (the request keeps
+    its activity flags and iterate in the grid between steps); reading the displacement
+    stays allowed, and once the request retires the grid solves again, with the same
+    result as the request."""
+    ctx = E.Context(0)
+    g = E.grid_from_problem(ctx, M.eshelby_sphere(17), mixed=True)
+    server = E.Server(ctx, max_active=1)
+    ticket = server.submit(g, rel_tol=1e-8)
+    refused = (lambda: g.solve(precision=E.MIXED, rel_tol=1e-8),
+               lambda: g.set_bc(0, 0, M.DIRICHLET, 0.0),
+               lambda: g.query_residual())
+    done = None
+    for step in range(500):
+        for call in refused:                    # waiting (step 0), then active
+            with pytest.raises(E.ElasError) as err:
+                call()
+            assert err.value.code == E.ERR_STATE
+        g.displacement()
+        server.step()
+        done = server.poll(ticket)
+        if done is not None:
+            break
+    assert done is not None and done[0]["status"] == 0
+    served = g.displacement()
+    info = g.solve(precision=E.MIXED, rel_tol=1e-8)
+    assert info["status"] == 0 and info["cycles"] == done[0]["cycles"]
+    assert np.abs(g.displacement() - served).max() <= 1e-14 * np.abs(served).max()
+    server.close()
+    g.close()
+    ctx.close()
