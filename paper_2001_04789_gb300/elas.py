@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libelas_gb300.so")
 
 OK = 0
+ERR_INVALID_ARG = -1
 ERR_NOT_CONVERGED = -3
 ERR_DIVERGED = -4
 ERR_STATE = -7

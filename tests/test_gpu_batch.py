@@ -135,3 +135,15 @@ def test_engine_plan_follows_new_loads(E, ctx):
     assert np.array_equal(grids[0].displacement(), ub) and alone["cycles"] == infos[0]["cycles"]
     for g in grids:
         g.close()
+
+
+def test_a_grid_listed_twice_is_refused(E, ctx):
+    """Members share nothing: a grid listed twice (its two solves would share one set of
+    buffers) is an invalid argument, refused before any launch; the grid stays usable."""
+    g = E.grid_from_problem(ctx, M.ellipsoid_rve(17, seed=3), mixed=True)
+    with pytest.raises(E.ElasError) as err:
+        E.batch_solve([g, g], precision=E.MIXED, rel_tol=1e-8)
+    assert err.value.code == E.ERR_INVALID_ARG
+    info = E.batch_solve([g], precision=E.MIXED, rel_tol=1e-8)[0]
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+    g.close()
