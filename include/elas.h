@@ -322,15 +322,20 @@ unsigned long long elas_launch_count(void);
  * of interior nodes with (threads per block, minimum resident blocks per SM) =
  * (256,1) (256,2) (256,3) (256,4) (128,8), the second number bounding registers per
  * thread (levels with FP16 moduli use shapes 1 and 2 only); 5 and 6 stage moduli and
- * displacement planes of a 32 x 16 (resp. 32 x 8)
- * tile in shared memory and march through z (FP32 levels with FP32 moduli only;
- * identical arithmetic, so every shape gives bitwise-equal results).  elas_autotune
+ * displacement planes of a 32 x 16 (resp. 32 x 8) tile in shared memory and march
+ * through z (FP32 levels with blocked FP32 moduli); 7 and 8 march 32 x 16 (resp. 32 x 8)
+ * tiles through z with every global read an asynchronous copy one plane ahead (FP32
+ * levels with colour-split moduli).  The arithmetic is identical, so every shape gives
+ * bitwise-equal results.  elas_autotune
  * times each shape on every level of the grid, in FP32 (mixed grids) and FP64,
  * and keeps the fastest per (level dimensions, moduli kind, precision) in a
  * process-wide table used by every later launch.  times_ms (optional) receives
  * the FP32 timings of the finest level, one per shape (-1 where a shape does not
  * apply).  The table can be saved
- * and restored as text (one "nx ny nz kind bytes divc shape" line per entry). */
+ * and restored as text: one "nx ny nz kind bytes layout shape" line per entry, bytes the
+ * element size (4 or 8), layout 0 for moduli stored plainly, 1 with the precomputed
+ * modulus divergence, 2 for colour-split records.  A line naming an unknown shape is
+ * skipped. */
 int  elas_autotune(elas_grid g, float* times_ms, int ntimes);
 int  elas_autotune_dump(char* buf, int cap);   /* returns the text length */
 int  elas_autotune_load(const char* text);     /* returns the entries read */

@@ -37,7 +37,7 @@ constexpr int kNumSweepVariants = 9;
 constexpr int kDefaultSweepVariant = 0;
 template <typename T>
 int tune_sweep(const Lv<T>& L, const T* u_in, T* u_out, const T* f, cudaStream_t s, float* ms_out);
-int tune_lookup(const std::array<int, 6>& key, int fallback);   // key: nx ny nz K bytes divc
+int tune_lookup(const std::array<int, 6>& key, int fallback);   // key: nx ny nz K bytes layout
 void tune_store(const std::array<int, 6>& key, int variant);
 int tune_table_dump(char* buf, int cap);
 int tune_table_load(const char* text);
