@@ -198,7 +198,8 @@ typedef struct {
 typedef struct {
     int    status;                     /* ELAS_OK, ELAS_ERR_NOT_CONVERGED, ...        */
     int    cycles;                     /* coarse-grid corrections performed           */
-    double rel_residual;               /* final ||r||/||r_0||, FP64 residual           */
+    double rel_residual;               /* final ||r||/||r_0|| (FP64, or the refinement
+                                          residual's double-float for mixed solves)     */
     double r0;                         /* ||r_0||: residual of the Dirichlet-only field */
     int    nlam;                       /* number of free rigid modes                  */
     double lam[6];                     /* equilibrating-load coefficients             */
