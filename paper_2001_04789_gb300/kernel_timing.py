@@ -7,8 +7,10 @@ random fields, and prints one JSON line with the mean device time per launch (CU
 events on the library's stream) and the algorithmic and issued bandwidth.  Kernels:
 ``sweep32`` (one FP32 red-black sweep = two half-sweep launches), ``resid32`` (FP32
 residual), ``resid64`` (FP64 residual), ``residdf`` (the double-float refinement
-residual; each call also splits u and f into double-float copies, two more launches).  It is also the small profiling target for
-ncu captures of these kernels.
+residual; each call also splits u and f into double-float copies, two more launches),
+``restrict32`` (FP32 full-weighting restriction of level 0 to level 1) and ``prolong32``
+(FP32 trilinear prolongation of a level-1 correction added to level 0).  It is also the
+small profiling target for ncu captures of these kernels.
 """
 from __future__ import annotations
 
@@ -21,7 +23,7 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=129)
-    ap.add_argument("--kernel", default="sweep32", choices=["sweep32", "resid32", "resid64", "residdf"])
+    ap.add_argument("--kernel", default="sweep32", choices=["sweep32", "resid32", "resid64", "residdf", "restrict32", "prolong32"])
     ap.add_argument("--shape", type=int, default=3, help="smoother launch shape (autotuner index)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--grains", type=int, default=10)
@@ -33,8 +35,9 @@ def main():
     from . import microstructure as M
     p = M.polycrystal(a.n, grains=a.grains, seed=0)
     ctx = E.Context(0)
-    # the double-float residual belongs to grids with a hierarchy; the others time level 0 alone
-    g = E.grid_from_problem(ctx, p, mixed=True, max_levels=0 if a.kernel == "residdf" else 1)
+    # the double-float residual and the transfers need the hierarchy; the others time level 0 alone
+    hier = a.kernel in ("residdf", "restrict32", "prolong32")
+    g = E.grid_from_problem(ctx, p, mixed=True, max_levels=0 if hier else 1)
     for flag in (0, 1, 2):
         E.autotune_load(f"{a.n} {a.n} {a.n} 21 4 {flag} {a.shape}")
     rng = np.random.default_rng(0)
@@ -42,11 +45,19 @@ def main():
     prec = {"resid64": E.FP64, "residdf": E.OP_DF}.get(a.kernel, E.MIXED)
     u = torch.as_tensor(rng.normal(size=(3,) + g.shape) * 1e-3, dtype=dt, device="cuda:0")
     f = torch.as_tensor(rng.normal(size=(3,) + g.shape), dtype=dt, device="cuda:0")
+    ec = None
+    if a.kernel == "prolong32":
+        nc = g.level_dims(1)
+        ec = torch.as_tensor(rng.normal(size=(3, nc[2], nc[1], nc[0])) * 1e-3, dtype=dt, device="cuda:0")
     torch.cuda.synchronize()
 
     def once():
         if a.kernel == "sweep32":
             g.op_sweep(0, prec, u, f)
+        elif a.kernel == "restrict32":
+            g.op_restrict(0, prec, f)
+        elif a.kernel == "prolong32":
+            g.op_prolong_add(0, prec, ec, u)
         else:
             g.op_residual(0, prec, u, f)
 
@@ -61,7 +72,10 @@ def main():
     ms = e0.elapsed_time(e1) / a.reps
     N = int(np.prod(p.n))
     launches = 2 if a.kernel == "sweep32" else 1
-    alg = {"sweep32": 120.0, "resid32": 120.0, "resid64": 240.0, "residdf": 240.0}[a.kernel]   # bytes per node per pass
+    # algorithmic bytes per finest node and pass: each array read once, written once (a
+    # coarse node per 8 fine ones)
+    alg = {"sweep32": 120.0, "resid32": 120.0, "resid64": 240.0, "residdf": 240.0,
+           "restrict32": 12.0 + 12.0 / 8, "prolong32": 12.0 / 8 + 24.0}[a.kernel]
     print(json.dumps({"kernel": a.kernel, "n": a.n, "nodes": N, "shape": a.shape, "reps": a.reps,
                       "ms_per_launch": ms / launches, "ms_per_pass": ms,
                       "alg_GBs": alg * N / (ms * 1e-3) / 1e9}), flush=True)
