@@ -237,6 +237,46 @@ def config1_oracle_timed(cores):
                           "mean_seconds_per_solve": statistics.mean(r[0] for r in res)}}
 
 
+def _import_oracle(_):
+    """Import the oracle and the input generators in a worker (untimed warm-up)."""
+    from oracle import multigrid  # noqa: F401
+    from paper_2001_04789_gb300 import microstructure  # noqa: F401
+    return 0
+
+
+def _rve_oracle_solve(args):
+    """One full oracle solve of a periodic ellipsoid RVE to 1e-8 (runs in a worker)."""
+    n, seed = args
+    from oracle import multigrid as MG
+    from paper_2001_04789_gb300 import microstructure as M
+    p = M.ellipsoid_rve(n, seed=seed)
+    t = time.perf_counter()
+    _, info = MG.solve(p, tol=1e-8, max_cycles=200)
+    return time.perf_counter() - t, info.cycles, info.rel_residual
+
+
+def rve_oracle_timed(cores, n=33):
+    """Timed full oracle solves of periodic ellipsoid RVEs of n^3 node planes (the smallest
+    size of the batched workload) to 1e-8: one on one core, then one per core on `cores`
+    spawned single-threaded workers at once (different seeds).  Returns solves/s for both."""
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        t1, cyc, rel = pool.map(_rve_oracle_solve, [(n, 0)])[0]
+    with ctx.Pool(cores) as pool:
+        pool.map(_import_oracle, range(cores))
+        t = time.perf_counter()
+        res = pool.map(_rve_oracle_solve, [(n, s) for s in range(cores)])
+        wall = time.perf_counter() - t
+    return {"workload": f"periodic ellipsoid RVE {n}^3 node planes, V(2,2) to 1e-8, FP64",
+            "cycles": int(cyc), "rel_residual": float(rel),
+            "one_core": {"seconds_per_solve": t1, "solves_per_s": 1.0 / t1},
+            "all_cores": {"cores": cores, "solves": cores, "wall_s": wall, "solves_per_s": cores / wall,
+                          "mean_seconds_per_solve": statistics.mean(r[0] for r in res)}}
+
+
 def cpu_solves_per_second(sec_per_node, n_nodes, cycles, nu1=2, nu2=2):
     # the oracle's half-sweep evaluates every row, so one V(nu1,nu2) cycle costs
     # 2(nu1+nu2)+1 finest-level residual evaluations; coarser levels add 1/7 + ...
@@ -531,10 +571,11 @@ def main():
         v, evals = cpu_solves_per_second(spn, N, fp64_info["cycles"])
         cores = os.cpu_count() or 1
         c1 = config1_oracle_timed(cores)
+        rve = rve_oracle_timed(cores)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "extrapolated": True,
                "sample": desc + f"; extrapolated to {fp64_info['cycles']} V(2,2) cycles "
                                 f"({evals:.0f} residual-evaluation equivalents) of the plain FP64 solve",
-               "config1_timed_full_solve": c1}
+               "config1_timed_full_solve": c1, "rve33_timed_full_solve": rve}
         cfg1["oracle_one_core_solves_per_s"] = c1["one_core"]["solves_per_s"]
         cfg1["oracle_all_cores_solves_per_s"] = c1["all_cores"]["solves_per_s"]
         cfg1["oracle_cores"] = cores

@@ -70,3 +70,14 @@ def test_clock_samples_median_and_throttle_reasons(tmp_path):
     assert out["sm_mhz"] == 1500 and out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
     assert _clocks_from(tmp_path, ["garbage"]) is None
     assert bench.Clocks(0).stop() is None          # never started: no record
+
+
+def test_rve_oracle_timing_reports_one_core_and_all_core_rates():
+    """The CPU baseline's timed oracle solves of a periodic RVE (spawned single-threaded
+    workers): one solve on one core, one per worker at once, each converged to 1e-8."""
+    out = bench.rve_oracle_timed(2, n=9)
+    assert out["cycles"] > 0 and out["rel_residual"] <= 1e-8
+    one, many = out["one_core"], out["all_cores"]
+    assert one["seconds_per_solve"] > 0 and one["solves_per_s"] == 1.0 / one["seconds_per_solve"]
+    assert many["cores"] == many["solves"] == 2 and many["solves_per_s"] == 2 / many["wall_s"]
+    assert many["mean_seconds_per_solve"] > 0
