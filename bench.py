@@ -320,6 +320,21 @@ def amr_penny_crack_timed(E, M, ctx, stream, reps=2):
         return {"error": f"{type(e).__name__}: {e}"}
 
 
+def batch_rve_timed(count=32):
+    """Batched RVE solves (the per-phase engine of elas_batch_solve) on `count` periodic
+    ellipsoid RVEs whose sizes are drawn from {33, 65, 97, 129}^3 node planes like the
+    256-member batch, against the same members solved one after another; on a context of
+    its own, after the headline's timed region."""
+    try:
+        from paper_2001_04789_gb300 import batch as Bt
+        out = Bt.run(count=count)
+        out["workload"] = (f"{count} periodic ellipsoid RVEs, sizes from 33-129^3 node planes, mixed precision "
+                           "to 1e-8; wall clock around each call with a device synchronise on both sides")
+        return out
+    except Exception as e:
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def stress_timed(g, n_nodes, reps=3):
     """The stress output sigma = C : (grad u - eps0) of the benchmark's converged field
     through the public call (the device kernel, then 6 x N doubles copied into pageable host
@@ -564,6 +579,7 @@ def main():
     g1.close()
     amr3 = amr_penny_crack_timed(E, M, ctx, stream)
     stress = stress_timed(g, N)
+    batch32 = batch_rve_timed(32)
 
     cpu = None
     if not args.quick and not args.no_cpu_baseline and world == 1:
@@ -603,7 +619,7 @@ def main():
         "finest_sweeps_per_solve": sweeps_per_solve,
         "dof_updates_per_s": value * 3 * N * sweeps_per_solve if sweeps_per_solve else None,
         "roofline": roof, "alu_peaks": alu, "kernels": kernels, "gpu_launches": int(launches),
-        "eshelby33": cfg1, "amr_penny_crack65": amr3, "stress": stress,
+        "eshelby33": cfg1, "amr_penny_crack65": amr3, "stress": stress, "batch_rve32": batch32,
         "autotune": {"finest_fp32_sweep_ms_per_shape": tune_ms, "table": E.autotune_dump().strip().splitlines()},
         "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
     }

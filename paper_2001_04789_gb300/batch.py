@@ -2,10 +2,12 @@
 
 The members are periodic ellipsoid RVEs of uneven sizes drawn from {33, 65, 97, 129}^3
 node planes (1-8 random ellipsoids each, random symmetric mean strain), all on one
-context. ``elas_batch_solve`` replays a few refinement steps of every member as
-parallel branches of one CUDA graph; each member stops on its own tolerance (FP32
-V-cycles inside FP64 refinement, relative residual 1e-8). For comparison, the same
-members are then solved one after another with ``elas_solve``.
+context. ``elas_batch_solve`` runs each phase of a refinement step (the double-float
+refinement residual, each level's half-sweeps, residual, transfers and bottom solve, the
+corrections) as one launch over a device work list of all members, replays two steps at a
+time from a captured CUDA graph, and stops each member on its own tolerance (FP32 V-cycles
+inside FP64 refinement, relative residual 1e-8). For comparison, the same members are then
+solved one after another with ``elas_solve``.
 
 ``python -m paper_2001_04789_gb300.batch --count 256`` prints one JSON line.
 """
