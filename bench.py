@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--quick", action="store_true", help="skip e2e and the CPU baseline")
+    ap.add_argument("--quick", action="store_true", help="skip e2e, the CPU baseline and the batched RVE run")
     ap.add_argument("--inner", type=int, default=3, help="FP32 V-cycles per FP64 refinement step")
     ap.add_argument("--graph", action="store_true", help="replay refinement steps as a CUDA graph")
     ap.add_argument("--half", action="store_true", help="FP16 moduli in the FP32 V-cycle")
@@ -579,7 +579,7 @@ def main():
     g1.close()
     amr3 = amr_penny_crack_timed(E, M, ctx, stream)
     stress = stress_timed(g, N)
-    batch32 = batch_rve_timed(32)
+    batch32 = batch_rve_timed(32) if not args.quick else None
 
     cpu = None
     if not args.quick and not args.no_cpu_baseline and world == 1:
