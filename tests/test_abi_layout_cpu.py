@@ -1,4 +1,5 @@
-"""The binding's ctypes structures match the C header's, field by field.
+"""The binding's ctypes declarations match the C header: structures field by field, and
+every function's arity and argument kinds.
 
 A small C program, generated from the ctypes field lists and compiled against
 include/elas.h, prints the size of each structure and the offset and size of each field
@@ -71,3 +72,52 @@ def test_option_defaults_and_keyword_mapping(E):
     assert (m.smoother, m.cycle, m.omega, m.outer_residual) == (E.SMOOTH_GS8, E.CYCLE_F, 0.5, E.OUTER_DF)
     d = E._opts()                                   # unset options keep the library's defaults
     assert (d.smoother, d.cycle, d.outer_residual) == (E.SMOOTH_RB, E.CYCLE_V, E.OUTER_AUTO)
+
+
+def _header_prototypes():
+    import re
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "elas.h")).read(), flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\n\s*([A-Za-z_][A-Za-z_ ]*?\**)\s*\b(elas_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        params = [p.strip() for p in m.group(3).split(",") if p.strip() and p.strip() != "void"]
+        protos[m.group(2)] = (m.group(1).strip(), params)
+    return protos
+
+
+def _c_kind(decl, is_return=False):
+    """Category of a C parameter declaration (or return type)."""
+    if "*" in decl or "[" in decl:
+        return "ptr"
+    words = decl.replace("const ", "").split()
+    if not is_return:
+        words = words[:-1]                      # drop the parameter name
+    t = " ".join(words)
+    if t.startswith("elas_") and t not in ("elas_solve_opts", "elas_solve_info"):
+        return "ptr"                            # handles are typedef'd pointers
+    return {"int": "i32", "double": "f64", "size_t": "u64", "unsigned long long": "u64",
+            "long long": "s64", "void": "void"}[t]
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return "void"
+    if t in (C.c_void_p, C.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "ptr"
+    return {C.c_int: "i32", C.c_double: "f64", C.c_size_t: "u64", C.c_ulonglong: "u64",
+            C.c_longlong: "s64"}[t]
+
+
+def test_binding_signatures_match_the_header(E):
+    """Every function elas.h declares has ctypes argument and result types in the binding,
+    with the header's arity and, per argument, the same kind (32-bit int, double, unsigned
+    or signed 64-bit integer, pointer or handle)."""
+    L = E.lib()
+    protos = _header_prototypes()
+    assert len(protos) > 40
+    for name, (ret, params) in protos.items():
+        fn = getattr(L, name)
+        assert fn.argtypes is not None, f"{name}: no ctypes signature in the binding"
+        assert len(fn.argtypes) == len(params), name
+        assert _ctypes_kind(fn.restype) == _c_kind(ret, is_return=True), name
+        for k, (decl, t) in enumerate(zip(params, fn.argtypes)):
+            assert _ctypes_kind(t) == _c_kind(decl), (name, k, decl, t)
